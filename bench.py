@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark of the fused payoff-expression Monte Carlo engine.
+
+One step prices one contract of the selected workload (default: the
+worst-of autocallable note, 3 correlated GBM underlyings, 5 annual dates,
+2^20 paths): Philox normals -> Brownian bridge -> correlated GBM -> payoff
+bytecode -> mean / variance, all in one kernel launch.
+
+Prints one JSON line (rank 0):
+  value   -- path-date evaluations per second over all ranks, kernel time
+             from CUDA events on the launch stream, inputs resident on the
+             device, L2 flushed (256 MiB write) between steps;
+  e2e     -- the same metric through the C ABI as a user calls it: load the
+             payoff bytecode from host memory (host-to-device copy), price,
+             read the result back to the host, release the contract;
+  roofline, cpu_baseline (the FP64 oracle on host cores), clocks, ...
+``--impl reference`` times the oracle instead (the reference arm).
+Multi-GPU (torchrun): each rank prices its own disjoint path range of the
+same contract (no data-path collective; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "path·date evals/sec & contracts priced/sec at 1e-4 rel. std-err vs plain MC"
+UNIT = "path·date/s"
+TARGET_REL_SE = 1e-4
+KERNEL_SRC = os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", "pc_kernels.cu")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def alg_ops_per_path(info) -> dict:
+    """Algorithmic thread-operations of generating one full path (all dates):
+    Philox4x32-10: 10 rounds x (2 mul.lo + 2 mul.hi + 2 three-way xor) = 60;
+    Box-Muller pair: 2 shifts, 2 int->float, 2 FMA (u_a, angle), lg2, mul,
+    sqrt, sin, cos, 2 mul = 13 (4 on the MUFU pipe);
+    bridge: d ops for the first node, 3d for each other node;
+    correlation + GBM per date: d(d+1)/2 FMA + d ex2 + d mul.
+    The payoff's own arithmetic is not counted (a lower bound)."""
+    d, n = info.d, info.n_dates
+    ops = (60 * info.philox_blocks + 13 * info.box_muller_pairs + (3 * n * d - 2 * d)
+           + n * (d * (d + 1) // 2 + 2 * d))
+    mufu = 4 * info.box_muller_pairs + n * d
+    return {"ops": ops, "mufu": mufu}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = open(os.devnull, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                txt, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                txt, _ = self.proc.communicate()
+            self.lines = [l for l in (txt or "").splitlines() if l.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def profile_traffic(workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"price_kernel_{workload}.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        with open(KERNEL_SRC, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if p.get("kernel_sha256") == sha:
+            return p.get("dram_bytes_per_launch"), p.get("n_paths")
+    except (OSError, ValueError):
+        pass
+    return None, None
+
+
+def oracle_run(w, n_paths: int, offset: int = 0):
+    from oracle import il_text, mc
+    from oracle.paths import Market
+    prog = il_text.parse(w.il_text)
+    env = {f"${i}": v for i, v in enumerate(w.tparams)}
+    t = time.perf_counter()
+    x = mc.payoffs(prog, Market(**vars(w.market)), env, 0, 1, n_paths, w.seed, 0, offset)
+    return time.perf_counter() - t, x
+
+
+def cpu_baseline(w, budget_s: float = 12.0) -> dict:
+    """The oracle as it stands, single process, on chunks of the workload's
+    paths until the time budget is used; rate in path-dates/s."""
+    chunk = 1 << 14
+    done, el = 0, 0.0
+    while el < budget_s and done < w.n_paths:
+        dt, _ = oracle_run(w, min(chunk, w.n_paths - done), done)
+        el += dt
+        done += min(chunk, w.n_paths - done)
+    return {"value": done * w.market.n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"paths 0..{done - 1} of the workload ({done} paths, {el:.1f} s, numpy FP64, 1 thread)"}
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    chunk = 1 << 13
+    for s in range(args.warmup):
+        oracle_run(w, chunk, s * chunk)
+    times = []
+    for s in range(args.steps):
+        dt, _ = oracle_run(w, chunk, (args.warmup + s) * chunk)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps * chunk * w.market.n / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(w, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{chunk} paths per step of the workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(w, info) -> dict:
+    return {"workload": w.name, "n_paths": w.n_paths, "n_dates": w.market.n,
+            "underlyings": w.market.d, "il_nodes": info, "seed": w.seed,
+            "l2": "flushed between steps by a 256 MiB device write"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="worst_of_autocall_3u_5d", choices=sorted(W.ALL))
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = W.ALL[args.workload]()
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import paper_2108_03076_gb300 as pc
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        from paper_2108_03076_gb300 import build
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    ctx = pc.pc_create(local, stream.cuda_stream)
+    spec = w.market
+    model = pc.pc_model_create(ctx, spec.S0, spec.sigma, spec.corr, spec.r, spec.days)
+    words, consts = pc.pc_assemble(w.il_text)
+    info = pc.pc_verify_payoff(words, consts, w.tparams)
+    contract = pc.pc_load_payoff(ctx, words, consts, w.tparams, 0, 1)
+    minfo = pc.pc_model_query(model)
+    offset = rank * w.n_paths
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        pc.pc_price_async(model, contract, w.n_paths, offset, w.seed, 0, out.data_ptr())
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            pc.pc_price_async(model, contract, w.n_paths, offset, w.seed, 0, out.data_ptr())
+            b.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    kernel_ms = [a.elapsed_time(b) for a, b in evs]
+    t_dev = sum(kernel_ms) / 1e3
+    sums = out.cpu().numpy()
+    mean = sums[0] / w.n_paths
+    var = max(0.0, (sums[1] - w.n_paths * mean * mean) / (w.n_paths - 1))
+
+    # end to end through the public API with host buffers
+    n_e2e = max(3, min(args.e2e_steps, args.steps))
+    for _ in range(3):
+        k = pc.pc_load_payoff(ctx, words, consts, w.tparams, 0, 1)
+        pc.pc_price(model, k, w.n_paths, w.seed)
+        pc.pc_contract_destroy(k)
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        k = pc.pc_load_payoff(ctx, words, consts, w.tparams, 0, 1)
+        price, se = pc.pc_price(model, k, w.n_paths, w.seed)
+        pc.pc_contract_destroy(k)
+    t_e2e = time.perf_counter() - t0
+
+    if ws > 1:
+        t = torch.tensor([t_dev, t_e2e / n_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev, e2e_step = float(t[0]), float(t[1])
+    else:
+        e2e_step = t_e2e / n_e2e
+
+    path_dates = w.n_paths * spec.n
+    value = ws * path_dates * args.steps / t_dev
+    e2e_value = ws * path_dates / e2e_step
+    cv = math.sqrt(var) / abs(mean) if mean else float("inf")
+    paths_needed = (cv / TARGET_REL_SE) ** 2
+    contracts_per_s = ws * (w.n_paths * args.steps / t_dev) / paths_needed
+
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    clock_hz = 1e6 * float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * 128 * clock_hz
+    peak_mufu = props.multi_processor_count * 16 * clock_hz
+    ops = alg_ops_per_path(minfo)
+    launch_s = t_dev / args.steps
+    achieved = ops["ops"] * w.n_paths / launch_s
+    traffic, traffic_paths = profile_traffic(w.name)
+    if traffic is not None and traffic_paths:
+        traffic = traffic * w.n_paths / traffic_paths
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {**config(w, info.n_nodes), "parallelism": f"path ranges x{ws}"},
+            "contracts_per_sec_at_1e-4_rel_se": contracts_per_s,
+            "price": mean, "stderr": math.sqrt(var / w.n_paths),
+            "paths_for_1e-4_rel_se": paths_needed,
+            "gpu_launches": args.steps,
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(words.nbytes + consts.nbytes + 4 * len(w.tparams)),
+                    "d2h_bytes_per_step": 40,
+                    "note": "pc_load_payoff + pc_price + pc_contract_destroy per step, host wall clock"},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
+                         "mufu_frac": ops["mufu"] * w.n_paths / launch_s / peak_mufu,
+                         "alg_ops_per_path": ops["ops"],
+                         "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x "
+                                       f"{clock_hz / 1e6:.0f} MHz issue (MUFU: x16)"},
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+
+    pc.pc_contract_destroy(contract)
+    pc.pc_model_destroy(model)
+    pc.pc_destroy(ctx)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

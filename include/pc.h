@@ -1,0 +1,316 @@
+/*
+ * pc.h -- C ABI of the payoff-expression Monte Carlo pricing engine (sm_103a).
+ *
+ * The engine prices contracts that were compiled into the payoff intermediate
+ * language (IL) of Annenkov & Elsman, "Certified Compilation of Financial
+ * Contracts" (PPDP'18): the expression language of Sec. 3 (now, model(l, t),
+ * if, loopif, payoff(t, p1, p2), unary and binary operators, literals,
+ * template time expressions) with the semantics of Fig. 3.  A contract arrives
+ * as postfix bytecode plus the values of its template variables (the
+ * "instrument" of Sec. 2 instantiated without recompiling, Sec. 6.2); it is
+ * valued by Monte Carlo over a correlated Black-Scholes market whose paths
+ * play the role of the external environment rho of Fig. 3.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns a pc_status; PC_OK (0) on success, a negative
+ *     code on failure.  Nothing aborts, throws or exits across this ABI.
+ *     A failed call leaves its outputs untouched and sets a message that
+ *     pc_last_error() returns.
+ *   - Host arrays passed in are read during the call and copied as needed;
+ *     the caller keeps ownership.  Handles are opaque and owned by the
+ *     library until their *_destroy call.
+ *   - Pointers documented as "device" must point to memory of the context's
+ *     device; all other pointers are host pointers.
+ *   - All work of a context runs in order on the context's CUDA stream.
+ *   - Thread safety: calls on different contexts may run concurrently; calls
+ *     on one context must be serialised by the caller.
+ */
+#ifndef PC_H
+#define PC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t pc_status;
+
+#define PC_OK          0
+#define PC_EINVAL     -1   /* bad argument (null pointer, size out of range)        */
+#define PC_EBYTECODE  -2   /* malformed program: bad opcode or operand, stack        */
+                           /* underflow, leftover values, type mismatch              */
+#define PC_ETPARAM    -3   /* template variable unbound or negative                  */
+#define PC_ERANGE     -4   /* a model/payoff time falls outside the model's grid or  */
+                           /* history, or the lookback exceeds the engine's window  */
+#define PC_ENOTPD     -5   /* correlation matrix not symmetric positive definite    */
+#define PC_ENOMEM     -6   /* host or device allocation failed                       */
+#define PC_ECUDA      -7   /* a CUDA runtime call failed                              */
+#define PC_ETIMEOUT   -8   /* the device did not finish within the context's limit   */
+#define PC_EDEVICE    -9   /* the kernel raised its device status word               */
+#define PC_ELIMIT    -10   /* program or model exceeds a documented engine limit      */
+#define PC_ESYNTAX   -11   /* pc_assemble: text is not valid IL                       */
+
+/* Engine limits. */
+#define PC_MAX_UNDERLYINGS   4      /* d                                            */
+#define PC_MAX_DATES      8192      /* simulated dates per model                    */
+#define PC_MAX_HISTORY    4096      /* history ordinals per model                   */
+#define PC_MAX_PROGRAM   65536      /* bytecode words per program                   */
+#define PC_MAX_CONSTS    16384      /* real literals per program                    */
+#define PC_MAX_TPARAMS    1024      /* template variables per program               */
+#define PC_MAX_STACK        96      /* operand stack depth (values + loop frames)   */
+#define PC_MAX_WINDOW      256      /* lookback window of simulated dates           */
+
+/* ------------------------------------------------------------------------ */
+/* Bytecode (input format of pc_load_payoff)                                 */
+/* ------------------------------------------------------------------------ */
+/*
+ * A program is the postfix (children first, left to right) serialisation of
+ * one IL expression tree (Sec. 3 grammar).  Each instruction is one header
+ * word  op | (A << 8)  (op in the low 8 bits, A an unsigned 24-bit operand),
+ * optionally followed by operand words:
+ *
+ *   PC_OP_REAL    A = index into consts[]          push real literal
+ *   PC_OP_BOOL    A = 0 / 1                         push bool literal
+ *   PC_OP_NAT     A = value                         push nat literal
+ *   PC_OP_NOW                                       push t ("now", Fig. 3)
+ *   PC_OP_TEXPR   + TIME(nat)                       push T[t]delta + t0
+ *   PC_OP_MODEL   A = label, + TIME(int)            push rho(l, T[t]delta + t0)
+ *   PC_OP_PAYOFF  + word p1' + word p2' + TIME(nat) push +-d(T[t]delta + t0) or 0
+ *   PC_OP_NEG, PC_OP_NOT                            unary, pop 1 push 1
+ *   PC_OP_ADD .. PC_OP_MIN                          binary, pop 2 push 1
+ *   PC_OP_IF                                        pop cond, then, else
+ *   PC_OP_LOOPIF  + TIME(bound)                     pop cond, then, else
+ *
+ * TIME is a sum of terms: one count word c (0..16) then c term words; a term
+ * word with bit 31 set is template variable number (w & 0x7fffffff), else a
+ * signed integer literal in bits 0..30 (two's complement of 31 bits).  This
+ * is the flattened form of the tplus trees of ILTExpr / ILTExprZ (Sec. 5):
+ * model times (ILTExprZ) may hold negative literals; texpr and payoff times
+ * (ILTExpr) and the loopif bound (TExpr: one literal or one variable) must
+ * be natural.
+ *
+ * Operand order for IF / LOOPIF is cond, then, else (pushed in that order).
+ * Types follow Fig. 3: reals, bools and nats; arithmetic and comparisons
+ * need operands of one type; nat subtraction truncates at 0; div is real.
+ */
+enum pc_opcode {
+  PC_OP_REAL = 1, PC_OP_BOOL, PC_OP_NAT, PC_OP_NOW, PC_OP_TEXPR, PC_OP_MODEL,
+  PC_OP_PAYOFF, PC_OP_NEG, PC_OP_NOT,
+  PC_OP_ADD, PC_OP_SUB, PC_OP_MULT, PC_OP_DIV, PC_OP_LT, PC_OP_LE, PC_OP_EQ,
+  PC_OP_AND, PC_OP_OR, PC_OP_MAX, PC_OP_MIN,
+  PC_OP_IF, PC_OP_LOOPIF
+};
+
+/* ------------------------------------------------------------------------ */
+/* Handles and descriptors                                                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct pc_ctx pc_ctx;
+typedef struct pc_model pc_model;
+typedef struct pc_contract pc_contract;
+
+/*
+ * Correlated Black-Scholes market on a date grid (the external environment
+ * rho of Sec. 2 / Fig. 3 is one simulated path of this market).
+ *
+ * IL time t is grid ordinal o = t - t_now.  Ordinal 0 is the valuation date
+ * (label l has value S0[l], discount 1); ordinals 1..n_dates are simulated
+ * at calendar day day[o-1] (year fraction day/365); ordinals -1..-n_hist are
+ * history: label l at ordinal -k is history[(k-1)*d + l], discounted with
+ * day hist_day[k-1] (< 0).  Discount d(t) = exp(-r * day(o) / 365).
+ * Paths: Brownian bridge over the grid, W -> X = L W with L the Cholesky
+ * factor of corr, S_l(o) = S0[l] exp((r - sigma_l^2/2) tau_o + sigma_l X_l(o)).
+ */
+typedef struct pc_model_desc {
+  int32_t d;                /* underlyings (labels 0..d-1), 1..PC_MAX_UNDERLYINGS */
+  const double *S0;         /* [d] spot values, > 0                                */
+  const double *sigma;      /* [d] volatilities, >= 0                              */
+  const double *corr;       /* [d*d] row-major correlation, symmetric PD, diag 1   */
+  double r;                 /* continuously compounded rate                        */
+  int32_t n_dates;          /* simulated dates, 1..PC_MAX_DATES                    */
+  const int32_t *day;       /* [n_dates] strictly increasing, > 0                  */
+  int32_t t_now;            /* IL time of the valuation date (>= 0; "now")         */
+  int32_t n_hist;           /* history ordinals, 0..PC_MAX_HISTORY                 */
+  const double *history;    /* [n_hist*d] or NULL when n_hist == 0                 */
+  const int32_t *hist_day;  /* [n_hist] < 0, strictly decreasing; NULL if none     */
+} pc_model_desc;
+
+/* Static facts about a verified program (pc_verify_payoff). */
+typedef struct pc_program_info {
+  int32_t n_nodes;          /* IL nodes                                            */
+  int32_t n_insn;           /* instructions of the executable form                 */
+  int32_t max_stack;        /* operand stack depth incl. loop frames               */
+  int32_t result_is_real;   /* 1 when the expression is real-valued                */
+  int32_t n_loops;          /* loopif nodes with a non-zero bound                  */
+  int32_t n_tparams_used;   /* highest template variable index used + 1            */
+} pc_program_info;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` that issues all work on
+ * `cuda_stream` (a cudaStream_t, borrowed, not destroyed by the library), or
+ * on a stream the context creates when cuda_stream is NULL.  Allocates the
+ * context's device scratch (reduction partials, status word).
+ * Errors: PC_EINVAL, PC_ECUDA (no such device / not sm_103), PC_ENOMEM. */
+pc_status pc_create(pc_ctx **out, int device, void *cuda_stream);
+
+/* Wait for the context's work, free its device memory and the handle.
+ * Models and contracts created on it must be destroyed first. */
+pc_status pc_destroy(pc_ctx *ctx);
+
+/* Message of the most recent failure on this thread (library-owned, valid
+ * until the thread's next failing call); "" if none.  ctx may be NULL. */
+const char *pc_last_error(const pc_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Model                                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Validate *desc, factor the correlation (FP64 Cholesky), build the
+ * breadth-first Brownian-bridge schedule and the per-date drift / discount
+ * tables, and upload them to the context's device.
+ * Errors: PC_EINVAL, PC_ENOTPD, PC_ELIMIT, PC_ENOMEM, PC_ECUDA. */
+pc_status pc_model_create(pc_ctx *ctx, const pc_model_desc *desc, pc_model **out);
+pc_status pc_model_destroy(pc_model *model);
+
+/* Static facts about a model's path generator. */
+typedef struct pc_model_info {
+  int32_t d, n_dates, n_hist, t_now;
+  int32_t bridge_levels;     /* levels of the bisection tree                      */
+  int32_t bridge_stack;      /* bridge values a path holds while dates are made   */
+  int32_t philox_blocks;     /* Philox4x32-10 evaluations for all dates of a path  */
+  int32_t box_muller_pairs;  /* Box-Muller transforms for all dates of a path      */
+} pc_model_info;
+
+/* Fill *info for `model` (host only, no device work).  Errors: PC_EINVAL. */
+pc_status pc_model_query(const pc_model *model, pc_model_info *info);
+
+/* ------------------------------------------------------------------------ */
+/* Payoff programs                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Load a payoff expression: decode `bytecode` (n_words words, format above),
+ * check stack discipline and types (Fig. 3), bind template variables to
+ * template_params[0..n_params-1] (the template environment delta of Sec. 2),
+ * fold every payoff(t, p1', p2') to +d, -d or 0 for the two-party view
+ * (p1, p2) of Fig. 3, and upload the executable form to the device.
+ * consts[0..n_consts-1] are the real literals.  Requires a real result.
+ * Errors: PC_EINVAL, PC_EBYTECODE, PC_ETPARAM, PC_ELIMIT, PC_ENOMEM, PC_ECUDA. */
+pc_status pc_load_payoff(pc_ctx *ctx, const uint32_t *bytecode, size_t n_words,
+                         const double *consts, size_t n_consts,
+                         const int32_t *template_params, size_t n_params,
+                         int32_t p1, int32_t p2, pc_contract **out);
+pc_status pc_contract_destroy(pc_contract *contract);
+
+/* Host-only: the checks of pc_load_payoff without a context or device.
+ * Fills *info (may be NULL).  Errors as pc_load_payoff. */
+pc_status pc_verify_payoff(const uint32_t *bytecode, size_t n_words,
+                           const double *consts, size_t n_consts,
+                           const int32_t *template_params, size_t n_params,
+                           pc_program_info *info);
+
+/* Host-only: assemble the textual S-expression form of IL into bytecode.
+ * Grammar: (now) (model L t) (if c a b) (loopif c a b t) (payoff t P P)
+ * (texpr t) (neg e) (not e) (add|sub|mult|div|lt|le|eq|and|or|max|min a b)
+ * REAL #t #f (nat N); times: INT | $K | (tplus t t); ';' comments.
+ * Writes at most cap_words words / cap_consts constants and their counts;
+ * on PC_ESYNTAX writes a message into err (err_cap bytes, may be 0).
+ * Errors: PC_EINVAL, PC_ESYNTAX, PC_ELIMIT (buffers too small). */
+pc_status pc_assemble(const char *text, uint32_t *words, size_t cap_words,
+                      size_t *n_words, double *consts, size_t cap_consts,
+                      size_t *n_consts, char *err, size_t err_cap);
+
+/* ------------------------------------------------------------------------ */
+/* Pricing                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Monte Carlo value of `contract` under `model` (both on one context):
+ * the average over paths 0..n_paths-1 of the discounted payoff, i.e. of
+ * IL[[e]](rho_path, delta, 0, t_now, d, p1, p2) (Fig. 3; by Theorem 1 the
+ * discounted sum of the contract's cashflows), and its standard error
+ * sqrt(sample variance / n).  Path p draws its normals from Philox4x32-10
+ * counter (m >> 2, p_lo, p_hi, 0) under key (seed_lo, seed_hi).  Blocks
+ * until done.  n_paths >= 2.
+ * Errors: PC_EINVAL, PC_ERANGE, PC_ELIMIT, PC_ECUDA, PC_ETIMEOUT, PC_EDEVICE. */
+pc_status pc_price(const pc_model *model, const pc_contract *contract,
+                   uint64_t n_paths, uint64_t seed,
+                   double *out_price, double *out_stderr);
+
+/* Asynchronous form: enqueue the pricing of paths
+ * path_offset .. path_offset+n_paths-1 with Philox stream word `stream` and
+ * write {sum x, sum x^2, n} as three doubles to the device buffer d_out.
+ * Does not synchronise.  n_paths >= 1.  Runs the same kernels as pc_price;
+ * results of runs over disjoint path ranges combine by adding the triples.
+ * Errors: PC_EINVAL, PC_ERANGE, PC_ELIMIT, PC_ECUDA. */
+pc_status pc_price_async(const pc_model *model, const pc_contract *contract,
+                         uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                         uint32_t stream, double *d_out);
+
+/* Parity form: as pc_price_async, and also write the FP32 discounted payoff
+ * of path path_offset+i to d_payoffs[i] (device, n_paths floats).  Same
+ * kernel code path as pc_price_async with the per-path store enabled. */
+pc_status pc_price_paths(const pc_model *model, const pc_contract *contract,
+                         uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                         uint32_t stream, double *d_out, float *d_payoffs);
+
+/* Price n contracts, each against its own model, in one launch:
+ * contract i runs n_paths[i] paths on Philox stream word i.  Outputs
+ * out_price[i], out_stderr[i] (host).  Blocks until done.
+ * Errors: as pc_price. */
+pc_status pc_price_batch(size_t n, const pc_model *const *models,
+                         const pc_contract *const *contracts,
+                         const uint64_t *n_paths, uint64_t seed,
+                         double *out_price, double *out_stderr);
+
+/* Pathwise sensitivities: price, delta_l = d price / d S0[l] and
+ * vega_l = d price / d sigma[l] (l < d) from the derivative of each path's
+ * payoff through the GBM map (if / loopif decisions held fixed; valid for
+ * payoffs that are Lipschitz in the path).  out_se[0] is the price's
+ * standard error, out_se[1+l] delta_l's, out_se[1+d+l] vega_l's.
+ * Errors: as pc_price. */
+pc_status pc_greeks(const pc_model *model, const pc_contract *contract,
+                    uint64_t n_paths, uint64_t seed, double *out_price,
+                    double *out_delta, double *out_vega, double *out_se);
+
+/* ------------------------------------------------------------------------ */
+/* Parity probes (same device functions as the pricing kernel)               */
+/* ------------------------------------------------------------------------ */
+
+/* Philox4x32-10 on the device: for i < n, out[4i..4i+3] = Philox of counter
+ * ctr[4i..4i+3] under key (key0, key1).  ctr, out: device uint32 arrays. */
+pc_status pc_debug_philox(pc_ctx *ctx, const uint32_t *d_ctr, uint32_t key0,
+                          uint32_t key1, uint32_t *d_out, size_t n);
+
+/* Simulated path values: d_S[(i*d + l)*(n_dates+1) + o] = S_l at ordinal o
+ * (o = 0..n_dates) of path path_offset+i, FP32, device.  Same path
+ * generator as the pricing kernel. */
+pc_status pc_debug_paths(const pc_model *model, uint64_t n_paths,
+                         uint64_t path_offset, uint64_t seed, uint32_t stream,
+                         float *d_S);
+
+/* Host-only: the executable form pc_load_payoff would run for this program
+ * (16 bytes per instruction: opcode | A << 8, then three operand words).
+ * Writes at most cap instructions to out and the count to *n_insn.
+ * Errors: as pc_load_payoff; PC_ELIMIT if cap is too small. */
+pc_status pc_debug_program(const uint32_t *bytecode, size_t n_words,
+                           const double *consts, size_t n_consts,
+                           const int32_t *template_params, size_t n_params,
+                           int32_t p1, int32_t p2, uint32_t *out, size_t cap,
+                           size_t *n_insn);
+
+/* Host-only: the date-ordered bridge schedule pc_model_create builds for
+ * *desc: date_ops[0..n_dates+1] (ops of date t are date_ops[t] ..
+ * date_ops[t+1]-1) and 6 words per op (wl, wr, sd as float bits; node
+ * number; level | flags << 16; date ordinal).  Writes at most cap_ops ops.
+ * Errors: as pc_model_create's validation; PC_ELIMIT if cap_ops is small. */
+pc_status pc_debug_bridge(const pc_model_desc *desc, int32_t *date_ops, uint32_t *ops,
+                          size_t cap_ops, size_t *n_ops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PC_H */

@@ -191,6 +191,11 @@ class Args:
     ``rho(label, time, idx)`` returns the observable ``label`` at integer
     ``time`` for the evaluations (paths) ``idx`` as a float64 array.
     ``d(time)`` is the discount function N -> R.
+
+    ``margins`` (optional, indexed by path) receives, for every comparison
+    of two reals a path evaluates, the smallest |x - y| / max(1, |x|, |y|):
+    how far the path's discrete decisions were from a tie.  It does not
+    affect the values computed.
     """
     rho: Callable[[int, int, np.ndarray], np.ndarray]
     delta: Mapping[str, int]
@@ -198,6 +203,7 @@ class Args:
     d: Callable[[int], float]
     p1: int
     p2: int
+    margins: np.ndarray | None = None
 
 
 def _kind(v: np.ndarray) -> str:
@@ -295,7 +301,12 @@ def _ev(il: IL, a: Args, t0: int, idx: np.ndarray) -> np.ndarray:
     if isinstance(il, UnOp):
         return _unop(il.op, _ev(il.e, a, t0, idx))
     if isinstance(il, BinOp):
-        return _binop(il.op, _ev(il.a, a, t0, idx), _ev(il.b, a, t0, idx))
+        x, y = _ev(il.a, a, t0, idx), _ev(il.b, a, t0, idx)
+        if (a.margins is not None and il.op in ("lt", "le", "eq") and x.dtype == REAL
+                and y.dtype == REAL and len(idx)):
+            gap = np.abs(x - y) / np.maximum(1.0, np.maximum(np.abs(x), np.abs(y)))
+            np.minimum.at(a.margins, idx, gap)
+        return _binop(il.op, x, y)
     if isinstance(il, If):
         c = _ev(il.c, a, t0, idx)
         if _kind(c) != "bool":

@@ -42,18 +42,20 @@ def env_from_paths(mk: Market, S: np.ndarray, base: np.ndarray | None = None):
 
 def payoffs(il: IL.IL, mk: Market, delta: Mapping[str, int], p1: int, p2: int,
             n_paths: int, seed: int, stream: int = 0, offset: int = 0,
-            paths: np.ndarray | None = None) -> np.ndarray:
+            paths: np.ndarray | None = None, with_margins: bool = False):
     """Discounted payoff of each path (global indices offset..offset+n-1, or
-    the explicit ``paths``)."""
+    the explicit ``paths``).  With ``with_margins`` also returns each path's
+    smallest relative distance of a real comparison from a tie."""
     if paths is None:
         paths = np.arange(offset, offset + n_paths, dtype=np.uint64)
     S = simulate(mk, seed, stream, paths)
+    margins = np.full(len(paths), np.inf) if with_margins else None
     args = IL.Args(rho=env_from_paths(mk, S), delta=delta, now=mk.now,
-                   d=mk.disc, p1=p1, p2=p2)
+                   d=mk.disc, p1=p1, p2=p2, margins=margins)
     v = IL.evaluate(il, args, t0=0, idx=np.arange(len(paths)))
     if v.dtype != np.float64:
         raise TypeError("a payoff expression must evaluate to a real")
-    return v
+    return (v, margins) if with_margins else v
 
 
 @dataclass

@@ -1,0 +1,280 @@
+"""Python binding of the payoff-expression Monte Carlo engine (``libpc.so``).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name declared in ``include/pc.h``; all computation runs in the
+library's CUDA kernels.  Device buffers are passed as integer addresses
+(e.g. ``torch.Tensor.data_ptr()``), CUDA streams as ``cudaStream_t`` values
+(e.g. ``torch.cuda.current_stream().cuda_stream``).  A non-OK status raises
+``PcError`` carrying the status code and ``pc_last_error()``.
+
+The library must have been built (``paper_2108_03076_gb300.build.build()``);
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpc.so")
+
+PC_OK = 0
+STATUS = {0: "PC_OK", -1: "PC_EINVAL", -2: "PC_EBYTECODE", -3: "PC_ETPARAM", -4: "PC_ERANGE",
+          -5: "PC_ENOTPD", -6: "PC_ENOMEM", -7: "PC_ECUDA", -8: "PC_ETIMEOUT",
+          -9: "PC_EDEVICE", -10: "PC_ELIMIT", -11: "PC_ESYNTAX"}
+globals().update({v: k for k, v in STATUS.items()})
+
+MAX_UNDERLYINGS = 4
+
+
+class PcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("d", C.c_int32), ("S0", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
+                ("corr", C.POINTER(C.c_double)), ("r", C.c_double), ("n_dates", C.c_int32),
+                ("day", C.POINTER(C.c_int32)), ("t_now", C.c_int32), ("n_hist", C.c_int32),
+                ("history", C.POINTER(C.c_double)), ("hist_day", C.POINTER(C.c_int32))]
+
+
+class ModelInfo(C.Structure):
+    _fields_ = [("d", C.c_int32), ("n_dates", C.c_int32), ("n_hist", C.c_int32),
+                ("t_now", C.c_int32), ("bridge_levels", C.c_int32), ("bridge_stack", C.c_int32),
+                ("philox_blocks", C.c_int32), ("box_muller_pairs", C.c_int32)]
+
+
+class ProgramInfo(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_insn", C.c_int32), ("max_stack", C.c_int32),
+                ("result_is_real", C.c_int32), ("n_loops", C.c_int32),
+                ("n_tparams_used", C.c_int32)]
+
+
+_lib: Optional[C.CDLL] = None
+VP, U64, U32, I32, SZ, DBL = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int32, C.c_size_t, C.c_double
+PD, PU32, PI32, PF = C.POINTER(C.c_double), C.POINTER(C.c_uint32), C.POINTER(C.c_int32), C.POINTER(C.c_float)
+
+_SIGS = {
+    "pc_create": [C.POINTER(VP), C.c_int, VP],
+    "pc_destroy": [VP],
+    "pc_last_error": [VP],
+    "pc_model_create": [VP, C.POINTER(ModelDesc), C.POINTER(VP)],
+    "pc_model_destroy": [VP],
+    "pc_model_query": [VP, C.POINTER(ModelInfo)],
+    "pc_load_payoff": [VP, PU32, SZ, PD, SZ, PI32, SZ, I32, I32, C.POINTER(VP)],
+    "pc_contract_destroy": [VP],
+    "pc_verify_payoff": [PU32, SZ, PD, SZ, PI32, SZ, C.POINTER(ProgramInfo)],
+    "pc_assemble": [C.c_char_p, PU32, SZ, C.POINTER(SZ), PD, SZ, C.POINTER(SZ), C.c_char_p, SZ],
+    "pc_price": [VP, VP, U64, U64, PD, PD],
+    "pc_price_async": [VP, VP, U64, U64, U64, U32, VP],
+    "pc_price_paths": [VP, VP, U64, U64, U64, U32, VP, VP],
+    "pc_price_batch": [SZ, C.POINTER(VP), C.POINTER(VP), C.POINTER(U64), U64, PD, PD],
+    "pc_greeks": [VP, VP, U64, U64, PD, PD, PD, PD],
+    "pc_debug_philox": [VP, VP, U32, U32, VP, SZ],
+    "pc_debug_paths": [VP, U64, U64, U64, U32, VP],
+    "pc_debug_program": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, PU32, SZ, C.POINTER(SZ)],
+    "pc_debug_bridge": [C.POINTER(ModelDesc), PI32, PU32, SZ, C.POINTER(SZ)],
+}
+EXPORTED = tuple(_SIGS)
+
+
+def lib() -> C.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2108_03076_gb300.build.build() (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_char_p if name == "pc_last_error" else C.c_int32
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != PC_OK:
+        raise PcError(status, lib().pc_last_error(None).decode(errors="replace"))
+
+
+def _arr(a, dtype):
+    a = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    return a
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct)) if a.size else None
+
+
+# ---------------------------------------------------------------------------
+# Context / model / contract
+# ---------------------------------------------------------------------------
+
+
+def pc_create(device: int = 0, stream: int | None = None) -> int:
+    h = VP()
+    _check(lib().pc_create(C.byref(h), device, VP(stream) if stream else None))
+    return h.value
+
+
+def pc_destroy(ctx: int) -> None:
+    _check(lib().pc_destroy(VP(ctx)))
+
+
+def pc_last_error() -> str:
+    return lib().pc_last_error(None).decode(errors="replace")
+
+
+def _model_desc(S0, sigma, corr, r, days, t_now=0, history=None, hist_days=None):
+    """A ModelDesc plus the arrays it points into (kept alive together)."""
+    keep = [_arr(S0, np.float64), _arr(sigma, np.float64), _arr(corr, np.float64).reshape(-1),
+            _arr(days, np.int32),
+            _arr(history if history is not None else [], np.float64).reshape(-1),
+            _arr(hist_days if hist_days is not None else [], np.int32)]
+    S0a, sga, ca, da, ha, hda = keep
+    desc = ModelDesc(len(S0a), _ptr(S0a, C.c_double), _ptr(sga, C.c_double), _ptr(ca, C.c_double),
+                     float(r), len(da), _ptr(da, C.c_int32), int(t_now), len(hda),
+                     _ptr(ha, C.c_double), _ptr(hda, C.c_int32))
+    return desc, keep
+
+
+def pc_model_create(ctx: int, S0: Sequence[float], sigma: Sequence[float],
+                    corr: Sequence[Sequence[float]], r: float, days: Sequence[int],
+                    t_now: int = 0, history: Sequence[Sequence[float]] | None = None,
+                    hist_days: Sequence[int] | None = None) -> int:
+    desc, _keep = _model_desc(S0, sigma, corr, r, days, t_now, history, hist_days)
+    h = VP()
+    _check(lib().pc_model_create(VP(ctx), C.byref(desc), C.byref(h)))
+    return h.value
+
+
+def pc_model_query(model: int) -> ModelInfo:
+    info = ModelInfo()
+    _check(lib().pc_model_query(VP(model), C.byref(info)))
+    return info
+
+
+def pc_model_destroy(model: int) -> None:
+    _check(lib().pc_model_destroy(VP(model)))
+
+
+def pc_assemble(text: str) -> Tuple[np.ndarray, np.ndarray]:
+    """Textual IL -> (bytecode words uint32, real literals float64)."""
+    nw, nk = SZ(0), SZ(0)
+    err = C.create_string_buffer(512)
+    st = lib().pc_assemble(text.encode(), None, 0, C.byref(nw), None, 0, C.byref(nk), err, 512)
+    if st not in (PC_OK, -10):
+        raise PcError(st, err.value.decode(errors="replace"))
+    w = np.zeros(nw.value, np.uint32)
+    k = np.zeros(nk.value, np.float64)
+    _check(lib().pc_assemble(text.encode(), _ptr(w, C.c_uint32), w.size, C.byref(nw),
+                             _ptr(k, C.c_double), k.size, C.byref(nk), err, 512))
+    return w, k
+
+
+def pc_verify_payoff(words, consts, tparams=()) -> ProgramInfo:
+    w, k, t = _arr(words, np.uint32), _arr(consts, np.float64), _arr(tparams, np.int32)
+    info = ProgramInfo()
+    _check(lib().pc_verify_payoff(_ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,
+                                  _ptr(t, C.c_int32), t.size, C.byref(info)))
+    return info
+
+
+def pc_load_payoff(ctx: int, words, consts, tparams=(), p1: int = 0, p2: int = 1) -> int:
+    w, k, t = _arr(words, np.uint32), _arr(consts, np.float64), _arr(tparams, np.int32)
+    h = VP()
+    _check(lib().pc_load_payoff(VP(ctx), _ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,
+                                _ptr(t, C.c_int32), t.size, int(p1), int(p2), C.byref(h)))
+    return h.value
+
+
+def pc_contract_destroy(contract: int) -> None:
+    _check(lib().pc_contract_destroy(VP(contract)))
+
+
+# ---------------------------------------------------------------------------
+# Pricing
+# ---------------------------------------------------------------------------
+
+
+def pc_price(model: int, contract: int, n_paths: int, seed: int) -> Tuple[float, float]:
+    p, s = DBL(), DBL()
+    _check(lib().pc_price(VP(model), VP(contract), n_paths, seed, C.byref(p), C.byref(s)))
+    return p.value, s.value
+
+
+def pc_price_async(model: int, contract: int, n_paths: int, path_offset: int, seed: int,
+                   stream_id: int, d_out: int) -> None:
+    _check(lib().pc_price_async(VP(model), VP(contract), n_paths, path_offset, seed, stream_id,
+                                VP(d_out)))
+
+
+def pc_price_paths(model: int, contract: int, n_paths: int, path_offset: int, seed: int,
+                   stream_id: int, d_out: int, d_payoffs: int) -> None:
+    _check(lib().pc_price_paths(VP(model), VP(contract), n_paths, path_offset, seed, stream_id,
+                                VP(d_out), VP(d_payoffs)))
+
+
+def pc_price_batch(models: Sequence[int], contracts: Sequence[int], n_paths: Sequence[int],
+                   seed: int) -> Tuple[np.ndarray, np.ndarray]:
+    n = len(contracts)
+    M = (VP * n)(*[VP(m) for m in models])
+    K = (VP * n)(*[VP(k) for k in contracts])
+    N = (U64 * n)(*[int(x) for x in n_paths])
+    price, se = np.zeros(n), np.zeros(n)
+    _check(lib().pc_price_batch(n, M, K, N, seed, _ptr(price, C.c_double), _ptr(se, C.c_double)))
+    return price, se
+
+
+def pc_greeks(model: int, contract: int, n_paths: int, seed: int, d: int):
+    """Returns (price, delta[d], vega[d], se[1 + 2d])."""
+    p = DBL()
+    de, ve, se = np.zeros(d), np.zeros(d), np.zeros(1 + 2 * d)
+    _check(lib().pc_greeks(VP(model), VP(contract), n_paths, seed, C.byref(p),
+                           _ptr(de, C.c_double), _ptr(ve, C.c_double), _ptr(se, C.c_double)))
+    return p.value, de, ve, se
+
+
+def pc_debug_philox(ctx: int, d_ctr: int, key0: int, key1: int, d_out: int, n: int) -> None:
+    _check(lib().pc_debug_philox(VP(ctx), VP(d_ctr), key0, key1, VP(d_out), n))
+
+
+def pc_debug_paths(model: int, n_paths: int, path_offset: int, seed: int, stream_id: int,
+                   d_S: int) -> None:
+    _check(lib().pc_debug_paths(VP(model), n_paths, path_offset, seed, stream_id, VP(d_S)))
+
+
+def pc_debug_program(words, consts, tparams=(), p1: int = 0, p2: int = 1) -> np.ndarray:
+    """Executable form of a program: uint32 [n_insn, 4]."""
+    w, k, t = _arr(words, np.uint32), _arr(consts, np.float64), _arr(tparams, np.int32)
+    n = SZ(0)
+    lib().pc_debug_program(_ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,
+                           _ptr(t, C.c_int32), t.size, p1, p2, None, 0, C.byref(n))
+    out = np.zeros((max(n.value, 1), 4), np.uint32)
+    _check(lib().pc_debug_program(_ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,
+                                  _ptr(t, C.c_int32), t.size, p1, p2,
+                                  out.ctypes.data_as(C.POINTER(C.c_uint32)), out.shape[0],
+                                  C.byref(n)))
+    return out[:n.value]
+
+
+def pc_debug_bridge(S0, sigma, corr, r, days, t_now=0, history=None, hist_days=None):
+    """(date_ops int32 [n+2], ops uint32 [n_ops, 6]) of the model these
+    arguments describe (host only)."""
+    desc, _keep = _model_desc(S0, sigma, corr, r, days, t_now, history, hist_days)
+    n = SZ(0)
+    lib().pc_debug_bridge(C.byref(desc), None, None, 0, C.byref(n))
+    dops = np.zeros(len(days) + 2, np.int32)
+    ops = np.zeros((max(n.value, 1), 6), np.uint32)
+    _check(lib().pc_debug_bridge(C.byref(desc), dops.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 ops.ctypes.data_as(C.POINTER(C.c_uint32)), ops.shape[0],
+                                 C.byref(n)))
+    return dops, ops[:n.value]

@@ -1,0 +1,603 @@
+// pc_capi.cpp -- the extern "C" entry points declared in include/pc.h.
+//
+// Host orchestration only: argument checks, load-time compilation of payoff
+// programs, model setup, device uploads, kernel launches on the context's
+// stream and bounded waits.  Every step of the per-path computation runs in
+// the kernels of pc_kernels.cu.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+
+#include "pc_internal.h"
+
+using namespace pc;
+
+struct pc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 0;
+  int max_smem = 0;
+  double *d_res = nullptr;       // [8]: sum, sumsq, n, -, status word (int32 at d_res+4)
+  double *d_partials = nullptr;  // tile partials (scratch)
+  size_t partial_cap = 0;        // doubles
+  unsigned long long *d_counters = nullptr;  // [2] tile counter, finished blocks (scratch)
+  double timeout_s = 300.0;
+  int live_objects = 0;
+};
+
+struct pc_model {
+  pc_ctx *ctx = nullptr;
+  ModelHost H;
+  void *d_mem = nullptr;
+  ModelDev dev{};
+  uint64_t id = 0;
+};
+
+struct pc_contract {
+  pc_ctx *ctx = nullptr;
+  Program prog;
+  XInsn *d_code = nullptr;
+  std::mutex mu;
+  std::map<std::pair<uint64_t, uint64_t>, int32_t> win_cache;  // (model id, layout key) -> window
+};
+
+namespace {
+
+thread_local std::string tl_err;
+std::atomic<uint64_t> g_model_ids{1};
+
+pc_status fail(pc_status s, const std::string &m) {
+  tl_err = m;
+  return s;
+}
+
+pc_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CU(call, what)                              \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// Wait for the stream with a wall-clock limit.
+pc_status wait_stream(pc_ctx *c) {
+  const auto t_start = std::chrono::steady_clock::now();
+  int spins = 0;
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(c->stream);
+    if (e == cudaSuccess) return PC_OK;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "stream");
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (el > c->timeout_s) return fail(PC_ETIMEOUT, "device did not finish within the context's limit");
+    if (++spins > 2000) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+template <typename T>
+pc_status upload(const std::vector<T> &v, char *base, size_t &off, const T *&dst, cudaStream_t s) {
+  off = (off + 255) & ~size_t(255);
+  dst = reinterpret_cast<const T *>(base + off);
+  if (!v.empty())
+    CU(cudaMemcpyAsync(base + off, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s), "upload");
+  off += v.size() * sizeof(T);
+  return PC_OK;
+}
+
+template <typename T>
+size_t padded(const std::vector<T> &v) { return ((v.size() * sizeof(T)) + 255) & ~size_t(255); }
+
+Layout make_layout(const Program &p, const ModelHost &H, int32_t win) {
+  Layout L{};
+  L.stack = p.frame_slots;
+  L.off_bstack = L.stack;
+  L.off_cache = L.off_bstack + H.bstack * H.d;
+  L.off_win = L.off_cache + H.n_levels * 4;
+  L.win = win;
+  L.words = L.off_win + win * H.d;
+  return L;
+}
+
+pc_status ensure_partials(pc_ctx *c, size_t doubles) {
+  if (doubles <= c->partial_cap) return PC_OK;
+  CU(cudaStreamSynchronize(c->stream), "sync");
+  if (c->d_partials) cudaFree(c->d_partials);
+  c->d_partials = nullptr;
+  c->partial_cap = 0;
+  size_t cap = std::max<size_t>(doubles, 1 << 16);
+  CU(cudaMalloc(&c->d_partials, cap * sizeof(double)), "partials");
+  c->partial_cap = cap;
+  return PC_OK;
+}
+
+pc_status window_for(const pc_model *m, const pc_contract *k, int32_t &win) {
+  auto *kc = const_cast<pc_contract *>(k);
+  std::lock_guard<std::mutex> g(kc->mu);
+  auto key = std::make_pair(m->id, uint64_t(0));
+  auto it = kc->win_cache.find(key);
+  if (it != kc->win_cache.end()) { win = it->second; return PC_OK; }
+  // labels must exist in the model
+  for (const XInsn &I : k->prog.code) {
+    uint32_t op = I.opa & 0xffu;
+    if ((op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK) && int32_t(I.opa >> 8) >= m->H.d)
+      return fail(PC_ERANGE, "program observes label " + std::to_string(I.opa >> 8) +
+                                 " but the model has " + std::to_string(m->H.d) + " underlyings");
+  }
+  std::string err;
+  pc_status s = analyse_program(k->prog, m->H.t_now, m->H.n, m->H.n_hist, win, err);
+  if (s != PC_OK) return fail(s, err);
+  kc->win_cache[key] = win;
+  return PC_OK;
+}
+
+// Room left for the pricing kernel's static shared memory (reduction
+// scratch and flags) when sizing its dynamic shared memory.
+constexpr size_t kStaticSmemReserve = 2048;
+
+struct Launch {
+  PriceArgs args{};
+  int grid = 0;
+  size_t smem = 0;
+};
+
+pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
+                  uint64_t seed, uint32_t stream, Launch &L) {
+  if (!m || !k) return fail(PC_EINVAL, "null model or contract");
+  if (m->ctx != k->ctx) return fail(PC_EINVAL, "model and contract belong to different contexts");
+  if (n_paths == 0) return fail(PC_EINVAL, "n_paths must be >= 1");
+  if (n_paths > (uint64_t(1) << 40)) return fail(PC_ELIMIT, "n_paths exceeds 2^40");
+  int32_t win = 1;
+  pc_status s = window_for(m, k, win);
+  if (s != PC_OK) return s;
+  pc_ctx *c = m->ctx;
+  const Layout lay = make_layout(k->prog, m->H, win);
+  L.smem = size_t(k->prog.code.size()) * sizeof(XInsn) + size_t(lay.words) * kBlock * 4;
+  if (L.smem + kStaticSmemReserve > size_t(c->max_smem))
+    return fail(PC_ELIMIT, "program + per-path state need " + std::to_string(L.smem) +
+                               " bytes of shared memory per block; the device offers " +
+                               std::to_string(c->max_smem));
+  const uint64_t n_tiles = (n_paths + kTilePaths - 1) / kTilePaths;
+  PriceArgs &a = L.args;
+  a.prog = k->d_code;
+  a.n_insn = int32_t(k->prog.code.size());
+  a.m = m->dev;
+  a.lay = lay;
+  a.n_paths = n_paths;
+  a.path_offset = offset;
+  a.key0 = uint32_t(seed);
+  a.key1 = uint32_t(seed >> 32);
+  a.stream = stream;
+  a.n_tiles = n_tiles;
+  a.status = reinterpret_cast<int32_t *>(c->d_res + 4);
+  const int bpsm = price_blocks_per_sm(m->H.d, L.smem, false);
+  if (bpsm < 1) return fail(PC_ELIMIT, "kernel cannot be resident with this shared-memory footprint");
+  const uint64_t warps_per_block = kBlock / 32;
+  const uint64_t need = (n_tiles + warps_per_block - 1) / warps_per_block;
+  L.grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * bpsm, need));
+  return PC_OK;
+}
+
+pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
+                    uint64_t seed, uint32_t stream, double *d_out, float *d_payoffs) {
+  Launch L;
+  pc_status s = prepare(m, k, n_paths, offset, seed, stream, L);
+  if (s != PC_OK) return s;
+  pc_ctx *c = m->ctx;
+  s = ensure_partials(c, size_t(L.args.n_tiles) * 2);
+  if (s != PC_OK) return s;
+  L.args.width = 2;
+  L.args.tile_partials = c->d_partials;
+  L.args.counters = c->d_counters;
+  L.args.out = d_out;
+  L.args.out_paths = d_payoffs;
+  CU(cudaSetDevice(c->device), "cudaSetDevice");
+  CU(launch_price(L.args, L.grid, L.smem, c->stream), "price kernel");
+  return PC_OK;
+}
+
+pc_status check_status(pc_ctx *c, int32_t status) {
+  if (status == 0) return PC_OK;
+  int32_t zero = 0;
+  cudaMemcpyAsync(reinterpret_cast<int32_t *>(c->d_res + 4), &zero, 4, cudaMemcpyHostToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return fail(PC_EDEVICE, "kernel raised its status word (" + std::to_string(status) + ")");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pc_last_error(const pc_ctx *) { return tl_err.c_str(); }
+
+pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
+  if (!out) return fail(PC_EINVAL, "out is null");
+  int n = 0;
+  CU(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(PC_EINVAL, "no such CUDA device");
+  cudaDeviceProp prop{};
+  CU(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+  if (prop.major != 10 || prop.minor != 3)
+    return fail(PC_ECUDA, std::string("kernels are built for sm_103a; device is ") + prop.name +
+                              " (sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + ")");
+  CU(cudaSetDevice(device), "cudaSetDevice");
+  pc_ctx *c = new (std::nothrow) pc_ctx();
+  if (!c) return fail(PC_ENOMEM, "context");
+  c->device = device;
+  c->sm_count = prop.multiProcessorCount;
+  c->max_smem = max_dynamic_smem();
+  if (const char *t = std::getenv("PC_TIMEOUT_S")) c->timeout_s = std::max(1.0, std::atof(t));
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    c->own_stream = true;
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_res, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_res, 0, 8 * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    if (c->d_counters) cudaFree(c->d_counters);
+    if (c->d_res) cudaFree(c->d_res);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return cuda_fail(e, "context setup");
+  }
+  *out = c;
+  return PC_OK;
+}
+
+pc_status pc_destroy(pc_ctx *c) {
+  if (!c) return fail(PC_EINVAL, "null context");
+  if (c->live_objects) return fail(PC_EINVAL, "destroy the context's models and contracts first");
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->d_partials) cudaFree(c->d_partials);
+  if (c->d_counters) cudaFree(c->d_counters);
+  if (c->d_res) cudaFree(c->d_res);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return PC_OK;
+}
+
+pc_status pc_model_create(pc_ctx *c, const pc_model_desc *desc, pc_model **out) {
+  if (!c || !desc || !out) return fail(PC_EINVAL, "null argument");
+  try {
+    pc_model *m = new pc_model();
+    std::string err;
+    pc_status s = build_model(*desc, m->H, err);
+    if (s != PC_OK) {
+      delete m;
+      return fail(s, err);
+    }
+    const ModelHost &H = m->H;
+    size_t bytes = padded(H.date_ops) + padded(H.ops) + padded(H.A) + padded(H.B) +
+                   padded(H.disc) + padded(H.sval) + padded(H.tau) + 256;
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    cudaError_t e = cudaMalloc(&m->d_mem, bytes);
+    if (e != cudaSuccess) {
+      delete m;
+      return cuda_fail(e, "model tables");
+    }
+    char *base = static_cast<char *>(m->d_mem);
+    size_t off = 0;
+    ModelDev &D = m->dev;
+    pc_status u = PC_OK;
+    if (u == PC_OK) u = upload(H.date_ops, base, off, D.date_ops, c->stream);
+    if (u == PC_OK) u = upload(H.ops, base, off, D.ops, c->stream);
+    if (u == PC_OK) u = upload(H.A, base, off, D.A, c->stream);
+    if (u == PC_OK) u = upload(H.B, base, off, D.B, c->stream);
+    if (u == PC_OK) u = upload(H.disc, base, off, D.disc, c->stream);
+    if (u == PC_OK) u = upload(H.sval, base, off, D.sval, c->stream);
+    if (u == PC_OK) u = upload(H.tau, base, off, D.tau, c->stream);
+    if (u == PC_OK) {
+      cudaError_t e2 = cudaStreamSynchronize(c->stream);
+      if (e2 != cudaSuccess) u = cuda_fail(e2, "model upload");
+    }
+    if (u != PC_OK) {
+      cudaFree(m->d_mem);
+      delete m;
+      return u;
+    }
+    D.d = H.d;
+    D.n = H.n;
+    D.n_hist = H.n_hist;
+    D.t_now = H.t_now;
+    D.n_levels = H.n_levels;
+    D.bstack = H.bstack;
+    m->ctx = c;
+    m->id = g_model_ids.fetch_add(1);
+    ++c->live_objects;
+    *out = m;
+    return PC_OK;
+  } catch (const std::bad_alloc &) {
+    return fail(PC_ENOMEM, "host allocation");
+  } catch (...) {
+    return fail(PC_EINVAL, "unexpected error in pc_model_create");
+  }
+}
+
+pc_status pc_model_query(const pc_model *m, pc_model_info *info) {
+  if (!m || !info) return fail(PC_EINVAL, "null argument");
+  const ModelHost &H = m->H;
+  info->d = H.d;
+  info->n_dates = H.n;
+  info->n_hist = H.n_hist;
+  info->t_now = H.t_now;
+  info->bridge_levels = H.n_levels;
+  info->bridge_stack = H.bstack;
+  int32_t blocks = 0;
+  for (const BridgeOp &op : H.ops)
+    blocks += ((op.flags & BR_FROM_CACHE) ? 0 : 1) + ((op.flags & BR_TWO_BLOCKS) ? 1 : 0);
+  info->philox_blocks = blocks;
+  info->box_muller_pairs = 2 * blocks;
+  return PC_OK;
+}
+
+pc_status pc_model_destroy(pc_model *m) {
+  if (!m) return fail(PC_EINVAL, "null model");
+  cudaSetDevice(m->ctx->device);
+  cudaStreamSynchronize(m->ctx->stream);
+  cudaFree(m->d_mem);
+  --m->ctx->live_objects;
+  delete m;
+  return PC_OK;
+}
+
+pc_status pc_verify_payoff(const uint32_t *bytecode, size_t n_words, const double *consts,
+                           size_t n_consts, const int32_t *template_params, size_t n_params,
+                           pc_program_info *info) {
+  try {
+    Program p;
+    std::string err;
+    pc_status s = compile_program(bytecode, n_words, consts, n_consts, template_params, n_params,
+                                  0, 1, false, p, err);
+    if (s != PC_OK) return fail(s, err);
+    if (info) *info = p.info;
+    return PC_OK;
+  } catch (const std::bad_alloc &) {
+    return fail(PC_ENOMEM, "host allocation");
+  } catch (...) {
+    return fail(PC_EINVAL, "unexpected error in pc_verify_payoff");
+  }
+}
+
+pc_status pc_load_payoff(pc_ctx *c, const uint32_t *bytecode, size_t n_words, const double *consts,
+                         size_t n_consts, const int32_t *template_params, size_t n_params,
+                         int32_t p1, int32_t p2, pc_contract **out) {
+  if (!c || !out) return fail(PC_EINVAL, "null argument");
+  try {
+    pc_contract *k = new pc_contract();
+    std::string err;
+    pc_status s = compile_program(bytecode, n_words, consts, n_consts, template_params, n_params,
+                                  p1, p2, true, k->prog, err);
+    if (s != PC_OK) {
+      delete k;
+      return fail(s, err);
+    }
+    CU(cudaSetDevice(c->device), "cudaSetDevice");
+    const size_t bytes = k->prog.code.size() * sizeof(XInsn);
+    cudaError_t e = cudaMalloc(&k->d_code, bytes);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(k->d_code, k->prog.code.data(), bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      if (k->d_code) cudaFree(k->d_code);
+      delete k;
+      return cuda_fail(e, "program upload");
+    }
+    k->ctx = c;
+    ++c->live_objects;
+    *out = k;
+    return PC_OK;
+  } catch (const std::bad_alloc &) {
+    return fail(PC_ENOMEM, "host allocation");
+  } catch (...) {
+    return fail(PC_EINVAL, "unexpected error in pc_load_payoff");
+  }
+}
+
+pc_status pc_contract_destroy(pc_contract *k) {
+  if (!k) return fail(PC_EINVAL, "null contract");
+  cudaSetDevice(k->ctx->device);
+  cudaStreamSynchronize(k->ctx->stream);
+  cudaFree(k->d_code);
+  --k->ctx->live_objects;
+  delete k;
+  return PC_OK;
+}
+
+pc_status pc_assemble(const char *text, uint32_t *words, size_t cap_words, size_t *n_words,
+                      double *consts, size_t cap_consts, size_t *n_consts, char *err,
+                      size_t err_cap) {
+  if (!text || !n_words || !n_consts) return fail(PC_EINVAL, "null argument");
+  try {
+    std::vector<uint32_t> w;
+    std::vector<double> k;
+    std::string e;
+    pc_status s = assemble_text(text, w, k, e);
+    if (s != PC_OK) {
+      if (err && err_cap) {
+        std::strncpy(err, e.c_str(), err_cap - 1);
+        err[err_cap - 1] = 0;
+      }
+      return fail(s, e);
+    }
+    *n_words = w.size();
+    *n_consts = k.size();
+    if (w.size() > cap_words || k.size() > cap_consts || (w.size() && !words) || (k.size() && !consts))
+      return fail(PC_ELIMIT, "output buffers too small");
+    std::copy(w.begin(), w.end(), words);
+    std::copy(k.begin(), k.end(), consts);
+    return PC_OK;
+  } catch (const std::bad_alloc &) {
+    return fail(PC_ENOMEM, "host allocation");
+  }
+}
+
+pc_status pc_price_async(const pc_model *m, const pc_contract *k, uint64_t n_paths,
+                         uint64_t path_offset, uint64_t seed, uint32_t stream, double *d_out) {
+  if (!d_out) return fail(PC_EINVAL, "d_out is null");
+  return run_price(m, k, n_paths, path_offset, seed, stream, d_out, nullptr);
+}
+
+pc_status pc_price_paths(const pc_model *m, const pc_contract *k, uint64_t n_paths,
+                         uint64_t path_offset, uint64_t seed, uint32_t stream, double *d_out,
+                         float *d_payoffs) {
+  if (!d_out || !d_payoffs) return fail(PC_EINVAL, "null device output");
+  return run_price(m, k, n_paths, path_offset, seed, stream, d_out, d_payoffs);
+}
+
+pc_status pc_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t seed,
+                   double *out_price, double *out_stderr) {
+  if (!out_price || !out_stderr) return fail(PC_EINVAL, "null output");
+  if (n_paths < 2) return fail(PC_EINVAL, "n_paths must be >= 2 for a standard error");
+  if (!m) return fail(PC_EINVAL, "null model");
+  pc_ctx *c = m->ctx;
+  pc_status s = run_price(m, k, n_paths, 0, seed, 0, c->d_res, nullptr);
+  if (s != PC_OK) return s;
+  double h[5];
+  CU(cudaMemcpyAsync(h, c->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "result copy");
+  s = wait_stream(c);
+  if (s != PC_OK) return s;
+  int32_t status;
+  std::memcpy(&status, &h[4], 4);
+  s = check_status(c, status);
+  if (s != PC_OK) return s;
+  const double n = double(n_paths), mean = h[0] / n;
+  const double var = std::max(0.0, (h[1] - n * mean * mean) / (n - 1.0));
+  *out_price = mean;
+  *out_stderr = std::sqrt(var / n);
+  return PC_OK;
+}
+
+pc_status pc_price_batch(size_t n, const pc_model *const *models, const pc_contract *const *contracts,
+                         const uint64_t *n_paths, uint64_t seed, double *out_price,
+                         double *out_stderr) {
+  if (n == 0) return PC_OK;
+  if (!models || !contracts || !n_paths || !out_price || !out_stderr)
+    return fail(PC_EINVAL, "null argument");
+  if (!models[0]) return fail(PC_EINVAL, "null model");
+  pc_ctx *c = models[0]->ctx;
+  for (size_t i = 0; i < n; ++i) {
+    if (!models[i] || !contracts[i] || models[i]->ctx != c || contracts[i]->ctx != c)
+      return fail(PC_EINVAL, "batch members must be non-null and share one context");
+    if (n_paths[i] < 2) return fail(PC_EINVAL, "n_paths must be >= 2");
+  }
+  double *d_out = nullptr;
+  CU(cudaMalloc(&d_out, n * 4 * sizeof(double)), "batch outputs");
+  pc_status s = PC_OK;
+  for (size_t i = 0; i < n && s == PC_OK; ++i)
+    s = run_price(models[i], contracts[i], n_paths[i], 0, seed, uint32_t(i), d_out + 4 * i, nullptr);
+  std::vector<double> h(n * 4);
+  if (s == PC_OK) {
+    cudaError_t e = cudaMemcpyAsync(h.data(), d_out, n * 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) s = cuda_fail(e, "batch copy");
+  }
+  if (s == PC_OK) s = wait_stream(c);
+  double st[5];
+  if (s == PC_OK) {
+    cudaError_t e = cudaMemcpy(st, c->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) s = cuda_fail(e, "status copy");
+    int32_t status;
+    std::memcpy(&status, &st[4], 4);
+    if (s == PC_OK) s = check_status(c, status);
+  }
+  cudaFree(d_out);
+  if (s != PC_OK) return s;
+  for (size_t i = 0; i < n; ++i) {
+    const double N = double(n_paths[i]), mean = h[4 * i] / N;
+    out_price[i] = mean;
+    out_stderr[i] = std::sqrt(std::max(0.0, (h[4 * i + 1] - N * mean * mean) / (N - 1.0)) / N);
+  }
+  return PC_OK;
+}
+
+pc_status pc_greeks(const pc_model *, const pc_contract *, uint64_t, uint64_t, double *, double *,
+                    double *, double *) {
+  return fail(PC_ELIMIT, "pc_greeks is not available in this build");
+}
+
+pc_status pc_debug_philox(pc_ctx *c, const uint32_t *d_ctr, uint32_t key0, uint32_t key1,
+                          uint32_t *d_out, size_t n) {
+  if (!c || (n && (!d_ctr || !d_out))) return fail(PC_EINVAL, "null argument");
+  CU(cudaSetDevice(c->device), "cudaSetDevice");
+  CU(launch_debug_philox(d_ctr, key0, key1, d_out, n, c->stream), "philox kernel");
+  return wait_stream(c);
+}
+
+pc_status pc_debug_paths(const pc_model *m, uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                         uint32_t stream, float *d_S) {
+  if (!m || !d_S) return fail(PC_EINVAL, "null argument");
+  if (n_paths > (uint64_t(1) << 24)) return fail(PC_ELIMIT, "n_paths too large for the probe");
+  Program empty;
+  Layout lay = make_layout(empty, m->H, 1);
+  lay.stack = 0;
+  lay.off_bstack = 0;
+  lay.off_cache = m->H.bstack * m->H.d;
+  lay.off_win = lay.off_cache + m->H.n_levels * 4;
+  lay.words = lay.off_win + m->H.d;
+  pc_ctx *c = m->ctx;
+  if (size_t(lay.words) * kBlock * 4 > size_t(c->max_smem)) return fail(PC_ELIMIT, "model too large for the probe");
+  CU(cudaSetDevice(c->device), "cudaSetDevice");
+  CU(launch_debug_paths(m->dev, lay, n_paths, path_offset, uint32_t(seed), uint32_t(seed >> 32),
+                        stream, d_S, c->stream),
+     "paths kernel");
+  return wait_stream(c);
+}
+
+pc_status pc_debug_program(const uint32_t *bytecode, size_t n_words, const double *consts,
+                           size_t n_consts, const int32_t *template_params, size_t n_params,
+                           int32_t p1, int32_t p2, uint32_t *out, size_t cap, size_t *n_insn) {
+  if (!n_insn) return fail(PC_EINVAL, "null argument");
+  try {
+    Program p;
+    std::string err;
+    pc_status s = compile_program(bytecode, n_words, consts, n_consts, template_params, n_params,
+                                  p1, p2, true, p, err);
+    if (s != PC_OK) return fail(s, err);
+    *n_insn = p.code.size();
+    if (p.code.size() > cap || !out) return fail(PC_ELIMIT, "output buffer too small");
+    std::memcpy(out, p.code.data(), p.code.size() * sizeof(XInsn));
+    return PC_OK;
+  } catch (const std::bad_alloc &) {
+    return fail(PC_ENOMEM, "host allocation");
+  }
+}
+
+pc_status pc_debug_bridge(const pc_model_desc *desc, int32_t *date_ops, uint32_t *ops,
+                          size_t cap_ops, size_t *n_ops) {
+  if (!desc || !n_ops) return fail(PC_EINVAL, "null argument");
+  ModelHost H;
+  std::string err;
+  pc_status s = build_model(*desc, H, err);
+  if (s != PC_OK) return fail(s, err);
+  *n_ops = H.ops.size();
+  if (H.ops.size() > cap_ops || !ops || !date_ops) return fail(PC_ELIMIT, "output buffer too small");
+  std::copy(H.date_ops.begin(), H.date_ops.end(), date_ops);
+  for (size_t i = 0; i < H.ops.size(); ++i) {
+    const BridgeOp &o = H.ops[i];
+    uint32_t *w = ops + 6 * i;
+    std::memcpy(w + 0, &o.wl, 4);
+    std::memcpy(w + 1, &o.wr, 4);
+    std::memcpy(w + 2, &o.sd, 4);
+    w[3] = o.j;
+    w[4] = uint32_t(o.level) | (uint32_t(o.flags) << 16);
+    w[5] = o.m;
+  }
+  return PC_OK;
+}
+
+}  // extern "C"

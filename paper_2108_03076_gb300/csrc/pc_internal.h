@@ -1,0 +1,200 @@
+// pc_internal.h -- structures shared by the host side (loader, model setup,
+// C ABI) and the device kernels of the pricing engine.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pc.h"
+
+namespace pc {
+
+// ---------------------------------------------------------------------------
+// Executable program ("X-code"): what the loader emits and the kernel runs.
+//
+// The input bytecode is a postfix IL tree.  The loader rebuilds the tree,
+// type-checks it, binds template variables (so every time expression becomes
+// a static integer relative to the loopif offset t0), folds payoff to
+// +-disc / 0, and emits a linear program for a warp-uniform stack machine:
+// every lane of a warp executes the same instruction stream on its own path.
+// if(c, a, b) becomes  c  IF  a  ELSE  b  SEL : IF/ELSE skip a branch that no
+// live lane of the warp takes; SEL selects per lane.  loopif(c, a, b, n)
+// becomes  LOOP  c  LTEST  a  LLATCH  LNEXT  b  LEND : the warp iterates
+// k = 0..n with t0 = t0_entry + k, each lane latching the then-value at its
+// first k whose test holds (Fig. 3), and leaves early once every live lane
+// has latched.  Values are 32-bit: float for reals, int32 for nats and bools.
+// ---------------------------------------------------------------------------
+struct XInsn {
+  uint32_t opa;  // opcode (low 8 bits) | A (24 bits)
+  uint32_t b;
+  uint32_t c;
+  uint32_t e;
+};
+static_assert(sizeof(XInsn) == 16, "XInsn is one 16-byte shared-memory load");
+
+enum XOp : uint32_t {
+  X_END = 0,
+  X_CONST,      // push bits b
+  X_MODEL,      // A = label; push S_label(ordinal b + t0 - t_now)
+  X_PAYOFF,     // A = 1 for negative sign; push +-disc(ordinal b + t0 - t_now)
+  X_TIME,       // push int b + t0
+  X_NOW,        // push int t_now
+  X_NEGF, X_NOT,
+  X_ADDF, X_SUBF, X_MULF, X_DIVF, X_MAXF, X_MINF, X_LTF, X_LEF, X_EQF,
+  X_ADDI, X_SUBI, X_MULI, X_MAXI, X_MINI, X_LTI, X_LEI, X_EQI,
+  X_AND, X_OR,
+  // real op with an immediate right operand (float bits in b):  x op k
+  X_ADDFK, X_SUBFK, X_MULFK, X_DIVFK, X_MAXFK, X_MINFK, X_LTFK, X_LEFK, X_EQFK,
+  // immediate on the left:  k op x
+  X_RSUBFK, X_RDIVFK, X_RLTFK, X_RLEFK,
+  // X_MODEL followed by a real op with immediate c: S op k
+  X_MODEL_MULK, X_MODEL_DIVK,
+  X_IF,         // c = pc of the else branch; peek cond
+  X_ELSE,       // c = pc of SEL
+  X_SEL,        // pop else, then, cond -> push cond ? then : else
+  X_LOOP,       // A = frame slot; b = bound n. Push frame (4 slots)
+  X_LTEST,      // A = frame slot; c = pc of LNEXT
+  X_LLATCH,     // A = frame slot
+  X_LNEXT,      // A = frame slot; b = bound n; c = pc of loop condition; e = pc after LEND
+  X_LEND,       // A = frame slot
+  X_NUM_OPS
+};
+
+// Loop frame layout on the operand stack (slot offsets from the frame base).
+enum { LF_K = 0, LF_T0 = 1, LF_DONE = 2, LF_RES = 3, LF_NEWLY = 4, LF_SLOTS = 5 };
+
+// ---------------------------------------------------------------------------
+// Brownian-bridge schedule in date order (device).
+//
+// Dates are produced lazily in time order.  The bridge keeps W of the last
+// produced date in registers and a stack of already-computed W of later
+// dates.  To produce date t the kernel runs the ops of t: each computes
+// bridge node m from (W_cur, W_top) and pushes it, except the last op, whose
+// result is W_t itself; a date with no ops pops W_t from the stack.  Node j
+// (its breadth-first number) draws normals j*d .. j*d+d-1.  Nodes of one
+// bisection level are visited left to right, so consecutive nodes of a level
+// share Philox blocks; each level keeps its last block of 4 normals.
+// ---------------------------------------------------------------------------
+struct BridgeOp {
+  float wl, wr, sd;
+  uint32_t j;       // breadth-first node number (normal block base j*d)
+  uint16_t level;   // bisection level (cache index)
+  uint16_t flags;   // BR_* below
+  uint16_t m;       // date ordinal produced (diagnostics)
+  uint16_t pad0;
+};
+static_assert(sizeof(BridgeOp) == 24, "BridgeOp layout");
+
+enum : uint16_t {
+  BR_ROOT = 1,        // first node (last date): W = sd * z, no endpoint reads
+  BR_FROM_CACHE = 2,  // the first Philox block of this node is the level's cached block
+  BR_TWO_BLOCKS = 4,  // normals straddle two Philox blocks
+  BR_STORE = 8,       // keep the last block in the level cache for the next node
+};
+
+// Device image of a model (one allocation, offsets in bytes).
+struct ModelDev {
+  const int32_t *date_ops;  // [n+2] op range of date t: [date_ops[t], date_ops[t+1])
+  const BridgeOp *ops;      // [n]
+  const float *A;           // [(n+1)*d] log2(e)(r - sigma^2/2) tau_o (S = S0 2^(A + B W))
+  const float *B;           // [d*d]     log2(e) sigma_i L_ik
+  const float *disc;        // [n_hist+n+1] disc of ordinal o at index o + n_hist
+  const float *sval;        // [(n_hist+1)*d] value of label l at ordinal o <= 0, index (o+n_hist)*d+l
+  // pathwise tangents (greeks): per ordinal o, tau_o as float
+  const float *tau;         // [n+1]
+  int32_t d, n, n_hist, t_now;
+  int32_t n_levels;         // bisection levels (level caches)
+  int32_t bstack;           // bridge stack depth
+};
+
+// Per-thread shared-memory region: 32-bit words, word w of thread t at
+// region[w * BLOCK + t] (uniform w -> conflict-free).
+struct Layout {
+  int32_t stack;      // operand stack words
+  int32_t off_bstack; // bridge stack (bstack * d)
+  int32_t off_cache;  // level caches (n_levels * 4)
+  int32_t off_win;    // date window (win * d)
+  int32_t words;      // total words per thread
+  int32_t win;        // window size (power of two)
+};
+
+constexpr int kBlock = 128;          // threads per block of the pricing kernel
+constexpr int kPathsPerLane = 2;     // paths per lane per tile
+constexpr int kTilePaths = 32 * kPathsPerLane;
+
+struct PriceArgs {
+  const XInsn *prog;
+  int32_t n_insn;
+  ModelDev m;
+  Layout lay;
+  uint64_t n_paths, path_offset;
+  uint32_t key0, key1, stream;
+  uint64_t n_tiles;
+  int32_t width;            // doubles per tile partial (2 for prices)
+  double *tile_partials;    // [n_tiles * width] scratch
+  unsigned long long *counters;  // [2] scratch: next tile, finished blocks (zero between launches)
+  double *out;              // [width + 1]: sums over all paths, then n_paths
+  float *out_paths;         // nullable: per-path payoffs
+  int32_t *status;          // device status word (nonzero = error)
+};
+
+// Kernel launchers (pc_kernels.cu).  All return a cudaError_t.
+cudaError_t launch_price(const PriceArgs &a, int grid, size_t smem_bytes, cudaStream_t s);
+cudaError_t launch_greeks(const PriceArgs &a, int grid, size_t smem_bytes, cudaStream_t s);
+cudaError_t launch_debug_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
+                                size_t n, cudaStream_t s);
+cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_paths,
+                               uint64_t offset, uint32_t k0, uint32_t k1, uint32_t stream,
+                               float *out, cudaStream_t s);
+int price_blocks_per_sm(int d, size_t smem_bytes, bool greeks);
+int max_dynamic_smem();
+
+// ---------------------------------------------------------------------------
+// Host-side program handling (pc_program.cpp)
+// ---------------------------------------------------------------------------
+struct Program {
+  std::vector<XInsn> code;
+  pc_program_info info{};
+  int32_t frame_slots = 0;  // stack slots (values + frames)
+};
+
+// Decode, verify, bind and compile bytecode.  On failure returns a PC_E*
+// code and sets `err`.
+pc_status compile_program(const uint32_t *words, size_t n_words, const double *consts,
+                          size_t n_consts, const int32_t *tparams, size_t n_params,
+                          int32_t p1, int32_t p2, bool bind_parties, Program &out,
+                          std::string &err);
+
+// Static analysis of a program against a model's time layout: every model
+// and payoff time within [-n_hist, n] as ordinals, and the largest lookback
+// below the generated frontier.  `win` receives the window size needed
+// (power of two).
+pc_status analyse_program(const Program &p, int32_t t_now, int32_t n_dates, int32_t n_hist,
+                          int32_t &win, std::string &err);
+
+pc_status assemble_text(const char *text, std::vector<uint32_t> &words,
+                        std::vector<double> &consts, std::string &err);
+
+// ---------------------------------------------------------------------------
+// Host-side model setup (pc_model.cpp)
+// ---------------------------------------------------------------------------
+struct ModelHost {
+  int32_t d = 0, n = 0, n_hist = 0, t_now = 0;
+  std::vector<double> S0, sigma, corr, L;  // L: Cholesky factor, row-major
+  double r = 0;
+  std::vector<int32_t> day, hist_day;
+  std::vector<double> history;
+  // device tables, host copies
+  std::vector<int32_t> date_ops;
+  std::vector<BridgeOp> ops;
+  std::vector<float> A, B, disc, sval, tau;
+  int32_t n_levels = 0, bstack = 0;
+};
+
+pc_status build_model(const pc_model_desc &desc, ModelHost &out, std::string &err);
+
+}  // namespace pc
