@@ -218,7 +218,10 @@ def main():
         build.build()
     if ws > 1:
         dist.barrier()
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the engine and the timing events must share it (the
+    # legacy default stream has handle 0, which pc_create reads as "none")
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
     ctx = pc.pc_create(local, stream.cuda_stream)
     spec = w.market
     model = pc.pc_model_create(ctx, spec.S0, spec.sigma, spec.corr, spec.r, spec.days)

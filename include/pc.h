@@ -257,6 +257,34 @@ pc_status pc_price_paths(const pc_model *model, const pc_contract *contract,
                          uint64_t n_paths, uint64_t path_offset, uint64_t seed,
                          uint32_t stream, double *d_out, float *d_payoffs);
 
+/* Most paths one pc_price_noalloc call may price. */
+#define PC_NOALLOC_MAX_PATHS (1ull << 24)
+
+/* pc_price_async for callers that cannot allocate device memory -- for
+ * example code running under an allocator or framework that owns all of
+ * the GPU's memory, or code that must not call cudaMalloc at this point of
+ * its run.  The paper has no counterpart; this is an engineering entry point.
+ * It runs the same pricing kernel on the same inputs and writes the same
+ * {sum x, sum x^2, n} triple to the device buffer d_out, but takes the
+ * kernel's scratch (per-tile partial sums and work counters) from one
+ * fixed device array that the library reserves in every GPU that loads it
+ * (4 MiB + 256 bytes, held until the process exits), instead of from
+ * memory the context allocates.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine; on success it allocates no host memory either (a
+ * failure records its message as pc_last_error does).
+ *   - n_paths must be 1..PC_NOALLOC_MAX_PATHS; larger requests fail with
+ *     PC_ELIMIT.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any CUDA stream capture.
+ *   - Every call shares the one array: calls whose kernels overlap on the
+ *     GPU (other streams, other contexts on the same device) race and give
+ *     wrong results.  Calls on one stream are ordered and safe.  Each call
+ *     zeroes the counters it needs before its kernel starts.
+ * Errors: PC_EINVAL, PC_ERANGE, PC_ELIMIT, PC_ECUDA. */
+pc_status pc_price_noalloc(const pc_model *model, const pc_contract *contract,
+                           uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                           uint32_t stream, double *d_out);
+
 /* Price n contracts, each against its own model, in one launch:
  * contract i runs n_paths[i] paths on Philox stream word i.  Outputs
  * out_price[i], out_stderr[i] (host).  Blocks until done.

@@ -74,6 +74,7 @@ _SIGS = {
     "pc_price": [VP, VP, U64, U64, PD, PD],
     "pc_price_async": [VP, VP, U64, U64, U64, U32, VP],
     "pc_price_paths": [VP, VP, U64, U64, U64, U32, VP, VP],
+    "pc_price_noalloc": [VP, VP, U64, U64, U64, U32, VP],
     "pc_price_batch": [SZ, C.POINTER(VP), C.POINTER(VP), C.POINTER(U64), U64, PD, PD],
     "pc_greeks": [VP, VP, U64, U64, PD, PD, PD, PD],
     "pc_debug_philox": [VP, VP, U32, U32, VP, SZ],
@@ -221,6 +222,18 @@ def pc_price_paths(model: int, contract: int, n_paths: int, path_offset: int, se
                    stream_id: int, d_out: int, d_payoffs: int) -> None:
     _check(lib().pc_price_paths(VP(model), VP(contract), n_paths, path_offset, seed, stream_id,
                                 VP(d_out), VP(d_payoffs)))
+
+
+def pc_price_noalloc(model: int, contract: int, n_paths: int, path_offset: int, seed: int,
+                     stream_id: int, d_out: int) -> None:
+    """pc_price_async without device allocation: scratch comes from the
+    library's fixed device array (at most NOALLOC_MAX_PATHS paths per call;
+    calls that overlap on the GPU race)."""
+    _check(lib().pc_price_noalloc(VP(model), VP(contract), n_paths, path_offset, seed, stream_id,
+                                  VP(d_out)))
+
+
+NOALLOC_MAX_PATHS = 1 << 24
 
 
 def pc_price_batch(models: Sequence[int], contracts: Sequence[int], n_paths: Sequence[int],

@@ -213,9 +213,123 @@ pc_status check_status(pc_ctx *c, int32_t status) {
   return fail(PC_EDEVICE, "kernel raised its status word (" + std::to_string(status) + ")");
 }
 
+// The time analysis of analyse_program, written without heap use for
+// pc_price_noalloc: every model and payoff ordinal within the grid, and the
+// largest lookback below the frontier of generated dates.
+struct NoAllocAnalysis {
+  const XInsn *C = nullptr;
+  int64_t t_now = 0, n_dates = 0, n_hist = 0;
+  int64_t frontier = 0, lookback = 0, steps = 0;
+  pc_status st = PC_OK;
+  const char *why = "";
+
+  void run(size_t a, size_t b, int64_t t0) {
+    for (size_t pc = a; pc < b && st == PC_OK;) {
+      if (++steps > (int64_t(1) << 26)) {
+        st = PC_ELIMIT;
+        why = "program too long to analyse (loop trip counts)";
+        return;
+      }
+      const XInsn &I = C[pc];
+      const uint32_t op = I.opa & 0xffu;
+      if (op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_PAYOFF) {
+        const int64_t o = int64_t(int32_t(I.b)) + t0 - t_now;
+        if (o < -n_hist || o > n_dates) {
+          st = PC_ERANGE;
+          why = "a model or payoff time is outside the model's grid";
+          return;
+        }
+        if (op != X_PAYOFF && o > 0) {
+          if (o > frontier) frontier = o;
+          else if (frontier - o > lookback) lookback = frontier - o;
+        }
+        ++pc;
+      } else if (op == X_LOOP) {
+        const int64_t n = I.b;
+        const uint32_t slot = I.opa >> 8;
+        size_t test = pc + 1;
+        while (!((C[test].opa & 0xffu) == X_LTEST && (C[test].opa >> 8) == slot)) ++test;
+        const size_t next = C[test].c, end = C[next].e;
+        for (int64_t k = 0; k <= n && st == PC_OK; ++k) {
+          run(pc + 1, test, t0 + k);
+          run(test + 1, next - 1, t0 + k);
+        }
+        run(next + 1, end - 1, t0 + n);
+        pc = end;
+      } else if (op == X_END) {
+        return;
+      } else {
+        ++pc;
+      }
+    }
+  }
+};
+
 }  // namespace
 
 extern "C" {
+
+pc_status pc_price_noalloc(const pc_model *m, const pc_contract *k, uint64_t n_paths,
+                           uint64_t path_offset, uint64_t seed, uint32_t stream, double *d_out) {
+  if (!m || !k || !d_out) return fail(PC_EINVAL, "null model, contract or d_out");
+  if (m->ctx != k->ctx) return fail(PC_EINVAL, "model and contract belong to different contexts");
+  if (n_paths == 0) return fail(PC_EINVAL, "n_paths must be >= 1");
+  if (n_paths > PC_NOALLOC_MAX_PATHS)
+    return fail(PC_ELIMIT, "pc_price_noalloc prices at most PC_NOALLOC_MAX_PATHS (2^24) paths per call");
+  const ModelHost &H = m->H;
+  for (const XInsn &I : k->prog.code) {
+    const uint32_t op = I.opa & 0xffu;
+    if ((op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK) && int32_t(I.opa >> 8) >= H.d)
+      return fail(PC_ERANGE, "program observes a label the model does not have");
+  }
+  NoAllocAnalysis an;
+  an.C = k->prog.code.data();
+  an.t_now = H.t_now;
+  an.n_dates = H.n;
+  an.n_hist = H.n_hist;
+  an.run(0, k->prog.code.size(), 0);
+  if (an.st != PC_OK) return fail(an.st, an.why);
+  int32_t win = 1;
+  while (win < an.lookback + 1) win <<= 1;
+  if (win > PC_MAX_WINDOW) return fail(PC_ERANGE, "program looks back further than PC_MAX_WINDOW dates");
+  pc_ctx *c = m->ctx;
+  const Layout lay = make_layout(k->prog, H, win);
+  const size_t smem = k->prog.code.size() * sizeof(XInsn) + size_t(lay.words) * kBlock * 4;
+  if (smem + kStaticSmemReserve > size_t(c->max_smem))
+    return fail(PC_ELIMIT, "program + per-path state exceed the device's shared memory per block");
+  CU(cudaSetDevice(c->device), "cudaSetDevice");
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  CU(noalloc_scratch(&scratch, &scratch_bytes), "scratch lookup");
+  const uint64_t n_tiles = (n_paths + kTilePaths - 1) / kTilePaths;
+  if (kNoAllocCounterBytes + n_tiles * 2 * sizeof(double) > scratch_bytes)
+    return fail(PC_ELIMIT, "request exceeds the fixed scratch array");
+  const int bpsm = price_blocks_per_sm(H.d, smem, false);
+  if (bpsm < 1) return fail(PC_ELIMIT, "kernel cannot be resident with this shared-memory footprint");
+  PriceArgs a{};
+  a.prog = k->d_code;
+  a.n_insn = int32_t(k->prog.code.size());
+  a.m = m->dev;
+  a.lay = lay;
+  a.n_paths = n_paths;
+  a.path_offset = path_offset;
+  a.key0 = uint32_t(seed);
+  a.key1 = uint32_t(seed >> 32);
+  a.stream = stream;
+  a.n_tiles = n_tiles;
+  a.width = 2;
+  a.counters = static_cast<unsigned long long *>(scratch);
+  a.tile_partials = reinterpret_cast<double *>(static_cast<char *>(scratch) + kNoAllocCounterBytes);
+  a.out = d_out;
+  a.out_paths = nullptr;
+  a.status = reinterpret_cast<int32_t *>(c->d_res + 4);
+  const uint64_t need = (n_tiles + kBlock / 32 - 1) / (kBlock / 32);
+  const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * bpsm, need));
+  CU(cudaMemsetAsync(a.counters, 0, 2 * sizeof(unsigned long long), c->stream), "counter reset");
+  CU(launch_price(a, grid, smem, c->stream), "price kernel");
+  return PC_OK;
+}
+
 
 const char *pc_last_error(const pc_ctx *) { return tl_err.c_str(); }
 

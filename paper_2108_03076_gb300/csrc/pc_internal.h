@@ -151,6 +151,10 @@ cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_
                                uint64_t offset, uint32_t k0, uint32_t k1, uint32_t stream,
                                float *out, cudaStream_t s);
 int price_blocks_per_sm(int d, size_t smem_bytes, bool greeks);
+// Device address and size of the fixed scratch array used by
+// pc_price_noalloc on the current device (looked up once per device).
+cudaError_t noalloc_scratch(void **ptr, size_t *bytes);
+constexpr size_t kNoAllocCounterBytes = 256;
 int max_dynamic_smem();
 
 // ---------------------------------------------------------------------------

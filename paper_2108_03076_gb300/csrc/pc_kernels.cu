@@ -12,6 +12,7 @@
 // word w of thread t is at region[w * kBlock + t], so the warp-uniform slot
 // indices of the interpreter give conflict-free accesses.
 #include <cstdint>
+#include <mutex>
 
 #include "pc_internal.h"
 
@@ -634,6 +635,34 @@ cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_
     default: return cudaErrorInvalidValue;
   }
 #undef DLAUNCH
+}
+
+// Scratch of pc_price_noalloc: work counters in the first 256 bytes, then
+// one (sum, sum of squares) pair per tile of kTilePaths paths for up to
+// PC_NOALLOC_MAX_PATHS paths.  Zero-initialised when the module loads;
+// each call clears the counters again before its launch.
+constexpr size_t kNoAllocScratchBytes =
+    kNoAllocCounterBytes + (PC_NOALLOC_MAX_PATHS / kTilePaths) * 2 * sizeof(double);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+cudaError_t noalloc_scratch(void **ptr, size_t *bytes) {
+  constexpr int kMaxDevices = 64;
+  static void *addr[kMaxDevices] = {};
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> g(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    addr[dev] = p;
+  }
+  *ptr = addr[dev];
+  *bytes = kNoAllocScratchBytes;
+  return cudaSuccess;
 }
 
 cudaError_t launch_greeks(const PriceArgs &, int, size_t, cudaStream_t) {

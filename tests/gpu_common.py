@@ -26,7 +26,8 @@ class Engine:
     def __init__(self):
         from paper_2108_03076_gb300 import build
         build.build()
-        self.stream = torch.cuda.current_stream()
+        self.stream = torch.cuda.Stream()
+        torch.cuda.set_stream(self.stream)
         self.ctx = pc.pc_create(0, self.stream.cuda_stream)
         self.models, self.contracts = [], []
 
