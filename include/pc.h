@@ -268,7 +268,7 @@ pc_status pc_price_paths(const pc_model *model, const pc_contract *contract,
  * {sum x, sum x^2, n} triple to the device buffer d_out, but takes the
  * kernel's scratch (per-tile partial sums and work counters) from one
  * fixed device array that the library reserves in every GPU that loads it
- * (4 MiB + 256 bytes, held until the process exits), instead of from
+ * (4 MiB + 18 KiB, held until the process exits), instead of from
  * memory the context allocates.  It calls no cudaMalloc, cudaFree or other
  * allocating routine; on success it allocates no host memory either (a
  * failure records its message as pc_last_error does).
@@ -320,20 +320,21 @@ pc_status pc_debug_paths(const pc_model *model, uint64_t n_paths,
                          uint64_t path_offset, uint64_t seed, uint32_t stream,
                          float *d_S);
 
-/* Host-only: the executable form pc_load_payoff would run for this program
- * (16 bytes per instruction: opcode | A << 8, then three operand words).
- * Writes at most cap instructions to out and the count to *n_insn.
- * Errors: as pc_load_payoff; PC_ELIMIT if cap is too small. */
+/* Host-only: the executable form pc_load_payoff would run for this program:
+ * 4 words per instruction (opcode | A << 8, then three operand words), then
+ * the program's constant pool (float bits).  Writes *n_insn and *n_pool,
+ * and the 4 * n_insn + n_pool words to out when cap_words allows.
+ * Errors: as pc_load_payoff; PC_ELIMIT if cap_words is too small. */
 pc_status pc_debug_program(const uint32_t *bytecode, size_t n_words,
                            const double *consts, size_t n_consts,
                            const int32_t *template_params, size_t n_params,
-                           int32_t p1, int32_t p2, uint32_t *out, size_t cap,
-                           size_t *n_insn);
+                           int32_t p1, int32_t p2, uint32_t *out, size_t cap_words,
+                           size_t *n_insn, size_t *n_pool);
 
 /* Host-only: the date-ordered bridge schedule pc_model_create builds for
  * *desc: date_ops[0..n_dates+1] (ops of date t are date_ops[t] ..
  * date_ops[t+1]-1) and 6 words per op (wl, wr, sd as float bits; node
- * number; level | flags << 16; date ordinal).  Writes at most cap_ops ops.
+ * number; cache slot | flags << 16; date ordinal).  Writes at most cap_ops ops.
  * Errors: as pc_model_create's validation; PC_ELIMIT if cap_ops is small. */
 pc_status pc_debug_bridge(const pc_model_desc *desc, int32_t *date_ops, uint32_t *ops,
                           size_t cap_ops, size_t *n_ops);

@@ -79,7 +79,8 @@ _SIGS = {
     "pc_greeks": [VP, VP, U64, U64, PD, PD, PD, PD],
     "pc_debug_philox": [VP, VP, U32, U32, VP, SZ],
     "pc_debug_paths": [VP, U64, U64, U64, U32, VP],
-    "pc_debug_program": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, PU32, SZ, C.POINTER(SZ)],
+    "pc_debug_program": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, PU32, SZ, C.POINTER(SZ),
+                         C.POINTER(SZ)],
     "pc_debug_bridge": [C.POINTER(ModelDesc), PI32, PU32, SZ, C.POINTER(SZ)],
 }
 EXPORTED = tuple(_SIGS)
@@ -265,18 +266,20 @@ def pc_debug_paths(model: int, n_paths: int, path_offset: int, seed: int, stream
     _check(lib().pc_debug_paths(VP(model), n_paths, path_offset, seed, stream_id, VP(d_S)))
 
 
-def pc_debug_program(words, consts, tparams=(), p1: int = 0, p2: int = 1) -> np.ndarray:
-    """Executable form of a program: uint32 [n_insn, 4]."""
+def pc_debug_program(words, consts, tparams=(), p1: int = 0, p2: int = 1):
+    """Executable form of a program: (uint32 [n_insn, 4], float32 pool)."""
     w, k, t = _arr(words, np.uint32), _arr(consts, np.float64), _arr(tparams, np.int32)
-    n = SZ(0)
+    n, npool = SZ(0), SZ(0)
     lib().pc_debug_program(_ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,
-                           _ptr(t, C.c_int32), t.size, p1, p2, None, 0, C.byref(n))
-    out = np.zeros((max(n.value, 1), 4), np.uint32)
+                           _ptr(t, C.c_int32), t.size, p1, p2, None, 0, C.byref(n), C.byref(npool))
+    out = np.zeros(4 * n.value + npool.value + 1, np.uint32)
     _check(lib().pc_debug_program(_ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,
                                   _ptr(t, C.c_int32), t.size, p1, p2,
-                                  out.ctypes.data_as(C.POINTER(C.c_uint32)), out.shape[0],
-                                  C.byref(n)))
-    return out[:n.value]
+                                  out.ctypes.data_as(C.POINTER(C.c_uint32)), out.size,
+                                  C.byref(n), C.byref(npool)))
+    code = out[:4 * n.value].reshape(n.value, 4)
+    pool = out[4 * n.value:4 * n.value + npool.value].view(np.float32)
+    return code, pool
 
 
 def pc_debug_bridge(S0, sigma, corr, r, days, t_now=0, history=None, hist_days=None):

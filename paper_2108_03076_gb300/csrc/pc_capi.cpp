@@ -28,7 +28,7 @@ struct pc_ctx {
   double *d_res = nullptr;       // [8]: sum, sumsq, n, -, status word (int32 at d_res+4)
   double *d_partials = nullptr;  // tile partials (scratch)
   size_t partial_cap = 0;        // doubles
-  unsigned long long *d_counters = nullptr;  // [2] tile counter, finished blocks (scratch)
+  unsigned char *d_control = nullptr;  // reduction control block (kControlBytes, zero between launches)
   double timeout_s = 300.0;
   int live_objects = 0;
 };
@@ -101,8 +101,8 @@ Layout make_layout(const Program &p, const ModelHost &H, int32_t win) {
   Layout L{};
   L.stack = p.frame_slots;
   L.off_bstack = L.stack;
-  L.off_cache = L.off_bstack + H.bstack * H.d;
-  L.off_win = L.off_cache + H.n_levels * 4;
+  L.off_cache = L.off_bstack + H.bstack * H.d;  // caches are in registers: no words
+  L.off_win = L.off_cache;
   L.win = win;
   L.words = L.off_win + win * H.d;
   return L;
@@ -120,6 +120,24 @@ pc_status ensure_partials(pc_ctx *c, size_t doubles) {
   return PC_OK;
 }
 
+// Constant-pool floats of a program, rounded up to whole 16-byte words.
+size_t pool_padded(const Program &p) { return (p.pool.size() + 3) & ~size_t(3); }
+
+// Highest underlying label a program reads (-1 if none).
+int32_t max_label(const Program &p) {
+  int32_t top = -1;
+  for (const XInsn &I : p.code) {
+    const uint32_t op = I.opa & 0xffu;
+    if (op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK) {
+      top = std::max(top, int32_t(I.opa >> 8));
+    } else if (op == X_LRED || op == X_LANY) {
+      const uint32_t n = ((I.opa >> 8 >> 8) & 3u) + 1;
+      for (uint32_t i = 0; i < n; ++i) top = std::max(top, int32_t((I.opa >> 8 >> (10 + 2 * i)) & 3u));
+    }
+  }
+  return top;
+}
+
 pc_status window_for(const pc_model *m, const pc_contract *k, int32_t &win) {
   auto *kc = const_cast<pc_contract *>(k);
   std::lock_guard<std::mutex> g(kc->mu);
@@ -127,12 +145,10 @@ pc_status window_for(const pc_model *m, const pc_contract *k, int32_t &win) {
   auto it = kc->win_cache.find(key);
   if (it != kc->win_cache.end()) { win = it->second; return PC_OK; }
   // labels must exist in the model
-  for (const XInsn &I : k->prog.code) {
-    uint32_t op = I.opa & 0xffu;
-    if ((op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK) && int32_t(I.opa >> 8) >= m->H.d)
-      return fail(PC_ERANGE, "program observes label " + std::to_string(I.opa >> 8) +
-                                 " but the model has " + std::to_string(m->H.d) + " underlyings");
-  }
+  const int32_t top = max_label(k->prog);
+  if (top >= m->H.d)
+    return fail(PC_ERANGE, "program observes label " + std::to_string(top) + " but the model has " +
+                               std::to_string(m->H.d) + " underlyings");
   std::string err;
   pc_status s = analyse_program(k->prog, m->H.t_now, m->H.n, m->H.n_hist, win, err);
   if (s != PC_OK) return fail(s, err);
@@ -147,8 +163,28 @@ constexpr size_t kStaticSmemReserve = 2048;
 struct Launch {
   PriceArgs args{};
   int grid = 0;
+  int block = kBlock;
   size_t smem = 0;
 };
+
+// Block size (128, 64 or 32 threads) that keeps the most warps resident per
+// SM given the program's shared-memory footprint; 0 if none fits.
+int pick_block(const Program &p, int words, int max_smem, int d, size_t &smem) {
+  int best = 0, best_warps = 0;
+  size_t best_smem = 0;
+  for (int b = kBlock; b >= 32; b /= 2) {
+    const size_t sm = price_smem_bytes(p.code.size(), pool_padded(p), words, b);
+    if (sm + kStaticSmemReserve > size_t(max_smem)) continue;
+    const int warps = price_blocks_per_sm(d, b, sm, false) * (b / 32);
+    if (warps > best_warps) {
+      best = b;
+      best_warps = warps;
+      best_smem = sm;
+    }
+  }
+  smem = best ? best_smem : price_smem_bytes(p.code.size(), pool_padded(p), words, 32);
+  return best;
+}
 
 pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
                   uint64_t seed, uint32_t stream, Launch &L) {
@@ -161,15 +197,16 @@ pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uin
   if (s != PC_OK) return s;
   pc_ctx *c = m->ctx;
   const Layout lay = make_layout(k->prog, m->H, win);
-  L.smem = size_t(k->prog.code.size()) * sizeof(XInsn) + size_t(lay.words) * kBlock * 4;
-  if (L.smem + kStaticSmemReserve > size_t(c->max_smem))
+  L.block = pick_block(k->prog, lay.words, c->max_smem, m->H.d, L.smem);
+  if (!L.block)
     return fail(PC_ELIMIT, "program + per-path state need " + std::to_string(L.smem) +
-                               " bytes of shared memory per block; the device offers " +
+                               " bytes of shared memory for a 32-thread block; the device offers " +
                                std::to_string(c->max_smem));
   const uint64_t n_tiles = (n_paths + kTilePaths - 1) / kTilePaths;
   PriceArgs &a = L.args;
   a.prog = k->d_code;
   a.n_insn = int32_t(k->prog.code.size());
+  a.n_pool = int32_t(pool_padded(k->prog));
   a.m = m->dev;
   a.lay = lay;
   a.n_paths = n_paths;
@@ -179,9 +216,9 @@ pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uin
   a.stream = stream;
   a.n_tiles = n_tiles;
   a.status = reinterpret_cast<int32_t *>(c->d_res + 4);
-  const int bpsm = price_blocks_per_sm(m->H.d, L.smem, false);
+  const int bpsm = price_blocks_per_sm(m->H.d, L.block, L.smem, false);
   if (bpsm < 1) return fail(PC_ELIMIT, "kernel cannot be resident with this shared-memory footprint");
-  const uint64_t warps_per_block = kBlock / 32;
+  const uint64_t warps_per_block = uint64_t(L.block) / 32;
   const uint64_t need = (n_tiles + warps_per_block - 1) / warps_per_block;
   L.grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * bpsm, need));
   return PC_OK;
@@ -196,12 +233,13 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
   s = ensure_partials(c, size_t(L.args.n_tiles) * 2);
   if (s != PC_OK) return s;
   L.args.width = 2;
+  reduction_chunks(L.args.n_tiles, L.args.chunk_tiles, L.args.n_chunks);
   L.args.tile_partials = c->d_partials;
-  L.args.counters = c->d_counters;
+  L.args.control = c->d_control;
   L.args.out = d_out;
   L.args.out_paths = d_payoffs;
   CU(cudaSetDevice(c->device), "cudaSetDevice");
-  CU(launch_price(L.args, L.grid, L.smem, c->stream), "price kernel");
+  CU(launch_price(L.args, L.grid, L.block, L.smem, c->stream), "price kernel");
   return PC_OK;
 }
 
@@ -232,7 +270,8 @@ struct NoAllocAnalysis {
       }
       const XInsn &I = C[pc];
       const uint32_t op = I.opa & 0xffu;
-      if (op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_PAYOFF) {
+      if (op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_PAYOFF ||
+          op == X_LRED || op == X_LANY) {
         const int64_t o = int64_t(int32_t(I.b)) + t0 - t_now;
         if (o < -n_hist || o > n_dates) {
           st = PC_ERANGE;
@@ -246,9 +285,14 @@ struct NoAllocAnalysis {
         ++pc;
       } else if (op == X_LOOP) {
         const int64_t n = I.b;
-        const uint32_t slot = I.opa >> 8;
-        size_t test = pc + 1;
-        while (!((C[test].opa & 0xffu) == X_LTEST && (C[test].opa >> 8) == slot)) ++test;
+        const size_t test = I.c;
+        if ((C[test].opa & 0xffu) == X_LSTEPK) {
+          const size_t end = C[test].e;
+          for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(pc + 1, test, t0 + k);
+          run(test + 1, end - 1, t0 + n);
+          pc = end;
+          continue;
+        }
         const size_t next = C[test].c, end = C[next].e;
         for (int64_t k = 0; k <= n && st == PC_OK; ++k) {
           run(pc + 1, test, t0 + k);
@@ -277,11 +321,8 @@ pc_status pc_price_noalloc(const pc_model *m, const pc_contract *k, uint64_t n_p
   if (n_paths > PC_NOALLOC_MAX_PATHS)
     return fail(PC_ELIMIT, "pc_price_noalloc prices at most PC_NOALLOC_MAX_PATHS (2^24) paths per call");
   const ModelHost &H = m->H;
-  for (const XInsn &I : k->prog.code) {
-    const uint32_t op = I.opa & 0xffu;
-    if ((op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK) && int32_t(I.opa >> 8) >= H.d)
-      return fail(PC_ERANGE, "program observes a label the model does not have");
-  }
+  if (max_label(k->prog) >= H.d)
+    return fail(PC_ERANGE, "program observes a label the model does not have");
   NoAllocAnalysis an;
   an.C = k->prog.code.data();
   an.t_now = H.t_now;
@@ -294,9 +335,9 @@ pc_status pc_price_noalloc(const pc_model *m, const pc_contract *k, uint64_t n_p
   if (win > PC_MAX_WINDOW) return fail(PC_ERANGE, "program looks back further than PC_MAX_WINDOW dates");
   pc_ctx *c = m->ctx;
   const Layout lay = make_layout(k->prog, H, win);
-  const size_t smem = k->prog.code.size() * sizeof(XInsn) + size_t(lay.words) * kBlock * 4;
-  if (smem + kStaticSmemReserve > size_t(c->max_smem))
-    return fail(PC_ELIMIT, "program + per-path state exceed the device's shared memory per block");
+  size_t smem = 0;
+  const int block = pick_block(k->prog, lay.words, c->max_smem, H.d, smem);
+  if (!block) return fail(PC_ELIMIT, "program + per-path state exceed the device's shared memory per block");
   CU(cudaSetDevice(c->device), "cudaSetDevice");
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -304,11 +345,12 @@ pc_status pc_price_noalloc(const pc_model *m, const pc_contract *k, uint64_t n_p
   const uint64_t n_tiles = (n_paths + kTilePaths - 1) / kTilePaths;
   if (kNoAllocCounterBytes + n_tiles * 2 * sizeof(double) > scratch_bytes)
     return fail(PC_ELIMIT, "request exceeds the fixed scratch array");
-  const int bpsm = price_blocks_per_sm(H.d, smem, false);
+  const int bpsm = price_blocks_per_sm(H.d, block, smem, false);
   if (bpsm < 1) return fail(PC_ELIMIT, "kernel cannot be resident with this shared-memory footprint");
   PriceArgs a{};
   a.prog = k->d_code;
   a.n_insn = int32_t(k->prog.code.size());
+  a.n_pool = int32_t(pool_padded(k->prog));
   a.m = m->dev;
   a.lay = lay;
   a.n_paths = n_paths;
@@ -318,15 +360,16 @@ pc_status pc_price_noalloc(const pc_model *m, const pc_contract *k, uint64_t n_p
   a.stream = stream;
   a.n_tiles = n_tiles;
   a.width = 2;
-  a.counters = static_cast<unsigned long long *>(scratch);
+  reduction_chunks(n_tiles, a.chunk_tiles, a.n_chunks);
+  a.control = static_cast<unsigned char *>(scratch);
   a.tile_partials = reinterpret_cast<double *>(static_cast<char *>(scratch) + kNoAllocCounterBytes);
   a.out = d_out;
   a.out_paths = nullptr;
   a.status = reinterpret_cast<int32_t *>(c->d_res + 4);
-  const uint64_t need = (n_tiles + kBlock / 32 - 1) / (kBlock / 32);
+  const uint64_t need = (n_tiles + block / 32 - 1) / (block / 32);
   const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * bpsm, need));
-  CU(cudaMemsetAsync(a.counters, 0, 2 * sizeof(unsigned long long), c->stream), "counter reset");
-  CU(launch_price(a, grid, smem, c->stream), "price kernel");
+  CU(cudaMemsetAsync(a.control, 0, kNoAllocCounterBytes, c->stream), "counter reset");
+  CU(launch_price(a, grid, block, smem, c->stream), "price kernel");
   return PC_OK;
 }
 
@@ -359,11 +402,11 @@ pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->d_res, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_res, 0, 8 * sizeof(double), c->stream);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_control, kControlBytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_control, 0, kControlBytes, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
-    if (c->d_counters) cudaFree(c->d_counters);
+    if (c->d_control) cudaFree(c->d_control);
     if (c->d_res) cudaFree(c->d_res);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -379,7 +422,7 @@ pc_status pc_destroy(pc_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   if (c->d_partials) cudaFree(c->d_partials);
-  if (c->d_counters) cudaFree(c->d_counters);
+  if (c->d_control) cudaFree(c->d_control);
   if (c->d_res) cudaFree(c->d_res);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -502,10 +545,17 @@ pc_status pc_load_payoff(pc_ctx *c, const uint32_t *bytecode, size_t n_words, co
       return fail(s, err);
     }
     CU(cudaSetDevice(c->device), "cudaSetDevice");
-    const size_t bytes = k->prog.code.size() * sizeof(XInsn);
-    cudaError_t e = cudaMalloc(&k->d_code, bytes);
+    // program then constant pool (padded to whole 16-byte words), one buffer
+    const size_t code_bytes = k->prog.code.size() * sizeof(XInsn);
+    const size_t pool_bytes = pool_padded(k->prog) * sizeof(float);
+    std::vector<float> pool(pool_padded(k->prog), 0.f);
+    std::copy(k->prog.pool.begin(), k->prog.pool.end(), pool.begin());
+    cudaError_t e = cudaMalloc(&k->d_code, code_bytes + pool_bytes + 16);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(k->d_code, k->prog.code.data(), bytes, cudaMemcpyHostToDevice, c->stream);
+      e = cudaMemcpyAsync(k->d_code, k->prog.code.data(), code_bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && pool_bytes)
+      e = cudaMemcpyAsync(reinterpret_cast<char *>(k->d_code) + code_bytes, pool.data(), pool_bytes,
+                          cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
       if (k->d_code) cudaFree(k->d_code);
@@ -661,10 +711,10 @@ pc_status pc_debug_paths(const pc_model *m, uint64_t n_paths, uint64_t path_offs
   lay.stack = 0;
   lay.off_bstack = 0;
   lay.off_cache = m->H.bstack * m->H.d;
-  lay.off_win = lay.off_cache + m->H.n_levels * 4;
+  lay.off_win = lay.off_cache;
   lay.words = lay.off_win + m->H.d;
   pc_ctx *c = m->ctx;
-  if (size_t(lay.words) * kBlock * 4 > size_t(c->max_smem)) return fail(PC_ELIMIT, "model too large for the probe");
+  if (size_t(lay.words) * 32 * 8 + 2048 > size_t(c->max_smem)) return fail(PC_ELIMIT, "model too large for the probe");
   CU(cudaSetDevice(c->device), "cudaSetDevice");
   CU(launch_debug_paths(m->dev, lay, n_paths, path_offset, uint32_t(seed), uint32_t(seed >> 32),
                         stream, d_S, c->stream),
@@ -674,8 +724,9 @@ pc_status pc_debug_paths(const pc_model *m, uint64_t n_paths, uint64_t path_offs
 
 pc_status pc_debug_program(const uint32_t *bytecode, size_t n_words, const double *consts,
                            size_t n_consts, const int32_t *template_params, size_t n_params,
-                           int32_t p1, int32_t p2, uint32_t *out, size_t cap, size_t *n_insn) {
-  if (!n_insn) return fail(PC_EINVAL, "null argument");
+                           int32_t p1, int32_t p2, uint32_t *out, size_t cap_words,
+                           size_t *n_insn, size_t *n_pool) {
+  if (!n_insn || !n_pool) return fail(PC_EINVAL, "null argument");
   try {
     Program p;
     std::string err;
@@ -683,8 +734,11 @@ pc_status pc_debug_program(const uint32_t *bytecode, size_t n_words, const doubl
                                   p1, p2, true, p, err);
     if (s != PC_OK) return fail(s, err);
     *n_insn = p.code.size();
-    if (p.code.size() > cap || !out) return fail(PC_ELIMIT, "output buffer too small");
+    *n_pool = p.pool.size();
+    if (4 * p.code.size() + p.pool.size() > cap_words || !out)
+      return fail(PC_ELIMIT, "output buffer too small");
     std::memcpy(out, p.code.data(), p.code.size() * sizeof(XInsn));
+    std::memcpy(out + 4 * p.code.size(), p.pool.data(), p.pool.size() * sizeof(float));
     return PC_OK;
   } catch (const std::bad_alloc &) {
     return fail(PC_ENOMEM, "host allocation");
@@ -708,7 +762,7 @@ pc_status pc_debug_bridge(const pc_model_desc *desc, int32_t *date_ops, uint32_t
     std::memcpy(w + 1, &o.wr, 4);
     std::memcpy(w + 2, &o.sd, 4);
     w[3] = o.j;
-    w[4] = uint32_t(o.level) | (uint32_t(o.flags) << 16);
+    w[4] = uint32_t(o.slot) | (uint32_t(o.flags) << 16);
     w[5] = o.m;
   }
   return PC_OK;

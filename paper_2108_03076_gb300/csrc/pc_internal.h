@@ -56,11 +56,27 @@ enum XOp : uint32_t {
   X_IF,         // c = pc of the else branch; peek cond
   X_ELSE,       // c = pc of SEL
   X_SEL,        // pop else, then, cond -> push cond ? then : else
-  X_LOOP,       // A = frame slot; b = bound n. Push frame (4 slots)
+  X_LOOP,       // A = frame slot; b = bound n; c = pc of the loop's LTEST or LSTEPK
   X_LTEST,      // A = frame slot; c = pc of LNEXT
   X_LLATCH,     // A = frame slot
   X_LNEXT,      // A = frame slot; b = bound n; c = pc of loop condition; e = pc after LEND
   X_LEND,       // A = frame slot
+  // Fused multi-asset ops (all leaves read at one static time b):
+  // X_LRED: v = leaf_0 (op) leaf_1 (op) ... left to right, op = min / max /
+  //   add; leaf_i = S_{l_i} [* or / pool[c + i]]; optionally compared with
+  //   the immediate e.  A: bits 0-1 op (0 min, 1 max, 2 add), 2-3 scale
+  //   (0 none, 1 mult, 2 div), 4-6 compare (0 none, 1 v<k, 2 v<=k, 3 k<v,
+  //   4 k<=v), 8-9 leaves-1, 10-17 labels (2 bits each).
+  X_LRED,
+  // X_LANY: p = cmp(leaf_0, k) or/and cmp(leaf_1, k) ...  A: bit 0 combine
+  //   (0 or, 1 and), 2-3 scale, 4-6 compare (1..4 as X_LRED), 8-9 leaves-1,
+  //   10-17 labels; c = pool offset of the scales; e = immediate k.
+  X_LANY,
+  // X_LSTEPK: one loopif iteration whose then-branch is the literal
+  //   pool[A >> 8]: pop the condition, latch the literal on newly true lanes,
+  //   then continue as X_LNEXT.  A: bits 0-7 frame slot, 8-23 pool index;
+  //   b = bound n; c = pc of the loop condition; e = pc after X_LEND.
+  X_LSTEPK,
   X_NUM_OPS
 };
 
@@ -82,12 +98,20 @@ enum { LF_K = 0, LF_T0 = 1, LF_DONE = 2, LF_RES = 3, LF_NEWLY = 4, LF_SLOTS = 5 
 struct BridgeOp {
   float wl, wr, sd;
   uint32_t j;       // breadth-first node number (normal block base j*d)
-  uint16_t level;   // bisection level (cache index)
+  uint16_t slot;    // register cache slot of the node's level (valid with BR_FROM_CACHE / BR_STORE)
   uint16_t flags;   // BR_* below
   uint16_t m;       // date ordinal produced (diagnostics)
-  uint16_t pad0;
+  uint16_t lane0;   // (j*d) & 3: first normal's word in its Philox block
+  uint32_t b0;      // (j*d) >> 2: the node's first Philox block
+  uint32_t level;   // bisection level (diagnostics)
 };
-static_assert(sizeof(BridgeOp) == 24, "BridgeOp layout");
+static_assert(sizeof(BridgeOp) == 32, "BridgeOp layout: two 16-byte loads");
+
+// Philox block caches live in registers: up to cache_slots(d) bisection
+// levels (the ones whose caching saves the most Philox evaluations) get a
+// slot.  With d = 4 a node uses exactly one block, so nothing is shared.
+constexpr int kMaxCacheSlots = 5;
+constexpr int cache_slots(int d) { return d == 1 ? 5 : d == 2 ? 4 : d == 3 ? 3 : 0; }
 
 enum : uint16_t {
   BR_ROOT = 1,        // first node (last date): W = sd * z, no endpoint reads
@@ -107,7 +131,7 @@ struct ModelDev {
   // pathwise tangents (greeks): per ordinal o, tau_o as float
   const float *tau;         // [n+1]
   int32_t d, n, n_hist, t_now;
-  int32_t n_levels;         // bisection levels (level caches)
+  int32_t n_levels;         // bisection levels
   int32_t bstack;           // bridge stack depth
 };
 
@@ -122,39 +146,64 @@ struct Layout {
   int32_t win;        // window size (power of two)
 };
 
-constexpr int kBlock = 128;          // threads per block of the pricing kernel
-constexpr int kPathsPerLane = 2;     // paths per lane per tile
+constexpr int kBlock = 128;          // largest block of the pricing kernel (32..128 threads)
+constexpr int kPathsPerLane = 2;     // paths a lane carries at once (float2 values)
 constexpr int kTilePaths = 32 * kPathsPerLane;
 
+// Dynamic shared memory of the pricing kernel: program (16 B per
+// instruction), constant pool (padded to 4 floats), and the per-thread
+// region of float2 slots.
+inline size_t price_smem_bytes(size_t n_insn, size_t n_pool_padded, int words, int block) {
+  return n_insn * 16 + n_pool_padded * 4 + size_t(words) * block * 8;
+}
+
 struct PriceArgs {
-  const XInsn *prog;
+  const XInsn *prog;        // program followed by its constant pool
   int32_t n_insn;
+  int32_t n_pool;           // pool floats, padded to a multiple of 4
   ModelDev m;
   Layout lay;
   uint64_t n_paths, path_offset;
   uint32_t key0, key1, stream;
   uint64_t n_tiles;
   int32_t width;            // doubles per tile partial (2 for prices)
+  uint32_t chunk_tiles;     // tiles per reduction chunk
+  uint32_t n_chunks;        // ceil(n_tiles / chunk_tiles) <= kMaxChunks
   double *tile_partials;    // [n_tiles * width] scratch
-  unsigned long long *counters;  // [2] scratch: next tile, finished blocks (zero between launches)
+  unsigned char *control;   // kControlBytes of scratch, zero between launches (see below)
   double *out;              // [width + 1]: sums over all paths, then n_paths
   float *out_paths;         // nullable: per-path payoffs
   int32_t *status;          // device status word (nonzero = error)
 };
 
+// Reduction scratch "control" block (zero between launches; every launch
+// leaves it zero): 64-bit counters at byte 0 (next tile, finished blocks,
+// finished chunks), 32-bit per-chunk tile counters at kChunkCountOff, and
+// the chunk partials (width doubles each) at kChunkPartOff.
+constexpr int kMaxChunks = 256;
+constexpr size_t kChunkCountOff = 256;
+constexpr size_t kChunkPartOff = 2048;
+constexpr size_t kControlBytes = kChunkPartOff + size_t(kMaxChunks) * 8 * sizeof(double);
+inline void reduction_chunks(uint64_t n_tiles, uint32_t &chunk_tiles, uint32_t &n_chunks) {
+  uint64_t c = (n_tiles + kMaxChunks - 1) / kMaxChunks;
+  if (c < 64) c = 64;
+  chunk_tiles = uint32_t(c);
+  n_chunks = uint32_t((n_tiles + c - 1) / c);
+}
+
 // Kernel launchers (pc_kernels.cu).  All return a cudaError_t.
-cudaError_t launch_price(const PriceArgs &a, int grid, size_t smem_bytes, cudaStream_t s);
+cudaError_t launch_price(const PriceArgs &a, int grid, int block, size_t smem_bytes, cudaStream_t s);
 cudaError_t launch_greeks(const PriceArgs &a, int grid, size_t smem_bytes, cudaStream_t s);
 cudaError_t launch_debug_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                                 size_t n, cudaStream_t s);
 cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_paths,
                                uint64_t offset, uint32_t k0, uint32_t k1, uint32_t stream,
                                float *out, cudaStream_t s);
-int price_blocks_per_sm(int d, size_t smem_bytes, bool greeks);
+int price_blocks_per_sm(int d, int block, size_t smem_bytes, bool greeks);
 // Device address and size of the fixed scratch array used by
 // pc_price_noalloc on the current device (looked up once per device).
 cudaError_t noalloc_scratch(void **ptr, size_t *bytes);
-constexpr size_t kNoAllocCounterBytes = 256;
+constexpr size_t kNoAllocCounterBytes = kControlBytes;
 int max_dynamic_smem();
 
 // ---------------------------------------------------------------------------
@@ -162,6 +211,7 @@ int max_dynamic_smem();
 // ---------------------------------------------------------------------------
 struct Program {
   std::vector<XInsn> code;
+  std::vector<float> pool;  // constants of fused ops (scales, loop literals)
   pc_program_info info{};
   int32_t frame_slots = 0;  // stack slots (values + frames)
 };

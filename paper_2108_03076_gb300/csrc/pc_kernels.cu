@@ -77,50 +77,92 @@ __device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float &z0, 
   z1 = -r * sin_approx(th);
 }
 
-struct Rng {
-  uint32_t plo, phi, stream, k0, k1;
+// Two paths per lane: every value of the stack machine is a float2 (.x for
+// the lane's first path, .y for its second), so each fetched and decoded
+// instruction does the work of two paths and the two independent dependency
+// chains (Philox rounds, Box-Muller, bridge) overlap in the pipeline.
+struct Rng2 {
+  uint32_t plo[2], phi[2];
+  uint32_t stream, k0, k1;
 };
 
-__device__ __forceinline__ void block_normals(uint32_t b, const Rng &g, float *z) {
-  const uint4 x = philox(make_uint4(b, g.plo, g.phi, g.stream), g.k0, g.k1);
-  box_muller(x.x, x.y, z[0], z[1]);
-  box_muller(x.z, x.w, z[2], z[3]);
+__device__ __forceinline__ void block_normals2(uint32_t b, const Rng2 &g, float2 *e) {
+  const uint4 x0 = philox(make_uint4(b, g.plo[0], g.phi[0], g.stream), g.k0, g.k1);
+  const uint4 x1 = philox(make_uint4(b, g.plo[1], g.phi[1], g.stream), g.k0, g.k1);
+  box_muller(x0.x, x0.y, e[0].x, e[1].x);
+  box_muller(x0.z, x0.w, e[2].x, e[3].x);
+  box_muller(x1.x, x1.y, e[0].y, e[1].y);
+  box_muller(x1.z, x1.w, e[2].y, e[3].y);
 }
 
-#define SLOT(s) R[(s) * kBlock]
+// Slot s of this thread in the word-interleaved per-thread region (the
+// stride is the block size, 32..kBlock threads).
+#define SL(s) R[(s) * blockDim.x]
 
 template <int D>
 struct PathState {
-  float w[D];   // W at the last produced date
-  int f;        // last produced ordinal (frontier)
-  int bsp;      // bridge stack size
+  static constexpr int kSlots = cache_slots(D) > 0 ? cache_slots(D) : 1;
+  float2 w[D];                  // W at the last produced date
+  float2 cache[kSlots][4];      // last Philox block (4 normals) of each cached level
+  int f;                        // last produced ordinal (frontier), warp-uniform
+  int bsp;                      // bridge stack size, warp-uniform
 };
 
-// Normals j*D .. j*D+D-1 of bridge node j (see BridgeOp).
-template <int D>
-__device__ __forceinline__ void node_normals(const BridgeOp &op, const Rng &g, float *R,
-                                             const Layout &lay, float (&z)[D]) {
-  const uint32_t m0 = op.j * D;
-  const uint32_t b0 = m0 >> 2;
-  const int lane0 = int(m0 & 3u);
-  float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int cbase = lay.off_cache + int(op.level) * 4;
-  if (op.flags & BR_FROM_CACHE) {
+// Register cache access with compile-time indices (slot is warp-uniform).
+template <int D, int S>
+__device__ __forceinline__ void cache_copy_in(const PathState<D> &ps, float2 *e) {
+  if constexpr (S < PathState<D>::kSlots) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) e[q] = SLOT(cbase + q);
+    for (int q = 0; q < 4; ++q) e[q] = ps.cache[S][q];
+  }
+}
+template <int D, int S>
+__device__ __forceinline__ void cache_copy_out(PathState<D> &ps, const float2 *e) {
+  if constexpr (S < PathState<D>::kSlots) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ps.cache[S][q] = e[q];
+  }
+}
+template <int D>
+__device__ __forceinline__ void cache_load(const PathState<D> &ps, int slot, float2 *e) {
+  switch (slot) {
+    case 0: cache_copy_in<D, 0>(ps, e); break;
+    case 1: cache_copy_in<D, 1>(ps, e); break;
+    case 2: cache_copy_in<D, 2>(ps, e); break;
+    case 3: cache_copy_in<D, 3>(ps, e); break;
+    default: cache_copy_in<D, 4>(ps, e); break;
+  }
+}
+template <int D>
+__device__ __forceinline__ void cache_store(PathState<D> &ps, int slot, const float2 *e) {
+  switch (slot) {
+    case 0: cache_copy_out<D, 0>(ps, e); break;
+    case 1: cache_copy_out<D, 1>(ps, e); break;
+    case 2: cache_copy_out<D, 2>(ps, e); break;
+    case 3: cache_copy_out<D, 3>(ps, e); break;
+    default: cache_copy_out<D, 4>(ps, e); break;
+  }
+}
+
+// Normals j*D .. j*D+D-1 of bridge node j for both paths (see BridgeOp).
+template <int D>
+__device__ __forceinline__ void node_normals(const BridgeOp &op, const Rng2 &g, PathState<D> &ps,
+                                             float2 (&z)[D]) {
+  const uint32_t b0 = op.b0;
+  const int lane0 = int(op.lane0);
+  float2 e[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) e[q] = make_float2(0.f, 0.f);
+  if (op.flags & BR_FROM_CACHE) {
+    cache_load(ps, op.slot, e);
   } else {
-    block_normals(b0, g, e);
+    block_normals2(b0, g, e);
   }
   const bool two = D > 1 && (op.flags & BR_TWO_BLOCKS);
-  if (two) block_normals(b0 + 1, g, e + 4);
+  if (two) block_normals2(b0 + 1, g, e + 4);
   if (op.flags & BR_STORE) {
-    if (two) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) SLOT(cbase + q) = e[4 + q];
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) SLOT(cbase + q) = e[q];
-    }
+    if (two) cache_store(ps, op.slot, e + 4);  // constant offsets keep e[] in registers
+    else cache_store(ps, op.slot, e);
   }
   switch (lane0) {
     case 0:
@@ -143,49 +185,58 @@ __device__ __forceinline__ void node_normals(const BridgeOp &op, const Rng &g, f
 }
 
 __device__ __forceinline__ BridgeOp load_op(const BridgeOp *p) {
-  const uint2 *q = reinterpret_cast<const uint2 *>(p);
-  uint2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+  const uint4 *q = reinterpret_cast<const uint4 *>(p);
+  const uint4 a = __ldg(q), b = __ldg(q + 1);
   BridgeOp op;
   op.wl = __uint_as_float(a.x);
   op.wr = __uint_as_float(a.y);
-  op.sd = __uint_as_float(b.x);
-  op.j = b.y;
-  op.level = uint16_t(c.x & 0xffffu);
-  op.flags = uint16_t(c.x >> 16);
-  op.m = uint16_t(c.y & 0xffffu);
-  op.pad0 = 0;
+  op.sd = __uint_as_float(a.z);
+  op.j = a.w;
+  op.slot = uint16_t(b.x & 0xffffu);
+  op.flags = uint16_t(b.x >> 16);
+  op.m = uint16_t(b.y & 0xffffu);
+  op.lane0 = uint16_t(b.y >> 16);
+  op.b0 = b.z;
+  op.level = b.w;
   return op;
 }
 
-// Produce date t (= frontier + 1): bridge ops of t, then GBM into the
-// window slot of t.
+__device__ __forceinline__ float2 ffma2(float a, float2 x, float2 y) {
+  return make_float2(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y));
+}
+
+// Produce date t (= frontier + 1) for both paths: bridge ops of t, then GBM
+// into the window slot of t.
 template <int D>
 __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev &m,
-                                         const Layout &lay, const Rng &g, float *R,
+                                         const Layout &lay, const Rng2 &g, float2 *R,
                                          const float (&Bm)[D * D], const float (&S0)[D]) {
   const int k0 = __ldg(m.date_ops + t), k1 = __ldg(m.date_ops + t + 1);
   if (k0 == k1) {
     --ps.bsp;
 #pragma unroll
-    for (int i = 0; i < D; ++i) ps.w[i] = SLOT(lay.off_bstack + ps.bsp * D + i);
+    for (int i = 0; i < D; ++i) ps.w[i] = SL(lay.off_bstack + ps.bsp * D + i);
   } else {
     for (int k = k0; k < k1; ++k) {
       const BridgeOp op = load_op(m.ops + k);
-      float z[D];
-      node_normals<D>(op, g, R, lay, z);
-      float nw[D];
+      float2 z[D];
+      node_normals<D>(op, g, ps, z);
+      float2 nw[D];
       if (op.flags & BR_ROOT) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) nw[i] = op.sd * z[i];
+        for (int i = 0; i < D; ++i) nw[i] = make_float2(op.sd * z[i].x, op.sd * z[i].y);
       } else {
         const int top = lay.off_bstack + (ps.bsp - 1) * D;
 #pragma unroll
-        for (int i = 0; i < D; ++i)
-          nw[i] = fmaf(op.wl, ps.w[i], fmaf(op.wr, SLOT(top + i), op.sd * z[i]));
+        for (int i = 0; i < D; ++i) {
+          const float2 wt = SL(top + i);
+          nw[i] = ffma2(op.wl, ps.w[i],
+                        ffma2(op.wr, wt, make_float2(op.sd * z[i].x, op.sd * z[i].y)));
+        }
       }
       if (k + 1 < k1) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) SLOT(lay.off_bstack + ps.bsp * D + i) = nw[i];
+        for (int i = 0; i < D; ++i) SL(lay.off_bstack + ps.bsp * D + i) = nw[i];
         ++ps.bsp;
       } else {
 #pragma unroll
@@ -196,10 +247,11 @@ __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev
   const int ws = lay.off_win + (t & (lay.win - 1)) * D;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    float x = __ldg(m.A + t * D + i);
+    const float a = __ldg(m.A + t * D + i);
+    float2 x = make_float2(a, a);
 #pragma unroll
-    for (int k = 0; k <= i; ++k) x = fmaf(Bm[i * D + k], ps.w[k], x);
-    SLOT(ws + i) = S0[i] * ex2_approx(x);
+    for (int k = 0; k <= i; ++k) x = ffma2(Bm[i * D + k], ps.w[k], x);
+    SL(ws + i) = make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y));
   }
   ps.f = t;
 }
@@ -213,79 +265,130 @@ __device__ __forceinline__ void load_model_regs(const ModelDev &m, float (&Bm)[D
   for (int i = 0; i < D; ++i) S0[i] = __ldg(m.sval + m.n_hist * D + i);
 }
 
-// The payoff expression of one path per lane, all lanes of the warp in step.
+__device__ __forceinline__ int bits(float v) { return __float_as_int(v); }
+__device__ __forceinline__ float fl(int v) { return __int_as_float(v); }
+__device__ __forceinline__ float2 fl2(int a, int b) { return make_float2(fl(a), fl(b)); }
+
+__device__ __forceinline__ float cmp_code(int code, float v, float k) {
+  // 1: v < k, 2: v <= k, 3: k < v, 4: k <= v
+  const bool r = code == 1 ? v < k : code == 2 ? v <= k : code == 3 ? k < v : k <= v;
+  return fl(int(r));
+}
+
+// The payoff expression of two paths per lane, all lanes of the warp in step.
 template <int D>
-__device__ float eval_path(const uint4 *P, float *R, const PriceArgs &a, const Rng &g,
-                           bool live, const float (&Bm)[D * D], const float (&S0)[D]) {
+__device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const PriceArgs &a,
+                            const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],
+                            const float (&S0)[D]) {
   const ModelDev &m = a.m;
   const Layout &lay = a.lay;
   PathState<D> ps;
 #pragma unroll
-  for (int i = 0; i < D; ++i) ps.w[i] = 0.f;
+  for (int i = 0; i < D; ++i) ps.w[i] = make_float2(0.f, 0.f);
   ps.f = 0;
   ps.bsp = 0;
   const int t_now = m.t_now;
   int pc = 0, sp = 0, t0 = 0;
-  float tos = 0.f;
-#define PUSH(v)         \
-  do {                  \
-    SLOT(sp) = tos;     \
-    ++sp;               \
-    tos = (v);          \
+  float2 tos = make_float2(0.f, 0.f);
+  // frontier advance + window / static read of label l at ordinal o
+  auto ensure = [&](int &o) {
+    if (o > m.n || o < -m.n_hist) {  // unreachable after the load-time analysis; stay in bounds
+      atomicOr(a.status, 1);
+      o = o > m.n ? m.n : -m.n_hist;
+    }
+    while (ps.f < o) gen_date<D>(ps.f + 1, ps, m, lay, g, R, Bm, S0);
+  };
+  auto read = [&](int o, int l) -> float2 {
+    l = l < D ? l : 0;
+    if (o > 0) return SL(lay.off_win + (o & (lay.win - 1)) * D + l);
+    const float v = __ldg(m.sval + (o + m.n_hist) * D + l);
+    return make_float2(v, v);
+  };
+#define PUSH(v)        \
+  do {                 \
+    SL(sp) = tos;      \
+    ++sp;              \
+    tos = (v);         \
   } while (0)
-#define BINF(expr)                  \
-  {                                 \
-    const float b_ = tos;           \
-    const float a_ = SLOT(sp - 1);  \
-    --sp;                           \
-    tos = (expr);                   \
-    ++pc;                           \
-    break;                          \
+#define BINF(expr)                                                         \
+  {                                                                        \
+    const float2 B_ = tos, A_ = SL(sp - 1);                                \
+    --sp;                                                                  \
+    { const float a_ = A_.x, b_ = B_.x; tos.x = (expr); }                  \
+    { const float a_ = A_.y, b_ = B_.y; tos.y = (expr); }                  \
+    ++pc;                                                                  \
+    break;                                                                 \
   }
-#define BINI(expr)                                  \
-  {                                                 \
-    const int b_ = __float_as_int(tos);             \
-    const int a_ = __float_as_int(SLOT(sp - 1));    \
-    --sp;                                           \
-    tos = __int_as_float(expr);                     \
-    ++pc;                                           \
-    break;                                          \
+#define BINI(expr)                                                         \
+  {                                                                        \
+    const float2 B_ = tos, A_ = SL(sp - 1);                                \
+    --sp;                                                                  \
+    { const int a_ = bits(A_.x), b_ = bits(B_.x); tos.x = fl(expr); }     \
+    { const int a_ = bits(A_.y), b_ = bits(B_.y); tos.y = fl(expr); }     \
+    ++pc;                                                                  \
+    break;                                                                 \
   }
-#define IMM(expr)                            \
-  {                                          \
-    const float k_ = __uint_as_float(I.y);   \
-    const float x_ = tos;                    \
-    tos = (expr);                            \
-    ++pc;                                    \
-    break;                                   \
+#define IMM(expr)                                                          \
+  {                                                                        \
+    const float k_ = __uint_as_float(I.y);                                 \
+    { const float x_ = tos.x; tos.x = (expr); }                            \
+    { const float x_ = tos.y; tos.y = (expr); }                            \
+    ++pc;                                                                  \
+    break;                                                                 \
   }
   for (;;) {
     const uint4 I = P[pc];
     switch (I.x & 0xffu) {
-      case X_CONST: PUSH(__uint_as_float(I.y)); ++pc; break;
+      case X_CONST: PUSH(make_float2(__uint_as_float(I.y), __uint_as_float(I.y))); ++pc; break;
       case X_MODEL:
       case X_MODEL_MULK:
       case X_MODEL_DIVK: {
         int o = int(I.y) + t0 - t_now;
-        const int l = int(I.x >> 8) & 7;
-        float v;
-        if (o > 0) {
-          if (o > m.n) {  // unreachable after the load-time analysis; keep memory safe
-            atomicOr(a.status, 1);
-            o = m.n;
-          }
-          while (ps.f < o) gen_date<D>(ps.f + 1, ps, m, lay, g, R, Bm, S0);
-          v = SLOT(lay.off_win + (o & (lay.win - 1)) * D + (l < D ? l : 0));
-        } else {
-          if (o < -m.n_hist) {
-            atomicOr(a.status, 1);
-            o = -m.n_hist;
-          }
-          v = __ldg(m.sval + (o + m.n_hist) * D + (l < D ? l : 0));
-        }
+        ensure(o);
+        float2 v = read(o, int(I.x >> 8) & 3);
         const uint32_t op = I.x & 0xffu;
-        if (op == X_MODEL_MULK) v *= __uint_as_float(I.z);
-        else if (op == X_MODEL_DIVK) v = __fdiv_rn(v, __uint_as_float(I.z));
+        const float k = __uint_as_float(I.z);
+        if (op == X_MODEL_MULK) v = make_float2(v.x * k, v.y * k);
+        else if (op == X_MODEL_DIVK) v = make_float2(__fdiv_rn(v.x, k), __fdiv_rn(v.y, k));
+        PUSH(v);
+        ++pc;
+        break;
+      }
+      case X_LRED:
+      case X_LANY: {
+        const uint32_t A = I.x >> 8;
+        int o = int(I.y) + t0 - t_now;
+        ensure(o);
+        const int n = int((A >> 8) & 3u) + 1, kind = int((A >> 2) & 3u), code = int((A >> 4) & 7u);
+        const bool any = (I.x & 0xffu) == X_LANY, conj = (A & 1u) != 0;
+        const int rop = int(A & 3u);
+        const float k = __uint_as_float(I.w);
+        float2 v = make_float2(0.f, 0.f);
+        for (int i = 0; i < n; ++i) {
+          float2 s = read(o, int(A >> (10 + 2 * i)) & 3);
+          if (kind == 1) {
+            const float c = pool[I.z + i];
+            s = make_float2(s.x * c, s.y * c);
+          } else if (kind == 2) {
+            const float c = pool[I.z + i];
+            s = make_float2(__fdiv_rn(s.x, c), __fdiv_rn(s.y, c));
+          }
+          if (any) {
+            const float2 p = make_float2(cmp_code(code, s.x, k), cmp_code(code, s.y, k));
+            if (i == 0) v = p;
+            else if (conj) v = fl2(bits(v.x) & bits(p.x), bits(v.y) & bits(p.y));
+            else v = fl2(bits(v.x) | bits(p.x), bits(v.y) | bits(p.y));
+          } else if (i == 0) {
+            v = s;
+          } else if (rop == 0) {
+            v = make_float2(fminf(v.x, s.x), fminf(v.y, s.y));
+          } else if (rop == 1) {
+            v = make_float2(fmaxf(v.x, s.x), fmaxf(v.y, s.y));
+          } else {
+            v = make_float2(v.x + s.x, v.y + s.y);
+          }
+        }
+        if (!any && code) v = make_float2(cmp_code(code, v.x, k), cmp_code(code, v.y, k));
         PUSH(v);
         ++pc;
         break;
@@ -298,23 +401,23 @@ __device__ float eval_path(const uint4 *P, float *R, const PriceArgs &a, const R
         }
         float v = __ldg(m.disc + o + m.n_hist);
         if (I.x >> 8) v = -v;
-        PUSH(v);
+        PUSH(make_float2(v, v));
         ++pc;
         break;
       }
-      case X_TIME: PUSH(__int_as_float(int(I.y) + t0)); ++pc; break;
-      case X_NOW: PUSH(__int_as_float(t_now)); ++pc; break;
-      case X_NEGF: tos = -tos; ++pc; break;
-      case X_NOT: tos = __int_as_float(__float_as_int(tos) ^ 1); ++pc; break;
+      case X_TIME: PUSH(fl2(int(I.y) + t0, int(I.y) + t0)); ++pc; break;
+      case X_NOW: PUSH(fl2(t_now, t_now)); ++pc; break;
+      case X_NEGF: tos = make_float2(-tos.x, -tos.y); ++pc; break;
+      case X_NOT: tos = fl2(bits(tos.x) ^ 1, bits(tos.y) ^ 1); ++pc; break;
       case X_ADDF: BINF(a_ + b_)
       case X_SUBF: BINF(a_ - b_)
       case X_MULF: BINF(a_ * b_)
       case X_DIVF: BINF(__fdiv_rn(a_, b_))
       case X_MAXF: BINF(fmaxf(a_, b_))
       case X_MINF: BINF(fminf(a_, b_))
-      case X_LTF: BINF(__int_as_float(int(a_ < b_)))
-      case X_LEF: BINF(__int_as_float(int(a_ <= b_)))
-      case X_EQF: BINF(__int_as_float(int(a_ == b_)))
+      case X_LTF: BINF(fl(int(a_ < b_)))
+      case X_LEF: BINF(fl(int(a_ <= b_)))
+      case X_EQF: BINF(fl(int(a_ == b_)))
       case X_ADDI: BINI(a_ + b_)
       case X_SUBI: BINI(a_ > b_ ? a_ - b_ : 0)
       case X_MULI: BINI(a_ * b_)
@@ -331,87 +434,106 @@ __device__ float eval_path(const uint4 *P, float *R, const PriceArgs &a, const R
       case X_DIVFK: IMM(__fdiv_rn(x_, k_))
       case X_MAXFK: IMM(fmaxf(x_, k_))
       case X_MINFK: IMM(fminf(x_, k_))
-      case X_LTFK: IMM(__int_as_float(int(x_ < k_)))
-      case X_LEFK: IMM(__int_as_float(int(x_ <= k_)))
-      case X_EQFK: IMM(__int_as_float(int(x_ == k_)))
+      case X_LTFK: IMM(fl(int(x_ < k_)))
+      case X_LEFK: IMM(fl(int(x_ <= k_)))
+      case X_EQFK: IMM(fl(int(x_ == k_)))
       case X_RSUBFK: IMM(k_ - x_)
       case X_RDIVFK: IMM(__fdiv_rn(k_, x_))
-      case X_RLTFK: IMM(__int_as_float(int(k_ < x_)))
-      case X_RLEFK: IMM(__int_as_float(int(k_ <= x_)))
+      case X_RLTFK: IMM(fl(int(k_ < x_)))
+      case X_RLEFK: IMM(fl(int(k_ <= x_)))
       case X_IF: {
-        const bool c = __float_as_int(tos) != 0;
-        if (__any_sync(kFull, live && c)) {
+        const bool c0 = bits(tos.x) != 0, c1 = bits(tos.y) != 0;
+        if (__any_sync(kFull, (live0 && c0) || (live1 && c1))) {
           ++pc;
         } else {
-          PUSH(0.f);
+          PUSH(make_float2(0.f, 0.f));
           pc = int(I.z);
         }
         break;
       }
       case X_ELSE: {
-        const bool c = __float_as_int(SLOT(sp - 1)) != 0;
-        if (__any_sync(kFull, live && !c)) {
+        const float2 c = SL(sp - 1);
+        const bool c0 = bits(c.x) != 0, c1 = bits(c.y) != 0;
+        if (__any_sync(kFull, (live0 && !c0) || (live1 && !c1))) {
           ++pc;
         } else {
-          PUSH(0.f);
+          PUSH(make_float2(0.f, 0.f));
           pc = int(I.z);
         }
         break;
       }
       case X_SEL: {
-        const float th = SLOT(sp - 1);
-        const int c = __float_as_int(SLOT(sp - 2));
+        const float2 th = SL(sp - 1), c = SL(sp - 2);
         sp -= 2;
-        tos = c ? th : tos;
+        tos = make_float2(bits(c.x) ? th.x : tos.x, bits(c.y) ? th.y : tos.y);
         ++pc;
         break;
       }
       case X_LOOP: {
         const int F = int(I.x >> 8);
-        SLOT(F + LF_K) = __int_as_float(0);
-        SLOT(F + LF_T0) = __int_as_float(t0);
-        SLOT(F + LF_DONE) = __int_as_float(live ? 0 : 1);
-        SLOT(F + LF_RES) = 0.f;
+        SL(F + LF_K) = fl2(0, 0);
+        SL(F + LF_T0) = fl2(t0, t0);
+        SL(F + LF_DONE) = fl2(live0 ? 0 : 1, live1 ? 0 : 1);
+        SL(F + LF_RES) = make_float2(0.f, 0.f);
         ++pc;
         break;
       }
       case X_LTEST: {
         const int F = int(I.x >> 8);
-        const int c = __float_as_int(tos);
+        const float2 c = tos;
         --sp;
-        tos = SLOT(sp);
-        const int nw = (c != 0) && (__float_as_int(SLOT(F + LF_DONE)) == 0);
-        SLOT(F + LF_NEWLY) = __int_as_float(nw);
-        pc = __any_sync(kFull, nw) ? pc + 1 : int(I.z);
+        tos = SL(sp);
+        const float2 d = SL(F + LF_DONE);
+        const int n0 = bits(c.x) != 0 && bits(d.x) == 0, n1 = bits(c.y) != 0 && bits(d.y) == 0;
+        SL(F + LF_NEWLY) = fl2(n0, n1);
+        pc = __any_sync(kFull, n0 | n1) ? pc + 1 : int(I.z);
         break;
       }
       case X_LLATCH: {
         const int F = int(I.x >> 8);
-        const float v = tos;
+        const float2 v = tos;
         --sp;
-        tos = SLOT(sp);
-        if (__float_as_int(SLOT(F + LF_NEWLY))) {
-          SLOT(F + LF_RES) = v;
-          SLOT(F + LF_DONE) = __int_as_float(1);
+        tos = SL(sp);
+        const float2 nw = SL(F + LF_NEWLY);
+        if (bits(nw.x) | bits(nw.y)) {
+          const float2 r = SL(F + LF_RES), d = SL(F + LF_DONE);
+          SL(F + LF_RES) = make_float2(bits(nw.x) ? v.x : r.x, bits(nw.y) ? v.y : r.y);
+          SL(F + LF_DONE) = fl2(bits(d.x) | bits(nw.x), bits(d.y) | bits(nw.y));
         }
         ++pc;
         break;
       }
+      case X_LSTEPK:
       case X_LNEXT: {
-        const int F = int(I.x >> 8);
-        const int t0e = __float_as_int(SLOT(F + LF_T0));
-        if (__all_sync(kFull, __float_as_int(SLOT(F + LF_DONE)) != 0)) {
+        const bool step = (I.x & 0xffu) == X_LSTEPK;
+        const int F = step ? int((I.x >> 8) & 0xffu) : int(I.x >> 8);
+        float2 d = SL(F + LF_DONE);
+        if (step) {  // latch the literal on lanes whose test newly holds
+          const float2 c = tos;
+          --sp;
+          tos = SL(sp);
+          const int n0 = bits(c.x) != 0 && bits(d.x) == 0, n1 = bits(c.y) != 0 && bits(d.y) == 0;
+          if (n0 | n1) {
+            const float lit = pool[I.x >> 16];
+            const float2 r = SL(F + LF_RES);
+            SL(F + LF_RES) = make_float2(n0 ? lit : r.x, n1 ? lit : r.y);
+            d = fl2(bits(d.x) | n0, bits(d.y) | n1);
+            SL(F + LF_DONE) = d;
+          }
+        }
+        const int t0e = bits(SL(F + LF_T0).x);
+        if (__all_sync(kFull, (bits(d.x) & bits(d.y)) != 0)) {
           t0 = t0e;
-          PUSH(SLOT(F + LF_RES));
+          PUSH(SL(F + LF_RES));
           pc = int(I.w);
         } else {
-          int k = __float_as_int(SLOT(F + LF_K));
+          int k = bits(SL(F + LF_K).x);
           if (k == int(I.y)) {
             t0 = t0e + k;
             ++pc;
           } else {
             ++k;
-            SLOT(F + LF_K) = __int_as_float(k);
+            SL(F + LF_K) = fl2(k, k);
             t0 = t0e + k;
             pc = int(I.z);
           }
@@ -420,8 +542,9 @@ __device__ float eval_path(const uint4 *P, float *R, const PriceArgs &a, const R
       }
       case X_LEND: {
         const int F = int(I.x >> 8);
-        if (__float_as_int(SLOT(F + LF_DONE))) tos = SLOT(F + LF_RES);
-        t0 = __float_as_int(SLOT(F + LF_T0));
+        const float2 d = SL(F + LF_DONE), r = SL(F + LF_RES);
+        tos = make_float2(bits(d.x) ? r.x : tos.x, bits(d.y) ? r.y : tos.y);
+        t0 = bits(SL(F + LF_T0).x);
         ++pc;
         break;
       }
@@ -441,86 +564,133 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Fixed-order sum of the tile partials by the last block to finish: thread t
-// adds tiles t, t + kBlock, ... in order, then a fixed tree over the block.
-__device__ void final_reduce(const PriceArgs &a, double *red) {
-  for (int v = 0; v < a.width; ++v) {
-    double s = 0.0;
-    for (uint64_t t = threadIdx.x; t < a.n_tiles; t += kBlock)
-      s += a.tile_partials[t * a.width + v];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = kBlock / 2; h > 0; h >>= 1) {
-      if (int(threadIdx.x) < h) red[threadIdx.x] += red[threadIdx.x + h];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) a.out[v] = red[0];
-    __syncthreads();
+// Deterministic reduction.  Tile t's partial (sum, sum of squares) is an FP64
+// warp sum in a fixed shuffle order.  Tiles form chunks of chunk_tiles
+// consecutive tiles; the warp that finishes a chunk's last tile sums the
+// chunk's partials in index order (lane l takes tiles l, l+32, ...; then a
+// fixed shuffle tree), and the warp that finishes the last chunk sums the
+// chunk partials the same way.  So the result depends only on n_paths, not
+// on which warp ran which tile.  Counters are consumed and re-zeroed by the
+// warps that read them; the tile counter by the last block to exit.
+template <int W>
+__device__ __forceinline__ void warp_sum_strided(const double *src, uint32_t n, int lane,
+                                                 double (&acc)[W]) {
+#pragma unroll
+  for (int v = 0; v < W; ++v) acc[v] = 0.0;
+  for (uint32_t i = lane; i < n; i += 32) {
+#pragma unroll
+    for (int v = 0; v < W; ++v) acc[v] += __ldcg(src + size_t(i) * W + v);
   }
-  if (threadIdx.x == 0) a.out[a.width] = double(a.n_paths);
+#pragma unroll
+  for (int v = 0; v < W; ++v) acc[v] = warp_sum(acc[v]);
 }
 
-// Tiles of kTilePaths consecutive paths are handed to warps through an
-// atomic counter; each tile's (sum, sum of squares) is reduced in FP64 over
-// the warp in a fixed shuffle order and stored at the tile's index, so the
-// result does not depend on which warp ran which tile.  The last block to
-// finish sums the tiles in index order and resets the counters.
+template <int W>
+__device__ __noinline__ void finish_tile(const PriceArgs &a, uint64_t tile, const double (&tp)[W],
+                                         int lane) {
+  unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
+  uint32_t *chunk_cnt = reinterpret_cast<uint32_t *>(a.control + kChunkCountOff);
+  double *chunk_part = reinterpret_cast<double *>(a.control + kChunkPartOff);
+  const uint32_t chunk = uint32_t(tile / a.chunk_tiles);
+  const uint64_t first = uint64_t(chunk) * a.chunk_tiles;
+  const uint64_t rest = a.n_tiles - first;
+  const uint32_t size = rest < a.chunk_tiles ? uint32_t(rest) : a.chunk_tiles;
+  uint32_t seen = 0;
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < W; ++v) a.tile_partials[tile * W + v] = tp[v];
+    __threadfence();
+    seen = atomicAdd(chunk_cnt + chunk, 1u);
+  }
+  seen = __shfl_sync(kFull, seen, 0);
+  if (seen != size - 1) return;
+  // this warp completed the chunk
+  __threadfence();
+  double acc[W];
+  warp_sum_strided<W>(a.tile_partials + first * W, size, lane, acc);
+  unsigned long long done = 0;
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < W; ++v) chunk_part[size_t(chunk) * W + v] = acc[v];
+    chunk_cnt[chunk] = 0;
+    __threadfence();
+    done = atomicAdd(ctr + 2, 1ull);
+  }
+  done = __shfl_sync(kFull, done, 0);
+  if (done != a.n_chunks - 1) return;
+  // this warp completed the last chunk
+  __threadfence();
+  warp_sum_strided<W>(chunk_part, a.n_chunks, lane, acc);
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < W; ++v) a.out[v] = acc[v];
+    a.out[W] = double(a.n_paths);
+    ctr[2] = 0;
+  }
+}
+
+// Tiles of kTilePaths consecutive paths (two per lane: tile*64 + lane and
+// tile*64 + 32 + lane) are handed to warps through an atomic counter.
 template <int D, bool WRITE>
 __global__ void __launch_bounds__(kBlock) price_kernel(const PriceArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ double red[kBlock];
   __shared__ int last_block;
   uint4 *P = reinterpret_cast<uint4 *>(smem);
-  const uint4 *src = reinterpret_cast<const uint4 *>(a.prog);
-  for (int i = threadIdx.x; i < a.n_insn; i += kBlock) P[i] = src[i];
+  const int prog_words = a.n_insn * 4 + a.n_pool;
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(a.prog);
+  for (int i = threadIdx.x; i < prog_words; i += blockDim.x) smem[i] = src[i];
   __syncthreads();
-  float *R = reinterpret_cast<float *>(smem + a.n_insn * 4) + threadIdx.x;
+  const float *pool = reinterpret_cast<const float *>(smem + a.n_insn * 4);
+  float2 *R = reinterpret_cast<float2 *>(smem + prog_words) + threadIdx.x;
   float Bm[D * D], S0[D];
   load_model_regs<D>(a.m, Bm, S0);
   const int lane = threadIdx.x & 31;
-  Rng g;
+  unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
+  Rng2 g;
   g.stream = a.stream;
   g.k0 = a.key0;
   g.k1 = a.key1;
   for (;;) {
     unsigned long long tile = 0;
-    if (lane == 0) tile = atomicAdd(a.counters, 1ull);
+    if (lane == 0) tile = atomicAdd(ctr, 1ull);
     tile = __shfl_sync(kFull, tile, 0);
     if (tile >= a.n_tiles) break;
-    double s = 0.0, s2 = 0.0;
-#pragma unroll 1
-    for (int q = 0; q < kPathsPerLane; ++q) {
-      const uint64_t idx = tile * kTilePaths + uint64_t(q) * 32 + lane;
-      const bool live = idx < a.n_paths;
-      const uint64_t p = a.path_offset + idx;
-      g.plo = uint32_t(p);
-      g.phi = uint32_t(p >> 32);
-      const float x = eval_path<D>(P, R, a, g, live, Bm, S0);
-      if (live) {
-        const double xd = double(x);
-        s += xd;
-        s2 = fma(xd, xd, s2);
-        if (WRITE) a.out_paths[idx] = x;
-      }
+    const uint64_t i0 = tile * kTilePaths + lane, i1 = i0 + 32;
+    const bool live0 = i0 < a.n_paths, live1 = i1 < a.n_paths;
+    const uint64_t p0 = a.path_offset + i0, p1 = a.path_offset + i1;
+    g.plo[0] = uint32_t(p0);
+    g.phi[0] = uint32_t(p0 >> 32);
+    g.plo[1] = uint32_t(p1);
+    g.phi[1] = uint32_t(p1 >> 32);
+    const float2 x = eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0);
+    double tp[2] = {0.0, 0.0};
+    if (live0) {
+      const double xd = double(x.x);
+      tp[0] += xd;
+      tp[1] = fma(xd, xd, tp[1]);
+      if (WRITE) a.out_paths[i0] = x.x;
     }
-    s = warp_sum(s);
-    s2 = warp_sum(s2);
-    if (lane == 0) {
-      a.tile_partials[2 * tile] = s;
-      a.tile_partials[2 * tile + 1] = s2;
+    if (live1) {
+      const double xd = double(x.y);
+      tp[0] += xd;
+      tp[1] = fma(xd, xd, tp[1]);
+      if (WRITE) a.out_paths[i1] = x.y;
     }
+    tp[0] = warp_sum(tp[0]);
+    tp[1] = warp_sum(tp[1]);
+    finish_tile<2>(a, tile, tp, lane);
   }
-  __threadfence();
+  // the last block to exit re-zeroes the tile counter: no warp grabs tiles
+  // any more once every block has left its loop
   __syncthreads();
-  if (threadIdx.x == 0) last_block = atomicAdd(a.counters + 1, 1ull) == gridDim.x - 1;
-  __syncthreads();
-  if (last_block) {
+  if (threadIdx.x == 0) {
     __threadfence();
-    final_reduce(a, red);
-    if (threadIdx.x == 0) {
-      a.counters[0] = 0;
-      a.counters[1] = 0;
-    }
+    last_block = atomicAdd(ctr + 1, 1ull) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last_block && threadIdx.x == 0) {
+    ctr[0] = 0;
+    ctr[1] = 0;
   }
 }
 
@@ -532,29 +702,46 @@ __global__ void debug_philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k
   reinterpret_cast<uint4 *>(out)[i] = philox(c, k0, k1);
 }
 
+// Thread t generates paths offset + 2t and offset + 2t + 1 with the pricing
+// kernel's generator and writes every date of both.
 template <int D>
 __global__ void __launch_bounds__(kBlock) debug_paths_kernel(const ModelDev m, const Layout lay,
                                                              uint64_t n_paths, uint64_t offset,
                                                              uint32_t k0, uint32_t k1,
                                                              uint32_t stream, float *out) {
   extern __shared__ __align__(16) uint32_t smem[];
-  float *R = reinterpret_cast<float *>(smem) + threadIdx.x;
-  const uint64_t i = uint64_t(blockIdx.x) * kBlock + threadIdx.x;
-  if (i >= n_paths) return;
+  float2 *R = reinterpret_cast<float2 *>(smem) + threadIdx.x;
+  const uint64_t i0 = 2 * (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x), i1 = i0 + 1;
+  if (i0 >= n_paths) return;
   float Bm[D * D], S0[D];
   load_model_regs<D>(m, Bm, S0);
-  Rng g{uint32_t(offset + i), uint32_t((offset + i) >> 32), stream, k0, k1};
+  Rng2 g;
+  g.plo[0] = uint32_t(offset + i0);
+  g.phi[0] = uint32_t((offset + i0) >> 32);
+  g.plo[1] = uint32_t(offset + i1);
+  g.phi[1] = uint32_t((offset + i1) >> 32);
+  g.stream = stream;
+  g.k0 = k0;
+  g.k1 = k1;
   PathState<D> ps;
 #pragma unroll
-  for (int l = 0; l < D; ++l) ps.w[l] = 0.f;
+  for (int l = 0; l < D; ++l) ps.w[l] = make_float2(0.f, 0.f);
   ps.f = 0;
   ps.bsp = 0;
   const size_t row = size_t(m.n) + 1;
-  for (int l = 0; l < D; ++l) out[(i * D + l) * row] = S0[l];
+  const bool has1 = i1 < n_paths;
+  for (int l = 0; l < D; ++l) {
+    out[(i0 * D + l) * row] = S0[l];
+    if (has1) out[(i1 * D + l) * row] = S0[l];
+  }
   for (int t = 1; t <= m.n; ++t) {
     gen_date<D>(t, ps, m, lay, g, R, Bm, S0);
     const int ws = lay.off_win + (t & (lay.win - 1)) * D;
-    for (int l = 0; l < D; ++l) out[(i * D + l) * row + t] = SLOT(ws + l);
+    for (int l = 0; l < D; ++l) {
+      const float2 v = SL(ws + l);
+      out[(i0 * D + l) * row + t] = v.x;
+      if (has1) out[(i1 * D + l) * row + t] = v.y;
+    }
   }
 }
 
@@ -565,14 +752,14 @@ cudaError_t set_smem(K kern, size_t smem) {
 
 }  // namespace
 
-cudaError_t launch_price(const PriceArgs &a, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_price(const PriceArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
   const bool w = a.out_paths != nullptr;
 #define LAUNCH(DD, WW)                                                             \
   do {                                                                             \
     auto k = price_kernel<DD, WW>;                                                 \
     cudaError_t e = set_smem(k, smem);                                             \
     if (e != cudaSuccess) return e;                                                \
-    k<<<grid, kBlock, smem, s>>>(a);                                               \
+    k<<<grid, block, smem, s>>>(a);                                                \
     return cudaGetLastError();                                                     \
   } while (0)
   switch (a.m.d) {
@@ -585,15 +772,15 @@ cudaError_t launch_price(const PriceArgs &a, int grid, size_t smem, cudaStream_t
 #undef LAUNCH
 }
 
-int price_blocks_per_sm(int d, size_t smem, bool greeks) {
+int price_blocks_per_sm(int d, int block, size_t smem, bool greeks) {
   (void)greeks;
   int nb = 0;
   cudaError_t e = cudaSuccess;
   switch (d) {
-    case 1: set_smem(price_kernel<1, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<1, false>, kBlock, smem); break;
-    case 2: set_smem(price_kernel<2, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<2, false>, kBlock, smem); break;
-    case 3: set_smem(price_kernel<3, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<3, false>, kBlock, smem); break;
-    case 4: set_smem(price_kernel<4, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<4, false>, kBlock, smem); break;
+    case 1: set_smem(price_kernel<1, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<1, false>, block, smem); break;
+    case 2: set_smem(price_kernel<2, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<2, false>, block, smem); break;
+    case 3: set_smem(price_kernel<3, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<3, false>, block, smem); break;
+    case 4: set_smem(price_kernel<4, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<4, false>, block, smem); break;
     default: return 0;
   }
   return e == cudaSuccess ? nb : 0;
@@ -616,15 +803,17 @@ cudaError_t launch_debug_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, u
 cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_paths,
                                uint64_t offset, uint32_t k0, uint32_t k1, uint32_t stream,
                                float *out, cudaStream_t s) {
-  const size_t smem = size_t(lay.words) * kBlock * 4;
-  const unsigned grid = unsigned((n_paths + kBlock - 1) / kBlock);
+  int block = kBlock;
+  while (block > 32 && size_t(lay.words) * block * 8 + 2048 > size_t(max_dynamic_smem())) block /= 2;
+  const size_t smem = size_t(lay.words) * block * 8;
+  const unsigned grid = unsigned((n_paths + 2 * block - 1) / (2 * block));
   if (grid == 0) return cudaSuccess;
 #define DLAUNCH(DD)                                                                 \
   do {                                                                              \
     auto k = debug_paths_kernel<DD>;                                                \
     cudaError_t e = set_smem(k, smem);                                              \
     if (e != cudaSuccess) return e;                                                 \
-    k<<<grid, kBlock, smem, s>>>(m, lay, n_paths, offset, k0, k1, stream, out);     \
+    k<<<grid, block, smem, s>>>(m, lay, n_paths, offset, k0, k1, stream, out);      \
     return cudaGetLastError();                                                      \
   } while (0)
   switch (m.d) {
@@ -637,10 +826,11 @@ cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_
 #undef DLAUNCH
 }
 
-// Scratch of pc_price_noalloc: work counters in the first 256 bytes, then
-// one (sum, sum of squares) pair per tile of kTilePaths paths for up to
-// PC_NOALLOC_MAX_PATHS paths.  Zero-initialised when the module loads;
-// each call clears the counters again before its launch.
+// Scratch of pc_price_noalloc: the reduction control block (counters and
+// chunk partials, kControlBytes) first, then one (sum, sum of squares) pair
+// per tile of kTilePaths paths for up to PC_NOALLOC_MAX_PATHS paths.
+// Zero-initialised when the module loads; each call clears the control
+// block again before its launch.
 constexpr size_t kNoAllocScratchBytes =
     kNoAllocCounterBytes + (PC_NOALLOC_MAX_PATHS / kTilePaths) * 2 * sizeof(double);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];

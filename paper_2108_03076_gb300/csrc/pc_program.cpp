@@ -126,9 +126,157 @@ pc_status typecheck(std::vector<TNode> &T, int root, std::string &err) {
 struct Emitter {
   const std::vector<TNode> &T;
   std::vector<XInsn> code;
+  std::vector<float> pool;
   int depth = 0, max_depth = 0, nest = 0, max_nest = 0, n_loops = 0;
 
   explicit Emitter(const std::vector<TNode> &t) : T(t) {}
+
+  // --- fused multi-asset ops ------------------------------------------------
+  // An S-term is model(l, t), model(l, t) * k, k * model(l, t) or
+  // model(l, t) / k with k a real literal.
+  struct STerm {
+    int label;
+    int64_t time;
+    int kind;  // 0 none, 1 mult, 2 div
+    float k;
+  };
+  bool sterm(int idx, STerm &s) const {
+    const TNode &x = T[idx];
+    if (x.op == PC_OP_MODEL) { s = {x.a, x.time, 0, 1.f}; return true; }
+    if ((x.op == PC_OP_MULT || x.op == PC_OP_DIV) && x.ty == T_REAL) {
+      const TNode &a = T[x.ch[0]], &b = T[x.ch[1]];
+      const int kind = x.op == PC_OP_MULT ? 1 : 2;
+      // a scale of exactly 1 is no scale (x * 1 and x / 1 are exact)
+      if (a.op == PC_OP_MODEL && b.op == PC_OP_REAL) {
+        s = {a.a, a.time, float(b.val) == 1.0f ? 0 : kind, float(b.val)};
+        return true;
+      }
+      if (kind == 1 && b.op == PC_OP_MODEL && a.op == PC_OP_REAL) {
+        s = {b.a, b.time, float(a.val) == 1.0f ? 0 : 1, float(a.val)};
+        return true;
+      }
+    }
+    return false;
+  }
+  // Leaves of the left-nested chain of `op` rooted at idx, in evaluation order.
+  void chain(int idx, uint32_t op, std::vector<int> &leaves) const {
+    std::vector<int> rights;
+    int y = idx;
+    while (T[y].op == op && T[y].ty == T[idx].ty) {
+      rights.push_back(T[y].ch[1]);
+      y = T[y].ch[0];
+    }
+    leaves.assign(1, y);
+    for (auto it = rights.rbegin(); it != rights.rend(); ++it) leaves.push_back(*it);
+  }
+  // S-terms of one time with compatible scales; returns the common kind or -1.
+  int terms_kind(const std::vector<STerm> &ts) const {
+    bool mult = false, div = false;
+    for (const STerm &t : ts) {
+      if (t.time != ts[0].time || t.label < 0 || t.label > 3) return -1;
+      mult |= t.kind == 1;
+      div |= t.kind == 2;
+    }
+    if (mult && div) return -1;
+    return mult ? 1 : div ? 2 : 0;
+  }
+  uint32_t pool_terms(const std::vector<STerm> &ts, int kind) {
+    const uint32_t off = uint32_t(pool.size());
+    if (kind) for (const STerm &t : ts) pool.push_back(t.kind ? t.k : 1.0f);
+    return off;
+  }
+  static uint32_t labels_field(const std::vector<STerm> &ts) {
+    uint32_t f = 0;
+    for (size_t i = 0; i < ts.size(); ++i) f |= uint32_t(ts[i].label) << (10 + 2 * i);
+    return f;
+  }
+  // chain of min/max/add over S-terms (1..4 leaves; 1 leaf only with a compare)
+  bool red_terms(int idx, uint32_t &rop, std::vector<STerm> &ts) const {
+    const TNode &x = T[idx];
+    ts.clear();
+    STerm s;
+    if (sterm(idx, s)) { rop = 0; ts.push_back(s); return true; }
+    if (x.ty != T_REAL || !(x.op == PC_OP_MIN || x.op == PC_OP_MAX || x.op == PC_OP_ADD)) return false;
+    std::vector<int> leaves;
+    chain(idx, x.op, leaves);
+    if (leaves.size() < 2 || leaves.size() > 4) return false;
+    for (int l : leaves) {
+      if (!sterm(l, s)) return false;
+      ts.push_back(s);
+    }
+    rop = x.op == PC_OP_MIN ? 0 : x.op == PC_OP_MAX ? 1 : 2;
+    return true;
+  }
+  // compare of an operand with a real literal: code 1 v<k, 2 v<=k, 3 k<v, 4 k<=v
+  bool lit_cmp(int idx, int &operand, int &code, float &k) const {
+    const TNode &x = T[idx];
+    if (!(x.op == PC_OP_LT || x.op == PC_OP_LE)) return false;
+    const TNode &a = T[x.ch[0]], &b = T[x.ch[1]];
+    if (a.ty != T_REAL) return false;
+    if (b.op == PC_OP_REAL && a.op != PC_OP_REAL) {
+      operand = x.ch[0]; code = x.op == PC_OP_LT ? 1 : 2; k = float(b.val); return true;
+    }
+    if (a.op == PC_OP_REAL && b.op != PC_OP_REAL) {
+      operand = x.ch[1]; code = x.op == PC_OP_LT ? 3 : 4; k = float(a.val); return true;
+    }
+    return false;
+  }
+  static uint32_t fbits_(float f) { uint32_t u; std::memcpy(&u, &f, 4); return u; }
+  bool try_fused(int idx) {
+    const TNode &x = T[idx];
+    uint32_t rop;
+    std::vector<STerm> ts;
+    // label reduce without compare
+    if (x.ty == T_REAL && (x.op == PC_OP_MIN || x.op == PC_OP_MAX || x.op == PC_OP_ADD) &&
+        red_terms(idx, rop, ts) && ts.size() >= 2) {
+      const int kind = terms_kind(ts);
+      if (kind < 0) return false;
+      const uint32_t off = pool_terms(ts, kind);
+      emit(X_LRED, rop | (uint32_t(kind) << 2) | (uint32_t(ts.size() - 1) << 8) | labels_field(ts),
+           uint32_t(int32_t(ts[0].time)), off, 0);
+      push();
+      return true;
+    }
+    // (label reduce or single S-term) compared with a literal
+    int operand, code;
+    float k;
+    if (lit_cmp(idx, operand, code, k) && red_terms(operand, rop, ts)) {
+      const int kind = terms_kind(ts);
+      if (kind < 0) return false;
+      const uint32_t off = pool_terms(ts, kind);
+      emit(X_LRED, rop | (uint32_t(kind) << 2) | (uint32_t(code) << 4) |
+                       (uint32_t(ts.size() - 1) << 8) | labels_field(ts),
+           uint32_t(int32_t(ts[0].time)), off, fbits_(k));
+      push();
+      return true;
+    }
+    // or / and of S-term compares against one literal
+    if (x.ty == T_BOOL && (x.op == PC_OP_OR || x.op == PC_OP_AND)) {
+      std::vector<int> leaves;
+      chain(idx, x.op, leaves);
+      if (leaves.size() < 2 || leaves.size() > 4) return false;
+      int code0 = -1;
+      float k0 = 0.f;
+      for (int l : leaves) {
+        int opd, c;
+        float kk;
+        STerm st;
+        if (!lit_cmp(l, opd, c, kk) || !sterm(opd, st)) return false;
+        if (code0 < 0) { code0 = c; k0 = kk; }
+        if (c != code0 || fbits_(kk) != fbits_(k0)) return false;
+        ts.push_back(st);
+      }
+      const int kind = terms_kind(ts);
+      if (kind < 0) return false;
+      const uint32_t off = pool_terms(ts, kind);
+      emit(X_LANY, (x.op == PC_OP_AND ? 1u : 0u) | (uint32_t(kind) << 2) | (uint32_t(code0) << 4) |
+                       (uint32_t(ts.size() - 1) << 8) | labels_field(ts),
+           uint32_t(int32_t(ts[0].time)), off, fbits_(k0));
+      push();
+      return true;
+    }
+    return false;
+  }
 
   size_t emit(uint32_t op, uint32_t A = 0, uint32_t b = 0, uint32_t c = 0, uint32_t e = 0) {
     code.push_back({op | (A << 8), b, c, e});
@@ -185,24 +333,40 @@ struct Emitter {
         const uint32_t frame = uint32_t(nest);   // frame index; slot resolved later
         max_nest = std::max(max_nest, ++nest);
         const uint32_t n = uint32_t(x.time);
-        emit(X_LOOP, frame, n);
+        const size_t i_loop = emit(X_LOOP, frame, n);
         size_t cond_pc = code.size();
         node(x.ch[0]);
-        size_t i_test = emit(X_LTEST, frame);
-        pop();
-        node(x.ch[1]);
-        emit(X_LLATCH, frame);
-        pop();
-        size_t i_next = emit(X_LNEXT, frame, n, uint32_t(cond_pc));
-        node(x.ch[2]);
-        emit(X_LEND, frame);
-        code[i_test].c = uint32_t(i_next);
-        code[i_next].e = uint32_t(code.size());
+        const TNode &th = T[x.ch[1]];
+        if (th.op == PC_OP_REAL || th.op == PC_OP_BOOL || th.op == PC_OP_NAT) {
+          // literal then-branch: test, latch and step in one instruction
+          const uint32_t pidx = uint32_t(pool.size());
+          pool.push_back(th.op == PC_OP_REAL ? float(th.val) : 0.f);
+          if (th.op != PC_OP_REAL) std::memcpy(&pool.back(), &th.a, 4);
+          const size_t i_step = emit(X_LSTEPK, frame | (pidx << 8), n, uint32_t(cond_pc));
+          pop();
+          code[i_loop].c = uint32_t(i_step);
+          node(x.ch[2]);
+          emit(X_LEND, frame);
+          code[i_step].e = uint32_t(code.size());
+        } else {
+          size_t i_test = emit(X_LTEST, frame);
+          pop();
+          code[i_loop].c = uint32_t(i_test);
+          node(x.ch[1]);
+          emit(X_LLATCH, frame);
+          pop();
+          size_t i_next = emit(X_LNEXT, frame, n, uint32_t(cond_pc));
+          node(x.ch[2]);
+          emit(X_LEND, frame);
+          code[i_test].c = uint32_t(i_next);
+          code[i_next].e = uint32_t(code.size());
+        }
         --nest;
         return;  // else-value popped and result pushed: net +1 as pushed by else
       }
       default: break;
     }
+    if (try_fused(k)) return;
     // binary operators
     const TNode &l = T[x.ch[0]], &r = T[x.ch[1]];
     const bool real = l.ty == T_REAL && x.op != PC_OP_AND && x.op != PC_OP_OR;
@@ -372,8 +536,14 @@ pc_status compile_program(const uint32_t *words, size_t n_words, const double *c
     if (op == X_LOOP || op == X_LTEST || op == X_LLATCH || op == X_LNEXT || op == X_LEND) {
       uint32_t f = I.opa >> 8;
       I.opa = op | (uint32_t(stack_slots + LF_SLOTS * f) << 8);
+    } else if (op == X_LSTEPK) {
+      uint32_t f = (I.opa >> 8) & 0xffu, pidx = I.opa >> 16;
+      I.opa = op | (uint32_t(stack_slots + LF_SLOTS * f) << 8) | (pidx << 16);
     }
   }
+  if (E.pool.size() > 0xffff) { err = "too many fused-op constants"; return PC_ELIMIT; }
+  if (stack_slots + LF_SLOTS * E.max_nest > 255) { err = "loop frames beyond slot 255"; return PC_ELIMIT; }
+  out.pool = std::move(E.pool);
   out.code = std::move(E.code);
   out.frame_slots = stack_slots + LF_SLOTS * E.max_nest;
   out.info.n_nodes = int32_t(T.size());
@@ -405,7 +575,8 @@ pc_status analyse_program(const Program &p, int32_t t_now, int32_t n_dates, int3
       }
       const XInsn &I = C[pc];
       const uint32_t op = I.opa & 0xffu;
-      if (op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_PAYOFF) {
+      if (op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_PAYOFF ||
+          op == X_LRED || op == X_LANY) {
         const int64_t o = int64_t(int32_t(I.b)) + t0 - t_now;
         if (o < -int64_t(n_hist) || o > n_dates) {
           err = "time " + std::to_string(int32_t(I.b) + t0) + " is outside the model's grid (ordinal " +
@@ -420,10 +591,14 @@ pc_status analyse_program(const Program &p, int32_t t_now, int32_t n_dates, int3
         ++pc;
       } else if (op == X_LOOP) {
         const int64_t n = I.b;
-        size_t cond = pc + 1, test = cond;
-        // find this loop's LTEST / LNEXT / LEND by frame slot
-        const uint32_t slot = I.opa >> 8;
-        while (!((C[test].opa & 0xffu) == X_LTEST && (C[test].opa >> 8) == slot)) ++test;
+        const size_t cond = pc + 1, test = I.c;
+        if ((C[test].opa & 0xffu) == X_LSTEPK) {
+          const size_t end = C[test].e;  // pc after LEND
+          for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(cond, test, t0 + k);
+          run(test + 1, end - 1, t0 + n);  // else-branch (before LEND)
+          pc = end;
+          continue;
+        }
         const size_t next = C[test].c;
         const size_t end = C[next].e;  // pc after LEND
         for (int64_t k = 0; k <= n && st == PC_OK; ++k) {

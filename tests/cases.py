@@ -23,7 +23,19 @@ M2_LATER = W.MarketSpec([100.0, 50.0], [0.25, 0.4], W.const_corr(2, 0.3), 0.02,
                         [30 * k for k in range(1, 11)], now=2,
                         history=[[99.0, 50.5], [98.0, 51.0]], hist_days=[-30, -60])
 
+M3 = W.MarketSpec([100.0, 50.0, 25.0], [0.2, 0.3, 0.25], W.const_corr(3, 0.4), 0.01,
+                  [365 * k for k in range(1, 6)])
+M3_MONTHLY = W.MarketSpec([100.0, 100.0, 100.0], [0.2, 0.3, 0.25], W.const_corr(3, 0.6), 0.01,
+                          [30 * k for k in range(1, 13)])
+
 STRESS = {
+    # worst-of on S_i / S0_i with unequal S0 (fused reduce with divide scales)
+    "autocall_scaled": (W.autocall_text([100.0, 50.0, 25.0]), [], M3, 1.0),
+    # and-chain of barrier tests and a weighted basket (fused ops, mult scales)
+    "basket_and": ("(loopif (and (and (le (model 0 0) 80.0) (le (model 1 0) 80.0)) (le (model 2 0) 80.0)) "
+                   "(mult (add (add (mult (model 0 0) 0.5) (mult 0.3 (model 1 0))) (mult (model 2 0) 0.2)) "
+                   "(payoff 0 0 1)) (mult (max (sub (add (add (model 0 0) (model 1 0)) (model 2 0)) 300.0) 0.0) "
+                   "(payoff 0 0 1)) 12)", [], M3_MONTHLY, 100.0),
     # nested loopif: outer window $0 on label 0, inner window $1 on label 1
     "nested_loops": ("(loopif (lt 105.0 (model 0 0)) "
                      "(loopif (lt (model 1 0) 48.0) (mult (sub (model 0 0) (model 1 0)) (payoff 0 0 1)) "
