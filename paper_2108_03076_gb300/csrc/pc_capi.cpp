@@ -283,6 +283,12 @@ struct NoAllocAnalysis {
           else if (frontier - o > lookback) lookback = frontier - o;
         }
         ++pc;
+      } else if (op == X_LOOPANY) {
+        const int64_t n = I.b;
+        const size_t end = I.e;
+        for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(pc + 1, pc + 2, t0 + k);
+        run(pc + 2, end - 1, t0 + n);
+        pc = end;
       } else if (op == X_LOOP) {
         const int64_t n = I.b;
         const size_t test = I.c;

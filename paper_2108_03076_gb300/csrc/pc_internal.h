@@ -40,7 +40,7 @@ enum XOp : uint32_t {
   X_END = 0,
   X_CONST,      // push bits b
   X_MODEL,      // A = label; push S_label(ordinal b + t0 - t_now)
-  X_PAYOFF,     // A = 1 for negative sign; push +-disc(ordinal b + t0 - t_now)
+  X_PAYOFF,     // A = 1 for negative sign; push +-c * disc(ordinal b + t0 - t_now), c float bits
   X_TIME,       // push int b + t0
   X_NOW,        // push int t_now
   X_NEGF, X_NOT,
@@ -77,6 +77,14 @@ enum XOp : uint32_t {
   //   then continue as X_LNEXT.  A: bits 0-7 frame slot, 8-23 pool index;
   //   b = bound n; c = pc of the loop condition; e = pc after X_LEND.
   X_LSTEPK,
+  // X_LOOPANY: a whole loopif whose condition is one X_LRED-with-compare or
+  //   X_LANY instruction (stored right after, as a descriptor that is not
+  //   dispatched) and whose then-branch is the literal pool[A >> 8]: tests
+  //   k = 0..n in a device loop, latching the literal; when every live lane
+  //   latched, pushes the results and jumps to e (after X_LEND); otherwise
+  //   fills the frame (A & 0xff) and runs the else-branch at pc + 2, which
+  //   X_LEND closes.  b = bound n.
+  X_LOOPANY,
   X_NUM_OPS
 };
 

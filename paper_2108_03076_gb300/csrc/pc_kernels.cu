@@ -275,7 +275,58 @@ __device__ __forceinline__ float cmp_code(int code, float v, float k) {
   return fl(int(r));
 }
 
+// Fused multi-asset value (X_LRED) or test (X_LANY) of instruction I at
+// ordinal o for both paths; results of compares are 0/1 int bits.
+template <int D>
+__device__ __forceinline__ float2 fused_value(const uint4 &I, int o, const float *pool,
+                                              const float2 *R, const ModelDev &m,
+                                              const Layout &lay) {
+  const uint32_t A = I.x >> 8;
+  const int n = int((A >> 8) & 3u) + 1, kind = int((A >> 2) & 3u), code = int((A >> 4) & 7u);
+  const bool any = (I.x & 0xffu) == X_LANY, conj = (A & 1u) != 0;
+  const int rop = int(A & 3u);
+  const float k = __uint_as_float(I.w);
+  const int base = lay.off_win + (o & (lay.win - 1)) * D;
+  float2 v = make_float2(0.f, 0.f);
+  for (int i = 0; i < n; ++i) {
+    int l = int(A >> (10 + 2 * i)) & 3;
+    l = l < D ? l : 0;
+    float2 s;
+    if (o > 0) {
+      s = SL(base + l);
+    } else {
+      const float sv = __ldg(m.sval + (o + m.n_hist) * D + l);
+      s = make_float2(sv, sv);
+    }
+    if (kind == 1) {
+      const float c = pool[I.z + i];
+      s = make_float2(s.x * c, s.y * c);
+    } else if (kind == 2) {
+      const float c = pool[I.z + i];
+      s = make_float2(__fdiv_rn(s.x, c), __fdiv_rn(s.y, c));
+    }
+    if (any) {
+      const float2 p = make_float2(cmp_code(code, s.x, k), cmp_code(code, s.y, k));
+      if (i == 0) v = p;
+      else if (conj) v = fl2(bits(v.x) & bits(p.x), bits(v.y) & bits(p.y));
+      else v = fl2(bits(v.x) | bits(p.x), bits(v.y) | bits(p.y));
+    } else if (i == 0) {
+      v = s;
+    } else if (rop == 0) {
+      v = make_float2(fminf(v.x, s.x), fminf(v.y, s.y));
+    } else if (rop == 1) {
+      v = make_float2(fmaxf(v.x, s.x), fmaxf(v.y, s.y));
+    } else {
+      v = make_float2(v.x + s.x, v.y + s.y);
+    }
+  }
+  if (!any && code) v = make_float2(cmp_code(code, v.x, k), cmp_code(code, v.y, k));
+  return v;
+}
+
 // The payoff expression of two paths per lane, all lanes of the warp in step.
+// The next instruction is fetched while the current one executes; jumps
+// fetch their target.
 template <int D>
 __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const PriceArgs &a,
                             const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],
@@ -290,9 +341,10 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
   const int t_now = m.t_now;
   int pc = 0, sp = 0, t0 = 0;
   float2 tos = make_float2(0.f, 0.f);
-  // frontier advance + window / static read of label l at ordinal o
+  // frontier advance to ordinal o (clamped into the grid if the load-time
+  // analysis were ever wrong)
   auto ensure = [&](int &o) {
-    if (o > m.n || o < -m.n_hist) {  // unreachable after the load-time analysis; stay in bounds
+    if (o > m.n || o < -m.n_hist) {
       atomicOr(a.status, 1);
       o = o > m.n ? m.n : -m.n_hist;
     }
@@ -304,6 +356,18 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
     const float v = __ldg(m.sval + (o + m.n_hist) * D + l);
     return make_float2(v, v);
   };
+#define NEXT      \
+  {               \
+    ++pc;         \
+    I = In;       \
+    break;        \
+  }
+#define JUMP(t)   \
+  {               \
+    pc = (t);     \
+    I = P[pc];    \
+    break;        \
+  }
 #define PUSH(v)        \
   do {                 \
     SL(sp) = tos;      \
@@ -316,8 +380,7 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
     --sp;                                                                  \
     { const float a_ = A_.x, b_ = B_.x; tos.x = (expr); }                  \
     { const float a_ = A_.y, b_ = B_.y; tos.y = (expr); }                  \
-    ++pc;                                                                  \
-    break;                                                                 \
+    NEXT                                                                   \
   }
 #define BINI(expr)                                                         \
   {                                                                        \
@@ -325,21 +388,20 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
     --sp;                                                                  \
     { const int a_ = bits(A_.x), b_ = bits(B_.x); tos.x = fl(expr); }     \
     { const int a_ = bits(A_.y), b_ = bits(B_.y); tos.y = fl(expr); }     \
-    ++pc;                                                                  \
-    break;                                                                 \
+    NEXT                                                                   \
   }
 #define IMM(expr)                                                          \
   {                                                                        \
     const float k_ = __uint_as_float(I.y);                                 \
     { const float x_ = tos.x; tos.x = (expr); }                            \
     { const float x_ = tos.y; tos.y = (expr); }                            \
-    ++pc;                                                                  \
-    break;                                                                 \
+    NEXT                                                                   \
   }
+  uint4 I = P[0];
   for (;;) {
-    const uint4 I = P[pc];
+    const uint4 In = P[pc + 1];
     switch (I.x & 0xffu) {
-      case X_CONST: PUSH(make_float2(__uint_as_float(I.y), __uint_as_float(I.y))); ++pc; break;
+      case X_CONST: PUSH(make_float2(__uint_as_float(I.y), __uint_as_float(I.y))); NEXT
       case X_MODEL:
       case X_MODEL_MULK:
       case X_MODEL_DIVK: {
@@ -351,47 +413,14 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
         if (op == X_MODEL_MULK) v = make_float2(v.x * k, v.y * k);
         else if (op == X_MODEL_DIVK) v = make_float2(__fdiv_rn(v.x, k), __fdiv_rn(v.y, k));
         PUSH(v);
-        ++pc;
-        break;
+        NEXT
       }
       case X_LRED:
       case X_LANY: {
-        const uint32_t A = I.x >> 8;
         int o = int(I.y) + t0 - t_now;
         ensure(o);
-        const int n = int((A >> 8) & 3u) + 1, kind = int((A >> 2) & 3u), code = int((A >> 4) & 7u);
-        const bool any = (I.x & 0xffu) == X_LANY, conj = (A & 1u) != 0;
-        const int rop = int(A & 3u);
-        const float k = __uint_as_float(I.w);
-        float2 v = make_float2(0.f, 0.f);
-        for (int i = 0; i < n; ++i) {
-          float2 s = read(o, int(A >> (10 + 2 * i)) & 3);
-          if (kind == 1) {
-            const float c = pool[I.z + i];
-            s = make_float2(s.x * c, s.y * c);
-          } else if (kind == 2) {
-            const float c = pool[I.z + i];
-            s = make_float2(__fdiv_rn(s.x, c), __fdiv_rn(s.y, c));
-          }
-          if (any) {
-            const float2 p = make_float2(cmp_code(code, s.x, k), cmp_code(code, s.y, k));
-            if (i == 0) v = p;
-            else if (conj) v = fl2(bits(v.x) & bits(p.x), bits(v.y) & bits(p.y));
-            else v = fl2(bits(v.x) | bits(p.x), bits(v.y) | bits(p.y));
-          } else if (i == 0) {
-            v = s;
-          } else if (rop == 0) {
-            v = make_float2(fminf(v.x, s.x), fminf(v.y, s.y));
-          } else if (rop == 1) {
-            v = make_float2(fmaxf(v.x, s.x), fmaxf(v.y, s.y));
-          } else {
-            v = make_float2(v.x + s.x, v.y + s.y);
-          }
-        }
-        if (!any && code) v = make_float2(cmp_code(code, v.x, k), cmp_code(code, v.y, k));
-        PUSH(v);
-        ++pc;
-        break;
+        PUSH(fused_value<D>(I, o, pool, R, m, lay));
+        NEXT
       }
       case X_PAYOFF: {
         int o = int(I.y) + t0 - t_now;
@@ -399,16 +428,15 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
           atomicOr(a.status, 1);
           o = 0;
         }
-        float v = __ldg(m.disc + o + m.n_hist);
+        float v = __uint_as_float(I.z) * __ldg(m.disc + o + m.n_hist);
         if (I.x >> 8) v = -v;
         PUSH(make_float2(v, v));
-        ++pc;
-        break;
+        NEXT
       }
-      case X_TIME: PUSH(fl2(int(I.y) + t0, int(I.y) + t0)); ++pc; break;
-      case X_NOW: PUSH(fl2(t_now, t_now)); ++pc; break;
-      case X_NEGF: tos = make_float2(-tos.x, -tos.y); ++pc; break;
-      case X_NOT: tos = fl2(bits(tos.x) ^ 1, bits(tos.y) ^ 1); ++pc; break;
+      case X_TIME: PUSH(fl2(int(I.y) + t0, int(I.y) + t0)); NEXT
+      case X_NOW: PUSH(fl2(t_now, t_now)); NEXT
+      case X_NEGF: tos = make_float2(-tos.x, -tos.y); NEXT
+      case X_NOT: tos = fl2(bits(tos.x) ^ 1, bits(tos.y) ^ 1); NEXT
       case X_ADDF: BINF(a_ + b_)
       case X_SUBF: BINF(a_ - b_)
       case X_MULF: BINF(a_ * b_)
@@ -443,31 +471,22 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
       case X_RLEFK: IMM(fl(int(k_ <= x_)))
       case X_IF: {
         const bool c0 = bits(tos.x) != 0, c1 = bits(tos.y) != 0;
-        if (__any_sync(kFull, (live0 && c0) || (live1 && c1))) {
-          ++pc;
-        } else {
-          PUSH(make_float2(0.f, 0.f));
-          pc = int(I.z);
-        }
-        break;
+        if (__any_sync(kFull, (live0 && c0) || (live1 && c1))) NEXT
+        PUSH(make_float2(0.f, 0.f));
+        JUMP(int(I.z))
       }
       case X_ELSE: {
         const float2 c = SL(sp - 1);
         const bool c0 = bits(c.x) != 0, c1 = bits(c.y) != 0;
-        if (__any_sync(kFull, (live0 && !c0) || (live1 && !c1))) {
-          ++pc;
-        } else {
-          PUSH(make_float2(0.f, 0.f));
-          pc = int(I.z);
-        }
-        break;
+        if (__any_sync(kFull, (live0 && !c0) || (live1 && !c1))) NEXT
+        PUSH(make_float2(0.f, 0.f));
+        JUMP(int(I.z))
       }
       case X_SEL: {
         const float2 th = SL(sp - 1), c = SL(sp - 2);
         sp -= 2;
         tos = make_float2(bits(c.x) ? th.x : tos.x, bits(c.y) ? th.y : tos.y);
-        ++pc;
-        break;
+        NEXT
       }
       case X_LOOP: {
         const int F = int(I.x >> 8);
@@ -475,8 +494,34 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
         SL(F + LF_T0) = fl2(t0, t0);
         SL(F + LF_DONE) = fl2(live0 ? 0 : 1, live1 ? 0 : 1);
         SL(F + LF_RES) = make_float2(0.f, 0.f);
-        ++pc;
-        break;
+        NEXT
+      }
+      case X_LOOPANY: {
+        const int F = int((I.x >> 8) & 0xffu);
+        const float lit = pool[I.x >> 16];
+        const uint4 Dsc = In;  // the condition descriptor
+        bool d0 = !live0, d1 = !live1;
+        float r0 = 0.f, r1 = 0.f;
+        const int n = int(I.y);
+        bool all = false;
+        for (int k = 0;; ++k) {
+          int o = int(Dsc.y) + t0 + k - t_now;
+          ensure(o);
+          const float2 c = fused_value<D>(Dsc, o, pool, R, m, lay);
+          if (bits(c.x) && !d0) { d0 = true; r0 = lit; }
+          if (bits(c.y) && !d1) { d1 = true; r1 = lit; }
+          all = __all_sync(kFull, d0 && d1);
+          if (all || k == n) break;
+        }
+        if (all) {
+          PUSH(make_float2(r0, r1));
+          JUMP(int(I.w))
+        }
+        SL(F + LF_T0) = fl2(t0, t0);
+        SL(F + LF_DONE) = fl2(d0, d1);
+        SL(F + LF_RES) = make_float2(r0, r1);
+        t0 += n;
+        JUMP(pc + 2)
       }
       case X_LTEST: {
         const int F = int(I.x >> 8);
@@ -486,8 +531,8 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
         const float2 d = SL(F + LF_DONE);
         const int n0 = bits(c.x) != 0 && bits(d.x) == 0, n1 = bits(c.y) != 0 && bits(d.y) == 0;
         SL(F + LF_NEWLY) = fl2(n0, n1);
-        pc = __any_sync(kFull, n0 | n1) ? pc + 1 : int(I.z);
-        break;
+        if (__any_sync(kFull, n0 | n1)) NEXT
+        JUMP(int(I.z))
       }
       case X_LLATCH: {
         const int F = int(I.x >> 8);
@@ -500,8 +545,7 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
           SL(F + LF_RES) = make_float2(bits(nw.x) ? v.x : r.x, bits(nw.y) ? v.y : r.y);
           SL(F + LF_DONE) = fl2(bits(d.x) | bits(nw.x), bits(d.y) | bits(nw.y));
         }
-        ++pc;
-        break;
+        NEXT
       }
       case X_LSTEPK:
       case X_LNEXT: {
@@ -525,33 +569,31 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
         if (__all_sync(kFull, (bits(d.x) & bits(d.y)) != 0)) {
           t0 = t0e;
           PUSH(SL(F + LF_RES));
-          pc = int(I.w);
-        } else {
-          int k = bits(SL(F + LF_K).x);
-          if (k == int(I.y)) {
-            t0 = t0e + k;
-            ++pc;
-          } else {
-            ++k;
-            SL(F + LF_K) = fl2(k, k);
-            t0 = t0e + k;
-            pc = int(I.z);
-          }
+          JUMP(int(I.w))
         }
-        break;
+        int k = bits(SL(F + LF_K).x);
+        if (k == int(I.y)) {
+          t0 = t0e + k;
+          NEXT
+        }
+        ++k;
+        SL(F + LF_K) = fl2(k, k);
+        t0 = t0e + k;
+        JUMP(int(I.z))
       }
       case X_LEND: {
         const int F = int(I.x >> 8);
         const float2 d = SL(F + LF_DONE), r = SL(F + LF_RES);
         tos = make_float2(bits(d.x) ? r.x : tos.x, bits(d.y) ? r.y : tos.y);
         t0 = bits(SL(F + LF_T0).x);
-        ++pc;
-        break;
+        NEXT
       }
       default:
         return tos;
     }
   }
+#undef NEXT
+#undef JUMP
 #undef PUSH
 #undef BINF
 #undef BINI

@@ -297,7 +297,7 @@ struct Emitter {
       case PC_OP_MODEL: emit(X_MODEL, uint32_t(x.a), uint32_t(int32_t(x.time))); push(); return;
       case PC_OP_PAYOFF:
         if (x.sign == 0) emit(X_CONST, 0, fbits(0.f));
-        else emit(X_PAYOFF, x.sign < 0 ? 1u : 0u, uint32_t(int32_t(x.time)));
+        else emit(X_PAYOFF, x.sign < 0 ? 1u : 0u, uint32_t(int32_t(x.time)), fbits(1.0f));
         push();
         return;
       case PC_OP_NEG: node(x.ch[0]); emit(X_NEGF); return;
@@ -337,7 +337,22 @@ struct Emitter {
         size_t cond_pc = code.size();
         node(x.ch[0]);
         const TNode &th = T[x.ch[1]];
-        if (th.op == PC_OP_REAL || th.op == PC_OP_BOOL || th.op == PC_OP_NAT) {
+        const bool lit_then = th.op == PC_OP_REAL || th.op == PC_OP_BOOL || th.op == PC_OP_NAT;
+        const uint32_t cop = code.back().opa & 0xffu;
+        const bool one_fused = code.size() == cond_pc + 1 &&
+                               (cop == X_LANY || (cop == X_LRED && ((code.back().opa >> 12) & 7u) != 0));
+        if (lit_then && one_fused) {
+          // whole loop in one instruction; the condition stays as a descriptor
+          const uint32_t pidx = uint32_t(pool.size());
+          pool.push_back(th.op == PC_OP_REAL ? float(th.val) : 0.f);
+          if (th.op != PC_OP_REAL) std::memcpy(&pool.back(), &th.a, 4);
+          code[i_loop].opa = X_LOOPANY | ((frame | (pidx << 8)) << 8);
+          code[i_loop].c = uint32_t(cond_pc);
+          pop();
+          node(x.ch[2]);
+          emit(X_LEND, frame);
+          code[i_loop].e = uint32_t(code.size());
+        } else if (lit_then) {
           // literal then-branch: test, latch and step in one instruction
           const uint32_t pidx = uint32_t(pool.size());
           pool.push_back(th.op == PC_OP_REAL ? float(th.val) : 0.f);
@@ -433,6 +448,10 @@ struct Emitter {
     if (xo == X_DIVFK && k == 1.0f) return;
     if (xo == X_MULFK && k == 1.0f) return;
     XInsn &prev = code.back();
+    if ((prev.opa & 0xff) == X_PAYOFF && xo == X_MULFK && prev.c == fbits(1.0f)) {
+      prev.c = fbits(k);  // k * payoff(t): one instruction
+      return;
+    }
     if ((prev.opa & 0xff) == X_MODEL && (xo == X_MULFK || xo == X_DIVFK)) {
       prev.opa = (xo == X_MULFK ? X_MODEL_MULK : X_MODEL_DIVK) | (prev.opa & ~0xffu);
       prev.c = fbits(k);
@@ -536,7 +555,7 @@ pc_status compile_program(const uint32_t *words, size_t n_words, const double *c
     if (op == X_LOOP || op == X_LTEST || op == X_LLATCH || op == X_LNEXT || op == X_LEND) {
       uint32_t f = I.opa >> 8;
       I.opa = op | (uint32_t(stack_slots + LF_SLOTS * f) << 8);
-    } else if (op == X_LSTEPK) {
+    } else if (op == X_LSTEPK || op == X_LOOPANY) {
       uint32_t f = (I.opa >> 8) & 0xffu, pidx = I.opa >> 16;
       I.opa = op | (uint32_t(stack_slots + LF_SLOTS * f) << 8) | (pidx << 16);
     }
@@ -589,6 +608,12 @@ pc_status analyse_program(const Program &p, int32_t t_now, int32_t n_dates, int3
           else lookback = std::max(lookback, frontier - o);
         }
         ++pc;
+      } else if (op == X_LOOPANY) {
+        const int64_t n = I.b;
+        const size_t end = I.e;  // pc after LEND
+        for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(pc + 1, pc + 2, t0 + k);
+        run(pc + 2, end - 1, t0 + n);
+        pc = end;
       } else if (op == X_LOOP) {
         const int64_t n = I.b;
         const size_t cond = pc + 1, test = I.c;

@@ -29,6 +29,12 @@ M3_MONTHLY = W.MarketSpec([100.0, 100.0, 100.0], [0.2, 0.3, 0.25], W.const_corr(
                           [30 * k for k in range(1, 13)])
 
 STRESS = {
+    # double barrier: two compares with different levels -> per-iteration loop step
+    "double_barrier": ("(loopif (or (le (model 0 0) 90.0) (lt 56.0 (model 1 0))) 0.0 "
+                       "(mult (model 0 0) (payoff 0 0 1)) 11)", [], M2, 100.0),
+    # knock-out on a worst-of ratio, literal rebate -> whole-loop instruction
+    "worst_knockout": ("(loopif (le (min (div (model 0 0) 100.0) (div (model 1 0) 50.0)) 0.85) 0.25 "
+                       "(mult (max (sub (div (model 0 0) 100.0) 1.0) 0.0) (payoff 0 0 1)) $0)", [12], M2, 1.0),
     # worst-of on S_i / S0_i with unequal S0 (fused reduce with divide scales)
     "autocall_scaled": (W.autocall_text([100.0, 50.0, 25.0]), [], M3, 1.0),
     # and-chain of barrier tests and a weighted basket (fused ops, mult scales)

@@ -21,7 +21,7 @@ OPS = ["END", "CONST", "MODEL", "PAYOFF", "TIME", "NOW", "NEGF", "NOT", "ADDF", 
        "DIVF", "MAXF", "MINF", "LTF", "LEF", "EQF", "ADDI", "SUBI", "MULI", "MAXI", "MINI", "LTI",
        "LEI", "EQI", "AND", "OR", "ADDFK", "SUBFK", "MULFK", "DIVFK", "MAXFK", "MINFK", "LTFK",
        "LEFK", "EQFK", "RSUBFK", "RDIVFK", "RLTFK", "RLEFK", "MODEL_MULK", "MODEL_DIVK", "IF",
-       "ELSE", "SEL", "LOOP", "LTEST", "LLATCH", "LNEXT", "LEND", "LRED", "LANY", "LSTEPK"]
+       "ELSE", "SEL", "LOOP", "LTEST", "LLATCH", "LNEXT", "LEND", "LRED", "LANY", "LSTEPK", "LOOPANY"]
 OP = {n: i for i, n in enumerate(OPS)}
 LF_K, LF_T0, LF_DONE, LF_RES, LF_NEWLY = range(5)
 
@@ -60,6 +60,35 @@ def run_warp(code, pool, S, sval, disc, n_hist, now, live):
         sp += 1
         tos = np.asarray(v, np.float32).copy()
 
+    def fused(ins, t0_):
+        opa_, b_, c_, e_ = (int(x) for x in ins)
+        A_ = opa_ >> 8
+        bs_ = b_ - (1 << 32) if b_ >= (1 << 31) else b_
+        o = bs_ + t0_ - now
+        n = ((A_ >> 8) & 3) + 1
+        kind, cmpc = (A_ >> 2) & 3, (A_ >> 4) & 7
+        kk = f32(e_)
+        v = None
+        for i in range(n):
+            lab = (A_ >> (10 + 2 * i)) & 3
+            sv = (S[:, lab, o] if o > 0 else np.full(L, sval[o + n_hist][lab])).astype(np.float32)
+            if kind == 1:
+                sv = sv * pool[c_ + i]
+            elif kind == 2:
+                sv = sv / pool[c_ + i]
+            if OPS[opa_ & 0xFF] == "LANY":
+                pi = _cmp(cmpc, sv, kk)
+                v = pi if v is None else ((v & pi) if A_ & 1 else (v | pi))
+            else:
+                rop = A_ & 3
+                v = sv if v is None else (np.fmin(v, sv) if rop == 0 else np.fmax(v, sv) if rop == 1
+                                          else (v + sv).astype(np.float32))
+        if OPS[opa_ & 0xFF] == "LANY":
+            return asf(v.astype(np.int32))
+        if cmpc:
+            return asf(_cmp(cmpc, v, kk).astype(np.int32))
+        return np.asarray(v, np.float32)
+
     while True:
         steps += 1
         assert steps < 10 ** 7, "runaway program"
@@ -82,6 +111,29 @@ def run_warp(code, pool, S, sval, disc, n_hist, now, live):
                 v = v / f32(c)
             push(v); pc_ += 1
         elif name in ("LRED", "LANY"):
+            push(fused(code[pc_], t0)); pc_ += 1
+        elif name == "LOOPANY":
+            F, lit = A & 0xFF, pool[A >> 8]
+            desc = code[pc_ + 1]
+            done, res = ~live, np.zeros(L, np.float32)
+            allv = False
+            for kk in range(b + 1):
+                cnd = asi(fused(desc, t0 + kk)) != 0
+                nw = cnd & ~done
+                res = np.where(nw, lit, res).astype(np.float32)
+                done = done | nw
+                allv = bool(np.all(done))
+                if allv:
+                    break
+            if allv:
+                push(res); pc_ = e
+            else:
+                st(F + LF_T0, asf(np.full(L, t0, np.int32)))
+                st(F + LF_DONE, asf(done.astype(np.int32)))
+                st(F + LF_RES, res)
+                t0 += b
+                pc_ += 2
+        elif name == "LRED_UNUSED":
             o = bs + t0 - now
             n = ((A >> 8) & 3) + 1
             kind, cmpc = (A >> 2) & 3, (A >> 4) & 7
@@ -130,7 +182,7 @@ def run_warp(code, pool, S, sval, disc, n_hist, now, live):
                     t0 = t0e + k; pc_ = c
         elif name == "PAYOFF":
             o = bs + t0 - now
-            v = np.float32(disc[o + n_hist])
+            v = np.float32(f32(c) * np.float32(disc[o + n_hist]))
             push(np.full(L, -v if A else v, np.float32)); pc_ += 1
         elif name == "TIME":
             push(asf(np.full(L, bs + t0, np.int32))); pc_ += 1
@@ -336,4 +388,4 @@ def test_fused_ops_are_emitted_for_workloads():
         code, pool = pc.pc_debug_program(w, k, tp)
         names.append([OPS[int(x) & 0xFF] for x in code[:, 0]])
     assert names[0].count("LRED") >= 10 and "MINF" not in names[0]
-    assert "LANY" in names[1] and "LSTEPK" in names[1]
+    assert "LANY" in names[1] and "LOOPANY" in names[1] and "LSTEPK" not in names[1]
