@@ -297,9 +297,11 @@ pc_status pc_price_batch(size_t n, const pc_model *const *models,
 /* Pathwise sensitivities: price, delta_l = d price / d S0[l] and
  * vega_l = d price / d sigma[l] (l < d) from the derivative of each path's
  * payoff through the GBM map (if / loopif decisions held fixed; valid for
- * payoffs that are Lipschitz in the path).  out_se[0] is the price's
+ * payoffs that are Lipschitz in the path).  Tangent (forward) mode, one
+ * launch per underlying on the same paths as pc_price with this seed.
+ * out_delta, out_vega: [d]; out_se: [1+2d] -- out_se[0] is the price's
  * standard error, out_se[1+l] delta_l's, out_se[1+d+l] vega_l's.
- * Errors: as pc_price. */
+ * Blocks until done.  Errors: as pc_price. */
 pc_status pc_greeks(const pc_model *model, const pc_contract *contract,
                     uint64_t n_paths, uint64_t seed, double *out_price,
                     double *out_delta, double *out_vega, double *out_se);
@@ -319,6 +321,15 @@ pc_status pc_debug_philox(pc_ctx *ctx, const uint32_t *d_ctr, uint32_t key0,
 pc_status pc_debug_paths(const pc_model *model, uint64_t n_paths,
                          uint64_t path_offset, uint64_t seed, uint32_t stream,
                          float *d_S);
+
+/* Per-path probe of pc_greeks for one underlying: writes (payoff,
+ * d payoff / d S0[underlying], d payoff / d sigma[underlying]) of path
+ * path_offset+i to d_paths[3i..3i+2] (device floats) and the six sums
+ * (value, value^2, delta, delta^2, vega, vega^2) then n to d_out[0..6]
+ * (device doubles).  Asynchronous on the context's stream. */
+pc_status pc_debug_greeks_paths(const pc_model *model, const pc_contract *contract,
+                                uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                                int32_t underlying, double *d_out, float *d_paths);
 
 /* Host-only: the executable form pc_load_payoff would run for this program:
  * 4 words per instruction (opcode | A << 8, then three operand words), then

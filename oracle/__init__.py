@@ -20,7 +20,11 @@ Annenkov & Elsman, "Certified Compilation of Financial Contracts" (PPDP'18):
                  bisection Brownian bridge, Cholesky correlation and GBM.
 * ``mc``      -- the Monte Carlo driver: per-path payoffs and mean/SE.
 * ``closed_forms`` -- Black-Scholes call/put, digital, zero-coupon,
-                 forward and Margrabe prices used as pins.
+                 forward and Margrabe prices (and call delta / vega) used as
+                 pins.
+* ``pathwise`` -- per-path derivatives of the payoff in S0_l and sigma_l
+                 (central differences of the oracle's own FP64 map on common
+                 normals).
 
 Every floating-point computation is FP64.  All functions cite the section,
 equation or figure of the paper they follow; readings of ambiguous passages

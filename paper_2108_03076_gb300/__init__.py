@@ -79,6 +79,7 @@ _SIGS = {
     "pc_greeks": [VP, VP, U64, U64, PD, PD, PD, PD],
     "pc_debug_philox": [VP, VP, U32, U32, VP, SZ],
     "pc_debug_paths": [VP, U64, U64, U64, U32, VP],
+    "pc_debug_greeks_paths": [VP, VP, U64, U64, U64, I32, VP, VP],
     "pc_debug_program": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, PU32, SZ, C.POINTER(SZ),
                          C.POINTER(SZ)],
     "pc_debug_bridge": [C.POINTER(ModelDesc), PI32, PU32, SZ, C.POINTER(SZ)],
@@ -259,6 +260,12 @@ def pc_greeks(model: int, contract: int, n_paths: int, seed: int, d: int):
 
 def pc_debug_philox(ctx: int, d_ctr: int, key0: int, key1: int, d_out: int, n: int) -> None:
     _check(lib().pc_debug_philox(VP(ctx), VP(d_ctr), key0, key1, VP(d_out), n))
+
+
+def pc_debug_greeks_paths(model: int, contract: int, n_paths: int, path_offset: int, seed: int,
+                          underlying: int, d_out: int, d_paths: int) -> None:
+    _check(lib().pc_debug_greeks_paths(VP(model), VP(contract), n_paths, path_offset, seed,
+                                       underlying, VP(d_out), VP(d_paths)))
 
 
 def pc_debug_paths(model: int, n_paths: int, path_offset: int, seed: int, stream_id: int,

@@ -26,6 +26,7 @@ struct pc_ctx {
   int sm_count = 0;
   int max_smem = 0;
   double *d_res = nullptr;       // [8]: sum, sumsq, n, -, status word (int32 at d_res+4)
+  double *d_gout = nullptr;      // [PC_MAX_UNDERLYINGS * 8]: sensitivity sums per underlying
   double *d_partials = nullptr;  // tile partials (scratch)
   size_t partial_cap = 0;        // doubles
   unsigned char *d_control = nullptr;  // reduction control block (kControlBytes, zero between launches)
@@ -224,6 +225,49 @@ pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uin
   return PC_OK;
 }
 
+// Sensitivity launch for underlying `label`: the pricing launch set-up with
+// three physical slots per program value and an extra window of X = L W.
+pc_status run_greeks(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
+                     uint64_t seed, int label, double *d_out, float *d_paths) {
+  Launch L;
+  pc_status s = prepare(m, k, n_paths, offset, seed, 0, L);
+  if (s != PC_OK) return s;
+  pc_ctx *c = m->ctx;
+  Layout lay = L.args.lay;
+  const int d = m->H.d;
+  lay.stack = 3 * k->prog.frame_slots;
+  lay.off_bstack = lay.stack;
+  lay.off_cache = lay.off_bstack + m->H.bstack * d;
+  lay.off_win = lay.off_cache;
+  lay.off_xwin = lay.off_win + lay.win * d;
+  lay.words = lay.off_xwin + lay.win * d;
+  int block = 0, best_warps = 0;
+  size_t smem = 0;
+  for (int b = kBlock; b >= 32; b /= 2) {
+    const size_t sm = price_smem_bytes(k->prog.code.size(), pool_padded(k->prog), lay.words, b);
+    if (sm + kStaticSmemReserve > size_t(c->max_smem)) continue;
+    const int warps = greeks_blocks_per_sm(d, b, sm) * (b / 32);
+    if (warps > best_warps) { block = b; best_warps = warps; smem = sm; }
+  }
+  if (!block) return fail(PC_ELIMIT, "program + per-path state with sensitivities exceed shared memory");
+  s = ensure_partials(c, size_t(L.args.n_tiles) * 6);
+  if (s != PC_OK) return s;
+  PriceArgs a = L.args;
+  a.lay = lay;
+  a.width = 6;
+  reduction_chunks(a.n_tiles, a.chunk_tiles, a.n_chunks);
+  a.tile_partials = c->d_partials;
+  a.control = c->d_control;
+  a.out = d_out;
+  a.out_paths = d_paths;
+  a.greek_label = label;
+  const uint64_t need = (a.n_tiles + block / 32 - 1) / (block / 32);
+  const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * best_warps / (block / 32), need));
+  CU(cudaSetDevice(c->device), "cudaSetDevice");
+  CU(launch_greeks(a, grid, block, smem, c->stream), "sensitivity kernel");
+  return PC_OK;
+}
+
 pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
                     uint64_t seed, uint32_t stream, double *d_out, float *d_payoffs) {
   Launch L;
@@ -408,11 +452,13 @@ pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
   }
   if (e == cudaSuccess) e = cudaMalloc(&c->d_res, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_res, 0, 8 * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_gout, PC_MAX_UNDERLYINGS * 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_control, kControlBytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_control, 0, kControlBytes, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     if (c->d_control) cudaFree(c->d_control);
+    if (c->d_gout) cudaFree(c->d_gout);
     if (c->d_res) cudaFree(c->d_res);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -429,6 +475,7 @@ pc_status pc_destroy(pc_ctx *c) {
   cudaStreamSynchronize(c->stream);
   if (c->d_partials) cudaFree(c->d_partials);
   if (c->d_control) cudaFree(c->d_control);
+  if (c->d_gout) cudaFree(c->d_gout);
   if (c->d_res) cudaFree(c->d_res);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -447,7 +494,8 @@ pc_status pc_model_create(pc_ctx *c, const pc_model_desc *desc, pc_model **out) 
     }
     const ModelHost &H = m->H;
     size_t bytes = padded(H.date_ops) + padded(H.ops) + padded(H.A) + padded(H.B) +
-                   padded(H.disc) + padded(H.sval) + padded(H.tau) + 256;
+                   padded(H.disc) + padded(H.sval) + padded(H.tau) + padded(H.Lf) +
+                   padded(H.sig) + 256;
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     cudaError_t e = cudaMalloc(&m->d_mem, bytes);
     if (e != cudaSuccess) {
@@ -465,6 +513,8 @@ pc_status pc_model_create(pc_ctx *c, const pc_model_desc *desc, pc_model **out) 
     if (u == PC_OK) u = upload(H.disc, base, off, D.disc, c->stream);
     if (u == PC_OK) u = upload(H.sval, base, off, D.sval, c->stream);
     if (u == PC_OK) u = upload(H.tau, base, off, D.tau, c->stream);
+    if (u == PC_OK) u = upload(H.Lf, base, off, D.L, c->stream);
+    if (u == PC_OK) u = upload(H.sig, base, off, D.sig, c->stream);
     if (u == PC_OK) {
       cudaError_t e2 = cudaStreamSynchronize(c->stream);
       if (e2 != cudaSuccess) u = cuda_fail(e2, "model upload");
@@ -695,9 +745,45 @@ pc_status pc_price_batch(size_t n, const pc_model *const *models, const pc_contr
   return PC_OK;
 }
 
-pc_status pc_greeks(const pc_model *, const pc_contract *, uint64_t, uint64_t, double *, double *,
-                    double *, double *) {
-  return fail(PC_ELIMIT, "pc_greeks is not available in this build");
+pc_status pc_greeks(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t seed,
+                    double *out_price, double *out_delta, double *out_vega, double *out_se) {
+  if (!m || !k || !out_price || !out_delta || !out_vega || !out_se) return fail(PC_EINVAL, "null argument");
+  if (n_paths < 2) return fail(PC_EINVAL, "n_paths must be >= 2 for a standard error");
+  pc_ctx *c = m->ctx;
+  const int d = m->H.d;
+  for (int l = 0; l < d; ++l) {
+    pc_status s = run_greeks(m, k, n_paths, 0, seed, l, c->d_gout + 8 * l, nullptr);
+    if (s != PC_OK) return s;
+  }
+  double h[PC_MAX_UNDERLYINGS * 8], st[5];
+  CU(cudaMemcpyAsync(h, c->d_gout, size_t(d) * 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+     "result copy");
+  CU(cudaMemcpyAsync(st, c->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "status copy");
+  pc_status s = wait_stream(c);
+  if (s != PC_OK) return s;
+  int32_t status;
+  std::memcpy(&status, &st[4], 4);
+  s = check_status(c, status);
+  if (s != PC_OK) return s;
+  const double n = double(n_paths);
+  auto mean_se = [&](double sum, double sumsq, double &mean, double &se) {
+    mean = sum / n;
+    se = std::sqrt(std::max(0.0, (sumsq - n * mean * mean) / (n - 1.0)) / n);
+  };
+  mean_se(h[0], h[1], *out_price, out_se[0]);
+  for (int l = 0; l < d; ++l) {
+    mean_se(h[8 * l + 2], h[8 * l + 3], out_delta[l], out_se[1 + l]);
+    mean_se(h[8 * l + 4], h[8 * l + 5], out_vega[l], out_se[1 + d + l]);
+  }
+  return PC_OK;
+}
+
+pc_status pc_debug_greeks_paths(const pc_model *m, const pc_contract *k, uint64_t n_paths,
+                                uint64_t path_offset, uint64_t seed, int32_t underlying,
+                                double *d_out, float *d_paths) {
+  if (!m || !k || !d_out || !d_paths) return fail(PC_EINVAL, "null argument");
+  if (underlying < 0 || underlying >= m->H.d) return fail(PC_EINVAL, "underlying out of range");
+  return run_greeks(m, k, n_paths, path_offset, seed, underlying, d_out, d_paths);
 }
 
 pc_status pc_debug_philox(pc_ctx *c, const uint32_t *d_ctr, uint32_t key0, uint32_t key1,

@@ -1,0 +1,408 @@
+// pc_device.cuh -- device building blocks shared by the pricing kernel
+// (pc_kernels.cu) and the pathwise-sensitivity kernel (pc_greeks.cu):
+// Philox4x32-10 (Salmon et al., SC'11), 24-bit uniforms, Box-Muller, the
+// date-ordered Brownian bridge with register Philox caches, correlated GBM,
+// the fused multi-asset reads, and the deterministic FP64 reduction.
+//
+// Per-thread state lives in shared memory as word-interleaved slots: slot s
+// of thread t is at region[s * blockDim.x + t] (float2: two paths per lane),
+// so the warp-uniform slot indices give conflict-free accesses.
+#pragma once
+
+#include <cstdint>
+
+#include "pc_internal.h"
+
+namespace pc {
+namespace {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+constexpr unsigned kFull = 0xffffffffu;
+
+// 2*pi*u - pi for u = (k + 1/2) 2^-24, as one FMA in k.
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr float kThetaScale = float(kTwoPi / 16777216.0);
+constexpr float kThetaOffset = float(kTwoPi / 33554432.0 - kTwoPi / 2.0);
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Philox4x32-10: ten rounds of two 32x32->64 multiplies, the key bumped by
+// the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Box-Muller on one word pair: u_a from the even word, u_b from the odd
+// word; even normal r cos(2 pi u_b), odd normal r sin(2 pi u_b).  The angle
+// is reduced to 2 pi u_b - pi in (-pi, pi), where cos and sin change sign.
+__device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float &z0, float &z1) {
+  const float ua = fmaf(__uint2float_rn(xa >> 8), 0x1p-24f, 0x1p-25f);
+  const float r = sqrt_approx(-2.0f * logf(ua));
+  const float th = fmaf(__uint2float_rn(xb >> 8), kThetaScale, kThetaOffset);
+  z0 = -r * cos_approx(th);
+  z1 = -r * sin_approx(th);
+}
+
+// Two paths per lane: every value of the stack machine is a float2 (.x for
+// the lane's first path, .y for its second), so each fetched and decoded
+// instruction does the work of two paths and the two independent dependency
+// chains (Philox rounds, Box-Muller, bridge) overlap in the pipeline.
+struct Rng2 {
+  uint32_t plo[2], phi[2];
+  uint32_t stream, k0, k1;
+};
+
+__device__ __forceinline__ void block_normals2(uint32_t b, const Rng2 &g, float2 *e) {
+  const uint4 x0 = philox(make_uint4(b, g.plo[0], g.phi[0], g.stream), g.k0, g.k1);
+  const uint4 x1 = philox(make_uint4(b, g.plo[1], g.phi[1], g.stream), g.k0, g.k1);
+  box_muller(x0.x, x0.y, e[0].x, e[1].x);
+  box_muller(x0.z, x0.w, e[2].x, e[3].x);
+  box_muller(x1.x, x1.y, e[0].y, e[1].y);
+  box_muller(x1.z, x1.w, e[2].y, e[3].y);
+}
+
+// Slot s of this thread in the word-interleaved per-thread region (the
+// stride is the block size, 32..kBlock threads).
+#define SL(s) R[(s) * blockDim.x]
+
+template <int D>
+struct PathState {
+  static constexpr int kSlots = cache_slots(D) > 0 ? cache_slots(D) : 1;
+  float2 w[D];                  // W at the last produced date
+  float2 cache[kSlots][4];      // last Philox block (4 normals) of each cached level
+  int f;                        // last produced ordinal (frontier), warp-uniform
+  int bsp;                      // bridge stack size, warp-uniform
+};
+
+// Register cache access with compile-time indices (slot is warp-uniform).
+template <int D, int S>
+__device__ __forceinline__ void cache_copy_in(const PathState<D> &ps, float2 *e) {
+  if constexpr (S < PathState<D>::kSlots) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e[q] = ps.cache[S][q];
+  }
+}
+template <int D, int S>
+__device__ __forceinline__ void cache_copy_out(PathState<D> &ps, const float2 *e) {
+  if constexpr (S < PathState<D>::kSlots) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ps.cache[S][q] = e[q];
+  }
+}
+template <int D>
+__device__ __forceinline__ void cache_load(const PathState<D> &ps, int slot, float2 *e) {
+  switch (slot) {
+    case 0: cache_copy_in<D, 0>(ps, e); break;
+    case 1: cache_copy_in<D, 1>(ps, e); break;
+    case 2: cache_copy_in<D, 2>(ps, e); break;
+    case 3: cache_copy_in<D, 3>(ps, e); break;
+    default: cache_copy_in<D, 4>(ps, e); break;
+  }
+}
+template <int D>
+__device__ __forceinline__ void cache_store(PathState<D> &ps, int slot, const float2 *e) {
+  switch (slot) {
+    case 0: cache_copy_out<D, 0>(ps, e); break;
+    case 1: cache_copy_out<D, 1>(ps, e); break;
+    case 2: cache_copy_out<D, 2>(ps, e); break;
+    case 3: cache_copy_out<D, 3>(ps, e); break;
+    default: cache_copy_out<D, 4>(ps, e); break;
+  }
+}
+
+// Normals j*D .. j*D+D-1 of bridge node j for both paths (see BridgeOp).
+template <int D>
+__device__ __forceinline__ void node_normals(const BridgeOp &op, const Rng2 &g, PathState<D> &ps,
+                                             float2 (&z)[D]) {
+  const uint32_t b0 = op.b0;
+  const int lane0 = int(op.lane0);
+  float2 e[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) e[q] = make_float2(0.f, 0.f);
+  if (op.flags & BR_FROM_CACHE) {
+    cache_load(ps, op.slot, e);
+  } else {
+    block_normals2(b0, g, e);
+  }
+  const bool two = D > 1 && (op.flags & BR_TWO_BLOCKS);
+  if (two) block_normals2(b0 + 1, g, e + 4);
+  if (op.flags & BR_STORE) {
+    if (two) cache_store(ps, op.slot, e + 4);  // constant offsets keep e[] in registers
+    else cache_store(ps, op.slot, e);
+  }
+  switch (lane0) {
+    case 0:
+#pragma unroll
+      for (int i = 0; i < D; ++i) z[i] = e[i];
+      break;
+    case 1:
+#pragma unroll
+      for (int i = 0; i < D; ++i) z[i] = e[1 + i];
+      break;
+    case 2:
+#pragma unroll
+      for (int i = 0; i < D; ++i) z[i] = e[2 + i];
+      break;
+    default:
+#pragma unroll
+      for (int i = 0; i < D; ++i) z[i] = e[3 + i];
+      break;
+  }
+}
+
+__device__ __forceinline__ BridgeOp load_op(const BridgeOp *p) {
+  const uint4 *q = reinterpret_cast<const uint4 *>(p);
+  const uint4 a = __ldg(q), b = __ldg(q + 1);
+  BridgeOp op;
+  op.wl = __uint_as_float(a.x);
+  op.wr = __uint_as_float(a.y);
+  op.sd = __uint_as_float(a.z);
+  op.j = a.w;
+  op.slot = uint16_t(b.x & 0xffffu);
+  op.flags = uint16_t(b.x >> 16);
+  op.m = uint16_t(b.y & 0xffffu);
+  op.lane0 = uint16_t(b.y >> 16);
+  op.b0 = b.z;
+  op.level = b.w;
+  return op;
+}
+
+__device__ __forceinline__ float2 ffma2(float a, float2 x, float2 y) {
+  return make_float2(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y));
+}
+
+// Produce date t (= frontier + 1) for both paths: bridge ops of t, then GBM
+// into the window slot of t.  With XW the correlated Brownian values
+// X = L W of the date are also kept (window at lay.off_xwin), which the
+// pathwise sensitivities need.
+template <int D, bool XW = false>
+__device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev &m,
+                                         const Layout &lay, const Rng2 &g, float2 *R,
+                                         const float (&Bm)[D * D], const float (&S0)[D],
+                                         const float *Lm = nullptr) {
+  const int k0 = __ldg(m.date_ops + t), k1 = __ldg(m.date_ops + t + 1);
+  if (k0 == k1) {
+    --ps.bsp;
+#pragma unroll
+    for (int i = 0; i < D; ++i) ps.w[i] = SL(lay.off_bstack + ps.bsp * D + i);
+  } else {
+    for (int k = k0; k < k1; ++k) {
+      const BridgeOp op = load_op(m.ops + k);
+      float2 z[D];
+      node_normals<D>(op, g, ps, z);
+      float2 nw[D];
+      if (op.flags & BR_ROOT) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) nw[i] = make_float2(op.sd * z[i].x, op.sd * z[i].y);
+      } else {
+        const int top = lay.off_bstack + (ps.bsp - 1) * D;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          const float2 wt = SL(top + i);
+          nw[i] = ffma2(op.wl, ps.w[i],
+                        ffma2(op.wr, wt, make_float2(op.sd * z[i].x, op.sd * z[i].y)));
+        }
+      }
+      if (k + 1 < k1) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) SL(lay.off_bstack + ps.bsp * D + i) = nw[i];
+        ++ps.bsp;
+      } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) ps.w[i] = nw[i];
+      }
+    }
+  }
+  const int ws = lay.off_win + (t & (lay.win - 1)) * D;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const float a = __ldg(m.A + t * D + i);
+    float2 x = make_float2(a, a);
+#pragma unroll
+    for (int k = 0; k <= i; ++k) x = ffma2(Bm[i * D + k], ps.w[k], x);
+    SL(ws + i) = make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y));
+  }
+  if constexpr (XW) {
+    const int xs = lay.off_xwin + (t & (lay.win - 1)) * D;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float2 x = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k <= i; ++k) x = ffma2(Lm[i * D + k], ps.w[k], x);
+      SL(xs + i) = x;
+    }
+  }
+  ps.f = t;
+}
+
+template <int D>
+__device__ __forceinline__ void load_model_regs(const ModelDev &m, float (&Bm)[D * D],
+                                                float (&S0)[D]) {
+#pragma unroll
+  for (int i = 0; i < D * D; ++i) Bm[i] = __ldg(m.B + i);
+#pragma unroll
+  for (int i = 0; i < D; ++i) S0[i] = __ldg(m.sval + m.n_hist * D + i);
+}
+
+__device__ __forceinline__ int bits(float v) { return __float_as_int(v); }
+__device__ __forceinline__ float fl(int v) { return __int_as_float(v); }
+__device__ __forceinline__ float2 fl2(int a, int b) { return make_float2(fl(a), fl(b)); }
+
+__device__ __forceinline__ float cmp_code(int code, float v, float k) {
+  // 1: v < k, 2: v <= k, 3: k < v, 4: k <= v
+  const bool r = code == 1 ? v < k : code == 2 ? v <= k : code == 3 ? k < v : k <= v;
+  return fl(int(r));
+}
+
+// Fused multi-asset value (X_LRED) or test (X_LANY) of instruction I at
+// ordinal o for both paths; results of compares are 0/1 int bits.
+template <int D>
+__device__ __forceinline__ float2 fused_value(const uint4 &I, int o, const float *pool,
+                                              const float2 *R, const ModelDev &m,
+                                              const Layout &lay) {
+  const uint32_t A = I.x >> 8;
+  const int n = int((A >> 8) & 3u) + 1, kind = int((A >> 2) & 3u), code = int((A >> 4) & 7u);
+  const bool any = (I.x & 0xffu) == X_LANY, conj = (A & 1u) != 0;
+  const int rop = int(A & 3u);
+  const float k = __uint_as_float(I.w);
+  const int base = lay.off_win + (o & (lay.win - 1)) * D;
+  float2 v = make_float2(0.f, 0.f);
+  for (int i = 0; i < n; ++i) {
+    int l = int(A >> (10 + 2 * i)) & 3;
+    l = l < D ? l : 0;
+    float2 s;
+    if (o > 0) {
+      s = SL(base + l);
+    } else {
+      const float sv = __ldg(m.sval + (o + m.n_hist) * D + l);
+      s = make_float2(sv, sv);
+    }
+    if (kind == 1) {
+      const float c = pool[I.z + i];
+      s = make_float2(s.x * c, s.y * c);
+    } else if (kind == 2) {
+      const float c = pool[I.z + i];
+      s = make_float2(__fdiv_rn(s.x, c), __fdiv_rn(s.y, c));
+    }
+    if (any) {
+      const float2 p = make_float2(cmp_code(code, s.x, k), cmp_code(code, s.y, k));
+      if (i == 0) v = p;
+      else if (conj) v = fl2(bits(v.x) & bits(p.x), bits(v.y) & bits(p.y));
+      else v = fl2(bits(v.x) | bits(p.x), bits(v.y) | bits(p.y));
+    } else if (i == 0) {
+      v = s;
+    } else if (rop == 0) {
+      v = make_float2(fminf(v.x, s.x), fminf(v.y, s.y));
+    } else if (rop == 1) {
+      v = make_float2(fmaxf(v.x, s.x), fmaxf(v.y, s.y));
+    } else {
+      v = make_float2(v.x + s.x, v.y + s.y);
+    }
+  }
+  if (!any && code) v = make_float2(cmp_code(code, v.x, k), cmp_code(code, v.y, k));
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Deterministic reduction.  Tile t's partial (sum, sum of squares) is an FP64
+// warp sum in a fixed shuffle order.  Tiles form chunks of chunk_tiles
+// consecutive tiles; the warp that finishes a chunk's last tile sums the
+// chunk's partials in index order (lane l takes tiles l, l+32, ...; then a
+// fixed shuffle tree), and the warp that finishes the last chunk sums the
+// chunk partials the same way.  So the result depends only on n_paths, not
+// on which warp ran which tile.  Counters are consumed and re-zeroed by the
+// warps that read them; the tile counter by the last block to exit.
+template <int W>
+__device__ __forceinline__ void warp_sum_strided(const double *src, uint32_t n, int lane,
+                                                 double (&acc)[W]) {
+#pragma unroll
+  for (int v = 0; v < W; ++v) acc[v] = 0.0;
+  for (uint32_t i = lane; i < n; i += 32) {
+#pragma unroll
+    for (int v = 0; v < W; ++v) acc[v] += __ldcg(src + size_t(i) * W + v);
+  }
+#pragma unroll
+  for (int v = 0; v < W; ++v) acc[v] = warp_sum(acc[v]);
+}
+
+template <int W>
+__device__ __noinline__ void finish_tile(const PriceArgs &a, uint64_t tile, const double (&tp)[W],
+                                         int lane) {
+  unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
+  uint32_t *chunk_cnt = reinterpret_cast<uint32_t *>(a.control + kChunkCountOff);
+  double *chunk_part = reinterpret_cast<double *>(a.control + kChunkPartOff);
+  const uint32_t chunk = uint32_t(tile / a.chunk_tiles);
+  const uint64_t first = uint64_t(chunk) * a.chunk_tiles;
+  const uint64_t rest = a.n_tiles - first;
+  const uint32_t size = rest < a.chunk_tiles ? uint32_t(rest) : a.chunk_tiles;
+  uint32_t seen = 0;
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < W; ++v) a.tile_partials[tile * W + v] = tp[v];
+    __threadfence();
+    seen = atomicAdd(chunk_cnt + chunk, 1u);
+  }
+  seen = __shfl_sync(kFull, seen, 0);
+  if (seen != size - 1) return;
+  // this warp completed the chunk
+  __threadfence();
+  double acc[W];
+  warp_sum_strided<W>(a.tile_partials + first * W, size, lane, acc);
+  unsigned long long done = 0;
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < W; ++v) chunk_part[size_t(chunk) * W + v] = acc[v];
+    chunk_cnt[chunk] = 0;
+    __threadfence();
+    done = atomicAdd(ctr + 2, 1ull);
+  }
+  done = __shfl_sync(kFull, done, 0);
+  if (done != a.n_chunks - 1) return;
+  // this warp completed the last chunk
+  __threadfence();
+  warp_sum_strided<W>(chunk_part, a.n_chunks, lane, acc);
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < W; ++v) a.out[v] = acc[v];
+    a.out[W] = double(a.n_paths);
+    ctr[2] = 0;
+  }
+}
+
+}  // namespace
+}  // namespace pc

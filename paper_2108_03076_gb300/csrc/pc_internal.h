@@ -136,8 +136,10 @@ struct ModelDev {
   const float *B;           // [d*d]     log2(e) sigma_i L_ik
   const float *disc;        // [n_hist+n+1] disc of ordinal o at index o + n_hist
   const float *sval;        // [(n_hist+1)*d] value of label l at ordinal o <= 0, index (o+n_hist)*d+l
-  // pathwise tangents (greeks): per ordinal o, tau_o as float
-  const float *tau;         // [n+1]
+  // pathwise tangents (greeks)
+  const float *tau;         // [n+1] year fraction of ordinal o
+  const float *L;           // [d*d] Cholesky factor (row-major)
+  const float *sig;         // [d] volatilities
   int32_t d, n, n_hist, t_now;
   int32_t n_levels;         // bisection levels
   int32_t bstack;           // bridge stack depth
@@ -150,6 +152,7 @@ struct Layout {
   int32_t off_bstack; // bridge stack (bstack * d)
   int32_t off_cache;  // level caches (n_levels * 4)
   int32_t off_win;    // date window (win * d)
+  int32_t off_xwin;   // window of X = L W (win * d), sensitivity kernel only
   int32_t words;      // total words per thread
   int32_t win;        // window size (power of two)
 };
@@ -180,8 +183,9 @@ struct PriceArgs {
   double *tile_partials;    // [n_tiles * width] scratch
   unsigned char *control;   // kControlBytes of scratch, zero between launches (see below)
   double *out;              // [width + 1]: sums over all paths, then n_paths
-  float *out_paths;         // nullable: per-path payoffs
+  float *out_paths;         // nullable: per-path payoffs (sensitivities: 3 floats per path)
   int32_t *status;          // device status word (nonzero = error)
+  int32_t greek_label;      // sensitivity kernel: the underlying g of the tangents
 };
 
 // Reduction scratch "control" block (zero between launches; every launch
@@ -201,7 +205,8 @@ inline void reduction_chunks(uint64_t n_tiles, uint32_t &chunk_tiles, uint32_t &
 
 // Kernel launchers (pc_kernels.cu).  All return a cudaError_t.
 cudaError_t launch_price(const PriceArgs &a, int grid, int block, size_t smem_bytes, cudaStream_t s);
-cudaError_t launch_greeks(const PriceArgs &a, int grid, size_t smem_bytes, cudaStream_t s);
+cudaError_t launch_greeks(const PriceArgs &a, int grid, int block, size_t smem_bytes, cudaStream_t s);
+int greeks_blocks_per_sm(int d, int block, size_t smem_bytes);
 cudaError_t launch_debug_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                                 size_t n, cudaStream_t s);
 cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_paths,
@@ -253,7 +258,7 @@ struct ModelHost {
   // device tables, host copies
   std::vector<int32_t> date_ops;
   std::vector<BridgeOp> ops;
-  std::vector<float> A, B, disc, sval, tau;
+  std::vector<float> A, B, disc, sval, tau, Lf, sig;
   int32_t n_levels = 0, bstack = 0;
 };
 

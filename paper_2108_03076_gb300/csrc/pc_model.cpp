@@ -221,6 +221,8 @@ pc_status build_model(const pc_model_desc &desc, ModelHost &M, std::string &err)
           float(o == 0 ? M.S0[l] : M.history[size_t(-o - 1) * d + l]);
   M.tau.assign(size_t(n + 1), 0.f);
   for (int o = 0; o <= n; ++o) M.tau[o] = float(tau[o]);
+  M.Lf.assign(M.L.begin(), M.L.end());
+  M.sig.assign(M.sigma.begin(), M.sigma.end());
   return PC_OK;
 }
 
