@@ -39,6 +39,8 @@ METRIC = "path·date evals/sec & contracts priced/sec at 1e-4 rel. std-err vs pl
 UNIT = "path·date/s"
 TARGET_REL_SE = 1e-4
 KERNEL_SRC = os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", "pc_kernels.cu")
+PORTFOLIO = "portfolio_1024"
+PORTFOLIO_SEED = 0x5EED0004
 
 
 def dist_env():
@@ -197,10 +199,13 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="worst_of_autocall_3u_5d", choices=sorted(W.ALL))
+    ap.add_argument("--workload", default="worst_of_autocall_3u_5d",
+                    choices=sorted(W.ALL) + [PORTFOLIO])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.workload == PORTFOLIO:
+        return run_portfolio(args)
     w = W.ALL[args.workload]()
     if args.impl == "reference":
         return run_reference(args, w)
@@ -329,6 +334,192 @@ def main():
     if ws > 1:
         dist.destroy_process_group()
 
+
+
+# ---------------------------------------------------------------------------
+# Portfolio: 1024 templated contracts priced by one replay of a batch plan
+# ---------------------------------------------------------------------------
+
+
+def portfolio_config(items, ws) -> dict:
+    from collections import Counter
+    return {"workload": PORTFOLIO, "contracts": len(items),
+            "total_paths": sum(it.n_paths for it in items),
+            "path_dates": sum(it.n_paths * it.market.n for it in items),
+            "templates": dict(Counter(it.template for it in items)),
+            "underlyings": "1-4", "dates": "1-365", "seed": PORTFOLIO_SEED,
+            "parallelism": f"contracts x{ws}",
+            "l2": "flushed between steps by a 256 MiB device write"}
+
+
+def portfolio_reference(args, items):
+    """The oracle on a bounded sample per step: 512 paths of each of the
+    next contracts in portfolio order until 2 s of CPU time are used."""
+    from oracle import il_text, mc
+    from oracle.paths import Market
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    i = 0
+
+    def step(budget=2.0):
+        nonlocal i
+        pd, el = 0, 0.0
+        while el < budget:
+            it = items[i % len(items)]
+            n = min(512, it.n_paths)
+            env = {f"${k}": v for k, v in enumerate(it.tparams)}
+            t = time.perf_counter()
+            mc.payoffs(il_text.parse(it.il_text), Market(**vars(it.market)), env, 0, 1, n,
+                       PORTFOLIO_SEED, i % len(items), 0)
+            el += time.perf_counter() - t
+            pd += n * it.market.n
+            i += 1
+        return pd, el
+    for _ in range(args.warmup):
+        step(0.2)
+    tot_pd, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        pd, el = step()
+        tot_pd += pd
+        tot_t += el
+    pd_rate = tot_pd / tot_t
+    # contracts priced per second at the portfolio's own path budgets
+    value = pd_rate * len(items) / sum(it.n_paths * it.market.n for it in items)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "contracts/s",
+            "path_date_evals_per_sec": pd_rate,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": portfolio_config(items, ws),
+            "cpu_baseline": {"value": value, "unit": "contracts/s", "cores": 1, "kind": "oracle",
+                             "sample": "512 paths of each contract in portfolio order, 2 s per "
+                                       "step; rate scaled to the full path budgets"},
+            "e2e": {"value": value, "unit": "contracts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_portfolio(args):
+    items = W.portfolio()
+    if args.impl == "reference":
+        return portfolio_reference(args, items)
+    import numpy as np
+    import torch
+    import paper_2108_03076_gb300 as pc
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        from paper_2108_03076_gb300 import build
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    mine = items[rank::ws]          # contracts are independent: shard them
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
+    ctx = pc.pc_create(local, stream.cuda_stream)
+    models, contracts, programs = [], [], []
+    for it in mine:
+        s = it.market
+        models.append(pc.pc_model_create(ctx, s.S0, s.sigma, s.corr, s.r, s.days))
+        w_, k_ = pc.pc_assemble(it.il_text)
+        programs.append((w_, k_, it.tparams))
+        contracts.append(pc.pc_load_payoff(ctx, w_, k_, it.tparams, 0, 1))
+    n_paths = [it.n_paths for it in mine]
+    plan = pc.pc_batch_create(models, contracts, n_paths, PORTFOLIO_SEED)
+    pc.pc_batch_tune(plan, 2)
+    binfo = pc.pc_batch_query(plan)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        pc.pc_batch_launch(plan)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            pc.pc_batch_launch(plan)
+            b.record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t_dev = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    price, se = pc.pc_batch_results(plan, len(mine))
+
+    # end to end through the public API: load every program from host
+    # memory, price the portfolio in one call, read the prices back
+    n_e2e = max(2, min(args.e2e_steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        ks = [pc.pc_load_payoff(ctx, w_, k_, tp, 0, 1) for (w_, k_, tp) in programs]
+        pc.pc_price_batch(models, ks, n_paths, PORTFOLIO_SEED)
+        for k in ks:
+            pc.pc_contract_destroy(k)
+    e2e_step = (time.perf_counter() - t0) / n_e2e
+
+    if ws > 1:
+        t = torch.tensor([t_dev, e2e_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_dev, e2e_step = float(t[0]), float(t[1])
+    step_s = t_dev / args.steps
+    path_dates = sum(it.n_paths * it.market.n for it in items)
+    ops = 0
+    mufu = 0
+    for m, it in zip(models, mine):
+        o = alg_ops_per_path(pc.pc_model_query(m))
+        ops += o["ops"] * it.n_paths
+        mufu += o["mufu"] * it.n_paths
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    clock_hz = 1e6 * float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * 128 * clock_hz
+    rel = np.abs(se / np.where(price != 0, price, np.nan))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ws * len(mine) / step_s,
+            "unit": "contracts/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": portfolio_config(items, ws),
+            "value_note": "contracts priced per second at their own path budgets "
+                          "(2^12-2^18); median rel. std-err of those prices below",
+            "path_date_evals_per_sec": ws * sum(it.n_paths * it.market.n for it in mine) / step_s,
+            "median_rel_stderr": float(np.nanmedian(rel)),
+            "path_dates_per_step": path_dates,
+            "gpu_launches": args.steps * binfo.n_groups,
+            "batch": {"groups": binfo.n_groups, "units": binfo.n_units, "tiles": binfo.n_tiles,
+                      "block": binfo.config.block, "unit_split": binfo.config.unit_split,
+                      "paths_per_thread": binfo.paths_per_thread, "tuned_ms": binfo.last_ms},
+            "e2e": {"value": ws * len(mine) / e2e_step, "unit": "contracts/s",
+                    "h2d_bytes_per_step": int(sum(w_.nbytes + k_.nbytes + 4 * len(tp)
+                                                  for (w_, k_, tp) in programs)),
+                    "d2h_bytes_per_step": 16 * len(mine) + 40,
+                    "note": "pc_load_payoff x contracts + pc_price_batch + pc_contract_destroy "
+                            "per step, host wall clock"},
+            "roofline": {"bound": "alu", "achieved": ops / step_s / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s", "frac": ops / step_s / peak_ops, "traffic": None,
+                         "mufu_frac": mufu / step_s / (props.multi_processor_count * 16 * clock_hz),
+                         "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x "
+                                       f"{clock_hz / 1e6:.0f} MHz issue (MUFU: x16)"},
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    pc.pc_batch_destroy(plan)
+    for k in contracts:
+        pc.pc_contract_destroy(k)
+    for m in models:
+        pc.pc_model_destroy(m)
+    pc.pc_destroy(ctx)
+    if ws > 1:
+        dist.destroy_process_group()
 
 if __name__ == "__main__":
     main()

@@ -285,10 +285,84 @@ pc_status pc_price_noalloc(const pc_model *model, const pc_contract *contract,
                            uint64_t n_paths, uint64_t path_offset, uint64_t seed,
                            uint32_t stream, double *d_out);
 
-/* Price n contracts, each against its own model, in one launch:
- * contract i runs n_paths[i] paths on Philox stream word i.  Outputs
- * out_price[i], out_stderr[i] (host).  Blocks until done.
- * Errors: as pc_price. */
+/* ------------------------------------------------------------------------ */
+/* Portfolio pricing                                                         */
+/* ------------------------------------------------------------------------ */
+/* The paper prices one contract per engine invocation; templating (Sec. 2,
+ * Sec. 6.2) is what makes many instruments of one shape cheap to set up.
+ * A batch plan prices many such contracts -- uneven program lengths, date
+ * counts and path budgets -- in persistent launches, one per group of
+ * contracts with the same underlying count and a similar per-path shared-
+ * memory footprint.  Work units (a contract and a run of its 64-path tiles)
+ * are ordered costliest first and taken by warps from a counter; each
+ * contract reduces into its own scratch, so its price and standard error
+ * are bit-identical to pc_price(models[i], contracts[i], n_paths[i], seed)
+ * with Philox stream word i -- i.e. to pc_price_paths/pc_price_async with
+ * stream = i, path_offset = 0.  The launches are captured once into a CUDA
+ * graph and replayed by pc_batch_launch. */
+typedef struct pc_batch pc_batch;
+
+/* Launch shape of a plan.  block: threads per block preferred for every
+ * group (128, 64 or 32; a group whose footprint does not fit falls back to
+ * the next smaller size).  unit_split: each warp's fair share of the plan's
+ * estimated work is cut into about this many units (>= 1); a contract's
+ * unit is its tiles grouped so that the unit's estimated cost is at most
+ * that share (at least one tile).  The paths a thread evaluates per unit
+ * are 2 x tiles per unit. */
+typedef struct pc_batch_config {
+  int32_t block;
+  int32_t unit_split;
+} pc_batch_config;
+
+typedef struct pc_batch_info {
+  uint64_t n_contracts;
+  uint64_t n_tiles;          /* 64-path tiles over all contracts            */
+  uint64_t n_units;          /* work units under the current config         */
+  int32_t n_groups;          /* persistent launches per replay              */
+  int32_t tuned;             /* 1 after pc_batch_tune                       */
+  pc_batch_config config;    /* current launch shape                        */
+  double paths_per_thread;   /* mean paths a thread evaluates per unit      */
+  double last_ms;            /* device time of the last timed replay (tune) */
+} pc_batch_info;
+
+/* Build a plan over n contracts: contract i is priced against models[i]
+ * with n_paths[i] paths (2 .. 2^40) on Philox stream word i under `seed`.
+ * All models and contracts must belong to one context and stay alive until
+ * pc_batch_destroy.  config may be NULL (block 128, unit_split 32).
+ * Allocates the plan's device memory (per-contract arguments, units,
+ * reduction scratch, outputs) and instantiates its graph.
+ * Errors: PC_EINVAL (null, empty, mixed contexts, n_paths out of range),
+ * PC_ERANGE (a program reads a label or date outside its model), PC_ELIMIT
+ * (a contract's per-path state exceeds shared memory), PC_ENOMEM, PC_ECUDA. */
+pc_status pc_batch_create(size_t n, const pc_model *const *models,
+                          const pc_contract *const *contracts,
+                          const uint64_t *n_paths, uint64_t seed,
+                          const pc_batch_config *config, pc_batch **out);
+
+/* Autotuner: times every candidate launch shape (block 128 / 64, unit_split
+ * 8 / 32 / 128) over `reps` replays each (>= 1, after one warm-up replay)
+ * with CUDA events on the context's stream, keeps the fastest and
+ * re-instantiates the graph with it.  Results of the plan are unchanged by
+ * the shape.  Blocks until done.  Errors: as pc_batch_launch. */
+pc_status pc_batch_tune(pc_batch *plan, int32_t reps);
+
+/* Replay the plan's graph on the context's stream (asynchronous).
+ * Errors: PC_EINVAL, PC_ECUDA. */
+pc_status pc_batch_launch(pc_batch *plan);
+
+/* Wait for the last replay and return out_price[i], out_stderr[i] (host,
+ * [n] each); out_sums (nullable, host [3n]) receives each contract's
+ * (sum x, sum x^2, n) for merging partial runs across processes.
+ * Errors: PC_ETIMEOUT, PC_EDEVICE, PC_ECUDA. */
+pc_status pc_batch_results(pc_batch *plan, double *out_price, double *out_stderr,
+                           double *out_sums);
+
+pc_status pc_batch_query(const pc_batch *plan, pc_batch_info *info);
+pc_status pc_batch_destroy(pc_batch *plan);
+
+/* One-shot portfolio pricing: pc_batch_create with the default shape,
+ * one replay, pc_batch_results, pc_batch_destroy.  Blocks until done.
+ * Errors: as pc_batch_create and pc_batch_results. */
 pc_status pc_price_batch(size_t n, const pc_model *const *models,
                          const pc_contract *const *contracts,
                          const uint64_t *n_paths, uint64_t seed,

@@ -98,3 +98,37 @@ def daily_barrier_cl(S0: Sequence[float], barrier: float = 0.7,
     for x in terms[1:]:
         ladder = op("add", ladder, x)
     return IfWithin(hit, T, Zero(), Scale(ladder, xfer()))
+
+
+def basket(d: int):
+    """(obs(0,0) + ... + obs(d-1,0)) / d, left-nested (every S0 = 1)."""
+    s = Obs(0, 0)
+    for i in range(1, d):
+        s = op("add", s, Obs(i, 0))
+    return op("div", s, RLit(float(d)))
+
+
+def basket_call_cl(d: int, K: float):
+    """translate(T, scale(max(basket - K, 0), transfer))."""
+    return Translate(T, Scale(op("max", op("sub", basket(d), RLit(K)), RLit(0.0)), xfer()))
+
+
+def basket_digital_cl(d: int, K: float):
+    return Translate(T, Scale(op("cond", gt(basket(d), RLit(K)), RLit(1.0), RLit(0.0)), xfer()))
+
+
+def call_spread_cl(d: int, K1: float, K2: float):
+    """translate(T, scale(max(basket - K1, 0) - max(basket - K2, 0), transfer))."""
+    return Translate(T, Scale(op("sub", op("max", op("sub", basket(d), RLit(K1)), RLit(0.0)),
+                                 op("max", op("sub", basket(d), RLit(K2)), RLit(0.0))), xfer()))
+
+
+def asian_cl(n: int, S0: float, K: float):
+    """Average-rate call: translate(T, scale(max(mean_{j<n} obs(0,-j) / S0 - K, 0),
+    transfer)), the mean over the n grid dates ending at T, summed oldest
+    fixing first."""
+    s = Obs(0, -(n - 1))
+    for j in reversed(range(n - 1)):
+        s = op("add", s, Obs(0, -j))
+    avg = op("div", op("div", s, RLit(float(n))), RLit(S0))
+    return Translate(T, Scale(op("max", op("sub", avg, RLit(K)), RLit(0.0)), xfer()))

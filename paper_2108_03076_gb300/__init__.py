@@ -50,6 +50,16 @@ class ModelInfo(C.Structure):
                 ("philox_blocks", C.c_int32), ("box_muller_pairs", C.c_int32)]
 
 
+class BatchConfig(C.Structure):
+    _fields_ = [("block", C.c_int32), ("unit_split", C.c_int32)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_contracts", C.c_uint64), ("n_tiles", C.c_uint64), ("n_units", C.c_uint64),
+                ("n_groups", C.c_int32), ("tuned", C.c_int32), ("config", BatchConfig),
+                ("paths_per_thread", C.c_double), ("last_ms", C.c_double)]
+
+
 class ProgramInfo(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_insn", C.c_int32), ("max_stack", C.c_int32),
                 ("result_is_real", C.c_int32), ("n_loops", C.c_int32),
@@ -76,6 +86,13 @@ _SIGS = {
     "pc_price_paths": [VP, VP, U64, U64, U64, U32, VP, VP],
     "pc_price_noalloc": [VP, VP, U64, U64, U64, U32, VP],
     "pc_price_batch": [SZ, C.POINTER(VP), C.POINTER(VP), C.POINTER(U64), U64, PD, PD],
+    "pc_batch_create": [SZ, C.POINTER(VP), C.POINTER(VP), C.POINTER(U64), U64,
+                        C.POINTER(BatchConfig), C.POINTER(VP)],
+    "pc_batch_tune": [VP, C.c_int32],
+    "pc_batch_launch": [VP],
+    "pc_batch_results": [VP, PD, PD, PD],
+    "pc_batch_query": [VP, C.POINTER(BatchInfo)],
+    "pc_batch_destroy": [VP],
     "pc_greeks": [VP, VP, U64, U64, PD, PD, PD, PD],
     "pc_debug_philox": [VP, VP, U32, U32, VP, SZ],
     "pc_debug_paths": [VP, U64, U64, U64, U32, VP],
@@ -238,15 +255,60 @@ def pc_price_noalloc(model: int, contract: int, n_paths: int, path_offset: int, 
 NOALLOC_MAX_PATHS = 1 << 24
 
 
-def pc_price_batch(models: Sequence[int], contracts: Sequence[int], n_paths: Sequence[int],
-                   seed: int) -> Tuple[np.ndarray, np.ndarray]:
+def _batch_arrays(models, contracts, n_paths):
     n = len(contracts)
+    if len(models) != n or len(n_paths) != n:
+        raise ValueError("models, contracts and n_paths must have the same length")
     M = (VP * n)(*[VP(m) for m in models])
     K = (VP * n)(*[VP(k) for k in contracts])
     N = (U64 * n)(*[int(x) for x in n_paths])
+    return n, M, K, N
+
+
+def pc_price_batch(models: Sequence[int], contracts: Sequence[int], n_paths: Sequence[int],
+                   seed: int) -> Tuple[np.ndarray, np.ndarray]:
+    n, M, K, N = _batch_arrays(models, contracts, n_paths)
     price, se = np.zeros(n), np.zeros(n)
     _check(lib().pc_price_batch(n, M, K, N, seed, _ptr(price, C.c_double), _ptr(se, C.c_double)))
     return price, se
+
+
+def pc_batch_create(models: Sequence[int], contracts: Sequence[int], n_paths: Sequence[int],
+                    seed: int, block: Optional[int] = None, unit_split: Optional[int] = None) -> int:
+    n, M, K, N = _batch_arrays(models, contracts, n_paths)
+    cfg = None
+    if block is not None or unit_split is not None:
+        cfg = C.byref(BatchConfig(block or 128, unit_split or 32))
+    h = VP()
+    _check(lib().pc_batch_create(n, M, K, N, seed, cfg, C.byref(h)))
+    return h.value
+
+
+def pc_batch_tune(plan: int, reps: int = 2) -> None:
+    _check(lib().pc_batch_tune(VP(plan), int(reps)))
+
+
+def pc_batch_launch(plan: int) -> None:
+    _check(lib().pc_batch_launch(VP(plan)))
+
+
+def pc_batch_results(plan: int, n: int, sums: bool = False):
+    """(price[n], stderr[n]) or, with sums, (price, stderr, sums[n, 3])."""
+    price, se = np.zeros(n), np.zeros(n)
+    out = np.zeros(3 * n) if sums else None
+    _check(lib().pc_batch_results(VP(plan), _ptr(price, C.c_double), _ptr(se, C.c_double),
+                                  _ptr(out, C.c_double) if sums else None))
+    return (price, se, out.reshape(n, 3)) if sums else (price, se)
+
+
+def pc_batch_query(plan: int) -> BatchInfo:
+    info = BatchInfo()
+    _check(lib().pc_batch_query(VP(plan), C.byref(info)))
+    return info
+
+
+def pc_batch_destroy(plan: int) -> None:
+    _check(lib().pc_batch_destroy(VP(plan)))
 
 
 def pc_greeks(model: int, contract: int, n_paths: int, seed: int, d: int):

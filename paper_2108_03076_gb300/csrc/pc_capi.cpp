@@ -15,45 +15,17 @@
 #include <new>
 #include <thread>
 
+#include "pc_handles.h"
 #include "pc_internal.h"
 
 using namespace pc;
 
-struct pc_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int sm_count = 0;
-  int max_smem = 0;
-  double *d_res = nullptr;       // [8]: sum, sumsq, n, -, status word (int32 at d_res+4)
-  double *d_gout = nullptr;      // [PC_MAX_UNDERLYINGS * 8]: sensitivity sums per underlying
-  double *d_partials = nullptr;  // tile partials (scratch)
-  size_t partial_cap = 0;        // doubles
-  unsigned char *d_control = nullptr;  // reduction control block (kControlBytes, zero between launches)
-  double timeout_s = 300.0;
-  int live_objects = 0;
-};
-
-struct pc_model {
-  pc_ctx *ctx = nullptr;
-  ModelHost H;
-  void *d_mem = nullptr;
-  ModelDev dev{};
-  uint64_t id = 0;
-};
-
-struct pc_contract {
-  pc_ctx *ctx = nullptr;
-  Program prog;
-  XInsn *d_code = nullptr;
-  std::mutex mu;
-  std::map<std::pair<uint64_t, uint64_t>, int32_t> win_cache;  // (model id, layout key) -> window
-};
-
 namespace {
-
 thread_local std::string tl_err;
 std::atomic<uint64_t> g_model_ids{1};
+}  // namespace
+
+namespace pc {
 
 pc_status fail(pc_status s, const std::string &m) {
   tl_err = m;
@@ -64,12 +36,6 @@ pc_status cuda_fail(cudaError_t e, const char *what) {
   return fail(e == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA,
               std::string(what) + ": " + cudaGetErrorString(e));
 }
-
-#define CU(call, what)                              \
-  do {                                              \
-    cudaError_t e_ = (call);                        \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-  } while (0)
 
 // Wait for the stream with a wall-clock limit.
 pc_status wait_stream(pc_ctx *c) {
@@ -156,17 +122,6 @@ pc_status window_for(const pc_model *m, const pc_contract *k, int32_t &win) {
   kc->win_cache[key] = win;
   return PC_OK;
 }
-
-// Room left for the pricing kernel's static shared memory (reduction
-// scratch and flags) when sizing its dynamic shared memory.
-constexpr size_t kStaticSmemReserve = 2048;
-
-struct Launch {
-  PriceArgs args{};
-  int grid = 0;
-  int block = kBlock;
-  size_t smem = 0;
-};
 
 // Block size (128, 64 or 32 threads) that keeps the most warps resident per
 // SM given the program's shared-memory footprint; 0 if none fits.
@@ -359,7 +314,7 @@ struct NoAllocAnalysis {
   }
 };
 
-}  // namespace
+}  // namespace pc
 
 extern "C" {
 
@@ -700,48 +655,6 @@ pc_status pc_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, ui
   const double var = std::max(0.0, (h[1] - n * mean * mean) / (n - 1.0));
   *out_price = mean;
   *out_stderr = std::sqrt(var / n);
-  return PC_OK;
-}
-
-pc_status pc_price_batch(size_t n, const pc_model *const *models, const pc_contract *const *contracts,
-                         const uint64_t *n_paths, uint64_t seed, double *out_price,
-                         double *out_stderr) {
-  if (n == 0) return PC_OK;
-  if (!models || !contracts || !n_paths || !out_price || !out_stderr)
-    return fail(PC_EINVAL, "null argument");
-  if (!models[0]) return fail(PC_EINVAL, "null model");
-  pc_ctx *c = models[0]->ctx;
-  for (size_t i = 0; i < n; ++i) {
-    if (!models[i] || !contracts[i] || models[i]->ctx != c || contracts[i]->ctx != c)
-      return fail(PC_EINVAL, "batch members must be non-null and share one context");
-    if (n_paths[i] < 2) return fail(PC_EINVAL, "n_paths must be >= 2");
-  }
-  double *d_out = nullptr;
-  CU(cudaMalloc(&d_out, n * 4 * sizeof(double)), "batch outputs");
-  pc_status s = PC_OK;
-  for (size_t i = 0; i < n && s == PC_OK; ++i)
-    s = run_price(models[i], contracts[i], n_paths[i], 0, seed, uint32_t(i), d_out + 4 * i, nullptr);
-  std::vector<double> h(n * 4);
-  if (s == PC_OK) {
-    cudaError_t e = cudaMemcpyAsync(h.data(), d_out, n * 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    if (e != cudaSuccess) s = cuda_fail(e, "batch copy");
-  }
-  if (s == PC_OK) s = wait_stream(c);
-  double st[5];
-  if (s == PC_OK) {
-    cudaError_t e = cudaMemcpy(st, c->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) s = cuda_fail(e, "status copy");
-    int32_t status;
-    std::memcpy(&status, &st[4], 4);
-    if (s == PC_OK) s = check_status(c, status);
-  }
-  cudaFree(d_out);
-  if (s != PC_OK) return s;
-  for (size_t i = 0; i < n; ++i) {
-    const double N = double(n_paths[i]), mean = h[4 * i] / N;
-    out_price[i] = mean;
-    out_stderr[i] = std::sqrt(std::max(0.0, (h[4 * i + 1] - N * mean * mean) / (N - 1.0)) / N);
-  }
   return PC_OK;
 }
 

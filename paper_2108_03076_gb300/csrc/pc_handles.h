@@ -1,0 +1,87 @@
+// pc_handles.h -- the opaque handles of include/pc.h and the host helpers
+// shared by the entry-point files (pc_capi.cpp, pc_batch.cpp).  Private to
+// the library.
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include <cuda_runtime.h>
+
+#include "pc.h"
+#include "pc_internal.h"
+
+struct pc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 0;
+  int max_smem = 0;
+  double *d_res = nullptr;       // [8]: sum, sumsq, n, -, status word (int32 at d_res+4)
+  double *d_gout = nullptr;      // [PC_MAX_UNDERLYINGS * 8]: sensitivity sums per underlying
+  double *d_partials = nullptr;  // tile partials (scratch)
+  size_t partial_cap = 0;        // doubles
+  unsigned char *d_control = nullptr;  // reduction control block (kControlBytes, zero between launches)
+  double timeout_s = 300.0;
+  int live_objects = 0;
+};
+
+struct pc_model {
+  pc_ctx *ctx = nullptr;
+  pc::ModelHost H;
+  void *d_mem = nullptr;
+  pc::ModelDev dev{};
+  uint64_t id = 0;
+};
+
+struct pc_contract {
+  pc_ctx *ctx = nullptr;
+  pc::Program prog;
+  pc::XInsn *d_code = nullptr;
+  std::mutex mu;
+  std::map<std::pair<uint64_t, uint64_t>, int32_t> win_cache;  // (model id, layout key) -> window
+};
+
+namespace pc {
+
+// Record a message for pc_last_error and return the status.
+pc_status fail(pc_status s, const std::string &m);
+pc_status cuda_fail(cudaError_t e, const char *what);
+
+#define CU(call, what)                                 \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return ::pc::cuda_fail(e_, what); \
+  } while (0)
+
+// Wait for the context's stream with its wall-clock limit.
+pc_status wait_stream(pc_ctx *c);
+
+// Room left for a kernel's static shared memory when sizing its dynamic
+// shared memory.
+constexpr size_t kStaticSmemReserve = 2048;
+
+// Constant-pool floats of a program, rounded up to whole 16-byte words.
+size_t pool_padded(const Program &p);
+
+// A pricing launch: per-contract arguments plus its single-launch shape.
+struct Launch {
+  PriceArgs args{};
+  int grid = 0;
+  int block = kBlock;
+  size_t smem = 0;
+};
+
+// Validate (model, contract, n_paths), resolve the contract's date window for
+// the model and fill the per-contract arguments (everything but the
+// reduction scratch and outputs) and a single-launch shape.
+pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
+                  uint64_t seed, uint32_t stream, Launch &L);
+
+// Turn a raised device status word into PC_EDEVICE (and clear it).
+pc_status check_status(pc_ctx *c, int32_t status);
+
+}  // namespace pc

@@ -213,6 +213,40 @@ cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_
                                uint64_t offset, uint32_t k0, uint32_t k1, uint32_t stream,
                                float *out, cudaStream_t s);
 int price_blocks_per_sm(int d, int block, size_t smem_bytes, bool greeks);
+
+// Portfolio pricing (one persistent launch per group of contracts with the
+// same underlying count and a similar per-path footprint).  A work unit is a
+// run of consecutive tiles of one contract; warps take units from the
+// group's counter in the order of the unit array (costliest first) and run
+// their tiles exactly as the single-contract kernel does, finishing each
+// tile into that contract's own reduction scratch.
+struct BatchUnit {
+  uint32_t item;     // index into the per-contract argument array
+  uint32_t n_tiles;  // tiles in the unit (>= 1)
+  uint64_t tile0;    // first tile
+};
+static_assert(sizeof(BatchUnit) == 16, "BatchUnit is 16 bytes");
+struct BatchArgs {
+  const PriceArgs *items;       // per-contract arguments (device)
+  const BatchUnit *units;       // this group's units (device)
+  uint32_t n_units;
+  uint32_t slot_bytes;          // per-warp slot: arguments + program + pool
+  unsigned long long *counter;  // next unit; zero before the launch
+};
+// Per-warp slot in shared memory (a contract's arguments, then its program
+// and constant pool), ahead of the per-thread regions.
+constexpr size_t kBatchArgsBytes = (sizeof(PriceArgs) + 15) & ~size_t(15);
+inline size_t batch_slot_bytes(size_t n_insn, size_t n_pool_padded) {
+  return kBatchArgsBytes + n_insn * 16 + n_pool_padded * 4;
+}
+inline size_t batch_smem_bytes(size_t slot_bytes, int words, int block) {
+  return slot_bytes * size_t(block / 32) + size_t(words) * size_t(block) * sizeof(float) * kPathsPerLane;
+}
+// Sets the kernel's dynamic shared-memory limit and returns its resident
+// blocks per SM (0 if it cannot run).  Call before any stream capture.
+int batch_blocks_per_sm(int d, int block, size_t smem_bytes);
+cudaError_t launch_batch(const BatchArgs &b, int d, int grid, int block, size_t smem_bytes,
+                         cudaStream_t s);
 // Device address and size of the fixed scratch array used by
 // pc_price_noalloc on the current device (looked up once per device).
 cudaError_t noalloc_scratch(void **ptr, size_t *bytes);

@@ -361,6 +361,74 @@ __global__ void __launch_bounds__(kBlock) price_kernel(const PriceArgs a) {
   }
 }
 
+// Portfolio kernel.  Warps take work units (a contract and a run of its
+// tiles) from the group's counter in the order of the unit array.  When a
+// warp's unit belongs to another contract than its previous one, the warp
+// copies that contract's arguments, program and constant pool into its own
+// slot of shared memory.  The tiles run as in price_kernel and finish into
+// the contract's own reduction scratch, so each contract's sums are those of
+// a single-contract launch.
+template <int D>
+__global__ void __launch_bounds__(kBlock) batch_kernel(const BatchArgs b) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *slot = smem + (b.slot_bytes / 4) * warp;
+  float2 *R = reinterpret_cast<float2 *>(smem + (b.slot_bytes / 4) * (blockDim.x >> 5)) + threadIdx.x;
+  const PriceArgs &a = *reinterpret_cast<const PriceArgs *>(slot);
+  const uint4 *P = reinterpret_cast<const uint4 *>(slot + kBatchArgsBytes / 4);
+  float Bm[D * D], S0[D];
+  Rng2 g;
+  uint32_t cur = 0xffffffffu;
+  for (;;) {
+    unsigned long long u = 0;
+    if (lane == 0) u = atomicAdd(b.counter, 1ull);
+    u = __shfl_sync(kFull, u, 0);
+    if (u >= b.n_units) break;
+    const BatchUnit U = b.units[u];
+    if (U.item != cur) {
+      __syncwarp();
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(b.items + U.item);
+      for (int i = lane; i < int(sizeof(PriceArgs) / 4); i += 32) slot[i] = __ldg(src + i);
+      __syncwarp();
+      const int n_words = a.n_insn * 4 + a.n_pool;
+      const uint32_t *code = reinterpret_cast<const uint32_t *>(a.prog);
+      for (int i = lane; i < n_words; i += 32) slot[kBatchArgsBytes / 4 + i] = __ldg(code + i);
+      __syncwarp();
+      cur = U.item;
+    }
+    const float *pool = reinterpret_cast<const float *>(P + a.n_insn);
+    load_model_regs<D>(a.m, Bm, S0);
+    g.stream = a.stream;
+    g.k0 = a.key0;
+    g.k1 = a.key1;
+    for (uint32_t k = 0; k < U.n_tiles; ++k) {
+      const uint64_t tile = U.tile0 + k;
+      const uint64_t i0 = tile * kTilePaths + lane, i1 = i0 + 32;
+      const bool live0 = i0 < a.n_paths, live1 = i1 < a.n_paths;
+      const uint64_t p0 = a.path_offset + i0, p1 = a.path_offset + i1;
+      g.plo[0] = uint32_t(p0);
+      g.phi[0] = uint32_t(p0 >> 32);
+      g.plo[1] = uint32_t(p1);
+      g.phi[1] = uint32_t(p1 >> 32);
+      const float2 x = eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0);
+      double tp[2] = {0.0, 0.0};
+      if (live0) {
+        const double xd = double(x.x);
+        tp[0] += xd;
+        tp[1] = fma(xd, xd, tp[1]);
+      }
+      if (live1) {
+        const double xd = double(x.y);
+        tp[0] += xd;
+        tp[1] = fma(xd, xd, tp[1]);
+      }
+      tp[0] = warp_sum(tp[0]);
+      tp[1] = warp_sum(tp[1]);
+      finish_tile<2>(a, tile, tp, lane);
+    }
+  }
+}
+
 __global__ void debug_philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                                     size_t n) {
   const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -451,6 +519,37 @@ int price_blocks_per_sm(int d, int block, size_t smem, bool greeks) {
     default: return 0;
   }
   return e == cudaSuccess ? nb : 0;
+}
+
+int batch_blocks_per_sm(int d, int block, size_t smem) {
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define OCC(DD)                                                                     \
+  do {                                                                              \
+    e = set_smem(batch_kernel<DD>, smem);                                           \
+    if (e == cudaSuccess)                                                           \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<DD>, block, smem); \
+  } while (0)
+  switch (d) {
+    case 1: OCC(1); break;
+    case 2: OCC(2); break;
+    case 3: OCC(3); break;
+    case 4: OCC(4); break;
+    default: return 0;
+  }
+#undef OCC
+  return e == cudaSuccess ? nb : 0;
+}
+
+cudaError_t launch_batch(const BatchArgs &b, int d, int grid, int block, size_t smem, cudaStream_t s) {
+  switch (d) {
+    case 1: batch_kernel<1><<<grid, block, smem, s>>>(b); break;
+    case 2: batch_kernel<2><<<grid, block, smem, s>>>(b); break;
+    case 3: batch_kernel<3><<<grid, block, smem, s>>>(b); break;
+    case 4: batch_kernel<4><<<grid, block, smem, s>>>(b); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 int max_dynamic_smem() {

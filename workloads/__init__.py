@@ -225,3 +225,108 @@ ALL = {
     "worst_of_autocall_3u_5d": worst_of_autocall,
     "daily_barrier_3u_365d": daily_barrier,
 }
+
+
+# ---------------------------------------------------------------------------
+# Portfolio of templated contracts (batched pricing)
+# ---------------------------------------------------------------------------
+
+
+def basket_text(d: int, t: str) -> str:
+    """(S_0 + ... + S_{d-1}) / d at time t (every S0 = 1), left-nested."""
+    out = f"(model 0 {t})"
+    for i in range(1, d):
+        out = f"(add {out} (model {i} {t}))"
+    return f"(div {out} {_fmt(float(d))})"
+
+
+def basket_call_text(d: int, K: float) -> str:
+    """translate($0, scale(max(basket - K, 0), transfer))."""
+    T = "(tplus 0 $0)"
+    return (f"(mult (max (sub {basket_text(d, f'(tplus {T} 0)')} {_fmt(K)}) 0.0) "
+            f"(payoff {T} {P_PAY} {P_RECV}))")
+
+
+def basket_digital_text(d: int, K: float) -> str:
+    """translate($0, scale(cond(basket > K, 1, 0), transfer))."""
+    T = "(tplus 0 $0)"
+    return (f"(mult (if (lt {_fmt(K)} {basket_text(d, f'(tplus {T} 0)')}) 1.0 0.0) "
+            f"(payoff {T} {P_PAY} {P_RECV}))")
+
+
+def call_spread_text(d: int, K1: float, K2: float) -> str:
+    """translate($0, scale(max(basket - K1, 0) - max(basket - K2, 0), transfer))."""
+    T = "(tplus 0 $0)"
+    b = basket_text(d, f"(tplus {T} 0)")
+    return (f"(mult (sub (max (sub {b} {_fmt(K1)}) 0.0) (max (sub {b} {_fmt(K2)}) 0.0)) "
+            f"(payoff {T} {P_PAY} {P_RECV}))")
+
+
+def asian_text(n: int, S0: float, K: float) -> str:
+    """translate($0, scale(max((sum_{j<n} obs(0,-j)) / n / S0 - K, 0), transfer)):
+    average-rate call on the n grid dates ending at maturity $0 = n.  The
+    sum runs in date order (oldest fixing first), so each fixing is read as
+    it is simulated."""
+    T = "(tplus 0 $0)"
+    terms = [f"(model 0 (tplus {T} {-j}))" for j in reversed(range(n))]
+    s = terms[0]
+    for x in terms[1:]:
+        s = f"(add {s} {x})"
+    return (f"(mult (max (sub (div (div {s} {_fmt(float(n))}) {_fmt(S0)}) {_fmt(K)}) 0.0) "
+            f"(payoff {T} {P_PAY} {P_RECV}))")
+
+
+@dataclass
+class PortfolioItem:
+    template: str
+    market: MarketSpec
+    il_text: str
+    tparams: List[int]
+    n_paths: int
+    notional: float
+
+
+PORTFOLIO_TEMPLATES = ("european", "digital", "call_spread", "autocall", "daily_barrier", "asian")
+
+
+def portfolio(n_contracts: int = 1024, seed: int = PARAM_SEED + 4) -> List[PortfolioItem]:
+    """Templated contracts on one 4-asset market (S0 = 1, sigma as the
+    autocall's draws plus one more, pairwise corr 0.5, r = 3 %): each
+    contract draws a template, d ~ U{1..4} underlyings (the first d assets;
+    the European, digital and call-spread pay on their equally weighted
+    basket, the average-rate call on the first asset),
+    a maturity ~ U(0.5, 10) years, a date count ~ log-U{1..365} (evenly
+    spaced to maturity), a strike level ~ U(0.8, 1.2) and a path budget
+    ~ lognormal clipped to [2^12, 2^18]."""
+    g = np.random.Generator(np.random.MT19937(seed))
+    sig4 = draw_sigmas(4)
+    items = []
+    for c in range(n_contracts):
+        tmpl = PORTFOLIO_TEMPLATES[int(g.integers(len(PORTFOLIO_TEMPLATES)))]
+        d = int(g.integers(1, 5))
+        years = float(g.uniform(0.5, 10.0))
+        n = int(np.clip(np.round(np.exp(g.uniform(0.0, np.log(365.0)))), 1, 365))
+        if tmpl == "asian":
+            n = min(n, 200)
+        last = max(int(round(years * 365)), n)
+        days = sorted({max(1, int(round(last * (k + 1) / n))) for k in range(n)})
+        n = len(days)
+        strike = float(g.uniform(0.8, 1.2))
+        budget = int(np.clip(np.exp(g.normal(np.log(2.0 ** 15), 1.0)), 2 ** 12, 2 ** 18))
+        S0 = [1.0] * d
+        mk = MarketSpec(S0, sig4[:d], const_corr(d, 0.5), 0.03, days)
+        if tmpl == "european":
+            text, tp = basket_call_text(d, strike), [n]
+        elif tmpl == "digital":
+            text, tp = basket_digital_text(d, strike), [n]
+        elif tmpl == "call_spread":
+            text, tp = call_spread_text(d, strike, strike + 0.2), [n]
+        elif tmpl == "autocall":
+            text, tp = autocall_text(S0, n_dates=min(n, 12)), []
+            mk = MarketSpec(S0, sig4[:d], const_corr(d, 0.5), 0.03, days[:min(n, 12)])
+        elif tmpl == "daily_barrier":
+            text, tp = barrier_ladder_text(S0, barrier=0.6 + 0.1 * strike, n_spreads=1 + c % 13), [n]
+        else:
+            text, tp = asian_text(n, 1.0, strike), [n]
+        items.append(PortfolioItem(tmpl, mk, text, tp, budget, 1.0))
+    return items
