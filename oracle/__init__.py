@@ -25,6 +25,12 @@ Annenkov & Elsman, "Certified Compilation of Financial Contracts" (PPDP'18):
 * ``pathwise`` -- per-path derivatives of the payoff in S0_l and sigma_l
                  (central differences of the oracle's own FP64 map on common
                  normals).
+* ``mlp``     -- the multilayer perceptron of the learned control variate:
+                 softplus layers, weighted squared loss, backpropagation,
+                 Adam (an extension of the method, not in the paper).
+* ``cv``      -- the delta-hedge martingale control variate for the worst-of
+                 autocallable template, its states, hedge-ratio tables and
+                 network features (an extension of the method).
 
 Every floating-point computation is FP64.  All functions cite the section,
 equation or figure of the paper they follow; readings of ambiguous passages
