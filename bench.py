@@ -38,7 +38,8 @@ import workloads as W  # noqa: E402
 METRIC = "path·date evals/sec & contracts priced/sec at 1e-4 rel. std-err vs plain MC"
 UNIT = "path·date/s"
 TARGET_REL_SE = 1e-4
-KERNEL_SRC = os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", "pc_kernels.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
+               for f in ("pc_kernels.cu", "pc_eval.cuh", "pc_device.cuh", "pc_internal.h")]
 PORTFOLIO = "portfolio_1024"
 PORTFOLIO_SEED = 0x5EED0004
 
@@ -131,8 +132,11 @@ def profile_traffic(workload: str):
     try:
         with open(path) as f:
             p = json.load(f)
-        with open(KERNEL_SRC, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        h = hashlib.sha256()
+        for src in KERNEL_SRCS:
+            with open(src, "rb") as f:
+                h.update(f.read())
+        sha = h.hexdigest()
         if p.get("kernel_sha256") == sha:
             return p.get("dram_bytes_per_launch"), p.get("n_paths")
     except (OSError, ValueError):
