@@ -381,6 +381,59 @@ pc_status pc_greeks(const pc_model *model, const pc_contract *contract,
                     double *out_delta, double *out_vega, double *out_se);
 
 /* ------------------------------------------------------------------------ */
+/* Learned control variate: network                                          */
+/* ------------------------------------------------------------------------ */
+/* Not in the paper (an extension of its Monte Carlo valuation).  A
+ * multilayer perceptron widths[0] -> ... -> widths[L]: softplus hidden
+ * layers, linear output; BF16 weights and activations, FP32 accumulation
+ * on the tensor cores, FP32 master weights updated by Adam.  Trained on the
+ * engine's own prices and sensitivities to give hedge ratios for the
+ * control variate below.  Samples are rows: x [n, widths[0]],
+ * y and targets [n, widths[L]], FP32.  Parameters, "unpadded layout": for
+ * each layer l, W_l [widths[l+1], widths[l]] row-major, then b_l
+ * [widths[l+1]].  Results are deterministic (fixed-order reductions). */
+typedef struct pc_mlp pc_mlp;
+
+typedef struct pc_mlp_info {
+  int32_t n_layers;          /* L                                            */
+  int32_t widths[9];         /* widths[0..L]                                 */
+  uint64_t n_params;         /* floats in the unpadded layout                */
+  uint64_t max_batch;        /* rows per forward / gradient call             */
+  uint64_t steps;            /* Adam steps taken                             */
+} pc_mlp_info;
+
+/* widths: n_widths = L + 1 (2..9) entries; widths[0] and widths[L] in
+ * 1..64, hidden widths multiples of 64 up to 1024.  max_batch: rows per
+ * call (>= 1).  Weights start uniform in +-1/sqrt(fan-in) from `seed`.
+ * Errors: PC_EINVAL, PC_ENOMEM, PC_ECUDA. */
+pc_status pc_mlp_create(pc_ctx *ctx, const int32_t *widths, int32_t n_widths, uint64_t max_batch,
+                        uint64_t seed, pc_mlp **out);
+pc_status pc_mlp_destroy(pc_mlp *net);
+pc_status pc_mlp_query(const pc_mlp *net, pc_mlp_info *info);
+/* Host arrays of n = info.n_params floats (unpadded layout).  set resets
+ * the Adam moments and step count. */
+pc_status pc_mlp_set_params(pc_mlp *net, const float *params, size_t n);
+pc_status pc_mlp_get_params(const pc_mlp *net, float *params, size_t n);
+/* d_y [n, widths[L]] = network(d_x [n, widths[0]]), device pointers, any n
+ * (processed in max_batch chunks).  Asynchronous on the context's stream. */
+pc_status pc_mlp_forward(pc_mlp *net, const float *d_x, size_t n, float *d_y);
+/* Loss (1/n) sum_b sum_j w_j (y_bj - t_bj)^2 of the n <= max_batch samples
+ * (device d_x, d_t; host w [widths[L]]) and its gradient with respect to
+ * every parameter, d_grads (device, unpadded layout, nullable).  No update.
+ * Blocks until done; *out_loss (host). */
+pc_status pc_mlp_gradients(pc_mlp *net, const float *d_x, const float *d_t, const float *w,
+                           size_t n, float *d_grads, double *out_loss);
+/* `steps` Adam steps (lr; b1 0.9, b2 0.999, eps 1e-8) on minibatches of
+ * `batch` rows (1..max_batch) drawn with replacement from the n_data rows of
+ * d_x / d_t by Philox4x32-10 under `seed` and the step number.  One step is
+ * captured once into a CUDA graph and replayed.  Blocks until done;
+ * *out_loss = loss of the last minibatch (before its update).
+ * Errors: PC_EINVAL, PC_ECUDA, PC_ETIMEOUT. */
+pc_status pc_mlp_train(pc_mlp *net, const float *d_x, const float *d_t, size_t n_data,
+                       const float *w, size_t batch, int32_t steps, float lr, uint64_t seed,
+                       double *out_loss);
+
+/* ------------------------------------------------------------------------ */
 /* Parity probes (same device functions as the pricing kernel)               */
 /* ------------------------------------------------------------------------ */
 

@@ -60,6 +60,11 @@ class BatchInfo(C.Structure):
                 ("paths_per_thread", C.c_double), ("last_ms", C.c_double)]
 
 
+class MlpInfo(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("widths", C.c_int32 * 9), ("n_params", C.c_uint64),
+                ("max_batch", C.c_uint64), ("steps", C.c_uint64)]
+
+
 class ProgramInfo(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_insn", C.c_int32), ("max_stack", C.c_int32),
                 ("result_is_real", C.c_int32), ("n_loops", C.c_int32),
@@ -93,6 +98,14 @@ _SIGS = {
     "pc_batch_results": [VP, PD, PD, PD],
     "pc_batch_query": [VP, C.POINTER(BatchInfo)],
     "pc_batch_destroy": [VP],
+    "pc_mlp_create": [VP, C.POINTER(C.c_int32), C.c_int32, U64, U64, C.POINTER(VP)],
+    "pc_mlp_destroy": [VP],
+    "pc_mlp_query": [VP, C.POINTER(MlpInfo)],
+    "pc_mlp_set_params": [VP, C.POINTER(C.c_float), SZ],
+    "pc_mlp_get_params": [VP, C.POINTER(C.c_float), SZ],
+    "pc_mlp_forward": [VP, VP, SZ, VP],
+    "pc_mlp_gradients": [VP, VP, VP, C.POINTER(C.c_float), SZ, VP, PD],
+    "pc_mlp_train": [VP, VP, VP, SZ, C.POINTER(C.c_float), SZ, C.c_int32, C.c_float, U64, PD],
     "pc_greeks": [VP, VP, U64, U64, PD, PD, PD, PD],
     "pc_debug_philox": [VP, VP, U32, U32, VP, SZ],
     "pc_debug_paths": [VP, U64, U64, U64, U32, VP],
@@ -309,6 +322,55 @@ def pc_batch_query(plan: int) -> BatchInfo:
 
 def pc_batch_destroy(plan: int) -> None:
     _check(lib().pc_batch_destroy(VP(plan)))
+
+
+def pc_mlp_create(ctx: int, widths: Sequence[int], max_batch: int, seed: int = 1) -> int:
+    w = _arr(widths, np.int32)
+    h = VP()
+    _check(lib().pc_mlp_create(VP(ctx), _ptr(w, C.c_int32), w.size, int(max_batch), int(seed), C.byref(h)))
+    return h.value
+
+
+def pc_mlp_destroy(net: int) -> None:
+    _check(lib().pc_mlp_destroy(VP(net)))
+
+
+def pc_mlp_query(net: int) -> MlpInfo:
+    info = MlpInfo()
+    _check(lib().pc_mlp_query(VP(net), C.byref(info)))
+    return info
+
+
+def pc_mlp_set_params(net: int, params) -> None:
+    p = _arr(params, np.float32)
+    _check(lib().pc_mlp_set_params(VP(net), _ptr(p, C.c_float), p.size))
+
+
+def pc_mlp_get_params(net: int) -> np.ndarray:
+    p = np.zeros(pc_mlp_query(net).n_params, np.float32)
+    _check(lib().pc_mlp_get_params(VP(net), _ptr(p, C.c_float), p.size))
+    return p
+
+
+def pc_mlp_forward(net: int, d_x: int, n: int, d_y: int) -> None:
+    _check(lib().pc_mlp_forward(VP(net), VP(d_x), n, VP(d_y)))
+
+
+def pc_mlp_gradients(net: int, d_x: int, d_t: int, w, n: int, d_grads: Optional[int] = None) -> float:
+    wv = _arr(w, np.float32)
+    loss = DBL()
+    _check(lib().pc_mlp_gradients(VP(net), VP(d_x), VP(d_t), _ptr(wv, C.c_float), n,
+                                  VP(d_grads) if d_grads else None, C.byref(loss)))
+    return loss.value
+
+
+def pc_mlp_train(net: int, d_x: int, d_t: int, n_data: int, w, batch: int, steps: int, lr: float,
+                 seed: int) -> float:
+    wv = _arr(w, np.float32)
+    loss = DBL()
+    _check(lib().pc_mlp_train(VP(net), VP(d_x), VP(d_t), n_data, _ptr(wv, C.c_float), batch, steps,
+                              float(lr), int(seed), C.byref(loss)))
+    return loss.value
 
 
 def pc_greeks(model: int, contract: int, n_paths: int, seed: int, d: int):

@@ -1,0 +1,271 @@
+// pc_cv.cu -- the delta-hedge control variate on the pricing paths, and the
+// kernels that turn the network into its hedge-ratio tables.
+//
+// For the worst-of autocallable template each path's payoff X comes from the
+// interpreter exactly as in price_kernel; the kernel then walks the dates
+// kept in the window and accumulates the discounted hedge gains
+//   M = sum_{k<n} alive_k sum_i Delta_i(k) (D_{k+1} S_i(t_{k+1}) - D_k S_i(t_k))
+// with Delta from a table over ln S (multilinear interpolation) per date and
+// knock-in state.  Every factor of a term is known at t_k, so E[M] = 0 and
+// Y = X - M estimates the same price; the tile sums carry Y, Y^2, X, X^2.
+// A hedge period whose end date the warp never generated (every lane's
+// program stopped before it) is skipped: that decision depends only on
+// information at t_k of this and of independent paths, so the terms kept are
+// still martingale increments.
+#include <cstdint>
+
+#include "pc_device.cuh"
+#include "pc_eval.cuh"
+#include "pc_cv.h"
+
+namespace pc {
+namespace {
+
+// Multilinear interpolation of the d hedge ratios at y = ln S.
+template <int D>
+__device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, const float (&y)[D],
+                                            float (&delta)[D]) {
+  const float *tab = c.tables + (size_t(k - 1) * 2 + ki) * size_t(c.nodes) * D;
+  int a[D];
+  float f[D];
+  const int G = c.grid;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    float u = (y[i] - c.lo[k - 1][i]) / c.h[k - 1][i];
+    u = fminf(fmaxf(u, 0.f), float(G - 1));
+    int ai = int(floorf(u));
+    ai = ai < G - 2 ? ai : G - 2;
+    a[i] = ai;
+    f[i] = u - float(ai);
+    delta[i] = 0.f;
+  }
+#pragma unroll
+  for (int corner = 0; corner < (1 << D); ++corner) {
+    float wgt = 1.f;
+    int node = 0;
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      const int bit = (corner >> (D - 1 - ax)) & 1;
+      wgt *= bit ? f[ax] : 1.f - f[ax];
+      node = node * G + a[ax] + bit;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) delta[i] = fmaf(wgt, __ldg(tab + size_t(node) * D + i), delta[i]);
+  }
+}
+
+// Hedge gains of one path: S at ordinal o is s(o, i) (o = 0: spot).
+template <int D, typename SFn>
+__device__ float hedge_gain(const CvArgs &c, const ModelDev &m, int frontier, SFn s) {
+  float M = 0.f;
+  bool alive = true;
+  int ki = 0;
+  for (int k = 0; k < c.n; ++k) {
+    if (k >= 1) {
+      float worst = s(k, 0) / c.ref[0];
+#pragma unroll
+      for (int i = 1; i < D; ++i) worst = fminf(worst, s(k, i) / c.ref[i]);
+      ki |= worst <= c.ki_level ? 1 : 0;
+      alive = alive && !(worst >= c.call_level);
+    }
+    if (!alive || k + 1 > frontier) break;
+    float delta[D];
+    if (k == 0) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) delta[i] = c.delta0[i];
+    } else {
+      float y[D];
+#pragma unroll
+      for (int i = 0; i < D; ++i) y[i] = logf(s(k, i));
+      table_delta<D>(c, k, ki, y, delta);
+    }
+    const float d0 = __ldg(m.disc + k + m.n_hist), d1 = __ldg(m.disc + k + 1 + m.n_hist);
+#pragma unroll
+    for (int i = 0; i < D; ++i) M = fmaf(delta[i], d1 * s(k + 1, i) - d0 * s(k, i), M);
+  }
+  return M;
+}
+
+template <int D, bool WRITE>
+__global__ void __launch_bounds__(kBlock) cv_kernel(const PriceArgs a, const CvArgs c) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int last_block;
+  uint4 *P = reinterpret_cast<uint4 *>(smem);
+  const int prog_words = a.n_insn * 4 + a.n_pool;
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(a.prog);
+  for (int i = threadIdx.x; i < prog_words; i += blockDim.x) smem[i] = src[i];
+  __syncthreads();
+  const float *pool = reinterpret_cast<const float *>(smem + a.n_insn * 4);
+  float2 *R = reinterpret_cast<float2 *>(smem + prog_words) + threadIdx.x;
+  float Bm[D * D], S0[D];
+  load_model_regs<D>(a.m, Bm, S0);
+  const int lane = threadIdx.x & 31;
+  unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
+  const Layout &lay = a.lay;
+  Rng2 g;
+  g.stream = a.stream;
+  g.k0 = a.key0;
+  g.k1 = a.key1;
+  for (;;) {
+    unsigned long long tile = 0;
+    if (lane == 0) tile = atomicAdd(ctr, 1ull);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= a.n_tiles) break;
+    const uint64_t i0 = tile * kTilePaths + lane, i1 = i0 + 32;
+    const bool live0 = i0 < a.n_paths, live1 = i1 < a.n_paths;
+    const uint64_t p0 = a.path_offset + i0, p1 = a.path_offset + i1;
+    g.plo[0] = uint32_t(p0);
+    g.phi[0] = uint32_t(p0 >> 32);
+    g.plo[1] = uint32_t(p1);
+    g.phi[1] = uint32_t(p1 >> 32);
+    int frontier = 0;
+    const float2 x = eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0, &frontier);
+    float Mv[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      auto s = [&](int o, int i) -> float {
+        if (o == 0) return S0[i];
+        const float2 v = SL(lay.off_win + (o & (lay.win - 1)) * D + i);
+        return q ? v.y : v.x;
+      };
+      Mv[q] = hedge_gain<D>(c, a.m, frontier, s);
+    }
+    double tp[4] = {0.0, 0.0, 0.0, 0.0};
+    const float xs[2] = {x.x, x.y};
+    const bool live[2] = {live0, live1};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (!live[q]) continue;
+      const double xd = double(xs[q]), yd = double(xs[q] - Mv[q]);
+      tp[0] += yd;
+      tp[1] = fma(yd, yd, tp[1]);
+      tp[2] += xd;
+      tp[3] = fma(xd, xd, tp[3]);
+      if (WRITE) {
+        const uint64_t i = q ? i1 : i0;
+        a.out_paths[2 * i] = xs[q];
+        a.out_paths[2 * i + 1] = Mv[q];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) tp[v] = warp_sum(tp[v]);
+    finish_tile<4>(a, tile, tp, lane);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last_block = atomicAdd(ctr + 1, 1ull) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last_block && threadIdx.x == 0) {
+    ctr[0] = 0;
+    ctr[1] = 0;
+  }
+}
+
+// Network inputs of every table node (row ((k-1) * 2 + ki) * G^d + node),
+// then one row for the spot at t_0 (k = 0, no knock-in).
+__global__ void cv_features_kernel(const CvArgs c, CvFeatureArgs fa, float *X, size_t rows) {
+  const size_t r = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
+  if (r >= rows) return;
+  float y[3] = {0.f, 0.f, 0.f};
+  int k = 0, ki = 0;
+  if (r + 1 < rows) {
+    size_t node = r % size_t(c.nodes);
+    const size_t grp = r / size_t(c.nodes);
+    k = int(grp / 2) + 1;
+    ki = int(grp % 2);
+    for (int ax = c.d - 1; ax >= 0; --ax) {
+      const int a = int(node % size_t(c.grid));
+      node /= size_t(c.grid);
+      y[ax] = c.lo[k - 1][ax] + float(a) * c.h[k - 1][ax];
+    }
+  } else {
+    for (int i = 0; i < c.d; ++i) y[i] = fa.ln_spot[i];
+  }
+  float *f = X + r * kCvFeatures;
+  for (int i = 0; i < 3; ++i) f[i] = i < c.d ? y[i] - logf(c.ref[i]) : 0.f;
+  for (int i = 0; i < 3; ++i) f[3 + i] = i < c.d ? fa.sigma[i] : 0.f;
+  f[6] = fa.rho;
+  f[7] = fa.r;
+  f[8] = fa.tau[k + 1] - fa.tau[k];
+  f[9] = float(c.n - k) / 5.f;
+  f[10] = float(k) / 5.f;
+  f[11] = float(ki);
+  f[12] = c.coupon;
+  f[13] = c.call_level;
+  f[14] = c.ki_level;
+  f[15] = 1.f;
+}
+
+// Table entries from the network outputs (value, then one hedge ratio per
+// underlying) of the rows above; the last row's ratios are delta0.
+__global__ void cv_scatter_kernel(const float *Y, int out_w, size_t rows, int d, float *tables,
+                                  float *delta0) {
+  const size_t r = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
+  if (r >= rows) return;
+  for (int i = 0; i < d; ++i) {
+    const float v = Y[r * out_w + 1 + i];
+    if (r + 1 < rows) tables[r * d + i] = v;
+    else delta0[i] = v;
+  }
+}
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t smem) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+}  // namespace
+
+cudaError_t launch_cv(const PriceArgs &a, const CvArgs &c, int grid, int block, size_t smem, cudaStream_t s) {
+  const bool w = a.out_paths != nullptr;
+#define CVL(DD, WW)                                  \
+  do {                                               \
+    auto k = cv_kernel<DD, WW>;                      \
+    cudaError_t e = set_smem(k, smem);               \
+    if (e != cudaSuccess) return e;                  \
+    k<<<grid, block, smem, s>>>(a, c);               \
+    return cudaGetLastError();                       \
+  } while (0)
+  switch (a.m.d) {
+    case 1: if (w) CVL(1, true); else CVL(1, false);
+    case 2: if (w) CVL(2, true); else CVL(2, false);
+    case 3: if (w) CVL(3, true); else CVL(3, false);
+    default: return cudaErrorInvalidValue;
+  }
+#undef CVL
+}
+
+int cv_blocks_per_sm(int d, int block, size_t smem) {
+  int nb = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define OCC(DD)                                                                        \
+  do {                                                                                 \
+    e = set_smem(cv_kernel<DD, false>, smem);                                          \
+    if (e == cudaSuccess)                                                              \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cv_kernel<DD, false>, block, smem); \
+  } while (0)
+  switch (d) {
+    case 1: OCC(1); break;
+    case 2: OCC(2); break;
+    case 3: OCC(3); break;
+    default: return 0;
+  }
+#undef OCC
+  return e == cudaSuccess ? nb : 0;
+}
+
+cudaError_t launch_cv_features(const CvArgs &c, const CvFeatureArgs &fa, float *X, size_t rows,
+                               cudaStream_t s) {
+  cv_features_kernel<<<unsigned((rows + 127) / 128), 128, 0, s>>>(c, fa, X, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cv_scatter(const float *Y, int out_w, size_t rows, int d, float *tables, float *delta0,
+                              cudaStream_t s) {
+  cv_scatter_kernel<<<unsigned((rows + 127) / 128), 128, 0, s>>>(Y, out_w, rows, d, tables, delta0);
+  return cudaGetLastError();
+}
+
+}  // namespace pc

@@ -1,0 +1,41 @@
+// pc_cv.h -- device arguments of the control-variate kernels (pc_cv.cu).
+// Private to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "pc_internal.h"
+
+namespace pc {
+
+constexpr int kCvMaxDates = 32;   // observation dates of the template
+constexpr int kCvMaxD = 3;        // underlyings
+constexpr int kCvFeatures = 16;   // network inputs
+constexpr int kCvOutputs = 5;     // network outputs: value, up to 4 hedge ratios
+
+struct CvArgs {
+  const float *tables;            // [(n-1) * 2][nodes][d]
+  int32_t d, n, grid, nodes;      // nodes = grid^d
+  float ref[kCvMaxD];
+  float call_level, ki_level, coupon;
+  float lo[kCvMaxDates][kCvMaxD], h[kCvMaxDates][kCvMaxD];  // row k-1: date k
+  float delta0[kCvMaxD];
+};
+
+struct CvFeatureArgs {
+  float ln_spot[kCvMaxD];
+  float sigma[kCvMaxD];
+  float rho, r;
+  float tau[kCvMaxDates + 1];     // year fractions of ordinals 0..n
+};
+
+cudaError_t launch_cv(const PriceArgs &a, const CvArgs &c, int grid, int block, size_t smem, cudaStream_t s);
+int cv_blocks_per_sm(int d, int block, size_t smem);
+cudaError_t launch_cv_features(const CvArgs &c, const CvFeatureArgs &fa, float *X, size_t rows,
+                               cudaStream_t s);
+cudaError_t launch_cv_scatter(const float *Y, int out_w, size_t rows, int d, float *tables, float *delta0,
+                              cudaStream_t s);
+
+}  // namespace pc

@@ -9,11 +9,12 @@ namespace {
 
 // The payoff expression of two paths per lane, all lanes of the warp in step.
 // The next instruction is fetched while the current one executes; jumps
-// fetch their target.
+// fetch their target.  `frontier` (optional) receives the last generated
+// date ordinal: the window holds the simulated dates up to it.
 template <int D>
 __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const PriceArgs &a,
                             const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],
-                            const float (&S0)[D]) {
+                            const float (&S0)[D], int *frontier = nullptr) {
   const ModelDev &m = a.m;
   const Layout &lay = a.lay;
   PathState<D> ps;
@@ -272,6 +273,7 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
         NEXT
       }
       default:
+        if (frontier) *frontier = ps.f;
         return tos;
     }
   }

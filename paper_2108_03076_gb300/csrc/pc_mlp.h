@@ -1,0 +1,69 @@
+// pc_mlp.h -- device-side pieces of the learned control variate's network
+// (pc_mlp.cu) and their host launchers.  Private to the library.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace pc {
+
+// GEMM epilogues of mlp_gemm.
+constexpr int kEpiBiasSoftplus = 0;  // Cb = bf16(softplus(acc + bias))
+constexpr int kEpiBias = 1;          // Cf = acc + bias (FP32)
+constexpr int kEpiDSoftplus = 2;     // Cb = bf16(acc * (1 - exp(-aux)))
+constexpr int kEpiPartial = 3;       // Cf[z] = acc over this k split (FP32)
+
+// C[M, N] = op(A) op(B) over K; M, N multiples of 64, K and k_split
+// multiples of 32; leading dimensions in elements, multiples of 8.
+struct GemmArgs {
+  const __nv_bfloat16 *A;
+  int lda;
+  const __nv_bfloat16 *B;
+  int ldb;
+  int M, N, K;
+  int k_split;                  // k range per blockIdx.z
+  const float *bias;            // [N] (bias epilogues)
+  const __nv_bfloat16 *aux;     // stored activations (kEpiDSoftplus)
+  int ldaux;
+  __nv_bfloat16 *Cb;            // BF16 output
+  float *Cf;                    // FP32 output (partials: [splits][M][ldc])
+  int ldc;
+};
+
+enum GemmKind { kGemmForward, kGemmDataGrad, kGemmWeightGrad };
+cudaError_t launch_gemm(GemmKind kind, int epi, const GemmArgs &g, int splits, cudaStream_t s);
+
+// x [n, fin] FP32 -> X [rows, ld] BF16, zero beyond n rows / fin columns.
+cudaError_t launch_to_bf16(const float *x, size_t n, int fin, __nv_bfloat16 *X, size_t rows, int ld,
+                           cudaStream_t s);
+// Gather a minibatch: rows idx = Philox(seed, step, b) mod n_data of
+// x [n_data, fin] and t [n_data, fout] into X (BF16, padded) and T (FP32).
+cudaError_t launch_gather(const float *x, const float *t, size_t n_data, int fin, int fout,
+                          const uint64_t *step, uint32_t seed_lo, uint32_t seed_hi, size_t batch,
+                          __nv_bfloat16 *X, int ldx, float *T, cudaStream_t s);
+// Weighted squared-error loss of Y [rows, ldy] (FP32) against T [n, fout]:
+// dY = (2 / n) w (Y - T) as BF16 [rows, ldd] (zero beyond n rows / fout
+// columns), per-block loss partials into part[blocks].
+cudaError_t launch_loss(const float *Y, int ldy, const float *T, const float *w, size_t n, int fout,
+                        size_t rows, __nv_bfloat16 *dY, int ldd, float *part, int blocks,
+                        cudaStream_t s);
+int loss_blocks(size_t rows);
+// out[i] = sum_s part[s * stride + i], s < splits, in order; i < count.
+cudaError_t launch_split_sum(const float *part, int splits, size_t stride, size_t count, float *out,
+                             cudaStream_t s);
+// Column sums of dZ [rows, ld] (BF16) for columns < cols into out (FP32),
+// in a fixed order (row chunks, then the chunk partials).
+cudaError_t launch_colsum(const __nv_bfloat16 *dZ, size_t rows, int ld, int cols, float *scratch,
+                          float *out, cudaStream_t s);
+// Adam over flat parameters p (FP32) with gradient g; moments m, v; bf16
+// copy pb; bias corrections for step *step + 1.
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, __nv_bfloat16 *pb, size_t n,
+                        uint64_t *step, float lr, float b1, float b2, float eps, cudaStream_t s);
+// Sum of part[0..blocks) into *loss (FP64) in order; then ++*step if step.
+cudaError_t launch_loss_total(const float *part, int blocks, double *loss, uint64_t *step, cudaStream_t s);
+// y [n, fout] FP32 from Y [rows, ldy].
+cudaError_t launch_unpad(const float *Y, int ldy, size_t n, int fout, float *y, cudaStream_t s);
+
+}  // namespace pc
