@@ -434,6 +434,63 @@ pc_status pc_mlp_train(pc_mlp *net, const float *d_x, const float *d_t, size_t n
                        double *out_loss);
 
 /* ------------------------------------------------------------------------ */
+/* Learned control variate: delta-hedge estimator                            */
+/* ------------------------------------------------------------------------ */
+/* For a worst-of autocallable contract (payments decided at the model's
+ * dates t_1..t_n by worst_k = min_i S_i(t_k) / ref_i: called at t_k < t_n
+ * when worst_k >= call_level, knock-in when some worst_k <= ki_level) the
+ * pricing kernel adds to each path's payoff X the discounted gains of a
+ * hedge held over [t_k, t_{k+1}] while the contract is alive,
+ *   M = sum_k alive_k sum_i Delta_i(k) (D_{k+1} S_i(t_{k+1}) - D_k S_i(t_k)),
+ * and reports Y = X - M.  The D S_i are martingales and every Delta_i(k)
+ * depends only on the path up to t_k, so E[M] = 0: Y is unbiased for any
+ * hedge ratios, and its variance is small when they are close to the
+ * contract's sensitivities.  Hedge ratios at t_k (k >= 1) come from a
+ * table over y = ln S per date and knock-in state, read by multilinear
+ * interpolation (per axis u = clamp((y - lo) / h, 0, G - 1),
+ * a = min(floor(u), G - 2), f = u - a), at t_0 from delta0.  Tables are
+ * filled by a trained network (pc_cv_tables) or by the caller.  Table
+ * layout (floats): [(k - 1) * 2 + ki][node][i], node = ((a_0 G + a_1) G + a_2)
+ * (axis 0 slowest), k = 1..n-1, ki = knock-in flag, i < d.
+ * Not in the paper (an extension of its Monte Carlo valuation). */
+#define PC_CV_MAX_DATES 32
+
+typedef struct pc_cv_desc {
+  int32_t d;                 /* underlyings, 1..3 (the model's d)            */
+  int32_t n;                 /* observation dates (the model's dates), 1..32 */
+  int32_t grid;              /* table nodes per axis G, 2..64                */
+  float ref[3];              /* worst = min_i S_i / ref_i                    */
+  float call_level, ki_level, coupon;
+  float lo[PC_CV_MAX_DATES][3];  /* table axes over ln S: row k - 1 = date k */
+  float h[PC_CV_MAX_DATES][3];
+  float delta0[3];           /* hedge ratios at t_0                          */
+} pc_cv_desc;
+
+/* Fill d, n, grid, lo and h from the model: axis i at date k is centred on
+ * ln S0_i + (r - sigma_i^2 / 2) tau_k with half-width width_sd sigma_i
+ * sqrt(tau_k).  The caller sets ref, the levels, coupon (and delta0 when it
+ * fills the tables itself).  Errors: PC_EINVAL, PC_ELIMIT (d > 3 or more
+ * than PC_CV_MAX_DATES dates). */
+pc_status pc_cv_grid(const pc_model *model, int32_t grid, float width_sd, pc_cv_desc *desc);
+/* Floats of the tables of desc: (n - 1) * 2 * grid^d * d. */
+pc_status pc_cv_table_size(const pc_cv_desc *desc, size_t *floats);
+/* Evaluate the network (16 inputs, outputs value and hedge ratios) at every
+ * table node and at the spot and write d_tables (device, cap_floats) and
+ * desc->delta0.  Network inputs of a state (date k, y = ln S, knock-in):
+ * y_i - ln ref_i (i < 3, 0 beyond d), sigma_i (i < 3), the correlation of
+ * underlyings 0 and 1 (0 if d = 1), r, tau_{k+1} - tau_k, (n - k) / 5,
+ * k / 5, knock-in, coupon, call_level, ki_level, 1.  Blocks until done.
+ * Errors: PC_EINVAL (widths other than 16 in / 5 out, cap too small). */
+pc_status pc_cv_tables(pc_mlp *net, const pc_model *model, pc_cv_desc *desc, float *d_tables,
+                       size_t cap_floats);
+/* Price with the control variate: out[0..3] (host) = price and standard
+ * error of Y, then of X on the same paths (pc_price's estimate with this
+ * seed).  d_tables: device tables laid out as above.  Blocks until done.
+ * Errors: as pc_price; PC_EINVAL for a desc that does not match the model. */
+pc_status pc_price_cv(const pc_model *model, const pc_contract *contract, const pc_cv_desc *desc,
+                      const float *d_tables, uint64_t n_paths, uint64_t seed, double *out);
+
+/* ------------------------------------------------------------------------ */
 /* Parity probes (same device functions as the pricing kernel)               */
 /* ------------------------------------------------------------------------ */
 
@@ -457,6 +514,12 @@ pc_status pc_debug_paths(const pc_model *model, uint64_t n_paths,
 pc_status pc_debug_greeks_paths(const pc_model *model, const pc_contract *contract,
                                 uint64_t n_paths, uint64_t path_offset, uint64_t seed,
                                 int32_t underlying, double *d_out, float *d_paths);
+
+/* Per path i < n_paths (paths 0.., Philox stream 0): d_xm[2i] = payoff X,
+ * d_xm[2i + 1] = hedge gain M of pc_price_cv (device floats).
+ * Asynchronous on the context's stream. */
+pc_status pc_debug_cv_paths(const pc_model *model, const pc_contract *contract, const pc_cv_desc *desc,
+                            const float *d_tables, uint64_t n_paths, uint64_t seed, float *d_xm);
 
 /* Host-only: the executable form pc_load_payoff would run for this program:
  * 4 words per instruction (opcode | A << 8, then three operand words), then

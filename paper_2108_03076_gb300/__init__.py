@@ -65,6 +65,16 @@ class MlpInfo(C.Structure):
                 ("max_batch", C.c_uint64), ("steps", C.c_uint64)]
 
 
+CV_MAX_DATES = 32
+
+
+class CvDesc(C.Structure):
+    _fields_ = [("d", C.c_int32), ("n", C.c_int32), ("grid", C.c_int32), ("ref", C.c_float * 3),
+                ("call_level", C.c_float), ("ki_level", C.c_float), ("coupon", C.c_float),
+                ("lo", (C.c_float * 3) * CV_MAX_DATES), ("h", (C.c_float * 3) * CV_MAX_DATES),
+                ("delta0", C.c_float * 3)]
+
+
 class ProgramInfo(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("n_insn", C.c_int32), ("max_stack", C.c_int32),
                 ("result_is_real", C.c_int32), ("n_loops", C.c_int32),
@@ -106,6 +116,11 @@ _SIGS = {
     "pc_mlp_forward": [VP, VP, SZ, VP],
     "pc_mlp_gradients": [VP, VP, VP, C.POINTER(C.c_float), SZ, VP, PD],
     "pc_mlp_train": [VP, VP, VP, SZ, C.POINTER(C.c_float), SZ, C.c_int32, C.c_float, U64, PD],
+    "pc_cv_grid": [VP, C.c_int32, C.c_float, C.POINTER(CvDesc)],
+    "pc_cv_table_size": [C.POINTER(CvDesc), C.POINTER(SZ)],
+    "pc_cv_tables": [VP, VP, C.POINTER(CvDesc), VP, SZ],
+    "pc_price_cv": [VP, VP, C.POINTER(CvDesc), VP, U64, U64, PD],
+    "pc_debug_cv_paths": [VP, VP, C.POINTER(CvDesc), VP, U64, U64, VP],
     "pc_greeks": [VP, VP, U64, U64, PD, PD, PD, PD],
     "pc_debug_philox": [VP, VP, U32, U32, VP, SZ],
     "pc_debug_paths": [VP, U64, U64, U64, U32, VP],
@@ -371,6 +386,42 @@ def pc_mlp_train(net: int, d_x: int, d_t: int, n_data: int, w, batch: int, steps
     _check(lib().pc_mlp_train(VP(net), VP(d_x), VP(d_t), n_data, _ptr(wv, C.c_float), batch, steps,
                               float(lr), int(seed), C.byref(loss)))
     return loss.value
+
+
+def pc_cv_grid(model: int, grid: int, width_sd: float, ref=(1.0, 1.0, 1.0), call_level: float = 1.0,
+               ki_level: float = 0.6, coupon: float = 0.05) -> CvDesc:
+    """A control-variate description with table axes from the model."""
+    desc = CvDesc()
+    _check(lib().pc_cv_grid(VP(model), int(grid), float(width_sd), C.byref(desc)))
+    for i in range(3):
+        desc.ref[i] = float(ref[i]) if i < len(ref) else 1.0
+    desc.call_level, desc.ki_level, desc.coupon = float(call_level), float(ki_level), float(coupon)
+    return desc
+
+
+def pc_cv_table_size(desc: CvDesc) -> int:
+    n = SZ(0)
+    _check(lib().pc_cv_table_size(C.byref(desc), C.byref(n)))
+    return n.value
+
+
+def pc_cv_tables(net: int, model: int, desc: CvDesc, d_tables: int, cap_floats: int) -> None:
+    _check(lib().pc_cv_tables(VP(net), VP(model), C.byref(desc), VP(d_tables), int(cap_floats)))
+
+
+def pc_price_cv(model: int, contract: int, desc: CvDesc, d_tables: int, n_paths: int, seed: int):
+    """(price, se) of the control-variate estimate, then (price, se) of the
+    plain estimate on the same paths."""
+    out = np.zeros(4)
+    _check(lib().pc_price_cv(VP(model), VP(contract), C.byref(desc), VP(d_tables), int(n_paths), int(seed),
+                             _ptr(out, C.c_double)))
+    return (out[0], out[1]), (out[2], out[3])
+
+
+def pc_debug_cv_paths(model: int, contract: int, desc: CvDesc, d_tables: int, n_paths: int, seed: int,
+                      d_xm: int) -> None:
+    _check(lib().pc_debug_cv_paths(VP(model), VP(contract), C.byref(desc), VP(d_tables), int(n_paths),
+                                   int(seed), VP(d_xm)))
 
 
 def pc_greeks(model: int, contract: int, n_paths: int, seed: int, d: int):

@@ -1,0 +1,219 @@
+// pc_cv_api.cpp -- pc_cv_* / pc_price_cv: table grids from the model, the
+// network evaluation at the table nodes, and the control-variate launch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pc_cv.h"
+#include "pc_handles.h"
+#include "pc_mlp.h"
+
+using namespace pc;
+
+extern "C" pc_status pc_mlp_query(const pc_mlp *net, pc_mlp_info *info);
+extern "C" pc_status pc_mlp_forward(pc_mlp *net, const float *d_x, size_t n, float *d_y);
+
+namespace {
+
+size_t nodes_of(const pc_cv_desc *c) {
+  size_t v = 1;
+  for (int i = 0; i < c->d; ++i) v *= size_t(c->grid);
+  return v;
+}
+
+pc_status check_desc(const pc_model *m, const pc_cv_desc *c) {
+  if (!m || !c) return fail(PC_EINVAL, "null argument");
+  if (c->d != m->H.d || c->n != m->H.n) return fail(PC_EINVAL, "control-variate description does not match the model");
+  if (c->d < 1 || c->d > kCvMaxD || c->n < 1 || c->n > kCvMaxDates)
+    return fail(PC_ELIMIT, "control variate: d must be 1..3 and n 1..32");
+  if (c->grid < 2 || c->grid > 64) return fail(PC_EINVAL, "grid must be 2..64");
+  for (int k = 0; k + 1 < c->n; ++k)
+    for (int i = 0; i < c->d; ++i)
+      if (!(c->h[k][i] > 0.f)) return fail(PC_EINVAL, "table spacing must be positive");
+  for (int i = 0; i < c->d; ++i)
+    if (!(c->ref[i] > 0.f)) return fail(PC_EINVAL, "reference levels must be positive");
+  return PC_OK;
+}
+
+CvArgs device_args(const pc_cv_desc *c, const float *tables) {
+  CvArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.tables = tables;
+  a.d = c->d;
+  a.n = c->n;
+  a.grid = c->grid;
+  a.nodes = int32_t(nodes_of(c));
+  for (int i = 0; i < 3; ++i) {
+    a.ref[i] = c->ref[i];
+    a.delta0[i] = c->delta0[i];
+  }
+  a.call_level = c->call_level;
+  a.ki_level = c->ki_level;
+  a.coupon = c->coupon;
+  std::memcpy(a.lo, c->lo, sizeof(a.lo));
+  std::memcpy(a.h, c->h, sizeof(a.h));
+  return a;
+}
+
+// The pricing launch with a window holding every date 1..n.
+pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c, const float *tables,
+                    uint64_t n_paths, uint64_t seed, double *d_out, float *d_xm) {
+  pc_status s = check_desc(m, c);
+  if (s != PC_OK) return s;
+  if (!tables && c->n > 1) return fail(PC_EINVAL, "null tables");
+  Launch L;
+  s = prepare(m, k, n_paths, 0, seed, 0, L);
+  if (s != PC_OK) return s;
+  pc_ctx *ctx = m->ctx;
+  Layout lay = L.args.lay;
+  int32_t win = lay.win;
+  while (win < c->n + 1) win *= 2;
+  lay.win = win;
+  lay.words = lay.off_win + win * c->d;
+  const size_t pool = (k->prog.pool.size() + 3) & ~size_t(3);
+  int block = 0, best = 0;
+  size_t smem = 0;
+  for (int b = kBlock; b >= 32; b /= 2) {
+    const size_t sm = price_smem_bytes(k->prog.code.size(), pool, lay.words, b);
+    if (sm + kStaticSmemReserve > size_t(ctx->max_smem)) continue;
+    const int warps = cv_blocks_per_sm(c->d, b, sm) * (b / 32);
+    if (warps > best) { best = warps; block = b; smem = sm; }
+  }
+  if (!block) return fail(PC_ELIMIT, "program + per-path state with the control variate exceed shared memory");
+  PriceArgs a = L.args;
+  a.lay = lay;
+  a.width = 4;
+  reduction_chunks(a.n_tiles, a.chunk_tiles, a.n_chunks);
+  s = ensure_partials(ctx, size_t(a.n_tiles) * 4);
+  if (s != PC_OK) return s;
+  a.tile_partials = ctx->d_partials;
+  a.control = ctx->d_control;
+  a.out = d_out;
+  a.out_paths = d_xm;
+  const uint64_t need = (a.n_tiles + block / 32 - 1) / (block / 32);
+  const int grid = int(std::min<uint64_t>(uint64_t(ctx->sm_count) * best / (block / 32), need));
+  CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CU(launch_cv(a, device_args(c, tables), grid, block, smem, ctx->stream), "control-variate kernel");
+  return PC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pc_status pc_cv_grid(const pc_model *m, int32_t grid, float width_sd, pc_cv_desc *c) {
+  if (!m || !c) return fail(PC_EINVAL, "null argument");
+  if (m->H.d > kCvMaxD || m->H.n > kCvMaxDates) return fail(PC_ELIMIT, "control variate: d <= 3, n <= 32");
+  if (grid < 2 || grid > 64 || !(width_sd > 0.f)) return fail(PC_EINVAL, "grid 2..64, width_sd > 0");
+  const ModelHost &H = m->H;
+  c->d = H.d;
+  c->n = H.n;
+  c->grid = grid;
+  for (int k = 1; k < H.n; ++k) {
+    const double tau = double(H.tau[k]);
+    for (int i = 0; i < 3; ++i) {
+      if (i < H.d) {
+        const double sg = H.sigma[i], mid = std::log(H.S0[i]) + (H.r - 0.5 * sg * sg) * tau;
+        const double half = double(width_sd) * sg * std::sqrt(tau);
+        c->lo[k - 1][i] = float(mid - half);
+        c->h[k - 1][i] = float(2.0 * half / (grid - 1));
+      } else {
+        c->lo[k - 1][i] = 0.f;
+        c->h[k - 1][i] = 1.f;
+      }
+    }
+  }
+  return PC_OK;
+}
+
+pc_status pc_cv_table_size(const pc_cv_desc *c, size_t *floats) {
+  if (!c || !floats) return fail(PC_EINVAL, "null argument");
+  if (c->d < 1 || c->d > 3 || c->n < 1 || c->grid < 2) return fail(PC_EINVAL, "bad description");
+  *floats = size_t(std::max(0, c->n - 1)) * 2 * nodes_of(c) * size_t(c->d);
+  return PC_OK;
+}
+
+pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_tables, size_t cap) {
+  pc_status s = check_desc(m, c);
+  if (s != PC_OK) return s;
+  pc_mlp_info info;
+  s = pc_mlp_query(net, &info);
+  if (s != PC_OK) return s;
+  if (info.widths[0] != kCvFeatures || info.widths[info.n_layers] != kCvOutputs)
+    return fail(PC_EINVAL, "network must map 16 inputs to 5 outputs");
+  size_t need = 0;
+  pc_cv_table_size(c, &need);
+  if (cap < need || (need && !d_tables)) return fail(PC_EINVAL, "table capacity too small");
+  const ModelHost &H = m->H;
+  CvFeatureArgs fa;
+  std::memset(&fa, 0, sizeof(fa));
+  for (int i = 0; i < H.d; ++i) {
+    fa.ln_spot[i] = float(std::log(H.S0[i]));
+    fa.sigma[i] = float(H.sigma[i]);
+  }
+  fa.rho = H.d > 1 ? float(H.corr[1]) : 0.f;
+  fa.r = float(H.r);
+  for (int o = 0; o <= H.n; ++o) fa.tau[o] = H.tau[o];
+  const size_t rows = need / size_t(c->d) + 1;
+  pc_ctx *ctx = m->ctx;
+  CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  float *buf = nullptr;
+  CU(cudaMalloc(&buf, rows * (kCvFeatures + kCvOutputs) * sizeof(float) + 64), "table scratch");
+  float *X = buf, *Y = buf + rows * kCvFeatures;
+  float *d0 = nullptr;
+  cudaError_t e = cudaMalloc(&d0, 4 * sizeof(float));
+  const CvArgs ca = device_args(c, nullptr);
+  if (e == cudaSuccess) e = launch_cv_features(ca, fa, X, rows, ctx->stream);
+  if (e != cudaSuccess) s = cuda_fail(e, "table features");
+  if (s == PC_OK) s = pc_mlp_forward(net, X, rows, Y);
+  if (s == PC_OK) {
+    e = launch_cv_scatter(Y, kCvOutputs, rows, c->d, d_tables, d0, ctx->stream);
+    if (e != cudaSuccess) s = cuda_fail(e, "table scatter");
+  }
+  float h0[4] = {0, 0, 0, 0};
+  if (s == PC_OK) {
+    e = cudaMemcpyAsync(h0, d0, 4 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) s = cuda_fail(e, "delta0 copy");
+  }
+  if (s == PC_OK) s = wait_stream(ctx);
+  cudaFree(buf);
+  if (d0) cudaFree(d0);
+  if (s != PC_OK) return s;
+  for (int i = 0; i < 3; ++i) c->delta0[i] = i < c->d ? h0[i] : 0.f;
+  return PC_OK;
+}
+
+pc_status pc_price_cv(const pc_model *m, const pc_contract *k, const pc_cv_desc *c, const float *d_tables,
+                      uint64_t n_paths, uint64_t seed, double *out) {
+  if (!out) return fail(PC_EINVAL, "null output");
+  if (n_paths < 2) return fail(PC_EINVAL, "n_paths must be >= 2 for a standard error");
+  if (!m) return fail(PC_EINVAL, "null model");
+  pc_ctx *ctx = m->ctx;
+  pc_status s = cv_launch(m, k, c, d_tables, n_paths, seed, ctx->d_gout, nullptr);
+  if (s != PC_OK) return s;
+  double h[5], st[5];
+  CU(cudaMemcpyAsync(h, ctx->d_gout, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "result copy");
+  CU(cudaMemcpyAsync(st, ctx->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "status copy");
+  s = wait_stream(ctx);
+  if (s != PC_OK) return s;
+  int32_t status;
+  std::memcpy(&status, &st[4], 4);
+  s = check_status(ctx, status);
+  if (s != PC_OK) return s;
+  const double N = double(n_paths);
+  for (int v = 0; v < 2; ++v) {
+    const double mean = h[2 * v] / N;
+    out[2 * v] = mean;
+    out[2 * v + 1] = std::sqrt(std::max(0.0, (h[2 * v + 1] - N * mean * mean) / (N - 1.0)) / N);
+  }
+  return PC_OK;
+}
+
+pc_status pc_debug_cv_paths(const pc_model *m, const pc_contract *k, const pc_cv_desc *c, const float *d_tables,
+                            uint64_t n_paths, uint64_t seed, float *d_xm) {
+  if (!m || !d_xm) return fail(PC_EINVAL, "null argument");
+  return cv_launch(m, k, c, d_tables, n_paths, seed, m->ctx->d_gout, d_xm);
+}
+
+}  // extern "C"

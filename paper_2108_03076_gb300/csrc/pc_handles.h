@@ -81,6 +81,9 @@ struct Launch {
 pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
                   uint64_t seed, uint32_t stream, Launch &L);
 
+// Grow the context's tile-partial scratch to at least `doubles`.
+pc_status ensure_partials(pc_ctx *c, size_t doubles);
+
 // Turn a raised device status word into PC_EDEVICE (and clear it).
 pc_status check_status(pc_ctx *c, int32_t status);
 

@@ -1,0 +1,115 @@
+"""GPU delta-hedge control variate (pc_price_cv) with caller-supplied hedge
+tables.
+
+* per path: the payoff X and the hedge gain M of the kernel against the
+  oracle (``oracle.cv``) on identical draws and the same tables;
+* the plain half of pc_price_cv is bit-identical to pc_price, and the
+  control-variate price agrees with it within the standard errors (E[M] = 0
+  for any hedge ratios);
+* a European call hedged at 32 dates with tabulated Black-Scholes deltas
+  removes most of the variance (the machinery works when the ratios are good).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import Engine, TIE, compare, market, tparam_env, torch
+import paper_2108_03076_gb300 as pc
+import workloads as W
+from oracle import closed_forms as cf, cv, il_text, mc
+from oracle.paths import simulate
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    e = Engine()
+    yield e
+    e.close()
+
+
+def random_tables(desc, seed):
+    n_f = pc.pc_cv_table_size(desc)
+    rng = np.random.default_rng(seed)
+    tab = (0.3 + 0.4 * rng.standard_normal(n_f)).astype(np.float32)
+    for i in range(3):
+        desc.delta0[i] = [0.35, 0.25, 0.15][i]
+    return tab
+
+
+def desc_arrays(desc):
+    n, d = desc.n, desc.d
+    lo = np.array([[desc.lo[k][i] for i in range(d)] for k in range(max(n - 1, 0))], np.float64)
+    h = np.array([[desc.h[k][i] for i in range(d)] for k in range(max(n - 1, 0))], np.float64)
+    return lo, h
+
+
+def test_per_path_payoff_and_hedge_gain_match_oracle(eng):
+    w = W.worst_of_autocall()
+    m = eng.model(w.market)
+    k = eng.contract(w.il_text, w.tparams)
+    desc = pc.pc_cv_grid(m, 8, 4.0)
+    tab = random_tables(desc, 1)
+    dtab = torch.tensor(tab, device="cuda")
+    n, seed = 4096 + 13, 0x5EED0101
+    xm = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+    pc.pc_debug_cv_paths(m, k, desc, dtab.data_ptr(), n, seed, xm.data_ptr())
+    torch.cuda.synchronize()
+    got = xm.double().cpu().numpy().reshape(n, 2)
+    mk = market(w.market)
+    x_ref, marg = mc.payoffs(il_text.parse(w.il_text), mk, tparam_env(w.tparams), 0, 1, n, seed, 0, 0,
+                             with_margins=True)
+    compare(got[:, 0], x_ref, marg, w.notional, "payoff")
+    S = np.moveaxis(simulate(mk, seed, 0, np.arange(n)), 1, 2)
+    alive, ki = cv.autocall_states(S, [1.0, 1.0, 1.0], 1.0, 0.6)
+    lo, h = desc_arrays(desc)
+    d, G = desc.d, desc.grid
+    tables = tab.astype(np.float64).reshape(desc.n - 1, 2, G ** d, d)
+    delta = cv.table_deltas(S, ki, tables, lo, h, G, [desc.delta0[i] for i in range(d)])
+    disc = [mk.disc(o) for o in range(mk.n + 1)]
+    M_ref = cv.hedge_martingale(S, disc, alive, delta)
+    worst = S.min(axis=2)[:, 1:mk.n]
+    amb = (np.abs(worst - 1.0) < TIE).any(1) | (np.abs(worst - 0.6) < TIE).any(1)
+    bad = np.abs(got[:, 1] - M_ref) > 1e-4 * (1.0 + np.abs(M_ref))
+    assert not np.any(bad & ~amb), np.nonzero(bad & ~amb)[0][:5]
+    assert int((bad & amb).sum()) <= max(2, 1e-3 * n)
+    assert np.std(M_ref) > 0.05
+
+
+def test_plain_half_is_pc_price_and_cv_is_unbiased(eng):
+    w = W.worst_of_autocall()
+    m = eng.model(w.market)
+    k = eng.contract(w.il_text, w.tparams)
+    desc = pc.pc_cv_grid(m, 12, 4.5)
+    dtab = torch.tensor(random_tables(desc, 2), device="cuda")
+    n, seed = 1 << 20, 0x5EED0002
+    (pcv, scv), (pp, sp) = pc.pc_price_cv(m, k, desc, dtab.data_ptr(), n, seed)
+    price, se = pc.pc_price(m, k, n, seed)
+    assert pp == price and sp == se
+    assert abs(pcv - pp) <= 4 * (scv + sp), (pcv, pp, scv, sp)
+
+
+def test_black_scholes_hedged_call_removes_most_variance(eng):
+    days = [int(round(365 * (j + 1) / 32)) for j in range(32)]
+    spec = W.MarketSpec([1.0], [0.2], [[1.0]], 0.03, days)
+    m = eng.model(spec)
+    k = eng.contract(W.european_text(1.0), [32])
+    desc = pc.pc_cv_grid(m, 64, 5.0, ref=(1.0,), call_level=1e30, ki_level=-1.0)
+    lo, h = desc_arrays(desc)
+    tau = np.array([0.0] + [dd / 365.0 for dd in days])
+    tab = np.zeros((31, 2, 64, 1))
+    for kk in range(1, 32):
+        y = lo[kk - 1, 0] + h[kk - 1, 0] * np.arange(64)
+        dl = np.array([cf.bs_delta_call(math.exp(v), 1.0, 0.03, 0.2, tau[-1] - tau[kk]) for v in y])
+        tab[kk - 1, 0, :, 0] = dl
+        tab[kk - 1, 1, :, 0] = dl
+    desc.delta0[0] = cf.bs_delta_call(1.0, 1.0, 0.03, 0.2, tau[-1])
+    dtab = torch.tensor(tab.ravel().astype(np.float32), device="cuda")
+    (pcv, scv), (pp, sp) = pc.pc_price_cv(m, k, desc, dtab.data_ptr(), 1 << 20, 0x5EED0003)
+    assert (sp / scv) ** 2 > 8.0, (sp, scv)
+    bs = cf.bs_call(1.0, 1.0, 0.03, 0.2, tau[-1])
+    assert abs(pcv - bs) < 4 * scv + 1e-4, (pcv, bs, scv)
