@@ -33,6 +33,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import workloads as W  # noqa: E402
 
 METRIC = "path·date evals/sec & contracts priced/sec at 1e-4 rel. std-err vs plain MC"
@@ -41,6 +43,7 @@ TARGET_REL_SE = 1e-4
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
                for f in ("pc_kernels.cu", "pc_eval.cuh", "pc_device.cuh", "pc_internal.h")]
 PORTFOLIO = "portfolio_1024"
+LEARNED = "learned_cv_worst_of_autocall"
 PORTFOLIO_SEED = 0x5EED0004
 
 
@@ -204,12 +207,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="worst_of_autocall_3u_5d",
-                    choices=sorted(W.ALL) + [PORTFOLIO])
+                    choices=sorted(W.ALL) + [PORTFOLIO, LEARNED])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload == PORTFOLIO:
         return run_portfolio(args)
+    if args.workload == LEARNED:
+        return run_learned(args)
     w = W.ALL[args.workload]()
     if args.impl == "reference":
         return run_reference(args, w)
@@ -524,6 +529,155 @@ def run_portfolio(args):
     pc.pc_destroy(ctx)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Learned control variate: time to a 1e-4 relative standard error
+# ---------------------------------------------------------------------------
+
+
+def learned_config(ws) -> dict:
+    return {"workload": LEARNED, "contract": "worst_of_autocall_3u_5d", "target_rel_se": TARGET_REL_SE,
+            "network": "16-256-256-256-5 softplus, BF16 weights, FP32 accumulation",
+            "training_set": "8192 engine-priced states x 128 paths (+6 bumped plans for hedge ratios)",
+            "training_steps": 6000, "table_grid": 12, "parallelism": f"replicas x{ws}",
+            "l2": "flushed between steps by a 256 MiB device write"}
+
+
+def run_learned(args):
+    w = W.worst_of_autocall()
+    if args.impl == "reference":
+        # the oracle, plain Monte Carlo, on a bounded sample; contracts/s at the target
+        ws, rank, _ = dist_env()
+        if rank != 0:
+            return
+        dt, x = oracle_run(w, 1 << 14)
+        for _ in range(args.warmup):
+            oracle_run(w, 1 << 12)
+        tot, n = 0.0, 0
+        for s_ in range(args.steps):
+            dt, x = oracle_run(w, 1 << 13, s_ << 13)
+            tot += dt
+            n += 1 << 13
+        cvx = x.std() / abs(x.mean())
+        need = (cvx / TARGET_REL_SE) ** 2
+        value = (n / tot) / need
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "contracts/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": learned_config(ws),
+                "cpu_baseline": {"value": value, "unit": "contracts/s", "cores": 1, "kind": "oracle",
+                                 "sample": "8192 paths per step, plain MC rate scaled to the paths a "
+                                           "1e-4 relative standard error needs"},
+                "e2e": {"value": value, "unit": "contracts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import torch
+    import paper_2108_03076_gb300 as pc
+    from paper_2108_03076_gb300 import learned_cv as LCV
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2108_03076_gb300 import build
+    build.build()
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
+    ctx = pc.pc_create(local, stream.cuda_stream)
+    spec = w.market
+    model = pc.pc_model_create(ctx, spec.S0, spec.sigma, spec.corr, spec.r, spec.days)
+    words, consts = pc.pc_assemble(w.il_text)
+    contract = pc.pc_load_payoff(ctx, words, consts, w.tparams, 0, 1)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    t0 = time.perf_counter()
+    data = LCV.engine_training_set(ctx, 8192, 128, 0x7A1)
+    t_data = time.perf_counter() - t0
+    net = LCV.LearnedCV(ctx, seed=5)
+    a, b = ev(), ev()
+    a.record(stream)
+    net.train(data, 6000)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_train = a.elapsed_time(b) / 1e3
+    a, b = ev(), ev()
+    a.record(stream)
+    desc, tabs = net.tables(model, grid=12)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_tables = a.elapsed_time(b) / 1e3
+    # pilot (independent paths): variances and beta
+    (_, scv), (pp, sp), beta = pc.pc_price_cv(model, contract, desc, tabs.data_ptr(), 1 << 18, 0x5EED7001,
+                                                with_beta=True)
+    desc.beta = float(beta)
+    (_, scv_b), _ = pc.pc_price_cv(model, contract, desc, tabs.data_ptr(), 1 << 18, 0x5EED7001)
+    n_plain = int(math.ceil((sp * math.sqrt(1 << 18) / (TARGET_REL_SE * abs(pp))) ** 2))
+    n_cv = int(math.ceil((scv_b * math.sqrt(1 << 18) / (TARGET_REL_SE * abs(pp))) ** 2))
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        pc.pc_price_async(model, contract, n_plain, 0, w.seed, 0, out.data_ptr())
+        pc.pc_price_cv(model, contract, desc, tabs.data_ptr(), n_cv, w.seed)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 50))
+    tp_ms, tc_ms, res = [], [], None
+    with ClockSampler(local) as clk:
+        for _ in range(steps):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record(stream)
+            pc.pc_price_async(model, contract, n_plain, 0, w.seed, 0, out.data_ptr())
+            b.record(stream)
+            torch.cuda.synchronize()
+            tp_ms.append(a.elapsed_time(b))
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record(stream)
+            res = pc.pc_price_cv(model, contract, desc, tabs.data_ptr(), n_cv, w.seed)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tc_ms.append(a.elapsed_time(b))
+    sums = out.cpu().numpy()
+    plain_price = sums[0] / n_plain
+    plain_se = math.sqrt(max(0.0, (sums[1] - n_plain * plain_price ** 2) / (n_plain - 1)) / n_plain)
+    (cv_price, cv_se), _ = res
+    t_plain = statistics.median(tp_ms) / 1e3
+    t_cv = statistics.median(tc_ms) / 1e3 + t_tables
+    # e2e through the public API: tables from the trained network + priced to the target
+    t0 = time.perf_counter()
+    for _ in range(3):
+        d2, t2 = net.tables(model, grid=12)
+        d2.beta = desc.beta
+        pc.pc_price_cv(model, contract, d2, t2.data_ptr(), n_cv, w.seed)
+    e2e = (time.perf_counter() - t0) / 3
+    # surrogate: the network's value at the spot
+    x = LCV.features(np.zeros((1, 3)), np.zeros(1, bool), np.zeros(1), 5, np.array(spec.sigma)[None, :], 0.5,
+                     spec.r, np.ones(1), 0.05, 1.0, 0.6)
+    surrogate = float(net.predict(x)[0, 0])
+    line = {
+        "metric": METRIC, "value": ws / t_cv, "unit": "contracts/s", "n_gpus": ws, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_cv, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 paths, bf16 network", "data": "synthetic",
+        "config": learned_config(ws),
+        "value_note": "contracts priced per second at a 1e-4 relative standard error with the learned "
+                      "control variate (hedge tables from the network + control-variate pricing)",
+        "plain_mc": {"contracts_per_sec": ws / t_plain, "paths": n_plain, "ms": 1e3 * t_plain,
+                     "price": plain_price, "stderr": plain_se},
+        "learned_cv": {"paths": n_cv, "ms_pricing": statistics.median(tc_ms), "ms_tables": 1e3 * t_tables,
+                       "price": cv_price, "stderr": cv_se, "beta": desc.beta,
+                       "variance_ratio": (sp / scv_b) ** 2, "variance_ratio_beta1": (sp / scv) ** 2},
+        "gpu_time_ratio_plain_over_cv": t_plain / t_cv,
+        "training": {"data_s_wall": t_data, "train_s_gpu": t_train, "samples": len(data.x)},
+        "surrogate": {"value": surrogate, "mc_price": plain_price,
+                      "rel_error": abs(surrogate - plain_price) / abs(plain_price)},
+        "gpu_launches": steps * 3,
+        "e2e": {"value": ws / e2e, "unit": "contracts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 48,
+                "note": "pc_cv_tables + pc_price_cv on resident model/contract, host wall clock"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    pc.pc_contract_destroy(contract)
+    pc.pc_model_destroy(model)
+    pc.pc_destroy(ctx)
 
 if __name__ == "__main__":
     main()

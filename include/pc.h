@@ -60,7 +60,7 @@ typedef int32_t pc_status;
 #define PC_MAX_CONSTS    16384      /* real literals per program                    */
 #define PC_MAX_TPARAMS    1024      /* template variables per program               */
 #define PC_MAX_STACK        96      /* operand stack depth (values + loop frames)   */
-#define PC_MAX_WINDOW      256      /* lookback window of simulated dates           */
+#define PC_MAX_WINDOW      256      /* lookback window kept in shared memory        */
 
 /* ------------------------------------------------------------------------ */
 /* Bytecode (input format of pc_load_payoff)                                 */
@@ -286,6 +286,43 @@ pc_status pc_price_noalloc(const pc_model *model, const pc_contract *contract,
                            uint32_t stream, double *d_out);
 
 /* ------------------------------------------------------------------------ */
+/* Window of simulated dates                                                 */
+/* ------------------------------------------------------------------------ */
+/* A path keeps the simulated values of its recent dates in a window of
+ * `win` dates (a power of two above the program's largest lookback below
+ * the newest simulated date, from the load-time analysis).  By default the
+ * window lives in shared memory.  Programs whose window does not fit there
+ * well -- more than PC_MAX_WINDOW dates, or fewer than 8 resident warps per
+ * SM -- are not streamable in shared memory; pc_price, pc_price_async and
+ * pc_price_paths then keep the window in HBM instead: one column of
+ * win * d float2 slots per thread of the launch (slot-major, coalesced),
+ * in a buffer the context grows as needed (see pc_price_info).  Results do
+ * not depend on where the window lives.  Portfolio, sensitivity,
+ * control-variate and no-allocation pricing keep the shared window (they
+ * return PC_ERANGE / PC_ELIMIT for programs that need the HBM window).
+ * Not in the paper: its generated code reads a path array (Sec. 6.2). */
+#define PC_WINDOW_AUTO    0
+#define PC_WINDOW_SHARED  1   /* never use the HBM window */
+#define PC_WINDOW_HBM     2   /* always use the HBM window (single-contract pricing) */
+
+/* Placement policy of the context's pricing launches.  Errors: PC_EINVAL. */
+pc_status pc_set_window_mode(pc_ctx *ctx, int32_t mode);
+
+typedef struct pc_launch_info {
+  int32_t window;              /* dates in the window                       */
+  int32_t hbm_window;          /* 1: window in HBM                          */
+  int32_t block, grid;         /* launch shape                              */
+  uint64_t smem_bytes;         /* dynamic shared memory per block           */
+  uint64_t hbm_window_bytes;   /* HBM window buffer this launch uses (0 if shared) */
+  uint64_t window_bytes_written_per_path_date;  /* HBM window: 4 d        */
+} pc_launch_info;
+
+/* How pc_price would launch (model, contract, n_paths) on this context.
+ * Host only apart from occupancy queries.  Errors: as pc_price. */
+pc_status pc_price_info(const pc_model *model, const pc_contract *contract, uint64_t n_paths,
+                        pc_launch_info *info);
+
+/* ------------------------------------------------------------------------ */
 /* Portfolio pricing                                                         */
 /* ------------------------------------------------------------------------ */
 /* The paper prices one contract per engine invocation; templating (Sec. 2,
@@ -442,10 +479,10 @@ pc_status pc_mlp_train(pc_mlp *net, const float *d_x, const float *d_t, size_t n
  * pricing kernel adds to each path's payoff X the discounted gains of a
  * hedge held over [t_k, t_{k+1}] while the contract is alive,
  *   M = sum_k alive_k sum_i Delta_i(k) (D_{k+1} S_i(t_{k+1}) - D_k S_i(t_k)),
- * and reports Y = X - M.  The D S_i are martingales and every Delta_i(k)
+ * and reports Y = X - beta M.  The D S_i are martingales and every Delta_i(k)
  * depends only on the path up to t_k, so E[M] = 0: Y is unbiased for any
- * hedge ratios, and its variance is small when they are close to the
- * contract's sensitivities.  Hedge ratios at t_k (k >= 1) come from a
+ * hedge ratios and any fixed beta, and its variance is small when the
+ * ratios are close to the contract's sensitivities.  Hedge ratios at t_k (k >= 1) come from a
  * table over y = ln S per date and knock-in state, read by multilinear
  * interpolation (per axis u = clamp((y - lo) / h, 0, G - 1),
  * a = min(floor(u), G - 2), f = u - a), at t_0 from delta0.  Tables are
@@ -464,6 +501,7 @@ typedef struct pc_cv_desc {
   float lo[PC_CV_MAX_DATES][3];  /* table axes over ln S: row k - 1 = date k */
   float h[PC_CV_MAX_DATES][3];
   float delta0[3];           /* hedge ratios at t_0                          */
+  float beta;                /* Y = X - beta M (pc_cv_grid sets 1)           */
 } pc_cv_desc;
 
 /* Fill d, n, grid, lo and h from the model: axis i at date k is centred on
@@ -483,9 +521,12 @@ pc_status pc_cv_table_size(const pc_cv_desc *desc, size_t *floats);
  * Errors: PC_EINVAL (widths other than 16 in / 5 out, cap too small). */
 pc_status pc_cv_tables(pc_mlp *net, const pc_model *model, pc_cv_desc *desc, float *d_tables,
                        size_t cap_floats);
-/* Price with the control variate: out[0..3] (host) = price and standard
- * error of Y, then of X on the same paths (pc_price's estimate with this
- * seed).  d_tables: device tables laid out as above.  Blocks until done.
+/* Price with the control variate: out[0..4] (host) = price and standard
+ * error of Y = X - desc->beta M, then of X on the same paths (pc_price's
+ * estimate with this seed), then the variance-minimising beta
+ * Cov(X, M) / Var(M) measured on these paths (to fix beta for a later,
+ * independent run).  d_tables: device tables laid out as above.  Blocks
+ * until done.
  * Errors: as pc_price; PC_EINVAL for a desc that does not match the model. */
 pc_status pc_price_cv(const pc_model *model, const pc_contract *contract, const pc_cv_desc *desc,
                       const float *d_tables, uint64_t n_paths, uint64_t seed, double *out);

@@ -9,6 +9,11 @@ library's CUDA kernels.  Device buffers are passed as integer addresses
 
 The library must have been built (``paper_2108_03076_gb300.build.build()``);
 there is no fallback implementation.
+
+Submodules: ``build`` (nvcc build of libpc.so), ``merge`` (host merge of
+per-process sums), ``autograd`` (pathwise-sensitivity autograd function),
+``learned_cv`` (training set, network and tables of the learned control
+variate).
 """
 from __future__ import annotations
 
@@ -72,7 +77,16 @@ class CvDesc(C.Structure):
     _fields_ = [("d", C.c_int32), ("n", C.c_int32), ("grid", C.c_int32), ("ref", C.c_float * 3),
                 ("call_level", C.c_float), ("ki_level", C.c_float), ("coupon", C.c_float),
                 ("lo", (C.c_float * 3) * CV_MAX_DATES), ("h", (C.c_float * 3) * CV_MAX_DATES),
-                ("delta0", C.c_float * 3)]
+                ("delta0", C.c_float * 3), ("beta", C.c_float)]
+
+
+class LaunchInfo(C.Structure):
+    _fields_ = [("window", C.c_int32), ("hbm_window", C.c_int32), ("block", C.c_int32),
+                ("grid", C.c_int32), ("smem_bytes", C.c_uint64), ("hbm_window_bytes", C.c_uint64),
+                ("window_bytes_written_per_path_date", C.c_uint64)]
+
+
+WINDOW_AUTO, WINDOW_SHARED, WINDOW_HBM = 0, 1, 2
 
 
 class ProgramInfo(C.Structure):
@@ -101,6 +115,8 @@ _SIGS = {
     "pc_price_paths": [VP, VP, U64, U64, U64, U32, VP, VP],
     "pc_price_noalloc": [VP, VP, U64, U64, U64, U32, VP],
     "pc_price_batch": [SZ, C.POINTER(VP), C.POINTER(VP), C.POINTER(U64), U64, PD, PD],
+    "pc_set_window_mode": [VP, C.c_int32],
+    "pc_price_info": [VP, VP, U64, C.POINTER(LaunchInfo)],
     "pc_batch_create": [SZ, C.POINTER(VP), C.POINTER(VP), C.POINTER(U64), U64,
                         C.POINTER(BatchConfig), C.POINTER(VP)],
     "pc_batch_tune": [VP, C.c_int32],
@@ -283,6 +299,16 @@ def pc_price_noalloc(model: int, contract: int, n_paths: int, path_offset: int, 
 NOALLOC_MAX_PATHS = 1 << 24
 
 
+def pc_set_window_mode(ctx: int, mode: int) -> None:
+    _check(lib().pc_set_window_mode(VP(ctx), int(mode)))
+
+
+def pc_price_info(model: int, contract: int, n_paths: int) -> LaunchInfo:
+    info = LaunchInfo()
+    _check(lib().pc_price_info(VP(model), VP(contract), int(n_paths), C.byref(info)))
+    return info
+
+
 def _batch_arrays(models, contracts, n_paths):
     n = len(contracts)
     if len(models) != n or len(n_paths) != n:
@@ -409,12 +435,16 @@ def pc_cv_tables(net: int, model: int, desc: CvDesc, d_tables: int, cap_floats: 
     _check(lib().pc_cv_tables(VP(net), VP(model), C.byref(desc), VP(d_tables), int(cap_floats)))
 
 
-def pc_price_cv(model: int, contract: int, desc: CvDesc, d_tables: int, n_paths: int, seed: int):
-    """(price, se) of the control-variate estimate, then (price, se) of the
-    plain estimate on the same paths."""
-    out = np.zeros(4)
+def pc_price_cv(model: int, contract: int, desc: CvDesc, d_tables: int, n_paths: int, seed: int,
+                with_beta: bool = False):
+    """(price, se) of the control-variate estimate Y = X - desc.beta M, then
+    (price, se) of the plain estimate on the same paths; with_beta adds the
+    variance-minimising beta measured on these paths."""
+    out = np.zeros(5)
     _check(lib().pc_price_cv(VP(model), VP(contract), C.byref(desc), VP(d_tables), int(n_paths), int(seed),
                              _ptr(out, C.c_double)))
+    if with_beta:
+        return (out[0], out[1]), (out[2], out[3]), out[4]
     return (out[0], out[1]), (out[2], out[3])
 
 

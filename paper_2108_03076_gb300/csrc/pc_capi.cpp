@@ -143,7 +143,7 @@ int pick_block(const Program &p, int words, int max_smem, int d, size_t &smem) {
 }
 
 pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
-                  uint64_t seed, uint32_t stream, Launch &L) {
+                  uint64_t seed, uint32_t stream, Launch &L, bool allow_hbm) {
   if (!m || !k) return fail(PC_EINVAL, "null model or contract");
   if (m->ctx != k->ctx) return fail(PC_EINVAL, "model and contract belong to different contexts");
   if (n_paths == 0) return fail(PC_EINVAL, "n_paths must be >= 1");
@@ -152,12 +152,37 @@ pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uin
   pc_status s = window_for(m, k, win);
   if (s != PC_OK) return s;
   pc_ctx *c = m->ctx;
-  const Layout lay = make_layout(k->prog, m->H, win);
-  L.block = pick_block(k->prog, lay.words, c->max_smem, m->H.d, L.smem);
-  if (!L.block)
+  const int mode = allow_hbm ? c->window_mode : PC_WINDOW_SHARED;
+  Layout lay = make_layout(k->prog, m->H, win);
+  int bpsm = 0;
+  bool hbm = mode == PC_WINDOW_HBM;
+  if (!hbm) {
+    L.block = win <= PC_MAX_WINDOW ? pick_block(k->prog, lay.words, c->max_smem, m->H.d, L.smem) : 0;
+    bpsm = L.block ? price_blocks_per_sm(m->H.d, L.block, L.smem, false) : 0;
+    const int warps = bpsm * L.block / 32;
+    if (mode == PC_WINDOW_AUTO && (!L.block || warps < 8)) hbm = true;
+  }
+  if (hbm) {
+    // shared region without the window; the window is a column of the
+    // context's HBM window buffer per thread of the launch
+    lay.off_win = lay.off_cache;
+    lay.words = lay.off_win;
+    L.block = kBlock;
+    L.smem = price_smem_bytes(k->prog.code.size(), pool_padded(k->prog), lay.words, L.block);
+    if (L.smem + kStaticSmemReserve > size_t(c->max_smem)) {
+      L.block = 32;
+      L.smem = price_smem_bytes(k->prog.code.size(), pool_padded(k->prog), lay.words, L.block);
+    }
+    bpsm = price_blocks_per_sm(m->H.d, L.block, L.smem, true);
+    L.hbm_window = true;
+  } else if (!L.block) {
+    if (win > PC_MAX_WINDOW)
+      return fail(PC_ERANGE, "program looks back " + std::to_string(win / 2) + "+ dates; this entry point "
+                             "keeps at most " + std::to_string(PC_MAX_WINDOW) + " in shared memory");
     return fail(PC_ELIMIT, "program + per-path state need " + std::to_string(L.smem) +
                                " bytes of shared memory for a 32-thread block; the device offers " +
                                std::to_string(c->max_smem));
+  }
   const uint64_t n_tiles = (n_paths + kTilePaths - 1) / kTilePaths;
   PriceArgs &a = L.args;
   a.prog = k->d_code;
@@ -172,11 +197,28 @@ pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uin
   a.stream = stream;
   a.n_tiles = n_tiles;
   a.status = reinterpret_cast<int32_t *>(c->d_res + 4);
-  const int bpsm = price_blocks_per_sm(m->H.d, L.block, L.smem, false);
   if (bpsm < 1) return fail(PC_ELIMIT, "kernel cannot be resident with this shared-memory footprint");
   const uint64_t warps_per_block = uint64_t(L.block) / 32;
   const uint64_t need = (n_tiles + warps_per_block - 1) / warps_per_block;
   L.grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * bpsm, need));
+  return PC_OK;
+}
+
+// Point the launch's window at the context's HBM window buffer (grown to
+// grid * block threads x win * d slots).
+pc_status bind_hbm_window(pc_ctx *c, Launch &L, int d) {
+  const size_t threads = size_t(L.grid) * size_t(L.block);
+  const size_t slots = threads * size_t(L.args.lay.win) * size_t(d);
+  if (slots > c->gwin_cap) {
+    CU(cudaStreamSynchronize(c->stream), "sync");
+    if (c->d_gwin) cudaFree(c->d_gwin);
+    c->d_gwin = nullptr;
+    c->gwin_cap = 0;
+    CU(cudaMalloc(&c->d_gwin, slots * sizeof(float2)), "HBM window");
+    c->gwin_cap = slots;
+  }
+  L.args.lay.gwin = c->d_gwin;
+  L.args.lay.gstride = int64_t(threads);
   return PC_OK;
 }
 
@@ -226,11 +268,15 @@ pc_status run_greeks(const pc_model *m, const pc_contract *k, uint64_t n_paths, 
 pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
                     uint64_t seed, uint32_t stream, double *d_out, float *d_payoffs) {
   Launch L;
-  pc_status s = prepare(m, k, n_paths, offset, seed, stream, L);
+  pc_status s = prepare(m, k, n_paths, offset, seed, stream, L, true);
   if (s != PC_OK) return s;
   pc_ctx *c = m->ctx;
   s = ensure_partials(c, size_t(L.args.n_tiles) * 2);
   if (s != PC_OK) return s;
+  if (L.hbm_window) {
+    s = bind_hbm_window(c, L, m->H.d);
+    if (s != PC_OK) return s;
+  }
   L.args.width = 2;
   reduction_chunks(L.args.n_tiles, L.args.chunk_tiles, L.args.n_chunks);
   L.args.tile_partials = c->d_partials;
@@ -430,6 +476,7 @@ pc_status pc_destroy(pc_ctx *c) {
   cudaStreamSynchronize(c->stream);
   if (c->d_partials) cudaFree(c->d_partials);
   if (c->d_control) cudaFree(c->d_control);
+  if (c->d_gwin) cudaFree(c->d_gwin);
   if (c->d_gout) cudaFree(c->d_gout);
   if (c->d_res) cudaFree(c->d_res);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -655,6 +702,31 @@ pc_status pc_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, ui
   const double var = std::max(0.0, (h[1] - n * mean * mean) / (n - 1.0));
   *out_price = mean;
   *out_stderr = std::sqrt(var / n);
+  return PC_OK;
+}
+
+pc_status pc_set_window_mode(pc_ctx *c, int32_t mode) {
+  if (!c) return fail(PC_EINVAL, "null context");
+  if (mode != PC_WINDOW_AUTO && mode != PC_WINDOW_SHARED && mode != PC_WINDOW_HBM)
+    return fail(PC_EINVAL, "window mode must be PC_WINDOW_AUTO, _SHARED or _HBM");
+  c->window_mode = mode;
+  return PC_OK;
+}
+
+pc_status pc_price_info(const pc_model *m, const pc_contract *k, uint64_t n_paths, pc_launch_info *info) {
+  if (!info) return fail(PC_EINVAL, "null info");
+  Launch L;
+  pc_status s = prepare(m, k, n_paths, 0, 0, 0, L, true);
+  if (s != PC_OK) return s;
+  const int d = m->H.d;
+  info->window = L.args.lay.win;
+  info->hbm_window = L.hbm_window ? 1 : 0;
+  info->block = L.block;
+  info->grid = L.grid;
+  info->smem_bytes = L.smem;
+  info->hbm_window_bytes =
+      L.hbm_window ? uint64_t(L.grid) * L.block * uint64_t(L.args.lay.win) * d * sizeof(float2) : 0;
+  info->window_bytes_written_per_path_date = L.hbm_window ? uint64_t(4 * d) : 0;
   return PC_OK;
 }
 

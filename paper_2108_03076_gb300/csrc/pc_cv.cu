@@ -7,7 +7,8 @@
 //   M = sum_{k<n} alive_k sum_i Delta_i(k) (D_{k+1} S_i(t_{k+1}) - D_k S_i(t_k))
 // with Delta from a table over ln S (multilinear interpolation) per date and
 // knock-in state.  Every factor of a term is known at t_k, so E[M] = 0 and
-// Y = X - M estimates the same price; the tile sums carry Y, Y^2, X, X^2.
+// Y = X - beta M estimates the same price for any fixed beta; the tile sums
+// carry X, X^2, M, M^2, X M, from which the host forms any beta's estimate.
 // A hedge period whose end date the warp never generated (every lane's
 // program stopped before it) is skipped: that decision depends only on
 // information at t_k of this and of independent paths, so the terms kept are
@@ -21,9 +22,10 @@
 namespace pc {
 namespace {
 
-// Multilinear interpolation of the d hedge ratios at y = ln S.
+// Multilinear interpolation of the d hedge ratios at ln S (given as
+// l2 = log2 S: the axis coordinate is u = l2 ln2 / h - lo / h).
 template <int D>
-__device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, const float (&y)[D],
+__device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, const float (&l2)[D],
                                             float (&delta)[D]) {
   const float *tab = c.tables + (size_t(k - 1) * 2 + ki) * size_t(c.nodes) * D;
   int a[D];
@@ -31,7 +33,7 @@ __device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, cons
   const int G = c.grid;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    float u = (y[i] - c.lo[k - 1][i]) / c.h[k - 1][i];
+    float u = fmaf(l2[i], c.ua[k - 1][i], -c.ub[k - 1][i]);
     u = fminf(fmaxf(u, 0.f), float(G - 1));
     int ai = int(floorf(u));
     ai = ai < G - 2 ? ai : G - 2;
@@ -62,9 +64,9 @@ __device__ float hedge_gain(const CvArgs &c, const ModelDev &m, int frontier, SF
   int ki = 0;
   for (int k = 0; k < c.n; ++k) {
     if (k >= 1) {
-      float worst = s(k, 0) / c.ref[0];
+      float worst = s(k, 0) * c.inv_ref[0];
 #pragma unroll
-      for (int i = 1; i < D; ++i) worst = fminf(worst, s(k, i) / c.ref[i]);
+      for (int i = 1; i < D; ++i) worst = fminf(worst, s(k, i) * c.inv_ref[i]);
       ki |= worst <= c.ki_level ? 1 : 0;
       alive = alive && !(worst >= c.call_level);
     }
@@ -74,10 +76,10 @@ __device__ float hedge_gain(const CvArgs &c, const ModelDev &m, int frontier, SF
 #pragma unroll
       for (int i = 0; i < D; ++i) delta[i] = c.delta0[i];
     } else {
-      float y[D];
+      float l2[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) y[i] = logf(s(k, i));
-      table_delta<D>(c, k, ki, y, delta);
+      for (int i = 0; i < D; ++i) l2[i] = __log2f(s(k, i));
+      table_delta<D>(c, k, ki, l2, delta);
     }
     const float d0 = __ldg(m.disc + k + m.n_hist), d1 = __ldg(m.disc + k + 1 + m.n_hist);
 #pragma unroll
@@ -130,17 +132,18 @@ __global__ void __launch_bounds__(kBlock) cv_kernel(const PriceArgs a, const CvA
       };
       Mv[q] = hedge_gain<D>(c, a.m, frontier, s);
     }
-    double tp[4] = {0.0, 0.0, 0.0, 0.0};
+    double tp[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     const float xs[2] = {x.x, x.y};
     const bool live[2] = {live0, live1};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       if (!live[q]) continue;
-      const double xd = double(xs[q]), yd = double(xs[q] - Mv[q]);
-      tp[0] += yd;
-      tp[1] = fma(yd, yd, tp[1]);
-      tp[2] += xd;
-      tp[3] = fma(xd, xd, tp[3]);
+      const double xd = double(xs[q]), md = double(Mv[q]);
+      tp[0] += xd;
+      tp[1] = fma(xd, xd, tp[1]);
+      tp[2] += md;
+      tp[3] = fma(md, md, tp[3]);
+      tp[4] = fma(xd, md, tp[4]);
       if (WRITE) {
         const uint64_t i = q ? i1 : i0;
         a.out_paths[2 * i] = xs[q];
@@ -148,8 +151,8 @@ __global__ void __launch_bounds__(kBlock) cv_kernel(const PriceArgs a, const CvA
       }
     }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) tp[v] = warp_sum(tp[v]);
-    finish_tile<4>(a, tile, tp, lane);
+    for (int v = 0; v < 5; ++v) tp[v] = warp_sum(tp[v]);
+    finish_tile<5>(a, tile, tp, lane);
   }
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -21,8 +21,14 @@ struct CvArgs {
   float ref[kCvMaxD];
   float call_level, ki_level, coupon;
   float lo[kCvMaxDates][kCvMaxD], h[kCvMaxDates][kCvMaxD];  // row k-1: date k
+  // u = log2(S) * ua - ub = (ln S - lo) / h: ua = ln 2 / h, ub = lo / h
+  float ua[kCvMaxDates][kCvMaxD], ub[kCvMaxDates][kCvMaxD];
+  float inv_ref[kCvMaxD];
   float delta0[kCvMaxD];
 };
+
+// Device scratch owned by a network (grow-only, freed with it).
+float *mlp_scratch(struct ::pc_mlp *net, size_t floats);
 
 struct CvFeatureArgs {
   float ln_spot[kCvMaxD];

@@ -53,6 +53,13 @@ CvArgs device_args(const pc_cv_desc *c, const float *tables) {
   a.coupon = c->coupon;
   std::memcpy(a.lo, c->lo, sizeof(a.lo));
   std::memcpy(a.h, c->h, sizeof(a.h));
+  for (int k = 0; k < kCvMaxDates; ++k)
+    for (int i = 0; i < kCvMaxD; ++i) {
+      const double h = c->h[k][i] > 0.f ? double(c->h[k][i]) : 1.0;
+      a.ua[k][i] = float(std::log(2.0) / h);
+      a.ub[k][i] = float(double(c->lo[k][i]) / h);
+    }
+  for (int i = 0; i < kCvMaxD; ++i) a.inv_ref[i] = c->ref[i] > 0.f ? float(1.0 / double(c->ref[i])) : 0.f;
   return a;
 }
 
@@ -83,9 +90,9 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
   if (!block) return fail(PC_ELIMIT, "program + per-path state with the control variate exceed shared memory");
   PriceArgs a = L.args;
   a.lay = lay;
-  a.width = 4;
+  a.width = 5;
   reduction_chunks(a.n_tiles, a.chunk_tiles, a.n_chunks);
-  s = ensure_partials(ctx, size_t(a.n_tiles) * 4);
+  s = ensure_partials(ctx, size_t(a.n_tiles) * 5);
   if (s != PC_OK) return s;
   a.tile_partials = ctx->d_partials;
   a.control = ctx->d_control;
@@ -110,6 +117,7 @@ pc_status pc_cv_grid(const pc_model *m, int32_t grid, float width_sd, pc_cv_desc
   c->d = H.d;
   c->n = H.n;
   c->grid = grid;
+  c->beta = 1.f;
   for (int k = 1; k < H.n; ++k) {
     const double tau = double(H.tau[k]);
     for (int i = 0; i < 3; ++i) {
@@ -158,13 +166,11 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
   const size_t rows = need / size_t(c->d) + 1;
   pc_ctx *ctx = m->ctx;
   CU(cudaSetDevice(ctx->device), "cudaSetDevice");
-  float *buf = nullptr;
-  CU(cudaMalloc(&buf, rows * (kCvFeatures + kCvOutputs) * sizeof(float) + 64), "table scratch");
-  float *X = buf, *Y = buf + rows * kCvFeatures;
-  float *d0 = nullptr;
-  cudaError_t e = cudaMalloc(&d0, 4 * sizeof(float));
+  float *buf = mlp_scratch(net, rows * (kCvFeatures + kCvOutputs) + 64);
+  if (!buf) return fail(PC_ENOMEM, "table scratch");
+  float *X = buf, *Y = buf + rows * kCvFeatures, *d0 = Y + rows * kCvOutputs;
   const CvArgs ca = device_args(c, nullptr);
-  if (e == cudaSuccess) e = launch_cv_features(ca, fa, X, rows, ctx->stream);
+  cudaError_t e = launch_cv_features(ca, fa, X, rows, ctx->stream);
   if (e != cudaSuccess) s = cuda_fail(e, "table features");
   if (s == PC_OK) s = pc_mlp_forward(net, X, rows, Y);
   if (s == PC_OK) {
@@ -177,8 +183,6 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
     if (e != cudaSuccess) s = cuda_fail(e, "delta0 copy");
   }
   if (s == PC_OK) s = wait_stream(ctx);
-  cudaFree(buf);
-  if (d0) cudaFree(d0);
   if (s != PC_OK) return s;
   for (int i = 0; i < 3; ++i) c->delta0[i] = i < c->d ? h0[i] : 0.f;
   return PC_OK;
@@ -192,8 +196,8 @@ pc_status pc_price_cv(const pc_model *m, const pc_contract *k, const pc_cv_desc 
   pc_ctx *ctx = m->ctx;
   pc_status s = cv_launch(m, k, c, d_tables, n_paths, seed, ctx->d_gout, nullptr);
   if (s != PC_OK) return s;
-  double h[5], st[5];
-  CU(cudaMemcpyAsync(h, ctx->d_gout, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "result copy");
+  double h[6], st[5];
+  CU(cudaMemcpyAsync(h, ctx->d_gout, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "result copy");
   CU(cudaMemcpyAsync(st, ctx->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "status copy");
   s = wait_stream(ctx);
   if (s != PC_OK) return s;
@@ -201,12 +205,17 @@ pc_status pc_price_cv(const pc_model *m, const pc_contract *k, const pc_cv_desc 
   std::memcpy(&status, &st[4], 4);
   s = check_status(ctx, status);
   if (s != PC_OK) return s;
-  const double N = double(n_paths);
-  for (int v = 0; v < 2; ++v) {
-    const double mean = h[2 * v] / N;
-    out[2 * v] = mean;
-    out[2 * v + 1] = std::sqrt(std::max(0.0, (h[2 * v + 1] - N * mean * mean) / (N - 1.0)) / N);
-  }
+  const double N = double(n_paths), beta = double(c->beta);
+  const double mx = h[0] / N, mm = h[2] / N;
+  const double vx = std::max(0.0, (h[1] - N * mx * mx) / (N - 1.0));
+  const double vm = std::max(0.0, (h[3] - N * mm * mm) / (N - 1.0));
+  const double cxm = (h[4] - N * mx * mm) / (N - 1.0);
+  const double vy = std::max(0.0, vx - 2.0 * beta * cxm + beta * beta * vm);
+  out[0] = mx - beta * mm;
+  out[1] = std::sqrt(vy / N);
+  out[2] = mx;
+  out[3] = std::sqrt(vx / N);
+  out[4] = vm > 0.0 ? cxm / vm : 0.0;
   return PC_OK;
 }
 

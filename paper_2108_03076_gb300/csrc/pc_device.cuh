@@ -95,6 +95,24 @@ __device__ __forceinline__ void block_normals2(uint32_t b, const Rng2 &g, float2
 // stride is the block size, 32..kBlock threads).
 #define SL(s) R[(s) * blockDim.x]
 
+// Window slot w (0 .. win * d - 1) of this thread: in the shared region
+// (word-interleaved after lay.off_win) or, with GW, in the thread's column
+// of the HBM window (coalesced across the warp for a uniform slot).
+template <bool GW>
+__device__ __forceinline__ float2 win_load(const float2 *R, const Layout &lay, int w) {
+  if constexpr (GW)
+    return lay.gwin[int64_t(w) * lay.gstride + int64_t(blockIdx.x) * blockDim.x + threadIdx.x];
+  else
+    return SL(lay.off_win + w);
+}
+template <bool GW>
+__device__ __forceinline__ void win_store(float2 *R, const Layout &lay, int w, float2 v) {
+  if constexpr (GW)
+    lay.gwin[int64_t(w) * lay.gstride + int64_t(blockIdx.x) * blockDim.x + threadIdx.x] = v;
+  else
+    SL(lay.off_win + w) = v;
+}
+
 template <int D>
 struct PathState {
   static constexpr int kSlots = cache_slots(D) > 0 ? cache_slots(D) : 1;
@@ -205,7 +223,7 @@ __device__ __forceinline__ float2 ffma2(float a, float2 x, float2 y) {
 // into the window slot of t.  With XW the correlated Brownian values
 // X = L W of the date are also kept (window at lay.off_xwin), which the
 // pathwise sensitivities need.
-template <int D, bool XW = false>
+template <int D, bool XW = false, bool GW = false>
 __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev &m,
                                          const Layout &lay, const Rng2 &g, float2 *R,
                                          const float (&Bm)[D * D], const float (&S0)[D],
@@ -243,14 +261,14 @@ __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev
       }
     }
   }
-  const int ws = lay.off_win + (t & (lay.win - 1)) * D;
+  const int ws = (t & (lay.win - 1)) * D;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     const float a = __ldg(m.A + t * D + i);
     float2 x = make_float2(a, a);
 #pragma unroll
     for (int k = 0; k <= i; ++k) x = ffma2(Bm[i * D + k], ps.w[k], x);
-    SL(ws + i) = make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y));
+    win_store<GW>(R, lay, ws + i, make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y)));
   }
   if constexpr (XW) {
     const int xs = lay.off_xwin + (t & (lay.win - 1)) * D;
@@ -286,7 +304,7 @@ __device__ __forceinline__ float cmp_code(int code, float v, float k) {
 
 // Fused multi-asset value (X_LRED) or test (X_LANY) of instruction I at
 // ordinal o for both paths; results of compares are 0/1 int bits.
-template <int D>
+template <int D, bool GW = false>
 __device__ __forceinline__ float2 fused_value(const uint4 &I, int o, const float *pool,
                                               const float2 *R, const ModelDev &m,
                                               const Layout &lay) {
@@ -295,14 +313,14 @@ __device__ __forceinline__ float2 fused_value(const uint4 &I, int o, const float
   const bool any = (I.x & 0xffu) == X_LANY, conj = (A & 1u) != 0;
   const int rop = int(A & 3u);
   const float k = __uint_as_float(I.w);
-  const int base = lay.off_win + (o & (lay.win - 1)) * D;
+  const int base = (o & (lay.win - 1)) * D;
   float2 v = make_float2(0.f, 0.f);
   for (int i = 0; i < n; ++i) {
     int l = int(A >> (10 + 2 * i)) & 3;
     l = l < D ? l : 0;
     float2 s;
     if (o > 0) {
-      s = SL(base + l);
+      s = win_load<GW>(R, lay, base + l);
     } else {
       const float sv = __ldg(m.sval + (o + m.n_hist) * D + l);
       s = make_float2(sv, sv);

@@ -11,7 +11,7 @@ namespace {
 // The next instruction is fetched while the current one executes; jumps
 // fetch their target.  `frontier` (optional) receives the last generated
 // date ordinal: the window holds the simulated dates up to it.
-template <int D>
+template <int D, bool GW = false>
 __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const PriceArgs &a,
                             const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],
                             const float (&S0)[D], int *frontier = nullptr) {
@@ -32,11 +32,11 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
       atomicOr(a.status, 1);
       o = o > m.n ? m.n : -m.n_hist;
     }
-    while (ps.f < o) gen_date<D>(ps.f + 1, ps, m, lay, g, R, Bm, S0);
+    while (ps.f < o) gen_date<D, false, GW>(ps.f + 1, ps, m, lay, g, R, Bm, S0);
   };
   auto read = [&](int o, int l) -> float2 {
     l = l < D ? l : 0;
-    if (o > 0) return SL(lay.off_win + (o & (lay.win - 1)) * D + l);
+    if (o > 0) return win_load<GW>(R, lay, (o & (lay.win - 1)) * D + l);
     const float v = __ldg(m.sval + (o + m.n_hist) * D + l);
     return make_float2(v, v);
   };
@@ -103,7 +103,7 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
       case X_LANY: {
         int o = int(I.y) + t0 - t_now;
         ensure(o);
-        PUSH(fused_value<D>(I, o, pool, R, m, lay));
+        PUSH((fused_value<D, GW>(I, o, pool, R, m, lay)));
         NEXT
       }
       case X_PAYOFF: {
@@ -191,7 +191,7 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
         for (int k = 0;; ++k) {
           int o = int(Dsc.y) + t0 + k - t_now;
           ensure(o);
-          const float2 c = fused_value<D>(Dsc, o, pool, R, m, lay);
+          const float2 c = fused_value<D, GW>(Dsc, o, pool, R, m, lay);
           if (bits(c.x) && !d0) { d0 = true; r0 = lit; }
           if (bits(c.y) && !d1) { d1 = true; r1 = lit; }
           all = __all_sync(kFull, d0 && d1);

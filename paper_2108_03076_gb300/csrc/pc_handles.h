@@ -25,6 +25,9 @@ struct pc_ctx {
   double *d_partials = nullptr;  // tile partials (scratch)
   size_t partial_cap = 0;        // doubles
   unsigned char *d_control = nullptr;  // reduction control block (kControlBytes, zero between launches)
+  float2 *d_gwin = nullptr;      // HBM windows of simulated dates (grow-only)
+  size_t gwin_cap = 0;           // float2 slots
+  int32_t window_mode = 0;       // PC_WINDOW_AUTO / _SHARED / _HBM
   double timeout_s = 300.0;
   int live_objects = 0;
 };
@@ -73,13 +76,17 @@ struct Launch {
   int grid = 0;
   int block = kBlock;
   size_t smem = 0;
+  bool hbm_window = false;  // window in HBM (args.lay.gwin set by the launcher)
 };
 
 // Validate (model, contract, n_paths), resolve the contract's date window for
 // the model and fill the per-contract arguments (everything but the
-// reduction scratch and outputs) and a single-launch shape.
+// reduction scratch and outputs) and a single-launch shape.  With
+// allow_hbm the window may be placed in HBM (pricing kernel only): when the
+// context asks for it, or (automatic mode) when the shared window would
+// leave fewer than 8 resident warps per SM or exceeds PC_MAX_WINDOW.
 pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
-                  uint64_t seed, uint32_t stream, Launch &L);
+                  uint64_t seed, uint32_t stream, Launch &L, bool allow_hbm = false);
 
 // Grow the context's tile-partial scratch to at least `doubles`.
 pc_status ensure_partials(pc_ctx *c, size_t doubles);

@@ -153,8 +153,13 @@ struct Layout {
   int32_t off_cache;  // level caches (n_levels * 4)
   int32_t off_win;    // date window (win * d)
   int32_t off_xwin;   // window of X = L W (win * d), sensitivity kernel only
-  int32_t words;      // total words per thread
+  int32_t words;      // total words per thread in shared memory
   int32_t win;        // window size (power of two)
+  // HBM window (programs whose lookback does not fit shared memory): the
+  // window of thread t of the launch is column t of gwin, slot s at
+  // gwin[s * gstride + t] (gstride = grid * block); null for the shared window.
+  float2 *gwin;
+  int64_t gstride;
 };
 
 constexpr int kBlock = 128;          // largest block of the pricing kernel (32..128 threads)
@@ -212,7 +217,7 @@ cudaError_t launch_debug_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, u
 cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_paths,
                                uint64_t offset, uint32_t k0, uint32_t k1, uint32_t stream,
                                float *out, cudaStream_t s);
-int price_blocks_per_sm(int d, int block, size_t smem_bytes, bool greeks);
+int price_blocks_per_sm(int d, int block, size_t smem_bytes, bool hbm_window);
 
 // Portfolio pricing (one persistent launch per group of contracts with the
 // same underlying count and a similar per-path footprint).  A work unit is a

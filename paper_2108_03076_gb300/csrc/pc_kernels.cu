@@ -23,8 +23,10 @@ namespace {
 
 
 // Tiles of kTilePaths consecutive paths (two per lane: tile*64 + lane and
-// tile*64 + 32 + lane) are handed to warps through an atomic counter.
-template <int D, bool WRITE>
+// tile*64 + 32 + lane) are handed to warps through an atomic counter.  GW:
+// the window of simulated dates lives in HBM (lay.gwin) instead of shared
+// memory, for programs that look back further than shared memory holds.
+template <int D, bool WRITE, bool GW = false>
 __global__ void __launch_bounds__(kBlock) price_kernel(const PriceArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ int last_block;
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(kBlock) price_kernel(const PriceArgs a) {
     g.phi[0] = uint32_t(p0 >> 32);
     g.plo[1] = uint32_t(p1);
     g.phi[1] = uint32_t(p1 >> 32);
-    const float2 x = eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0);
+    const float2 x = eval_path<D, GW>(P, pool, R, a, g, live0, live1, Bm, S0);
     double tp[2] = {0.0, 0.0};
     if (live0) {
       const double xd = double(x.x);
@@ -214,36 +216,52 @@ cudaError_t set_smem(K kern, size_t smem) {
 }  // namespace
 
 cudaError_t launch_price(const PriceArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
-  const bool w = a.out_paths != nullptr;
-#define LAUNCH(DD, WW)                                                             \
+  const bool w = a.out_paths != nullptr, gw = a.lay.gwin != nullptr;
+#define LAUNCH(DD, WW, GG)                                                         \
   do {                                                                             \
-    auto k = price_kernel<DD, WW>;                                                 \
+    auto k = price_kernel<DD, WW, GG>;                                             \
     cudaError_t e = set_smem(k, smem);                                             \
     if (e != cudaSuccess) return e;                                                \
     k<<<grid, block, smem, s>>>(a);                                                \
     return cudaGetLastError();                                                     \
   } while (0)
+#define LAUNCH_D(DD)                                                               \
+  do {                                                                             \
+    if (gw) { if (w) LAUNCH(DD, true, true); else LAUNCH(DD, false, true); }       \
+    else { if (w) LAUNCH(DD, true, false); else LAUNCH(DD, false, false); }        \
+  } while (0)
   switch (a.m.d) {
-    case 1: if (w) LAUNCH(1, true); else LAUNCH(1, false);
-    case 2: if (w) LAUNCH(2, true); else LAUNCH(2, false);
-    case 3: if (w) LAUNCH(3, true); else LAUNCH(3, false);
-    case 4: if (w) LAUNCH(4, true); else LAUNCH(4, false);
+    case 1: LAUNCH_D(1);
+    case 2: LAUNCH_D(2);
+    case 3: LAUNCH_D(3);
+    case 4: LAUNCH_D(4);
     default: return cudaErrorInvalidValue;
   }
+#undef LAUNCH_D
 #undef LAUNCH
 }
 
-int price_blocks_per_sm(int d, int block, size_t smem, bool greeks) {
-  (void)greeks;
+int price_blocks_per_sm(int d, int block, size_t smem, bool hbm_window) {
   int nb = 0;
   cudaError_t e = cudaSuccess;
+#define OCC(DD)                                                                                      \
+  do {                                                                                               \
+    if (hbm_window) {                                                                                \
+      set_smem(price_kernel<DD, false, true>, smem);                                                 \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<DD, false, true>, block, smem); \
+    } else {                                                                                         \
+      set_smem(price_kernel<DD, false, false>, smem);                                                \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<DD, false, false>, block, smem); \
+    }                                                                                                \
+  } while (0)
   switch (d) {
-    case 1: set_smem(price_kernel<1, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<1, false>, block, smem); break;
-    case 2: set_smem(price_kernel<2, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<2, false>, block, smem); break;
-    case 3: set_smem(price_kernel<3, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<3, false>, block, smem); break;
-    case 4: set_smem(price_kernel<4, false>, smem); e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, price_kernel<4, false>, block, smem); break;
+    case 1: OCC(1); break;
+    case 2: OCC(2); break;
+    case 3: OCC(3); break;
+    case 4: OCC(4); break;
     default: return 0;
   }
+#undef OCC
   return e == cudaSuccess ? nb : 0;
 }
 

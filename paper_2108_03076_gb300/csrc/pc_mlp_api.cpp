@@ -54,7 +54,22 @@ struct pc_mlp {
   float g_lr = 0.f;
   uint64_t g_seed = 0;
   std::vector<float> g_w;
+  float *scratch = nullptr;         // caller scratch (mlp_scratch), grow-only
+  size_t scratch_cap = 0;
 };
+
+namespace pc {
+float *mlp_scratch(pc_mlp *N, size_t floats) {
+  if (floats <= N->scratch_cap) return N->scratch;
+  if (wait_stream(N->ctx) != PC_OK) return nullptr;
+  if (N->scratch) cudaFree(N->scratch);
+  N->scratch = nullptr;
+  N->scratch_cap = 0;
+  if (cudaMalloc(&N->scratch, floats * sizeof(float)) != cudaSuccess) return nullptr;
+  N->scratch_cap = floats;
+  return N->scratch;
+}
+}  // namespace pc
 
 namespace {
 
@@ -315,6 +330,7 @@ pc_status pc_mlp_destroy(pc_mlp *N) {
   wait_stream(N->ctx);
   if (N->exec) cudaGraphExecDestroy(N->exec);
   if (N->mem) cudaFree(N->mem);
+  if (N->scratch) cudaFree(N->scratch);
   delete N;
   return PC_OK;
 }

@@ -643,12 +643,7 @@ pc_status analyse_program(const Program &p, int32_t t_now, int32_t n_dates, int3
   if (st != PC_OK) return st;
   int32_t w = 1;
   while (w < lookback + 1) w <<= 1;
-  if (w > PC_MAX_WINDOW) {
-    err = "program looks back " + std::to_string(lookback) + " dates; the engine keeps " +
-          std::to_string(PC_MAX_WINDOW);
-    return PC_ERANGE;
-  }
-  win = w;
+  win = w;  // <= 2 * PC_MAX_DATES: callers decide where such a window can live
   return PC_OK;
 }
 

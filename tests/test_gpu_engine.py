@@ -204,8 +204,14 @@ def test_error_statuses(eng):
     expect_error("PC_ERANGE", pc.pc_price, m12, eng.contract("(mult (model 0 -1) (payoff 1 0 1))"), 100, 1)
     expect_error("PC_ERANGE", pc.pc_price, m12, eng.contract("(payoff 13 0 1)"), 100, 1)
     m400 = eng.model(W.MarketSpec([1.0], [0.2], [[1.0]], 0.0, list(range(1, 401))))
-    expect_error("PC_ERANGE", pc.pc_price, m400, eng.contract("(add (model 0 301) (model 0 1))"), 100, 1)
-    pc.pc_price(m400, eng.contract("(add (model 0 201) (model 0 1))"), 100, 1)   # lookback 200 fits
+    far = eng.contract("(add (model 0 301) (model 0 1))")
+    pc.pc_set_window_mode(eng.ctx, pc.WINDOW_SHARED)      # lookback 300: shared windows keep 256
+    try:
+        expect_error("PC_ERANGE", pc.pc_price, m400, far, 100, 1)
+        pc.pc_price(m400, eng.contract("(add (model 0 201) (model 0 1))"), 100, 1)   # lookback 200 fits
+    finally:
+        pc.pc_set_window_mode(eng.ctx, pc.WINDOW_AUTO)
+    pc.pc_price(m400, far, 100, 1)                         # the HBM window holds it
     expect_error("PC_EINVAL", pc.pc_price, m12, eng.contract("(model 0 1)"), 1, 1)
     expect_error("PC_ENOTPD", pc.pc_model_create, eng.ctx, [1.0, 1.0], [0.2, 0.2],
                  [[1.0, 1.0], [1.0, 1.0]], 0.0, [1])
