@@ -118,8 +118,10 @@ static_assert(sizeof(BridgeOp) == 32, "BridgeOp layout: two 16-byte loads");
 // Philox block caches live in registers: up to cache_slots(d) bisection
 // levels (the ones whose caching saves the most Philox evaluations) get a
 // slot.  With d = 4 a node uses exactly one block, so nothing is shared.
+// More slots save Philox evaluations but cost registers and resident warps;
+// these counts were the fastest measured on GB300 for 365-date barriers.
 constexpr int kMaxCacheSlots = 5;
-constexpr int cache_slots(int d) { return d == 1 ? 5 : d == 2 ? 4 : d == 3 ? 3 : 0; }
+constexpr int cache_slots(int d) { return d == 1 ? 3 : d == 2 ? 2 : d == 3 ? 1 : 0; }
 
 enum : uint16_t {
   BR_ROOT = 1,        // first node (last date): W = sd * z, no endpoint reads
