@@ -71,7 +71,9 @@ Layout make_layout(const Program &p, const ModelHost &H, int32_t win) {
   L.off_cache = L.off_bstack + H.bstack * H.d;  // caches are in registers: no words
   L.off_win = L.off_cache;
   L.win = win;
-  L.words = L.off_win + win * H.d;
+  // slot of ordinal o is o & (win - 1); when the whole grid fits (n < win)
+  // that is o itself, so only slots 0..n are ever touched
+  L.words = L.off_win + std::min(win, H.n + 1) * H.d;
   return L;
 }
 
