@@ -28,6 +28,18 @@ cell corners of prod_axis (f or 1 - f) times the corner entry.  Table
 layout [k - 1][ki][node][i] with node = ((a_0 G + a_1) G + a_2) (asset 0
 slowest), d values per node.
 
+Second-order (gamma) term: with X_i = D_{k+1} S_i(t_{k+1}) - D_k S_i(t_k)
+and any adapted symmetric Gamma(k),
+
+    M2 = sum_{k>=1} alive_k 1/2 sum_ij Gamma_ij(k) (X_i X_j - E_k[X_i X_j]),
+    E_k[X_i X_j] = D_k^2 S_i(t_k) S_j(t_k) (exp(rho_ij sigma_i sigma_j dt_k) - 1)
+
+(the discounted returns D_{k+1} S_{k+1} / (D_k S_k) are lognormal with mean
+1 and E[R_i R_j] = exp(rho_ij sigma_i sigma_j dt)), so E[M2] = 0 as well.
+Gamma comes from the slopes of the multilinear hedge-ratio table: along
+axis j the interpolant's derivative s_ij = d Delta_i / d u_j (u_j = (ln S_j
+- lo_j) / h_j), Gamma_ij = (s_ij / (h_j S_j) + s_ji / (h_i S_i)) / 2.
+
 Network features of a state (the 16 inputs of the learned model):
 ln(S_i / ref_i) for i < 3 (0 beyond d), sigma_i for i < 3, rho, r, the time
 to the next date (years), remaining dates / 5, elapsed dates / 5, knock-in
@@ -130,3 +142,65 @@ def autocall_features(lnS: np.ndarray, ki: np.ndarray, k: int, n: int, sigma: Se
     F[:, 14] = ki_level
     F[:, 15] = 1.0
     return F
+
+
+def table_slopes(table: np.ndarray, lo: np.ndarray, h: np.ndarray, G: int,
+                 y: np.ndarray) -> np.ndarray:
+    """d (interpolated Delta_i) / d u_j on the cell of each point: [N, d, d]
+    (same clamping and cell choice as ``table_lookup``)."""
+    N, d = y.shape
+    u = np.clip((y - lo[None, :]) / h[None, :], 0.0, G - 1.0)
+    a = np.minimum(np.floor(u).astype(np.int64), G - 2)
+    f = u - a
+    out = np.zeros((N, d, d))
+    for corner in range(1 << d):
+        node = np.zeros(N, np.int64)
+        bits = []
+        for ax in range(d):
+            bit = (corner >> (d - 1 - ax)) & 1
+            bits.append(bit)
+            node = node * G + a[:, ax] + bit
+        for j in range(d):
+            wgt = np.ones(N)
+            for ax in range(d):
+                if ax == j:
+                    wgt = wgt * (1.0 if bits[ax] else -1.0)
+                else:
+                    wgt = wgt * (f[:, ax] if bits[ax] else 1.0 - f[:, ax])
+            out[:, :, j] += wgt[:, None] * table[node]
+    return out
+
+
+def gamma_martingale(S: np.ndarray, disc: Sequence[float], alive: np.ndarray, gamma: np.ndarray,
+                     corr: np.ndarray, sigma: Sequence[float], tau: Sequence[float]) -> np.ndarray:
+    """M2 per path; gamma [N, n, d, d] symmetric (entries for k = 0 unused)."""
+    D = np.asarray(disc, dtype=np.float64)
+    sig = np.asarray(sigma, dtype=np.float64)
+    n = alive.shape[1]
+    M2 = np.zeros(S.shape[0])
+    for k in range(1, n):
+        dt = tau[k + 1] - tau[k]
+        c = np.exp(np.asarray(corr) * np.outer(sig, sig) * dt) - 1.0
+        X = D[k + 1] * S[:, k + 1, :] - D[k] * S[:, k, :]
+        q = np.einsum("pi,pij,pj->p", X, gamma[:, k], X)
+        e = D[k] ** 2 * np.einsum("pi,pij,pj,ij->p", S[:, k, :], gamma[:, k], S[:, k, :], c)
+        M2 += np.where(alive[:, k], 0.5 * (q - e), 0.0)
+    return M2
+
+
+def table_gammas(S: np.ndarray, ki: np.ndarray, tables: np.ndarray, lo: np.ndarray, h: np.ndarray,
+                 G: int) -> np.ndarray:
+    """Gamma [N, n, d, d] from the table slopes (zero at t_0)."""
+    N, n1, d = S.shape
+    n = n1 - 1
+    out = np.zeros((N, n, d, d))
+    for k in range(1, n):
+        y = np.log(S[:, k, :])
+        for s in (0, 1):
+            sel = ki[:, k] == bool(s)
+            if not sel.any():
+                continue
+            sl = table_slopes(tables[k - 1, s], lo[k - 1], h[k - 1], G, y[sel])
+            g = sl / (h[k - 1][None, None, :] * S[sel, k, :][:, None, :])
+            out[sel, k] = 0.5 * (g + np.swapaxes(g, 1, 2))
+    return out

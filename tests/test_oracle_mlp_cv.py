@@ -9,7 +9,10 @@ Control variate: the autocall states on hand-made paths, the hedge
 martingale has mean zero for an arbitrary adapted hedge, a European call
 hedged daily with its Black-Scholes delta replicates the payoff (variance
 nearly removed), and multilinear interpolation reproduces multilinear
-functions exactly and clamps outside the grid.
+functions exactly and clamps outside the grid.  Second-order term: mean
+zero for an arbitrary adapted gamma, a quarterly delta+gamma hedge of a
+call (closed-form gamma) beats delta alone, and the table slopes are the
+interpolant's derivatives (central differences).
 """
 import math
 
@@ -180,3 +183,59 @@ def test_feature_layout():
                              [0.2, 0.25, 0.3], 0.5, 0.03, 1.0, 0.05, 1.0, 0.6)
     np.testing.assert_allclose(F[0], [0.1, -0.2, 0.3, 0.2, 0.25, 0.3, 0.5, 0.03, 1.0, 0.6, 0.4, 1.0,
                                       0.05, 1.0, 0.6, 1.0])
+
+
+def test_gamma_martingale_has_mean_zero_for_any_adapted_gamma():
+    corr = np.array([[1, .5, .3], [.5, 1, .4], [.3, .4, 1]])
+    mk = Market([1.0, 1.2, 0.8], [0.3, 0.2, 0.25], corr.tolist(), 0.03, [365, 730, 1095, 1460])
+    S = _paths(mk, 1 << 15, 12)
+    disc = [mk.disc(o) for o in range(mk.n + 1)]
+    tau = [0.0] + [dd / 365.0 for dd in mk.days]
+    g = np.stack([np.einsum("pi,pj->pij", np.cos(S[:, k, :]), np.cos(S[:, k, :])) for k in range(mk.n)], 1)
+    alive = np.ones((len(S), mk.n), bool)
+    M2 = cv.gamma_martingale(S, disc, alive, g, corr, mk.sigma, tau)
+    assert abs(M2.mean()) < 4 * M2.std() / math.sqrt(len(M2))
+    assert M2.std() > 0.01
+
+
+def test_quarterly_delta_gamma_hedge_beats_delta_alone():
+    """A call hedged at 4 dates with Black-Scholes delta, then with delta and
+    gamma (closed-form gamma): the second-order term removes most of what
+    the delta hedge leaves."""
+    K, sig, r = 1.0, 0.3, 0.02
+    days = [91, 182, 273, 365]
+    mk = Market([1.0], [sig], [[1.0]], r, days)
+    tau = np.array([0.0] + [dd / 365.0 for dd in days])
+    S = _paths(mk, 1 << 15, 6)
+    disc = np.exp(-r * tau)
+    x = disc[-1] * np.maximum(S[:, -1, 0] - K, 0.0)
+    n = len(days)
+    dl, gm = np.zeros((len(S), n, 1)), np.zeros((len(S), n, 1, 1))
+    for k in range(n):
+        T = tau[-1] - tau[k]
+        s = S[:, k, 0]
+        d1 = (np.log(s / K) + (r + 0.5 * sig * sig) * T) / (sig * np.sqrt(T))
+        dl[:, k, 0] = [cf.Phi(v) for v in d1]
+        # Gamma of the value in today's money: disc_k * bs gamma
+        gm[:, k, 0, 0] = np.exp(-0.5 * d1 * d1) / np.sqrt(2 * np.pi) / (s * sig * np.sqrt(T)) / disc[k]
+    alive = np.ones((len(S), n), bool)
+    M = cv.hedge_martingale(S, disc, alive, dl)
+    M2 = cv.gamma_martingale(S, disc, alive, gm, np.array([[1.0]]), [sig], tau)
+    v1, v2 = (x - M).var(), (x - M - M2).var()
+    assert v2 < 0.6 * v1, (v1, v2)
+
+
+def test_table_slopes_are_the_derivatives_of_the_interpolant():
+    rng = np.random.default_rng(4)
+    G, d = 5, 3
+    lo, h = np.array([-0.5, 0.0, 0.3]), np.array([0.2, 0.3, 0.1])
+    table = rng.normal(size=(G ** d, d))
+    y = lo + h * rng.uniform(0.05, G - 1.05, size=(200, d))
+    sl = cv.table_slopes(table, lo, h, G, y)
+    eps = 1e-6
+    for j in range(d):
+        yp, ym = y.copy(), y.copy()
+        yp[:, j] += eps * h[j]
+        ym[:, j] -= eps * h[j]
+        fd = (cv.table_lookup(table, lo, h, G, yp) - cv.table_lookup(table, lo, h, G, ym)) / (2 * eps)
+        np.testing.assert_allclose(sl[:, :, j], fd, rtol=1e-6, atol=1e-8)
