@@ -540,7 +540,9 @@ def learned_config(ws) -> dict:
     return {"workload": LEARNED, "contract": "worst_of_autocall_3u_5d", "target_rel_se": TARGET_REL_SE,
             "network": "16-256-256-256-5 softplus, BF16 weights, FP32 accumulation",
             "training_set": "8192 engine-priced states x 128 paths (+6 bumped plans for hedge ratios)",
-            "training_steps": 6000, "table_grid": 12, "parallelism": f"replicas x{ws}",
+            "training_steps": 6000, "table_grid": 12,
+            "betas": "calibrated once per template on a pilot run with its own seed",
+            "parallelism": f"replicas x{ws}",
             "l2": "flushed between steps by a 256 MiB device write"}
 
 
@@ -598,21 +600,27 @@ def run_learned(args):
     b.record(stream)
     torch.cuda.synchronize()
     t_train = a.elapsed_time(b) / 1e3
-    net.tables(model, grid=12)          # first call sizes the network's scratch
+    # betas fixed once for the template (a pilot run on its own seed): any
+    # fixed betas keep the estimate unbiased
+    betas = net.calibrate(model, contract)
+    net.tables(model)                   # first call sizes the network's scratch
     tt = []
     for _ in range(5):
         a, b = ev(), ev()
         a.record(stream)
-        desc, tabs = net.tables(model, grid=12)
+        desc, tabs = net.tables(model)
         b.record(stream)
         torch.cuda.synchronize()
         tt.append(a.elapsed_time(b))
     t_tables = statistics.median(tt) / 1e3
-    # pilot (independent paths): variances and beta
-    (_, scv), (pp, sp), beta = pc.pc_price_cv(model, contract, desc, tabs.data_ptr(), 1 << 18, 0x5EED7001,
-                                                with_beta=True)
-    desc.beta = float(beta)
-    (_, scv_b), _ = pc.pc_price_cv(model, contract, desc, tabs.data_ptr(), 1 << 18, 0x5EED7001)
+    # variances on an independent run: plain, first-order hedge, with second order
+    VS = 0x5EED7001
+    d1, t1 = net.tables(model, gamma=False)
+    (_, s_delta), (pp, sp) = pc.pc_price_cv(model, contract, d1, t1.data_ptr(), 1 << 18, VS)
+    (_, s_gamma), _ = pc.pc_price_cv(model, contract, desc, tabs.data_ptr(), 1 << 18, VS)
+    if s_gamma >= s_delta:          # keep the first-order control alone
+        desc, tabs = d1, t1
+    scv_b = min(s_gamma, s_delta)
     n_plain = int(math.ceil((sp * math.sqrt(1 << 18) / (TARGET_REL_SE * abs(pp))) ** 2))
     n_cv = int(math.ceil((scv_b * math.sqrt(1 << 18) / (TARGET_REL_SE * abs(pp))) ** 2))
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
@@ -648,8 +656,7 @@ def run_learned(args):
     # e2e through the public API: tables from the trained network + priced to the target
     t0 = time.perf_counter()
     for _ in range(3):
-        d2, t2 = net.tables(model, grid=12)
-        d2.beta = desc.beta
+        d2, t2 = net.tables(model, gamma=bool(desc.use_gamma))
         pc.pc_price_cv(model, contract, d2, t2.data_ptr(), n_cv, w.seed)
     e2e = (time.perf_counter() - t0) / 3
     # surrogate: the network's value at the spot
@@ -666,8 +673,10 @@ def run_learned(args):
         "plain_mc": {"contracts_per_sec": ws / t_plain, "paths": n_plain, "ms": 1e3 * t_plain,
                      "price": plain_price, "stderr": plain_se},
         "learned_cv": {"paths": n_cv, "ms_pricing": statistics.median(tc_ms), "ms_tables": 1e3 * t_tables,
-                       "price": cv_price, "stderr": cv_se, "beta": desc.beta,
-                       "variance_ratio": (sp / scv_b) ** 2, "variance_ratio_beta1": (sp / scv) ** 2},
+                       "price": cv_price, "stderr": cv_se,
+                       "second_order_term": bool(desc.use_gamma), "beta": desc.beta, "beta2": desc.beta2,
+                       "variance_ratio": (sp / scv_b) ** 2,
+                       "variance_ratio_first_order_only": (sp / s_delta) ** 2},
         "gpu_time_ratio_plain_over_cv": t_plain / t_cv,
         "training": {"data_s_wall": t_data, "train_s_gpu": t_train, "samples": len(data.x)},
         "surrogate": {"value": surrogate, "mc_price": plain_price,

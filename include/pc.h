@@ -479,16 +479,24 @@ pc_status pc_mlp_train(pc_mlp *net, const float *d_x, const float *d_t, size_t n
  * pricing kernel adds to each path's payoff X the discounted gains of a
  * hedge held over [t_k, t_{k+1}] while the contract is alive,
  *   M = sum_k alive_k sum_i Delta_i(k) (D_{k+1} S_i(t_{k+1}) - D_k S_i(t_k)),
- * and reports Y = X - beta M.  The D S_i are martingales and every Delta_i(k)
- * depends only on the path up to t_k, so E[M] = 0: Y is unbiased for any
- * hedge ratios and any fixed beta, and its variance is small when the
- * ratios are close to the contract's sensitivities.  Hedge ratios at t_k (k >= 1) come from a
+ * and reports Y = X - beta M - beta2 M2.  The D S_i are martingales and
+ * every Delta_i(k) depends only on the path up to t_k, so E[M] = 0: Y is
+ * unbiased for any hedge ratios and any fixed betas, and its variance is
+ * small when the ratios are close to the contract's sensitivities.  The
+ * optional second-order term (use_gamma) is
+ *   M2 = sum_{k>=1} alive_k 1/2 sum_ij Gamma_ij(k) (X_i X_j - E_k[X_i X_j]),
+ * X_i = D_{k+1} S_i(t_{k+1}) - D_k S_i(t_k), with E_k[X_i X_j] =
+ * D_k^2 S_i S_j (exp(rho_ij sigma_i sigma_j (tau_{k+1} - tau_k)) - 1) in
+ * closed form and Gamma from the slopes of the table's interpolant
+ * (Gamma_ij = (s_ij / (h_j S_j) + s_ji / (h_i S_i)) / 2, s_ij = d Delta_i /
+ * d u_j), so E[M2] = 0 as well.  Hedge ratios at t_k (k >= 1) come from a
  * table over y = ln S per date and knock-in state, read by multilinear
  * interpolation (per axis u = clamp((y - lo) / h, 0, G - 1),
  * a = min(floor(u), G - 2), f = u - a), at t_0 from delta0.  Tables are
  * filled by a trained network (pc_cv_tables) or by the caller.  Table
- * layout (floats): [(k - 1) * 2 + ki][node][i], node = ((a_0 G + a_1) G + a_2)
- * (axis 0 slowest), k = 1..n-1, ki = knock-in flag, i < d.
+ * layout (floats, 16-byte aligned): [(k - 1) * 2 + ki][node][4] with the d
+ * ratios first in each group of four, node = ((a_0 G + a_1) G + a_2) (axis
+ * 0 slowest), k = 1..n-1, ki = knock-in flag.
  * Not in the paper (an extension of its Monte Carlo valuation). */
 #define PC_CV_MAX_DATES 32
 
@@ -501,7 +509,9 @@ typedef struct pc_cv_desc {
   float lo[PC_CV_MAX_DATES][3];  /* table axes over ln S: row k - 1 = date k */
   float h[PC_CV_MAX_DATES][3];
   float delta0[3];           /* hedge ratios at t_0                          */
-  float beta;                /* Y = X - beta M (pc_cv_grid sets 1)           */
+  float beta;                /* Y = X - beta M - beta2 M2 (pc_cv_grid: 1)    */
+  float beta2;               /* (pc_cv_grid: 1)                              */
+  int32_t use_gamma;         /* 1: include M2 (pc_cv_grid: 0)                */
 } pc_cv_desc;
 
 /* Fill d, n, grid, lo and h from the model: axis i at date k is centred on
@@ -510,7 +520,7 @@ typedef struct pc_cv_desc {
  * fills the tables itself).  Errors: PC_EINVAL, PC_ELIMIT (d > 3 or more
  * than PC_CV_MAX_DATES dates). */
 pc_status pc_cv_grid(const pc_model *model, int32_t grid, float width_sd, pc_cv_desc *desc);
-/* Floats of the tables of desc: (n - 1) * 2 * grid^d * d. */
+/* Floats of the tables of desc: (n - 1) * 2 * grid^d * 4. */
 pc_status pc_cv_table_size(const pc_cv_desc *desc, size_t *floats);
 /* Evaluate the network (16 inputs, outputs value and hedge ratios) at every
  * table node and at the spot and write d_tables (device, cap_floats) and
@@ -521,15 +531,20 @@ pc_status pc_cv_table_size(const pc_cv_desc *desc, size_t *floats);
  * Errors: PC_EINVAL (widths other than 16 in / 5 out, cap too small). */
 pc_status pc_cv_tables(pc_mlp *net, const pc_model *model, pc_cv_desc *desc, float *d_tables,
                        size_t cap_floats);
-/* Price with the control variate: out[0..4] (host) = price and standard
- * error of Y = X - desc->beta M, then of X on the same paths (pc_price's
- * estimate with this seed), then the variance-minimising beta
- * Cov(X, M) / Var(M) measured on these paths (to fix beta for a later,
- * independent run).  d_tables: device tables laid out as above.  Blocks
- * until done.
+/* Price with the control variate: out[0..3] (host) = price and standard
+ * error of Y = X - beta M - beta2 M2 (betas from desc), then of X on the
+ * same paths (pc_price's estimate with this seed).  d_tables: device
+ * tables laid out as above.  Blocks until done.
  * Errors: as pc_price; PC_EINVAL for a desc that does not match the model. */
 pc_status pc_price_cv(const pc_model *model, const pc_contract *contract, const pc_cv_desc *desc,
                       const float *d_tables, uint64_t n_paths, uint64_t seed, double *out);
+/* Pilot run: the variance-minimising betas measured on n_paths (>= 16)
+ * paths under `seed` (use an independent seed or stream for the priced run
+ * so that its betas are fixed): beta[0] (and beta[1] with use_gamma, else
+ * 0) solve Cov([M, M2]) beta = Cov(X, [M, M2]).  Blocks until done.
+ * Errors: as pc_price_cv. */
+pc_status pc_cv_beta(const pc_model *model, const pc_contract *contract, const pc_cv_desc *desc,
+                     const float *d_tables, uint64_t n_paths, uint64_t seed, double *beta);
 
 /* ------------------------------------------------------------------------ */
 /* Parity probes (same device functions as the pricing kernel)               */
@@ -556,8 +571,9 @@ pc_status pc_debug_greeks_paths(const pc_model *model, const pc_contract *contra
                                 uint64_t n_paths, uint64_t path_offset, uint64_t seed,
                                 int32_t underlying, double *d_out, float *d_paths);
 
-/* Per path i < n_paths (paths 0.., Philox stream 0): d_xm[2i] = payoff X,
- * d_xm[2i + 1] = hedge gain M of pc_price_cv (device floats).
+/* Per path i < n_paths (paths 0.., Philox stream 0): d_xm[3i] = payoff X,
+ * d_xm[3i + 1] = hedge gain M, d_xm[3i + 2] = second-order gain M2 of
+ * pc_price_cv (device floats; M2 computed whatever desc->use_gamma).
  * Asynchronous on the context's stream. */
 pc_status pc_debug_cv_paths(const pc_model *model, const pc_contract *contract, const pc_cv_desc *desc,
                             const float *d_tables, uint64_t n_paths, uint64_t seed, float *d_xm);

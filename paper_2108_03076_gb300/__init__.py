@@ -77,7 +77,8 @@ class CvDesc(C.Structure):
     _fields_ = [("d", C.c_int32), ("n", C.c_int32), ("grid", C.c_int32), ("ref", C.c_float * 3),
                 ("call_level", C.c_float), ("ki_level", C.c_float), ("coupon", C.c_float),
                 ("lo", (C.c_float * 3) * CV_MAX_DATES), ("h", (C.c_float * 3) * CV_MAX_DATES),
-                ("delta0", C.c_float * 3), ("beta", C.c_float)]
+                ("delta0", C.c_float * 3), ("beta", C.c_float), ("beta2", C.c_float),
+                ("use_gamma", C.c_int32)]
 
 
 class LaunchInfo(C.Structure):
@@ -136,6 +137,7 @@ _SIGS = {
     "pc_cv_table_size": [C.POINTER(CvDesc), C.POINTER(SZ)],
     "pc_cv_tables": [VP, VP, C.POINTER(CvDesc), VP, SZ],
     "pc_price_cv": [VP, VP, C.POINTER(CvDesc), VP, U64, U64, PD],
+    "pc_cv_beta": [VP, VP, C.POINTER(CvDesc), VP, U64, U64, PD],
     "pc_debug_cv_paths": [VP, VP, C.POINTER(CvDesc), VP, U64, U64, VP],
     "pc_greeks": [VP, VP, U64, U64, PD, PD, PD, PD],
     "pc_debug_philox": [VP, VP, U32, U32, VP, SZ],
@@ -435,17 +437,21 @@ def pc_cv_tables(net: int, model: int, desc: CvDesc, d_tables: int, cap_floats: 
     _check(lib().pc_cv_tables(VP(net), VP(model), C.byref(desc), VP(d_tables), int(cap_floats)))
 
 
-def pc_price_cv(model: int, contract: int, desc: CvDesc, d_tables: int, n_paths: int, seed: int,
-                with_beta: bool = False):
-    """(price, se) of the control-variate estimate Y = X - desc.beta M, then
-    (price, se) of the plain estimate on the same paths; with_beta adds the
-    variance-minimising beta measured on these paths."""
-    out = np.zeros(5)
+def pc_price_cv(model: int, contract: int, desc: CvDesc, d_tables: int, n_paths: int, seed: int):
+    """(price, se) of the control-variate estimate Y = X - beta M - beta2 M2,
+    then (price, se) of the plain estimate on the same paths."""
+    out = np.zeros(4)
     _check(lib().pc_price_cv(VP(model), VP(contract), C.byref(desc), VP(d_tables), int(n_paths), int(seed),
                              _ptr(out, C.c_double)))
-    if with_beta:
-        return (out[0], out[1]), (out[2], out[3]), out[4]
     return (out[0], out[1]), (out[2], out[3])
+
+
+def pc_cv_beta(model: int, contract: int, desc: CvDesc, d_tables: int, n_paths: int, seed: int):
+    """Variance-minimising (beta, beta2) measured on a pilot run."""
+    out = np.zeros(2)
+    _check(lib().pc_cv_beta(VP(model), VP(contract), C.byref(desc), VP(d_tables), int(n_paths), int(seed),
+                            _ptr(out, C.c_double)))
+    return float(out[0]), float(out[1])
 
 
 def pc_debug_cv_paths(model: int, contract: int, desc: CvDesc, d_tables: int, n_paths: int, seed: int,

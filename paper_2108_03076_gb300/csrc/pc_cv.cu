@@ -6,9 +6,13 @@
 // kept in the window and accumulates the discounted hedge gains
 //   M = sum_{k<n} alive_k sum_i Delta_i(k) (D_{k+1} S_i(t_{k+1}) - D_k S_i(t_k))
 // with Delta from a table over ln S (multilinear interpolation) per date and
-// knock-in state.  Every factor of a term is known at t_k, so E[M] = 0 and
-// Y = X - beta M estimates the same price for any fixed beta; the tile sums
-// carry X, X^2, M, M^2, X M, from which the host forms any beta's estimate.
+// knock-in state.  Every factor of a term is known at t_k, so E[M] = 0.  An
+// optional second-order term M2 (gamma from the table's slopes, the
+// quadratic moments of the discounted returns in closed form) also has mean
+// zero, and Y = X - beta M - beta2 M2 estimates the same price for any fixed
+// betas.  The tile sums carry X, X^2, Y, Y^2, or in the pilot mode the
+// eight first and second moments of X, M, M2 that the variance-minimising
+// betas need.
 // A hedge period whose end date the warp never generated (every lane's
 // program stopped before it) is skipped: that decision depends only on
 // information at t_k of this and of independent paths, so the terms kept are
@@ -23,11 +27,13 @@ namespace pc {
 namespace {
 
 // Multilinear interpolation of the d hedge ratios at ln S (given as
-// l2 = log2 S: the axis coordinate is u = l2 ln2 / h - lo / h).
-template <int D>
+// l2 = log2 S: the axis coordinate is u = l2 ln2 / h - lo / h), and with
+// SLOPES the interpolant's derivatives s[i][j] = d Delta_i / d u_j on the
+// cell (from the same corner values).
+template <int D, bool SLOPES>
 __device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, const float (&l2)[D],
-                                            float (&delta)[D]) {
-  const float *tab = c.tables + (size_t(k - 1) * 2 + ki) * size_t(c.nodes) * D;
+                                            float (&delta)[D], float (&s)[D][D]) {
+  const float4 *tab = reinterpret_cast<const float4 *>(c.tables) + (size_t(k - 1) * 2 + ki) * size_t(c.nodes);
   int a[D];
   float f[D];
   const int G = c.grid;
@@ -40,56 +46,122 @@ __device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, cons
     a[i] = ai;
     f[i] = u - float(ai);
     delta[i] = 0.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) s[i][j] = 0.f;
   }
 #pragma unroll
   for (int corner = 0; corner < (1 << D); ++corner) {
-    float wgt = 1.f;
+    float g[D];
     int node = 0;
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
       const int bit = (corner >> (D - 1 - ax)) & 1;
-      wgt *= bit ? f[ax] : 1.f - f[ax];
+      g[ax] = bit ? f[ax] : 1.f - f[ax];
       node = node * G + a[ax] + bit;
     }
+    const float4 v4 = __ldg(tab + node);  // one 16-byte load per corner
+    const float v[3] = {v4.x, v4.y, v4.z};
+    float wgt = 1.f;
 #pragma unroll
-    for (int i = 0; i < D; ++i) delta[i] = fmaf(wgt, __ldg(tab + size_t(node) * D + i), delta[i]);
+    for (int ax = 0; ax < D; ++ax) wgt *= g[ax];
+#pragma unroll
+    for (int i = 0; i < D; ++i) delta[i] = fmaf(wgt, v[i], delta[i]);
+    if (SLOPES) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float wj = ((corner >> (D - 1 - j)) & 1) ? 1.f : -1.f;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax)
+          if (ax != j) wj *= g[ax];
+#pragma unroll
+        for (int i = 0; i < D; ++i) s[i][j] = fmaf(wj, v[i], s[i][j]);
+      }
+    }
   }
 }
 
-// Hedge gains of one path: S at ordinal o is s(o, i) (o = 0: spot).
-template <int D, typename SFn>
-__device__ float hedge_gain(const CvArgs &c, const ModelDev &m, int frontier, SFn s) {
-  float M = 0.f;
-  bool alive = true;
-  int ki = 0;
-  for (int k = 0; k < c.n; ++k) {
-    if (k >= 1) {
-      float worst = s(k, 0) * c.inv_ref[0];
+// Hedge gains of the lane's two paths (q = 0, 1): first order M and second
+// order M2.  S of path q at ordinal o is s(q, o, i) (o = 0: spot).  Both
+// paths are worked in step (independent table reads in flight together);
+// a dead path's terms are computed and discarded.
+template <int D, bool GAMMA, typename SFn>
+__device__ void hedge_gain2(const CvArgs &c, const ModelDev &m, int frontier, SFn s, float (&M)[2],
+                            float (&M2)[2]) {
+  bool alive[2] = {true, true};
+  int ki[2] = {0, 0};
 #pragma unroll
-      for (int i = 1; i < D; ++i) worst = fminf(worst, s(k, i) * c.inv_ref[i]);
-      ki |= worst <= c.ki_level ? 1 : 0;
-      alive = alive && !(worst >= c.call_level);
+  for (int q = 0; q < 2; ++q) M[q] = M2[q] = 0.f;
+  for (int k = 0; k < c.n; ++k) {
+    if (k + 1 > frontier) break;
+    if (k >= 1) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float worst = s(q, k, 0) * c.inv_ref[0];
+#pragma unroll
+        for (int i = 1; i < D; ++i) worst = fminf(worst, s(q, k, i) * c.inv_ref[i]);
+        ki[q] |= worst <= c.ki_level ? 1 : 0;
+        alive[q] = alive[q] && !(worst >= c.call_level);
+      }
     }
-    if (!alive || k + 1 > frontier) break;
-    float delta[D];
+    if (!alive[0] && !alive[1]) break;
+    const float d0 = __ldg(m.disc + k + m.n_hist), d1 = __ldg(m.disc + k + 1 + m.n_hist);
+    float delta[2][D], sl[2][D][D];
     if (k == 0) {
 #pragma unroll
-      for (int i = 0; i < D; ++i) delta[i] = c.delta0[i];
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int i = 0; i < D; ++i) delta[q][i] = c.delta0[i];
     } else {
-      float l2[D];
 #pragma unroll
-      for (int i = 0; i < D; ++i) l2[i] = __log2f(s(k, i));
-      table_delta<D>(c, k, ki, l2, delta);
+      for (int q = 0; q < 2; ++q) {
+        float l2[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) l2[i] = __log2f(s(q, k, i));
+        table_delta<D, GAMMA>(c, k, ki[q], l2, delta[q], sl[q]);
+      }
     }
-    const float d0 = __ldg(m.disc + k + m.n_hist), d1 = __ldg(m.disc + k + 1 + m.n_hist);
 #pragma unroll
-    for (int i = 0; i < D; ++i) M = fmaf(delta[i], d1 * s(k + 1, i) - d0 * s(k, i), M);
+    for (int q = 0; q < 2; ++q) {
+      float X[D], Sk[D], inv[D];
+      float dm = 0.f;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        Sk[i] = s(q, k, i);
+        X[i] = d1 * s(q, k + 1, i) - d0 * Sk[i];
+        dm = fmaf(delta[q][i], X[i], dm);
+        inv[i] = __frcp_rn(Sk[i]);
+      }
+      M[q] += alive[q] ? dm : 0.f;
+      if (GAMMA && k >= 1) {
+        // Gamma = sym(t), t_ij = s_ij / (h_j S_j); the quadratic forms of
+        // a symmetric weight need only t itself
+        float qf = 0.f, e = 0.f;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          float rq = 0.f, re = 0.f;
+#pragma unroll
+          for (int j = 0; j < D; ++j) {
+            const float t = sl[q][i][j] * c.inv_h[k - 1][j] * inv[j];
+            rq = fmaf(t, X[j], rq);
+            re = fmaf(t, Sk[j] * c.cq[k][i * kCvMaxD + j], re);
+          }
+          qf = fmaf(X[i], rq, qf);
+          e = fmaf(Sk[i], re, e);
+        }
+        M2[q] += alive[q] ? 0.5f * (qf - d0 * d0 * e) : 0.f;
+      }
+    }
   }
-  return M;
 }
 
-template <int D, bool WRITE>
+// MODE bits: kCvWrite (per-path X, M, M2 out), kCvGamma (second-order
+// term), kCvPilot (moment sums for the betas instead of X, X^2, Y, Y^2).
+constexpr int kCvWrite = 1, kCvGamma = 2, kCvPilot = 4;
+
+template <int D, int MODE>
 __global__ void __launch_bounds__(kBlock) cv_kernel(const PriceArgs a, const CvArgs c) {
+  constexpr bool WRITE = (MODE & kCvWrite) != 0, GAMMA = (MODE & kCvGamma) != 0,
+                 PILOT = (MODE & kCvPilot) != 0;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ int last_block;
   uint4 *P = reinterpret_cast<uint4 *>(smem);
@@ -122,37 +194,59 @@ __global__ void __launch_bounds__(kBlock) cv_kernel(const PriceArgs a, const CvA
     g.phi[1] = uint32_t(p1 >> 32);
     int frontier = 0;
     const float2 x = eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0, &frontier);
-    float Mv[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      auto s = [&](int o, int i) -> float {
-        if (o == 0) return S0[i];
-        const float2 v = SL(lay.off_win + (o & (lay.win - 1)) * D + i);
-        return q ? v.y : v.x;
-      };
-      Mv[q] = hedge_gain<D>(c, a.m, frontier, s);
-    }
-    double tp[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    float Mv[2], M2v[2];
+    auto s = [&](int q, int o, int i) -> float {
+      if (o == 0) return S0[i];
+      const float2 v = SL(lay.off_win + (o & (lay.win - 1)) * D + i);
+      return q ? v.y : v.x;
+    };
+    hedge_gain2<D, GAMMA>(c, a.m, frontier, s, Mv, M2v);
     const float xs[2] = {x.x, x.y};
     const bool live[2] = {live0, live1};
+    if (WRITE) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      if (!live[q]) continue;
-      const double xd = double(xs[q]), md = double(Mv[q]);
-      tp[0] += xd;
-      tp[1] = fma(xd, xd, tp[1]);
-      tp[2] += md;
-      tp[3] = fma(md, md, tp[3]);
-      tp[4] = fma(xd, md, tp[4]);
-      if (WRITE) {
+      for (int q = 0; q < 2; ++q) {
+        if (!live[q]) continue;
         const uint64_t i = q ? i1 : i0;
-        a.out_paths[2 * i] = xs[q];
-        a.out_paths[2 * i + 1] = Mv[q];
+        a.out_paths[3 * i] = xs[q];
+        a.out_paths[3 * i + 1] = Mv[q];
+        a.out_paths[3 * i + 2] = M2v[q];
       }
     }
+    if (PILOT) {
+      double tp[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int v = 0; v < 5; ++v) tp[v] = warp_sum(tp[v]);
-    finish_tile<5>(a, tile, tp, lane);
+      for (int q = 0; q < 2; ++q) {
+        if (!live[q]) continue;
+        const double xd = double(xs[q]), md = double(Mv[q]), m2 = double(M2v[q]);
+        tp[0] += xd;
+        tp[1] += md;
+        tp[2] += m2;
+        tp[3] = fma(xd, md, tp[3]);
+        tp[4] = fma(xd, m2, tp[4]);
+        tp[5] = fma(md, md, tp[5]);
+        tp[6] = fma(m2, m2, tp[6]);
+        tp[7] = fma(md, m2, tp[7]);
+      }
+#pragma unroll
+      for (int v = 0; v < 8; ++v) tp[v] = warp_sum(tp[v]);
+      finish_tile<8>(a, tile, tp, lane);
+    } else {
+      double tp[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (!live[q]) continue;
+        const double xd = double(xs[q]);
+        const double yd = double(xs[q] - c.beta * Mv[q] - c.beta2 * M2v[q]);
+        tp[0] += xd;
+        tp[1] = fma(xd, xd, tp[1]);
+        tp[2] += yd;
+        tp[3] = fma(yd, yd, tp[3]);
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) tp[v] = warp_sum(tp[v]);
+      finish_tile<4>(a, tile, tp, lane);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -202,14 +296,15 @@ __global__ void cv_features_kernel(const CvArgs c, CvFeatureArgs fa, float *X, s
 }
 
 // Table entries from the network outputs (value, then one hedge ratio per
-// underlying) of the rows above; the last row's ratios are delta0.
+// underlying) of the rows above, four floats per node (d used); the last
+// row's ratios are delta0.
 __global__ void cv_scatter_kernel(const float *Y, int out_w, size_t rows, int d, float *tables,
                                   float *delta0) {
   const size_t r = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
   if (r >= rows) return;
   for (int i = 0; i < d; ++i) {
     const float v = Y[r * out_w + 1 + i];
-    if (r + 1 < rows) tables[r * d + i] = v;
+    if (r + 1 < rows) tables[r * 4 + i] = v;
     else delta0[i] = v;
   }
 }
@@ -219,44 +314,81 @@ cudaError_t set_smem(K kern, size_t smem) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
 }
 
-}  // namespace
-
-cudaError_t launch_cv(const PriceArgs &a, const CvArgs &c, int grid, int block, size_t smem, cudaStream_t s) {
-  const bool w = a.out_paths != nullptr;
-#define CVL(DD, WW)                                  \
+template <int D>
+cudaError_t launch_cv_d(int mode, const PriceArgs &a, const CvArgs &c, int grid, int block, size_t smem,
+                        cudaStream_t s) {
+#define CVL(MM)                                      \
   do {                                               \
-    auto k = cv_kernel<DD, WW>;                      \
+    auto k = cv_kernel<D, MM>;                       \
     cudaError_t e = set_smem(k, smem);               \
     if (e != cudaSuccess) return e;                  \
     k<<<grid, block, smem, s>>>(a, c);               \
     return cudaGetLastError();                       \
   } while (0)
-  switch (a.m.d) {
-    case 1: if (w) CVL(1, true); else CVL(1, false);
-    case 2: if (w) CVL(2, true); else CVL(2, false);
-    case 3: if (w) CVL(3, true); else CVL(3, false);
+  switch (mode) {
+    case 0: CVL(0);
+    case kCvGamma: CVL(kCvGamma);
+    case kCvPilot: CVL(kCvPilot);
+    case kCvPilot | kCvGamma: CVL(kCvPilot | kCvGamma);
+    case kCvWrite | kCvGamma: CVL(kCvWrite | kCvGamma);
     default: return cudaErrorInvalidValue;
   }
 #undef CVL
 }
 
-int cv_blocks_per_sm(int d, int block, size_t smem) {
+int cv_mode(const PriceArgs &a, const CvArgs &c) {
+  if (a.out_paths) return kCvWrite | kCvGamma;
+  return (c.use_gamma ? kCvGamma : 0) | (c.pilot ? kCvPilot : 0);
+}
+
+}  // namespace
+
+cudaError_t launch_cv(const PriceArgs &a, const CvArgs &c, int grid, int block, size_t smem, cudaStream_t s) {
+  const int mode = cv_mode(a, c);
+  switch (a.m.d) {
+    case 1: return launch_cv_d<1>(mode, a, c, grid, block, smem, s);
+    case 2: return launch_cv_d<2>(mode, a, c, grid, block, smem, s);
+    case 3: return launch_cv_d<3>(mode, a, c, grid, block, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+namespace {
+int cv_occupancy(uint64_t v, int block, size_t smem) {
+  const int d = int(v & 0xff), mode = int((v >> 8) & 0xff);
   int nb = 0;
   cudaError_t e = cudaErrorInvalidValue;
-#define OCC(DD)                                                                        \
-  do {                                                                                 \
-    e = set_smem(cv_kernel<DD, false>, smem);                                          \
-    if (e == cudaSuccess)                                                              \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cv_kernel<DD, false>, block, smem); \
+#define OCC(DD, MM)                                                                      \
+  do {                                                                                   \
+    e = set_smem(cv_kernel<DD, MM>, smem);                                               \
+    if (e == cudaSuccess)                                                                \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cv_kernel<DD, MM>, block, smem); \
+  } while (0)
+#define OCC_D(DD)                                                      \
+  do {                                                                 \
+    switch (mode) {                                                    \
+      case 0: OCC(DD, 0); break;                                       \
+      case kCvGamma: OCC(DD, kCvGamma); break;                         \
+      case kCvPilot: OCC(DD, kCvPilot); break;                         \
+      default: OCC(DD, kCvPilot | kCvGamma); break;                    \
+    }                                                                  \
   } while (0)
   switch (d) {
-    case 1: OCC(1); break;
-    case 2: OCC(2); break;
-    case 3: OCC(3); break;
+    case 1: OCC_D(1); break;
+    case 2: OCC_D(2); break;
+    case 3: OCC_D(3); break;
     default: return 0;
   }
+#undef OCC_D
 #undef OCC
   return e == cudaSuccess ? nb : 0;
+}
+}  // namespace
+
+int cv_blocks_per_sm(int d, int block, size_t smem, const CvArgs &c) {
+  PriceArgs dummy{};
+  const int mode = cv_mode(dummy, c);
+  return occupancy_memo((uint64_t(2) << 32) | (uint64_t(mode) << 8) | uint64_t(d), block, smem, cv_occupancy);
 }
 
 cudaError_t launch_cv_features(const CvArgs &c, const CvFeatureArgs &fa, float *X, size_t rows,

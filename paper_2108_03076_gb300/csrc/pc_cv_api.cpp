@@ -2,6 +2,7 @@
 // network evaluation at the table nodes, and the control-variate launch.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -36,7 +37,7 @@ pc_status check_desc(const pc_model *m, const pc_cv_desc *c) {
   return PC_OK;
 }
 
-CvArgs device_args(const pc_cv_desc *c, const float *tables) {
+CvArgs device_args(const pc_cv_desc *c, const float *tables, const ModelHost &H, bool pilot) {
   CvArgs a;
   std::memset(&a, 0, sizeof(a));
   a.tables = tables;
@@ -58,17 +59,31 @@ CvArgs device_args(const pc_cv_desc *c, const float *tables) {
       const double h = c->h[k][i] > 0.f ? double(c->h[k][i]) : 1.0;
       a.ua[k][i] = float(std::log(2.0) / h);
       a.ub[k][i] = float(double(c->lo[k][i]) / h);
+      a.inv_h[k][i] = float(1.0 / h);
     }
+  // closed-form second moments of the discounted returns per period
+  for (int k = 0; k < std::min(H.n, kCvMaxDates); ++k) {
+    const double dt = double(H.tau[k + 1]) - double(H.tau[k]);
+    for (int i = 0; i < H.d && i < kCvMaxD; ++i)
+      for (int j = 0; j < H.d && j < kCvMaxD; ++j)
+        a.cq[k][i * kCvMaxD + j] =
+            float(std::expm1(H.corr[size_t(i) * H.d + j] * H.sigma[i] * H.sigma[j] * dt));
+  }
   for (int i = 0; i < kCvMaxD; ++i) a.inv_ref[i] = c->ref[i] > 0.f ? float(1.0 / double(c->ref[i])) : 0.f;
+  a.beta = c->beta;
+  a.beta2 = c->use_gamma ? c->beta2 : 0.f;
+  a.use_gamma = c->use_gamma ? 1 : 0;
+  a.pilot = pilot ? 1 : 0;
   return a;
 }
 
 // The pricing launch with a window holding every date 1..n.
 pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c, const float *tables,
-                    uint64_t n_paths, uint64_t seed, double *d_out, float *d_xm) {
+                    uint64_t n_paths, uint64_t seed, double *d_out, float *d_xm, bool pilot) {
   pc_status s = check_desc(m, c);
   if (s != PC_OK) return s;
   if (!tables && c->n > 1) return fail(PC_EINVAL, "null tables");
+  if (reinterpret_cast<uintptr_t>(tables) & 15u) return fail(PC_EINVAL, "tables must be 16-byte aligned");
   Launch L;
   s = prepare(m, k, n_paths, 0, seed, 0, L);
   if (s != PC_OK) return s;
@@ -77,22 +92,22 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
   int32_t win = lay.win;
   while (win < c->n + 1) win *= 2;
   lay.win = win;
-  lay.words = lay.off_win + win * c->d;
+  lay.words = lay.off_win + std::min(win, c->n + 1) * c->d;  // slots 0..n (o & (win - 1) = o)
   const size_t pool = (k->prog.pool.size() + 3) & ~size_t(3);
   int block = 0, best = 0;
   size_t smem = 0;
   for (int b = kBlock; b >= 32; b /= 2) {
     const size_t sm = price_smem_bytes(k->prog.code.size(), pool, lay.words, b);
     if (sm + kStaticSmemReserve > size_t(ctx->max_smem)) continue;
-    const int warps = cv_blocks_per_sm(c->d, b, sm) * (b / 32);
+    const int warps = cv_blocks_per_sm(c->d, b, sm, device_args(c, tables, m->H, pilot)) * (b / 32);
     if (warps > best) { best = warps; block = b; smem = sm; }
   }
   if (!block) return fail(PC_ELIMIT, "program + per-path state with the control variate exceed shared memory");
   PriceArgs a = L.args;
   a.lay = lay;
-  a.width = 5;
+  a.width = pilot ? 8 : 4;
   reduction_chunks(a.n_tiles, a.chunk_tiles, a.n_chunks);
-  s = ensure_partials(ctx, size_t(a.n_tiles) * 5);
+  s = ensure_partials(ctx, size_t(a.n_tiles) * size_t(a.width));
   if (s != PC_OK) return s;
   a.tile_partials = ctx->d_partials;
   a.control = ctx->d_control;
@@ -101,7 +116,7 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
   const uint64_t need = (a.n_tiles + block / 32 - 1) / (block / 32);
   const int grid = int(std::min<uint64_t>(uint64_t(ctx->sm_count) * best / (block / 32), need));
   CU(cudaSetDevice(ctx->device), "cudaSetDevice");
-  CU(launch_cv(a, device_args(c, tables), grid, block, smem, ctx->stream), "control-variate kernel");
+  CU(launch_cv(a, device_args(c, tables, m->H, pilot), grid, block, smem, ctx->stream), "control-variate kernel");
   return PC_OK;
 }
 
@@ -118,6 +133,8 @@ pc_status pc_cv_grid(const pc_model *m, int32_t grid, float width_sd, pc_cv_desc
   c->n = H.n;
   c->grid = grid;
   c->beta = 1.f;
+  c->beta2 = 1.f;
+  c->use_gamma = 0;
   for (int k = 1; k < H.n; ++k) {
     const double tau = double(H.tau[k]);
     for (int i = 0; i < 3; ++i) {
@@ -138,7 +155,7 @@ pc_status pc_cv_grid(const pc_model *m, int32_t grid, float width_sd, pc_cv_desc
 pc_status pc_cv_table_size(const pc_cv_desc *c, size_t *floats) {
   if (!c || !floats) return fail(PC_EINVAL, "null argument");
   if (c->d < 1 || c->d > 3 || c->n < 1 || c->grid < 2) return fail(PC_EINVAL, "bad description");
-  *floats = size_t(std::max(0, c->n - 1)) * 2 * nodes_of(c) * size_t(c->d);
+  *floats = size_t(std::max(0, c->n - 1)) * 2 * nodes_of(c) * 4;
   return PC_OK;
 }
 
@@ -153,6 +170,7 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
   size_t need = 0;
   pc_cv_table_size(c, &need);
   if (cap < need || (need && !d_tables)) return fail(PC_EINVAL, "table capacity too small");
+  if (reinterpret_cast<uintptr_t>(d_tables) & 15u) return fail(PC_EINVAL, "tables must be 16-byte aligned");
   const ModelHost &H = m->H;
   CvFeatureArgs fa;
   std::memset(&fa, 0, sizeof(fa));
@@ -163,13 +181,13 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
   fa.rho = H.d > 1 ? float(H.corr[1]) : 0.f;
   fa.r = float(H.r);
   for (int o = 0; o <= H.n; ++o) fa.tau[o] = H.tau[o];
-  const size_t rows = need / size_t(c->d) + 1;
+  const size_t rows = need / 4 + 1;
   pc_ctx *ctx = m->ctx;
   CU(cudaSetDevice(ctx->device), "cudaSetDevice");
   float *buf = mlp_scratch(net, rows * (kCvFeatures + kCvOutputs) + 64);
   if (!buf) return fail(PC_ENOMEM, "table scratch");
   float *X = buf, *Y = buf + rows * kCvFeatures, *d0 = Y + rows * kCvOutputs;
-  const CvArgs ca = device_args(c, nullptr);
+  const CvArgs ca = device_args(c, nullptr, m->H, false);
   cudaError_t e = launch_cv_features(ca, fa, X, rows, ctx->stream);
   if (e != cudaSuccess) s = cuda_fail(e, "table features");
   if (s == PC_OK) s = pc_mlp_forward(net, X, rows, Y);
@@ -188,41 +206,72 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
   return PC_OK;
 }
 
+// Sums of the launch (width doubles) to the host, with the status check.
+pc_status cv_sums(pc_ctx *ctx, int width, double *h) {
+  double st[5];
+  CU(cudaMemcpyAsync(h, ctx->d_gout, size_t(width) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+     "result copy");
+  CU(cudaMemcpyAsync(st, ctx->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "status copy");
+  pc_status s = wait_stream(ctx);
+  if (s != PC_OK) return s;
+  int32_t status;
+  std::memcpy(&status, &st[4], 4);
+  return check_status(ctx, status);
+}
+
 pc_status pc_price_cv(const pc_model *m, const pc_contract *k, const pc_cv_desc *c, const float *d_tables,
                       uint64_t n_paths, uint64_t seed, double *out) {
   if (!out) return fail(PC_EINVAL, "null output");
   if (n_paths < 2) return fail(PC_EINVAL, "n_paths must be >= 2 for a standard error");
   if (!m) return fail(PC_EINVAL, "null model");
   pc_ctx *ctx = m->ctx;
-  pc_status s = cv_launch(m, k, c, d_tables, n_paths, seed, ctx->d_gout, nullptr);
+  pc_status s = cv_launch(m, k, c, d_tables, n_paths, seed, ctx->d_gout, nullptr, false);
   if (s != PC_OK) return s;
-  double h[6], st[5];
-  CU(cudaMemcpyAsync(h, ctx->d_gout, 6 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "result copy");
-  CU(cudaMemcpyAsync(st, ctx->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "status copy");
-  s = wait_stream(ctx);
+  double h[4];
+  s = cv_sums(ctx, 4, h);
   if (s != PC_OK) return s;
-  int32_t status;
-  std::memcpy(&status, &st[4], 4);
-  s = check_status(ctx, status);
-  if (s != PC_OK) return s;
-  const double N = double(n_paths), beta = double(c->beta);
-  const double mx = h[0] / N, mm = h[2] / N;
-  const double vx = std::max(0.0, (h[1] - N * mx * mx) / (N - 1.0));
-  const double vm = std::max(0.0, (h[3] - N * mm * mm) / (N - 1.0));
-  const double cxm = (h[4] - N * mx * mm) / (N - 1.0);
-  const double vy = std::max(0.0, vx - 2.0 * beta * cxm + beta * beta * vm);
-  out[0] = mx - beta * mm;
-  out[1] = std::sqrt(vy / N);
+  const double N = double(n_paths);
+  const double mx = h[0] / N, my = h[2] / N;
+  out[0] = my;
+  out[1] = std::sqrt(std::max(0.0, (h[3] - N * my * my) / (N - 1.0)) / N);
   out[2] = mx;
-  out[3] = std::sqrt(vx / N);
-  out[4] = vm > 0.0 ? cxm / vm : 0.0;
+  out[3] = std::sqrt(std::max(0.0, (h[1] - N * mx * mx) / (N - 1.0)) / N);
+  return PC_OK;
+}
+
+pc_status pc_cv_beta(const pc_model *m, const pc_contract *k, const pc_cv_desc *c, const float *d_tables,
+                     uint64_t n_paths, uint64_t seed, double *beta) {
+  if (!beta) return fail(PC_EINVAL, "null output");
+  if (n_paths < 16) return fail(PC_EINVAL, "n_paths must be >= 16");
+  if (!m) return fail(PC_EINVAL, "null model");
+  pc_ctx *ctx = m->ctx;
+  pc_status s = cv_launch(m, k, c, d_tables, n_paths, seed, ctx->d_gout, nullptr, true);
+  if (s != PC_OK) return s;
+  double h[8];
+  s = cv_sums(ctx, 8, h);
+  if (s != PC_OK) return s;
+  // moments: X, M, M2, XM, XM2, MM, M2M2, MM2
+  const double N = double(n_paths);
+  const double mx = h[0] / N, mm = h[1] / N, m2 = h[2] / N;
+  const double cxm = h[3] / N - mx * mm, cxm2 = h[4] / N - mx * m2;
+  const double vm = h[5] / N - mm * mm, vm2 = h[6] / N - m2 * m2, cmm2 = h[7] / N - mm * m2;
+  if (c->use_gamma) {
+    const double det = vm * vm2 - cmm2 * cmm2;
+    if (det > 0.0) {
+      beta[0] = (cxm * vm2 - cxm2 * cmm2) / det;
+      beta[1] = (cxm2 * vm - cxm * cmm2) / det;
+      return PC_OK;
+    }
+  }
+  beta[0] = vm > 0.0 ? cxm / vm : 0.0;
+  beta[1] = 0.0;
   return PC_OK;
 }
 
 pc_status pc_debug_cv_paths(const pc_model *m, const pc_contract *k, const pc_cv_desc *c, const float *d_tables,
                             uint64_t n_paths, uint64_t seed, float *d_xm) {
   if (!m || !d_xm) return fail(PC_EINVAL, "null argument");
-  return cv_launch(m, k, c, d_tables, n_paths, seed, m->ctx->d_gout, d_xm);
+  return cv_launch(m, k, c, d_tables, n_paths, seed, m->ctx->d_gout, d_xm, false);
 }
 
 }  // extern "C"

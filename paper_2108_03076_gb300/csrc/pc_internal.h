@@ -254,6 +254,11 @@ inline size_t batch_smem_bytes(size_t slot_bytes, int words, int block) {
 int batch_blocks_per_sm(int d, int block, size_t smem_bytes);
 cudaError_t launch_batch(const BatchArgs &b, int d, int grid, int block, size_t smem_bytes,
                          cudaStream_t s);
+// Occupancy results keyed by (device, kernel variant, block, shared memory):
+// the query runs once per key (it sets the kernel's shared-memory limit and
+// costs microseconds), later calls return the stored count.
+int occupancy_memo(uint64_t variant, int block, size_t smem, int (*query)(uint64_t, int, size_t));
+
 // Device address and size of the fixed scratch array used by
 // pc_price_noalloc on the current device (looked up once per device).
 cudaError_t noalloc_scratch(void **ptr, size_t *bytes);

@@ -12,7 +12,9 @@
 // word w of thread t is at region[w * kBlock + t], so the warp-uniform slot
 // indices of the interpreter give conflict-free accesses.
 #include <cstdint>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "pc_device.cuh"
 #include "pc_eval.cuh"
@@ -241,7 +243,10 @@ cudaError_t launch_price(const PriceArgs &a, int grid, int block, size_t smem, c
 #undef LAUNCH
 }
 
-int price_blocks_per_sm(int d, int block, size_t smem, bool hbm_window) {
+namespace {
+int price_occupancy(uint64_t v, int block, size_t smem) {
+  const int d = int(v & 0xff);
+  const bool hbm_window = (v >> 8) & 1;
   int nb = 0;
   cudaError_t e = cudaSuccess;
 #define OCC(DD)                                                                                      \
@@ -263,6 +268,31 @@ int price_blocks_per_sm(int d, int block, size_t smem, bool hbm_window) {
   }
 #undef OCC
   return e == cudaSuccess ? nb : 0;
+}
+}  // namespace
+
+int price_blocks_per_sm(int d, int block, size_t smem, bool hbm_window) {
+  return occupancy_memo((uint64_t(1) << 32) | (uint64_t(hbm_window) << 8) | uint64_t(d), block, smem,
+                        price_occupancy);
+}
+
+int occupancy_memo(uint64_t variant, int block, size_t smem, int (*query)(uint64_t, int, size_t)) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, uint64_t, int, size_t>, int> memo;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return query(variant, block, smem);
+  const auto key = std::make_tuple(dev, variant, block, smem);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+  }
+  const int nb = query(variant, block, smem);
+  if (nb > 0) {
+    std::lock_guard<std::mutex> g(mu);
+    memo[key] = nb;
+  }
+  return nb;
 }
 
 int batch_blocks_per_sm(int d, int block, size_t smem) {

@@ -27,7 +27,7 @@ from typing import List, Sequence, Tuple
 import numpy as np
 
 from . import (pc_assemble, pc_batch_create, pc_batch_destroy, pc_batch_launch, pc_batch_results,
-               pc_contract_destroy, pc_cv_grid, pc_cv_table_size, pc_cv_tables, pc_load_payoff,
+               pc_contract_destroy, pc_cv_beta, pc_cv_grid, pc_cv_table_size, pc_cv_tables, pc_load_payoff,
                pc_mlp_create, pc_mlp_destroy, pc_mlp_forward, pc_mlp_train, pc_model_create,
                pc_model_destroy, pc_price_cv)
 
@@ -181,9 +181,10 @@ def engine_training_set(ctx: int, n_samples: int, paths: int, seed: int, bump: f
 class LearnedCV:
     """The trained network and its use as the hedge of pc_price_cv."""
 
-    def __init__(self, ctx: int, seed: int = 7, max_batch: int = 8192):
+    def __init__(self, ctx: int, seed: int = 7, max_batch: int = 16384):
         self.ctx = ctx
         self.net = pc_mlp_create(ctx, WIDTHS, max_batch, seed)
+        self.betas = (1.0, 1.0)     # (beta, beta2) for the hedge terms; see calibrate()
 
     def close(self):
         if self.net:
@@ -216,15 +217,30 @@ class LearnedCV:
         torch.cuda.synchronize()
         return dy.cpu().numpy()
 
-    def tables(self, model: int, grid: int = 24, width_sd: float = 4.5, call_level: float = 1.0,
-               ki_level: float = 0.6, coupon: float = 0.05):
-        """(description, device tables) for a model of the template."""
+    def tables(self, model: int, grid: int = 12, width_sd: float = 4.5, call_level: float = 1.0,
+               ki_level: float = 0.6, coupon: float = 0.05, gamma: bool = True):
+        """(description, device tables) for a model of the template, with the
+        calibrated betas (and the second-order term when ``gamma``)."""
         import torch
         desc = pc_cv_grid(model, grid, width_sd, (1.0, 1.0, 1.0), call_level, ki_level, coupon)
         n = pc_cv_table_size(desc)
         dt = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
         pc_cv_tables(self.net, model, desc, dt.data_ptr(), n)
+        desc.use_gamma = 1 if gamma else 0
+        desc.beta, desc.beta2 = self.betas if gamma else (self.betas_first_order, 0.0)
         return desc, dt
+
+    betas_first_order = 1.0
+
+    def calibrate(self, model: int, contract: int, n_paths: int = 1 << 18, seed: int = 0xCA11B):
+        """Fix the betas once for the template: the variance-minimising
+        values on a pilot run (its own seed, so later prices use fixed
+        betas and stay unbiased)."""
+        desc, dt = self.tables(model, gamma=True)
+        self.betas = pc_cv_beta(model, contract, desc, dt.data_ptr(), n_paths, seed)
+        desc, dt = self.tables(model, gamma=False)
+        self.betas_first_order = pc_cv_beta(model, contract, desc, dt.data_ptr(), n_paths, seed)[0]
+        return self.betas
 
     @staticmethod
     def price(model: int, contract: int, desc, d_tables, n_paths: int, seed: int):

@@ -56,10 +56,10 @@ def test_per_path_payoff_and_hedge_gain_match_oracle(eng):
     tab = random_tables(desc, 1)
     dtab = torch.tensor(tab, device="cuda")
     n, seed = 4096 + 13, 0x5EED0101
-    xm = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+    xm = torch.empty(3 * n, dtype=torch.float32, device="cuda")
     pc.pc_debug_cv_paths(m, k, desc, dtab.data_ptr(), n, seed, xm.data_ptr())
     torch.cuda.synchronize()
-    got = xm.double().cpu().numpy().reshape(n, 2)
+    got = xm.double().cpu().numpy().reshape(n, 3)
     mk = market(w.market)
     x_ref, marg = mc.payoffs(il_text.parse(w.il_text), mk, tparam_env(w.tparams), 0, 1, n, seed, 0, 0,
                              with_margins=True)
@@ -68,7 +68,7 @@ def test_per_path_payoff_and_hedge_gain_match_oracle(eng):
     alive, ki = cv.autocall_states(S, [1.0, 1.0, 1.0], 1.0, 0.6)
     lo, h = desc_arrays(desc)
     d, G = desc.d, desc.grid
-    tables = tab.astype(np.float64).reshape(desc.n - 1, 2, G ** d, d)
+    tables = tab.astype(np.float64).reshape(desc.n - 1, 2, G ** d, 4)[..., :d]
     delta = cv.table_deltas(S, ki, tables, lo, h, G, [desc.delta0[i] for i in range(d)])
     disc = [mk.disc(o) for o in range(mk.n + 1)]
     M_ref = cv.hedge_martingale(S, disc, alive, delta)
@@ -78,19 +78,38 @@ def test_per_path_payoff_and_hedge_gain_match_oracle(eng):
     assert not np.any(bad & ~amb), np.nonzero(bad & ~amb)[0][:5]
     assert int((bad & amb).sum()) <= max(2, 1e-3 * n)
     assert np.std(M_ref) > 0.05
+    # second-order term: gamma from the table slopes; a path whose ln S lies
+    # within 1e-4 of a cell boundary may take the neighbouring cell's slope
+    gam = cv.table_gammas(S, ki, tables, lo, h, G)
+    tau = [0.0] + [dd / 365.0 for dd in mk.days]
+    M2_ref = cv.gamma_martingale(S, disc, alive, gam, np.asarray(mk.corr), mk.sigma, tau)
+    u = (np.log(S[:, 1:mk.n, :]) - lo[None]) / h[None]
+    edge = (np.abs(u - np.round(u)) < 1e-4).any((1, 2))
+    bad2 = np.abs(got[:, 2] - M2_ref) > 2e-4 * (1.0 + np.abs(M2_ref))
+    assert not np.any(bad2 & ~(amb | edge)), np.nonzero(bad2 & ~(amb | edge))[0][:5]
+    assert int((bad2 & (amb | edge)).sum()) <= max(2, 1e-3 * n)
+    assert np.std(M2_ref) > 1e-3
 
 
-def test_plain_half_is_pc_price_and_cv_is_unbiased(eng):
+@pytest.mark.parametrize("gamma", [0, 1])
+def test_plain_half_is_pc_price_and_cv_is_unbiased(eng, gamma):
     w = W.worst_of_autocall()
     m = eng.model(w.market)
     k = eng.contract(w.il_text, w.tparams)
     desc = pc.pc_cv_grid(m, 12, 4.5)
+    desc.use_gamma = gamma
     dtab = torch.tensor(random_tables(desc, 2), device="cuda")
     n, seed = 1 << 20, 0x5EED0002
     (pcv, scv), (pp, sp) = pc.pc_price_cv(m, k, desc, dtab.data_ptr(), n, seed)
     price, se = pc.pc_price(m, k, n, seed)
     assert pp == price and sp == se
     assert abs(pcv - pp) <= 4 * (scv + sp), (pcv, pp, scv, sp)
+    # betas from a pilot on another seed; beta = 0 gives back the plain estimate
+    b1, b2 = pc.pc_cv_beta(m, k, desc, dtab.data_ptr(), 1 << 16, seed + 1)
+    assert np.isfinite(b1) and (b2 == 0.0) == (gamma == 0)
+    desc.beta, desc.beta2 = 0.0, 0.0
+    (p0, s0), _ = pc.pc_price_cv(m, k, desc, dtab.data_ptr(), n, seed)
+    assert p0 == pytest.approx(pp, rel=1e-12) and s0 == pytest.approx(sp, rel=1e-9)
 
 
 def test_black_scholes_hedged_call_removes_most_variance(eng):
@@ -101,7 +120,7 @@ def test_black_scholes_hedged_call_removes_most_variance(eng):
     desc = pc.pc_cv_grid(m, 64, 5.0, ref=(1.0,), call_level=1e30, ki_level=-1.0)
     lo, h = desc_arrays(desc)
     tau = np.array([0.0] + [dd / 365.0 for dd in days])
-    tab = np.zeros((31, 2, 64, 1))
+    tab = np.zeros((31, 2, 64, 4))
     for kk in range(1, 32):
         y = lo[kk - 1, 0] + h[kk - 1, 0] * np.arange(64)
         dl = np.array([cf.bs_delta_call(math.exp(v), 1.0, 0.03, 0.2, tau[-1] - tau[kk]) for v in y])
@@ -113,3 +132,8 @@ def test_black_scholes_hedged_call_removes_most_variance(eng):
     assert (sp / scv) ** 2 > 8.0, (sp, scv)
     bs = cf.bs_call(1.0, 1.0, 0.03, 0.2, tau[-1])
     assert abs(pcv - bs) < 4 * scv + 1e-4, (pcv, bs, scv)
+    # the second-order term from the table's slopes removes more
+    desc.use_gamma = 1
+    (pg, sg), _ = pc.pc_price_cv(m, k, desc, dtab.data_ptr(), 1 << 20, 0x5EED0003)
+    assert sg < scv, (sg, scv)
+    assert abs(pg - bs) < 4 * sg + 1e-4, (pg, bs, sg)

@@ -44,16 +44,23 @@ def test_learned_hedge_reduces_variance_without_bias(eng, trained):
     w = W.worst_of_autocall()
     m = eng.model(w.market)
     k = eng.contract(w.il_text, w.tparams)
-    desc, tabs = trained.tables(m)
+    b1, b2 = trained.calibrate(m, k, 1 << 16)
+    assert np.isfinite(b1) and np.isfinite(b2)
     n, seed = 1 << 20, 0x5EED0001
+    desc, tabs = trained.tables(m, gamma=False)
     (pcv, scv), (pp, sp) = trained.price(m, k, desc, tabs, n, seed)
     assert abs(pcv - pp) <= 4 * (scv + sp), (pcv, pp, scv, sp)
     gain = (sp / scv) ** 2
     assert gain > 1.5, gain
+    # with the second-order term (betas fixed by the calibration's own seed)
+    desc, tabs = trained.tables(m, gamma=True)
+    (pg, sg), _ = trained.price(m, k, desc, tabs, n, seed)
+    assert abs(pg - pp) <= 4 * (sg + sp), (pg, pp, sg, sp)
+    assert sg <= 1.02 * scv, (sg, scv)
     # an untrained network of the same shape
     raw = L.LearnedCV(eng.ctx, seed=99)
     try:
-        d0, t0 = raw.tables(m)
+        d0, t0 = raw.tables(m, gamma=False)
         (_, s0), _ = raw.price(m, k, d0, t0, n, seed)
     finally:
         raw.close()
