@@ -41,7 +41,11 @@ METRIC = "path·date evals/sec & contracts priced/sec at 1e-4 rel. std-err vs pl
 UNIT = "path·date/s"
 TARGET_REL_SE = 1e-4
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
-               for f in ("pc_kernels.cu", "pc_eval.cuh", "pc_device.cuh", "pc_internal.h")]
+               for f in ("pc_kernels.cu", "pc_eval.cuh", "pc_eval_state.inc", "pc_ops.inc", "pc_price.cuh",
+                         "pc_device.cuh", "pc_types.h")]
+JIT_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
+            for f in ("pc_jit.cpp", "pc_eval_state.inc", "pc_ops.inc", "pc_price.cuh", "pc_device.cuh",
+                      "pc_types.h")]
 PORTFOLIO = "portfolio_1024"
 LEARNED = "learned_cv_worst_of_autocall"
 PORTFOLIO_SEED = 0x5EED0004
@@ -128,15 +132,16 @@ def measured_peaks() -> dict:
         return {}
 
 
-def profile_traffic(workload: str):
+def profile_traffic(workload: str, kind: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"price_kernel_{workload}.json")
+    name = "price_kernel" if kind == "interpreter" else "jit_price_kernel"
+    path = os.path.join(ROOT, "profiles", f"{name}_{workload}.json")
     try:
         with open(path) as f:
             p = json.load(f)
         h = hashlib.sha256()
-        for src in KERNEL_SRCS:
+        for src in (KERNEL_SRCS if kind == "interpreter" else JIT_SRCS):
             with open(src, "rb") as f:
                 h.update(f.read())
         sha = h.hexdigest()
@@ -210,6 +215,8 @@ def main():
                     choices=sorted(W.ALL) + [PORTFOLIO, LEARNED])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--interpret", action="store_true",
+                    help="time the interpreting kernel instead of the contract's specialised kernel")
     args = ap.parse_args()
     if args.workload == PORTFOLIO:
         return run_portfolio(args)
@@ -244,6 +251,14 @@ def main():
     contract = pc.pc_load_payoff(ctx, words, consts, w.tparams, 0, 1)
     minfo = pc.pc_model_query(model)
     offset = rank * w.n_paths
+    jit_s = None
+    if not args.interpret:
+        # the paper's per-instrument compilation: a kernel specialised to this
+        # program, compiled once (outside the timed region)
+        pc.pc_set_jit(ctx, True)
+        t0 = time.perf_counter()
+        pc.pc_jit_compile(model, contract)
+        jit_s = time.perf_counter() - t0
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -268,6 +283,21 @@ def main():
     kernel_ms = [a.elapsed_time(b) for a, b in evs]
     t_dev = sum(kernel_ms) / 1e3
     sums = out.cpu().numpy()
+    interp_ms = None
+    if not args.interpret:
+        # the interpreting kernel on the same inputs, for comparison
+        pc.pc_set_jit(ctx, False)
+        ims = []
+        for _ in range(max(3, min(args.steps, 50))):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pc.pc_price_async(model, contract, w.n_paths, offset, w.seed, 0, out.data_ptr())
+            b.record(stream)
+            torch.cuda.synchronize()
+            ims.append(a.elapsed_time(b))
+        interp_ms = statistics.median(ims)
+        pc.pc_set_jit(ctx, True)
     mean = sums[0] / w.n_paths
     var = max(0.0, (sums[1] - w.n_paths * mean * mean) / (w.n_paths - 1))
 
@@ -306,7 +336,7 @@ def main():
     ops = alg_ops_per_path(minfo)
     launch_s = t_dev / args.steps
     achieved = ops["ops"] * w.n_paths / launch_s
-    traffic, traffic_paths = profile_traffic(w.name)
+    traffic, traffic_paths = profile_traffic(w.name, "interpreter" if args.interpret else "specialised")
     if traffic is not None and traffic_paths:
         traffic = traffic * w.n_paths / traffic_paths
 
@@ -316,7 +346,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {**config(w, info.n_nodes), "parallelism": f"path ranges x{ws}"},
+            "config": {**config(w, info.n_nodes), "parallelism": f"path ranges x{ws}",
+                       "kernel": "interpreter" if args.interpret else
+                                 "specialised to the program (run-time compiled, NVRTC)"},
+            "interpreter_ms_per_step": interp_ms, "specialised_compile_s": jit_s,
             "contracts_per_sec_at_1e-4_rel_se": contracts_per_s,
             "price": mean, "stderr": math.sqrt(var / w.n_paths),
             "paths_for_1e-4_rel_se": paths_needed,
@@ -324,7 +357,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(words.nbytes + consts.nbytes + 4 * len(w.tparams)),
                     "d2h_bytes_per_step": 40,
-                    "note": "pc_load_payoff + pc_price + pc_contract_destroy per step, host wall clock"},
+                    "note": "pc_load_payoff + pc_price + pc_contract_destroy per step, host wall clock "
+                            "(a reloaded program finds its compiled kernel in the context's cache)"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
                          "mufu_frac": ops["mufu"] * w.n_paths / launch_s / peak_mufu,

@@ -323,6 +323,24 @@ pc_status pc_price_info(const pc_model *model, const pc_contract *contract, uint
                         pc_launch_info *info);
 
 /* ------------------------------------------------------------------------ */
+/* Run-time specialised pricing kernels                                      */
+/* ------------------------------------------------------------------------ */
+/* The paper compiles each contract into its own payoff function (Sec. 6).
+ * With pc_set_jit(ctx, 1), pc_price / pc_price_async / pc_price_paths run a
+ * kernel specialised to the contract's executable program (compiled at run
+ * time by NVRTC on first use for each underlying count, cached on the
+ * context by program content -- reloading the same program reuses it --
+ * and freed by pc_destroy): the same operations in the same order as the
+ * interpreting kernel, without the per-instruction dispatch.
+ * Launches that need the HBM window keep the interpreting kernel.
+ * Default: 0 (interpret).  Errors: PC_EINVAL. */
+pc_status pc_set_jit(pc_ctx *ctx, int32_t enabled);
+/* Compile (now) the contract's specialised kernel for the model's
+ * underlying count.  Blocks; typically tens to hundreds of milliseconds.
+ * Errors: PC_EINVAL, PC_ECUDA (the compiler's log in pc_last_error). */
+pc_status pc_jit_compile(const pc_model *model, const pc_contract *contract);
+
+/* ------------------------------------------------------------------------ */
 /* Portfolio pricing                                                         */
 /* ------------------------------------------------------------------------ */
 /* The paper prices one contract per engine invocation; templating (Sec. 2,
@@ -577,6 +595,14 @@ pc_status pc_debug_greeks_paths(const pc_model *model, const pc_contract *contra
  * Asynchronous on the context's stream. */
 pc_status pc_debug_cv_paths(const pc_model *model, const pc_contract *contract, const pc_cv_desc *desc,
                             const float *d_tables, uint64_t n_paths, uint64_t seed, float *d_xm);
+
+/* Host-only: generate and compile (NVRTC, sm_103a) the specialised pricing
+ * kernel of a program for d underlyings, without loading it; *cubin_bytes
+ * receives the size of the result.  Errors: as pc_verify_payoff; PC_ECUDA
+ * with the compiler's log. */
+pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_words, const double *consts,
+                               size_t n_consts, const int32_t *template_params, size_t n_params,
+                               int32_t p1, int32_t p2, int32_t d, size_t *cubin_bytes);
 
 /* Host-only: the executable form pc_load_payoff would run for this program:
  * 4 words per instruction (opcode | A << 8, then three operand words), then

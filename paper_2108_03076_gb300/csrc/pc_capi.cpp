@@ -286,6 +286,22 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
   L.args.out = d_out;
   L.args.out_paths = d_payoffs;
   CU(cudaSetDevice(c->device), "cudaSetDevice");
+  if (c->jit && !L.hbm_window) {
+    // the contract's run-time specialised kernel (same arguments and shape)
+    cudaKernel_t jk = nullptr;
+    s = jit_kernel(k, m->H.d, d_payoffs != nullptr, jk);
+    if (s != PC_OK) return s;
+    const void *kern = reinterpret_cast<const void *>(jk);
+    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.smem)), "jit attribute");
+    int nb = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, L.block, L.smem), "jit occupancy");
+    if (nb < 1) return fail(PC_ELIMIT, "specialised kernel cannot be resident");
+    const uint64_t wpb = uint64_t(L.block) / 32;
+    const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * nb, (L.args.n_tiles + wpb - 1) / wpb));
+    void *args[] = {&L.args};
+    CU(cudaLaunchKernel(kern, dim3(grid), dim3(L.block), args, L.smem, c->stream), "specialised price kernel");
+    return PC_OK;
+  }
   CU(launch_price(L.args, L.grid, L.block, L.smem, c->stream), "price kernel");
   return PC_OK;
 }
@@ -479,6 +495,7 @@ pc_status pc_destroy(pc_ctx *c) {
   if (c->d_partials) cudaFree(c->d_partials);
   if (c->d_control) cudaFree(c->d_control);
   if (c->d_gwin) cudaFree(c->d_gwin);
+  jit_release(c);
   if (c->d_gout) cudaFree(c->d_gout);
   if (c->d_res) cudaFree(c->d_res);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -713,6 +730,21 @@ pc_status pc_set_window_mode(pc_ctx *c, int32_t mode) {
     return fail(PC_EINVAL, "window mode must be PC_WINDOW_AUTO, _SHARED or _HBM");
   c->window_mode = mode;
   return PC_OK;
+}
+
+pc_status pc_set_jit(pc_ctx *c, int32_t enabled) {
+  if (!c) return fail(PC_EINVAL, "null context");
+  if (enabled != 0 && enabled != 1) return fail(PC_EINVAL, "enabled must be 0 or 1");
+  c->jit = enabled;
+  return PC_OK;
+}
+
+pc_status pc_jit_compile(const pc_model *m, const pc_contract *k) {
+  if (!m || !k) return fail(PC_EINVAL, "null model or contract");
+  if (m->ctx != k->ctx) return fail(PC_EINVAL, "model and contract belong to different contexts");
+  CU(cudaSetDevice(m->ctx->device), "cudaSetDevice");
+  cudaKernel_t jk = nullptr;
+  return jit_kernel(k, m->H.d, false, jk);
 }
 
 pc_status pc_price_info(const pc_model *m, const pc_contract *k, uint64_t n_paths, pc_launch_info *info) {

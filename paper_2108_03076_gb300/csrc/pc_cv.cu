@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "pc_device.cuh"
+#include "pc_internal.h"
 #include "pc_eval.cuh"
 #include "pc_cv.h"
 

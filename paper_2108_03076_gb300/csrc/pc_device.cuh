@@ -9,9 +9,7 @@
 // so the warp-uniform slot indices give conflict-free accesses.
 #pragma once
 
-#include <cstdint>
-
-#include "pc_internal.h"
+#include "pc_types.h"
 
 namespace pc {
 namespace {
@@ -283,6 +281,15 @@ __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev
   ps.f = t;
 }
 
+// Dates ps.f + 1 .. o, out of line (the specialised evaluator calls it from
+// every instruction that reads a date, so it is not inlined there).
+template <int D, bool GW>
+__device__ __noinline__ void advance_dates(int o, PathState<D> &ps, const ModelDev &m, const Layout &lay,
+                                           const Rng2 &g, float2 *R, const float (&Bm)[D * D],
+                                           const float (&S0)[D]) {
+  while (ps.f < o) gen_date<D, false, GW>(ps.f + 1, ps, m, lay, g, R, Bm, S0);
+}
+
 template <int D>
 __device__ __forceinline__ void load_model_regs(const ModelDev &m, float (&Bm)[D * D],
                                                 float (&S0)[D]) {
@@ -327,7 +334,7 @@ __device__ __forceinline__ float2 fused_value(const uint4 &I, int o, const float
     }
     if (kind == 1) {
       const float c = pool[I.z + i];
-      s = make_float2(s.x * c, s.y * c);
+      s = make_float2(__fmul_rn(s.x, c), __fmul_rn(s.y, c));
     } else if (kind == 2) {
       const float c = pool[I.z + i];
       s = make_float2(__fdiv_rn(s.x, c), __fdiv_rn(s.y, c));
@@ -344,7 +351,7 @@ __device__ __forceinline__ float2 fused_value(const uint4 &I, int o, const float
     } else if (rop == 1) {
       v = make_float2(fmaxf(v.x, s.x), fmaxf(v.y, s.y));
     } else {
-      v = make_float2(v.x + s.x, v.y + s.y);
+      v = make_float2(__fadd_rn(v.x, s.x), __fadd_rn(v.y, s.y));
     }
   }
   if (!any && code) v = make_float2(cmp_code(code, v.x, k), cmp_code(code, v.y, k));

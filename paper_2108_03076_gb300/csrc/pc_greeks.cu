@@ -17,6 +17,7 @@
 #include <cstdint>
 
 #include "pc_device.cuh"
+#include "pc_internal.h"
 
 namespace pc {
 namespace {

@@ -8,11 +8,22 @@
 #include <mutex>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include <cuda_runtime.h>
 
 #include "pc.h"
 #include "pc_internal.h"
+
+// A run-time specialised pricing kernel: the program it was compiled from
+// (code and pool words), the underlying count and the per-path variant.
+struct JitEntry {
+  std::vector<uint32_t> program;
+  int d = 0;
+  bool write = false;
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kernel = nullptr;
+};
 
 struct pc_ctx {
   int device = 0;
@@ -28,6 +39,9 @@ struct pc_ctx {
   float2 *d_gwin = nullptr;      // HBM windows of simulated dates (grow-only)
   size_t gwin_cap = 0;           // float2 slots
   int32_t window_mode = 0;       // PC_WINDOW_AUTO / _SHARED / _HBM
+  int32_t jit = 0;               // 1: price with run-time specialised kernels
+  std::mutex jit_mu;
+  std::multimap<uint64_t, JitEntry> jit_cache;  // program hash -> compiled kernels
   double timeout_s = 300.0;
   int live_objects = 0;
 };
@@ -39,6 +53,7 @@ struct pc_model {
   pc::ModelDev dev{};
   uint64_t id = 0;
 };
+
 
 struct pc_contract {
   pc_ctx *ctx = nullptr;
@@ -90,6 +105,12 @@ pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uin
 
 // Grow the context's tile-partial scratch to at least `doubles`.
 pc_status ensure_partials(pc_ctx *c, size_t doubles);
+
+// The run-time specialised kernel of the contract's program for d
+// underlyings (compiled on first use, cached on the context by program
+// content); `write`: the per-path variant.
+pc_status jit_kernel(const pc_contract *k, int d, bool write, cudaKernel_t &out);
+void jit_release(pc_ctx *c);
 
 // Turn a raised device status word into PC_EDEVICE (and clear it).
 pc_status check_status(pc_ctx *c, int32_t status);

@@ -17,7 +17,9 @@
 #include <tuple>
 
 #include "pc_device.cuh"
+#include "pc_internal.h"
 #include "pc_eval.cuh"
+#include "pc_price.cuh"
 
 namespace pc {
 
@@ -25,70 +27,16 @@ namespace {
 
 
 // Tiles of kTilePaths consecutive paths (two per lane: tile*64 + lane and
-// tile*64 + 32 + lane) are handed to warps through an atomic counter.  GW:
-// the window of simulated dates lives in HBM (lay.gwin) instead of shared
-// memory, for programs that look back further than shared memory holds.
+// tile*64 + 32 + lane) are handed to warps through an atomic counter
+// (price_tiles, pc_price.cuh).  GW: the window of simulated dates lives in
+// HBM (lay.gwin) instead of shared memory, for programs that look back
+// further than shared memory holds.
 template <int D, bool WRITE, bool GW = false>
 __global__ void __launch_bounds__(kBlock) price_kernel(const PriceArgs a) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ int last_block;
-  uint4 *P = reinterpret_cast<uint4 *>(smem);
-  const int prog_words = a.n_insn * 4 + a.n_pool;
-  const uint32_t *src = reinterpret_cast<const uint32_t *>(a.prog);
-  for (int i = threadIdx.x; i < prog_words; i += blockDim.x) smem[i] = src[i];
-  __syncthreads();
-  const float *pool = reinterpret_cast<const float *>(smem + a.n_insn * 4);
-  float2 *R = reinterpret_cast<float2 *>(smem + prog_words) + threadIdx.x;
-  float Bm[D * D], S0[D];
-  load_model_regs<D>(a.m, Bm, S0);
-  const int lane = threadIdx.x & 31;
-  unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
-  Rng2 g;
-  g.stream = a.stream;
-  g.k0 = a.key0;
-  g.k1 = a.key1;
-  for (;;) {
-    unsigned long long tile = 0;
-    if (lane == 0) tile = atomicAdd(ctr, 1ull);
-    tile = __shfl_sync(kFull, tile, 0);
-    if (tile >= a.n_tiles) break;
-    const uint64_t i0 = tile * kTilePaths + lane, i1 = i0 + 32;
-    const bool live0 = i0 < a.n_paths, live1 = i1 < a.n_paths;
-    const uint64_t p0 = a.path_offset + i0, p1 = a.path_offset + i1;
-    g.plo[0] = uint32_t(p0);
-    g.phi[0] = uint32_t(p0 >> 32);
-    g.plo[1] = uint32_t(p1);
-    g.phi[1] = uint32_t(p1 >> 32);
-    const float2 x = eval_path<D, GW>(P, pool, R, a, g, live0, live1, Bm, S0);
-    double tp[2] = {0.0, 0.0};
-    if (live0) {
-      const double xd = double(x.x);
-      tp[0] += xd;
-      tp[1] = fma(xd, xd, tp[1]);
-      if (WRITE) a.out_paths[i0] = x.x;
-    }
-    if (live1) {
-      const double xd = double(x.y);
-      tp[0] += xd;
-      tp[1] = fma(xd, xd, tp[1]);
-      if (WRITE) a.out_paths[i1] = x.y;
-    }
-    tp[0] = warp_sum(tp[0]);
-    tp[1] = warp_sum(tp[1]);
-    finish_tile<2>(a, tile, tp, lane);
-  }
-  // the last block to exit re-zeroes the tile counter: no warp grabs tiles
-  // any more once every block has left its loop
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last_block = atomicAdd(ctr + 1, 1ull) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last_block && threadIdx.x == 0) {
-    ctr[0] = 0;
-    ctr[1] = 0;
-  }
+  price_tiles<D, WRITE>(a, [&](const uint4 *P, const float *pool, float2 *R, const Rng2 &g, bool live0,
+                               bool live1, const float(&Bm)[D * D], const float(&S0)[D]) {
+    return eval_path<D, GW>(P, pool, R, a, g, live0, live1, Bm, S0);
+  });
 }
 
 // Portfolio kernel.  Warps take work units (a contract and a run of its

@@ -1,0 +1,75 @@
+// pc_price.cuh -- the pricing kernel's body: program staging, the tile
+// loop and the per-tile FP64 reduction, generic in the payoff evaluator
+// (the interpreter eval_path, or a run-time specialised evaluator).
+#pragma once
+
+#include "pc_device.cuh"
+
+namespace pc {
+
+// EVAL(P, pool, R, g, live0, live1, Bm, S0) -> float2 payoffs of the lane's
+// two paths.
+template <int D, bool WRITE, typename EVAL>
+__device__ __forceinline__ void price_tiles(const PriceArgs &a, EVAL eval) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int last_block;
+  uint4 *P = reinterpret_cast<uint4 *>(smem);
+  const int prog_words = a.n_insn * 4 + a.n_pool;
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(a.prog);
+  for (int i = threadIdx.x; i < prog_words; i += blockDim.x) smem[i] = src[i];
+  __syncthreads();
+  const float *pool = reinterpret_cast<const float *>(smem + a.n_insn * 4);
+  float2 *R = reinterpret_cast<float2 *>(smem + prog_words) + threadIdx.x;
+  float Bm[D * D], S0[D];
+  load_model_regs<D>(a.m, Bm, S0);
+  const int lane = threadIdx.x & 31;
+  unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
+  Rng2 g;
+  g.stream = a.stream;
+  g.k0 = a.key0;
+  g.k1 = a.key1;
+  for (;;) {
+    unsigned long long tile = 0;
+    if (lane == 0) tile = atomicAdd(ctr, 1ull);
+    tile = __shfl_sync(kFull, tile, 0);
+    if (tile >= a.n_tiles) break;
+    const uint64_t i0 = tile * kTilePaths + lane, i1 = i0 + 32;
+    const bool live0 = i0 < a.n_paths, live1 = i1 < a.n_paths;
+    const uint64_t p0 = a.path_offset + i0, p1 = a.path_offset + i1;
+    g.plo[0] = uint32_t(p0);
+    g.phi[0] = uint32_t(p0 >> 32);
+    g.plo[1] = uint32_t(p1);
+    g.phi[1] = uint32_t(p1 >> 32);
+    const float2 x = eval(P, pool, R, g, live0, live1, Bm, S0);
+    double tp[2] = {0.0, 0.0};
+    if (live0) {
+      const double xd = double(x.x);
+      tp[0] += xd;
+      tp[1] = fma(xd, xd, tp[1]);
+      if (WRITE) a.out_paths[i0] = x.x;
+    }
+    if (live1) {
+      const double xd = double(x.y);
+      tp[0] += xd;
+      tp[1] = fma(xd, xd, tp[1]);
+      if (WRITE) a.out_paths[i1] = x.y;
+    }
+    tp[0] = warp_sum(tp[0]);
+    tp[1] = warp_sum(tp[1]);
+    finish_tile<2>(a, tile, tp, lane);
+  }
+  // the last block to exit re-zeroes the tile counter: no warp grabs tiles
+  // any more once every block has left its loop
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last_block = atomicAdd(ctr + 1, 1ull) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last_block && threadIdx.x == 0) {
+    ctr[0] = 0;
+    ctr[1] = 0;
+  }
+}
+
+}  // namespace pc

@@ -1,0 +1,86 @@
+"""GPU run-time specialised kernels (pc_set_jit): the same per-path payoffs,
+bit for bit, and the same sums as the interpreting kernel on every test
+program, the oracle's values on a sample, the compiled kernel reused when
+the same program is loaded again, and the HBM-window launches left to the
+interpreter."""
+import numpy as np
+import pytest
+
+from cases import CASES
+from gpu_common import Engine, compare, oracle_paths, torch
+import paper_2108_03076_gb300 as pc
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    e = Engine()
+    yield e
+    pc.pc_set_jit(e.ctx, False)
+    e.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_specialised_equals_interpreter(eng, name):
+    text, tp, spec, notional = CASES[name]
+    m, k = eng.model(spec), eng.contract(text, tp)
+    n, seed = 4096 + 37, 0xABC + len(name)
+    pc.pc_set_jit(eng.ctx, False)
+    x0, s0 = eng.paths(m, k, n, seed)
+    pc.pc_set_jit(eng.ctx, True)
+    try:
+        x1, s1 = eng.paths(m, k, n, seed)
+        a1 = eng.sums(m, k, 1 << 16, seed)
+    finally:
+        pc.pc_set_jit(eng.ctx, False)
+    a0 = eng.sums(m, k, 1 << 16, seed)
+    np.testing.assert_array_equal(x1, x0)
+    np.testing.assert_array_equal(s1, s0)
+    np.testing.assert_array_equal(a1, a0)
+
+
+def test_specialised_matches_oracle_and_is_reused(eng):
+    w = W.worst_of_autocall()
+    m = eng.model(w.market)
+    k = eng.contract(w.il_text, w.tparams)
+    pc.pc_set_jit(eng.ctx, True)
+    try:
+        pc.pc_jit_compile(m, k)
+        n, seed = 3000, 77
+        x, _ = eng.paths(m, k, n, seed)
+        ref, marg = oracle_paths(w.il_text, w.market, w.tparams, n, seed)
+        compare(x, ref, marg, w.notional, "specialised autocall")
+        # the same program loaded again finds the compiled kernel
+        import time
+        k2 = eng.contract(w.il_text, w.tparams)
+        t = time.perf_counter()
+        pc.pc_jit_compile(m, k2)
+        assert time.perf_counter() - t < 0.05
+        p1 = pc.pc_price(m, k, 1 << 18, 5)
+        p2 = pc.pc_price(m, k2, 1 << 18, 5)
+        assert p1 == p2
+    finally:
+        pc.pc_set_jit(eng.ctx, False)
+    assert p1 == pc.pc_price(m, k, 1 << 18, 5)
+
+
+def test_hbm_window_launch_keeps_the_interpreter(eng):
+    days = list(range(1, 301))
+    spec = W.MarketSpec([1.0], [0.25], [[1.0]], 0.02, days)
+    terms = [f"(model 0 (tplus (tplus 0 $0) {-j}))" for j in range(300)]
+    s = terms[0]
+    for t_ in terms[1:]:
+        s = f"(add {s} {t_})"
+    text = f"(mult (max (sub (div {s} 300.0) 1.0) 0.0) (payoff (tplus 0 $0) 0 1))"
+    m, k = eng.model(spec), eng.contract(text, [300])
+    assert pc.pc_price_info(m, k, 1 << 16).hbm_window == 1
+    pc.pc_set_jit(eng.ctx, True)
+    try:
+        p1 = pc.pc_price(m, k, 1 << 16, 9)
+    finally:
+        pc.pc_set_jit(eng.ctx, False)
+    assert p1 == pc.pc_price(m, k, 1 << 16, 9)
