@@ -292,14 +292,24 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
     s = jit_kernel(k, m->H.d, d_payoffs != nullptr, jk);
     if (s != PC_OK) return s;
     const void *kern = reinterpret_cast<const void *>(jk);
-    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.smem)), "jit attribute");
+    // the specialised evaluator keeps its operand stack in registers: drop
+    // the stack words from the per-thread shared region
+    Layout &lay = L.args.lay;
+    const int shift = lay.off_bstack;
+    lay.stack = 0;
+    lay.off_bstack -= shift;
+    lay.off_cache -= shift;
+    lay.off_win -= shift;
+    lay.words -= shift;
+    const size_t smem = price_smem_bytes(k->prog.code.size(), pool_padded(k->prog), lay.words, L.block);
+    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), "jit attribute");
     int nb = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, L.block, L.smem), "jit occupancy");
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, L.block, smem), "jit occupancy");
     if (nb < 1) return fail(PC_ELIMIT, "specialised kernel cannot be resident");
     const uint64_t wpb = uint64_t(L.block) / 32;
     const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * nb, (L.args.n_tiles + wpb - 1) / wpb));
     void *args[] = {&L.args};
-    CU(cudaLaunchKernel(kern, dim3(grid), dim3(L.block), args, L.smem, c->stream), "specialised price kernel");
+    CU(cudaLaunchKernel(kern, dim3(grid), dim3(L.block), args, smem, c->stream), "specialised price kernel");
     return PC_OK;
   }
   CU(launch_price(L.args, L.grid, L.block, L.smem, c->stream), "price kernel");

@@ -47,6 +47,7 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
 #undef JUMP_2
 #undef NEXT_INSN
 #undef PUSH
+#undef STK
 #undef BINF
 #undef BINI
 #undef IMM

@@ -10,6 +10,7 @@
 // interpreter's own text, so both evaluators compute the same operations in
 // the same order.  NVRTC compiles the module for the device the context
 // runs on; the kernel is price_tiles (pc_price.cuh) with this evaluator.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <sstream>
@@ -52,6 +53,7 @@ std::string generate(const Program &p, int d, bool write) {
     << "namespace {\n"
     << "constexpr int D = " << d << ";\n"
     << "constexpr bool GW = false;\n"
+    << "#define PC_JIT_STACK_SLOTS " << std::max(1, int(p.frame_slots)) << "\n"
     << "__device__ __forceinline__ float2 jit_eval(const uint4 *P, const float *pool, float2 *R,\n"
     << "    const PriceArgs &a, const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],\n"
     << "    const float (&S0)[D], int *frontier = nullptr) {\n"
@@ -73,7 +75,7 @@ std::string generate(const Program &p, int d, bool write) {
       << "}\n";
   }
   o << "  return tos;\n"
-    << "#undef PUSH\n#undef BINF\n#undef BINI\n#undef IMM\n"
+    << "#undef PUSH\n#undef STK\n#undef BINF\n#undef BINI\n#undef IMM\n"
     << "}\n"
     << "}  // namespace\n"
     << "}  // namespace pc\n";
