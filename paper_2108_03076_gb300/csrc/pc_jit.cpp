@@ -43,11 +43,26 @@ std::string insn_literal(const XInsn &I) {
   return "make_uint4(" + hex(I.opa) + ", " + hex(I.b) + ", " + hex(I.c) + ", " + hex(I.e) + ")";
 }
 
+// Instructions that read simulated dates (and may have to generate them);
+// above this many, the date generator is called out of line instead of
+// being inlined at each of them.
+constexpr int kInlineDateSites = 12;
+
+int date_sites(const Program &p) {
+  int n = 0;
+  for (const XInsn &I : p.code) {
+    const uint32_t op = I.opa & 0xffu;
+    n += op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_LRED || op == X_LANY;
+  }
+  return n;
+}
+
 // Straight-line evaluator for the program and d underlyings, and the
 // pricing kernel around it (per-path payoffs written out when `write`).
 std::string generate(const Program &p, int d, bool write) {
   std::ostringstream o;
   const size_t n = p.code.size();
+  if (date_sites(p) > kInlineDateSites) o << "#define PC_JIT_OUTLINE_DATES 1\n";
   o << "#include \"pc_price.cuh\"\n"
     << "namespace pc {\n"
     << "namespace {\n"
