@@ -478,6 +478,21 @@ pc_status pc_mlp_forward(pc_mlp *net, const float *d_x, size_t n, float *d_y);
  * Blocks until done; *out_loss (host). */
 pc_status pc_mlp_gradients(pc_mlp *net, const float *d_x, const float *d_t, const float *w,
                            size_t n, float *d_grads, double *out_loss);
+/* Product kernels of the network.  PC_MLP_GEMM_AUTO (the default): the
+ * forward products run on the tcgen05 tensor cores (TMA-staged operands,
+ * TMEM accumulators) where the device has them, the backward products and
+ * every product elsewhere on the warp-level BF16 MMA kernel;
+ * PC_MLP_GEMM_MMA_SYNC: the warp-level kernel for every product.  Both
+ * accumulate in FP32 (results differ by summation order only).  Changing
+ * the choice re-captures the training step.  pc_mlp_gemm_info:
+ * *tensor_cores = 1 when the forward products use tcgen05.  A tensor-core
+ * product whose bounded wait expires sets a status that the next blocking
+ * call on the network (pc_mlp_gradients, pc_mlp_train, pc_cv_tables)
+ * reports as PC_ETIMEOUT.  Errors: PC_EINVAL. */
+#define PC_MLP_GEMM_AUTO 0
+#define PC_MLP_GEMM_MMA_SYNC 1
+pc_status pc_mlp_set_gemm(pc_mlp *net, int32_t kind);
+pc_status pc_mlp_gemm_info(const pc_mlp *net, int32_t *tensor_cores);
 /* `steps` Adam steps (lr; b1 0.9, b2 0.999, eps 1e-8) on minibatches of
  * `batch` rows (1..max_batch) drawn with replacement from the n_data rows of
  * d_x / d_t by Philox4x32-10 under `seed` and the step number.  One step is

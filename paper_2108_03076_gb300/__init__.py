@@ -88,6 +88,7 @@ class LaunchInfo(C.Structure):
 
 
 WINDOW_AUTO, WINDOW_SHARED, WINDOW_HBM = 0, 1, 2
+MLP_GEMM_AUTO, MLP_GEMM_MMA_SYNC = 0, 1
 
 
 class ProgramInfo(C.Structure):
@@ -134,6 +135,8 @@ _SIGS = {
     "pc_mlp_set_params": [VP, C.POINTER(C.c_float), SZ],
     "pc_mlp_get_params": [VP, C.POINTER(C.c_float), SZ],
     "pc_mlp_forward": [VP, VP, SZ, VP],
+    "pc_mlp_set_gemm": [VP, C.c_int32],
+    "pc_mlp_gemm_info": [VP, C.POINTER(C.c_int32)],
     "pc_mlp_gradients": [VP, VP, VP, C.POINTER(C.c_float), SZ, VP, PD],
     "pc_mlp_train": [VP, VP, VP, SZ, C.POINTER(C.c_float), SZ, C.c_int32, C.c_float, U64, PD],
     "pc_cv_grid": [VP, C.c_int32, C.c_float, C.POINTER(CvDesc)],
@@ -417,6 +420,19 @@ def pc_mlp_get_params(net: int) -> np.ndarray:
 
 def pc_mlp_forward(net: int, d_x: int, n: int, d_y: int) -> None:
     _check(lib().pc_mlp_forward(VP(net), VP(d_x), n, VP(d_y)))
+
+
+def pc_mlp_set_gemm(net: int, kind: int) -> None:
+    """MLP_GEMM_AUTO (tcgen05 forward products where available) or
+    MLP_GEMM_MMA_SYNC (the warp-level kernel for every product)."""
+    _check(lib().pc_mlp_set_gemm(VP(net), int(kind)))
+
+
+def pc_mlp_gemm_info(net: int) -> bool:
+    """True when the forward products run on the tcgen05 tensor cores."""
+    v = C.c_int32(0)
+    _check(lib().pc_mlp_gemm_info(VP(net), C.byref(v)))
+    return bool(v.value)
 
 
 def pc_mlp_gradients(net: int, d_x: int, d_t: int, w, n: int, d_grads: Optional[int] = None) -> float:

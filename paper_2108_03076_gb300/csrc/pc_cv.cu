@@ -30,11 +30,17 @@ namespace {
 // Multilinear interpolation of the d hedge ratios at ln S (given as
 // l2 = log2 S: the axis coordinate is u = l2 ln2 / h - lo / h), and with
 // SLOPES the interpolant's derivatives s[i][j] = d Delta_i / d u_j on the
-// cell (from the same corner values).
+// cell.  The 2^d corner values are reduced one axis at a time, last axis
+// first: a pair (lo, hi) along the axis becomes lo + f (hi - lo), its
+// difference hi - lo is the slope along that axis there, and slopes along
+// axes already reduced are interpolated like the values.  Same interpolant
+// as the sum over corners of the products of (f or 1 - f), in about a third
+// of the arithmetic.
 template <int D, bool SLOPES>
 __device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, const float (&l2)[D],
                                             float (&delta)[D], float (&s)[D][D]) {
   const float4 *tab = reinterpret_cast<const float4 *>(c.tables) + (size_t(k - 1) * 2 + ki) * size_t(c.nodes);
+  constexpr int NC = 1 << D;
   int a[D];
   float f[D];
   const int G = c.grid;
@@ -46,38 +52,45 @@ __device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, cons
     ai = ai < G - 2 ? ai : G - 2;
     a[i] = ai;
     f[i] = u - float(ai);
-    delta[i] = 0.f;
-#pragma unroll
-    for (int j = 0; j < D; ++j) s[i][j] = 0.f;
   }
+  int base = 0;
 #pragma unroll
-  for (int corner = 0; corner < (1 << D); ++corner) {
-    float g[D];
-    int node = 0;
+  for (int ax = 0; ax < D; ++ax) base = base * G + a[ax];
+  // corner c: bit (D - 1 - ax) selects a[ax] + 1 on axis ax
+  float v[NC][D];
 #pragma unroll
-    for (int ax = 0; ax < D; ++ax) {
-      const int bit = (corner >> (D - 1 - ax)) & 1;
-      g[ax] = bit ? f[ax] : 1.f - f[ax];
-      node = node * G + a[ax] + bit;
-    }
-    const float4 v4 = __ldg(tab + node);  // one 16-byte load per corner
-    const float v[3] = {v4.x, v4.y, v4.z};
-    float wgt = 1.f;
+  for (int cn = 0; cn < NC; ++cn) {
+    int off = 0;
 #pragma unroll
-    for (int ax = 0; ax < D; ++ax) wgt *= g[ax];
+    for (int ax = 0; ax < D; ++ax) off = off * G + ((cn >> (D - 1 - ax)) & 1);
+    const float4 v4 = __ldg(tab + base + off);  // one 16-byte load per corner
+    const float w3[3] = {v4.x, v4.y, v4.z};
 #pragma unroll
-    for (int i = 0; i < D; ++i) delta[i] = fmaf(wgt, v[i], delta[i]);
-    if (SLOPES) {
+    for (int i = 0; i < D; ++i) v[cn][i] = w3[i];
+  }
+  float sj[D][NC / 2][D];
 #pragma unroll
-      for (int j = 0; j < D; ++j) {
-        float wj = ((corner >> (D - 1 - j)) & 1) ? 1.f : -1.f;
+  for (int ax = D - 1; ax >= 0; --ax) {
 #pragma unroll
-        for (int ax = 0; ax < D; ++ax)
-          if (ax != j) wj *= g[ax];
+    for (int cn = 0; cn < (1 << ax); ++cn) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) s[i][j] = fmaf(wj, v[i], s[i][j]);
+      for (int i = 0; i < D; ++i) {
+        const float lo = v[2 * cn][i], dd = v[2 * cn + 1][i] - lo;
+        if (SLOPES) {
+#pragma unroll
+          for (int j = ax + 1; j < D; ++j)
+            sj[j][cn][i] = fmaf(f[ax], sj[j][2 * cn + 1][i] - sj[j][2 * cn][i], sj[j][2 * cn][i]);
+          sj[ax][cn][i] = dd;
+        }
+        v[cn][i] = fmaf(f[ax], dd, lo);
       }
     }
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    delta[i] = v[0][i];
+#pragma unroll
+    for (int j = 0; j < D; ++j) s[i][j] = SLOPES ? sj[j][0][i] : 0.f;
   }
 }
 
@@ -215,37 +228,35 @@ __global__ void __launch_bounds__(kBlock) cv_kernel(const PriceArgs a, const CvA
       }
     }
     if (PILOT) {
-      double tp[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      Moments<8> mo;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (!live[q]) continue;
-        const double xd = double(xs[q]), md = double(Mv[q]), m2 = double(M2v[q]);
-        tp[0] += xd;
-        tp[1] += md;
-        tp[2] += m2;
-        tp[3] = fma(xd, md, tp[3]);
-        tp[4] = fma(xd, m2, tp[4]);
-        tp[5] = fma(md, md, tp[5]);
-        tp[6] = fma(m2, m2, tp[6]);
-        tp[7] = fma(md, m2, tp[7]);
+        mo.add(0, xs[q]);
+        mo.add(1, Mv[q]);
+        mo.add(2, M2v[q]);
+        mo.add_prod(3, xs[q], Mv[q]);
+        mo.add_prod(4, xs[q], M2v[q]);
+        mo.add_prod(5, Mv[q], Mv[q]);
+        mo.add_prod(6, M2v[q], M2v[q]);
+        mo.add_prod(7, Mv[q], M2v[q]);
       }
-#pragma unroll
-      for (int v = 0; v < 8; ++v) tp[v] = warp_sum(tp[v]);
+      double tp[8];
+      mo.warp_total(tp);
       finish_tile<8>(a, tile, tp, lane);
     } else {
-      double tp[4] = {0.0, 0.0, 0.0, 0.0};
+      Moments<4> mo;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (!live[q]) continue;
-        const double xd = double(xs[q]);
-        const double yd = double(xs[q] - c.beta * Mv[q] - c.beta2 * M2v[q]);
-        tp[0] += xd;
-        tp[1] = fma(xd, xd, tp[1]);
-        tp[2] += yd;
-        tp[3] = fma(yd, yd, tp[3]);
+        const float y = xs[q] - c.beta * Mv[q] - c.beta2 * M2v[q];
+        mo.add(0, xs[q]);
+        mo.add_prod(1, xs[q], xs[q]);
+        mo.add(2, y);
+        mo.add_prod(3, y, y);
       }
-#pragma unroll
-      for (int v = 0; v < 4; ++v) tp[v] = warp_sum(tp[v]);
+      double tp[4];
+      mo.warp_total(tp);
       finish_tile<4>(a, tile, tp, lane);
     }
   }

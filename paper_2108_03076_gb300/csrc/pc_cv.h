@@ -35,6 +35,9 @@ struct CvArgs {
 
 // Device scratch owned by a network (grow-only, freed with it).
 float *mlp_scratch(struct ::pc_mlp *net, size_t floats);
+// Waits for the context's stream; PC_ETIMEOUT (and the status cleared) if a
+// tensor-core product of the network reported an expired wait.
+pc_status mlp_status(struct ::pc_mlp *net);
 
 struct CvFeatureArgs {
   float ln_spot[kCvMaxD];

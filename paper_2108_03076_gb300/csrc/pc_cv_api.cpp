@@ -200,7 +200,7 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
     e = cudaMemcpyAsync(h0, d0, 4 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) s = cuda_fail(e, "delta0 copy");
   }
-  if (s == PC_OK) s = wait_stream(ctx);
+  if (s == PC_OK) s = mlp_status(net);
   if (s != PC_OK) return s;
   for (int i = 0; i < 3; ++i) c->delta0[i] = i < c->d ? h0[i] : 0.f;
   return PC_OK;

@@ -2,7 +2,8 @@
 // (pc_kernels.cu) and the pathwise-sensitivity kernel (pc_greeks.cu):
 // Philox4x32-10 (Salmon et al., SC'11), 24-bit uniforms, Box-Muller, the
 // date-ordered Brownian bridge with register Philox caches, correlated GBM,
-// the fused multi-asset reads, and the deterministic FP64 reduction.
+// the fused multi-asset reads, and the deterministic reduction (float-pair
+// tile sums, FP64 chunk sums).
 //
 // Per-thread state lives in shared memory as word-interleaved slots: slot s
 // of thread t is at region[s * blockDim.x + t] (float2: two paths per lane),
@@ -364,8 +365,55 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Deterministic reduction.  Tile t's partial (sum, sum of squares) is an FP64
-// warp sum in a fixed shuffle order.  Tiles form chunks of chunk_tiles
+// A tile's moment sums (sum of payoffs, of squares, of products) without
+// the FP64 pipe, which issues at a small fraction of the FP32 rate here:
+// each sum is an unevaluated pair hi + lo of floats.  An addend enters by
+// Knuth's two-sum (hi + x = s + e exactly, e added into lo); a product of
+// two floats enters exactly as its rounded value plus the FMA residual.
+// Only the low parts round, so a warp's 64-path sums carry a relative
+// error of order 2^-45 of the sum of magnitudes (an FP64 sum of the same
+// terms: 2^-47), and become doubles once per tile for the chunk sums.
+template <int W>
+struct Moments {
+  float hi[W], lo[W];
+  __device__ __forceinline__ Moments() {
+#pragma unroll
+    for (int v = 0; v < W; ++v) hi[v] = lo[v] = 0.f;
+  }
+  __device__ __forceinline__ void add(int v, float x) {
+    const float s = __fadd_rn(hi[v], x);
+    const float b = __fsub_rn(s, hi[v]);
+    const float e = __fadd_rn(__fsub_rn(hi[v], __fsub_rn(s, b)), __fsub_rn(x, b));
+    hi[v] = s;
+    lo[v] = __fadd_rn(lo[v], e);
+  }
+  __device__ __forceinline__ void add_prod(int v, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    add(v, p);
+    lo[v] = __fadd_rn(lo[v], __fmaf_rn(x, y, -p));
+  }
+  // warp totals (identical in every lane: the butterfly's additions are
+  // commutative) as doubles
+  __device__ __forceinline__ void warp_total(double (&tp)[W]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int v = 0; v < W; ++v) {
+        const float h = __shfl_xor_sync(kFull, hi[v], o), l = __shfl_xor_sync(kFull, lo[v], o);
+        const float s = __fadd_rn(hi[v], h);
+        const float b = __fsub_rn(s, hi[v]);
+        const float e = __fadd_rn(__fsub_rn(hi[v], __fsub_rn(s, b)), __fsub_rn(h, b));
+        hi[v] = s;
+        lo[v] = __fadd_rn(__fadd_rn(lo[v], l), e);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < W; ++v) tp[v] = double(hi[v]) + double(lo[v]);
+  }
+};
+
+// Deterministic reduction.  Tile t's partials (sum, sum of squares, ...) are
+// the warp's Moments totals, in a fixed shuffle order, as doubles.  Tiles form chunks of chunk_tiles
 // consecutive tiles; the warp that finishes a chunk's last tile sums the
 // chunk's partials in index order (lane l takes tiles l, l+32, ...; then a
 // fixed shuffle tree), and the warp that finishes the last chunk sums the

@@ -443,28 +443,26 @@ __global__ void __launch_bounds__(kBlock) greeks_kernel(const PriceArgs a) {
     g.plo[1] = uint32_t(p1);
     g.phi[1] = uint32_t(p1 >> 32);
     const TV x = eval_greeks<D>(P, pool, R, a, g, live0, live1, Bm, S0, Lm, gl, sig_g);
-    double tp[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    Moments<6> mo;
     const float q0[3] = {x.v.x, x.a.x, x.b.x}, q1[3] = {x.v.y, x.a.y, x.b.y};
     if (live0) {
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        const double v = double(q0[j]);
-        tp[2 * j] += v;
-        tp[2 * j + 1] = fma(v, v, tp[2 * j + 1]);
+        mo.add(2 * j, q0[j]);
+        mo.add_prod(2 * j + 1, q0[j], q0[j]);
         if (WRITE) a.out_paths[i0 * 3 + j] = q0[j];
       }
     }
     if (live1) {
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        const double v = double(q1[j]);
-        tp[2 * j] += v;
-        tp[2 * j + 1] = fma(v, v, tp[2 * j + 1]);
+        mo.add(2 * j, q1[j]);
+        mo.add_prod(2 * j + 1, q1[j], q1[j]);
         if (WRITE) a.out_paths[i1 * 3 + j] = q1[j];
       }
     }
-#pragma unroll
-    for (int j = 0; j < 6; ++j) tp[j] = warp_sum(tp[j]);
+    double tp[6];
+    mo.warp_total(tp);
     finish_tile<6>(a, tile, tp, lane);
   }
   __syncthreads();

@@ -89,19 +89,17 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchArgs b) {
       g.plo[1] = uint32_t(p1);
       g.phi[1] = uint32_t(p1 >> 32);
       const float2 x = eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0);
-      double tp[2] = {0.0, 0.0};
+      Moments<2> mo;
       if (live0) {
-        const double xd = double(x.x);
-        tp[0] += xd;
-        tp[1] = fma(xd, xd, tp[1]);
+        mo.add(0, x.x);
+        mo.add_prod(1, x.x, x.x);
       }
       if (live1) {
-        const double xd = double(x.y);
-        tp[0] += xd;
-        tp[1] = fma(xd, xd, tp[1]);
+        mo.add(0, x.y);
+        mo.add_prod(1, x.y, x.y);
       }
-      tp[0] = warp_sum(tp[0]);
-      tp[1] = warp_sum(tp[1]);
+      double tp[2];
+      mo.warp_total(tp);
       finish_tile<2>(a, tile, tp, lane);
     }
   }

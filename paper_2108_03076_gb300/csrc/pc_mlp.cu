@@ -58,8 +58,6 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float softplus(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
-
 // Stage one k step of an operand: a K-major operand tile is 64 rows of 32
 // halves (row r at s + r*SK), an M/N-major one 32 rows (k) of 64 halves
 // (row k at s + k*SC).  128 threads, two 16-byte chunks each.
@@ -153,7 +151,7 @@ __global__ void __launch_bounds__(128) mlp_gemm(const GemmArgs g) {
         }
         if (EPI == kEpiBiasSoftplus) {
           *reinterpret_cast<__nv_bfloat162 *>(g.Cb + size_t(r) * g.ldc + c) =
-              __floats2bfloat162_rn(softplus(v0), softplus(v1));
+              __floats2bfloat162_rn(softplus_sfu(v0), softplus_sfu(v1));
         } else if (EPI == kEpiBias) {
           *reinterpret_cast<float2 *>(g.Cf + size_t(r) * g.ldc + c) = make_float2(v0, v1);
         } else if (EPI == kEpiDSoftplus) {

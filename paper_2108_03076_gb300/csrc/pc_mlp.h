@@ -2,12 +2,23 @@
 // (pc_mlp.cu) and their host launchers.  Private to the library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
 
 namespace pc {
+
+#ifdef __CUDACC__
+// softplus(z) = max(z, 0) + log(1 + exp(-|z|)) on the SFU (ex2, lg2): the
+// absolute error (about 1e-7) is far inside the BF16 rounding (2^-9
+// relative) of the stored activation, at a fifth of the accurate
+// functions' instructions -- the forward epilogues' main cost.
+__device__ __forceinline__ float softplus_sfu(float z) {
+  return fmaxf(z, 0.f) + __logf(1.f + __expf(-fabsf(z)));
+}
+#endif
 
 // GEMM epilogues of mlp_gemm.
 constexpr int kEpiBiasSoftplus = 0;  // Cb = bf16(softplus(acc + bias))
@@ -34,6 +45,21 @@ struct GemmArgs {
 
 enum GemmKind { kGemmForward, kGemmDataGrad, kGemmWeightGrad };
 cudaError_t launch_gemm(GemmKind kind, int epi, const GemmArgs &g, int splits, cudaStream_t s);
+
+// Forward products on the tcgen05 tensor cores (pc_mlp_tc.cu): both
+// operands K-major, K a multiple of 64, M of 64, N = 64 or a multiple of
+// 128; epilogues kEpiBiasSoftplus and kEpiBias.  *status |= 4 when a
+// bounded wait expires.  gemm_tc_init (once, outside stream capture):
+// cudaErrorNotSupported on devices or drivers without them.
+// The TMA descriptors of a product's operands (encoded once per buffer and
+// shape on the host; kernel parameters by value).
+struct TcMaps {
+  CUtensorMap a, b;
+};
+cudaError_t gemm_tc_init();
+bool gemm_tc_supported(const GemmArgs &g);
+bool make_tc_maps(const GemmArgs &g, TcMaps &m);
+cudaError_t launch_gemm_tc(int epi, const GemmArgs &g, const TcMaps &m, int32_t *status, cudaStream_t s);
 
 // x [n, fin] FP32 -> X [rows, ld] BF16, zero beyond n rows / fin columns.
 cudaError_t launch_to_bf16(const float *x, size_t n, int fin, __nv_bfloat16 *X, size_t rows, int ld,

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "pc_handles.h"
@@ -56,6 +57,10 @@ struct pc_mlp {
   std::vector<float> g_w;
   float *scratch = nullptr;         // caller scratch (mlp_scratch), grow-only
   size_t scratch_cap = 0;
+  int32_t *dstatus = nullptr;       // device status of the tensor-core products
+  int32_t gemm = PC_MLP_GEMM_AUTO;  // product kernel choice (pc_mlp_set_gemm)
+  bool tc_ok = false;               // tcgen05 products available on this device
+  std::map<uint64_t, TcMaps> tc_maps;  // forward operand descriptors by (layer, rows)
 };
 
 namespace pc {
@@ -68,6 +73,17 @@ float *mlp_scratch(pc_mlp *N, size_t floats) {
   if (cudaMalloc(&N->scratch, floats * sizeof(float)) != cudaSuccess) return nullptr;
   N->scratch_cap = floats;
   return N->scratch;
+}
+
+pc_status mlp_status(pc_mlp *N) {
+  int32_t st = 0;
+  CU(cudaMemcpyAsync(&st, N->dstatus, sizeof(st), cudaMemcpyDeviceToHost, N->ctx->stream), "status copy");
+  pc_status r = wait_stream(N->ctx);
+  if (r != PC_OK) return r;
+  if (st == 0) return PC_OK;
+  CU(cudaMemsetAsync(N->dstatus, 0, sizeof(st), N->ctx->stream), "status reset");
+  wait_stream(N->ctx);
+  return fail(PC_ETIMEOUT, "tensor-core product: a bounded wait expired");
 }
 }  // namespace pc
 
@@ -138,6 +154,7 @@ size_t layout(pc_mlp *N, size_t rows) {
   N->loss_part = c.take<float>(512);
   N->loss = c.take<double>(1);
   N->step = c.take<uint64_t>(1);
+  N->dstatus = c.take<int32_t>(1);
   return c.off;
 }
 
@@ -167,7 +184,20 @@ cudaError_t forward(pc_mlp *N, size_t rows, cudaStream_t s) {
       a.Cb = N->H[l];
     }
     a.ldc = N->wp[l + 1];
-    cudaError_t e = launch_gemm(kGemmForward, last ? kEpiBias : kEpiBiasSoftplus, a, 1, s);
+    const int epi = last ? kEpiBias : kEpiBiasSoftplus;
+    bool tc = N->tc_ok && N->gemm == PC_MLP_GEMM_AUTO && gemm_tc_supported(a);
+    const TcMaps *maps = nullptr;
+    if (tc) {
+      const uint64_t key = (uint64_t(l) << 40) | uint64_t(rows);
+      auto it = N->tc_maps.find(key);
+      if (it == N->tc_maps.end()) {
+        TcMaps m;
+        if (make_tc_maps(a, m)) it = N->tc_maps.emplace(key, m).first;
+      }
+      if (it != N->tc_maps.end()) maps = &it->second;
+      tc = maps != nullptr;
+    }
+    cudaError_t e = tc ? launch_gemm_tc(epi, a, *maps, N->dstatus, s) : launch_gemm(kGemmForward, epi, a, 1, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -314,6 +344,8 @@ pc_status pc_mlp_create(pc_ctx *c, const int32_t *widths, int32_t n_widths, uint
     }
   }
   cudaMemsetAsync(N->mem, 0, bytes, c->stream);
+  N->tc_ok = gemm_tc_init() == cudaSuccess;
+  cudaGetLastError();
   pc_status s = upload_padded(N, init.data());
   if (s != PC_OK) {
     cudaFree(N->mem);
@@ -395,7 +427,7 @@ pc_status pc_mlp_gradients(pc_mlp *N, const float *d_x, const float *d_t, const 
     if (st != PC_OK) return st;
   }
   CU(cudaMemcpyAsync(out_loss, N->loss, sizeof(double), cudaMemcpyDeviceToHost, s), "loss copy");
-  return wait_stream(N->ctx);
+  return mlp_status(N);
 }
 
 pc_status pc_mlp_train(pc_mlp *N, const float *d_x, const float *d_t, size_t n_data, const float *w,
@@ -451,9 +483,27 @@ pc_status pc_mlp_train(pc_mlp *N, const float *d_x, const float *d_t, size_t n_d
   }
   for (int32_t i = 0; i < steps; ++i) CU(cudaGraphLaunch(N->exec, c->stream), "training step");
   CU(cudaMemcpyAsync(out_loss, N->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss copy");
-  pc_status st = wait_stream(c);
+  pc_status st = mlp_status(N);
   if (st != PC_OK) return st;
   N->steps += uint64_t(steps);
+  return PC_OK;
+}
+
+pc_status pc_mlp_set_gemm(pc_mlp *N, int32_t kind) {
+  if (!N) return fail(PC_EINVAL, "null network");
+  if (kind != PC_MLP_GEMM_AUTO && kind != PC_MLP_GEMM_MMA_SYNC) return fail(PC_EINVAL, "unknown product kind");
+  if (kind != N->gemm) {
+    wait_stream(N->ctx);
+    if (N->exec) cudaGraphExecDestroy(N->exec);  // the training step is captured again
+    N->exec = nullptr;
+    N->gemm = kind;
+  }
+  return PC_OK;
+}
+
+pc_status pc_mlp_gemm_info(const pc_mlp *N, int32_t *tensor_cores) {
+  if (!N || !tensor_cores) return fail(PC_EINVAL, "null argument");
+  *tensor_cores = N->tc_ok && N->gemm == PC_MLP_GEMM_AUTO ? 1 : 0;
   return PC_OK;
 }
 

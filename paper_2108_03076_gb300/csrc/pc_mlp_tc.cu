@@ -1,0 +1,344 @@
+// pc_mlp_tc.cu -- the network's forward products on the fifth-generation
+// tensor cores: tcgen05.mma with the accumulator in tensor memory (TMEM),
+// operands staged in shared memory by TMA (cp.async.bulk.tensor) in the
+// 128-byte swizzled K-major layout the MMA reads through its shared-memory
+// descriptors.
+//
+// Z[M, N] = H[M, K] W[N, K]^T + b, H the activations (rows = samples,
+// K contiguous) and W a layer's BF16 weights ([out, in], in contiguous):
+// both operands K-major, FP32 accumulation.  One CTA computes a 128 x BN
+// tile (BN = 64 or 128) over the whole K range:
+//   warp 0, lane 0   TMA producer: 64-deep k chunks into a ring of kStages
+//                    stage buffers (A 16 KB, B BN x 128 B), one "full"
+//                    mbarrier per stage (expect_tx = the chunk's bytes) and
+//                    one "empty" mbarrier the MMA side frees it with;
+//   warp 1, lane 0   MMA issuer: four 128 x BN x 16 tcgen05.mma per chunk
+//                    (the descriptor start advanced by 32 bytes per step of
+//                    16 inside the 128-byte swizzle row), tcgen05.commit to
+//                    the stage's empty barrier, and after the last chunk to
+//                    the "done" barrier;
+//   all eight warps  epilogue: warp w reads TMEM lanes 32(w % 4) .. +31
+//                    (tile rows), columns of half w / 4 of the tile, with
+//                    tcgen05.ld 32 columns at a time, adds the bias, applies
+//                    softplus and stores BF16 (hidden layers) or stores
+//                    FP32 (output layer).
+// Two stages (64 KB at BN = 128) let three CTAs share an SM, so 24 warps
+// hide the epilogue's latency.
+// Warp 0 allocates BN TMEM columns and frees them after the epilogue.
+// Every wait is bounded (about a second of SM clocks): on expiry the kernel
+// sets *status, stops issuing work, still commits so the done barrier
+// completes, waits (bounded) for its copies in flight, frees TMEM and
+// returns; the host reports the status.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <mutex>
+
+#include "pc_mlp.h"
+
+namespace pc {
+namespace {
+
+constexpr int kTcBM = 128, kTcBK = 64, kStages = 2, kTcThreads = 256;
+constexpr uint32_t kATileBytes = kTcBM * kTcBK * 2;  // 16 KB
+constexpr long long kWaitCycles = 2000000000ll;      // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of `parity` to complete; false on expiry.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
+// layout (rows of 128 bytes, 8-row groups 1024 bytes apart; the group base
+// 1024-byte aligned).  Fields: start address >> 4 (bits 0-13), leading byte
+// offset >> 4 (16-29, unused by this layout: 1), stride byte offset >> 4
+// (32-45: 1024 B), the fixed value 1 at bits 46-48, base offset 0, swizzle
+// mode 2 = 128 bytes (61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
+         (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1),
+// A and B BF16 (7-9 = 1, 10-12 = 1), both K-major (15, 16 = 0), N >> 3 at
+// bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16_tc(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+        "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+        "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+  int M, N, K;
+  const float *bias;
+  __nv_bfloat16 *Cb;
+  float *Cf;
+  int ldc;
+  int32_t *status;
+};
+
+template <int EPI, int BN>
+__global__ void __launch_bounds__(kTcThreads)
+    mlp_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcArgs g) {
+  constexpr uint32_t kBTileBytes = BN * kTcBK * 2;
+  constexpr uint32_t kStageBytes = kATileBytes + kBTileBytes;
+  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * kStages + 1];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
+  const int nk = g.K / kTcBK;
+  const uint32_t base = (su32(tc_smem_raw) + 1023u) & ~1023u;
+  const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[kStages]), done = su32(&bars[2 * kStages]);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < 2 * kStages + 1; ++s) mbar_init(su32(&bars[s]), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // TMA producer
+    int issued = 0;
+    for (int c = 0; c < nk; ++c) {
+      const int s = c % kStages;
+      if (c >= kStages && !mbar_wait(empty0 + 8 * s, ((c / kStages) + 1) & 1)) {
+        atomicOr(g.status, 4);
+        atomicExch(&abort_flag, 1);
+      }
+      if (*(volatile int *)&abort_flag) break;
+      const uint32_t sa = base + s * kStageBytes, sb = sa + kATileBytes;
+      mbar_expect_tx(full0 + 8 * s, kStageBytes);
+      tma_load_2d(sa, &ta, c * kTcBK, m0, full0 + 8 * s);
+      tma_load_2d(sb, &tb, c * kTcBK, n0, full0 + 8 * s);
+      issued = c + 1;
+    }
+    // copies still in flight finish before the CTA can exit
+    for (int c = issued - kStages > 0 ? issued - kStages : 0; c < issued; ++c)
+      if (!mbar_wait(full0 + 8 * (c % kStages), (c / kStages) & 1)) atomicOr(g.status, 4);
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(kTcBM, BN);
+    for (int c = 0; c < nk; ++c) {
+      const int s = c % kStages;
+      if (*(volatile int *)&abort_flag) break;
+      if (!mbar_wait(full0 + 8 * s, (c / kStages) & 1)) {
+        atomicOr(g.status, 4);
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t sa = base + s * kStageBytes, sb = sa + kATileBytes;
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 16; ++kk)
+        mma_bf16_tc(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc, (c | kk) != 0);
+      mma_commit(empty0 + 8 * s);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+  // epilogue: all warps wait for the accumulator
+  if (!mbar_wait(done, 0)) atomicOr(g.status, 4);
+  __syncwarp();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = m0 + 32 * quarter + lane;
+  const uint32_t trow = tmem + (uint32_t(32 * quarter) << 16);
+#pragma unroll 1
+  for (int j = half * (BN / 2); j < (half + 1) * (BN / 2); j += 32) {
+    float v[32];
+    tmem_ld32(trow + j, v);
+    if (row < g.M) {
+      const float *bias = g.bias + n0 + j;
+      if (EPI == kEpiBiasSoftplus) {
+        uint32_t pk[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float a0 = softplus_sfu(v[2 * i] + __ldg(bias + 2 * i));
+          const float a1 = softplus_sfu(v[2 * i + 1] + __ldg(bias + 2 * i + 1));
+          const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+          pk[i] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(g.Cb + size_t(row) * g.ldc + n0 + j);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+      } else {
+        float4 *dst = reinterpret_cast<float4 *>(g.Cf + size_t(row) * g.ldc + n0 + j);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          dst[q] = make_float4(v[4 * q] + __ldg(bias + 4 * q), v[4 * q + 1] + __ldg(bias + 4 * q + 1),
+                               v[4 * q + 2] + __ldg(bias + 4 * q + 2), v[4 * q + 3] + __ldg(bias + 4 * q + 3));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// 2-D BF16 tensor [rows, cols] (cols contiguous, row stride ld elements),
+// box of box_rows x 64 columns, 128-byte swizzle, zero fill out of range.
+bool make_map(CUtensorMap &m, const __nv_bfloat16 *p, uint64_t rows, uint64_t cols, uint64_t ld,
+              uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint32_t box[2] = {uint32_t(kTcBK), box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(p), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int EPI, int BN>
+constexpr size_t tc_smem() {
+  return size_t(kStages) * (kATileBytes + size_t(BN) * kTcBK * 2) + 1024;
+}
+
+template <int EPI, int BN>
+cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, const TcArgs &a, cudaStream_t s) {
+  const dim3 grid(unsigned(a.N / BN), unsigned((a.M + kTcBM - 1) / kTcBM));
+  mlp_gemm_tc<EPI, BN><<<grid, kTcThreads, tc_smem<EPI, BN>(), s>>>(ta, tb, a);
+  return cudaGetLastError();
+}
+
+template <int EPI, int BN>
+cudaError_t tc_attr() {
+  return cudaFuncSetAttribute(mlp_gemm_tc<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              int(tc_smem<EPI, BN>()));
+}
+
+}  // namespace
+
+cudaError_t gemm_tc_init() {
+  static std::once_flag once;
+  static cudaError_t r = cudaSuccess;
+  std::call_once(once, [] {
+    int dev = 0, major = 0;
+    r = cudaGetDevice(&dev);
+    if (r == cudaSuccess) r = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    if (r == cudaSuccess && major < 10) r = cudaErrorNotSupported;
+    if (r == cudaSuccess && !encode_fn()) r = cudaErrorNotSupported;
+    if (r == cudaSuccess) r = tc_attr<kEpiBiasSoftplus, 64>();
+    if (r == cudaSuccess) r = tc_attr<kEpiBiasSoftplus, 128>();
+    if (r == cudaSuccess) r = tc_attr<kEpiBias, 64>();
+    if (r == cudaSuccess) r = tc_attr<kEpiBias, 128>();
+  });
+  return r;
+}
+
+bool gemm_tc_supported(const GemmArgs &g) {
+  return g.K % kTcBK == 0 && g.K >= kTcBK && g.M % 64 == 0 && g.M > 0 && (g.N == 64 || g.N % 128 == 0) &&
+         g.lda % 8 == 0 && g.ldb % 8 == 0 && g.ldc % 8 == 0;
+}
+
+bool make_tc_maps(const GemmArgs &g, TcMaps &m) {
+  if (!gemm_tc_supported(g) || gemm_tc_init() != cudaSuccess) return false;
+  const int bn = g.N == 64 ? 64 : 128;
+  return make_map(m.a, g.A, uint64_t(g.M), uint64_t(g.K), uint64_t(g.lda), kTcBM) &&
+         make_map(m.b, g.B, uint64_t(g.N), uint64_t(g.K), uint64_t(g.ldb), uint32_t(bn));
+}
+
+cudaError_t launch_gemm_tc(int epi, const GemmArgs &g, const TcMaps &m, int32_t *status, cudaStream_t s) {
+  if (!status || !gemm_tc_supported(g) || (epi != kEpiBiasSoftplus && epi != kEpiBias))
+    return cudaErrorInvalidValue;
+  const cudaError_t r = gemm_tc_init();
+  if (r != cudaSuccess) return r;
+  const int bn = g.N == 64 ? 64 : 128;
+  TcArgs a{g.M, g.N, g.K, g.bias, g.Cb, g.Cf, g.ldc, status};
+  if (epi == kEpiBiasSoftplus) return bn == 64 ? launch_tc<kEpiBiasSoftplus, 64>(m.a, m.b, a, s)
+                                               : launch_tc<kEpiBiasSoftplus, 128>(m.a, m.b, a, s);
+  return bn == 64 ? launch_tc<kEpiBias, 64>(m.a, m.b, a, s) : launch_tc<kEpiBias, 128>(m.a, m.b, a, s);
+}
+
+}  // namespace pc

@@ -1,5 +1,5 @@
 // pc_price.cuh -- the pricing kernel's body: program staging, the tile
-// loop and the per-tile FP64 reduction, generic in the payoff evaluator
+// loop and the per-tile reduction, generic in the payoff evaluator
 // (the interpreter eval_path, or a run-time specialised evaluator).
 #pragma once
 
@@ -41,21 +41,19 @@ __device__ __forceinline__ void price_tiles(const PriceArgs &a, EVAL eval) {
     g.plo[1] = uint32_t(p1);
     g.phi[1] = uint32_t(p1 >> 32);
     const float2 x = eval(P, pool, R, g, live0, live1, Bm, S0);
-    double tp[2] = {0.0, 0.0};
+    Moments<2> mo;
     if (live0) {
-      const double xd = double(x.x);
-      tp[0] += xd;
-      tp[1] = fma(xd, xd, tp[1]);
+      mo.add(0, x.x);
+      mo.add_prod(1, x.x, x.x);
       if (WRITE) a.out_paths[i0] = x.x;
     }
     if (live1) {
-      const double xd = double(x.y);
-      tp[0] += xd;
-      tp[1] = fma(xd, xd, tp[1]);
+      mo.add(0, x.y);
+      mo.add_prod(1, x.y, x.y);
       if (WRITE) a.out_paths[i1] = x.y;
     }
-    tp[0] = warp_sum(tp[0]);
-    tp[1] = warp_sum(tp[1]);
+    double tp[2];
+    mo.warp_total(tp);
     finish_tile<2>(a, tile, tp, lane);
   }
   // the last block to exit re-zeroes the tile counter: no warp grabs tiles

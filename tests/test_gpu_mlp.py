@@ -125,3 +125,66 @@ def test_training_fits_and_is_deterministic(ctx):
             pc.pc_mlp_destroy(net)
         assert last < 0.05 * first, (first, last)
     np.testing.assert_array_equal(runs[0], runs[1])
+
+
+@pytest.mark.parametrize("widths,n", [(WIDTHS, 13825), ([16, 1024, 384, 5], 4099), ([9, 128, 64], 200)])
+def test_tensor_core_forward_matches_oracle_and_warp_kernel(ctx, widths, n):
+    """tcgen05 forward products (TMA-staged, TMEM accumulators) on the
+    table-build size (13,825 rows: 109 row tiles, the last one ragged), a
+    deep K (1024: sixteen 64-deep chunks through the four-stage ring) and
+    narrow layers (N = 64 tiles), against the oracle and the warp-level
+    kernel (same BF16 operands, FP32 sums in another order)."""
+    rng = np.random.default_rng(n + len(widths))
+    params = mlp.init(widths, rng)
+    net = pc.pc_mlp_create(ctx, widths, 16384)
+    try:
+        assert pc.pc_mlp_gemm_info(net), "tcgen05 products not available"
+        pc.pc_mlp_set_params(net, flat(params))
+        x = rng.normal(size=(n, widths[0])).astype(np.float32)
+        dx = torch.tensor(x, device="cuda")
+        outs = []
+        for kind in (pc.MLP_GEMM_AUTO, pc.MLP_GEMM_MMA_SYNC):
+            pc.pc_mlp_set_gemm(net, kind)
+            dy = torch.full((n, widths[-1]), float("nan"), dtype=torch.float32, device="cuda")
+            pc.pc_mlp_forward(net, dx.data_ptr(), n, dy.data_ptr())
+            torch.cuda.synchronize()
+            outs.append(dy.double().cpu().numpy())
+        assert not pc.pc_mlp_gemm_info(net)
+        ref, _ = mlp.forward(rounded(params), bf16(x))
+        tc, ws = outs
+        assert np.isfinite(tc).all()
+        assert rel_err(tc, ref) < 1.5e-2, rel_err(tc, ref)
+        assert np.abs(tc - ref).max() < 5e-2 * np.abs(ref).max() + 1e-3
+        # the two kernels differ only by FP32 summation order (and the BF16
+        # rounding of hidden activations it can flip)
+        assert rel_err(tc, ws) < 5e-3, rel_err(tc, ws)
+    finally:
+        pc.pc_mlp_destroy(net)
+
+
+def test_tensor_core_training_matches_warp_kernel(ctx):
+    """The training step with tcgen05 forward products fits like the
+    warp-level kernel's and is deterministic."""
+    rng = np.random.default_rng(19)
+    n = 1 << 13
+    x = rng.uniform(-1, 1, size=(n, 16)).astype(np.float32)
+    t = np.stack([x[:, :4].sum(1), np.sin(2 * x[:, 0]), x[:, 1] * x[:, 2], np.maximum(x[:, 3], 0),
+                  np.zeros(n)], 1).astype(np.float32)
+    w = np.array([1, 1, 1, 1, 0], np.float32)
+    dx, dt = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    res = {}
+    for kind, rep in ((pc.MLP_GEMM_AUTO, 0), (pc.MLP_GEMM_AUTO, 1), (pc.MLP_GEMM_MMA_SYNC, 0)):
+        net = pc.pc_mlp_create(ctx, WIDTHS, 1024, seed=3)
+        try:
+            pc.pc_mlp_set_gemm(net, kind)
+            first = pc.pc_mlp_train(net, dx.data_ptr(), dt.data_ptr(), n, w, 512, 1, 1e-3, 77)
+            last = pc.pc_mlp_train(net, dx.data_ptr(), dt.data_ptr(), n, w, 512, 800, 1e-3, 77)
+            res[kind, rep] = (first, last, pc.pc_mlp_get_params(net))
+        finally:
+            pc.pc_mlp_destroy(net)
+    np.testing.assert_array_equal(res[pc.MLP_GEMM_AUTO, 0][2], res[pc.MLP_GEMM_AUTO, 1][2])
+    f_tc, l_tc, _ = res[pc.MLP_GEMM_AUTO, 0]
+    f_ws, l_ws, _ = res[pc.MLP_GEMM_MMA_SYNC, 0]
+    assert f_tc == pytest.approx(f_ws, rel=1e-2)
+    assert l_tc < 0.1 * f_tc and l_ws < 0.1 * f_ws
+    assert l_tc == pytest.approx(l_ws, rel=0.5)
