@@ -447,8 +447,8 @@ __device__ __noinline__ void finish_tile(const PriceArgs &a, uint64_t tile, cons
   if (lane == 0) {
 #pragma unroll
     for (int v = 0; v < W; ++v) a.tile_partials[tile * W + v] = tp[v];
-    __threadfence();
-    seen = atomicAdd(chunk_cnt + chunk, 1u);
+    // release: the partials are visible before the count that reports them
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], 1;" : "=r"(seen) : "l"(chunk_cnt + chunk) : "memory");
   }
   seen = __shfl_sync(kFull, seen, 0);
   if (seen != size - 1) return;
@@ -461,8 +461,7 @@ __device__ __noinline__ void finish_tile(const PriceArgs &a, uint64_t tile, cons
 #pragma unroll
     for (int v = 0; v < W; ++v) chunk_part[size_t(chunk) * W + v] = acc[v];
     chunk_cnt[chunk] = 0;
-    __threadfence();
-    done = atomicAdd(ctr + 2, 1ull);
+    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(done) : "l"(ctr + 2) : "memory");
   }
   done = __shfl_sync(kFull, done, 0);
   if (done != a.n_chunks - 1) return;
