@@ -34,6 +34,7 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
 #define JUMP_W JUMP_TO(int(I.w))
 #define JUMP_2 JUMP_TO(pc + 2)
 #define NEXT_INSN P[pc + 1]
+#define ENSURE(o) ensure(o)
   uint4 I = P[0];
   for (;;) {
     switch (I.x & 0xffu) {
@@ -46,6 +47,7 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
 #undef JUMP_W
 #undef JUMP_2
 #undef NEXT_INSN
+#undef ENSURE
 #undef PUSH
 #undef STK
 #undef BINF

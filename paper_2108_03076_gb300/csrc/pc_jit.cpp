@@ -43,26 +43,113 @@ std::string insn_literal(const XInsn &I) {
   return "make_uint4(" + hex(I.opa) + ", " + hex(I.b) + ", " + hex(I.c) + ", " + hex(I.e) + ")";
 }
 
-// Instructions that read simulated dates (and may have to generate them);
-// above this many, the date generator is called out of line instead of
-// being inlined at each of them.
+// Above this many reading instructions a program whose stack depths are
+// not known calls the date generator out of line.
 constexpr int kInlineDateSites = 12;
+
+// Instructions that read simulated dates (and may have to generate them).
+bool reads_dates(const XInsn &I) {
+  const uint32_t op = I.opa & 0xffu;
+  return op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_LRED || op == X_LANY;
+}
 
 int date_sites(const Program &p) {
   int n = 0;
-  for (const XInsn &I : p.code) {
-    const uint32_t op = I.opa & 0xffu;
-    n += op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_LRED || op == X_LANY;
-  }
+  for (const XInsn &I : p.code) n += reads_dates(I);
   return n;
+}
+
+// The evaluator's operand-stack pointer (sp) before each instruction, from
+// every opcode's effect on each of its exits (the cases of pc_ops.inc):
+// -1 for instructions no path reaches.  False when an opcode has no known
+// effect, a depth leaves [0, frame_slots), or two paths meet with different
+// depths -- the program is then specialised without re-entry points.
+bool stack_depths(const Program &p, std::vector<int> &sp_at) {
+  const int n = int(p.code.size());
+  sp_at.assign(size_t(n), -1);
+  if (n == 0) return false;
+  std::vector<int> work;
+  bool ok = true;
+  auto flow = [&](uint32_t t, int v) {
+    if (t >= uint32_t(n) || v < 0 || v >= std::max(1, int(p.frame_slots))) {
+      ok = false;
+      return;
+    }
+    if (sp_at[t] < 0) {
+      sp_at[t] = v;
+      work.push_back(int(t));
+    } else if (sp_at[t] != v) {
+      ok = false;
+    }
+  };
+  flow(0, 0);
+  while (ok && !work.empty()) {
+    const int i = work.back();
+    work.pop_back();
+    const XInsn &I = p.code[size_t(i)];
+    const int s = sp_at[size_t(i)];
+    const uint32_t nx = uint32_t(i + 1);
+    switch (I.opa & 0xffu) {
+      case X_END: break;
+      case X_CONST: case X_MODEL: case X_PAYOFF: case X_TIME: case X_NOW: case X_MODEL_MULK:
+      case X_MODEL_DIVK: case X_LRED: case X_LANY:
+        flow(nx, s + 1);
+        break;
+      case X_NEGF: case X_NOT: case X_ADDFK: case X_SUBFK: case X_MULFK: case X_DIVFK: case X_MAXFK:
+      case X_MINFK: case X_LTFK: case X_LEFK: case X_EQFK: case X_RSUBFK: case X_RDIVFK: case X_RLTFK:
+      case X_RLEFK: case X_LOOP: case X_LEND:
+        flow(nx, s);
+        break;
+      case X_ADDF: case X_SUBF: case X_MULF: case X_DIVF: case X_MAXF: case X_MINF: case X_LTF: case X_LEF:
+      case X_EQF: case X_ADDI: case X_SUBI: case X_MULI: case X_MAXI: case X_MINI: case X_LTI: case X_LEI:
+      case X_EQI: case X_AND: case X_OR: case X_LLATCH:
+        flow(nx, s - 1);
+        break;
+      case X_SEL: flow(nx, s - 2); break;
+      case X_IF: case X_ELSE:  // NEXT, or push a placeholder and JUMP_Z
+        flow(nx, s);
+        flow(I.c, s + 1);
+        break;
+      case X_LTEST:  // pop; NEXT or JUMP_Z
+        flow(nx, s - 1);
+        flow(I.c, s - 1);
+        break;
+      case X_LSTEPK:  // pop; push the result and JUMP_W, NEXT, or JUMP_Z
+        flow(I.e, s);
+        flow(nx, s - 1);
+        flow(I.c, s - 1);
+        break;
+      case X_LNEXT:
+        flow(I.e, s + 1);
+        flow(nx, s);
+        flow(I.c, s);
+        break;
+      case X_LOOPANY:  // push the result and JUMP_W, or JUMP_2 (pc + 1 is a descriptor)
+        flow(I.e, s + 1);
+        flow(uint32_t(i + 2), s);
+        break;
+      default: ok = false; break;
+    }
+  }
+  return ok;
 }
 
 // Straight-line evaluator for the program and d underlyings, and the
 // pricing kernel around it (per-path payoffs written out when `write`).
+// With two or more reading instructions and known stack depths, the date
+// generator has one copy: a reading instruction that needs dates jumps to
+// it and it jumps back to the top of that instruction, restoring the
+// static stack pointer there (so the operand stack stays in registers).
+// Otherwise the generator is inlined at each reading instruction (out of
+// line beyond kInlineDateSites of them).
 std::string generate(const Program &p, int d, bool write) {
   std::ostringstream o;
   const size_t n = p.code.size();
-  if (date_sites(p) > kInlineDateSites) o << "#define PC_JIT_OUTLINE_DATES 1\n";
+  std::vector<int> sp_at;
+  const bool shared = date_sites(p) >= 2 && stack_depths(p, sp_at);
+  // without re-entry points, many reading instructions call one
+  // out-of-line copy instead of inlining the generator at each
+  if (!shared && date_sites(p) > kInlineDateSites) o << "#define PC_JIT_OUTLINE_DATES 1\n";
   o << "#include \"pc_price.cuh\"\n"
     << "namespace pc {\n"
     << "namespace {\n"
@@ -74,6 +161,18 @@ std::string generate(const Program &p, int d, bool write) {
     << "    const float (&S0)[D], int *frontier = nullptr) {\n"
     << "#include \"pc_eval_state.inc\"\n"
     << "  (void)pc;\n";
+  if (shared) {
+    o << "  int need_ = 0, resume_ = -1;\n"
+      << "  goto L0;\n"
+      << "PC_GEN:\n"
+      << "  while (ps.f < need_) gen_date<D, false, GW>(ps.f + 1, ps, m, lay, g, R, Bm, S0);\n"
+      << "  switch (resume_) {\n";
+    for (size_t i = 0; i < n; ++i)
+      if (reads_dates(p.code[i]) && sp_at[i] >= 0)
+        o << "    case " << i << ": sp = " << sp_at[i] << "; goto L" << i << ";\n";
+    o << "    default: return tos;\n"
+      << "  }\n";
+  }
   for (size_t i = 0; i < n; ++i) {
     const XInsn &I = p.code[i];
     const size_t nx = i + 1 < n ? i + 1 : i;
@@ -83,10 +182,16 @@ std::string generate(const Program &p, int d, bool write) {
       << "#define JUMP_Z { goto " << lbl(I.c) << "; }\n"
       << "#define JUMP_W { goto " << lbl(I.e) << "; }\n"
       << "#define JUMP_2 { goto " << lbl(i + 2) << "; }\n"
-      << "#define NEXT_INSN " << (i + 1 < n ? insn_literal(p.code[i + 1]) : insn_literal(I)) << "\n"
-      << "  const uint4 I = " << insn_literal(I) << ";\n"
+      << "#define NEXT_INSN " << (i + 1 < n ? insn_literal(p.code[i + 1]) : insn_literal(I)) << "\n";
+    if (shared && reads_dates(I) && sp_at[i] >= 0)
+      o << "#define ENSURE(o) { if ((o) > m.n || (o) < -m.n_hist) { atomicOr(a.status, 1); "
+           "(o) = (o) > m.n ? m.n : -m.n_hist; } if (ps.f < (o)) { need_ = (o); resume_ = "
+        << i << "; goto PC_GEN; } }\n";
+    else
+      o << "#define ENSURE(o) ensure(o)\n";
+    o << "  const uint4 I = " << insn_literal(I) << ";\n"
       << "  {\n" << case_text(I.opa & 0xffu) << "  }\n"
-      << "#undef NEXT\n#undef JUMP_Z\n#undef JUMP_W\n#undef JUMP_2\n#undef NEXT_INSN\n"
+      << "#undef NEXT\n#undef JUMP_Z\n#undef JUMP_W\n#undef JUMP_2\n#undef NEXT_INSN\n#undef ENSURE\n"
       << "}\n";
   }
   o << "  return tos;\n"
