@@ -10,9 +10,10 @@ the scheme below is the one the GPU engine implements, restated plainly:
   "Parallel Random Numbers: As Easy as 1, 2, 3" (SC'11), from its published
   definition: 10 rounds, multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key
   increments 0x9E3779B9 / 0xBB67AE85, key bumped between rounds.
-* normal number m of a path (m = j*d + i: bridge node j, underlying i) comes
-  from Philox counter (m >> 2, path_lo, path_hi, stream), key (seed_lo,
-  seed_hi), output word m & 3.
+* normal number m of a path (m = j*s + i: bridge node j, underlying i,
+  stride s = d, except s = 4 for d = 3 so that a node's three normals are
+  the first three words of one block) comes from Philox counter (m >> 2,
+  path_lo, path_hi, stream), key (seed_lo, seed_hi), output word m & 3.
 * uniform u = ((x >> 8) + 0.5) * 2^-24 for a 32-bit output x.
 * Box-Muller on the word pairs (0,1) and (2,3): with u_a the even word and
   u_b the odd word, r = sqrt(-2 ln u_a); the even word's normal is
@@ -205,13 +206,19 @@ class Market:
         return math.exp(-self.r * self.hist_days[k - 1] / 365.0)
 
 
+def normal_stride(d: int) -> int:
+    """Normals reserved per bridge node (m = j * stride + i)."""
+    return 4 if d == 3 else d
+
+
 def simulate(mk: Market, seed: int, stream: int, paths: np.ndarray) -> np.ndarray:
     """S[p, i, o] for the paths ``paths`` (global indices), o = 0..n."""
     n, d = mk.n, mk.d
     paths = np.asarray(paths, dtype=np.uint64)
     tau = mk.tau()
     nodes = bridge_schedule(tau)
-    z = normals(seed, stream, paths, n * d).reshape(len(paths), n, d)   # [p, j, i]
+    s = normal_stride(d)
+    z = normals(seed, stream, paths, n * s).reshape(len(paths), n, s)[:, :, :d]   # [p, j, i]
     W = bridge_apply(nodes, np.moveaxis(z, 2, 1), n)                     # [p, i, o]
     L = mk.cholesky()
     X = np.einsum("ik,pko->pio", L, W)

@@ -130,9 +130,10 @@ pc_status build_model(const pc_model_desc &desc, ModelHost &M, std::string &err)
 
   // Register cache slots: caching level l saves one Philox block for every
   // node of l whose first block is the previous same-level node's last one.
+  const uint32_t stride = uint32_t(normal_stride(d));
   std::vector<int> saved(n_levels, 0);
   for (size_t j = 1; j < nodes.size(); ++j) {
-    const uint32_t m0 = uint32_t(j) * d;
+    const uint32_t m0 = uint32_t(j) * stride;
     if (nodes[j - 1].level == nodes[j].level && ((m0 - 1) >> 2) == (m0 >> 2)) ++saved[nodes[j].level];
   }
   std::vector<int> slot_of(n_levels, -1);
@@ -178,7 +179,7 @@ pc_status build_model(const pc_model_desc &desc, ModelHost &M, std::string &err)
       op.m = uint16_t(nd.m);
       op.flags = 0;
       if (nd.r < 0) op.flags |= BR_ROOT;
-      const uint32_t m0 = uint32_t(j) * d, b0 = m0 >> 2, b1 = (m0 + d - 1) >> 2;
+      const uint32_t m0 = uint32_t(j) * stride, b0 = m0 >> 2, b1 = (m0 + d - 1) >> 2;
       op.b0 = b0;
       op.lane0 = uint16_t(m0 & 3u);
       op.slot = 0;
@@ -189,7 +190,7 @@ pc_status build_model(const pc_model_desc &desc, ModelHost &M, std::string &err)
         if (j > 0 && nodes[j - 1].level == nd.level && ((m0 - 1) >> 2) == b0)
           op.flags |= BR_FROM_CACHE;
         if (j + 1 < int(nodes.size()) && nodes[j + 1].level == nd.level &&
-            ((uint32_t(j + 1) * d) >> 2) == b1)
+            ((uint32_t(j + 1) * stride) >> 2) == b1)
           op.flags |= BR_STORE;
       }
       M.ops.push_back(op);

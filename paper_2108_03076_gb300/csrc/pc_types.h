@@ -121,13 +121,22 @@ struct BridgeOp {
 };
 static_assert(sizeof(BridgeOp) == 32, "BridgeOp layout: two 16-byte loads");
 
+// Normal number m of a path for bridge node j and underlying i is
+// m = j * normal_stride(d) + i; it is word m & 3 of Philox block m >> 2.
+// With d = 3 the stride is 4: a node's three normals are the first three
+// words of its own block, instead of straddling blocks that date-ordered
+// traversal visits far apart (one block per node, against about 1.3 with
+// packed normals and a one-level cache).
+constexpr int normal_stride(int d) { return d == 3 ? 4 : d; }
+
 // Philox block caches live in registers: up to cache_slots(d) bisection
 // levels (the ones whose caching saves the most Philox evaluations) get a
-// slot.  With d = 4 a node uses exactly one block, so nothing is shared.
-// More slots save Philox evaluations but cost registers and resident warps;
-// these counts were the fastest measured on GB300 for 365-date barriers.
+// slot.  With d = 3 (padded) and d = 4 a node uses exactly one block, so
+// nothing is shared.  More slots save Philox evaluations but cost registers
+// and resident warps; these counts were the fastest measured on GB300 for
+// 365-date barriers.
 constexpr int kMaxCacheSlots = 5;
-constexpr int cache_slots(int d) { return d == 1 ? 3 : d == 2 ? 2 : d == 3 ? 1 : 0; }
+constexpr int cache_slots(int d) { return d == 1 ? 3 : d == 2 ? 2 : 0; }
 
 enum : uint16_t {
   BR_ROOT = 1,        // first node (last date): W = sd * z, no endpoint reads
