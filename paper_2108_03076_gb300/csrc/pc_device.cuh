@@ -115,6 +115,7 @@ __device__ __forceinline__ void win_store(float2 *R, const Layout &lay, int w, f
 template <int D>
 struct PathState {
   static constexpr int kSlots = cache_slots(D) > 0 ? cache_slots(D) : 1;
+  static constexpr bool kOwnBlock = normal_stride(D) == 4;  // a node's normals: words 0..D-1 of one block
   float2 w[D];                  // W at the last produced date
   float2 cache[kSlots][4];      // last Philox block (4 normals) of each cached level
   int f;                        // last produced ordinal (frontier), warp-uniform
@@ -161,6 +162,14 @@ __device__ __forceinline__ void cache_store(PathState<D> &ps, int slot, const fl
 template <int D>
 __device__ __forceinline__ void node_normals(const BridgeOp &op, const Rng2 &g, PathState<D> &ps,
                                              float2 (&z)[D]) {
+  if constexpr (PathState<D>::kOwnBlock) {
+    // a node owns its block: words 0 .. D-1, no cache, no straddling
+    float2 e[4];
+    block_normals2(op.b0, g, e);
+#pragma unroll
+    for (int i = 0; i < D; ++i) z[i] = e[i];
+    return;
+  }
   const uint32_t b0 = op.b0;
   const int lane0 = int(op.lane0);
   float2 e[8];
