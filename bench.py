@@ -57,7 +57,10 @@ def dist_env():
 
 
 def alg_ops_per_path(info) -> dict:
-    """Algorithmic thread-operations of generating one full path (all dates):
+    """Algorithmic thread-operations of generating one full path (all dates),
+    counted on the method's minimum of random numbers (n d normals: n d / 4
+    Philox blocks, n d / 2 Box-Muller pairs; the kernel draws one block per
+    bridge node, which is more for d < 4 and is not counted):
     Philox4x32-10: 10 rounds x (2 mul.lo + 2 mul.hi + 2 three-way xor) = 60;
     Box-Muller pair: 2 shifts, 2 int->float, 2 FMA (u_a, angle), lg2, mul,
     sqrt, sin, cos, 2 mul = 13 (4 on the MUFU pipe);
@@ -65,9 +68,9 @@ def alg_ops_per_path(info) -> dict:
     correlation + GBM per date: d(d+1)/2 FMA + d ex2 + d mul.
     The payoff's own arithmetic is not counted (a lower bound)."""
     d, n = info.d, info.n_dates
-    ops = (60 * info.philox_blocks + 13 * info.box_muller_pairs + (3 * n * d - 2 * d)
-           + n * (d * (d + 1) // 2 + 2 * d))
-    mufu = 4 * info.box_muller_pairs + n * d
+    blocks, pairs = n * d / 4.0, n * d / 2.0
+    ops = (60 * blocks + 13 * pairs + (3 * n * d - 2 * d) + n * (d * (d + 1) // 2 + 2 * d))
+    mufu = 4 * pairs + n * d
     return {"ops": ops, "mufu": mufu}
 
 

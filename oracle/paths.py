@@ -10,9 +10,8 @@ the scheme below is the one the GPU engine implements, restated plainly:
   "Parallel Random Numbers: As Easy as 1, 2, 3" (SC'11), from its published
   definition: 10 rounds, multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key
   increments 0x9E3779B9 / 0xBB67AE85, key bumped between rounds.
-* normal number m of a path (m = j*s + i: bridge node j, underlying i,
-  stride s = d, except s = 4 for d = 3 so that a node's three normals are
-  the first three words of one block) comes from Philox counter (m >> 2,
+* normal number m of a path (m = 4 j + i: bridge node j owns Philox block j,
+  underlying i < d <= 4 takes its word i) comes from Philox counter (m >> 2,
   path_lo, path_hi, stream), key (seed_lo, seed_hi), output word m & 3.
 * uniform u = ((x >> 8) + 0.5) * 2^-24 for a 32-bit output x.
 * Box-Muller on the word pairs (0,1) and (2,3): with u_a the even word and
@@ -207,8 +206,9 @@ class Market:
 
 
 def normal_stride(d: int) -> int:
-    """Normals reserved per bridge node (m = j * stride + i)."""
-    return 4 if d == 3 else d
+    """Normals reserved per bridge node (m = j * stride + i): one Philox
+    block of 4 words per node, whatever d (<= 4)."""
+    return 4
 
 
 def simulate(mk: Market, seed: int, stream: int, paths: np.ndarray) -> np.ndarray:

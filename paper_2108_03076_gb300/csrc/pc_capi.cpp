@@ -582,11 +582,10 @@ pc_status pc_model_query(const pc_model *m, pc_model_info *info) {
   info->t_now = H.t_now;
   info->bridge_levels = H.n_levels;
   info->bridge_stack = H.bstack;
-  int32_t blocks = 0;
-  for (const BridgeOp &op : H.ops)
-    blocks += ((op.flags & BR_FROM_CACHE) ? 0 : 1) + ((op.flags & BR_TWO_BLOCKS) ? 1 : 0);
+  // one Philox block per bridge node; d <= 2 uses one Box-Muller pair of it
+  const int32_t blocks = int32_t(H.ops.size());
   info->philox_blocks = blocks;
-  info->box_muller_pairs = 2 * blocks;
+  info->box_muller_pairs = (H.d <= 2 ? 1 : 2) * blocks;
   return PC_OK;
 }
 
@@ -883,7 +882,7 @@ pc_status pc_debug_bridge(const pc_model_desc *desc, int32_t *date_ops, uint32_t
     std::memcpy(w + 1, &o.wr, 4);
     std::memcpy(w + 2, &o.sd, 4);
     w[3] = o.j;
-    w[4] = uint32_t(o.slot) | (uint32_t(o.flags) << 16);
+    w[4] = uint32_t(o.flags) << 16;
     w[5] = o.m;
   }
   return PC_OK;

@@ -1,7 +1,7 @@
 // pc_device.cuh -- device building blocks shared by the pricing kernel
 // (pc_kernels.cu) and the pathwise-sensitivity kernel (pc_greeks.cu):
 // Philox4x32-10 (Salmon et al., SC'11), 24-bit uniforms, Box-Muller, the
-// date-ordered Brownian bridge with register Philox caches, correlated GBM,
+// date-ordered Brownian bridge (one Philox block per node), correlated GBM,
 // the fused multi-asset reads, and the deterministic reduction (float-pair
 // tile sums, FP64 chunk sums).
 //
@@ -114,95 +114,28 @@ __device__ __forceinline__ void win_store(float2 *R, const Layout &lay, int w, f
 
 template <int D>
 struct PathState {
-  static constexpr int kSlots = cache_slots(D) > 0 ? cache_slots(D) : 1;
-  static constexpr bool kOwnBlock = normal_stride(D) == 4;  // a node's normals: words 0..D-1 of one block
   float2 w[D];                  // W at the last produced date
-  float2 cache[kSlots][4];      // last Philox block (4 normals) of each cached level
   int f;                        // last produced ordinal (frontier), warp-uniform
   int bsp;                      // bridge stack size, warp-uniform
 };
 
-// Register cache access with compile-time indices (slot is warp-uniform).
-template <int D, int S>
-__device__ __forceinline__ void cache_copy_in(const PathState<D> &ps, float2 *e) {
-  if constexpr (S < PathState<D>::kSlots) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) e[q] = ps.cache[S][q];
-  }
-}
-template <int D, int S>
-__device__ __forceinline__ void cache_copy_out(PathState<D> &ps, const float2 *e) {
-  if constexpr (S < PathState<D>::kSlots) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) ps.cache[S][q] = e[q];
-  }
-}
+// The normals of bridge node j for both paths: words 0 .. D-1 of Philox
+// block j (see BridgeOp).  D <= 2 needs only the first Box-Muller pair.
 template <int D>
-__device__ __forceinline__ void cache_load(const PathState<D> &ps, int slot, float2 *e) {
-  switch (slot) {
-    case 0: cache_copy_in<D, 0>(ps, e); break;
-    case 1: cache_copy_in<D, 1>(ps, e); break;
-    case 2: cache_copy_in<D, 2>(ps, e); break;
-    case 3: cache_copy_in<D, 3>(ps, e); break;
-    default: cache_copy_in<D, 4>(ps, e); break;
-  }
-}
-template <int D>
-__device__ __forceinline__ void cache_store(PathState<D> &ps, int slot, const float2 *e) {
-  switch (slot) {
-    case 0: cache_copy_out<D, 0>(ps, e); break;
-    case 1: cache_copy_out<D, 1>(ps, e); break;
-    case 2: cache_copy_out<D, 2>(ps, e); break;
-    case 3: cache_copy_out<D, 3>(ps, e); break;
-    default: cache_copy_out<D, 4>(ps, e); break;
-  }
-}
-
-// Normals j*D .. j*D+D-1 of bridge node j for both paths (see BridgeOp).
-template <int D>
-__device__ __forceinline__ void node_normals(const BridgeOp &op, const Rng2 &g, PathState<D> &ps,
-                                             float2 (&z)[D]) {
-  if constexpr (PathState<D>::kOwnBlock) {
-    // a node owns its block: words 0 .. D-1, no cache, no straddling
-    float2 e[4];
-    block_normals2(op.b0, g, e);
+__device__ __forceinline__ void node_normals(const BridgeOp &op, const Rng2 &g, float2 (&z)[D]) {
+  if constexpr (D <= 2) {
+    const uint4 x0 = philox(make_uint4(op.j, g.plo[0], g.phi[0], g.stream), g.k0, g.k1);
+    const uint4 x1 = philox(make_uint4(op.j, g.plo[1], g.phi[1], g.stream), g.k0, g.k1);
+    float2 e[2];
+    box_muller(x0.x, x0.y, e[0].x, e[1].x);
+    box_muller(x1.x, x1.y, e[0].y, e[1].y);
 #pragma unroll
     for (int i = 0; i < D; ++i) z[i] = e[i];
-    return;
-  }
-  const uint32_t b0 = op.b0;
-  const int lane0 = int(op.lane0);
-  float2 e[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) e[q] = make_float2(0.f, 0.f);
-  if (op.flags & BR_FROM_CACHE) {
-    cache_load(ps, op.slot, e);
   } else {
-    block_normals2(b0, g, e);
-  }
-  const bool two = D > 1 && (op.flags & BR_TWO_BLOCKS);
-  if (two) block_normals2(b0 + 1, g, e + 4);
-  if (op.flags & BR_STORE) {
-    if (two) cache_store(ps, op.slot, e + 4);  // constant offsets keep e[] in registers
-    else cache_store(ps, op.slot, e);
-  }
-  switch (lane0) {
-    case 0:
+    float2 e[4];
+    block_normals2(op.j, g, e);
 #pragma unroll
-      for (int i = 0; i < D; ++i) z[i] = e[i];
-      break;
-    case 1:
-#pragma unroll
-      for (int i = 0; i < D; ++i) z[i] = e[1 + i];
-      break;
-    case 2:
-#pragma unroll
-      for (int i = 0; i < D; ++i) z[i] = e[2 + i];
-      break;
-    default:
-#pragma unroll
-      for (int i = 0; i < D; ++i) z[i] = e[3 + i];
-      break;
+    for (int i = 0; i < D; ++i) z[i] = e[i];
   }
 }
 
@@ -214,11 +147,11 @@ __device__ __forceinline__ BridgeOp load_op(const BridgeOp *p) {
   op.wr = __uint_as_float(a.y);
   op.sd = __uint_as_float(a.z);
   op.j = a.w;
-  op.slot = uint16_t(b.x & 0xffffu);
+  op.pad0 = 0;
   op.flags = uint16_t(b.x >> 16);
   op.m = uint16_t(b.y & 0xffffu);
-  op.lane0 = uint16_t(b.y >> 16);
-  op.b0 = b.z;
+  op.pad1 = 0;
+  op.pad2 = 0;
   op.level = b.w;
   return op;
 }
@@ -245,7 +178,7 @@ __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev
     for (int k = k0; k < k1; ++k) {
       const BridgeOp op = load_op(m.ops + k);
       float2 z[D];
-      node_normals<D>(op, g, ps, z);
+      node_normals<D>(op, g, z);
       float2 nw[D];
       if (op.flags & BR_ROOT) {
 #pragma unroll

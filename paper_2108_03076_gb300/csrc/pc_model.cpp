@@ -128,24 +128,7 @@ pc_status build_model(const pc_model_desc &desc, ModelHost &M, std::string &err)
   int n_levels = 0;
   for (auto &nd : nodes) n_levels = std::max(n_levels, nd.level + 1);
 
-  // Register cache slots: caching level l saves one Philox block for every
-  // node of l whose first block is the previous same-level node's last one.
-  const uint32_t stride = uint32_t(normal_stride(d));
-  std::vector<int> saved(n_levels, 0);
-  for (size_t j = 1; j < nodes.size(); ++j) {
-    const uint32_t m0 = uint32_t(j) * stride;
-    if (nodes[j - 1].level == nodes[j].level && ((m0 - 1) >> 2) == (m0 >> 2)) ++saved[nodes[j].level];
-  }
-  std::vector<int> slot_of(n_levels, -1);
-  for (int s = 0; s < cache_slots(d); ++s) {
-    int best = -1;
-    for (int l = 0; l < n_levels; ++l)
-      if (slot_of[l] < 0 && saved[l] > 0 && (best < 0 || saved[l] > saved[best])) best = l;
-    if (best < 0) break;
-    slot_of[best] = s;
-  }
-
-  // Date-order schedule (see BridgeOp in pc_internal.h).
+  // Date-order schedule (see BridgeOp in pc_types.h).
   M.date_ops.assign(n + 2, 0);
   M.ops.clear();
   std::vector<int> stk;  // dates whose W is computed but not yet produced
@@ -177,22 +160,7 @@ pc_status build_model(const pc_model_desc &desc, ModelHost &M, std::string &err)
       op.j = uint32_t(j);
       op.level = uint32_t(nd.level);
       op.m = uint16_t(nd.m);
-      op.flags = 0;
-      if (nd.r < 0) op.flags |= BR_ROOT;
-      const uint32_t m0 = uint32_t(j) * stride, b0 = m0 >> 2, b1 = (m0 + d - 1) >> 2;
-      op.b0 = b0;
-      op.lane0 = uint16_t(m0 & 3u);
-      op.slot = 0;
-      if (b1 != b0) op.flags |= BR_TWO_BLOCKS;
-      const int slot = slot_of[nd.level];
-      if (slot >= 0) {
-        op.slot = uint16_t(slot);
-        if (j > 0 && nodes[j - 1].level == nd.level && ((m0 - 1) >> 2) == b0)
-          op.flags |= BR_FROM_CACHE;
-        if (j + 1 < int(nodes.size()) && nodes[j + 1].level == nd.level &&
-            ((uint32_t(j + 1) * stride) >> 2) == b1)
-          op.flags |= BR_STORE;
-      }
+      op.flags = nd.r < 0 ? BR_ROOT : 0;  // node j draws Philox block j
       M.ops.push_back(op);
     }
   }

@@ -104,45 +104,31 @@ enum { LF_K = 0, LF_T0 = 1, LF_DONE = 2, LF_RES = 3, LF_NEWLY = 4, LF_SLOTS = 5 
 // produced date in registers and a stack of already-computed W of later
 // dates.  To produce date t the kernel runs the ops of t: each computes
 // bridge node m from (W_cur, W_top) and pushes it, except the last op, whose
-// result is W_t itself; a date with no ops pops W_t from the stack.  Node j
-// (its breadth-first number) draws normals j*d .. j*d+d-1.  Nodes of one
-// bisection level are visited left to right, so consecutive nodes of a level
-// share Philox blocks; each level keeps its last block of 4 normals.
+// result is W_t itself; a date with no ops pops W_t from the stack.
+//
+// Normals: node j (its breadth-first number) owns Philox block j; the
+// normal of underlying i (d <= 4) is word i of that block (normal number
+// m = 4 j + i: counter (m >> 2, ...), word m & 3).  Date-ordered traversal
+// visits the nodes that would share a packed block far apart, so packing d
+// normals per node into consecutive words needs per-level block caches and
+// still evaluates 1.3-1.6 blocks per node; one block per node needs no
+// cache and no straddling, and measured faster for every d on GB300
+// (d = 1, 2: one Box-Muller pair per node).
 // ---------------------------------------------------------------------------
 struct BridgeOp {
   float wl, wr, sd;
-  uint32_t j;       // breadth-first node number (normal block base j*d)
-  uint16_t slot;    // register cache slot of the node's level (valid with BR_FROM_CACHE / BR_STORE)
+  uint32_t j;       // breadth-first node number = the node's Philox block
+  uint16_t pad0;
   uint16_t flags;   // BR_* below
   uint16_t m;       // date ordinal produced (diagnostics)
-  uint16_t lane0;   // (j*d) & 3: first normal's word in its Philox block
-  uint32_t b0;      // (j*d) >> 2: the node's first Philox block
+  uint16_t pad1;
+  uint32_t pad2;
   uint32_t level;   // bisection level (diagnostics)
 };
 static_assert(sizeof(BridgeOp) == 32, "BridgeOp layout: two 16-byte loads");
 
-// Normal number m of a path for bridge node j and underlying i is
-// m = j * normal_stride(d) + i; it is word m & 3 of Philox block m >> 2.
-// With d = 3 the stride is 4: a node's three normals are the first three
-// words of its own block, instead of straddling blocks that date-ordered
-// traversal visits far apart (one block per node, against about 1.3 with
-// packed normals and a one-level cache).
-constexpr int normal_stride(int d) { return d == 3 ? 4 : d; }
-
-// Philox block caches live in registers: up to cache_slots(d) bisection
-// levels (the ones whose caching saves the most Philox evaluations) get a
-// slot.  With d = 3 (padded) and d = 4 a node uses exactly one block, so
-// nothing is shared.  More slots save Philox evaluations but cost registers
-// and resident warps; these counts were the fastest measured on GB300 for
-// 365-date barriers.
-constexpr int kMaxCacheSlots = 5;
-constexpr int cache_slots(int d) { return d == 1 ? 3 : d == 2 ? 2 : 0; }
-
 enum : uint16_t {
-  BR_ROOT = 1,        // first node (last date): W = sd * z, no endpoint reads
-  BR_FROM_CACHE = 2,  // the first Philox block of this node is the level's cached block
-  BR_TWO_BLOCKS = 4,  // normals straddle two Philox blocks
-  BR_STORE = 8,       // keep the last block in the level cache for the next node
+  BR_ROOT = 1,  // first node (last date): W = sd * z, no endpoint reads
 };
 
 // Device image of a model (one allocation, offsets in bytes).
@@ -167,7 +153,7 @@ struct ModelDev {
 struct Layout {
   int32_t stack;      // operand stack words
   int32_t off_bstack; // bridge stack (bstack * d)
-  int32_t off_cache;  // level caches (n_levels * 4)
+  int32_t off_cache;  // = off_win (no shared-memory caches)
   int32_t off_win;    // date window (win * d)
   int32_t off_xwin;   // window of X = L W (win * d), sensitivity kernel only
   int32_t words;      // total words per thread in shared memory
