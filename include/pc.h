@@ -633,7 +633,7 @@ pc_status pc_debug_program(const uint32_t *bytecode, size_t n_words,
 /* Host-only: the date-ordered bridge schedule pc_model_create builds for
  * *desc: date_ops[0..n_dates+1] (ops of date t are date_ops[t] ..
  * date_ops[t+1]-1) and 6 words per op (wl, wr, sd as float bits; node
- * number; cache slot | flags << 16; date ordinal).  Writes at most cap_ops ops.
+ * number; flags << 16; date ordinal).  Writes at most cap_ops ops.
  * Errors: as pc_model_create's validation; PC_ELIMIT if cap_ops is small. */
 pc_status pc_debug_bridge(const pc_model_desc *desc, int32_t *date_ops, uint32_t *ops,
                           size_t cap_ops, size_t *n_ops);

@@ -46,8 +46,13 @@ struct BatchArgs {
 // Per-warp slot in shared memory (a contract's arguments, then its program
 // and constant pool), ahead of the per-thread regions.
 constexpr size_t kBatchArgsBytes = (sizeof(PriceArgs) + 15) & ~size_t(15);
+// A warp's slot holds its unit's arguments; programs and pools are read
+// from global memory through L1 (a slot sized for the group's largest
+// program -- up to 6.5 KB -- cost half the resident warps).
 inline size_t batch_slot_bytes(size_t n_insn, size_t n_pool_padded) {
-  return kBatchArgsBytes + n_insn * 16 + n_pool_padded * 4;
+  (void)n_insn;
+  (void)n_pool_padded;
+  return kBatchArgsBytes;
 }
 inline size_t batch_smem_bytes(size_t slot_bytes, int words, int block) {
   return slot_bytes * size_t(block / 32) + size_t(words) * size_t(block) * sizeof(float) * kPathsPerLane;

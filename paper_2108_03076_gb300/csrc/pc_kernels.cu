@@ -42,8 +42,9 @@ __global__ void __launch_bounds__(kBlock) price_kernel(const PriceArgs a) {
 // Portfolio kernel.  Warps take work units (a contract and a run of its
 // tiles) from the group's counter in the order of the unit array.  When a
 // warp's unit belongs to another contract than its previous one, the warp
-// copies that contract's arguments, program and constant pool into its own
-// slot of shared memory.  The tiles run as in price_kernel and finish into
+// copies that contract's arguments into its own slot of shared memory; the
+// program and constant pool are read from global memory through L1.  The
+// tiles run as in price_kernel and finish into
 // the contract's own reduction scratch, so each contract's sums are those of
 // a single-contract launch.
 template <int D>
@@ -53,7 +54,6 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchArgs b) {
   uint32_t *slot = smem + (b.slot_bytes / 4) * warp;
   float2 *R = reinterpret_cast<float2 *>(smem + (b.slot_bytes / 4) * (blockDim.x >> 5)) + threadIdx.x;
   const PriceArgs &a = *reinterpret_cast<const PriceArgs *>(slot);
-  const uint4 *P = reinterpret_cast<const uint4 *>(slot + kBatchArgsBytes / 4);
   float Bm[D * D], S0[D];
   Rng2 g;
   uint32_t cur = 0xffffffffu;
@@ -68,12 +68,9 @@ __global__ void __launch_bounds__(kBlock) batch_kernel(const BatchArgs b) {
       const uint32_t *src = reinterpret_cast<const uint32_t *>(b.items + U.item);
       for (int i = lane; i < int(sizeof(PriceArgs) / 4); i += 32) slot[i] = __ldg(src + i);
       __syncwarp();
-      const int n_words = a.n_insn * 4 + a.n_pool;
-      const uint32_t *code = reinterpret_cast<const uint32_t *>(a.prog);
-      for (int i = lane; i < n_words; i += 32) slot[kBatchArgsBytes / 4 + i] = __ldg(code + i);
-      __syncwarp();
       cur = U.item;
     }
+    const uint4 *P = reinterpret_cast<const uint4 *>(a.prog);
     const float *pool = reinterpret_cast<const float *>(P + a.n_insn);
     load_model_regs<D>(a.m, Bm, S0);
     g.stream = a.stream;
