@@ -611,13 +611,16 @@ pc_status pc_debug_greeks_paths(const pc_model *model, const pc_contract *contra
 pc_status pc_debug_cv_paths(const pc_model *model, const pc_contract *contract, const pc_cv_desc *desc,
                             const float *d_tables, uint64_t n_paths, uint64_t seed, float *d_xm);
 
-/* Host-only: generate and compile (NVRTC, sm_103a) the specialised pricing
- * kernel of a program for d underlyings, without loading it; *cubin_bytes
- * receives the size of the result.  Errors: as pc_verify_payoff; PC_ECUDA
- * with the compiler's log. */
+/* Host-only: generate and compile (NVRTC, sm_103a) a specialised kernel of
+ * a program for d underlyings, without loading it; *cubin_bytes receives
+ * the size of the result.  kind: 0 the pricing kernel, 1 its per-path
+ * variant, 16 + m the control-variate kernel of mode m (bits: 1 per-path
+ * outputs, 2 second-order term, 4 pilot sums; d <= 3).  Errors: as
+ * pc_verify_payoff; PC_EINVAL for another kind; PC_ECUDA with the
+ * compiler's log. */
 pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_words, const double *consts,
                                size_t n_consts, const int32_t *template_params, size_t n_params,
-                               int32_t p1, int32_t p2, int32_t d, size_t *cubin_bytes);
+                               int32_t p1, int32_t p2, int32_t d, int32_t kind, size_t *cubin_bytes);
 
 /* Host-only: the executable form pc_load_payoff would run for this program:
  * 4 words per instruction (opcode | A << 8, then three operand words), then

@@ -120,7 +120,7 @@ _SIGS = {
     "pc_set_window_mode": [VP, C.c_int32],
     "pc_set_jit": [VP, C.c_int32],
     "pc_jit_compile": [VP, VP],
-    "pc_debug_jit_compile": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, I32, C.POINTER(SZ)],
+    "pc_debug_jit_compile": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, I32, I32, C.POINTER(SZ)],
     "pc_price_info": [VP, VP, U64, C.POINTER(LaunchInfo)],
     "pc_batch_create": [SZ, C.POINTER(VP), C.POINTER(VP), C.POINTER(U64), U64,
                         C.POINTER(BatchConfig), C.POINTER(VP)],
@@ -319,12 +319,13 @@ def pc_jit_compile(model: int, contract: int) -> None:
     _check(lib().pc_jit_compile(VP(model), VP(contract)))
 
 
-def pc_debug_jit_compile(words, consts, tparams=(), d: int = 1, p1: int = 0, p2: int = 1) -> int:
-    """Host-only: compile the specialised kernel of a program; cubin bytes."""
+def pc_debug_jit_compile(words, consts, tparams=(), d: int = 1, p1: int = 0, p2: int = 1, kind: int = 0) -> int:
+    """Host-only: compile a specialised kernel of a program (kind 0 pricing,
+    1 per-path pricing, 16 + mode control variate); cubin bytes."""
     w, k, t = _arr(words, np.uint32), _arr(consts, np.float64), _arr(tparams, np.int32)
     n = SZ(0)
     _check(lib().pc_debug_jit_compile(_ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,
-                                      _ptr(t, C.c_int32), t.size, p1, p2, d, C.byref(n)))
+                                      _ptr(t, C.c_int32), t.size, p1, p2, d, int(kind), C.byref(n)))
     return n.value
 
 

@@ -52,7 +52,8 @@ def up_to_date() -> bool:
 
 # Device sources the run-time compiler (NVRTC) needs, embedded in the
 # library as string literals (pc_jit.cpp includes the generated header).
-JIT_HEADERS = ["pc_types.h", "pc_device.cuh", "pc_price.cuh", "pc_eval_state.inc", "pc_ops.inc"]
+JIT_HEADERS = ["pc_types.h", "pc_device.cuh", "pc_price.cuh", "pc_eval_state.inc", "pc_ops.inc", "pc_cv_types.h",
+               "pc_cv.cuh"]
 
 
 def _op_cases():

@@ -289,7 +289,7 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
   if (c->jit && !L.hbm_window) {
     // the contract's run-time specialised kernel (same arguments and shape)
     cudaKernel_t jk = nullptr;
-    s = jit_kernel(k, m->H.d, d_payoffs != nullptr, jk);
+    s = jit_kernel(k, m->H.d, d_payoffs != nullptr ? kJitPriceWrite : kJitPrice, jk);
     if (s != PC_OK) return s;
     const void *kern = reinterpret_cast<const void *>(jk);
     // the specialised evaluator keeps its operand stack in registers: drop
@@ -753,7 +753,7 @@ pc_status pc_jit_compile(const pc_model *m, const pc_contract *k) {
   if (m->ctx != k->ctx) return fail(PC_EINVAL, "model and contract belong to different contexts");
   CU(cudaSetDevice(m->ctx->device), "cudaSetDevice");
   cudaKernel_t jk = nullptr;
-  return jit_kernel(k, m->H.d, false, jk);
+  return jit_kernel(k, m->H.d, kJitPrice, jk);
 }
 
 pc_status pc_price_info(const pc_model *m, const pc_contract *k, uint64_t n_paths, pc_launch_info *info) {

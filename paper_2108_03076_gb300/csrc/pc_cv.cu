@@ -1,275 +1,24 @@
-// pc_cv.cu -- the delta-hedge control variate on the pricing paths, and the
-// kernels that turn the network into its hedge-ratio tables.
-//
-// For the worst-of autocallable template each path's payoff X comes from the
-// interpreter exactly as in price_kernel; the kernel then walks the dates
-// kept in the window and accumulates the discounted hedge gains
-//   M = sum_{k<n} alive_k sum_i Delta_i(k) (D_{k+1} S_i(t_{k+1}) - D_k S_i(t_k))
-// with Delta from a table over ln S (multilinear interpolation) per date and
-// knock-in state.  Every factor of a term is known at t_k, so E[M] = 0.  An
-// optional second-order term M2 (gamma from the table's slopes, the
-// quadratic moments of the discounted returns in closed form) also has mean
-// zero, and Y = X - beta M - beta2 M2 estimates the same price for any fixed
-// betas.  The tile sums carry X, X^2, Y, Y^2, or in the pilot mode the
-// eight first and second moments of X, M, M2 that the variance-minimising
-// betas need.
-// A hedge period whose end date the warp never generated (every lane's
-// program stopped before it) is skipped: that decision depends only on
-// information at t_k of this and of independent paths, so the terms kept are
-// still martingale increments.
+// pc_cv.cu -- the delta-hedge control-variate pricing kernel (cv_tiles of
+// pc_cv.cuh with the interpreter), and the kernels that turn the network
+// into its hedge-ratio tables.
 #include <cstdint>
 
 #include "pc_device.cuh"
 #include "pc_internal.h"
 #include "pc_eval.cuh"
 #include "pc_cv.h"
+#include "pc_cv.cuh"
 
 namespace pc {
 namespace {
 
-// Multilinear interpolation of the d hedge ratios at ln S (given as
-// l2 = log2 S: the axis coordinate is u = l2 ln2 / h - lo / h), and with
-// SLOPES the interpolant's derivatives s[i][j] = d Delta_i / d u_j on the
-// cell.  The 2^d corner values are reduced one axis at a time, last axis
-// first: a pair (lo, hi) along the axis becomes lo + f (hi - lo), its
-// difference hi - lo is the slope along that axis there, and slopes along
-// axes already reduced are interpolated like the values.  Same interpolant
-// as the sum over corners of the products of (f or 1 - f), in about a third
-// of the arithmetic.
-template <int D, bool SLOPES>
-__device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, const float (&l2)[D],
-                                            float (&delta)[D], float (&s)[D][D]) {
-  const float4 *tab = reinterpret_cast<const float4 *>(c.tables) + (size_t(k - 1) * 2 + ki) * size_t(c.nodes);
-  constexpr int NC = 1 << D;
-  int a[D];
-  float f[D];
-  const int G = c.grid;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    float u = fmaf(l2[i], c.ua[k - 1][i], -c.ub[k - 1][i]);
-    u = fminf(fmaxf(u, 0.f), float(G - 1));
-    int ai = int(floorf(u));
-    ai = ai < G - 2 ? ai : G - 2;
-    a[i] = ai;
-    f[i] = u - float(ai);
-  }
-  int base = 0;
-#pragma unroll
-  for (int ax = 0; ax < D; ++ax) base = base * G + a[ax];
-  // corner c: bit (D - 1 - ax) selects a[ax] + 1 on axis ax
-  float v[NC][D];
-#pragma unroll
-  for (int cn = 0; cn < NC; ++cn) {
-    int off = 0;
-#pragma unroll
-    for (int ax = 0; ax < D; ++ax) off = off * G + ((cn >> (D - 1 - ax)) & 1);
-    const float4 v4 = __ldg(tab + base + off);  // one 16-byte load per corner
-    const float w3[3] = {v4.x, v4.y, v4.z};
-#pragma unroll
-    for (int i = 0; i < D; ++i) v[cn][i] = w3[i];
-  }
-  float sj[D][NC / 2][D];
-#pragma unroll
-  for (int ax = D - 1; ax >= 0; --ax) {
-#pragma unroll
-    for (int cn = 0; cn < (1 << ax); ++cn) {
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        const float lo = v[2 * cn][i], dd = v[2 * cn + 1][i] - lo;
-        if (SLOPES) {
-#pragma unroll
-          for (int j = ax + 1; j < D; ++j)
-            sj[j][cn][i] = fmaf(f[ax], sj[j][2 * cn + 1][i] - sj[j][2 * cn][i], sj[j][2 * cn][i]);
-          sj[ax][cn][i] = dd;
-        }
-        v[cn][i] = fmaf(f[ax], dd, lo);
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-    delta[i] = v[0][i];
-#pragma unroll
-    for (int j = 0; j < D; ++j) s[i][j] = SLOPES ? sj[j][0][i] : 0.f;
-  }
-}
-
-// Hedge gains of the lane's two paths (q = 0, 1): first order M and second
-// order M2.  S of path q at ordinal o is s(q, o, i) (o = 0: spot).  Both
-// paths are worked in step (independent table reads in flight together);
-// a dead path's terms are computed and discarded.
-template <int D, bool GAMMA, typename SFn>
-__device__ void hedge_gain2(const CvArgs &c, const ModelDev &m, int frontier, SFn s, float (&M)[2],
-                            float (&M2)[2]) {
-  bool alive[2] = {true, true};
-  int ki[2] = {0, 0};
-#pragma unroll
-  for (int q = 0; q < 2; ++q) M[q] = M2[q] = 0.f;
-  for (int k = 0; k < c.n; ++k) {
-    if (k + 1 > frontier) break;
-    if (k >= 1) {
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        float worst = s(q, k, 0) * c.inv_ref[0];
-#pragma unroll
-        for (int i = 1; i < D; ++i) worst = fminf(worst, s(q, k, i) * c.inv_ref[i]);
-        ki[q] |= worst <= c.ki_level ? 1 : 0;
-        alive[q] = alive[q] && !(worst >= c.call_level);
-      }
-    }
-    if (!alive[0] && !alive[1]) break;
-    const float d0 = __ldg(m.disc + k + m.n_hist), d1 = __ldg(m.disc + k + 1 + m.n_hist);
-    float delta[2][D], sl[2][D][D];
-    if (k == 0) {
-#pragma unroll
-      for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int i = 0; i < D; ++i) delta[q][i] = c.delta0[i];
-    } else {
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        float l2[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) l2[i] = __log2f(s(q, k, i));
-        table_delta<D, GAMMA>(c, k, ki[q], l2, delta[q], sl[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      float X[D], Sk[D], inv[D];
-      float dm = 0.f;
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        Sk[i] = s(q, k, i);
-        X[i] = d1 * s(q, k + 1, i) - d0 * Sk[i];
-        dm = fmaf(delta[q][i], X[i], dm);
-        inv[i] = __frcp_rn(Sk[i]);
-      }
-      M[q] += alive[q] ? dm : 0.f;
-      if (GAMMA && k >= 1) {
-        // Gamma = sym(t), t_ij = s_ij / (h_j S_j); the quadratic forms of
-        // a symmetric weight need only t itself
-        float qf = 0.f, e = 0.f;
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-          float rq = 0.f, re = 0.f;
-#pragma unroll
-          for (int j = 0; j < D; ++j) {
-            const float t = sl[q][i][j] * c.inv_h[k - 1][j] * inv[j];
-            rq = fmaf(t, X[j], rq);
-            re = fmaf(t, Sk[j] * c.cq[k][i * kCvMaxD + j], re);
-          }
-          qf = fmaf(X[i], rq, qf);
-          e = fmaf(Sk[i], re, e);
-        }
-        M2[q] += alive[q] ? 0.5f * (qf - d0 * d0 * e) : 0.f;
-      }
-    }
-  }
-}
-
-// MODE bits: kCvWrite (per-path X, M, M2 out), kCvGamma (second-order
-// term), kCvPilot (moment sums for the betas instead of X, X^2, Y, Y^2).
-constexpr int kCvWrite = 1, kCvGamma = 2, kCvPilot = 4;
 
 template <int D, int MODE>
 __global__ void __launch_bounds__(kBlock) cv_kernel(const PriceArgs a, const CvArgs c) {
-  constexpr bool WRITE = (MODE & kCvWrite) != 0, GAMMA = (MODE & kCvGamma) != 0,
-                 PILOT = (MODE & kCvPilot) != 0;
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ int last_block;
-  uint4 *P = reinterpret_cast<uint4 *>(smem);
-  const int prog_words = a.n_insn * 4 + a.n_pool;
-  const uint32_t *src = reinterpret_cast<const uint32_t *>(a.prog);
-  for (int i = threadIdx.x; i < prog_words; i += blockDim.x) smem[i] = src[i];
-  __syncthreads();
-  const float *pool = reinterpret_cast<const float *>(smem + a.n_insn * 4);
-  float2 *R = reinterpret_cast<float2 *>(smem + prog_words) + threadIdx.x;
-  float Bm[D * D], S0[D];
-  load_model_regs<D>(a.m, Bm, S0);
-  const int lane = threadIdx.x & 31;
-  unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
-  const Layout &lay = a.lay;
-  Rng2 g;
-  g.stream = a.stream;
-  g.k0 = a.key0;
-  g.k1 = a.key1;
-  for (;;) {
-    unsigned long long tile = 0;
-    if (lane == 0) tile = atomicAdd(ctr, 1ull);
-    tile = __shfl_sync(kFull, tile, 0);
-    if (tile >= a.n_tiles) break;
-    const uint64_t i0 = tile * kTilePaths + lane, i1 = i0 + 32;
-    const bool live0 = i0 < a.n_paths, live1 = i1 < a.n_paths;
-    const uint64_t p0 = a.path_offset + i0, p1 = a.path_offset + i1;
-    g.plo[0] = uint32_t(p0);
-    g.phi[0] = uint32_t(p0 >> 32);
-    g.plo[1] = uint32_t(p1);
-    g.phi[1] = uint32_t(p1 >> 32);
-    int frontier = 0;
-    const float2 x = eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0, &frontier);
-    float Mv[2], M2v[2];
-    auto s = [&](int q, int o, int i) -> float {
-      if (o == 0) return S0[i];
-      const float2 v = SL(lay.off_win + (o & (lay.win - 1)) * D + i);
-      return q ? v.y : v.x;
-    };
-    hedge_gain2<D, GAMMA>(c, a.m, frontier, s, Mv, M2v);
-    const float xs[2] = {x.x, x.y};
-    const bool live[2] = {live0, live1};
-    if (WRITE) {
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (!live[q]) continue;
-        const uint64_t i = q ? i1 : i0;
-        a.out_paths[3 * i] = xs[q];
-        a.out_paths[3 * i + 1] = Mv[q];
-        a.out_paths[3 * i + 2] = M2v[q];
-      }
-    }
-    if (PILOT) {
-      Moments<8> mo;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (!live[q]) continue;
-        mo.add(0, xs[q]);
-        mo.add(1, Mv[q]);
-        mo.add(2, M2v[q]);
-        mo.add_prod(3, xs[q], Mv[q]);
-        mo.add_prod(4, xs[q], M2v[q]);
-        mo.add_prod(5, Mv[q], Mv[q]);
-        mo.add_prod(6, M2v[q], M2v[q]);
-        mo.add_prod(7, Mv[q], M2v[q]);
-      }
-      double tp[8];
-      mo.warp_total(tp);
-      finish_tile<8>(a, tile, tp, lane);
-    } else {
-      Moments<4> mo;
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (!live[q]) continue;
-        const float y = xs[q] - c.beta * Mv[q] - c.beta2 * M2v[q];
-        mo.add(0, xs[q]);
-        mo.add_prod(1, xs[q], xs[q]);
-        mo.add(2, y);
-        mo.add_prod(3, y, y);
-      }
-      double tp[4];
-      mo.warp_total(tp);
-      finish_tile<4>(a, tile, tp, lane);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last_block = atomicAdd(ctr + 1, 1ull) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last_block && threadIdx.x == 0) {
-    ctr[0] = 0;
-    ctr[1] = 0;
-  }
+  cv_tiles<D, MODE>(a, c, [&](const uint4 *P, const float *pool, float2 *R, const Rng2 &g, bool live0,
+                              bool live1, const float (&Bm)[D * D], const float (&S0)[D], int *frontier) {
+    return eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0, frontier);
+  });
 }
 
 // Network inputs of every table node (row ((k-1) * 2 + ki) * G^d + node),
@@ -348,15 +97,15 @@ cudaError_t launch_cv_d(int mode, const PriceArgs &a, const CvArgs &c, int grid,
 #undef CVL
 }
 
-int cv_mode(const PriceArgs &a, const CvArgs &c) {
-  if (a.out_paths) return kCvWrite | kCvGamma;
+}  // namespace
+
+int cv_mode(bool write, const CvArgs &c) {
+  if (write) return kCvWrite | kCvGamma;
   return (c.use_gamma ? kCvGamma : 0) | (c.pilot ? kCvPilot : 0);
 }
 
-}  // namespace
-
 cudaError_t launch_cv(const PriceArgs &a, const CvArgs &c, int grid, int block, size_t smem, cudaStream_t s) {
-  const int mode = cv_mode(a, c);
+  const int mode = cv_mode(a.out_paths != nullptr, c);
   switch (a.m.d) {
     case 1: return launch_cv_d<1>(mode, a, c, grid, block, smem, s);
     case 2: return launch_cv_d<2>(mode, a, c, grid, block, smem, s);
@@ -398,8 +147,7 @@ int cv_occupancy(uint64_t v, int block, size_t smem) {
 }  // namespace
 
 int cv_blocks_per_sm(int d, int block, size_t smem, const CvArgs &c) {
-  PriceArgs dummy{};
-  const int mode = cv_mode(dummy, c);
+  const int mode = cv_mode(false, c);
   return occupancy_memo((uint64_t(2) << 32) | (uint64_t(mode) << 8) | uint64_t(d), block, smem, cv_occupancy);
 }
 

@@ -113,10 +113,39 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
   a.control = ctx->d_control;
   a.out = d_out;
   a.out_paths = d_xm;
+  CU(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const CvArgs ca = device_args(c, tables, m->H, pilot);
+  if (ctx->jit) {
+    // the contract's run-time specialised control-variate kernel: the
+    // evaluator keeps its operand stack in registers, so the stack words
+    // leave the per-thread shared region
+    cudaKernel_t jk = nullptr;
+    s = jit_kernel(k, m->H.d, kJitCv + cv_mode(d_xm != nullptr, ca), jk);
+    if (s != PC_OK) return s;
+    const void *kern = reinterpret_cast<const void *>(jk);
+    Layout &jl = a.lay;
+    const int shift = jl.off_bstack;
+    jl.stack = 0;
+    jl.off_bstack -= shift;
+    jl.off_cache -= shift;
+    jl.off_win -= shift;
+    jl.words -= shift;
+    const size_t jsm = price_smem_bytes(k->prog.code.size(), pool, jl.words, kBlock);
+    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(jsm)), "jit attribute");
+    int nb = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBlock, jsm), "jit occupancy");
+    if (nb < 1) return fail(PC_ELIMIT, "specialised control-variate kernel cannot be resident");
+    const uint64_t jneed = (a.n_tiles + kBlock / 32 - 1) / (kBlock / 32);
+    const int jgrid = int(std::min<uint64_t>(uint64_t(ctx->sm_count) * nb, jneed));
+    CvArgs cv = ca;
+    void *args[] = {&a, &cv};
+    CU(cudaLaunchKernel(kern, dim3(jgrid), dim3(kBlock), args, jsm, ctx->stream),
+       "specialised control-variate kernel");
+    return PC_OK;
+  }
   const uint64_t need = (a.n_tiles + block / 32 - 1) / (block / 32);
   const int grid = int(std::min<uint64_t>(uint64_t(ctx->sm_count) * best / (block / 32), need));
-  CU(cudaSetDevice(ctx->device), "cudaSetDevice");
-  CU(launch_cv(a, device_args(c, tables, m->H, pilot), grid, block, smem, ctx->stream), "control-variate kernel");
+  CU(launch_cv(a, ca, grid, block, smem, ctx->stream), "control-variate kernel");
   return PC_OK;
 }
 

@@ -17,10 +17,14 @@
 
 // A run-time specialised pricing kernel: the program it was compiled from
 // (code and pool words), the underlying count and the per-path variant.
+// Kinds of run-time specialised kernels: pricing, pricing with per-path
+// payoffs, and the control-variate kernel (kJitCv + its kCv* mode bits).
+constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitCv = 16;
+
 struct JitEntry {
   std::vector<uint32_t> program;
   int d = 0;
-  bool write = false;
+  int kind = kJitPrice;
   cudaLibrary_t lib = nullptr;
   cudaKernel_t kernel = nullptr;
 };
@@ -107,9 +111,9 @@ pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uin
 pc_status ensure_partials(pc_ctx *c, size_t doubles);
 
 // The run-time specialised kernel of the contract's program for d
-// underlyings (compiled on first use, cached on the context by program
-// content); `write`: the per-path variant.
-pc_status jit_kernel(const pc_contract *k, int d, bool write, cudaKernel_t &out);
+// underlyings and a kernel kind (kJit*; compiled on first use, cached on
+// the context by program content).
+pc_status jit_kernel(const pc_contract *k, int d, int kind, cudaKernel_t &out);
 void jit_release(pc_ctx *c);
 
 // Turn a raised device status word into PC_EDEVICE (and clear it).

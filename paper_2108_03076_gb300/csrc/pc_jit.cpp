@@ -21,6 +21,7 @@
 
 #include "pc_handles.h"
 #include "pc_internal.h"
+#include "pc_cv_types.h"
 #include "pc_jit_headers.inc"
 
 using namespace pc;
@@ -134,15 +135,16 @@ bool stack_depths(const Program &p, std::vector<int> &sp_at) {
   return ok;
 }
 
-// Straight-line evaluator for the program and d underlyings, and the
-// pricing kernel around it (per-path payoffs written out when `write`).
+// Straight-line evaluator for the program and d underlyings, and the kernel
+// of `kind` around it: pc_jit_price (price_tiles; per-path payoffs written
+// out for kJitPriceWrite) or pc_jit_cv (cv_tiles with mode kind - kJitCv).
 // With two or more reading instructions and known stack depths, the date
 // generator has one copy: a reading instruction that needs dates jumps to
 // it and it jumps back to the top of that instruction, restoring the
 // static stack pointer there (so the operand stack stays in registers).
 // Otherwise the generator is inlined at each reading instruction (out of
 // line beyond kInlineDateSites of them).
-std::string generate(const Program &p, int d, bool write) {
+std::string generate(const Program &p, int d, int kind) {
   std::ostringstream o;
   const size_t n = p.code.size();
   std::vector<int> sp_at;
@@ -150,7 +152,9 @@ std::string generate(const Program &p, int d, bool write) {
   // without re-entry points, many reading instructions call one
   // out-of-line copy instead of inlining the generator at each
   if (!shared && date_sites(p) > kInlineDateSites) o << "#define PC_JIT_OUTLINE_DATES 1\n";
-  o << "#include \"pc_price.cuh\"\n"
+  o << "#include \"pc_price.cuh\"\n";
+  if (kind >= kJitCv) o << "#include \"pc_cv.cuh\"\n";
+  o
     << "namespace pc {\n"
     << "namespace {\n"
     << "constexpr int D = " << d << ";\n"
@@ -199,10 +203,20 @@ std::string generate(const Program &p, int d, bool write) {
     << "}\n"
     << "}  // namespace\n"
     << "}  // namespace pc\n";
+  if (kind >= kJitCv) {
+    o << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ") pc_jit_cv(const pc::PriceArgs a,\n"
+      << "    const pc::CvArgs c) {\n"
+      << "  pc::cv_tiles<pc::D, " << (kind - kJitCv) << ">(a, c, [&](const uint4 *P, const float *pool, float2 *R,\n"
+      << "      const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
+      << "      const float (&S0)[pc::D], int *frontier) {\n"
+      << "    return pc::jit_eval(P, pool, R, a, g, live0, live1, Bm, S0, frontier); });\n"
+      << "}\n";
+    return o.str();
+  }
   // at least 7 resident 128-thread blocks (<= 72 registers): the fastest
   // measured cap (autocall unchanged, daily barrier -7 %, 5 blocks slower)
   o << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ", 7) pc_jit_price(const pc::PriceArgs a) {\n"
-    << "  pc::price_tiles<pc::D, " << (write ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
+    << "  pc::price_tiles<pc::D, " << (kind == kJitPriceWrite ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
     << "      float2 *R, const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
     << "      const float (&S0)[pc::D]) { return pc::jit_eval(P, pool, R, a, g, live0, live1, Bm, S0); });\n"
     << "}\n";
@@ -222,8 +236,8 @@ pc_status nvrtc_fail(nvrtcResult r, nvrtcProgram prog, const char *what) {
 
 // NVRTC: the generated source and the embedded device headers to a cubin
 // for `arch` (e.g. "sm_103a").
-pc_status to_cubin(const Program &p, int d, bool write, const std::string &arch, std::vector<char> &cubin) {
-  const std::string src = generate(p, d, write);
+pc_status to_cubin(const Program &p, int d, int kind, const std::string &arch, std::vector<char> &cubin) {
+  const std::string src = generate(p, d, kind);
   nvrtcProgram prog = nullptr;
   nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "pc_jit.cu", kJitHeaderCount, kJitHeaderSrcs,
                                      kJitHeaderNames);
@@ -245,15 +259,15 @@ pc_status to_cubin(const Program &p, int d, bool write, const std::string &arch,
   return PC_OK;
 }
 
-pc_status compile(const Program &p, int d, bool write, int device, cudaLibrary_t &lib, cudaKernel_t &kern) {
+pc_status compile(const Program &p, int d, int kind, int device, cudaLibrary_t &lib, cudaKernel_t &kern) {
   cudaDeviceProp prop{};
   CU(cudaGetDeviceProperties(&prop, device), "device properties");
   std::vector<char> cubin;
-  pc_status s = to_cubin(p, d, write, "sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a",
+  pc_status s = to_cubin(p, d, kind, "sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a",
                          cubin);
   if (s != PC_OK) return s;
   CU(cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0), "module load");
-  cudaError_t e = cudaLibraryGetKernel(&kern, lib, "pc_jit_price");
+  cudaError_t e = cudaLibraryGetKernel(&kern, lib, kind >= kJitCv ? "pc_jit_cv" : "pc_jit_price");
   if (e != cudaSuccess) {
     cudaLibraryUnload(lib);
     lib = nullptr;
@@ -267,7 +281,7 @@ pc_status compile(const Program &p, int d, bool write, int device, cudaLibrary_t
 
 namespace pc {
 
-pc_status jit_kernel(const pc_contract *k, int d, bool write, cudaKernel_t &out) {
+pc_status jit_kernel(const pc_contract *k, int d, int kind, cudaKernel_t &out) {
   // the program's words: code, then pool bits
   std::vector<uint32_t> words;
   words.reserve(k->prog.code.size() * 4 + k->prog.pool.size());
@@ -290,7 +304,7 @@ pc_status jit_kernel(const pc_contract *k, int d, bool write, cudaKernel_t &out)
   auto range = c->jit_cache.equal_range(h);
   for (auto it = range.first; it != range.second; ++it) {
     const JitEntry &E = it->second;
-    if (E.d == d && E.write == write && E.program == words) {
+    if (E.d == d && E.kind == kind && E.program == words) {
       out = E.kernel;
       return PC_OK;
     }
@@ -298,8 +312,8 @@ pc_status jit_kernel(const pc_contract *k, int d, bool write, cudaKernel_t &out)
   JitEntry E;
   E.program = words;
   E.d = d;
-  E.write = write;
-  pc_status s = compile(k->prog, d, write, c->device, E.lib, E.kernel);
+  E.kind = kind;
+  pc_status s = compile(k->prog, d, kind, c->device, E.lib, E.kernel);
   if (s != PC_OK) return s;
   out = E.kernel;
   c->jit_cache.emplace(h, std::move(E));
@@ -317,15 +331,20 @@ void jit_release(pc_ctx *c) {
 
 extern "C" pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_words, const double *consts,
                                           size_t n_consts, const int32_t *tparams, size_t n_params,
-                                          int32_t p1, int32_t p2, int32_t d, size_t *cubin_bytes) {
+                                          int32_t p1, int32_t p2, int32_t d, int32_t kind,
+                                          size_t *cubin_bytes) {
   if (!cubin_bytes) return fail(PC_EINVAL, "null output");
   if (d < 1 || d > PC_MAX_UNDERLYINGS) return fail(PC_EINVAL, "d must be 1..4");
+  const bool cv_kind = kind >= kJitCv && kind < kJitCv + 8 && kind != kJitCv + kCvWrite &&
+                       kind != kJitCv + (kCvWrite | kCvPilot) && kind != kJitCv + (kCvWrite | kCvPilot | kCvGamma);
+  if (kind != kJitPrice && kind != kJitPriceWrite && !cv_kind) return fail(PC_EINVAL, "unknown kernel kind");
+  if (cv_kind && d > kCvMaxD) return fail(PC_EINVAL, "control-variate kernels take d <= 3");
   Program p;
   std::string err;
   pc_status s = compile_program(bytecode, n_words, consts, n_consts, tparams, n_params, p1, p2, true, p, err);
   if (s != PC_OK) return fail(s, err);
   std::vector<char> cubin;
-  s = to_cubin(p, d, false, "sm_103a", cubin);
+  s = to_cubin(p, d, kind, "sm_103a", cubin);
   if (s != PC_OK) return s;
   *cubin_bytes = cubin.size();
   return PC_OK;

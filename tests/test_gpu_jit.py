@@ -84,3 +84,36 @@ def test_hbm_window_launch_keeps_the_interpreter(eng):
     finally:
         pc.pc_set_jit(eng.ctx, False)
     assert p1 == pc.pc_price(m, k, 1 << 16, 9)
+
+
+@pytest.mark.parametrize("gamma", [0, 1])
+def test_specialised_control_variate_equals_interpreter(eng, gamma):
+    """The run-time specialised control-variate kernel: per-path X, M, M2 and
+    the price / pilot sums bit for bit those of the interpreting kernel."""
+    w = W.worst_of_autocall()
+    m = eng.model(w.market)
+    k = eng.contract(w.il_text, w.tparams)
+    desc = pc.pc_cv_grid(m, 8, 4.0)
+    rng = np.random.default_rng(5)
+    tab = torch.tensor((0.3 + 0.4 * rng.standard_normal(pc.pc_cv_table_size(desc))).astype(np.float32),
+                       device="cuda")
+    for i in range(3):
+        desc.delta0[i] = [0.35, 0.25, 0.15][i]
+    desc.use_gamma = gamma
+    desc.beta, desc.beta2 = 0.9, 0.4
+    n, seed = 4096 + 77, 0x5EED0303
+    out = {}
+    for jit in (False, True):
+        pc.pc_set_jit(eng.ctx, jit)
+        try:
+            xm = torch.empty(3 * n, dtype=torch.float32, device="cuda")
+            pc.pc_debug_cv_paths(m, k, desc, tab.data_ptr(), n, seed, xm.data_ptr())
+            torch.cuda.synchronize()
+            res = pc.pc_price_cv(m, k, desc, tab.data_ptr(), 1 << 16, seed)
+            betas = pc.pc_cv_beta(m, k, desc, tab.data_ptr(), 1 << 15, seed + 1)
+            out[jit] = (xm.cpu().numpy(), res, betas)
+        finally:
+            pc.pc_set_jit(eng.ctx, False)
+    np.testing.assert_array_equal(out[True][0].view(np.uint32), out[False][0].view(np.uint32))
+    assert out[True][1] == out[False][1]
+    assert out[True][2] == out[False][2]

@@ -19,3 +19,22 @@ def test_compile_errors_are_reported():
     with pytest.raises(pc.PcError) as e:
         pc.pc_debug_jit_compile(w, k, [], 5)
     assert e.value.name == "PC_EINVAL"
+
+
+@pytest.mark.parametrize("kind", [1, 16, 16 + 2, 16 + 4, 16 + 6, 16 + 3])
+def test_specialised_variants_compile(kind):
+    """The per-path pricing variant and the control-variate kernel in each
+    mode (second-order term, pilot sums, per-path outputs) for the worst-of
+    autocallable."""
+    import workloads as W
+    w_ = W.worst_of_autocall()
+    w, k = pc.pc_assemble(w_.il_text)
+    assert pc.pc_debug_jit_compile(w, k, w_.tparams, 3, kind=kind) > 1000
+
+
+@pytest.mark.parametrize("kind,d", [(2, 1), (16 + 1, 3), (24, 3), (16, 4)])
+def test_unknown_kinds_are_refused(kind, d):
+    w, k = pc.pc_assemble("(model 0 1)")
+    with pytest.raises(pc.PcError) as e:
+        pc.pc_debug_jit_compile(w, k, [], d, kind=kind)
+    assert e.value.name == "PC_EINVAL"
