@@ -51,6 +51,36 @@ pc_status wait_stream(pc_ctx *c) {
   }
 }
 
+cudaError_t ctx_alloc(pc_ctx *c, void **p, size_t bytes, bool &pooled) {
+  pooled = c->pool != nullptr;
+  if (pooled) return cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream);
+  return cudaMalloc(p, bytes);
+}
+
+void ctx_free(pc_ctx *c, void *p, bool pooled) {
+  if (!p) return;
+  if (pooled) {
+    cudaFreeAsync(p, c->stream);
+  } else {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(p);
+  }
+}
+
+cudaError_t jit_occupancy(pc_ctx *c, const void *kern, int block, size_t smem, int &blocks) {
+  std::lock_guard<std::mutex> g(c->jit_mu);
+  const auto key = std::make_pair(kern, smem * 1024 + size_t(block));
+  auto it = c->jit_occ.find(key);
+  if (it != c->jit_occ.end()) {
+    blocks = it->second;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, block, smem);
+  if (e == cudaSuccess) c->jit_occ.emplace(key, blocks);
+  return e;
+}
+
 template <typename T>
 pc_status upload(const std::vector<T> &v, char *base, size_t &off, const T *&dst, cudaStream_t s) {
   off = (off + 255) & ~size_t(255);
@@ -302,9 +332,8 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
     lay.off_win -= shift;
     lay.words -= shift;
     const size_t smem = price_smem_bytes(k->prog.code.size(), pool_padded(k->prog), lay.words, L.block);
-    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)), "jit attribute");
     int nb = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, L.block, smem), "jit occupancy");
+    CU(jit_occupancy(c, kern, L.block, smem, nb), "jit occupancy");
     if (nb < 1) return fail(PC_ELIMIT, "specialised kernel cannot be resident");
     const uint64_t wpb = uint64_t(L.block) / 32;
     const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * nb, (L.args.n_tiles + wpb - 1) / wpb));
@@ -479,6 +508,21 @@ pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
     e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     c->own_stream = true;
   }
+  if (e == cudaSuccess) {
+    // a memory pool of the context's own, keeping freed memory (contracts
+    // are loaded and dropped often): stream-ordered, no device-wide sync
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+      uint64_t keep = ~uint64_t(0);
+      cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      c->pool = nullptr;
+      cudaGetLastError();
+    }
+  }
   if (e == cudaSuccess) e = cudaMalloc(&c->d_res, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_res, 0, 8 * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_gout, PC_MAX_UNDERLYINGS * 8 * sizeof(double));
@@ -489,6 +533,7 @@ pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
     if (c->d_control) cudaFree(c->d_control);
     if (c->d_gout) cudaFree(c->d_gout);
     if (c->d_res) cudaFree(c->d_res);
+    if (c->pool) cudaMemPoolDestroy(c->pool);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return cuda_fail(e, "context setup");
@@ -508,6 +553,7 @@ pc_status pc_destroy(pc_ctx *c) {
   jit_release(c);
   if (c->d_gout) cudaFree(c->d_gout);
   if (c->d_res) cudaFree(c->d_res);
+  if (c->pool) cudaMemPoolDestroy(c->pool);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return PC_OK;
@@ -632,19 +678,19 @@ pc_status pc_load_payoff(pc_ctx *c, const uint32_t *bytecode, size_t n_words, co
     }
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     // program then constant pool (padded to whole 16-byte words), one buffer
-    const size_t code_bytes = k->prog.code.size() * sizeof(XInsn);
-    const size_t pool_bytes = pool_padded(k->prog) * sizeof(float);
-    std::vector<float> pool(pool_padded(k->prog), 0.f);
-    std::copy(k->prog.pool.begin(), k->prog.pool.end(), pool.begin());
-    cudaError_t e = cudaMalloc(&k->d_code, code_bytes + pool_bytes + 16);
+    const size_t code_words = k->prog.code.size() * 4;
+    k->image.assign(code_words + pool_padded(k->prog), 0u);
+    std::memcpy(k->image.data(), k->prog.code.data(), code_words * 4);
+    std::memcpy(k->image.data() + code_words, k->prog.pool.data(), k->prog.pool.size() * 4);
+    void *dp = nullptr;
+    cudaError_t e = ctx_alloc(c, &dp, k->image.size() * 4 + 16, k->pooled);
+    k->d_code = static_cast<XInsn *>(dp);
+    // ordered on the context's stream before any launch that reads it; the
+    // source stays alive with the contract
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(k->d_code, k->prog.code.data(), code_bytes, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess && pool_bytes)
-      e = cudaMemcpyAsync(reinterpret_cast<char *>(k->d_code) + code_bytes, pool.data(), pool_bytes,
-                          cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      e = cudaMemcpyAsync(k->d_code, k->image.data(), k->image.size() * 4, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) {
-      if (k->d_code) cudaFree(k->d_code);
+      ctx_free(c, k->d_code, k->pooled);
       delete k;
       return cuda_fail(e, "program upload");
     }
@@ -662,8 +708,7 @@ pc_status pc_load_payoff(pc_ctx *c, const uint32_t *bytecode, size_t n_words, co
 pc_status pc_contract_destroy(pc_contract *k) {
   if (!k) return fail(PC_EINVAL, "null contract");
   cudaSetDevice(k->ctx->device);
-  cudaStreamSynchronize(k->ctx->stream);
-  cudaFree(k->d_code);
+  ctx_free(k->ctx, k->d_code, k->pooled);  // after the stream's launches that read it
   --k->ctx->live_objects;
   delete k;
   return PC_OK;

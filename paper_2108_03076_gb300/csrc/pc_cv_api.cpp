@@ -131,9 +131,8 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
     jl.off_win -= shift;
     jl.words -= shift;
     const size_t jsm = price_smem_bytes(k->prog.code.size(), pool, jl.words, kBlock);
-    CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(jsm)), "jit attribute");
     int nb = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBlock, jsm), "jit occupancy");
+    CU(jit_occupancy(ctx, kern, kBlock, jsm, nb), "jit occupancy");
     if (nb < 1) return fail(PC_ELIMIT, "specialised control-variate kernel cannot be resident");
     const uint64_t jneed = (a.n_tiles + kBlock / 32 - 1) / (kBlock / 32);
     const int jgrid = int(std::min<uint64_t>(uint64_t(ctx->sm_count) * nb, jneed));

@@ -46,6 +46,8 @@ struct pc_ctx {
   int32_t jit = 0;               // 1: price with run-time specialised kernels
   std::mutex jit_mu;
   std::multimap<uint64_t, JitEntry> jit_cache;  // program hash -> compiled kernels
+  std::map<std::pair<const void *, size_t>, int> jit_occ;  // (kernel, smem) -> resident blocks
+  cudaMemPool_t pool = nullptr;  // stream-ordered allocations of contracts (null: cudaMalloc)
   double timeout_s = 300.0;
   int live_objects = 0;
 };
@@ -63,11 +65,21 @@ struct pc_contract {
   pc_ctx *ctx = nullptr;
   pc::Program prog;
   pc::XInsn *d_code = nullptr;
+  bool pooled = false;            // d_code came from the context's memory pool
+  std::vector<uint32_t> image;    // program then padded pool: the uploaded words
   std::mutex mu;
   std::map<std::pair<uint64_t, uint64_t>, int32_t> win_cache;  // (model id, layout key) -> window
 };
 
 namespace pc {
+
+// Device memory on the context's stream: from its memory pool (stream
+// ordered, no device synchronisation) when it has one, else cudaMalloc.
+cudaError_t ctx_alloc(pc_ctx *c, void **p, size_t bytes, bool &pooled);
+void ctx_free(pc_ctx *c, void *p, bool pooled);
+// Resident blocks per SM of a run-time compiled kernel at this dynamic
+// shared memory (sets its shared-memory limit on first use; memoised).
+cudaError_t jit_occupancy(pc_ctx *c, const void *kern, int block, size_t smem, int &blocks);
 
 // Record a message for pc_last_error and return the status.
 pc_status fail(pc_status s, const std::string &m);
