@@ -523,6 +523,12 @@ pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
       cudaGetLastError();
     }
   }
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&c->h_res), 16 * sizeof(double), 0);
+  if (e == cudaSuccess) {
+    c->stage_words = 16384;
+    e = cudaHostAlloc(reinterpret_cast<void **>(&c->h_stage), c->stage_words * 4, 0);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_res, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_res, 0, 8 * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_gout, PC_MAX_UNDERLYINGS * 8 * sizeof(double));
@@ -533,6 +539,9 @@ pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
     if (c->d_control) cudaFree(c->d_control);
     if (c->d_gout) cudaFree(c->d_gout);
     if (c->d_res) cudaFree(c->d_res);
+    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->h_res) cudaFreeHost(c->h_res);
     if (c->pool) cudaMemPoolDestroy(c->pool);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -553,6 +562,9 @@ pc_status pc_destroy(pc_ctx *c) {
   jit_release(c);
   if (c->d_gout) cudaFree(c->d_gout);
   if (c->d_res) cudaFree(c->d_res);
+  if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->h_res) cudaFreeHost(c->h_res);
   if (c->pool) cudaMemPoolDestroy(c->pool);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -669,12 +681,47 @@ pc_status pc_load_payoff(pc_ctx *c, const uint32_t *bytecode, size_t n_words, co
   if (!c || !out) return fail(PC_EINVAL, "null argument");
   try {
     pc_contract *k = new pc_contract();
-    std::string err;
-    pc_status s = compile_program(bytecode, n_words, consts, n_consts, template_params, n_params,
-                                  p1, p2, true, k->prog, err);
-    if (s != PC_OK) {
-      delete k;
-      return fail(s, err);
+    // the compiler's inputs as words: the cache key
+    std::vector<uint32_t> key;
+    key.reserve(n_words + 2 * n_consts + n_params + 5);
+    key.push_back(uint32_t(n_words));
+    key.push_back(uint32_t(n_consts));
+    key.push_back(uint32_t(n_params));
+    key.push_back(uint32_t(p1));
+    key.push_back(uint32_t(p2));
+    if (bytecode) key.insert(key.end(), bytecode, bytecode + n_words);
+    for (size_t i = 0; consts && i < n_consts; ++i) {
+      uint64_t b;
+      std::memcpy(&b, consts + i, 8);
+      key.push_back(uint32_t(b));
+      key.push_back(uint32_t(b >> 32));
+    }
+    for (size_t i = 0; template_params && i < n_params; ++i) key.push_back(uint32_t(template_params[i]));
+    uint64_t h = 1469598103934665603ull;  // FNV-1a
+    for (uint32_t w : key)
+      for (int b = 0; b < 4; ++b) h = (h ^ ((w >> (8 * b)) & 0xffu)) * 1099511628211ull;
+    bool hit = false;
+    {
+      std::lock_guard<std::mutex> g(c->load_mu);
+      auto range = c->program_cache.equal_range(h);
+      for (auto it = range.first; it != range.second; ++it)
+        if (it->second.first == key) {
+          k->prog = it->second.second;
+          hit = true;
+          break;
+        }
+    }
+    if (!hit) {
+      std::string err;
+      pc_status s = compile_program(bytecode, n_words, consts, n_consts, template_params, n_params,
+                                    p1, p2, true, k->prog, err);
+      if (s != PC_OK) {
+        delete k;
+        return fail(s, err);
+      }
+      std::lock_guard<std::mutex> g(c->load_mu);
+      if (c->program_cache.size() >= 4096) c->program_cache.clear();
+      c->program_cache.emplace(h, std::make_pair(std::move(key), k->prog));
     }
     CU(cudaSetDevice(c->device), "cudaSetDevice");
     // program then constant pool (padded to whole 16-byte words), one buffer
@@ -685,10 +732,23 @@ pc_status pc_load_payoff(pc_ctx *c, const uint32_t *bytecode, size_t n_words, co
     void *dp = nullptr;
     cudaError_t e = ctx_alloc(c, &dp, k->image.size() * 4 + 16, k->pooled);
     k->d_code = static_cast<XInsn *>(dp);
-    // ordered on the context's stream before any launch that reads it; the
-    // source stays alive with the contract
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(k->d_code, k->image.data(), k->image.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    // ordered on the context's stream before any launch that reads it:
+    // through the pinned stage when it is large enough (asynchronous), else
+    // from the contract's own copy
+    if (e == cudaSuccess) {
+      std::lock_guard<std::mutex> g(c->load_mu);
+      if (k->image.size() <= c->stage_words) {
+        if (c->stage_pending) e = cudaEventSynchronize(c->stage_ev);
+        if (e == cudaSuccess) {
+          std::memcpy(c->h_stage, k->image.data(), k->image.size() * 4);
+          e = cudaMemcpyAsync(k->d_code, c->h_stage, k->image.size() * 4, cudaMemcpyHostToDevice, c->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(c->stage_ev, c->stream);
+        c->stage_pending = e == cudaSuccess;
+      } else {
+        e = cudaMemcpyAsync(k->d_code, k->image.data(), k->image.size() * 4, cudaMemcpyHostToDevice, c->stream);
+      }
+    }
     if (e != cudaSuccess) {
       ctx_free(c, k->d_code, k->pooled);
       delete k;
@@ -763,10 +823,12 @@ pc_status pc_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, ui
   pc_ctx *c = m->ctx;
   pc_status s = run_price(m, k, n_paths, 0, seed, 0, c->d_res, nullptr);
   if (s != PC_OK) return s;
-  double h[5];
-  CU(cudaMemcpyAsync(h, c->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "result copy");
+  // pinned read-back: the copy is queued and the bounded wait covers it
+  CU(cudaMemcpyAsync(c->h_res, c->d_res, 5 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "result copy");
   s = wait_stream(c);
   if (s != PC_OK) return s;
+  double h[5];
+  std::memcpy(h, c->h_res, sizeof(h));
   int32_t status;
   std::memcpy(&status, &h[4], 4);
   s = check_status(c, status);

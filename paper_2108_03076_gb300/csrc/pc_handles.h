@@ -48,6 +48,17 @@ struct pc_ctx {
   std::multimap<uint64_t, JitEntry> jit_cache;  // program hash -> compiled kernels
   std::map<std::pair<const void *, size_t>, int> jit_occ;  // (kernel, smem) -> resident blocks
   cudaMemPool_t pool = nullptr;  // stream-ordered allocations of contracts (null: cudaMalloc)
+  double *h_res = nullptr;       // pinned [16]: results read back by the blocking calls
+  // pinned staging of program uploads: the previous upload has left it when
+  // stage_ev completes
+  uint32_t *h_stage = nullptr;
+  size_t stage_words = 0;
+  cudaEvent_t stage_ev = nullptr;
+  bool stage_pending = false;
+  // compiled programs by their inputs (bytecode, constants, template
+  // parameters, parties): reloading a program skips the compiler
+  std::mutex load_mu;
+  std::multimap<uint64_t, std::pair<std::vector<uint32_t>, pc::Program>> program_cache;
   double timeout_s = 300.0;
   int live_objects = 0;
 };
