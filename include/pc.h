@@ -383,7 +383,7 @@ typedef struct pc_batch_info {
 /* Build a plan over n contracts: contract i is priced against models[i]
  * with n_paths[i] paths (2 .. 2^40) on Philox stream word i under `seed`.
  * All models and contracts must belong to one context and stay alive until
- * pc_batch_destroy.  config may be NULL (block 128, unit_split 32).
+ * pc_batch_destroy.  config may be NULL (block 128, unit_split 128).
  * Allocates the plan's device memory (per-contract arguments, units,
  * reduction scratch, outputs) and instantiates its graph.
  * Errors: PC_EINVAL (null, empty, mixed contexts, n_paths out of range),

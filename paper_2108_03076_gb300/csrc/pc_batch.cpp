@@ -62,7 +62,7 @@ struct pc_batch {
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> joins;
   cudaGraphExec_t exec = nullptr;
-  pc_batch_config cfg{128, 32};
+  pc_batch_config cfg{128, 128};
   uint64_t n_units = 0;
   double paths_per_thread = 0.0;
   bool tuned = false;
@@ -328,7 +328,8 @@ pc_status create(size_t n, const pc_model *const *models, const pc_contract *con
   CU(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming), "event");
   build_groups(B);
   if (B->groups.size() > size_t(kMaxGroups)) return fail(PC_ELIMIT, "too many batch groups");
-  pc_batch_config cfg{128, 32};
+  // default: the tuner's pick on the 1024-contract synthetic portfolio
+  pc_batch_config cfg{128, 128};
   if (config) cfg = *config;
   pc_status s = configure(B, cfg);
   if (s != PC_OK) return s;

@@ -526,9 +526,9 @@ pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void **>(&c->h_res), 16 * sizeof(double), 0);
   if (e == cudaSuccess) {
     c->stage_words = 16384;
-    e = cudaHostAlloc(reinterpret_cast<void **>(&c->h_stage), c->stage_words * 4, 0);
+    e = cudaHostAlloc(reinterpret_cast<void **>(&c->h_stage), 2 * c->stage_words * 4, 0);
   }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+  for (int h = 0; h < 2 && e == cudaSuccess; ++h) e = cudaEventCreateWithFlags(&c->stage_ev[h], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_res, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_res, 0, 8 * sizeof(double), c->stream);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_gout, PC_MAX_UNDERLYINGS * 8 * sizeof(double));
@@ -539,7 +539,8 @@ pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
     if (c->d_control) cudaFree(c->d_control);
     if (c->d_gout) cudaFree(c->d_gout);
     if (c->d_res) cudaFree(c->d_res);
-    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    for (cudaEvent_t ev : c->stage_ev)
+      if (ev) cudaEventDestroy(ev);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->h_res) cudaFreeHost(c->h_res);
     if (c->pool) cudaMemPoolDestroy(c->pool);
@@ -562,7 +563,8 @@ pc_status pc_destroy(pc_ctx *c) {
   jit_release(c);
   if (c->d_gout) cudaFree(c->d_gout);
   if (c->d_res) cudaFree(c->d_res);
-  if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+  for (cudaEvent_t ev : c->stage_ev)
+    if (ev) cudaEventDestroy(ev);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->h_res) cudaFreeHost(c->h_res);
   if (c->pool) cudaMemPoolDestroy(c->pool);
@@ -737,14 +739,24 @@ pc_status pc_load_payoff(pc_ctx *c, const uint32_t *bytecode, size_t n_words, co
     // from the contract's own copy
     if (e == cudaSuccess) {
       std::lock_guard<std::mutex> g(c->load_mu);
-      if (k->image.size() <= c->stage_words) {
-        if (c->stage_pending) e = cudaEventSynchronize(c->stage_ev);
-        if (e == cudaSuccess) {
-          std::memcpy(c->h_stage, k->image.data(), k->image.size() * 4);
-          e = cudaMemcpyAsync(k->d_code, c->h_stage, k->image.size() * 4, cudaMemcpyHostToDevice, c->stream);
+      const size_t words = (k->image.size() + 3) & ~size_t(3);  // 16-byte steps
+      if (words <= c->stage_words) {
+        if (c->stage_off + words > c->stage_words) {
+          // leave this half (its copies complete at the event) and take the
+          // other one once its own copies are done
+          e = cudaEventRecord(c->stage_ev[c->stage_half], c->stream);
+          c->stage_pending[c->stage_half] = e == cudaSuccess;
+          c->stage_half ^= 1;
+          c->stage_off = 0;
+          if (e == cudaSuccess && c->stage_pending[c->stage_half]) e = cudaEventSynchronize(c->stage_ev[c->stage_half]);
+          c->stage_pending[c->stage_half] = false;
         }
-        if (e == cudaSuccess) e = cudaEventRecord(c->stage_ev, c->stream);
-        c->stage_pending = e == cudaSuccess;
+        if (e == cudaSuccess) {
+          uint32_t *dst = c->h_stage + size_t(c->stage_half) * c->stage_words + c->stage_off;
+          std::memcpy(dst, k->image.data(), k->image.size() * 4);
+          e = cudaMemcpyAsync(k->d_code, dst, k->image.size() * 4, cudaMemcpyHostToDevice, c->stream);
+          c->stage_off += words;
+        }
       } else {
         e = cudaMemcpyAsync(k->d_code, k->image.data(), k->image.size() * 4, cudaMemcpyHostToDevice, c->stream);
       }

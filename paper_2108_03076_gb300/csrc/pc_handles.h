@@ -49,12 +49,14 @@ struct pc_ctx {
   std::map<std::pair<const void *, size_t>, int> jit_occ;  // (kernel, smem) -> resident blocks
   cudaMemPool_t pool = nullptr;  // stream-ordered allocations of contracts (null: cudaMalloc)
   double *h_res = nullptr;       // pinned [16]: results read back by the blocking calls
-  // pinned staging of program uploads: the previous upload has left it when
-  // stage_ev completes
+  // pinned staging of program uploads, two halves filled in turn: a half is
+  // reused once the event recorded when it was left has completed
   uint32_t *h_stage = nullptr;
-  size_t stage_words = 0;
-  cudaEvent_t stage_ev = nullptr;
-  bool stage_pending = false;
+  size_t stage_words = 0;        // words per half
+  size_t stage_off = 0;          // next free word in the current half
+  int stage_half = 0;
+  cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  bool stage_pending[2] = {false, false};
   // compiled programs by their inputs (bytecode, constants, template
   // parameters, parties): reloading a program skips the compiler
   std::mutex load_mu;
