@@ -204,7 +204,11 @@ std::string generate(const Program &p, int d, int kind) {
     << "}  // namespace\n"
     << "}  // namespace pc\n";
   if (kind >= kJitCv) {
-    o << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ") pc_jit_cv(const pc::PriceArgs a,\n"
+    // the second-order term needs many registers: at least 5 resident
+    // blocks there (-10 %; the first-order kernel is fastest uncapped)
+    const bool gamma = ((kind - kJitCv) & kCvGamma) != 0;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << (gamma ? ", 5" : "")
+      << ") pc_jit_cv(const pc::PriceArgs a,\n"
       << "    const pc::CvArgs c) {\n"
       << "  pc::cv_tiles<pc::D, " << (kind - kJitCv) << ">(a, c, [&](const uint4 *P, const float *pool, float2 *R,\n"
       << "      const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
