@@ -47,8 +47,10 @@ __global__ void __launch_bounds__(kBlock) price_kernel(const PriceArgs a) {
 // tiles run as in price_kernel and finish into
 // the contract's own reduction scratch, so each contract's sums are those of
 // a single-contract launch.
+// At least 5 resident 128-thread blocks (<= 102 registers): -4 % per
+// portfolio replay against the uncapped 112 registers, 6 blocks spill.
 template <int D>
-__global__ void __launch_bounds__(kBlock) batch_kernel(const BatchArgs b) {
+__global__ void __launch_bounds__(kBlock, 5) batch_kernel(const BatchArgs b) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *slot = smem + (b.slot_bytes / 4) * warp;
