@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "pc_internal.h"
 #include "pc_cv_types.h"
@@ -16,6 +17,13 @@ float *mlp_scratch(struct ::pc_mlp *net, size_t floats);
 // Waits for the context's stream; PC_ETIMEOUT (and the status cleared) if a
 // tensor-core product of the network reported an expired wait.
 pc_status mlp_status(struct ::pc_mlp *net);
+// The network's forward on a given stream (capturable), and what a
+// captured table build needs: the slot of its graph by key (created empty),
+// the network's pinned read-back buffer [8] (null if none), its status word.
+pc_status mlp_forward_on(struct ::pc_mlp *net, const float *d_x, size_t n, float *d_y, cudaStream_t s);
+cudaGraphExec_t *mlp_graph(struct ::pc_mlp *net, const std::vector<uint8_t> &key);
+float *mlp_pinned(struct ::pc_mlp *net);
+int32_t *mlp_status_word(struct ::pc_mlp *net);
 
 struct CvFeatureArgs {
   float ln_spot[kCvMaxD];

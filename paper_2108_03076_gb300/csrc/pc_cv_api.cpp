@@ -216,6 +216,58 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
   if (!buf) return fail(PC_ENOMEM, "table scratch");
   float *X = buf, *Y = buf + rows * kCvFeatures, *d0 = Y + rows * kCvOutputs;
   const CvArgs ca = device_args(c, nullptr, m->H, false);
+  float *pin = mlp_pinned(net);
+  if (pin) {
+    // the whole build (features, forward, scatter, read-back of delta0 and
+    // the network's status) as one CUDA graph, captured once per set of
+    // arguments and replayed
+    // (the pricing-only fields -- betas, the second-order switch, delta0,
+    // which this call outputs -- do not enter the features kernel)
+    CvArgs kc = ca;
+    kc.beta = kc.beta2 = 0.f;
+    kc.use_gamma = kc.pilot = 0;
+    for (float &v : kc.delta0) v = 0.f;
+    std::vector<uint8_t> key(sizeof(kc) + sizeof(fa) + 3 * sizeof(uint64_t));
+    const uint64_t extra[3] = {reinterpret_cast<uint64_t>(d_tables), reinterpret_cast<uint64_t>(buf), rows};
+    std::memcpy(key.data(), &kc, sizeof(kc));
+    std::memcpy(key.data() + sizeof(ca), &fa, sizeof(fa));
+    std::memcpy(key.data() + sizeof(ca) + sizeof(fa), extra, sizeof(extra));
+    cudaGraphExec_t *slot = mlp_graph(net, key);
+    if (!*slot) {
+      cudaStream_t cap = nullptr;
+      CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      pc_status st = PC_OK;
+      if (e == cudaSuccess) {
+        e = launch_cv_features(kc, fa, X, rows, cap);
+        if (e == cudaSuccess) st = mlp_forward_on(net, X, rows, Y, cap);
+        if (e == cudaSuccess && st == PC_OK) e = launch_cv_scatter(Y, kCvOutputs, rows, c->d, d_tables, d0, cap);
+        if (e == cudaSuccess && st == PC_OK)
+          e = cudaMemcpyAsync(pin, d0, 4 * sizeof(float), cudaMemcpyDeviceToHost, cap);
+        if (e == cudaSuccess && st == PC_OK)
+          e = cudaMemcpyAsync(pin + 4, mlp_status_word(net), sizeof(int32_t), cudaMemcpyDeviceToHost, cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess && st == PC_OK) e = cudaGraphInstantiate(slot, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+      }
+      cudaStreamDestroy(cap);
+      if (st != PC_OK) return st;
+      if (e != cudaSuccess) {
+        *slot = nullptr;
+        return cuda_fail(e, "table-build graph");
+      }
+    }
+    CU(cudaGraphLaunch(*slot, ctx->stream), "table build");
+    s = wait_stream(ctx);
+    if (s != PC_OK) return s;
+    int32_t status = 0;
+    std::memcpy(&status, pin + 4, sizeof(status));
+    if (status != 0) return mlp_status(net);  // clears the word, reports PC_ETIMEOUT
+    for (int i = 0; i < 3; ++i) c->delta0[i] = i < c->d ? pin[i] : 0.f;
+    return PC_OK;
+  }
   cudaError_t e = launch_cv_features(ca, fa, X, rows, ctx->stream);
   if (e != cudaSuccess) s = cuda_fail(e, "table features");
   if (s == PC_OK) s = pc_mlp_forward(net, X, rows, Y);

@@ -61,12 +61,17 @@ struct pc_mlp {
   int32_t gemm = PC_MLP_GEMM_AUTO;  // product kernel choice (pc_mlp_set_gemm)
   bool tc_ok = false;               // tcgen05 products available on this device
   std::map<uint64_t, TcMaps> tc_maps;  // forward operand descriptors by (layer, rows)
+  float *h_pin = nullptr;             // pinned [8]: read-back of captured table builds
+  std::vector<std::pair<std::vector<uint8_t>, cudaGraphExec_t>> graphs;  // captured table builds
 };
 
 namespace pc {
+void mlp_drop_graphs(pc_mlp *N);
+
 float *mlp_scratch(pc_mlp *N, size_t floats) {
   if (floats <= N->scratch_cap) return N->scratch;
   if (wait_stream(N->ctx) != PC_OK) return nullptr;
+  mlp_drop_graphs(N);
   if (N->scratch) cudaFree(N->scratch);
   N->scratch = nullptr;
   N->scratch_cap = 0;
@@ -85,6 +90,7 @@ pc_status mlp_status(pc_mlp *N) {
   wait_stream(N->ctx);
   return fail(PC_ETIMEOUT, "tensor-core product: a bounded wait expired");
 }
+
 }  // namespace pc
 
 namespace {
@@ -302,6 +308,36 @@ pc_status set_weights(pc_mlp *N, const float *w) {
 
 }  // namespace
 
+namespace pc {
+
+void mlp_drop_graphs(pc_mlp *N) {
+  for (auto &g : N->graphs)
+    if (g.second) cudaGraphExecDestroy(g.second);
+  N->graphs.clear();
+}
+
+cudaGraphExec_t *mlp_graph(pc_mlp *N, const std::vector<uint8_t> &key) {
+  for (auto &g : N->graphs)
+    if (g.first == key) return &g.second;
+  if (N->graphs.size() >= 16) mlp_drop_graphs(N);
+  N->graphs.emplace_back(key, nullptr);
+  return &N->graphs.back().second;
+}
+
+float *mlp_pinned(pc_mlp *N) { return N->h_pin; }
+int32_t *mlp_status_word(pc_mlp *N) { return N->dstatus; }
+
+pc_status mlp_forward_on(pc_mlp *N, const float *d_x, size_t n, float *d_y, cudaStream_t s) {
+  for (size_t b0 = 0; b0 < n; b0 += N->max_rows) {
+    const size_t nb = std::min(N->max_rows, n - b0), rows = rows_for(nb);
+    CU(launch_to_bf16(d_x + b0 * N->w[0], nb, N->w[0], N->X, rows, N->wp[0], s), "input");
+    CU(forward(N, rows, s), "forward");
+    CU(launch_unpad(N->Y, N->wp[N->L], nb, N->w[N->L], d_y + b0 * N->w[N->L], s), "output");
+  }
+  return PC_OK;
+}
+}  // namespace pc
+
 extern "C" {
 
 pc_status pc_mlp_create(pc_ctx *c, const int32_t *widths, int32_t n_widths, uint64_t max_batch,
@@ -346,6 +382,10 @@ pc_status pc_mlp_create(pc_ctx *c, const int32_t *widths, int32_t n_widths, uint
   cudaMemsetAsync(N->mem, 0, bytes, c->stream);
   N->tc_ok = gemm_tc_init() == cudaSuccess;
   cudaGetLastError();
+  if (cudaHostAlloc(reinterpret_cast<void **>(&N->h_pin), 8 * sizeof(float), 0) != cudaSuccess) {
+    N->h_pin = nullptr;
+    cudaGetLastError();
+  }
   pc_status s = upload_padded(N, init.data());
   if (s != PC_OK) {
     cudaFree(N->mem);
@@ -361,6 +401,8 @@ pc_status pc_mlp_destroy(pc_mlp *N) {
   cudaSetDevice(N->ctx->device);
   wait_stream(N->ctx);
   if (N->exec) cudaGraphExecDestroy(N->exec);
+  mlp_drop_graphs(N);
+  if (N->h_pin) cudaFreeHost(N->h_pin);
   if (N->mem) cudaFree(N->mem);
   if (N->scratch) cudaFree(N->scratch);
   delete N;
@@ -397,15 +439,8 @@ pc_status pc_mlp_get_params(const pc_mlp *N, float *params, size_t n) {
 
 pc_status pc_mlp_forward(pc_mlp *N, const float *d_x, size_t n, float *d_y) {
   if (!N || (n && (!d_x || !d_y))) return fail(PC_EINVAL, "null argument");
-  cudaStream_t s = N->ctx->stream;
   CU(cudaSetDevice(N->ctx->device), "cudaSetDevice");
-  for (size_t b0 = 0; b0 < n; b0 += N->max_rows) {
-    const size_t nb = std::min(N->max_rows, n - b0), rows = rows_for(nb);
-    CU(launch_to_bf16(d_x + b0 * N->w[0], nb, N->w[0], N->X, rows, N->wp[0], s), "input");
-    CU(forward(N, rows, s), "forward");
-    CU(launch_unpad(N->Y, N->wp[N->L], nb, N->w[N->L], d_y + b0 * N->w[N->L], s), "output");
-  }
-  return PC_OK;
+  return mlp_forward_on(N, d_x, n, d_y, N->ctx->stream);
 }
 
 pc_status pc_mlp_gradients(pc_mlp *N, const float *d_x, const float *d_t, const float *w, size_t n,
@@ -496,6 +531,7 @@ pc_status pc_mlp_set_gemm(pc_mlp *N, int32_t kind) {
     wait_stream(N->ctx);
     if (N->exec) cudaGraphExecDestroy(N->exec);  // the training step is captured again
     N->exec = nullptr;
+    mlp_drop_graphs(N);
     N->gemm = kind;
   }
   return PC_OK;

@@ -218,13 +218,16 @@ class LearnedCV:
         return dy.cpu().numpy()
 
     def tables(self, model: int, grid: int = 12, width_sd: float = 4.5, call_level: float = 1.0,
-               ki_level: float = 0.6, coupon: float = 0.05, gamma: bool = True):
+               ki_level: float = 0.6, coupon: float = 0.05, gamma: bool = True, out=None):
         """(description, device tables) for a model of the template, with the
-        calibrated betas (and the second-order term when ``gamma``)."""
+        calibrated betas (and the second-order term when ``gamma``).  ``out``:
+        a float32 CUDA tensor to fill (large enough), else a new one; rebuilding
+        into the same buffer replays the build's captured graph."""
         import torch
         desc = pc_cv_grid(model, grid, width_sd, (1.0, 1.0, 1.0), call_level, ki_level, coupon)
         n = pc_cv_table_size(desc)
-        dt = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+        dt = out if out is not None and out.numel() >= max(n, 1) else torch.empty(max(n, 1), dtype=torch.float32,
+                                                                                 device="cuda")
         pc_cv_tables(self.net, model, desc, dt.data_ptr(), n)
         desc.use_gamma = 1 if gamma else 0
         desc.beta, desc.beta2 = self.betas if gamma else (self.betas_first_order, 0.0)
