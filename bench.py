@@ -446,6 +446,46 @@ def portfolio_reference(args, items):
     print(json.dumps(line), flush=True)
 
 
+def portfolio_cpu_baseline(items, budget_s: float = 12.0) -> dict:
+    """The oracle as it stands, single process: 512 paths of each contract in
+    portfolio order until the time budget is used; its path-date rate scaled
+    to contracts/s at the portfolio's own path budgets."""
+    from oracle import il_text, mc
+    from oracle.paths import Market
+    pd, el, i = 0, 0.0, 0
+    while el < budget_s and i < len(items):
+        it = items[i]
+        n = min(512, it.n_paths)
+        env = {f"${k}": v for k, v in enumerate(it.tparams)}
+        t = time.perf_counter()
+        mc.payoffs(il_text.parse(it.il_text), Market(**vars(it.market)), env, 0, 1, n, PORTFOLIO_SEED, i, 0)
+        el += time.perf_counter() - t
+        pd += n * it.market.n
+        i += 1
+    value = (pd / el) * len(items) / sum(it.n_paths * it.market.n for it in items)
+    return {"value": value, "unit": "contracts/s", "cores": 1, "kind": "oracle",
+            "sample": f"512 paths of contracts 0..{i - 1} ({pd} path-dates, {el:.1f} s, numpy FP64, 1 thread), "
+                      "rate scaled to the portfolio's path budgets"}
+
+
+def learned_cpu_baseline(w, budget_s: float = 12.0) -> dict:
+    """The oracle's plain Monte Carlo on chunks of 2^13 paths until the time
+    budget is used, scaled to the paths a 1e-4 relative standard error
+    needs (no control variate: the oracle prices plainly)."""
+    import numpy as np
+    xs, el, off = [], 0.0, 0
+    while el < budget_s:
+        dt, x = oracle_run(w, 1 << 13, off)
+        el += dt
+        xs.append(x)
+        off += 1 << 13
+    x = np.concatenate(xs)
+    need = (x.std() / abs(x.mean()) / TARGET_REL_SE) ** 2
+    return {"value": (len(x) / el) / need, "unit": "contracts/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(x)} paths of the contract ({el:.1f} s, numpy FP64, 1 thread), plain MC rate "
+                      "scaled to the paths a 1e-4 relative standard error needs"}
+
+
 def run_portfolio(args):
     items = W.portfolio()
     if args.impl == "reference":
@@ -557,6 +597,8 @@ def run_portfolio(args):
                                        f"{clock_hz / 1e6:.0f} MHz issue (MUFU: x16)"},
             "clocks": clk.summary(),
         }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = portfolio_cpu_baseline(items)
         print(json.dumps(line), flush=True)
     pc.pc_batch_destroy(plan)
     for k in contracts:
@@ -731,11 +773,16 @@ def run_learned(args):
         "training": {"data_s_wall": t_data, "train_s_gpu": t_train, "samples": len(data.x)},
         "surrogate": {"value": surrogate, "mc_price": plain_price,
                       "rel_error": abs(surrogate - plain_price) / abs(plain_price)},
-        "gpu_launches": steps * 3,
+        # per step one plain and one control-variate launch, plus the five
+        # timed table builds (features, input conversion, 4 products,
+        # output, scatter: 8 kernels each)
+        "gpu_launches": steps * 2 + 5 * 8,
         "e2e": {"value": ws / e2e, "unit": "contracts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 48,
                 "note": "pc_cv_tables + pc_price_cv on resident model/contract, host wall clock"},
         "clocks": clk.summary(),
     }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = learned_cpu_baseline(w)
     print(json.dumps(line), flush=True)
     net.close()
     pc.pc_contract_destroy(contract)
