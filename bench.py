@@ -135,6 +135,23 @@ def measured_peaks() -> dict:
         return {}
 
 
+def profile_record(workload: str, kind: str) -> dict:
+    """The committed ncu summary of the workload's kernel (profiles/*.json)
+    if it was taken on the current kernel source, else {}."""
+    name = "price_kernel" if kind == "interpreter" else "jit_price_kernel"
+    path = os.path.join(ROOT, "profiles", f"{name}_{workload}.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        h = hashlib.sha256()
+        for src in (KERNEL_SRCS if kind == "interpreter" else JIT_SRCS):
+            with open(src, "rb") as f:
+                h.update(f.read())
+        return p if p.get("kernel_sha256") == h.hexdigest() else {}
+    except (OSError, ValueError):
+        return {}
+
+
 def profile_traffic(workload: str, kind: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source."""
@@ -165,39 +182,82 @@ def oracle_run(w, n_paths: int, offset: int = 0):
     return time.perf_counter() - t, x
 
 
+def _oracle_chunk(task):
+    """Worker of the all-core oracle timing: paths [off, off + n)."""
+    w, n, off = task
+    oracle_run(w, n, off)
+    return n
+
+
 def cpu_baseline(w, budget_s: float = 12.0) -> dict:
-    """The oracle as it stands, single process, on chunks of the workload's
-    paths until the time budget is used; rate in path-dates/s."""
+    """The oracle as it stands, on chunks of the workload's paths: one
+    process until the time budget is used, then every host core (a spawned
+    process pool over path ranges, sized to about the same wall time);
+    rates in path-dates/s, the all-core one reported as the value."""
     chunk = 1 << 14
     done, el = 0, 0.0
     while el < budget_s and done < w.n_paths:
         dt, _ = oracle_run(w, min(chunk, w.n_paths - done), done)
         el += dt
         done += min(chunk, w.n_paths - done)
-    return {"value": done * w.market.n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"paths 0..{done - 1} of the workload ({done} paths, {el:.1f} s, numpy FP64, 1 thread)"}
+    rate1 = done * w.market.n / el
+    out = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle", "value_1_core": rate1,
+           "sample": f"paths 0..{done - 1} of the workload ({done} paths, {el:.1f} s, numpy FP64, 1 thread)"}
+    cores = os.cpu_count() or 1
+    if cores > 1:
+        import multiprocessing as mp
+        per = max(1, int(rate1 / w.market.n * budget_s / chunk))      # chunks one core does in the budget
+        tasks = [(w, chunk, (i * chunk) % max(w.n_paths - chunk, 1)) for i in range(per * cores)]
+        # spawn: the parent holds a CUDA context, a forked child would not start cleanly
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_chunk, [(w, 256, 0)] * cores)            # imports and first call
+            t0 = time.perf_counter()
+            n_all = sum(pool.map(_oracle_chunk, tasks, chunksize=1))
+            el_all = time.perf_counter() - t0
+        out.update({"value": n_all * w.market.n / el_all, "cores": cores,
+                    "sample": out["sample"] + f"; then {n_all} paths over {cores} spawned processes "
+                              f"in {el_all:.1f} s wall"})
+    return out
 
 
 def run_reference(args, w):
+    """The oracle as it stands on the host cores: each step prices one chunk
+    per core (a spawned process pool over path ranges) of about 80 k
+    path-dates (2^14 paths of the 5-date autocall): enough to hide the
+    pool's dispatch, short enough for a thousand steps in about a minute."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    chunk = 1 << 13
-    for s in range(args.warmup):
-        oracle_run(w, chunk, s * chunk)
-    times = []
-    for s in range(args.steps):
-        dt, _ = oracle_run(w, chunk, (args.warmup + s) * chunk)
-        times.append(dt)
-    total = sum(times)
-    value = args.steps * chunk * w.market.n / total
+    chunk = max(256, ((1 << 14) * 5 // max(w.market.n, 1)) // 256 * 256)
+    cores = os.cpu_count() or 1
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(cores) as pool:
+        off = 0
+
+        def step():
+            nonlocal off
+            tasks = [(w, chunk, (off + i * chunk) % max(w.n_paths - chunk, 1)) for i in range(cores)]
+            off += cores * chunk
+            t = time.perf_counter()
+            n = sum(pool.map(_oracle_chunk, tasks, chunksize=1))
+            return time.perf_counter() - t, n
+
+        for _ in range(args.warmup):
+            step()
+        total, paths = 0.0, 0
+        for _ in range(args.steps):
+            dt, n = step()
+            total += dt
+            paths += n
+    value = paths * w.market.n / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config(w, None),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{chunk} paths per step of the workload"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{chunk} paths per core per step of the workload, {cores} spawned "
+                                       "processes (numpy FP64)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -340,6 +400,7 @@ def main():
     launch_s = t_dev / args.steps
     achieved = ops["ops"] * w.n_paths / launch_s
     traffic, traffic_paths = profile_traffic(w.name, "interpreter" if args.interpret else "specialised")
+    prof = profile_record(w.name, "interpreter" if args.interpret else "specialised")
     if traffic is not None and traffic_paths:
         traffic = traffic * w.n_paths / traffic_paths
 
@@ -365,6 +426,11 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": traffic,
                          "mufu_frac": ops["mufu"] * w.n_paths / launch_s / peak_mufu,
+                         # the busiest pipe's issue rate and the issue-active fraction from the
+                         # committed ncu capture of this kernel source (null if none)
+                         "ncu_max_pipe": prof.get("ncu_max_pipe"),
+                         "ncu_max_pipe_frac": prof.get("ncu_max_pipe_frac"),
+                         "ncu_issue_active": prof.get("ncu_issue_active"),
                          "alg_ops_per_path": ops["ops"],
                          "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x "
                                        f"{clock_hz / 1e6:.0f} MHz issue (MUFU: x16)"},
