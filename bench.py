@@ -275,7 +275,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="worst_of_autocall_3u_5d",
-                    choices=sorted(W.ALL) + [PORTFOLIO, LEARNED])
+                    choices=sorted(W.ALL) + sorted(W.GREEKS) + [PORTFOLIO, LEARNED])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--interpret", action="store_true",
@@ -285,6 +285,8 @@ def main():
         return run_portfolio(args)
     if args.workload == LEARNED:
         return run_learned(args)
+    if args.workload in W.GREEKS:
+        return run_greeks(args)
     w = W.ALL[args.workload]()
     if args.impl == "reference":
         return run_reference(args, w)
@@ -313,6 +315,7 @@ def main():
     info = pc.pc_verify_payoff(words, consts, w.tparams)
     contract = pc.pc_load_payoff(ctx, words, consts, w.tparams, 0, 1)
     minfo = pc.pc_model_query(model)
+    linfo = pc.pc_price_info(model, contract, w.n_paths)
     offset = rank * w.n_paths
     jit_s = None
     if not args.interpret:
@@ -411,8 +414,15 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {**config(w, info.n_nodes), "parallelism": f"path ranges x{ws}",
-                       "kernel": "interpreter" if args.interpret else
-                                 "specialised to the program (run-time compiled, NVRTC)"},
+                       "kernel": ("interpreter (window of dates in HBM)" if linfo.hbm_window else
+                                  "interpreter" if args.interpret else
+                                  "specialised to the program (run-time compiled, NVRTC)")},
+            # where the window of simulated dates lives (a program that looks
+            # far back keeps it in HBM: bytes of the launch's buffer, bytes
+            # each path writes per simulated date)
+            "window": {"dates": linfo.window, "placement": "hbm" if linfo.hbm_window else "shared",
+                       "hbm_bytes": int(linfo.hbm_window_bytes),
+                       "bytes_written_per_path_date": int(linfo.window_bytes_written_per_path_date)},
             "interpreter_ms_per_step": interp_ms, "specialised_compile_s": jit_s,
             "contracts_per_sec_at_1e-4_rel_se": contracts_per_s,
             "price": mean, "stderr": math.sqrt(var / w.n_paths),
@@ -436,6 +446,20 @@ def main():
                                        f"{clock_hz / 1e6:.0f} MHz issue (MUFU: x16)"},
             "clocks": clk.summary(),
         }
+        if linfo.hbm_window:
+            # the window in HBM: every simulated date is written once and the
+            # program reads it back -- algorithmically n d floats out and in
+            # per path; bound by HBM when that fraction exceeds the issue one
+            hbm_peak = 1e9 * float(peaks.get("hbm_gbs", 6800.0))
+            alg_bytes = 2.0 * 4.0 * spec.n * spec.d * w.n_paths
+            hbm_frac = alg_bytes / launch_s / hbm_peak
+            line["roofline"]["hbm"] = {"achieved": alg_bytes / launch_s / 1e9, "peak": hbm_peak / 1e9,
+                                       "unit": "GB/s", "frac": hbm_frac, "alg_bytes_per_launch": alg_bytes,
+                                       "peak_basis": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks
+                                       else "fallback 6.8 TB/s"}
+            if hbm_frac > line["roofline"]["frac"]:
+                line["roofline"].update({"bound": "hbm", "achieved": alg_bytes / launch_s / 1e9,
+                                         "peak": hbm_peak / 1e9, "unit": "GB/s", "frac": hbm_frac})
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
@@ -674,6 +698,133 @@ def run_portfolio(args):
     pc.pc_destroy(ctx)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Pathwise sensitivities: delta and vega of every underlying
+# ---------------------------------------------------------------------------
+
+
+def greeks_oracle_rate(w, budget_s: float) -> tuple:
+    """The oracle's pathwise derivatives (oracle.pathwise: payoff and its
+    S0 / sigma derivatives per path, every underlying) on chunks of 2^10
+    paths until the budget is used: (path-date tangent evaluations per s,
+    paths, seconds)."""
+    from oracle import il_text
+    from oracle import pathwise as OP
+    from oracle.paths import Market
+    il = il_text.parse(w.il_text)
+    mk = Market(**vars(w.market))
+    env = {f"${i}": v for i, v in enumerate(w.tparams)}
+    done, el = 0, 0.0
+    while el < budget_s:
+        t = time.perf_counter()
+        for g in range(mk.d):
+            OP.pathwise(il, mk, env, 0, 1, 1 << 10, w.seed, g, offset=done)
+        el += time.perf_counter() - t
+        done += 1 << 10
+    return mk.d * done * mk.n / el, done, el
+
+
+def run_greeks(args):
+    w = W.GREEKS[args.workload]()
+    spec = w.market
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        greeks_oracle_rate(w, 0.5)
+        rate, done, el = greeks_oracle_rate(w, 12.0)
+        line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": greeks_config(w, ws),
+                "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{done} paths x {spec.d} underlyings (central differences of the "
+                                           "FP64 payoff on common paths), 1 thread"},
+                "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import torch
+    import paper_2108_03076_gb300 as pc
+    torch.cuda.set_device(local)
+    from paper_2108_03076_gb300 import build
+    build.build()
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
+    ctx = pc.pc_create(local, stream.cuda_stream)
+    model = pc.pc_model_create(ctx, spec.S0, spec.sigma, spec.corr, spec.r, spec.days)
+    words, consts = pc.pc_assemble(w.il_text)
+    contract = pc.pc_load_payoff(ctx, words, consts, w.tparams, 0, 1)
+    d = spec.d
+    for _ in range(args.warmup):
+        res = pc.pc_greeks(model, contract, w.n_paths, w.seed, d)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    steps = max(3, min(args.steps, 200))
+    ms = []
+    with ClockSampler(local) as clk:
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            res = pc.pc_greeks(model, contract, w.n_paths, w.seed, d)      # d tangent launches, blocking
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+    t_step = statistics.median(ms) / 1e3
+    price, delta, vega, se = res
+    # end to end through the public API: load, sensitivities, drop
+    t0 = time.perf_counter()
+    for _ in range(5):
+        k = pc.pc_load_payoff(ctx, words, consts, w.tparams, 0, 1)
+        pc.pc_greeks(model, k, w.n_paths, w.seed, d)
+        pc.pc_contract_destroy(k)
+    e2e_step = (time.perf_counter() - t0) / 5
+    path_dates = d * w.n_paths * spec.n          # every underlying's launch re-simulates the paths
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    clock_hz = 1e6 * float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = props.multi_processor_count * 128 * clock_hz
+    ops = alg_ops_per_path(pc.pc_model_query(model))
+    line = {
+        "metric": METRIC, "value": ws * path_dates / t_step, "unit": UNIT, "n_gpus": ws, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": greeks_config(w, ws),
+        "value_note": "path-dates per second, each of the d tangent launches (delta and vega of one "
+                      "underlying) counted",
+        "price": price, "delta": list(delta), "vega": list(vega), "stderr": list(se),
+        "gpu_launches": steps * d,
+        "e2e": {"value": ws * path_dates / e2e_step, "unit": UNIT,
+                "h2d_bytes_per_step": int(words.nbytes + consts.nbytes + 4 * len(w.tparams)),
+                "d2h_bytes_per_step": 8 * (2 + 4 * d),
+                "note": "pc_load_payoff + pc_greeks + pc_contract_destroy per step, host wall clock"},
+        "roofline": {"bound": "alu", "achieved": d * ops["ops"] * w.n_paths / t_step / 1e12,
+                     "peak": peak_ops / 1e12, "unit": "Tops/s",
+                     "frac": d * ops["ops"] * w.n_paths / t_step / peak_ops, "traffic": None,
+                     "alg_ops_per_path": ops["ops"],
+                     "note": "path generation of each tangent launch counted (the tangent arithmetic "
+                             "is not: a lower bound)",
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x "
+                                   f"{clock_hz / 1e6:.0f} MHz issue"},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        rate, done, el = greeks_oracle_rate(w, 12.0)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{done} paths x {d} underlyings ({el:.1f} s, FP64 central "
+                                          "differences on common paths, 1 thread)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    pc.pc_contract_destroy(contract)
+    pc.pc_model_destroy(model)
+    pc.pc_destroy(ctx)
+
+
+def greeks_config(w, ws) -> dict:
+    return {"workload": w.name, "n_paths": w.n_paths, "n_dates": w.market.n, "underlyings": w.market.d,
+            "sensitivities": "pathwise delta and vega of every underlying (tangent mode, one launch each)",
+            "seed": w.seed, "parallelism": f"replicas x{ws}",
+            "l2": "flushed between steps by a 256 MiB device write"}
 
 
 # ---------------------------------------------------------------------------

@@ -220,11 +220,43 @@ def daily_barrier(n_paths: int = 1 << 22) -> Workload:
                     n_paths, PATH_SEED_BASE + 2, 1.0)
 
 
+def reverse_asian_text(n: int, K: float = 1.0) -> str:
+    """Average of assets 0 and 1 over the n dates ending at $0, summed newest
+    fixing first (each term looks one date further back): a program that
+    is not streamable in a short window (lookback n - 1)."""
+    T = "(tplus 0 $0)"
+    terms = [f"(add (model 0 (tplus {T} {-j})) (model 1 (tplus {T} {-j})))" for j in range(n)]
+    s = terms[0]
+    for x in terms[1:]:
+        s = f"(add {s} {x})"
+    return f"(mult (max (sub (div {s} {float(2 * n)}) {_fmt(K)}) 0.0) (payoff {T} 0 1))"
+
+
+def reverse_asian(n_paths: int = 1 << 20) -> Workload:
+    """2 correlated GBMs (corr 0.5), 300 daily dates, the average-rate call
+    summed newest fixing first: window of 512 dates, kept in HBM."""
+    d = 2
+    mk = MarketSpec([1.0] * d, draw_sigmas(d), const_corr(d, 0.5), 0.03, list(range(1, 301)))
+    return Workload("reverse_asian_2u_300d", mk, reverse_asian_text(300), [300], n_paths,
+                    PATH_SEED_BASE + 3, 1.0)
+
+
+def basket_call_greeks(n_paths: int = 1 << 20) -> Workload:
+    """The autocall's market (3 GBMs, 5 annual dates) with an equally
+    weighted basket call struck at 1 paid at the fifth date: Lipschitz in
+    the path, so pathwise delta and vega hold."""
+    mk = worst_of_autocall().market
+    return Workload("greeks_basket_call_3u_5d", mk, basket_call_text(3, 1.0), [5], n_paths,
+                    PATH_SEED_BASE + 4, 1.0)
+
+
 ALL = {
     "european_call_1u_1d": european_call,
     "worst_of_autocall_3u_5d": worst_of_autocall,
     "daily_barrier_3u_365d": daily_barrier,
+    "reverse_asian_2u_300d": reverse_asian,
 }
+GREEKS = {"greeks_basket_call_3u_5d": basket_call_greeks}
 
 
 # ---------------------------------------------------------------------------
