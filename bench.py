@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -75,7 +76,12 @@ def alg_ops_per_path(info) -> dict:
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clocks and throttle reasons while running."""
+    """nvidia-smi samples of SM clocks and throttle reasons while running.
+
+    The sampler is up (first sample read) before the region starts and
+    stops after a sample taken once the region has ended, so a region
+    shorter than the sampling period still has its neighbours recorded
+    (`in_region` counts the samples taken inside it)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -84,29 +90,47 @@ class ClockSampler:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.out = None
+        self.samples = []  # (host time, line)
+        self.t0 = self.t1 = None
+        self.cv = threading.Condition()
+
+    def _read(self):
+        for l in self.proc.stdout:
+            if l.strip():
+                with self.cv:
+                    self.samples.append((time.perf_counter(), l))
+                    self.cv.notify_all()
+
+    def _wait(self, pred, timeout):
+        with self.cv:
+            self.cv.wait_for(pred, timeout)
 
     def __enter__(self):
         try:
-            self.out = open(os.devnull, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+            self._wait(lambda: len(self.samples) > 0, 5.0)
         except OSError:
             self.proc = None
+        self.t0 = time.perf_counter()
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
+        self.t1 = time.perf_counter()
         if self.proc is not None:
+            self._wait(lambda: any(t > self.t1 for t, _ in self.samples), 2.0)
             self.proc.terminate()
             try:
-                txt, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                txt, _ = self.proc.communicate()
-            self.lines = [l for l in (txt or "").splitlines() if l.strip()]
+                self.proc.wait()
+        with self.cv:
+            self.lines = [l for _, l in self.samples]
+            self.in_region = sum(1 for t, _ in self.samples if self.t0 <= t <= self.t1)
 
     def summary(self) -> dict:
         sm, mx, reasons = [], None, set()
@@ -124,7 +148,8 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "in_region": getattr(self, "in_region", 0)}
 
 
 def measured_peaks() -> dict:
@@ -414,9 +439,12 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {**config(w, info.n_nodes), "parallelism": f"path ranges x{ws}",
-                       "kernel": ("interpreter (window of dates in HBM)" if linfo.hbm_window else
-                                  "interpreter" if args.interpret else
-                                  "specialised to the program (run-time compiled, NVRTC)")},
+                       "kernel": ("interpreter" if args.interpret else
+                                  "specialised to the program (run-time compiled, NVRTC)"
+                                  if info.n_insn <= pc.JIT_MAX_INSNS else
+                                  f"interpreter ({info.n_insn} instructions: above the "
+                                  f"{pc.JIT_MAX_INSNS} that are specialised)")
+                                 + (", window of dates in HBM" if linfo.hbm_window else "")},
             # where the window of simulated dates lives (a program that looks
             # far back keeps it in HBM: bytes of the launch's buffer, bytes
             # each path writes per simulated date)

@@ -331,12 +331,18 @@ pc_status pc_price_info(const pc_model *model, const pc_contract *contract, uint
  * time by NVRTC on first use for each underlying count, cached on the
  * context by program content -- reloading the same program reuses it --
  * and freed by pc_destroy): the same operations in the same order as the
- * interpreting kernel, without the per-instruction dispatch.
- * Launches that need the HBM window keep the interpreting kernel.
+ * interpreting kernel, without the per-instruction dispatch, with the
+ * window of dates in shared memory or in HBM as the launch places it.
+ * Programs of more than PC_JIT_MAX_INSNS executable instructions are not
+ * specialised (NVRTC's time grows faster than the program's length: about
+ * 20 s for 600 instructions); their launches interpret them.
  * Default: 0 (interpret).  Errors: PC_EINVAL. */
+#define PC_JIT_MAX_INSNS 384
 pc_status pc_set_jit(pc_ctx *ctx, int32_t enabled);
 /* Compile (now) the contract's specialised kernel for the model's
- * underlying count.  Blocks; typically tens to hundreds of milliseconds.
+ * underlying count (shared-memory window, pooled sums); does nothing for a
+ * program beyond PC_JIT_MAX_INSNS instructions.  Blocks; typically tens
+ * of milliseconds to a few seconds.
  * Errors: PC_EINVAL, PC_ECUDA (the compiler's log in pc_last_error). */
 pc_status pc_jit_compile(const pc_model *model, const pc_contract *contract);
 

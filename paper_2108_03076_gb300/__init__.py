@@ -89,6 +89,7 @@ class LaunchInfo(C.Structure):
 
 WINDOW_AUTO, WINDOW_SHARED, WINDOW_HBM = 0, 1, 2
 MLP_GEMM_AUTO, MLP_GEMM_MMA_SYNC = 0, 1
+JIT_MAX_INSNS = 384  # longer programs are interpreted with pc_set_jit on (pc.h)
 
 
 class ProgramInfo(C.Structure):

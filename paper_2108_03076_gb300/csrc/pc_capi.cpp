@@ -305,10 +305,6 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
   pc_ctx *c = m->ctx;
   s = ensure_partials(c, size_t(L.args.n_tiles) * 2);
   if (s != PC_OK) return s;
-  if (L.hbm_window) {
-    s = bind_hbm_window(c, L, m->H.d);
-    if (s != PC_OK) return s;
-  }
   L.args.width = 2;
   reduction_chunks(L.args.n_tiles, L.args.chunk_tiles, L.args.n_chunks);
   L.args.tile_partials = c->d_partials;
@@ -316,10 +312,11 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
   L.args.out = d_out;
   L.args.out_paths = d_payoffs;
   CU(cudaSetDevice(c->device), "cudaSetDevice");
-  if (c->jit && !L.hbm_window) {
+  if (c->jit && jit_eligible(k)) {
     // the contract's run-time specialised kernel (same arguments and shape)
     cudaKernel_t jk = nullptr;
-    s = jit_kernel(k, m->H.d, d_payoffs != nullptr ? kJitPriceWrite : kJitPrice, jk);
+    s = jit_kernel(k, m->H.d, (d_payoffs != nullptr ? kJitPriceWrite : kJitPrice) | (L.hbm_window ? kJitHbm : 0),
+                   jk);
     if (s != PC_OK) return s;
     const void *kern = reinterpret_cast<const void *>(jk);
     // the specialised evaluator keeps its operand stack in registers: drop
@@ -337,9 +334,19 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
     if (nb < 1) return fail(PC_ELIMIT, "specialised kernel cannot be resident");
     const uint64_t wpb = uint64_t(L.block) / 32;
     const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * nb, (L.args.n_tiles + wpb - 1) / wpb));
+    if (L.hbm_window) {
+      // the HBM window holds a column per thread of this launch's grid
+      L.grid = grid;
+      s = bind_hbm_window(c, L, m->H.d);
+      if (s != PC_OK) return s;
+    }
     void *args[] = {&L.args};
     CU(cudaLaunchKernel(kern, dim3(grid), dim3(L.block), args, smem, c->stream), "specialised price kernel");
     return PC_OK;
+  }
+  if (L.hbm_window) {
+    s = bind_hbm_window(c, L, m->H.d);
+    if (s != PC_OK) return s;
   }
   CU(launch_price(L.args, L.grid, L.block, L.smem, c->stream), "price kernel");
   return PC_OK;
@@ -870,6 +877,7 @@ pc_status pc_set_jit(pc_ctx *c, int32_t enabled) {
 pc_status pc_jit_compile(const pc_model *m, const pc_contract *k) {
   if (!m || !k) return fail(PC_EINVAL, "null model or contract");
   if (m->ctx != k->ctx) return fail(PC_EINVAL, "model and contract belong to different contexts");
+  if (!jit_eligible(k)) return PC_OK;  // launches interpret it
   CU(cudaSetDevice(m->ctx->device), "cudaSetDevice");
   cudaKernel_t jk = nullptr;
   return jit_kernel(k, m->H.d, kJitPrice, jk);

@@ -115,7 +115,7 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
   a.out_paths = d_xm;
   CU(cudaSetDevice(ctx->device), "cudaSetDevice");
   const CvArgs ca = device_args(c, tables, m->H, pilot);
-  if (ctx->jit) {
+  if (ctx->jit && jit_eligible(k)) {
     // the contract's run-time specialised control-variate kernel: the
     // evaluator keeps its operand stack in registers, so the stack words
     // leave the per-thread shared region

@@ -17,9 +17,10 @@
 
 // A run-time specialised pricing kernel: the program it was compiled from
 // (code and pool words), the underlying count and the per-path variant.
-// Kinds of run-time specialised kernels: pricing, pricing with per-path
-// payoffs, and the control-variate kernel (kJitCv + its kCv* mode bits).
-constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitCv = 16;
+// Kinds of run-time specialised kernels: pricing (bit kJitPriceWrite: with
+// per-path payoffs; bit kJitHbm: the window of dates in HBM), and the
+// control-variate kernel (kJitCv + its kCv* mode bits).
+constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitHbm = 2, kJitCv = 16;
 
 struct JitEntry {
   std::vector<uint32_t> program;
@@ -139,6 +140,9 @@ pc_status ensure_partials(pc_ctx *c, size_t doubles);
 // underlyings and a kernel kind (kJit*; compiled on first use, cached on
 // the context by program content).
 pc_status jit_kernel(const pc_contract *k, int d, int kind, cudaKernel_t &out);
+// Programs of at most PC_JIT_MAX_INSNS instructions are specialised; the
+// launches of longer ones interpret them.
+bool jit_eligible(const pc_contract *k);
 void jit_release(pc_ctx *c);
 
 // Turn a raised device status word into PC_EDEVICE (and clear it).

@@ -47,6 +47,10 @@ std::string insn_literal(const XInsn &I) {
 // Above this many reading instructions a program whose stack depths are
 // not known calls the date generator out of line.
 constexpr int kInlineDateSites = 12;
+// Above this many reading instructions the re-entry switch of the shared
+// generator makes NVRTC's time grow faster than the program (100 terms of
+// a two-asset average: 13 s shared, 3.2 s out of line): call it out of line.
+constexpr int kSharedDateSites = 64;
 
 // Instructions that read simulated dates (and may have to generate them).
 bool reads_dates(const XInsn &I) {
@@ -137,7 +141,8 @@ bool stack_depths(const Program &p, std::vector<int> &sp_at) {
 
 // Straight-line evaluator for the program and d underlyings, and the kernel
 // of `kind` around it: pc_jit_price (price_tiles; per-path payoffs written
-// out for kJitPriceWrite) or pc_jit_cv (cv_tiles with mode kind - kJitCv).
+// out with kJitPriceWrite, the window of dates in HBM with kJitHbm) or
+// pc_jit_cv (cv_tiles with mode kind - kJitCv).
 // With two or more reading instructions and known stack depths, the date
 // generator has one copy: a reading instruction that needs dates jumps to
 // it and it jumps back to the top of that instruction, restoring the
@@ -148,7 +153,7 @@ std::string generate(const Program &p, int d, int kind) {
   std::ostringstream o;
   const size_t n = p.code.size();
   std::vector<int> sp_at;
-  const bool shared = date_sites(p) >= 2 && stack_depths(p, sp_at);
+  const bool shared = date_sites(p) >= 2 && date_sites(p) <= kSharedDateSites && stack_depths(p, sp_at);
   // without re-entry points, many reading instructions call one
   // out-of-line copy instead of inlining the generator at each
   if (!shared && date_sites(p) > kInlineDateSites) o << "#define PC_JIT_OUTLINE_DATES 1\n";
@@ -158,7 +163,7 @@ std::string generate(const Program &p, int d, int kind) {
     << "namespace pc {\n"
     << "namespace {\n"
     << "constexpr int D = " << d << ";\n"
-    << "constexpr bool GW = false;\n"
+    << "constexpr bool GW = " << (kind < kJitCv && (kind & kJitHbm) ? "true" : "false") << ";\n"
     << "#define PC_JIT_STACK_SLOTS " << std::max(1, int(p.frame_slots)) << "\n"
     << "__device__ __forceinline__ float2 jit_eval(const uint4 *P, const float *pool, float2 *R,\n"
     << "    const PriceArgs &a, const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],\n"
@@ -220,7 +225,7 @@ std::string generate(const Program &p, int d, int kind) {
   // at least 7 resident 128-thread blocks (<= 72 registers): the fastest
   // measured cap (autocall unchanged, daily barrier -7 %, 5 blocks slower)
   o << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ", 7) pc_jit_price(const pc::PriceArgs a) {\n"
-    << "  pc::price_tiles<pc::D, " << (kind == kJitPriceWrite ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
+    << "  pc::price_tiles<pc::D, " << (kind & kJitPriceWrite ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
     << "      float2 *R, const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
     << "      const float (&S0)[pc::D]) { return pc::jit_eval(P, pool, R, a, g, live0, live1, Bm, S0); });\n"
     << "}\n";
@@ -285,6 +290,8 @@ pc_status compile(const Program &p, int d, int kind, int device, cudaLibrary_t &
 
 namespace pc {
 
+bool jit_eligible(const pc_contract *k) { return k->prog.code.size() <= size_t(PC_JIT_MAX_INSNS); }
+
 pc_status jit_kernel(const pc_contract *k, int d, int kind, cudaKernel_t &out) {
   // the program's words: code, then pool bits
   std::vector<uint32_t> words;
@@ -341,7 +348,7 @@ extern "C" pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_wor
   if (d < 1 || d > PC_MAX_UNDERLYINGS) return fail(PC_EINVAL, "d must be 1..4");
   const bool cv_kind = kind >= kJitCv && kind < kJitCv + 8 && kind != kJitCv + kCvWrite &&
                        kind != kJitCv + (kCvWrite | kCvPilot) && kind != kJitCv + (kCvWrite | kCvPilot | kCvGamma);
-  if (kind != kJitPrice && kind != kJitPriceWrite && !cv_kind) return fail(PC_EINVAL, "unknown kernel kind");
+  if ((kind < 0 || kind > (kJitPriceWrite | kJitHbm)) && !cv_kind) return fail(PC_EINVAL, "unknown kernel kind");
   if (cv_kind && d > kCvMaxD) return fail(PC_EINVAL, "control-variate kernels take d <= 3");
   Program p;
   std::string err;

@@ -1,8 +1,11 @@
 """GPU run-time specialised kernels (pc_set_jit): the same per-path payoffs,
 bit for bit, and the same sums as the interpreting kernel on every test
 program, the oracle's values on a sample, the compiled kernel reused when
-the same program is loaded again, and the HBM-window launches left to the
-interpreter."""
+the same program is loaded again, the same again for launches whose
+window of dates lives in HBM, and programs beyond the specialising limit
+interpreted."""
+import time
+
 import numpy as np
 import pytest
 
@@ -68,7 +71,10 @@ def test_specialised_matches_oracle_and_is_reused(eng):
     assert p1 == pc.pc_price(m, k, 1 << 18, 5)
 
 
-def test_hbm_window_launch_keeps_the_interpreter(eng):
+def test_long_program_is_interpreted(eng):
+    """A 300-date average (beyond the specialising limit in instructions)
+    is interpreted with pc_set_jit on: pc_jit_compile returns at once and
+    the price is the interpreter's, bit for bit."""
     days = list(range(1, 301))
     spec = W.MarketSpec([1.0], [0.25], [[1.0]], 0.02, days)
     terms = [f"(model 0 (tplus (tplus 0 $0) {-j}))" for j in range(300)]
@@ -78,8 +84,12 @@ def test_hbm_window_launch_keeps_the_interpreter(eng):
     text = f"(mult (max (sub (div {s} 300.0) 1.0) 0.0) (payoff (tplus 0 $0) 0 1))"
     m, k = eng.model(spec), eng.contract(text, [300])
     assert pc.pc_price_info(m, k, 1 << 16).hbm_window == 1
+    assert pc.pc_verify_payoff(*pc.pc_assemble(text), [300]).n_insn > pc.JIT_MAX_INSNS
     pc.pc_set_jit(eng.ctx, True)
     try:
+        t = time.perf_counter()
+        pc.pc_jit_compile(m, k)
+        assert time.perf_counter() - t < 0.05
         p1 = pc.pc_price(m, k, 1 << 16, 9)
     finally:
         pc.pc_set_jit(eng.ctx, False)
@@ -117,3 +127,32 @@ def test_specialised_control_variate_equals_interpreter(eng, gamma):
     np.testing.assert_array_equal(out[True][0].view(np.uint32), out[False][0].view(np.uint32))
     assert out[True][1] == out[False][1]
     assert out[True][2] == out[False][2]
+
+
+@pytest.mark.parametrize("name", ["autocall", "lookback", "double_barrier", "nested_loops", "average_40"])
+def test_specialised_hbm_window_equals_interpreter(eng, name):
+    """Launches whose window of dates lives in HBM (forced, or needed by a
+    300-date lookback) run the specialised kernel too: per-path payoffs and
+    sums bit for bit those of the interpreting kernel."""
+    if name == "average_40":  # 40 dates of a two-asset average, 85 instructions
+        w = W.reverse_asian()
+        text, tp, spec = W.reverse_asian_text(40), [40], w.market
+    else:
+        text, tp, spec, _ = CASES[name]
+    m, k = eng.model(spec), eng.contract(text, tp)
+    pc.pc_set_window_mode(eng.ctx, pc.WINDOW_HBM)
+    try:
+        assert pc.pc_price_info(m, k, 4096).hbm_window
+        n, seed = 4096 + 29, 0x77 + len(name)
+        pc.pc_set_jit(eng.ctx, False)
+        x0, s0 = eng.paths(m, k, n, seed)
+        a0 = eng.sums(m, k, 1 << 15, seed)
+        pc.pc_set_jit(eng.ctx, True)
+        x1, s1 = eng.paths(m, k, n, seed)
+        a1 = eng.sums(m, k, 1 << 15, seed)
+    finally:
+        pc.pc_set_jit(eng.ctx, False)
+        pc.pc_set_window_mode(eng.ctx, pc.WINDOW_AUTO)
+    np.testing.assert_array_equal(x1, x0)
+    np.testing.assert_array_equal(s1, s0)
+    np.testing.assert_array_equal(a1, a0)
