@@ -427,8 +427,9 @@ def main():
     ops = alg_ops_per_path(minfo)
     launch_s = t_dev / args.steps
     achieved = ops["ops"] * w.n_paths / launch_s
-    traffic, traffic_paths = profile_traffic(w.name, "interpreter" if args.interpret else "specialised")
-    prof = profile_record(w.name, "interpreter" if args.interpret else "specialised")
+    kind = "interpreter" if args.interpret or info.n_insn > pc.JIT_MAX_INSNS else "specialised"
+    traffic, traffic_paths = profile_traffic(w.name, kind)
+    prof = profile_record(w.name, kind)
     if traffic is not None and traffic_paths:
         traffic = traffic * w.n_paths / traffic_paths
 
