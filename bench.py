@@ -47,6 +47,8 @@ KERNEL_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
 JIT_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
             for f in ("pc_jit.cpp", "pc_eval_state.inc", "pc_ops.inc", "pc_price.cuh", "pc_device.cuh",
                       "pc_types.h")]
+GREEKS_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
+               for f in ("pc_greeks.cu", "pc_device.cuh", "pc_types.h")]
 PORTFOLIO = "portfolio_1024"
 LEARNED = "learned_cv_worst_of_autocall"
 PORTFOLIO_SEED = 0x5EED0004
@@ -160,16 +162,23 @@ def measured_peaks() -> dict:
         return {}
 
 
+PROFILED = {  # kernel kind: (profiles/ file prefix, sources the capture's hash covers)
+    "interpreter": ("price_kernel", KERNEL_SRCS),
+    "specialised": ("jit_price_kernel", JIT_SRCS),
+    "greeks": ("greeks_kernel", GREEKS_SRCS),
+}
+
+
 def profile_record(workload: str, kind: str) -> dict:
     """The committed ncu summary of the workload's kernel (profiles/*.json)
     if it was taken on the current kernel source, else {}."""
-    name = "price_kernel" if kind == "interpreter" else "jit_price_kernel"
+    name, srcs = PROFILED[kind]
     path = os.path.join(ROOT, "profiles", f"{name}_{workload}.json")
     try:
         with open(path) as f:
             p = json.load(f)
         h = hashlib.sha256()
-        for src in (KERNEL_SRCS if kind == "interpreter" else JIT_SRCS):
+        for src in srcs:
             with open(src, "rb") as f:
                 h.update(f.read())
         return p if p.get("kernel_sha256") == h.hexdigest() else {}
@@ -178,23 +187,10 @@ def profile_record(workload: str, kind: str) -> dict:
 
 
 def profile_traffic(workload: str, kind: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source."""
-    name = "price_kernel" if kind == "interpreter" else "jit_price_kernel"
-    path = os.path.join(ROOT, "profiles", f"{name}_{workload}.json")
-    try:
-        with open(path) as f:
-            p = json.load(f)
-        h = hashlib.sha256()
-        for src in (KERNEL_SRCS if kind == "interpreter" else JIT_SRCS):
-            with open(src, "rb") as f:
-                h.update(f.read())
-        sha = h.hexdigest()
-        if p.get("kernel_sha256") == sha:
-            return p.get("dram_bytes_per_launch"), p.get("n_paths")
-    except (OSError, ValueError):
-        pass
-    return None, None
+    """DRAM bytes per launch and the paths that launch ran, from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    p = profile_record(workload, kind)
+    return p.get("dram_bytes_per_launch"), p.get("n_paths")
 
 
 def oracle_run(w, n_paths: int, offset: int = 0):
@@ -815,6 +811,10 @@ def run_greeks(args):
     clock_hz = 1e6 * float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = props.multi_processor_count * 128 * clock_hz
     ops = alg_ops_per_path(pc.pc_model_query(model))
+    prof = profile_record(w.name, "greeks")
+    traffic = prof.get("dram_bytes_per_launch")
+    if traffic is not None and prof.get("n_paths"):
+        traffic = traffic * w.n_paths / prof["n_paths"]
     line = {
         "metric": METRIC, "value": ws * path_dates / t_step, "unit": UNIT, "n_gpus": ws, "steps": steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
@@ -829,7 +829,10 @@ def run_greeks(args):
                 "note": "pc_load_payoff + pc_greeks + pc_contract_destroy per step, host wall clock"},
         "roofline": {"bound": "alu", "achieved": d * ops["ops"] * w.n_paths / t_step / 1e12,
                      "peak": peak_ops / 1e12, "unit": "Tops/s",
-                     "frac": d * ops["ops"] * w.n_paths / t_step / peak_ops, "traffic": None,
+                     "frac": d * ops["ops"] * w.n_paths / t_step / peak_ops, "traffic": traffic,
+                     "ncu_max_pipe": prof.get("ncu_max_pipe"),
+                     "ncu_max_pipe_frac": prof.get("ncu_max_pipe_frac"),
+                     "ncu_issue_active": prof.get("ncu_issue_active"),
                      "alg_ops_per_path": ops["ops"],
                      "note": "path generation of each tangent launch counted (the tangent arithmetic "
                              "is not: a lower bound)",

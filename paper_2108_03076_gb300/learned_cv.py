@@ -7,7 +7,7 @@ and used as the hedge of the delta-hedge control variate of
 ``pc_price_cv``: Y = X - sum_k Delta(k) . (D_{k+1} S_{k+1} - D_k S_k) has
 the price as its mean for any hedge ratios, so the network only decides
 how much variance is removed; plain Monte Carlo (the X half of the same
-launch) stays the judge of the result.
+launch) is the unbiased check on the result.
 
 Training data: random template parameters and states (observation date k,
 spots S relative to the reference levels, knock-in flag).  Each sample's
