@@ -7,7 +7,9 @@
   stress programs (nested loopif, lookback, history, now/texpr, parties),
   at sizes spanning many tiles with a ragged tail, counters crossing 2^32;
 * full-size workloads in the launch configuration the benchmark times, on
-  sampled paths the oracle computes one by one;
+  sampled paths the oracle computes one by one (the window of dates in HBM
+  for the 300-date average), and the specialised kernel the benchmark
+  runs equal to the interpreter there, bit for bit;
 * prices against closed forms; edge cases and error statuses.
 """
 import math
@@ -109,7 +111,8 @@ def test_party_folding_signs(eng):
 # ---------------------------------------------------------------------------
 
 
-@pytest.mark.parametrize("wl", ["european_call_1u_1d", "worst_of_autocall_3u_5d", "daily_barrier_3u_365d"])
+@pytest.mark.parametrize("wl", ["european_call_1u_1d", "worst_of_autocall_3u_5d", "daily_barrier_3u_365d",
+                                "reverse_asian_2u_300d"])
 def test_full_size_sampled_parity(eng, wl):
     w = W.ALL[wl]()
     m, k = eng.model(w.market), eng.contract(w.il_text, w.tparams)
@@ -121,6 +124,25 @@ def test_full_size_sampled_parity(eng, wl):
     idx = np.unique(np.concatenate([rng.integers(0, w.n_paths, 1500), np.arange(w.n_paths - 40, w.n_paths)]))
     ref, marg = oracle_paths(w.il_text, w.market, w.tparams, 0, w.seed, paths=idx.astype(np.uint64))
     compare(x[idx], ref, marg, w.notional, wl)
+
+
+@pytest.mark.parametrize("wl", ["worst_of_autocall_3u_5d", "daily_barrier_3u_365d"])
+def test_full_size_specialised_kernel_equals_interpreter(eng, wl):
+    """The benchmark's default kernel (specialised to the program) at the
+    benchmark's size and seed: the interpreter's sums and per-path payoffs,
+    bit for bit (so the sampled oracle parity above carries over)."""
+    w = W.ALL[wl]()
+    m, k = eng.model(w.market), eng.contract(w.il_text, w.tparams)
+    x0, s0 = eng.paths(m, k, w.n_paths, w.seed)
+    pc.pc_set_jit(eng.ctx, True)
+    try:
+        x1, s1 = eng.paths(m, k, w.n_paths, w.seed)
+        plain = eng.sums(m, k, w.n_paths, w.seed)
+    finally:
+        pc.pc_set_jit(eng.ctx, False)
+    np.testing.assert_array_equal(x1, x0)
+    np.testing.assert_array_equal(s1, s0)
+    np.testing.assert_array_equal(plain, s0)
 
 
 # ---------------------------------------------------------------------------

@@ -1,7 +1,8 @@
 """GPU pathwise sensitivities (pc_greeks, tangent kernel) against the oracle.
 
 * per path and per underlying: (payoff, d/dS0, d/dsigma) from the kernel
-  match the oracle's FP64 pathwise derivative on the same draws;
+  match the oracle's FP64 pathwise derivative on the same draws, at test
+  sizes and, on sampled runs of paths, at the benchmark's size;
 * pc_greeks equals the average of the per-path probe;
 * European call delta / vega within 3 SE of Black-Scholes;
 * pc_greeks agrees with common-random-number bumps of pc_price;
@@ -70,6 +71,31 @@ def test_per_path_sensitivities_match_oracle(eng, name):
         assert sums[6] == n
         assert sums[2] == pytest.approx(dS.sum(), rel=1e-9, abs=1e-9)
         assert sums[4] == pytest.approx(dv.sum(), rel=1e-9, abs=1e-9)
+
+
+def test_full_size_sampled_sensitivities(eng):
+    """The sensitivities workload at the benchmark's size and seed: per-path
+    (payoff, d/dS0, d/dsigma) of every underlying on three runs of paths
+    (the first, one in the middle, the ragged end) match the oracle's, and
+    the launch's sums are those of all its paths."""
+    w = W.GREEKS["greeks_basket_call_3u_5d"]()
+    m, k = eng.model(w.market), eng.contract(w.il_text, w.tparams)
+    prog = il_text.parse(w.il_text)
+    n = w.n_paths
+    mid = int(np.random.default_rng(8).integers(1, n // 512 - 1)) * 512 + 17
+    for label in range(w.market.d):
+        v, dS, dv, sums = greek_paths(eng, m, k, n, w.seed, label)
+        for off in (0, mid, n - 300):
+            cnt = min(512, n - off)
+            x, rS, rv, marg = pathwise.pathwise(prog, market(w.market), tparam_env(w.tparams), 0, 1, cnt,
+                                                w.seed, label, offset=off)
+            sl = slice(off, off + cnt)
+            compare(v[sl], x, marg, w.notional, ("value", label, off))
+            check_close(dS[sl], rS, marg, ("delta", label, off))
+            check_close(dv[sl], rv, marg, ("vega", label, off))
+        assert sums[6] == n
+        assert sums[2] == pytest.approx(dS.sum(), rel=1e-9)
+        assert sums[4] == pytest.approx(dv.sum(), rel=1e-9)
 
 
 def test_pc_greeks_is_the_mean_of_the_paths(eng):
