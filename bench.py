@@ -48,7 +48,11 @@ JIT_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
             for f in ("pc_jit.cpp", "pc_eval_state.inc", "pc_ops.inc", "pc_price.cuh", "pc_device.cuh",
                       "pc_types.h")]
 GREEKS_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
-               for f in ("pc_greeks.cu", "pc_device.cuh", "pc_types.h")]
+               for f in ("pc_greeks.cu", "pc_greeks.cuh", "pc_greeks_state.inc", "pc_greeks_ops.inc",
+                         "pc_device.cuh", "pc_types.h")]
+JIT_GREEKS_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
+                   for f in ("pc_jit.cpp", "pc_greeks.cuh", "pc_greeks_state.inc", "pc_greeks_ops.inc",
+                             "pc_device.cuh", "pc_types.h")]
 PORTFOLIO = "portfolio_1024"
 LEARNED = "learned_cv_worst_of_autocall"
 PORTFOLIO_SEED = 0x5EED0004
@@ -166,6 +170,7 @@ PROFILED = {  # kernel kind: (profiles/ file prefix, sources the capture's hash 
     "interpreter": ("price_kernel", KERNEL_SRCS),
     "specialised": ("jit_price_kernel", JIT_SRCS),
     "greeks": ("greeks_kernel", GREEKS_SRCS),
+    "greeks_specialised": ("jit_greeks_kernel", JIT_GREEKS_SRCS),
 }
 
 
@@ -782,9 +787,26 @@ def run_greeks(args):
     words, consts = pc.pc_assemble(w.il_text)
     contract = pc.pc_load_payoff(ctx, words, consts, w.tparams, 0, 1)
     d = spec.d
+    specialised = not args.interpret and pc.pc_verify_payoff(words, consts, w.tparams).n_insn <= pc.JIT_MAX_INSNS
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    interp_ms = None
+    if specialised:
+        # the interpreting tangent kernel on the same inputs, for comparison
+        for _ in range(args.warmup):
+            pc.pc_greeks(model, contract, w.n_paths, w.seed, d)
+        im = []
+        for _ in range(max(3, min(args.steps, 20))):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pc.pc_greeks(model, contract, w.n_paths, w.seed, d)
+            b.record(stream)
+            torch.cuda.synchronize()
+            im.append(a.elapsed_time(b))
+        interp_ms = statistics.median(im)
+        pc.pc_set_jit(ctx, True)   # compiled on the first warm-up call
     for _ in range(args.warmup):
         res = pc.pc_greeks(model, contract, w.n_paths, w.seed, d)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     steps = max(3, min(args.steps, 200))
     ms = []
     with ClockSampler(local) as clk:
@@ -811,14 +833,18 @@ def run_greeks(args):
     clock_hz = 1e6 * float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = props.multi_processor_count * 128 * clock_hz
     ops = alg_ops_per_path(pc.pc_model_query(model))
-    prof = profile_record(w.name, "greeks")
+    prof = profile_record(w.name, "greeks_specialised" if specialised else "greeks")
     traffic = prof.get("dram_bytes_per_launch")
     if traffic is not None and prof.get("n_paths"):
         traffic = traffic * w.n_paths / prof["n_paths"]
     line = {
         "metric": METRIC, "value": ws * path_dates / t_step, "unit": UNIT, "n_gpus": ws, "steps": steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": greeks_config(w, ws),
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**greeks_config(w, ws),
+                   "kernel": "specialised to the program (run-time compiled, NVRTC)" if specialised
+                   else "interpreter"},
+        "interpreter_ms_per_step": interp_ms,
         "value_note": "path-dates per second, each of the d tangent launches (delta and vega of one "
                       "underlying) counted",
         "price": price, "delta": list(delta), "vega": list(vega), "stderr": list(se),

@@ -333,7 +333,8 @@ pc_status pc_price_info(const pc_model *model, const pc_contract *contract, uint
  * and freed by pc_destroy): the same operations in the same order as the
  * interpreting kernel, without the per-instruction dispatch, with the
  * window of dates in shared memory or in HBM as the launch places it.
- * Programs of more than PC_JIT_MAX_INSNS executable instructions are not
+ * pc_price_cv and pc_greeks likewise run specialised control-variate and
+ * tangent kernels.  Programs of more than PC_JIT_MAX_INSNS executable instructions are not
  * specialised (NVRTC's time grows faster than the program's length: about
  * 20 s for 600 instructions); their launches interpret them.
  * Default: 0 (interpret).  Errors: PC_EINVAL. */
@@ -620,8 +621,10 @@ pc_status pc_debug_cv_paths(const pc_model *model, const pc_contract *contract, 
 /* Host-only: generate and compile (NVRTC, sm_103a) a specialised kernel of
  * a program for d underlyings, without loading it; *cubin_bytes receives
  * the size of the result.  kind: 0 the pricing kernel, 1 its per-path
- * variant, 16 + m the control-variate kernel of mode m (bits: 1 per-path
- * outputs, 2 second-order term, 4 pilot sums; d <= 3).  Errors: as
+ * variant, 2 and 3 those two with the window of dates in HBM, 16 + m the
+ * control-variate kernel of mode m (bits: 1 per-path outputs, 2
+ * second-order term, 4 pilot sums; d <= 3), 32 the sensitivity kernel and
+ * 33 its per-path variant.  Errors: as
  * pc_verify_payoff; PC_EINVAL for another kind; PC_ECUDA with the
  * compiler's log. */
 pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_words, const double *consts,

@@ -322,7 +322,8 @@ def pc_jit_compile(model: int, contract: int) -> None:
 
 def pc_debug_jit_compile(words, consts, tparams=(), d: int = 1, p1: int = 0, p2: int = 1, kind: int = 0) -> int:
     """Host-only: compile a specialised kernel of a program (kind 0 pricing,
-    1 per-path pricing, 16 + mode control variate); cubin bytes."""
+    1 per-path pricing, 2 / 3 the same with the window in HBM, 16 + mode
+    control variate, 32 / 33 sensitivities); cubin bytes."""
     w, k, t = _arr(words, np.uint32), _arr(consts, np.float64), _arr(tparams, np.int32)
     n = SZ(0)
     _check(lib().pc_debug_jit_compile(_ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,

@@ -291,8 +291,23 @@ pc_status run_greeks(const pc_model *m, const pc_contract *k, uint64_t n_paths, 
   a.out_paths = d_paths;
   a.greek_label = label;
   const uint64_t need = (a.n_tiles + block / 32 - 1) / (block / 32);
-  const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * best_warps / (block / 32), need));
   CU(cudaSetDevice(c->device), "cudaSetDevice");
+  if (c->jit && jit_eligible(k)) {
+    // the contract's run-time specialised tangent kernel (same arguments,
+    // shared-memory layout and block)
+    cudaKernel_t jk = nullptr;
+    s = jit_kernel(k, d, kJitGreeks + (d_paths != nullptr ? 1 : 0), jk);
+    if (s != PC_OK) return s;
+    const void *kern = reinterpret_cast<const void *>(jk);
+    int nb = 0;
+    CU(jit_occupancy(c, kern, block, smem, nb), "jit occupancy");
+    if (nb < 1) return fail(PC_ELIMIT, "specialised sensitivity kernel cannot be resident");
+    const int jgrid = int(std::min<uint64_t>(uint64_t(c->sm_count) * nb, need));
+    void *args[] = {&a};
+    CU(cudaLaunchKernel(kern, dim3(jgrid), dim3(block), args, smem, c->stream), "specialised sensitivity kernel");
+    return PC_OK;
+  }
+  const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * best_warps / (block / 32), need));
   CU(launch_greeks(a, grid, block, smem, c->stream), "sensitivity kernel");
   return PC_OK;
 }

@@ -20,7 +20,7 @@
 // Kinds of run-time specialised kernels: pricing (bit kJitPriceWrite: with
 // per-path payoffs; bit kJitHbm: the window of dates in HBM), and the
 // control-variate kernel (kJitCv + its kCv* mode bits).
-constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitHbm = 2, kJitCv = 16;
+constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitHbm = 2, kJitCv = 16, kJitGreeks = 32;
 
 struct JitEntry {
   std::vector<uint32_t> program;

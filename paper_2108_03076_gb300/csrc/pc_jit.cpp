@@ -139,6 +139,53 @@ bool stack_depths(const Program &p, std::vector<int> &sp_at) {
   return ok;
 }
 
+// Straight-line tangent evaluator (pc_jit_greeks around greeks_tiles; the
+// per-path triples written out with kJitGreeks + 1): each instruction is
+// the interpreter's case for its constant opcode and fields, followed by a
+// jump to whichever of its possible successors the case left in pc.  The
+// operand stack of value-with-tangents stays in shared memory, as in the
+// interpreter.
+std::string generate_greeks(const Program &p, int d, bool write) {
+  std::ostringstream o;
+  const size_t n = p.code.size();
+  o << "#include \"pc_greeks.cuh\"\n"
+    << "namespace pc {\n"
+    << "namespace {\n"
+    << "constexpr int D = " << d << ";\n"
+    << "__device__ __forceinline__ TV jit_eval_greeks(const uint4 *P, const float *pool, float2 *R,\n"
+    << "    const PriceArgs &a, const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],\n"
+    << "    const float (&S0)[D], const float (&Lm)[D * D], int gl, float sig_g) {\n"
+    << "#include \"pc_greeks_state.inc\"\n"
+    << "  goto L0;\n";
+  for (size_t i = 0; i < n; ++i) {
+    const XInsn &I = p.code[i];
+    o << "L" << i << ": {\n"
+      << "  pc = " << i << ";\n"
+      << "  const uint4 I = " << insn_literal(I) << ";\n"
+      << "  const uint32_t op = " << hex(I.opa & 0xffu) << ";\n"
+      << "  const float kk = __uint_as_float(" << hex(I.b) << ");\n"
+      << "#include \"pc_greeks_ops.inc\"\n";
+    std::vector<uint32_t> next = {uint32_t(i + 1), I.c, I.e, uint32_t(i + 2)};
+    for (size_t j = 0; j < next.size(); ++j) {
+      bool seen = false;
+      for (size_t q = 0; q < j; ++q) seen = seen || next[q] == next[j];
+      if (!seen && next[j] < n) o << "  if (pc == " << next[j] << ") goto L" << next[j] << ";\n";
+    }
+    o << "  return tos;\n"
+      << "}\n";
+  }
+  o << "}\n"
+    << "}  // namespace\n"
+    << "}  // namespace pc\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ") pc_jit_greeks(const pc::PriceArgs a) {\n"
+    << "  pc::greeks_tiles<pc::D, " << (write ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
+    << "      float2 *R, const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
+    << "      const float (&S0)[pc::D], const float (&Lm)[pc::D * pc::D], int gl, float sig_g) {\n"
+    << "    return pc::jit_eval_greeks(P, pool, R, a, g, live0, live1, Bm, S0, Lm, gl, sig_g); });\n"
+    << "}\n";
+  return o.str();
+}
+
 // Straight-line evaluator for the program and d underlyings, and the kernel
 // of `kind` around it: pc_jit_price (price_tiles; per-path payoffs written
 // out with kJitPriceWrite, the window of dates in HBM with kJitHbm) or
@@ -150,6 +197,7 @@ bool stack_depths(const Program &p, std::vector<int> &sp_at) {
 // Otherwise the generator is inlined at each reading instruction (out of
 // line beyond kInlineDateSites of them).
 std::string generate(const Program &p, int d, int kind) {
+  if (kind >= kJitGreeks) return generate_greeks(p, d, (kind & 1) != 0);
   std::ostringstream o;
   const size_t n = p.code.size();
   std::vector<int> sp_at;
@@ -276,7 +324,8 @@ pc_status compile(const Program &p, int d, int kind, int device, cudaLibrary_t &
                          cubin);
   if (s != PC_OK) return s;
   CU(cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0), "module load");
-  cudaError_t e = cudaLibraryGetKernel(&kern, lib, kind >= kJitCv ? "pc_jit_cv" : "pc_jit_price");
+  cudaError_t e = cudaLibraryGetKernel(&kern, lib, kind >= kJitGreeks ? "pc_jit_greeks"
+                                                    : kind >= kJitCv ? "pc_jit_cv" : "pc_jit_price");
   if (e != cudaSuccess) {
     cudaLibraryUnload(lib);
     lib = nullptr;
@@ -348,7 +397,9 @@ extern "C" pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_wor
   if (d < 1 || d > PC_MAX_UNDERLYINGS) return fail(PC_EINVAL, "d must be 1..4");
   const bool cv_kind = kind >= kJitCv && kind < kJitCv + 8 && kind != kJitCv + kCvWrite &&
                        kind != kJitCv + (kCvWrite | kCvPilot) && kind != kJitCv + (kCvWrite | kCvPilot | kCvGamma);
-  if ((kind < 0 || kind > (kJitPriceWrite | kJitHbm)) && !cv_kind) return fail(PC_EINVAL, "unknown kernel kind");
+  const bool greeks_kind = kind == kJitGreeks || kind == kJitGreeks + 1;
+  if ((kind < 0 || kind > (kJitPriceWrite | kJitHbm)) && !cv_kind && !greeks_kind)
+    return fail(PC_EINVAL, "unknown kernel kind");
   if (cv_kind && d > kCvMaxD) return fail(PC_EINVAL, "control-variate kernels take d <= 3");
   Program p;
   std::string err;

@@ -6,7 +6,9 @@
 * pc_greeks equals the average of the per-path probe;
 * European call delta / vega within 3 SE of Black-Scholes;
 * pc_greeks agrees with common-random-number bumps of pc_price;
-* the torch.autograd.Function returns pc_greeks as gradients.
+* the torch.autograd.Function returns pc_greeks as gradients;
+* the specialised tangent kernel (pc_set_jit) equals the interpreting one,
+  bit for bit.
 """
 import math
 
@@ -96,6 +98,31 @@ def test_full_size_sampled_sensitivities(eng):
         assert sums[6] == n
         assert sums[2] == pytest.approx(dS.sum(), rel=1e-9)
         assert sums[4] == pytest.approx(dv.sum(), rel=1e-9)
+
+
+@pytest.mark.parametrize("name", GREEK_CASES)
+def test_specialised_sensitivities_equal_interpreter(eng, name):
+    """With pc_set_jit the tangent kernel is specialised to the program: the
+    per-path triples and sums of every underlying's launch, and pc_greeks,
+    bit for bit those of the interpreting kernel."""
+    text, tp, spec, _ = CASES[name]
+    n, seed = 4096 + 37, 0x4242 + len(name)
+    m, k = eng.model(spec), eng.contract(text, tp)
+    got = {}
+    for jit in (False, True):
+        pc.pc_set_jit(eng.ctx, jit)
+        try:
+            got[jit] = ([greek_paths(eng, m, k, n, seed, l) for l in range(spec.d)],
+                        pc.pc_greeks(m, k, 1 << 15, seed, spec.d))
+        finally:
+            pc.pc_set_jit(eng.ctx, False)
+    (p0, g0), (p1, g1) = got[False], got[True]
+    for a, b in zip(p0, p1):
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(y, x)
+    assert g1[0] == g0[0]
+    for x, y in zip(g0[1:], g1[1:]):
+        np.testing.assert_array_equal(y, x)
 
 
 def test_pc_greeks_is_the_mean_of_the_paths(eng):
