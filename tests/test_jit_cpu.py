@@ -1,6 +1,6 @@
-"""The run-time specialised pricing kernel compiles (NVRTC, sm_103a, no GPU
-needed) for every test and workload program at its model's underlying
-count."""
+"""The run-time specialised pricing and sensitivity kernels compile (NVRTC,
+sm_103a, no GPU needed) for every test and workload program at its model's
+underlying count."""
 import pytest
 
 from cases import CASES
@@ -12,6 +12,16 @@ def test_specialised_kernel_compiles(name):
     text, tp, spec, _ = CASES[name]
     w, k = pc.pc_assemble(text)
     assert pc.pc_debug_jit_compile(w, k, tp, len(spec.S0)) > 1000
+
+
+@pytest.mark.parametrize("name", ["european", "lookback", "nested_loops", "double_barrier", "basket_and",
+                                  "history_now", "nat_ops"])
+def test_specialised_sensitivity_kernel_compiles(name):
+    """Loops (loopif frames, fused loop tests), lookbacks, history reads and
+    integer arithmetic through the tangent generator's successor jumps."""
+    text, tp, spec, _ = CASES[name]
+    w, k = pc.pc_assemble(text)
+    assert pc.pc_debug_jit_compile(w, k, tp, len(spec.S0), kind=32) > 1000
 
 
 def test_compile_errors_are_reported():
