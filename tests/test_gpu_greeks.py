@@ -100,7 +100,7 @@ def test_full_size_sampled_sensitivities(eng):
         assert sums[4] == pytest.approx(dv.sum(), rel=1e-9)
 
 
-@pytest.mark.parametrize("name", GREEK_CASES)
+@pytest.mark.parametrize("name", sorted(CASES))
 def test_specialised_sensitivities_equal_interpreter(eng, name):
     """With pc_set_jit the tangent kernel is specialised to the program: the
     per-path triples and sums of every underlying's launch, and pc_greeks,
