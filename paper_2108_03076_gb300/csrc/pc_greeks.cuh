@@ -72,6 +72,15 @@ __device__ __forceinline__ TV model_read(int o, int l, int g, const float2 *R, c
   return r;
 }
 
+// Dates up to o with the window of X = L W beside S, out of line (for a
+// specialised evaluator with many reading instructions).
+template <int D>
+__device__ __noinline__ void advance_dates_x(int o, PathState<D> &ps, const ModelDev &m, const Layout &lay,
+                                             const Rng2 &g, float2 *R, const float (&Bm)[D * D],
+                                             const float (&S0)[D], const float (&Lm)[D * D]) {
+  while (ps.f < o) gen_date<D, true>(ps.f + 1, ps, m, lay, g, R, Bm, S0, Lm);
+}
+
 // X_LRED / X_LANY with tangents (comparisons give zero tangents; min and
 // max carry the tangent of the operand they select, the first on ties).
 template <int D>

@@ -51,6 +51,9 @@ constexpr int kInlineDateSites = 12;
 // generator makes NVRTC's time grow faster than the program (100 terms of
 // a two-asset average: 13 s shared, 3.2 s out of line): call it out of line.
 constexpr int kSharedDateSites = 64;
+// The tangent date generator (S and X windows) is about twice the size of
+// the pricing one: inlined at up to this many reading instructions.
+constexpr int kInlineTangentDateSites = 6;
 
 // Instructions that read simulated dates (and may have to generate them).
 bool reads_dates(const XInsn &I) {
@@ -144,10 +147,12 @@ bool stack_depths(const Program &p, std::vector<int> &sp_at) {
 // the interpreter's case for its constant opcode and fields, followed by a
 // jump to whichever of its possible successors the case left in pc.  The
 // operand stack of value-with-tangents stays in shared memory, as in the
-// interpreter.
+// interpreter.  Beyond kInlineTangentDateSites reading instructions they
+// call one out-of-line copy of the date generator.
 std::string generate_greeks(const Program &p, int d, bool write) {
   std::ostringstream o;
   const size_t n = p.code.size();
+  if (date_sites(p) > kInlineTangentDateSites) o << "#define PC_JIT_OUTLINE_DATES 1\n";
   o << "#include \"pc_greeks.cuh\"\n"
     << "namespace pc {\n"
     << "namespace {\n"
