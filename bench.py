@@ -44,15 +44,16 @@ TARGET_REL_SE = 1e-4
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
                for f in ("pc_kernels.cu", "pc_eval.cuh", "pc_eval_state.inc", "pc_ops.inc", "pc_price.cuh",
                          "pc_device.cuh", "pc_types.h")]
+# a specialised kernel is identified by the CUDA source generated for the
+# program (pc_debug_jit_source) and the device headers that source includes
 JIT_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
-            for f in ("pc_jit.cpp", "pc_eval_state.inc", "pc_ops.inc", "pc_price.cuh", "pc_device.cuh",
-                      "pc_types.h")]
+            for f in ("pc_types.h", "pc_device.cuh", "pc_price.cuh", "pc_eval_state.inc", "pc_ops.inc")]
 GREEKS_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
                for f in ("pc_greeks.cu", "pc_greeks.cuh", "pc_greeks_state.inc", "pc_greeks_ops.inc",
                          "pc_device.cuh", "pc_types.h")]
 JIT_GREEKS_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
-                   for f in ("pc_jit.cpp", "pc_greeks.cuh", "pc_greeks_state.inc", "pc_greeks_ops.inc",
-                             "pc_device.cuh", "pc_types.h")]
+                   for f in ("pc_types.h", "pc_device.cuh", "pc_greeks.cuh", "pc_greeks_state.inc",
+                             "pc_greeks_ops.inc")]
 PORTFOLIO = "portfolio_1024"
 LEARNED = "learned_cv_worst_of_autocall"
 PORTFOLIO_SEED = 0x5EED0004
@@ -166,35 +167,46 @@ def measured_peaks() -> dict:
         return {}
 
 
-PROFILED = {  # kernel kind: (profiles/ file prefix, sources the capture's hash covers)
-    "interpreter": ("price_kernel", KERNEL_SRCS),
-    "specialised": ("jit_price_kernel", JIT_SRCS),
-    "greeks": ("greeks_kernel", GREEKS_SRCS),
-    "greeks_specialised": ("jit_greeks_kernel", JIT_GREEKS_SRCS),
+PROFILED = {  # kernel kind: (profiles/ file prefix, sources, specialised-kernel kind or None)
+    "interpreter": ("price_kernel", KERNEL_SRCS, None),
+    "specialised": ("jit_price_kernel", JIT_SRCS, 0),
+    "greeks": ("greeks_kernel", GREEKS_SRCS, None),
+    "greeks_specialised": ("jit_greeks_kernel", JIT_GREEKS_SRCS, 32),
 }
 
 
-def profile_record(workload: str, kind: str) -> dict:
+def kernel_sha(w, kind: str) -> str:
+    """Hash of what the workload's kernel of this kind is compiled from: the
+    sources, and for a specialised kernel the CUDA source generated for the
+    workload's program."""
+    _, srcs, jit_kind = PROFILED[kind]
+    h = hashlib.sha256()
+    if jit_kind is not None:
+        import paper_2108_03076_gb300 as pc
+        words, consts = pc.pc_assemble(w.il_text)
+        h.update(pc.pc_debug_jit_source(words, consts, w.tparams, w.market.d, 0, 1, jit_kind).encode())
+    for src in srcs:
+        with open(src, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profile_record(w, kind: str) -> dict:
     """The committed ncu summary of the workload's kernel (profiles/*.json)
     if it was taken on the current kernel source, else {}."""
-    name, srcs = PROFILED[kind]
-    path = os.path.join(ROOT, "profiles", f"{name}_{workload}.json")
+    path = os.path.join(ROOT, "profiles", f"{PROFILED[kind][0]}_{w.name}.json")
     try:
         with open(path) as f:
             p = json.load(f)
-        h = hashlib.sha256()
-        for src in srcs:
-            with open(src, "rb") as f:
-                h.update(f.read())
-        return p if p.get("kernel_sha256") == h.hexdigest() else {}
+        return p if p.get("kernel_sha256") == kernel_sha(w, kind) else {}
     except (OSError, ValueError):
         return {}
 
 
-def profile_traffic(workload: str, kind: str):
+def profile_traffic(w, kind: str):
     """DRAM bytes per launch and the paths that launch ran, from the
     committed ncu summary, if it was taken on the current kernel source."""
-    p = profile_record(workload, kind)
+    p = profile_record(w, kind)
     return p.get("dram_bytes_per_launch"), p.get("n_paths")
 
 
@@ -429,8 +441,8 @@ def main():
     launch_s = t_dev / args.steps
     achieved = ops["ops"] * w.n_paths / launch_s
     kind = "interpreter" if args.interpret or info.n_insn > pc.JIT_MAX_INSNS else "specialised"
-    traffic, traffic_paths = profile_traffic(w.name, kind)
-    prof = profile_record(w.name, kind)
+    traffic, traffic_paths = profile_traffic(w, kind)
+    prof = profile_record(w, kind)
     if traffic is not None and traffic_paths:
         traffic = traffic * w.n_paths / traffic_paths
 
@@ -833,7 +845,7 @@ def run_greeks(args):
     clock_hz = 1e6 * float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = props.multi_processor_count * 128 * clock_hz
     ops = alg_ops_per_path(pc.pc_model_query(model))
-    prof = profile_record(w.name, "greeks_specialised" if specialised else "greeks")
+    prof = profile_record(w, "greeks_specialised" if specialised else "greeks")
     traffic = prof.get("dram_bytes_per_launch")
     if traffic is not None and prof.get("n_paths"):
         traffic = traffic * w.n_paths / prof["n_paths"]

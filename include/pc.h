@@ -631,6 +631,17 @@ pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_words, const d
                                size_t n_consts, const int32_t *template_params, size_t n_params,
                                int32_t p1, int32_t p2, int32_t d, int32_t kind, size_t *cubin_bytes);
 
+/* Host-only: the CUDA C++ source that pc_debug_jit_compile hands to NVRTC
+ * for the same arguments (it includes the library's device headers by
+ * name).  *len receives its length; the text and a terminating NUL are
+ * written to out when cap > *len (out may be NULL to query the length).
+ * Identifies the kernel a profile was taken on.  Errors: as
+ * pc_debug_jit_compile. */
+pc_status pc_debug_jit_source(const uint32_t *bytecode, size_t n_words, const double *consts,
+                              size_t n_consts, const int32_t *template_params, size_t n_params,
+                              int32_t p1, int32_t p2, int32_t d, int32_t kind, char *out, size_t cap,
+                              size_t *len);
+
 /* Host-only: the executable form pc_load_payoff would run for this program:
  * 4 words per instruction (opcode | A << 8, then three operand words), then
  * the program's constant pool (float bits).  Writes *n_insn and *n_pool,

@@ -122,6 +122,7 @@ _SIGS = {
     "pc_set_jit": [VP, C.c_int32],
     "pc_jit_compile": [VP, VP],
     "pc_debug_jit_compile": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, I32, I32, C.POINTER(SZ)],
+    "pc_debug_jit_source": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, I32, I32, C.c_char_p, SZ, C.POINTER(SZ)],
     "pc_price_info": [VP, VP, U64, C.POINTER(LaunchInfo)],
     "pc_batch_create": [SZ, C.POINTER(VP), C.POINTER(VP), C.POINTER(U64), U64,
                         C.POINTER(BatchConfig), C.POINTER(VP)],
@@ -329,6 +330,19 @@ def pc_debug_jit_compile(words, consts, tparams=(), d: int = 1, p1: int = 0, p2:
     _check(lib().pc_debug_jit_compile(_ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,
                                       _ptr(t, C.c_int32), t.size, p1, p2, d, int(kind), C.byref(n)))
     return n.value
+
+
+def pc_debug_jit_source(words, consts, tparams=(), d: int = 1, p1: int = 0, p2: int = 1, kind: int = 0) -> str:
+    """Host-only: the CUDA source of a specialised kernel (as handed to
+    NVRTC; it includes the library's device headers by name)."""
+    w, k, t = _arr(words, np.uint32), _arr(consts, np.float64), _arr(tparams, np.int32)
+    n = SZ(0)
+    args = (_ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size, _ptr(t, C.c_int32), t.size,
+            p1, p2, d, int(kind))
+    _check(lib().pc_debug_jit_source(*args, None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value + 1)
+    _check(lib().pc_debug_jit_source(*args, buf, n.value + 1, C.byref(n)))
+    return buf.value.decode()
 
 
 def pc_price_info(model: int, contract: int, n_paths: int) -> LaunchInfo:

@@ -416,3 +416,22 @@ extern "C" pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_wor
   *cubin_bytes = cubin.size();
   return PC_OK;
 }
+
+extern "C" pc_status pc_debug_jit_source(const uint32_t *bytecode, size_t n_words, const double *consts,
+                                         size_t n_consts, const int32_t *tparams, size_t n_params,
+                                         int32_t p1, int32_t p2, int32_t d, int32_t kind, char *out,
+                                         size_t cap, size_t *len) {
+  if (!len) return fail(PC_EINVAL, "null output");
+  if (d < 1 || d > PC_MAX_UNDERLYINGS) return fail(PC_EINVAL, "d must be 1..4");
+  const bool known = (kind >= 0 && kind <= (kJitPriceWrite | kJitHbm)) || (kind >= kJitCv && kind < kJitCv + 8) ||
+                     kind == kJitGreeks || kind == kJitGreeks + 1;
+  if (!known) return fail(PC_EINVAL, "unknown kernel kind");
+  Program p;
+  std::string err;
+  pc_status s = compile_program(bytecode, n_words, consts, n_consts, tparams, n_params, p1, p2, true, p, err);
+  if (s != PC_OK) return fail(s, err);
+  const std::string src = generate(p, d, kind);
+  *len = src.size();
+  if (out && cap > src.size()) std::memcpy(out, src.c_str(), src.size() + 1);
+  return PC_OK;
+}

@@ -49,3 +49,21 @@ def test_unknown_kinds_are_refused(kind, d):
     with pytest.raises(pc.PcError) as e:
         pc.pc_debug_jit_compile(w, k, [], d, kind=kind)
     assert e.value.name == "PC_EINVAL"
+
+
+def test_generated_source_is_what_the_compiler_gets():
+    """pc_debug_jit_source returns the kernel's CUDA source: one entry point
+    per kind, the same text for the same program, another for another."""
+    import workloads as W
+    w_ = W.worst_of_autocall()
+    w, k = pc.pc_assemble(w_.il_text)
+    price = pc.pc_debug_jit_source(w, k, w_.tparams, 3, kind=0)
+    assert "pc_jit_price" in price and "pc_jit_greeks" not in price
+    assert pc.pc_debug_jit_source(w, k, w_.tparams, 3, kind=0) == price
+    assert "pc_jit_greeks" in pc.pc_debug_jit_source(w, k, w_.tparams, 3, kind=32)
+    assert "pc_jit_cv" in pc.pc_debug_jit_source(w, k, w_.tparams, 3, kind=16)
+    w2, k2 = pc.pc_assemble(W.daily_barrier().il_text)
+    assert pc.pc_debug_jit_source(w2, k2, W.daily_barrier().tparams, 3, kind=0) != price
+    with pytest.raises(pc.PcError) as e:
+        pc.pc_debug_jit_source(w, k, w_.tparams, 3, kind=34)
+    assert e.value.name == "PC_EINVAL"
