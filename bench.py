@@ -66,9 +66,8 @@ def dist_env():
 
 def alg_ops_per_path(info) -> dict:
     """Algorithmic thread-operations of generating one full path (all dates),
-    counted on the method's minimum of random numbers (n d normals: n d / 4
-    Philox blocks, n d / 2 Box-Muller pairs; the kernel draws one block per
-    bridge node, which is more for d < 4 and is not counted):
+    counted on the method's n d normals (n d / 4 Philox blocks, n d / 2
+    Box-Muller pairs, which is what the kernel draws):
     Philox4x32-10: 10 rounds x (2 mul.lo + 2 mul.hi + 2 three-way xor) = 60;
     Box-Muller pair: 2 shifts, 2 int->float, 2 FMA (u_a, angle), lg2, mul,
     sqrt, sin, cos, 2 mul = 13 (4 on the MUFU pipe);

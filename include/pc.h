@@ -264,18 +264,25 @@ pc_status pc_price_paths(const pc_model *model, const pc_contract *contract,
  * example code running under an allocator or framework that owns all of
  * the GPU's memory, or code that must not call cudaMalloc at this point of
  * its run.  The paper has no counterpart; this is an engineering entry point.
- * It runs the same pricing kernel on the same inputs and writes the same
- * {sum x, sum x^2, n} triple to the device buffer d_out, but takes the
- * kernel's scratch (per-tile partial sums and work counters) from one
+ * It writes the same {sum x, sum x^2, n} triple to the device buffer d_out
+ * as pc_price_async would with the context's default settings, but takes
+ * the kernel's scratch (per-tile partial sums and work counters) from one
  * fixed device array that the library reserves in every GPU that loads it
- * (4 MiB + 18 KiB, held until the process exits), instead of from
- * memory the context allocates.  It calls no cudaMalloc, cudaFree or other
- * allocating routine; on success it allocates no host memory either (a
- * failure records its message as pc_last_error does).
+ * (4 MiB + 18 KiB, held until the process exits), instead of from memory
+ * the context allocates.  pc_create looks the array's device address up for
+ * its device, so the array is in place before the first call.  The call
+ * makes no cudaMalloc, cudaFree or other allocating call, and the library
+ * allocates no host memory in it on success (a failure records its message
+ * as pc_last_error does).
  *   - n_paths must be 1..PC_NOALLOC_MAX_PATHS; larger requests fail with
  *     PC_ELIMIT.
- *   - The first call on a device looks up the array's device address; make
- *     that first call before any CUDA stream capture.
+ *   - Only the interpreting kernel with the window of dates in shared
+ *     memory: programs that look back more than PC_MAX_WINDOW dates fail
+ *     with PC_ERANGE, and programs whose per-path state leaves no resident
+ *     block fail with PC_ELIMIT, where pc_price_async would keep their
+ *     window in HBM.  pc_set_jit and pc_set_window_mode do not apply; the
+ *     sums equal pc_price_async's bit for bit (its specialised kernel is
+ *     bit-identical to the interpreter).
  *   - Every call shares the one array: calls whose kernels overlap on the
  *     GPU (other streams, other contexts on the same device) race and give
  *     wrong results.  Calls on one stream are ordered and safe.  Each call

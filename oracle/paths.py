@@ -10,9 +10,12 @@ the scheme below is the one the GPU engine implements, restated plainly:
   "Parallel Random Numbers: As Easy as 1, 2, 3" (SC'11), from its published
   definition: 10 rounds, multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key
   increments 0x9E3779B9 / 0xBB67AE85, key bumped between rounds.
-* normal number m of a path (m = 4 j + i: bridge node j owns Philox block j,
-  underlying i < d <= 4 takes its word i) comes from Philox counter (m >> 2,
-  path_lo, path_hi, stream), key (seed_lo, seed_hi), output word m & 3.
+* normal number m of a path comes from Philox counter (m >> 2, path_lo,
+  path_hi, stream), key (seed_lo, seed_hi), output word m & 3.  Bridge node
+  j takes the d normals m = d k_j + i (underlying i < d), where k_j is the
+  node's rank in the order a date-ordered walk of the bridge computes the
+  nodes (``generation_order``): the normals are used in counter order, four
+  per Philox block, with none left over.
 * uniform u = ((x >> 8) + 0.5) * 2^-24 for a 32-bit output x.
 * Box-Muller on the word pairs (0,1) and (2,3): with u_a the even word and
   u_b the odd word, r = sqrt(-2 ln u_a); the even word's normal is
@@ -142,6 +145,30 @@ def bridge_schedule(tau: Sequence[float]) -> List[BridgeNode]:
     return nodes
 
 
+def generation_order(nodes: List[BridgeNode]) -> np.ndarray:
+    """Rank of each node in the order a walk that produces the dates in
+    increasing order computes them.  To produce date t from the last
+    produced date t - 1, the walk needs W at the nearest later date already
+    computed, and bisects towards t: it computes every node whose bisection
+    interval starts at t - 1, the widest interval (largest midpoint) first.
+    The root (date n) is computed first, with the nodes of intervals
+    starting at 0.  So the rank orders nodes by (left end, -date)."""
+    keys = [(nd.l, -nd.m) for nd in nodes]
+    order = sorted(range(len(nodes)), key=lambda j: keys[j])
+    rank = np.empty(len(nodes), dtype=np.int64)
+    rank[np.asarray(order, dtype=np.int64)] = np.arange(len(nodes))
+    return rank
+
+
+def node_normals(nodes: List[BridgeNode], d: int, seed: int, stream: int,
+                 paths: np.ndarray) -> np.ndarray:
+    """z[p, j, i]: normal of underlying i at bridge node j, i.e. normal
+    number d k_j + i of the path (k = ``generation_order``)."""
+    n = len(nodes)
+    z = normals(seed, stream, paths, n * d).reshape(len(paths), n, d)     # [p, k, i]
+    return z[:, generation_order(nodes), :]
+
+
 def bridge_apply(nodes: List[BridgeNode], z: np.ndarray, n: int) -> np.ndarray:
     """W[..., o] for o = 0..n from normals z[..., j] (one per node)."""
     W = np.zeros(z.shape[:-1] + (n + 1,), dtype=np.float64)
@@ -205,20 +232,13 @@ class Market:
         return math.exp(-self.r * self.hist_days[k - 1] / 365.0)
 
 
-def normal_stride(d: int) -> int:
-    """Normals reserved per bridge node (m = j * stride + i): one Philox
-    block of 4 words per node, whatever d (<= 4)."""
-    return 4
-
-
 def simulate(mk: Market, seed: int, stream: int, paths: np.ndarray) -> np.ndarray:
     """S[p, i, o] for the paths ``paths`` (global indices), o = 0..n."""
     n, d = mk.n, mk.d
     paths = np.asarray(paths, dtype=np.uint64)
     tau = mk.tau()
     nodes = bridge_schedule(tau)
-    s = normal_stride(d)
-    z = normals(seed, stream, paths, n * s).reshape(len(paths), n, s)[:, :, :d]   # [p, j, i]
+    z = node_normals(nodes, d, seed, stream, paths)                     # [p, j, i]
     W = bridge_apply(nodes, np.moveaxis(z, 2, 1), n)                     # [p, i, o]
     L = mk.cholesky()
     X = np.einsum("ik,pko->pio", L, W)

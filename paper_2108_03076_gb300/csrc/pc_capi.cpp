@@ -156,14 +156,15 @@ pc_status window_for(const pc_model *m, const pc_contract *k, int32_t &win) {
 }
 
 // Block size (128, 64 or 32 threads) that keeps the most warps resident per
-// SM given the program's shared-memory footprint; 0 if none fits.
-int pick_block(const Program &p, int words, int max_smem, int d, size_t &smem) {
+// SM given the program's shared-memory footprint; 0 if none fits.  Without
+// `memoise` the occupancy queries store nothing (no host allocation).
+int pick_block(const Program &p, int words, int max_smem, int d, size_t &smem, bool memoise = true) {
   int best = 0, best_warps = 0;
   size_t best_smem = 0;
   for (int b = kBlock; b >= 32; b /= 2) {
     const size_t sm = price_smem_bytes(p.code.size(), pool_padded(p), words, b);
     if (sm + kStaticSmemReserve > size_t(max_smem)) continue;
-    const int warps = price_blocks_per_sm(d, b, sm, false) * (b / 32);
+    const int warps = price_blocks_per_sm(d, b, sm, false, memoise) * (b / 32);
     if (warps > best_warps) {
       best = b;
       best_warps = warps;
@@ -226,6 +227,7 @@ pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uin
   a.path_offset = offset;
   a.key0 = uint32_t(seed);
   a.key1 = uint32_t(seed >> 32);
+  philox_round_keys(seed, a.rk);
   a.stream = stream;
   a.n_tiles = n_tiles;
   a.status = reinterpret_cast<int32_t *>(c->d_res + 4);
@@ -375,70 +377,6 @@ pc_status check_status(pc_ctx *c, int32_t status) {
   return fail(PC_EDEVICE, "kernel raised its status word (" + std::to_string(status) + ")");
 }
 
-// The time analysis of analyse_program, written without heap use for
-// pc_price_noalloc: every model and payoff ordinal within the grid, and the
-// largest lookback below the frontier of generated dates.
-struct NoAllocAnalysis {
-  const XInsn *C = nullptr;
-  int64_t t_now = 0, n_dates = 0, n_hist = 0;
-  int64_t frontier = 0, lookback = 0, steps = 0;
-  pc_status st = PC_OK;
-  const char *why = "";
-
-  void run(size_t a, size_t b, int64_t t0) {
-    for (size_t pc = a; pc < b && st == PC_OK;) {
-      if (++steps > (int64_t(1) << 26)) {
-        st = PC_ELIMIT;
-        why = "program too long to analyse (loop trip counts)";
-        return;
-      }
-      const XInsn &I = C[pc];
-      const uint32_t op = I.opa & 0xffu;
-      if (op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_PAYOFF ||
-          op == X_LRED || op == X_LANY) {
-        const int64_t o = int64_t(int32_t(I.b)) + t0 - t_now;
-        if (o < -n_hist || o > n_dates) {
-          st = PC_ERANGE;
-          why = "a model or payoff time is outside the model's grid";
-          return;
-        }
-        if (op != X_PAYOFF && o > 0) {
-          if (o > frontier) frontier = o;
-          else if (frontier - o > lookback) lookback = frontier - o;
-        }
-        ++pc;
-      } else if (op == X_LOOPANY) {
-        const int64_t n = I.b;
-        const size_t end = I.e;
-        for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(pc + 1, pc + 2, t0 + k);
-        run(pc + 2, end - 1, t0 + n);
-        pc = end;
-      } else if (op == X_LOOP) {
-        const int64_t n = I.b;
-        const size_t test = I.c;
-        if ((C[test].opa & 0xffu) == X_LSTEPK) {
-          const size_t end = C[test].e;
-          for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(pc + 1, test, t0 + k);
-          run(test + 1, end - 1, t0 + n);
-          pc = end;
-          continue;
-        }
-        const size_t next = C[test].c, end = C[next].e;
-        for (int64_t k = 0; k <= n && st == PC_OK; ++k) {
-          run(pc + 1, test, t0 + k);
-          run(test + 1, next - 1, t0 + k);
-        }
-        run(next + 1, end - 1, t0 + n);
-        pc = end;
-      } else if (op == X_END) {
-        return;
-      } else {
-        ++pc;
-      }
-    }
-  }
-};
-
 }  // namespace pc
 
 extern "C" {
@@ -453,29 +391,44 @@ pc_status pc_price_noalloc(const pc_model *m, const pc_contract *k, uint64_t n_p
   const ModelHost &H = m->H;
   if (max_label(k->prog) >= H.d)
     return fail(PC_ERANGE, "program observes a label the model does not have");
-  NoAllocAnalysis an;
-  an.C = k->prog.code.data();
-  an.t_now = H.t_now;
-  an.n_dates = H.n;
-  an.n_hist = H.n_hist;
-  an.run(0, k->prog.code.size(), 0);
-  if (an.st != PC_OK) return fail(an.st, an.why);
-  int32_t win = 1;
-  while (win < an.lookback + 1) win <<= 1;
-  if (win > PC_MAX_WINDOW) return fail(PC_ERANGE, "program looks back further than PC_MAX_WINDOW dates");
   pc_ctx *c = m->ctx;
+  CU(cudaSetDevice(c->device), "cudaSetDevice");
+  // the window: from the contract's cache when an allocating call resolved
+  // it for this model already (a lookup, no insertion), else by the same
+  // analysis without storing it
+  int32_t win = 0;
+  {
+    auto *kc = const_cast<pc_contract *>(k);
+    std::lock_guard<std::mutex> g(kc->mu);
+    const auto it = kc->win_cache.find(std::make_pair(m->id, uint64_t(0)));
+    if (it != kc->win_cache.end()) {
+      win = it->second;
+    } else {
+      const char *why = "";
+      auto on_fail = [&](pc_status st, int64_t, int64_t) {
+        why = st == PC_ELIMIT ? "program too long to analyse (loop trip counts)"
+                              : "a model or payoff time is outside the model's grid";
+      };
+      TimeWalk<decltype(on_fail)> walk{k->prog.code.data(), H.t_now, H.n, H.n_hist, on_fail};
+      walk.run(0, k->prog.code.size(), 0);
+      if (walk.st != PC_OK) return fail(walk.st, why);
+      win = walk.window();
+    }
+  }
+  if (win > PC_MAX_WINDOW)
+    return fail(PC_ERANGE, "program looks back further than PC_MAX_WINDOW dates; pc_price_noalloc keeps "
+                           "the window of dates in shared memory only");
   const Layout lay = make_layout(k->prog, H, win);
   size_t smem = 0;
-  const int block = pick_block(k->prog, lay.words, c->max_smem, H.d, smem);
+  const int block = pick_block(k->prog, lay.words, c->max_smem, H.d, smem, false);
   if (!block) return fail(PC_ELIMIT, "program + per-path state exceed the device's shared memory per block");
-  CU(cudaSetDevice(c->device), "cudaSetDevice");
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
   CU(noalloc_scratch(&scratch, &scratch_bytes), "scratch lookup");
   const uint64_t n_tiles = (n_paths + kTilePaths - 1) / kTilePaths;
   if (kNoAllocCounterBytes + n_tiles * 2 * sizeof(double) > scratch_bytes)
     return fail(PC_ELIMIT, "request exceeds the fixed scratch array");
-  const int bpsm = price_blocks_per_sm(H.d, block, smem, false);
+  const int bpsm = price_blocks_per_sm(H.d, block, smem, false, false);
   if (bpsm < 1) return fail(PC_ELIMIT, "kernel cannot be resident with this shared-memory footprint");
   PriceArgs a{};
   a.prog = k->d_code;
@@ -487,6 +440,7 @@ pc_status pc_price_noalloc(const pc_model *m, const pc_contract *k, uint64_t n_p
   a.path_offset = path_offset;
   a.key0 = uint32_t(seed);
   a.key1 = uint32_t(seed >> 32);
+  philox_round_keys(seed, a.rk);
   a.stream = stream;
   a.n_tiles = n_tiles;
   a.width = 2;
@@ -556,6 +510,14 @@ pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_gout, PC_MAX_UNDERLYINGS * 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_control, kControlBytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_control, 0, kControlBytes, c->stream);
+  if (e == cudaSuccess) {
+    // pc_price_noalloc's fixed scratch array: looking its address up here
+    // loads the kernels' module on this device, which reserves the array,
+    // when the context is created rather than inside a pc_price_noalloc call
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    e = noalloc_scratch(&scratch, &scratch_bytes);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     if (c->d_control) cudaFree(c->d_control);
@@ -637,6 +599,8 @@ pc_status pc_model_create(pc_ctx *c, const pc_model_desc *desc, pc_model **out) 
       delete m;
       return u;
     }
+    for (size_t i = 0; i < H.B.size() && i < 16; ++i) D.Bv[i] = H.B[i];
+    for (int i = 0; i < H.d; ++i) D.S0v[i] = H.sval[size_t(H.n_hist) * H.d + i];
     D.d = H.d;
     D.n = H.n;
     D.n_hist = H.n_hist;
@@ -664,10 +628,10 @@ pc_status pc_model_query(const pc_model *m, pc_model_info *info) {
   info->t_now = H.t_now;
   info->bridge_levels = H.n_levels;
   info->bridge_stack = H.bstack;
-  // one Philox block per bridge node; d <= 2 uses one Box-Muller pair of it
-  const int32_t blocks = int32_t(H.ops.size());
+  // the n d normals of a path in counter order: four per Philox block
+  const int32_t blocks = int32_t((int64_t(H.ops.size()) * H.d + 3) / 4);
   info->philox_blocks = blocks;
-  info->box_muller_pairs = (H.d <= 2 ? 1 : 2) * blocks;
+  info->box_muller_pairs = 2 * blocks;
   return PC_OK;
 }
 

@@ -14,7 +14,7 @@ namespace {
 
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(kBlock) cv_kernel(const PriceArgs a, const CvArgs c) {
+__global__ void __launch_bounds__(kBlock) cv_kernel(const __grid_constant__ PriceArgs a, const CvArgs c) {
   cv_tiles<D, MODE>(a, c, [&](const uint4 *P, const float *pool, float2 *R, const Rng2 &g, bool live0,
                               bool live1, const float (&Bm)[D * D], const float (&S0)[D], int *frontier) {
     return eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0, frontier);

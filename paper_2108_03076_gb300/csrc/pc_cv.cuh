@@ -182,15 +182,14 @@ __device__ __forceinline__ void cv_tiles(const PriceArgs &a, const CvArgs &c, EV
   __syncthreads();
   const float *pool = reinterpret_cast<const float *>(smem + a.n_insn * 4);
   float2 *R = reinterpret_cast<float2 *>(smem + prog_words) + threadIdx.x;
-  float Bm[D * D], S0[D];
-  load_model_regs<D>(a.m, Bm, S0);
+  const float(&Bm)[D * D] = *reinterpret_cast<const float(*)[D * D]>(a.m.Bv);
+  const float(&S0)[D] = *reinterpret_cast<const float(*)[D]>(a.m.S0v);
   const int lane = threadIdx.x & 31;
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
   const Layout &lay = a.lay;
   Rng2 g;
   g.stream = a.stream;
-  g.k0 = a.key0;
-  g.k1 = a.key1;
+  g.rk = a.rk;
   for (;;) {
     unsigned long long tile = 0;
     if (lane == 0) tile = atomicAdd(ctr, 1ull);

@@ -1,9 +1,9 @@
 // pc_device.cuh -- device building blocks shared by the pricing kernel
 // (pc_kernels.cu) and the pathwise-sensitivity kernel (pc_greeks.cu):
 // Philox4x32-10 (Salmon et al., SC'11), 24-bit uniforms, Box-Muller, the
-// date-ordered Brownian bridge (one Philox block per node), correlated GBM,
-// the fused multi-asset reads, and the deterministic reduction (float-pair
-// tile sums, FP64 chunk sums).
+// date-ordered Brownian bridge (normals in the order the walk uses them),
+// correlated GBM, the fused multi-asset reads, and the deterministic
+// reduction (float-pair tile sums, FP64 chunk sums).
 //
 // Per-thread state lives in shared memory as word-interleaved slots: slot s
 // of thread t is at region[s * blockDim.x + t] (float2: two paths per lane),
@@ -45,6 +45,29 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
+// Packed FP32 pairs (f32x2): one instruction for both paths of a lane; each
+// half is rounded as the scalar operation rounds it, so results are those
+// of two scalar operations.
+__device__ __forceinline__ float2 fma_x2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul_x2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
 // Philox4x32-10: ten rounds of two 32x32->64 multiplies, the key bumped by
 // the Weyl constants between rounds.
 __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
@@ -61,15 +84,53 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
-// Box-Muller on one word pair: u_a from the even word, u_b from the odd
-// word; even normal r cos(2 pi u_b), odd normal r sin(2 pi u_b).  The angle
-// is reduced to 2 pi u_b - pi in (-pi, pi), where cos and sin change sign.
-__device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float &z0, float &z1) {
-  const float ua = fmaf(__uint2float_rn(xa >> 8), 0x1p-24f, 0x1p-25f);
-  const float r = sqrt_approx(-2.0f * logf(ua));
-  const float th = fmaf(__uint2float_rn(xb >> 8), kThetaScale, kThetaOffset);
-  z0 = -r * cos_approx(th);
-  z1 = -r * sin_approx(th);
+// The same with the round keys precomputed (rk[2r], rk[2r + 1]: PriceArgs):
+// no key arithmetic, and in a kernel parameter the keys come from the
+// constant bank.
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t *rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// q = -2 ln u for the uniform u = (k + 1/2) 2^-24 of a 24-bit integer k
+// (given as the float kf, exact).  Away from u = 1: -2 ln 2 lg2.approx(u),
+// whose absolute error (about 7e-8 over (0, 1)) is small beside q.  Near 1,
+// where q is tiny and both that error and the rounding of u to a float
+// would dominate, the series 2v + v^2 + (2/3) v^3 of q = -2 ln(1 - v) in
+// v = 1 - u, which is exact in float for u > 1/2 (an odd multiple of 2^-25
+// below 2^-1); for v < 2^-8 the terms left out are below 2^-26 of q.
+__device__ __forceinline__ float neg2log_u24(float kf) {
+  const float u = fmaf(kf, 0x1p-24f, 0x1p-25f);
+  const float v = __fadd_rn(fmaf(kf, -0x1p-24f, 1.0f), -0x1p-25f);
+  const float ql = -1.3862943611198906f * lg2_approx(u);
+  const float qs = v * fmaf(v, fmaf(v, 0.6666666666666666f, 1.0f), 2.0f);
+  return v < 0x1p-8f ? qs : ql;
+}
+
+// Box-Muller on one word pair of each of the lane's two paths: u_a from the
+// even word, u_b from the odd word (path 0 in .x, path 1 in .y); even normal
+// r cos(2 pi u_b), odd normal r sin(2 pi u_b) with r = sqrt(-2 ln u_a).  The
+// angle is reduced to 2 pi u_b - pi in (-pi, pi), where cos and sin change
+// sign.
+__device__ __forceinline__ void box_muller2(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1,
+                                            float2 &ze, float2 &zo) {
+  const float2 nr = make_float2(-sqrt_approx(neg2log_u24(__uint2float_rn(a0 >> 8))),
+                                -sqrt_approx(neg2log_u24(__uint2float_rn(a1 >> 8))));
+  const float th0 = fmaf(__uint2float_rn(b0 >> 8), kThetaScale, kThetaOffset);
+  const float th1 = fmaf(__uint2float_rn(b1 >> 8), kThetaScale, kThetaOffset);
+  ze = mul_x2(nr, make_float2(cos_approx(th0), cos_approx(th1)));
+  zo = mul_x2(nr, make_float2(sin_approx(th0), sin_approx(th1)));
 }
 
 // Two paths per lane: every value of the stack machine is a float2 (.x for
@@ -78,16 +139,16 @@ __device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float &z0, 
 // chains (Philox rounds, Box-Muller, bridge) overlap in the pipeline.
 struct Rng2 {
   uint32_t plo[2], phi[2];
-  uint32_t stream, k0, k1;
+  uint32_t stream;
+  const uint32_t *rk;  // round keys (PriceArgs::rk)
 };
 
-__device__ __forceinline__ void block_normals2(uint32_t b, const Rng2 &g, float2 *e) {
-  const uint4 x0 = philox(make_uint4(b, g.plo[0], g.phi[0], g.stream), g.k0, g.k1);
-  const uint4 x1 = philox(make_uint4(b, g.plo[1], g.phi[1], g.stream), g.k0, g.k1);
-  box_muller(x0.x, x0.y, e[0].x, e[1].x);
-  box_muller(x0.z, x0.w, e[2].x, e[3].x);
-  box_muller(x1.x, x1.y, e[0].y, e[1].y);
-  box_muller(x1.z, x1.w, e[2].y, e[3].y);
+// The four normals of Philox block b of both paths.
+__device__ __forceinline__ void block_normals2(uint32_t b, const Rng2 &g, float2 (&e)[4]) {
+  const uint4 x0 = philox_rk(make_uint4(b, g.plo[0], g.phi[0], g.stream), g.rk);
+  const uint4 x1 = philox_rk(make_uint4(b, g.plo[1], g.phi[1], g.stream), g.rk);
+  box_muller2(x0.x, x0.y, x1.x, x1.y, e[0], e[1]);
+  box_muller2(x0.z, x0.w, x1.z, x1.w, e[2], e[3]);
 }
 
 // Slot s of this thread in the word-interleaved per-thread region (the
@@ -115,84 +176,135 @@ __device__ __forceinline__ void win_store(float2 *R, const Layout &lay, int w, f
 template <int D>
 struct PathState {
   float2 w[D];                  // W at the last produced date
+  float2 zc[3];                 // words 1..3 of the last Philox block (d < 4)
   int f;                        // last produced ordinal (frontier), warp-uniform
   int bsp;                      // bridge stack size, warp-uniform
+  int k;                        // ops run so far (the next op's number), warp-uniform
 };
 
-// The normals of bridge node j for both paths: words 0 .. D-1 of Philox
-// block j (see BridgeOp).  D <= 2 needs only the first Box-Muller pair.
 template <int D>
-__device__ __forceinline__ void node_normals(const BridgeOp &op, const Rng2 &g, float2 (&z)[D]) {
-  if constexpr (D <= 2) {
-    const uint4 x0 = philox(make_uint4(op.j, g.plo[0], g.phi[0], g.stream), g.k0, g.k1);
-    const uint4 x1 = philox(make_uint4(op.j, g.plo[1], g.phi[1], g.stream), g.k0, g.k1);
-    float2 e[2];
-    box_muller(x0.x, x0.y, e[0].x, e[1].x);
-    box_muller(x1.x, x1.y, e[0].y, e[1].y);
+__device__ __forceinline__ void path_state_init(PathState<D> &ps) {
 #pragma unroll
-    for (int i = 0; i < D; ++i) z[i] = e[i];
-  } else {
+  for (int i = 0; i < D; ++i) ps.w[i] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) ps.zc[i] = make_float2(0.f, 0.f);
+  ps.f = 0;
+  ps.bsp = 0;
+  ps.k = 0;
+}
+
+// The normals of op k for both paths: normals D k .. D k + D - 1 of the
+// path (Philox block m >> 2, word m & 3).  Ops run in order, so the block
+// holding normal D k is either new or the last block computed, whose words
+// 1..3 the state keeps (zc); a new block is computed at most once per op.
+template <int D>
+__device__ __forceinline__ void node_normals(uint32_t k, const Rng2 &g, float2 (&zc)[3],
+                                             float2 (&z)[D]) {
+  if constexpr (D == 4) {
     float2 e[4];
-    block_normals2(op.j, g, e);
+    block_normals2(k, g, e);
 #pragma unroll
-    for (int i = 0; i < D; ++i) z[i] = e[i];
+    for (int i = 0; i < 4; ++i) z[i] = e[i];
+  } else if constexpr (D == 2) {
+    if (k & 1) {  // words 2, 3 of block k / 2
+      z[0] = zc[1];
+      z[1] = zc[2];
+    } else {
+      float2 e[4];
+      block_normals2(k >> 1, g, e);
+      z[0] = e[0];
+      z[1] = e[1];
+      zc[1] = e[2];
+      zc[2] = e[3];
+    }
+  } else if constexpr (D == 1) {
+    const uint32_t ph = k & 3;
+    if (ph == 0) {
+      float2 e[4];
+      block_normals2(k >> 2, g, e);
+      z[0] = e[0];
+      zc[0] = e[1];
+      zc[1] = e[2];
+      zc[2] = e[3];
+    } else {
+      z[0] = ph == 1 ? zc[0] : ph == 2 ? zc[1] : zc[2];
+    }
+  } else {  // D == 3: the first normal is word ph = 3k & 3 of its block
+    const uint32_t ph = (3 * k) & 3;
+    if (ph == 1) {  // words 1..3 of the last block
+      z[0] = zc[0];
+      z[1] = zc[1];
+      z[2] = zc[2];
+    } else {
+      float2 e[4];
+      block_normals2((3 * k + 2) >> 2, g, e);
+      if (ph == 0) {
+        z[0] = e[0];
+        z[1] = e[1];
+        z[2] = e[2];
+      } else if (ph == 2) {
+        z[0] = zc[1];
+        z[1] = zc[2];
+        z[2] = e[0];
+      } else {
+        z[0] = zc[2];
+        z[1] = e[0];
+        z[2] = e[1];
+      }
+      zc[0] = e[1];
+      zc[1] = e[2];
+      zc[2] = e[3];
+    }
   }
 }
 
-__device__ __forceinline__ BridgeOp load_op(const BridgeOp *p) {
-  const uint4 *q = reinterpret_cast<const uint4 *>(p);
-  const uint4 a = __ldg(q), b = __ldg(q + 1);
-  BridgeOp op;
-  op.wl = __uint_as_float(a.x);
-  op.wr = __uint_as_float(a.y);
-  op.sd = __uint_as_float(a.z);
-  op.j = a.w;
-  op.pad0 = 0;
-  op.flags = uint16_t(b.x >> 16);
-  op.m = uint16_t(b.y & 0xffffu);
-  op.pad1 = 0;
-  op.pad2 = 0;
-  op.level = b.w;
-  return op;
-}
-
-__device__ __forceinline__ float2 ffma2(float a, float2 x, float2 y) {
-  return make_float2(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y));
+// A bridge op's weights as packed pairs and its flags (two 16-byte loads
+// through the read-only path: the address is the same in every lane).
+struct OpRegs {
+  float2 wl, wr, sd;
+  uint32_t flags;
+};
+__device__ __forceinline__ OpRegs load_op(const BridgeOp *p) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+  const float4 a = __ldg(q), b = __ldg(q + 1);
+  OpRegs o;
+  o.wl = make_float2(a.x, a.y);
+  o.wr = make_float2(a.z, a.w);
+  o.sd = make_float2(b.x, b.y);
+  o.flags = __float_as_uint(b.w) & 0xffffu;
+  return o;
 }
 
 // Produce date t (= frontier + 1) for both paths: bridge ops of t, then GBM
 // into the window slot of t.  With XW the correlated Brownian values
 // X = L W of the date are also kept (window at lay.off_xwin), which the
-// pathwise sensitivities need.
+// pathwise sensitivities need.  The bridge, correlation and GBM products run
+// on packed pairs (the two paths of the lane).
 template <int D, bool XW = false, bool GW = false>
 __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev &m,
                                          const Layout &lay, const Rng2 &g, float2 *R,
                                          const float (&Bm)[D * D], const float (&S0)[D],
                                          const float *Lm = nullptr) {
-  const int k0 = __ldg(m.date_ops + t), k1 = __ldg(m.date_ops + t + 1);
-  if (k0 == k1) {
+  const int k1 = __ldg(m.date_ops + t + 1);  // ops of date t: [ps.k, k1)
+  if (ps.k == k1) {
     --ps.bsp;
 #pragma unroll
     for (int i = 0; i < D; ++i) ps.w[i] = SL(lay.off_bstack + ps.bsp * D + i);
   } else {
-    for (int k = k0; k < k1; ++k) {
-      const BridgeOp op = load_op(m.ops + k);
+    for (; ps.k < k1; ++ps.k) {
+      const OpRegs op = load_op(m.ops + ps.k);
       float2 z[D];
-      node_normals<D>(op, g, z);
+      node_normals<D>(uint32_t(ps.k), g, ps.zc, z);
       float2 nw[D];
       if (op.flags & BR_ROOT) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) nw[i] = make_float2(op.sd * z[i].x, op.sd * z[i].y);
+        for (int i = 0; i < D; ++i) nw[i] = mul_x2(op.sd, z[i]);
       } else {
         const int top = lay.off_bstack + (ps.bsp - 1) * D;
 #pragma unroll
-        for (int i = 0; i < D; ++i) {
-          const float2 wt = SL(top + i);
-          nw[i] = ffma2(op.wl, ps.w[i],
-                        ffma2(op.wr, wt, make_float2(op.sd * z[i].x, op.sd * z[i].y)));
-        }
+        for (int i = 0; i < D; ++i) nw[i] = fma_x2(op.wl, ps.w[i], fma_x2(op.wr, SL(top + i), mul_x2(op.sd, z[i])));
       }
-      if (k + 1 < k1) {
+      if (ps.k + 1 < k1) {
 #pragma unroll
         for (int i = 0; i < D; ++i) SL(lay.off_bstack + ps.bsp * D + i) = nw[i];
         ++ps.bsp;
@@ -205,19 +317,19 @@ __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev
   const int ws = (t & (lay.win - 1)) * D;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    const float a = __ldg(m.A + t * D + i);
-    float2 x = make_float2(a, a);
+    float2 x = __ldg(m.A + t * D + i);
 #pragma unroll
-    for (int k = 0; k <= i; ++k) x = ffma2(Bm[i * D + k], ps.w[k], x);
+    for (int k = 0; k <= i; ++k)
+      x = make_float2(fmaf(Bm[i * D + k], ps.w[k].x, x.x), fmaf(Bm[i * D + k], ps.w[k].y, x.y));
     win_store<GW>(R, lay, ws + i, make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y)));
   }
   if constexpr (XW) {
     const int xs = lay.off_xwin + (t & (lay.win - 1)) * D;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      float2 x = make_float2(0.f, 0.f);
+      float2 x = mul_x2(dup2(Lm[i * D]), ps.w[0]);
 #pragma unroll
-      for (int k = 0; k <= i; ++k) x = ffma2(Lm[i * D + k], ps.w[k], x);
+      for (int k = 1; k <= i; ++k) x = fma_x2(dup2(Lm[i * D + k]), ps.w[k], x);
       SL(xs + i) = x;
     }
   }
@@ -237,9 +349,9 @@ template <int D>
 __device__ __forceinline__ void load_model_regs(const ModelDev &m, float (&Bm)[D * D],
                                                 float (&S0)[D]) {
 #pragma unroll
-  for (int i = 0; i < D * D; ++i) Bm[i] = __ldg(m.B + i);
+  for (int i = 0; i < D * D; ++i) Bm[i] = m.Bv[i];
 #pragma unroll
-  for (int i = 0; i < D; ++i) S0[i] = __ldg(m.sval + m.n_hist * D + i);
+  for (int i = 0; i < D; ++i) S0[i] = m.S0v[i];
 }
 
 __device__ __forceinline__ int bits(float v) { return __float_as_int(v); }

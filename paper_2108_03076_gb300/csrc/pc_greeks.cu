@@ -10,7 +10,7 @@ namespace pc {
 namespace {
 
 template <int D, bool WRITE>
-__global__ void __launch_bounds__(kBlock) greeks_kernel(const PriceArgs a) {
+__global__ void __launch_bounds__(kBlock) greeks_kernel(const __grid_constant__ PriceArgs a) {
   greeks_tiles<D, WRITE>(a, [&](const uint4 *P, const float *pool, float2 *R, const Rng2 &g, bool live0,
                                 bool live1, const float (&Bm)[D * D], const float (&S0)[D],
                                 const float (&Lm)[D * D], int gl, float sig_g) {

@@ -155,8 +155,9 @@ __device__ __forceinline__ void greeks_tiles(const PriceArgs &a, EVAL eval) {
   __syncthreads();
   const float *pool = reinterpret_cast<const float *>(smem + a.n_insn * 4);
   float2 *R = reinterpret_cast<float2 *>(smem + prog_words) + threadIdx.x;
-  float Bm[D * D], S0[D], Lm[D * D];
-  load_model_regs<D>(a.m, Bm, S0);
+  const float(&Bm)[D * D] = *reinterpret_cast<const float(*)[D * D]>(a.m.Bv);
+  const float(&S0)[D] = *reinterpret_cast<const float(*)[D]>(a.m.S0v);
+  float Lm[D * D];
 #pragma unroll
   for (int i = 0; i < D * D; ++i) Lm[i] = __ldg(a.m.L + i);
   const int gl = a.greek_label;
@@ -165,8 +166,7 @@ __device__ __forceinline__ void greeks_tiles(const PriceArgs &a, EVAL eval) {
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
   Rng2 g;
   g.stream = a.stream;
-  g.k0 = a.key0;
-  g.k1 = a.key1;
+  g.rk = a.rk;
   for (;;) {
     unsigned long long tile = 0;
     if (lane == 0) tile = atomicAdd(ctr, 1ull);

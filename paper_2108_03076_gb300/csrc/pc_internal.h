@@ -22,7 +22,7 @@ cudaError_t launch_debug_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, u
 cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_paths,
                                uint64_t offset, uint32_t k0, uint32_t k1, uint32_t stream,
                                float *out, cudaStream_t s);
-int price_blocks_per_sm(int d, int block, size_t smem_bytes, bool hbm_window);
+int price_blocks_per_sm(int d, int block, size_t smem_bytes, bool hbm_window, bool memoise = true);
 
 // Portfolio pricing (one persistent launch per group of contracts with the
 // same underlying count and a similar per-path footprint).  A work unit is a
@@ -64,8 +64,10 @@ cudaError_t launch_batch(const BatchArgs &b, int d, int grid, int block, size_t 
                          cudaStream_t s);
 // Occupancy results keyed by (device, kernel variant, block, shared memory):
 // the query runs once per key (it sets the kernel's shared-memory limit and
-// costs microseconds), later calls return the stored count.
-int occupancy_memo(uint64_t variant, int block, size_t smem, int (*query)(uint64_t, int, size_t));
+// costs microseconds), later calls return the stored count.  With `store`
+// false a missing key is queried and not stored (no host allocation).
+int occupancy_memo(uint64_t variant, int block, size_t smem, int (*query)(uint64_t, int, size_t),
+                   bool store = true);
 
 // Device address and size of the fixed scratch array used by
 // pc_price_noalloc on the current device (looked up once per device).
@@ -90,10 +92,89 @@ pc_status compile_program(const uint32_t *words, size_t n_words, const double *c
                           int32_t p1, int32_t p2, bool bind_parties, Program &out,
                           std::string &err);
 
-// Static analysis of a program against a model's time layout: every model
-// and payoff time within [-n_hist, n] as ordinals, and the largest lookback
-// below the generated frontier.  `win` receives the window size needed
-// (power of two).
+// Abstract run of the executable form with every branch taken, as the warp
+// would run it if some lane took each branch at every loop iteration: gives
+// every ordinal the program can touch and the largest lookback below the
+// frontier of generated dates.  Skipping branches only lowers the frontier
+// at any later point, so this bound holds for every actual run.  No heap
+// use: pc_price_noalloc runs it too.  On the first failure it stops and
+// calls on_fail(status, time, ordinal) (time and ordinal of an out-of-grid
+// read; 0 for PC_ELIMIT, a program whose loop trip counts exceed 2^26
+// analysis steps).
+template <typename OnFail>
+struct TimeWalk {
+  const XInsn *C;
+  int64_t t_now, n_dates, n_hist;
+  OnFail on_fail;
+  int64_t frontier = 0, lookback = 0, steps = 0;
+  pc_status st = PC_OK;
+
+  void run(size_t a, size_t b, int64_t t0) {
+    for (size_t pc = a; pc < b && st == PC_OK;) {
+      if (++steps > (int64_t(1) << 26)) {
+        st = PC_ELIMIT;
+        on_fail(st, 0, 0);
+        return;
+      }
+      const XInsn &I = C[pc];
+      const uint32_t op = I.opa & 0xffu;
+      if (op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_PAYOFF ||
+          op == X_LRED || op == X_LANY) {
+        const int64_t o = int64_t(int32_t(I.b)) + t0 - t_now;
+        if (o < -n_hist || o > n_dates) {
+          st = PC_ERANGE;
+          on_fail(st, int64_t(int32_t(I.b)) + t0, o);
+          return;
+        }
+        if (op != X_PAYOFF && o > 0) {
+          if (o > frontier) frontier = o;
+          else if (frontier - o > lookback) lookback = frontier - o;
+        }
+        ++pc;
+      } else if (op == X_LOOPANY) {
+        const int64_t n = I.b;
+        const size_t end = I.e;  // pc after LEND
+        for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(pc + 1, pc + 2, t0 + k);
+        run(pc + 2, end - 1, t0 + n);
+        pc = end;
+      } else if (op == X_LOOP) {
+        const int64_t n = I.b;
+        const size_t cond = pc + 1, test = I.c;
+        if ((C[test].opa & 0xffu) == X_LSTEPK) {
+          const size_t end = C[test].e;  // pc after LEND
+          for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(cond, test, t0 + k);
+          run(test + 1, end - 1, t0 + n);  // else-branch (before LEND)
+          pc = end;
+          continue;
+        }
+        const size_t next = C[test].c;
+        const size_t end = C[next].e;  // pc after LEND
+        for (int64_t k = 0; k <= n && st == PC_OK; ++k) {
+          run(cond, test, t0 + k);
+          run(test + 1, next - 1, t0 + k);  // then-branch (before LLATCH)
+        }
+        run(next + 1, end - 1, t0 + n);  // else-branch (before LEND)
+        pc = end;
+      } else if (op == X_END) {
+        return;
+      } else {
+        ++pc;
+      }
+    }
+  }
+
+  // the window (power of two) that holds the largest lookback
+  int32_t window() const {
+    int32_t w = 1;
+    while (w < lookback + 1) w <<= 1;
+    return w;
+  }
+};
+
+// Static analysis of a program against a model's time layout (TimeWalk):
+// every model and payoff time within [-n_hist, n] as ordinals; `win`
+// receives the window size needed (power of two, <= 2 * PC_MAX_DATES:
+// callers decide where such a window can live).
 pc_status analyse_program(const Program &p, int32_t t_now, int32_t n_dates, int32_t n_hist,
                           int32_t &win, std::string &err);
 
@@ -112,7 +193,8 @@ struct ModelHost {
   // device tables, host copies
   std::vector<int32_t> date_ops;
   std::vector<BridgeOp> ops;
-  std::vector<float> A, B, disc, sval, tau, Lf, sig;
+  std::vector<float2> A;  // drift exponents, each twice (packed pairs)
+  std::vector<float> B, disc, sval, tau, Lf, sig;
   int32_t n_levels = 0, bstack = 0;
 };
 

@@ -182,7 +182,7 @@ std::string generate_greeks(const Program &p, int d, bool write) {
   o << "}\n"
     << "}  // namespace\n"
     << "}  // namespace pc\n"
-    << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ") pc_jit_greeks(const pc::PriceArgs a) {\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ") pc_jit_greeks(const __grid_constant__ pc::PriceArgs a) {\n"
     << "  pc::greeks_tiles<pc::D, " << (write ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
     << "      float2 *R, const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
     << "      const float (&S0)[pc::D], const float (&Lm)[pc::D * pc::D], int gl, float sig_g) {\n"
@@ -266,7 +266,7 @@ std::string generate(const Program &p, int d, int kind) {
     // blocks there (-10 %; the first-order kernel is fastest uncapped)
     const bool gamma = ((kind - kJitCv) & kCvGamma) != 0;
     o << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << (gamma ? ", 5" : "")
-      << ") pc_jit_cv(const pc::PriceArgs a,\n"
+      << ") pc_jit_cv(const __grid_constant__ pc::PriceArgs a,\n"
       << "    const pc::CvArgs c) {\n"
       << "  pc::cv_tiles<pc::D, " << (kind - kJitCv) << ">(a, c, [&](const uint4 *P, const float *pool, float2 *R,\n"
       << "      const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
@@ -277,7 +277,7 @@ std::string generate(const Program &p, int d, int kind) {
   }
   // at least 7 resident 128-thread blocks (<= 72 registers): the fastest
   // measured cap (autocall unchanged, daily barrier -7 %, 5 blocks slower)
-  o << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ", 7) pc_jit_price(const pc::PriceArgs a) {\n"
+  o << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ", 7) pc_jit_price(const __grid_constant__ pc::PriceArgs a) {\n"
     << "  pc::price_tiles<pc::D, " << (kind & kJitPriceWrite ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
     << "      float2 *R, const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
     << "      const float (&S0)[pc::D]) { return pc::jit_eval(P, pool, R, a, g, live0, live1, Bm, S0); });\n"

@@ -32,7 +32,7 @@ namespace {
 // HBM (lay.gwin) instead of shared memory, for programs that look back
 // further than shared memory holds.
 template <int D, bool WRITE, bool GW = false>
-__global__ void __launch_bounds__(kBlock) price_kernel(const PriceArgs a) {
+__global__ void __launch_bounds__(kBlock) price_kernel(const __grid_constant__ PriceArgs a) {
   price_tiles<D, WRITE>(a, [&](const uint4 *P, const float *pool, float2 *R, const Rng2 &g, bool live0,
                                bool live1, const float(&Bm)[D * D], const float(&S0)[D]) {
     return eval_path<D, GW>(P, pool, R, a, g, live0, live1, Bm, S0);
@@ -76,8 +76,7 @@ __global__ void __launch_bounds__(kBlock, 5) batch_kernel(const BatchArgs b) {
     const float *pool = reinterpret_cast<const float *>(P + a.n_insn);
     load_model_regs<D>(a.m, Bm, S0);
     g.stream = a.stream;
-    g.k0 = a.key0;
-    g.k1 = a.key1;
+    g.rk = a.rk;
     for (uint32_t k = 0; k < U.n_tiles; ++k) {
       const uint64_t tile = U.tile0 + k;
       const uint64_t i0 = tile * kTilePaths + lane, i1 = i0 + 32;
@@ -115,9 +114,9 @@ __global__ void debug_philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k
 // Thread t generates paths offset + 2t and offset + 2t + 1 with the pricing
 // kernel's generator and writes every date of both.
 template <int D>
-__global__ void __launch_bounds__(kBlock) debug_paths_kernel(const ModelDev m, const Layout lay,
+__global__ void __launch_bounds__(kBlock) debug_paths_kernel(const __grid_constant__ ModelDev m, const Layout lay,
                                                              uint64_t n_paths, uint64_t offset,
-                                                             uint32_t k0, uint32_t k1,
+                                                             const __grid_constant__ RoundKeys rk,
                                                              uint32_t stream, float *out) {
   extern __shared__ __align__(16) uint32_t smem[];
   float2 *R = reinterpret_cast<float2 *>(smem) + threadIdx.x;
@@ -131,13 +130,9 @@ __global__ void __launch_bounds__(kBlock) debug_paths_kernel(const ModelDev m, c
   g.plo[1] = uint32_t(offset + i1);
   g.phi[1] = uint32_t((offset + i1) >> 32);
   g.stream = stream;
-  g.k0 = k0;
-  g.k1 = k1;
+  g.rk = rk.k;
   PathState<D> ps;
-#pragma unroll
-  for (int l = 0; l < D; ++l) ps.w[l] = make_float2(0.f, 0.f);
-  ps.f = 0;
-  ps.bsp = 0;
+  path_state_init<D>(ps);
   const size_t row = size_t(m.n) + 1;
   const bool has1 = i1 < n_paths;
   for (int l = 0; l < D; ++l) {
@@ -216,12 +211,13 @@ int price_occupancy(uint64_t v, int block, size_t smem) {
 }
 }  // namespace
 
-int price_blocks_per_sm(int d, int block, size_t smem, bool hbm_window) {
+int price_blocks_per_sm(int d, int block, size_t smem, bool hbm_window, bool memoise) {
   return occupancy_memo((uint64_t(1) << 32) | (uint64_t(hbm_window) << 8) | uint64_t(d), block, smem,
-                        price_occupancy);
+                        price_occupancy, memoise);
 }
 
-int occupancy_memo(uint64_t variant, int block, size_t smem, int (*query)(uint64_t, int, size_t)) {
+int occupancy_memo(uint64_t variant, int block, size_t smem, int (*query)(uint64_t, int, size_t),
+                   bool store) {
   static std::mutex mu;
   static std::map<std::tuple<int, uint64_t, int, size_t>, int> memo;
   int dev = 0;
@@ -233,7 +229,7 @@ int occupancy_memo(uint64_t variant, int block, size_t smem, int (*query)(uint64
     if (it != memo.end()) return it->second;
   }
   const int nb = query(variant, block, smem);
-  if (nb > 0) {
+  if (nb > 0 && store) {
     std::lock_guard<std::mutex> g(mu);
     memo[key] = nb;
   }
@@ -292,13 +288,15 @@ cudaError_t launch_debug_paths(const ModelDev &m, const Layout &lay, uint64_t n_
   while (block > 32 && size_t(lay.words) * block * 8 + 2048 > size_t(max_dynamic_smem())) block /= 2;
   const size_t smem = size_t(lay.words) * block * 8;
   const unsigned grid = unsigned((n_paths + 2 * block - 1) / (2 * block));
+  RoundKeys rk;
+  philox_round_keys(uint64_t(k0) | (uint64_t(k1) << 32), rk.k);
   if (grid == 0) return cudaSuccess;
 #define DLAUNCH(DD)                                                                 \
   do {                                                                              \
     auto k = debug_paths_kernel<DD>;                                                \
     cudaError_t e = set_smem(k, smem);                                              \
     if (e != cudaSuccess) return e;                                                 \
-    k<<<grid, block, smem, s>>>(m, lay, n_paths, offset, k0, k1, stream, out);      \
+    k<<<grid, block, smem, s>>>(m, lay, n_paths, offset, rk, stream, out);          \
     return cudaGetLastError();                                                      \
   } while (0)
   switch (m.d) {

@@ -154,14 +154,13 @@ pc_status build_model(const pc_model_desc &desc, ModelHost &M, std::string &err)
     for (int j : js) {
       BridgeOp op{};
       const Node &nd = nodes[j];
-      op.wl = float(nd.wl);
-      op.wr = float(nd.wr);
-      op.sd = float(nd.sd);
+      op.wl = op.wl_ = float(nd.wl);
+      op.wr = op.wr_ = float(nd.wr);
+      op.sd = op.sd_ = float(nd.sd);
       op.j = uint32_t(j);
-      op.level = uint32_t(nd.level);
       op.m = uint16_t(nd.m);
-      op.flags = nd.r < 0 ? BR_ROOT : 0;  // node j draws Philox block j
-      M.ops.push_back(op);
+      op.flags = nd.r < 0 ? BR_ROOT : 0;
+      M.ops.push_back(op);  // op k takes normals d k .. d k + d - 1
     }
   }
   M.date_ops[n + 1] = int(M.ops.size());
@@ -170,11 +169,12 @@ pc_status build_model(const pc_model_desc &desc, ModelHost &M, std::string &err)
 
   // Tables.
   const double log2e = 1.4426950408889634;
-  M.A.assign(size_t(n + 1) * d, 0.f);
+  M.A.assign(size_t(n + 1) * d, float2{0.f, 0.f});
   for (int o = 0; o <= n; ++o)
-    for (int i = 0; i < d; ++i)
-      M.A[size_t(o) * d + i] =
-          float(log2e * (M.r - 0.5 * M.sigma[i] * M.sigma[i]) * tau[o]);
+    for (int i = 0; i < d; ++i) {
+      const float a = float(log2e * (M.r - 0.5 * M.sigma[i] * M.sigma[i]) * tau[o]);
+      M.A[size_t(o) * d + i] = float2{a, a};
+    }
   M.B.assign(size_t(d) * d, 0.f);
   for (int i = 0; i < d; ++i)
     for (int k = 0; k < d; ++k) M.B[size_t(i) * d + k] = float(log2e * M.sigma[i] * M.L[size_t(i) * d + k]);

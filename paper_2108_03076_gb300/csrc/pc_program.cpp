@@ -574,76 +574,19 @@ pc_status compile_program(const uint32_t *words, size_t n_words, const double *c
   return PC_OK;
 }
 
-// Abstract run of the executable form with every branch taken, as the warp
-// would run it if some lane took each branch at every loop iteration: gives
-// every ordinal the program can touch and the largest lookback below the
-// frontier of generated dates.  Skipping branches only lowers the frontier
-// at any later point, so this bound holds for every actual run.
 pc_status analyse_program(const Program &p, int32_t t_now, int32_t n_dates, int32_t n_hist,
                           int32_t &win, std::string &err) {
-  const auto &C = p.code;
-  int64_t frontier = 0, lookback = 0, steps = 0;
-  const int64_t kMaxSteps = int64_t(1) << 26;
-  pc_status st = PC_OK;
-  std::function<void(size_t, size_t, int64_t)> run = [&](size_t a, size_t b, int64_t t0) {
-    for (size_t pc = a; pc < b && st == PC_OK;) {
-      if (++steps > kMaxSteps) {
-        err = "program too long to analyse (loop trip counts)";
-        st = PC_ELIMIT;
-        return;
-      }
-      const XInsn &I = C[pc];
-      const uint32_t op = I.opa & 0xffu;
-      if (op == X_MODEL || op == X_MODEL_MULK || op == X_MODEL_DIVK || op == X_PAYOFF ||
-          op == X_LRED || op == X_LANY) {
-        const int64_t o = int64_t(int32_t(I.b)) + t0 - t_now;
-        if (o < -int64_t(n_hist) || o > n_dates) {
-          err = "time " + std::to_string(int32_t(I.b) + t0) + " is outside the model's grid (ordinal " +
-                std::to_string(o) + ", grid " + std::to_string(-n_hist) + ".." + std::to_string(n_dates) + ")";
-          st = PC_ERANGE;
-          return;
-        }
-        if (op != X_PAYOFF && o > 0) {
-          if (o > frontier) frontier = o;
-          else lookback = std::max(lookback, frontier - o);
-        }
-        ++pc;
-      } else if (op == X_LOOPANY) {
-        const int64_t n = I.b;
-        const size_t end = I.e;  // pc after LEND
-        for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(pc + 1, pc + 2, t0 + k);
-        run(pc + 2, end - 1, t0 + n);
-        pc = end;
-      } else if (op == X_LOOP) {
-        const int64_t n = I.b;
-        const size_t cond = pc + 1, test = I.c;
-        if ((C[test].opa & 0xffu) == X_LSTEPK) {
-          const size_t end = C[test].e;  // pc after LEND
-          for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(cond, test, t0 + k);
-          run(test + 1, end - 1, t0 + n);  // else-branch (before LEND)
-          pc = end;
-          continue;
-        }
-        const size_t next = C[test].c;
-        const size_t end = C[next].e;  // pc after LEND
-        for (int64_t k = 0; k <= n && st == PC_OK; ++k) {
-          run(cond, test, t0 + k);
-          run(test + 1, next - 1, t0 + k);  // then-branch (before LLATCH)
-        }
-        run(next + 1, end - 1, t0 + n);    // else-branch (before LEND)
-        pc = end;
-      } else if (op == X_END) {
-        return;
-      } else {
-        ++pc;
-      }
-    }
+  auto on_fail = [&](pc_status st, int64_t t, int64_t o) {
+    if (st == PC_ELIMIT)
+      err = "program too long to analyse (loop trip counts)";
+    else
+      err = "time " + std::to_string(t) + " is outside the model's grid (ordinal " + std::to_string(o) +
+            ", grid " + std::to_string(-n_hist) + ".." + std::to_string(n_dates) + ")";
   };
-  run(0, C.size(), 0);
-  if (st != PC_OK) return st;
-  int32_t w = 1;
-  while (w < lookback + 1) w <<= 1;
-  win = w;  // <= 2 * PC_MAX_DATES: callers decide where such a window can live
+  TimeWalk<decltype(on_fail)> walk{p.code.data(), t_now, n_dates, n_hist, on_fail};
+  walk.run(0, p.code.size(), 0);
+  if (walk.st != PC_OK) return walk.st;
+  win = walk.window();
   return PC_OK;
 }
 

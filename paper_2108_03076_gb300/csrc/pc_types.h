@@ -106,24 +106,20 @@ enum { LF_K = 0, LF_T0 = 1, LF_DONE = 2, LF_RES = 3, LF_NEWLY = 4, LF_SLOTS = 5 
 // bridge node m from (W_cur, W_top) and pushes it, except the last op, whose
 // result is W_t itself; a date with no ops pops W_t from the stack.
 //
-// Normals: node j (its breadth-first number) owns Philox block j; the
-// normal of underlying i (d <= 4) is word i of that block (normal number
-// m = 4 j + i: counter (m >> 2, ...), word m & 3).  Date-ordered traversal
-// visits the nodes that would share a packed block far apart, so packing d
-// normals per node into consecutive words needs per-level block caches and
-// still evaluates 1.3-1.6 blocks per node; one block per node needs no
-// cache and no straddling, and measured faster for every d on GB300
-// (d = 1, 2: one Box-Muller pair per node).
+// Normals: the ops are numbered k = 0, 1, ... in the order the walk runs
+// them (every path runs the same sequence), and op k takes the d normals
+// m = d k + i (underlying i < d) of the path: Philox counter m >> 2, word
+// m & 3.  So the normals are used in counter order, four per Philox block,
+// none left over; a node whose normals start inside the block of the
+// previous node takes them from the registers that kept that block's later
+// words (for d < 4 at most three).
 // ---------------------------------------------------------------------------
 struct BridgeOp {
-  float wl, wr, sd;
-  uint32_t j;       // breadth-first node number = the node's Philox block
-  uint16_t pad0;
-  uint16_t flags;   // BR_* below
-  uint16_t m;       // date ordinal produced (diagnostics)
-  uint16_t pad1;
-  uint32_t pad2;
-  uint32_t level;   // bisection level (diagnostics)
+  float wl, wl_, wr, wr_;  // endpoint weights, each twice: a packed pair for the lane's two paths
+  float sd, sd_;           // conditional standard deviation, twice
+  uint32_t j;              // breadth-first node number (diagnostics)
+  uint16_t flags;          // BR_* below
+  uint16_t m;              // date ordinal produced (diagnostics)
 };
 static_assert(sizeof(BridgeOp) == 32, "BridgeOp layout: two 16-byte loads");
 
@@ -135,7 +131,7 @@ enum : uint16_t {
 struct ModelDev {
   const int32_t *date_ops;  // [n+2] op range of date t: [date_ops[t], date_ops[t+1])
   const BridgeOp *ops;      // [n]
-  const float *A;           // [(n+1)*d] log2(e)(r - sigma^2/2) tau_o (S = S0 2^(A + B W))
+  const float2 *A;          // [(n+1)*d] log2(e)(r - sigma^2/2) tau_o (S = S0 2^(A + B W)), each twice
   const float *B;           // [d*d]     log2(e) sigma_i L_ik
   const float *disc;        // [n_hist+n+1] disc of ordinal o at index o + n_hist
   const float *sval;        // [(n_hist+1)*d] value of label l at ordinal o <= 0, index (o+n_hist)*d+l
@@ -146,6 +142,10 @@ struct ModelDev {
   int32_t d, n, n_hist, t_now;
   int32_t n_levels;         // bisection levels
   int32_t bstack;           // bridge stack depth
+  // B and S0 by value: in a kernel parameter they are read from the
+  // constant bank where used, and take no registers
+  float Bv[16];             // B row-major over d x d (the first d*d entries)
+  float S0v[4];             // S0 of each underlying
 };
 
 // Per-thread shared-memory region: 32-bit words, word w of thread t at
@@ -176,6 +176,22 @@ inline size_t price_smem_bytes(size_t n_insn, size_t n_pool_padded, int words, i
   return n_insn * 16 + n_pool_padded * 4 + size_t(words) * block * 8;
 }
 
+struct RoundKeys {
+  uint32_t k[20];
+};
+
+// Philox4x32-10 round keys of a 64-bit seed: round r XORs (key0 + r W0,
+// key1 + r W1), the key bumped by the Weyl constants between rounds.
+inline void philox_round_keys(uint64_t seed, uint32_t *rk) {
+  uint32_t k0 = uint32_t(seed), k1 = uint32_t(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk[2 * r] = k0;
+    rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
 struct PriceArgs {
   const XInsn *prog;        // program followed by its constant pool
   int32_t n_insn;
@@ -184,6 +200,7 @@ struct PriceArgs {
   Layout lay;
   uint64_t n_paths, path_offset;
   uint32_t key0, key1, stream;
+  uint32_t rk[20];          // Philox round keys: (key0 + r W0, key1 + r W1) for r = 0..9
   uint64_t n_tiles;
   int32_t width;            // doubles per tile partial (2 for prices)
   uint32_t chunk_tiles;     // tiles per reduction chunk

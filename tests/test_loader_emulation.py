@@ -326,15 +326,12 @@ def test_date_ordered_bridge_matches_array_form(days, d):
     corr = np.eye(d).tolist()
     dops, ops = pc.pc_debug_bridge([1.0] * d, [0.2] * d, corr, 0.0, days)
     P = 8
-    s = opaths.normal_stride(d)
-    z = opaths.normals(99, 0, np.arange(P, dtype=np.uint64), n * s)        # [p, m]
+    z = opaths.normals(99, 0, np.arange(P, dtype=np.uint64), n * d)        # [p, m]
     tau = np.concatenate([[0.0], np.asarray(days, float) / 365.0])
-    want = opaths.bridge_apply(opaths.bridge_schedule(tau),
-                               np.moveaxis(z.reshape(P, n, s)[:, :, :d], 2, 1), n)    # [p, i, o]
-    nblk = (n * s + 3) // 4 + 1
-    zb = np.zeros((P, 4 * nblk))
-    zb[:, :n * s] = z
-    blocks = zb.reshape(P, nblk, 4)
+    nodes = opaths.bridge_schedule(tau)
+    want = opaths.bridge_apply(nodes, np.moveaxis(opaths.node_normals(
+        nodes, d, 99, 0, np.arange(P, dtype=np.uint64)), 2, 1), n)        # [p, i, o]
+    rank = opaths.generation_order(nodes)
     wl, wr, sd = (ops[:, k].view(np.float32).astype(np.float64) for k in range(3))
     cur = np.zeros((P, d))
     stack = []
@@ -347,7 +344,9 @@ def test_date_ordered_bridge_matches_array_form(days, d):
         for k in range(a, b):
             j, fl = int(ops[k, 3]), int(ops[k, 4]) >> 16
             nodes_seen.append(j)
-            zz = blocks[:, j, :d]        # node j owns Philox block j: words 0..d-1
+            # op k is the k-th node the walk computes: normals d k .. d k + d - 1
+            assert rank[j] == k
+            zz = z[:, d * k:d * k + d]
             if fl & 1:
                 nw = np.float64(sd[k]) * zz
             else:
@@ -360,7 +359,7 @@ def test_date_ordered_bridge_matches_array_form(days, d):
         assert int(ops[dops[t + 1] - 1, 5]) == t if b > a else True
     # float32 weights vs FP64 weights: agree to float rounding
     np.testing.assert_allclose(got, want, rtol=0, atol=3e-6 * max(1.0, np.sqrt(tau[-1])))
-    # every bridge node is visited once: one Philox block per node
+    # every bridge node is visited once
     assert sorted(nodes_seen) == list(range(n))
 
 

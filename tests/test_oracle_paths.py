@@ -125,6 +125,45 @@ def test_normal_index_layout():
         assert z[m] == zz
 
 
+def _walk_order(nodes, n):
+    """The nodes in the order a walk producing dates 1..n in turn computes
+    them, by brute force: the walk holds the set of dates whose W is known;
+    to produce date t it takes the nearest known date r above t and
+    computes the node whose interval is (t - 1, r), then repeats with that
+    node's date, until t itself is known."""
+    by_interval = {(nd.l, nd.r): j for j, nd in enumerate(nodes) if nd.r >= 0}
+    root = [j for j, nd in enumerate(nodes) if nd.r < 0][0]
+    known, order = {0}, []
+    for t in range(1, n + 1):
+        if t not in known and not [x for x in known if x > t]:
+            order.append(root)
+            known.add(n)
+        while t not in known:
+            r = min(x for x in known if x > t)
+            j = by_interval[(t - 1, r)]
+            order.append(j)
+            known.add(nodes[j].m)
+    return order
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12, 31, 100, 365])
+def test_generation_order_is_the_date_ordered_walk(n):
+    """generation_order ranks the nodes in the order a date-by-date walk
+    computes them (checked against the walk itself); with d normals per node
+    in that order, node k takes normals d k .. d k + d - 1."""
+    nodes = paths.bridge_schedule(np.arange(n + 1) / 365.0)
+    order = _walk_order(nodes, n)
+    assert sorted(order) == list(range(n))
+    rank = paths.generation_order(nodes)
+    assert [int(rank[j]) for j in order] == list(range(n))
+    p = np.array([3, 2 ** 32 + 9], dtype=np.uint64)
+    for d in (1, 2, 3, 4):
+        z = paths.node_normals(nodes, d, 0xBEEF, 2, p)
+        flat = paths.normals(0xBEEF, 2, p, n * d)
+        for k, j in enumerate(order):
+            assert np.array_equal(z[:, j, :], flat[:, d * k:d * k + d])
+
+
 @pytest.mark.parametrize("days", [[365], [100, 365], [1, 2, 3, 4, 5], list(range(1, 366)),
                                   [7, 30, 31, 90, 200, 201, 364, 900], list(range(10, 3651, 10))])
 def test_bridge_covariance_is_min_of_times(days):
