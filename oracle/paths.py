@@ -232,8 +232,9 @@ class Market:
         return math.exp(-self.r * self.hist_days[k - 1] / 365.0)
 
 
-def simulate(mk: Market, seed: int, stream: int, paths: np.ndarray) -> np.ndarray:
-    """S[p, i, o] for the paths ``paths`` (global indices), o = 0..n."""
+def simulate_sx(mk: Market, seed: int, stream: int, paths: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """(S[p, i, o], X[p, i, o]) for the paths ``paths`` (global indices),
+    o = 0..n: the prices and the correlated Brownian values X = L W."""
     n, d = mk.n, mk.d
     paths = np.asarray(paths, dtype=np.uint64)
     tau = mk.tau()
@@ -244,7 +245,12 @@ def simulate(mk: Market, seed: int, stream: int, paths: np.ndarray) -> np.ndarra
     X = np.einsum("ik,pko->pio", L, W)
     sig = np.asarray(mk.sigma, dtype=np.float64)[None, :, None]
     S0 = np.asarray(mk.S0, dtype=np.float64)[None, :, None]
-    return S0 * np.exp((mk.r - 0.5 * sig ** 2) * tau[None, None, :] + sig * X)
+    return S0 * np.exp((mk.r - 0.5 * sig ** 2) * tau[None, None, :] + sig * X), X
+
+
+def simulate(mk: Market, seed: int, stream: int, paths: np.ndarray) -> np.ndarray:
+    """S[p, i, o] for the paths ``paths`` (global indices), o = 0..n."""
+    return simulate_sx(mk, seed, stream, paths)[0]
 
 
 def simulate_from_normals(mk: Market, z: np.ndarray) -> np.ndarray:
