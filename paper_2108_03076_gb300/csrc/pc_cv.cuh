@@ -189,7 +189,8 @@ __device__ __forceinline__ void cv_tiles(const PriceArgs &a, const CvArgs &c, EV
   const Layout &lay = a.lay;
   Rng2 g;
   g.stream = a.stream;
-  g.rk = a.rk;
+#pragma unroll
+  for (int i = 0; i < 20; ++i) g.rk[i] = a.rk[i];
   for (;;) {
     unsigned long long tile = 0;
     if (lane == 0) tile = atomicAdd(ctr, 1ull);

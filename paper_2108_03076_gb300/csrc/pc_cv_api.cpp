@@ -120,7 +120,7 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
     // evaluator keeps its operand stack in registers, so the stack words
     // leave the per-thread shared region
     cudaKernel_t jk = nullptr;
-    s = jit_kernel(k, m->H.d, kJitCv + cv_mode(d_xm != nullptr, ca), jk);
+    s = jit_kernel(k, m->H.d, kJitCv + cv_mode(d_xm != nullptr, ca), kBlock, jk);
     if (s != PC_OK) return s;
     const void *kern = reinterpret_cast<const void *>(jk);
     Layout &jl = a.lay;

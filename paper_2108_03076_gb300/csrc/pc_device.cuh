@@ -140,7 +140,7 @@ __device__ __forceinline__ void box_muller2(uint32_t a0, uint32_t b0, uint32_t a
 struct Rng2 {
   uint32_t plo[2], phi[2];
   uint32_t stream;
-  const uint32_t *rk;  // round keys (PriceArgs::rk)
+  uint32_t rk[20];  // Philox round keys (PriceArgs::rk), copied: the compiler keeps them uniform
 };
 
 // The four normals of Philox block b of both paths.
@@ -152,8 +152,13 @@ __device__ __forceinline__ void block_normals2(uint32_t b, const Rng2 &g, float2
 }
 
 // Slot s of this thread in the word-interleaved per-thread region (the
-// stride is the block size, 32..kBlock threads).
+// stride is the block size, 32..kBlock threads; a run-time specialised
+// kernel is compiled for its block size, so its slot offsets are constants).
+#ifdef PC_SLOT_STRIDE
+#define SL(s) R[(s) * PC_SLOT_STRIDE]
+#else
 #define SL(s) R[(s) * blockDim.x]
+#endif
 
 // Window slot w (0 .. win * d - 1) of this thread: in the shared region
 // (word-interleaved after lay.off_win) or, with GW, in the thread's column

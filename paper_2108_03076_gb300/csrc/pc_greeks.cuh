@@ -166,7 +166,8 @@ __device__ __forceinline__ void greeks_tiles(const PriceArgs &a, EVAL eval) {
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
   Rng2 g;
   g.stream = a.stream;
-  g.rk = a.rk;
+#pragma unroll
+  for (int i = 0; i < 20; ++i) g.rk[i] = a.rk[i];
   for (;;) {
     unsigned long long tile = 0;
     if (lane == 0) tile = atomicAdd(ctr, 1ull);

@@ -26,6 +26,7 @@ struct JitEntry {
   std::vector<uint32_t> program;
   int d = 0;
   int kind = kJitPrice;
+  int block = 0;  // the launch block the kernel is compiled for (its slot stride)
   cudaLibrary_t lib = nullptr;
   cudaKernel_t kernel = nullptr;
 };
@@ -41,6 +42,8 @@ struct pc_ctx {
   double *d_partials = nullptr;  // tile partials (scratch)
   size_t partial_cap = 0;        // doubles
   unsigned char *d_control = nullptr;  // reduction control block (kControlBytes, zero between launches)
+  void *d_tape = nullptr;        // adjoint tapes, one region per resident warp (grow-only)
+  size_t tape_cap = 0;           // bytes
   float2 *d_gwin = nullptr;      // HBM windows of simulated dates (grow-only)
   size_t gwin_cap = 0;           // float2 slots
   int32_t window_mode = 0;       // PC_WINDOW_AUTO / _SHARED / _HBM
@@ -63,6 +66,7 @@ struct pc_ctx {
   std::mutex load_mu;
   std::multimap<uint64_t, std::pair<std::vector<uint32_t>, pc::Program>> program_cache;
   double timeout_s = 300.0;
+  int32_t fail_allocs = 0;       // failure injection: this many next allocations fail (pc_debug_fail_allocations)
   int live_objects = 0;
 };
 
@@ -108,6 +112,11 @@ pc_status cuda_fail(cudaError_t e, const char *what);
 // Wait for the context's stream with its wall-clock limit.
 pc_status wait_stream(pc_ctx *c);
 
+// cudaMalloc for the context's buffers, or a simulated out-of-memory
+// (cudaErrorMemoryAllocation, nothing allocated) while the context's
+// failure injection count is positive.
+cudaError_t ctx_malloc(pc_ctx *c, void **p, size_t bytes);
+
 // Room left for a kernel's static shared memory when sizing its dynamic
 // shared memory.
 constexpr size_t kStaticSmemReserve = 2048;
@@ -137,9 +146,10 @@ pc_status prepare(const pc_model *m, const pc_contract *k, uint64_t n_paths, uin
 pc_status ensure_partials(pc_ctx *c, size_t doubles);
 
 // The run-time specialised kernel of the contract's program for d
-// underlyings and a kernel kind (kJit*; compiled on first use, cached on
-// the context by program content).
-pc_status jit_kernel(const pc_contract *k, int d, int kind, cudaKernel_t &out);
+// underlyings, a kernel kind (kJit*) and the launch's block size (the
+// per-thread slot stride, a constant in the compiled code); compiled on
+// first use, cached on the context by program content.
+pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKernel_t &out);
 // Programs of at most PC_JIT_MAX_INSNS instructions are specialised; the
 // launches of longer ones interpret them.
 bool jit_eligible(const pc_contract *k);

@@ -298,15 +298,17 @@ pc_status nvrtc_fail(nvrtcResult r, nvrtcProgram prog, const char *what) {
 
 // NVRTC: the generated source and the embedded device headers to a cubin
 // for `arch` (e.g. "sm_103a").
-pc_status to_cubin(const Program &p, int d, int kind, const std::string &arch, std::vector<char> &cubin) {
+pc_status to_cubin(const Program &p, int d, int kind, int block, const std::string &arch,
+                   std::vector<char> &cubin) {
   const std::string src = generate(p, d, kind);
   nvrtcProgram prog = nullptr;
   nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "pc_jit.cu", kJitHeaderCount, kJitHeaderSrcs,
                                      kJitHeaderNames);
   if (r != NVRTC_SUCCESS) return nvrtc_fail(r, nullptr, "run-time compiler");
   const std::string a = "-arch=" + arch;
-  const char *opts[] = {a.c_str(), "-std=c++17", "-default-device", "-DPC_JIT"};
-  r = nvrtcCompileProgram(prog, 4, opts);
+  const std::string stride = "-DPC_SLOT_STRIDE=" + std::to_string(block);
+  const char *opts[] = {a.c_str(), "-std=c++17", "-default-device", "-DPC_JIT", stride.c_str()};
+  r = nvrtcCompileProgram(prog, 5, opts);
   if (r != NVRTC_SUCCESS) {
     pc_status s = nvrtc_fail(r, prog, "run-time compilation");
     nvrtcDestroyProgram(&prog);
@@ -321,11 +323,12 @@ pc_status to_cubin(const Program &p, int d, int kind, const std::string &arch, s
   return PC_OK;
 }
 
-pc_status compile(const Program &p, int d, int kind, int device, cudaLibrary_t &lib, cudaKernel_t &kern) {
+pc_status compile(const Program &p, int d, int kind, int block, int device, cudaLibrary_t &lib,
+                  cudaKernel_t &kern) {
   cudaDeviceProp prop{};
   CU(cudaGetDeviceProperties(&prop, device), "device properties");
   std::vector<char> cubin;
-  pc_status s = to_cubin(p, d, kind, "sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a",
+  pc_status s = to_cubin(p, d, kind, block, "sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a",
                          cubin);
   if (s != PC_OK) return s;
   CU(cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0), "module load");
@@ -346,7 +349,7 @@ namespace pc {
 
 bool jit_eligible(const pc_contract *k) { return k->prog.code.size() <= size_t(PC_JIT_MAX_INSNS); }
 
-pc_status jit_kernel(const pc_contract *k, int d, int kind, cudaKernel_t &out) {
+pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKernel_t &out) {
   // the program's words: code, then pool bits
   std::vector<uint32_t> words;
   words.reserve(k->prog.code.size() * 4 + k->prog.pool.size());
@@ -369,7 +372,7 @@ pc_status jit_kernel(const pc_contract *k, int d, int kind, cudaKernel_t &out) {
   auto range = c->jit_cache.equal_range(h);
   for (auto it = range.first; it != range.second; ++it) {
     const JitEntry &E = it->second;
-    if (E.d == d && E.kind == kind && E.program == words) {
+    if (E.d == d && E.kind == kind && E.block == block && E.program == words) {
       out = E.kernel;
       return PC_OK;
     }
@@ -378,7 +381,8 @@ pc_status jit_kernel(const pc_contract *k, int d, int kind, cudaKernel_t &out) {
   E.program = words;
   E.d = d;
   E.kind = kind;
-  pc_status s = compile(k->prog, d, kind, c->device, E.lib, E.kernel);
+  E.block = block;
+  pc_status s = compile(k->prog, d, kind, block, c->device, E.lib, E.kernel);
   if (s != PC_OK) return s;
   out = E.kernel;
   c->jit_cache.emplace(h, std::move(E));
@@ -411,7 +415,7 @@ extern "C" pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_wor
   pc_status s = compile_program(bytecode, n_words, consts, n_consts, tparams, n_params, p1, p2, true, p, err);
   if (s != PC_OK) return fail(s, err);
   std::vector<char> cubin;
-  s = to_cubin(p, d, kind, "sm_103a", cubin);
+  s = to_cubin(p, d, kind, kBlock, "sm_103a", cubin);
   if (s != PC_OK) return s;
   *cubin_bytes = cubin.size();
   return PC_OK;

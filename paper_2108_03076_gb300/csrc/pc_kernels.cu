@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(kBlock, 5) batch_kernel(const BatchArgs b) {
     const float *pool = reinterpret_cast<const float *>(P + a.n_insn);
     load_model_regs<D>(a.m, Bm, S0);
     g.stream = a.stream;
-    g.rk = a.rk;
+#pragma unroll
+    for (int i = 0; i < 20; ++i) g.rk[i] = a.rk[i];
     for (uint32_t k = 0; k < U.n_tiles; ++k) {
       const uint64_t tile = U.tile0 + k;
       const uint64_t i0 = tile * kTilePaths + lane, i1 = i0 + 32;
@@ -130,7 +131,8 @@ __global__ void __launch_bounds__(kBlock) debug_paths_kernel(const __grid_consta
   g.plo[1] = uint32_t(offset + i1);
   g.phi[1] = uint32_t((offset + i1) >> 32);
   g.stream = stream;
-  g.rk = rk.k;
+#pragma unroll
+  for (int i = 0; i < 20; ++i) g.rk[i] = rk.k[i];
   PathState<D> ps;
   path_state_init<D>(ps);
   const size_t row = size_t(m.n) + 1;
