@@ -164,6 +164,13 @@ pc_status pc_destroy(pc_ctx *ctx);
 
 /* Message of the most recent failure on this thread (library-owned, valid
  * until the thread's next failing call); "" if none.  ctx may be NULL. */
+/* Wall-clock limit of the context's blocking calls (seconds > 0; default
+ * 300, or the environment variable PC_TIMEOUT_S at pc_create): a call whose
+ * device work has not finished by then returns PC_ETIMEOUT.  The work is
+ * not cancelled -- it completes on the context's stream, and later calls
+ * are ordered after it, so the context stays usable.  Errors: PC_EINVAL. */
+pc_status pc_set_timeout(pc_ctx *ctx, double seconds);
+
 const char *pc_last_error(const pc_ctx *ctx);
 
 /* ------------------------------------------------------------------------ */
@@ -223,6 +230,20 @@ pc_status pc_verify_payoff(const uint32_t *bytecode, size_t n_words,
 pc_status pc_assemble(const char *text, uint32_t *words, size_t cap_words,
                       size_t *n_words, double *consts, size_t cap_consts,
                       size_t *n_consts, char *err, size_t err_cap);
+
+/* Host-only: cutPayoff (Sec. 4.1) on bytecode.  Every payoff(t, p1', p2')
+ * becomes if(t < now, 0, payoff(t, p1', p2')), so a contract loaded once
+ * can be priced at any valuation time: with the model's t_now = now the
+ * payments before now are dropped (Theorem 5: the result is the value of
+ * the cashflows from now on).  Every other instruction is copied; the
+ * literal 0.0 is appended to the constants unless one is present.  Writes at
+ * most cap_words words / cap_consts constants and their counts.
+ * Errors: PC_EINVAL, PC_EBYTECODE (bad opcode or truncated operands),
+ * PC_ELIMIT (buffers too small, or more than PC_MAX_PROGRAM input words). */
+pc_status pc_cut_payoff(const uint32_t *bytecode, size_t n_words, const double *consts,
+                        size_t n_consts, uint32_t *out_words, size_t cap_words,
+                        size_t *n_out_words, double *out_consts, size_t cap_consts,
+                        size_t *n_out_consts);
 
 /* ------------------------------------------------------------------------ */
 /* Pricing                                                                   */
@@ -449,6 +470,33 @@ pc_status pc_greeks(const pc_model *model, const pc_contract *contract,
                     uint64_t n_paths, uint64_t seed, double *out_price,
                     double *out_delta, double *out_vega, double *out_se);
 
+/* The same sensitivities by the chain rule in reverse (adjoint mode): one
+ * launch gives the price and every underlying's delta and vega.  Each
+ * path's payoff program records a tape of its real arithmetic (decisions
+ * held fixed as above) and the path state it reads at each observed date
+ * (S and X = L W of the read underlying); a reverse sweep of the tape gives
+ * d payoff / d S0[l] = sum over reads of the adjoint times S / S0[l], and
+ * d / d sigma[l] = sum of the adjoint times S (X - sigma[l] tau).  The paper
+ * has no sensitivities; this is the pathwise method (Glasserman, Monte
+ * Carlo Methods in Financial Engineering, Sec. 7.2) on the IL semantics of
+ * Fig. 3.  Same paths as pc_price with this seed.  The tape lives in a
+ * context buffer of grid x warps x (bound on the program's tape entries)
+ * x 776 bytes, grown as needed; programs keep their window of dates in
+ * shared memory (no HBM window: PC_ERANGE / PC_ELIMIT as pc_price_noalloc).
+ * Outputs as pc_greeks.  Blocks until done.  Errors: as pc_price, and
+ * PC_ELIMIT for a tape bound above 2^24 entries. */
+pc_status pc_greeks_adjoint(const pc_model *model, const pc_contract *contract,
+                            uint64_t n_paths, uint64_t seed, double *out_price,
+                            double *out_delta, double *out_vega, double *out_se);
+
+/* Asynchronous form on the context's stream, paths path_offset.. of Philox
+ * stream `stream`: d_out (device, 2 (1 + 2d) + 1 doubles) receives the sums
+ * and sums of squares of (payoff, delta_0..delta_{d-1}, vega_0..vega_{d-1})
+ * per path, interleaved (sum, sum of squares) per quantity, then n_paths. */
+pc_status pc_greeks_adjoint_async(const pc_model *model, const pc_contract *contract,
+                                  uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                                  uint32_t stream, double *d_out);
+
 /* ------------------------------------------------------------------------ */
 /* Learned control variate: network                                          */
 /* ------------------------------------------------------------------------ */
@@ -609,6 +657,27 @@ pc_status pc_debug_paths(const pc_model *model, uint64_t n_paths,
                          uint64_t path_offset, uint64_t seed, uint32_t stream,
                          float *d_S);
 
+/* Failure injection for tests of the error paths (no device fault is
+ * involved): the context's next `count` device allocations fail as if the
+ * device were out of memory (the call reports PC_ENOMEM; nothing is
+ * allocated or leaked).  count = 0 ends the injection. */
+pc_status pc_debug_fail_allocations(pc_ctx *ctx, int32_t count);
+
+/* Write `value` into the context's device status word (as a kernel that
+ * clamped an access would): the next blocking call reports PC_EDEVICE and
+ * clears it.  Blocks until written. */
+pc_status pc_debug_set_status(pc_ctx *ctx, int32_t value);
+
+/* Failure test of the network's tensor-core product: while `on`, its TMA
+ * producer withholds the copies of the first k-chunk, so the MMA issuer's
+ * and the producer's bounded mbarrier waits expire (after about 10 ms
+ * instead of the normal second); the kernel sets the network's status word,
+ * stops issuing, lets the copies it did issue land, frees its tensor memory
+ * and returns.  The next blocking network call (pc_mlp_gradients,
+ * pc_mlp_train) reports PC_ETIMEOUT and clears the word.  Drops the
+ * network's captured graphs. */
+pc_status pc_debug_mlp_withhold_tma(pc_mlp *net, int32_t on);
+
 /* Per-path probe of pc_greeks for one underlying: writes (payoff,
  * d payoff / d S0[underlying], d payoff / d sigma[underlying]) of path
  * path_offset+i to d_paths[3i..3i+2] (device floats) and the six sums
@@ -617,6 +686,14 @@ pc_status pc_debug_paths(const pc_model *model, uint64_t n_paths,
 pc_status pc_debug_greeks_paths(const pc_model *model, const pc_contract *contract,
                                 uint64_t n_paths, uint64_t path_offset, uint64_t seed,
                                 int32_t underlying, double *d_out, float *d_paths);
+
+/* Per-path probe of pc_greeks_adjoint: path path_offset+i writes (payoff,
+ * delta_0..delta_{d-1}, vega_0..vega_{d-1}) to d_paths[(1+2d)i ..] (device
+ * floats); d_out as pc_greeks_adjoint_async.  Asynchronous on the
+ * context's stream. */
+pc_status pc_debug_adjoint_paths(const pc_model *model, const pc_contract *contract,
+                                 uint64_t n_paths, uint64_t path_offset, uint64_t seed,
+                                 double *d_out, float *d_paths);
 
 /* Per path i < n_paths (paths 0.., Philox stream 0): d_xm[3i] = payoff X,
  * d_xm[3i + 1] = hedge gain M, d_xm[3i + 2] = second-order gain M2 of

@@ -117,6 +117,14 @@ _SIGS = {
     "pc_price_async": [VP, VP, U64, U64, U64, U32, VP],
     "pc_price_paths": [VP, VP, U64, U64, U64, U32, VP, VP],
     "pc_price_noalloc": [VP, VP, U64, U64, U64, U32, VP],
+    "pc_cut_payoff": [PU32, SZ, PD, SZ, PU32, SZ, C.POINTER(SZ), PD, SZ, C.POINTER(SZ)],
+    "pc_set_timeout": [VP, DBL],
+    "pc_debug_fail_allocations": [VP, I32],
+    "pc_debug_set_status": [VP, I32],
+    "pc_debug_mlp_withhold_tma": [VP, I32],
+    "pc_greeks_adjoint": [VP, VP, U64, U64, PD, PD, PD, PD],
+    "pc_greeks_adjoint_async": [VP, VP, U64, U64, U64, U32, VP],
+    "pc_debug_adjoint_paths": [VP, VP, U64, U64, U64, VP, VP],
     "pc_price_batch": [SZ, C.POINTER(VP), C.POINTER(VP), C.POINTER(U64), U64, PD, PD],
     "pc_set_window_mode": [VP, C.c_int32],
     "pc_set_jit": [VP, C.c_int32],
@@ -254,6 +262,25 @@ def pc_assemble(text: str) -> Tuple[np.ndarray, np.ndarray]:
     return w, k
 
 
+def pc_cut_payoff(words, consts) -> Tuple[np.ndarray, np.ndarray]:
+    """cutPayoff (Sec. 4.1) of a bytecode program: (words, consts)."""
+    w = _arr(words, np.uint32)
+    k = _arr(consts, np.float64)
+    nw, nk = C.c_size_t(0), C.c_size_t(0)
+    cap_w, cap_k = 2 * w.size + 64, k.size + 1
+    ow, ok = np.zeros(cap_w, np.uint32), np.zeros(cap_k, np.float64)
+    while True:
+        st = lib().pc_cut_payoff(_ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,
+                                 _ptr(ow, C.c_uint32), cap_w, C.byref(nw), _ptr(ok, C.c_double), cap_k,
+                                 C.byref(nk))
+        if st == PC_ELIMIT and (nw.value > cap_w or nk.value > cap_k):
+            cap_w, cap_k = nw.value, nk.value
+            ow, ok = np.zeros(cap_w, np.uint32), np.zeros(cap_k, np.float64)
+            continue
+        _check(st)
+        return ow[:nw.value].copy(), ok[:nk.value].copy()
+
+
 def pc_verify_payoff(words, consts, tparams=()) -> ProgramInfo:
     w, k, t = _arr(words, np.uint32), _arr(consts, np.float64), _arr(tparams, np.int32)
     info = ProgramInfo()
@@ -311,6 +338,22 @@ NOALLOC_MAX_PATHS = 1 << 24
 
 def pc_set_window_mode(ctx: int, mode: int) -> None:
     _check(lib().pc_set_window_mode(VP(ctx), int(mode)))
+
+
+def pc_set_timeout(ctx: int, seconds: float) -> None:
+    _check(lib().pc_set_timeout(VP(ctx), float(seconds)))
+
+
+def pc_debug_fail_allocations(ctx: int, count: int) -> None:
+    _check(lib().pc_debug_fail_allocations(VP(ctx), int(count)))
+
+
+def pc_debug_set_status(ctx: int, value: int) -> None:
+    _check(lib().pc_debug_set_status(VP(ctx), int(value)))
+
+
+def pc_debug_mlp_withhold_tma(net: int, on: bool) -> None:
+    _check(lib().pc_debug_mlp_withhold_tma(VP(net), int(bool(on))))
 
 
 def pc_set_jit(ctx: int, enabled: bool) -> None:
@@ -520,6 +563,27 @@ def pc_greeks(model: int, contract: int, n_paths: int, seed: int, d: int):
     _check(lib().pc_greeks(VP(model), VP(contract), n_paths, seed, C.byref(p),
                            _ptr(de, C.c_double), _ptr(ve, C.c_double), _ptr(se, C.c_double)))
     return p.value, de, ve, se
+
+
+def pc_greeks_adjoint(model: int, contract: int, n_paths: int, seed: int, d: int):
+    """(price, delta[d], vega[d], se[1+2d]) from one adjoint launch."""
+    price = DBL()
+    delta, vega, se = np.zeros(d), np.zeros(d), np.zeros(1 + 2 * d)
+    _check(lib().pc_greeks_adjoint(VP(model), VP(contract), n_paths, seed, C.byref(price),
+                                   _ptr(delta, C.c_double), _ptr(vega, C.c_double), _ptr(se, C.c_double)))
+    return price.value, delta, vega, se
+
+
+def pc_greeks_adjoint_async(model: int, contract: int, n_paths: int, path_offset: int, seed: int,
+                            stream: int, d_out: int) -> None:
+    _check(lib().pc_greeks_adjoint_async(VP(model), VP(contract), n_paths, path_offset, seed, stream,
+                                         VP(d_out)))
+
+
+def pc_debug_adjoint_paths(model: int, contract: int, n_paths: int, path_offset: int, seed: int,
+                           d_out: int, d_paths: int) -> None:
+    _check(lib().pc_debug_adjoint_paths(VP(model), VP(contract), n_paths, path_offset, seed,
+                                        VP(d_out), VP(d_paths)))
 
 
 def pc_debug_philox(ctx: int, d_ctr: int, key0: int, key1: int, d_out: int, n: int) -> None:

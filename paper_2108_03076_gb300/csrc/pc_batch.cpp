@@ -306,7 +306,7 @@ pc_status create(size_t n, const pc_model *const *models, const pc_contract *con
   const size_t part_b = align256(part_doubles * sizeof(double));
   const size_t out_b = align256(n * 4 * sizeof(double));
   CU(cudaSetDevice(c->device), "cudaSetDevice");
-  CU(cudaMalloc(&B->d_mem, items_b + units_b + zero_b + part_b + out_b), "batch memory");
+  CU(ctx_malloc(c, &B->d_mem, items_b + units_b + zero_b + part_b + out_b), "batch memory");
   unsigned char *base = static_cast<unsigned char *>(B->d_mem);
   B->d_items = reinterpret_cast<PriceArgs *>(base);
   B->d_units = reinterpret_cast<BatchUnit *>(base + items_b);

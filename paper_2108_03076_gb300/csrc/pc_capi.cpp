@@ -51,8 +51,22 @@ pc_status wait_stream(pc_ctx *c) {
   }
 }
 
+cudaError_t ctx_malloc(pc_ctx *c, void **p, size_t bytes) {
+  if (c->fail_allocs > 0) {
+    --c->fail_allocs;
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 cudaError_t ctx_alloc(pc_ctx *c, void **p, size_t bytes, bool &pooled) {
   pooled = c->pool != nullptr;
+  if (c->fail_allocs > 0) {
+    --c->fail_allocs;
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   if (pooled) return cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream);
   return cudaMalloc(p, bytes);
 }
@@ -114,7 +128,7 @@ pc_status ensure_partials(pc_ctx *c, size_t doubles) {
   c->d_partials = nullptr;
   c->partial_cap = 0;
   size_t cap = std::max<size_t>(doubles, 1 << 16);
-  CU(cudaMalloc(&c->d_partials, cap * sizeof(double)), "partials");
+  CU(ctx_malloc(c, reinterpret_cast<void **>(&c->d_partials), cap * sizeof(double)), "partials");
   c->partial_cap = cap;
   return PC_OK;
 }
@@ -248,7 +262,7 @@ pc_status bind_hbm_window(pc_ctx *c, Launch &L, int d) {
     if (c->d_gwin) cudaFree(c->d_gwin);
     c->d_gwin = nullptr;
     c->gwin_cap = 0;
-    CU(cudaMalloc(&c->d_gwin, slots * sizeof(float2)), "HBM window");
+    CU(ctx_malloc(c, reinterpret_cast<void **>(&c->d_gwin), slots * sizeof(float2)), "HBM window");
     c->gwin_cap = slots;
   }
   L.args.lay.gwin = c->d_gwin;
@@ -298,7 +312,7 @@ pc_status run_greeks(const pc_model *m, const pc_contract *k, uint64_t n_paths, 
     // the contract's run-time specialised tangent kernel (same arguments,
     // shared-memory layout and block)
     cudaKernel_t jk = nullptr;
-    s = jit_kernel(k, d, kJitGreeks + (d_paths != nullptr ? 1 : 0), jk);
+    s = jit_kernel(k, d, kJitGreeks + (d_paths != nullptr ? 1 : 0), block, jk);
     if (s != PC_OK) return s;
     const void *kern = reinterpret_cast<const void *>(jk);
     int nb = 0;
@@ -333,7 +347,7 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
     // the contract's run-time specialised kernel (same arguments and shape)
     cudaKernel_t jk = nullptr;
     s = jit_kernel(k, m->H.d, (d_payoffs != nullptr ? kJitPriceWrite : kJitPrice) | (L.hbm_window ? kJitHbm : 0),
-                   jk);
+                   L.block, jk);
     if (s != PC_OK) return s;
     const void *kern = reinterpret_cast<const void *>(jk);
     // the specialised evaluator keeps its operand stack in registers: drop
@@ -458,6 +472,28 @@ pc_status pc_price_noalloc(const pc_model *m, const pc_contract *k, uint64_t n_p
 }
 
 
+pc_status pc_set_timeout(pc_ctx *c, double seconds) {
+  if (!c) return fail(PC_EINVAL, "null context");
+  if (!(seconds > 0.0) || !std::isfinite(seconds)) return fail(PC_EINVAL, "the limit must be a positive number of seconds");
+  c->timeout_s = seconds;
+  return PC_OK;
+}
+
+pc_status pc_debug_fail_allocations(pc_ctx *c, int32_t count) {
+  if (!c) return fail(PC_EINVAL, "null context");
+  if (count < 0) return fail(PC_EINVAL, "count must be >= 0");
+  c->fail_allocs = count;
+  return PC_OK;
+}
+
+pc_status pc_debug_set_status(pc_ctx *c, int32_t value) {
+  if (!c) return fail(PC_EINVAL, "null context");
+  CU(cudaSetDevice(c->device), "cudaSetDevice");
+  CU(cudaMemcpyAsync(reinterpret_cast<int32_t *>(c->d_res + 4), &value, 4, cudaMemcpyHostToDevice, c->stream),
+     "status write");
+  return wait_stream(c);
+}
+
 const char *pc_last_error(const pc_ctx *) { return tl_err.c_str(); }
 
 pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
@@ -544,6 +580,7 @@ pc_status pc_destroy(pc_ctx *c) {
   if (c->d_partials) cudaFree(c->d_partials);
   if (c->d_control) cudaFree(c->d_control);
   if (c->d_gwin) cudaFree(c->d_gwin);
+  if (c->d_tape) cudaFree(c->d_tape);
   jit_release(c);
   if (c->d_gout) cudaFree(c->d_gout);
   if (c->d_res) cudaFree(c->d_res);
@@ -572,7 +609,7 @@ pc_status pc_model_create(pc_ctx *c, const pc_model_desc *desc, pc_model **out) 
                    padded(H.disc) + padded(H.sval) + padded(H.tau) + padded(H.Lf) +
                    padded(H.sig) + 256;
     CU(cudaSetDevice(c->device), "cudaSetDevice");
-    cudaError_t e = cudaMalloc(&m->d_mem, bytes);
+    cudaError_t e = ctx_malloc(c, &m->d_mem, bytes);
     if (e != cudaSuccess) {
       delete m;
       return cuda_fail(e, "model tables");
@@ -772,6 +809,29 @@ pc_status pc_contract_destroy(pc_contract *k) {
   return PC_OK;
 }
 
+pc_status pc_cut_payoff(const uint32_t *bytecode, size_t n_words, const double *consts, size_t n_consts,
+                        uint32_t *out_words, size_t cap_words, size_t *n_out_words, double *out_consts,
+                        size_t cap_consts, size_t *n_out_consts) {
+  if (!bytecode || !n_out_words || !n_out_consts || (n_consts && !consts)) return fail(PC_EINVAL, "null argument");
+  if (n_words > PC_MAX_PROGRAM) return fail(PC_ELIMIT, "program exceeds PC_MAX_PROGRAM words");
+  try {
+    std::vector<uint32_t> w;
+    std::vector<double> k;
+    std::string e;
+    pc_status s = cut_payoff(bytecode, n_words, consts, n_consts, w, k, e);
+    if (s != PC_OK) return fail(s, e);
+    *n_out_words = w.size();
+    *n_out_consts = k.size();
+    if (w.size() > cap_words || k.size() > cap_consts || (w.size() && !out_words) || (k.size() && !out_consts))
+      return fail(PC_ELIMIT, "output buffers too small");
+    std::copy(w.begin(), w.end(), out_words);
+    std::copy(k.begin(), k.end(), out_consts);
+    return PC_OK;
+  } catch (const std::bad_alloc &) {
+    return fail(PC_ENOMEM, "host allocation");
+  }
+}
+
 pc_status pc_assemble(const char *text, uint32_t *words, size_t cap_words, size_t *n_words,
                       double *consts, size_t cap_consts, size_t *n_consts, char *err,
                       size_t err_cap) {
@@ -857,9 +917,14 @@ pc_status pc_jit_compile(const pc_model *m, const pc_contract *k) {
   if (!m || !k) return fail(PC_EINVAL, "null model or contract");
   if (m->ctx != k->ctx) return fail(PC_EINVAL, "model and contract belong to different contexts");
   if (!jit_eligible(k)) return PC_OK;  // launches interpret it
+  // the block a pricing launch of this pair uses (it does not depend on
+  // the path count)
+  Launch L;
+  pc_status s = prepare(m, k, 1u << 20, 0, 0, 0, L, true);
+  if (s != PC_OK) return s;
   CU(cudaSetDevice(m->ctx->device), "cudaSetDevice");
   cudaKernel_t jk = nullptr;
-  return jit_kernel(k, m->H.d, kJitPrice, jk);
+  return jit_kernel(k, m->H.d, kJitPrice | (L.hbm_window ? kJitHbm : 0), L.block, jk);
 }
 
 pc_status pc_price_info(const pc_model *m, const pc_contract *k, uint64_t n_paths, pc_launch_info *info) {

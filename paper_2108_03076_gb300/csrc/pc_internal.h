@@ -62,6 +62,11 @@ inline size_t batch_smem_bytes(size_t slot_bytes, int words, int block) {
 int batch_blocks_per_sm(int d, int block, size_t smem_bytes);
 cudaError_t launch_batch(const BatchArgs &b, int d, int grid, int block, size_t smem_bytes,
                          cudaStream_t s);
+// The adjoint sensitivity kernel (pc_adjoint.cuh): launch, and resident
+// blocks per SM for a shared-memory footprint (sets the kernel's limit).
+cudaError_t launch_adjoint(const PriceArgs &a, const TapeArgs &t, int grid, int block, size_t smem,
+                           cudaStream_t s);
+int adjoint_blocks_per_sm(int d, int block, size_t smem_bytes);
 // Occupancy results keyed by (device, kernel variant, block, shared memory):
 // the query runs once per key (it sets the kernel's shared-memory limit and
 // costs microseconds), later calls return the stored count.  With `store`
@@ -101,13 +106,35 @@ pc_status compile_program(const uint32_t *words, size_t n_words, const double *c
 // calls on_fail(status, time, ordinal) (time and ordinal of an out-of-grid
 // read; 0 for PC_ELIMIT, a program whose loop trip counts exceed 2^26
 // analysis steps).
+//
+// The walk also counts `entries`: an upper bound on the entries a run of
+// the program appends to the adjoint tape (pc_adjoint.cuh): one per model
+// read, real arithmetic operation, select, loop latch and loop end, and
+// 2n - 1 per fused n-leaf reduction (none for tests).
 template <typename OnFail>
 struct TimeWalk {
   const XInsn *C;
   int64_t t_now, n_dates, n_hist;
   OnFail on_fail;
-  int64_t frontier = 0, lookback = 0, steps = 0;
+  int64_t frontier = 0, lookback = 0, steps = 0, entries = 0;
   pc_status st = PC_OK;
+
+  static int64_t entry_count(const XInsn &I) {
+    const uint32_t op = I.opa & 0xffu;
+    switch (op) {
+      case X_MODEL: case X_MODEL_MULK: case X_MODEL_DIVK:
+      case X_NEGF: case X_ADDF: case X_SUBF: case X_MULF: case X_DIVF: case X_MAXF: case X_MINF:
+      case X_ADDFK: case X_SUBFK: case X_MULFK: case X_DIVFK: case X_MAXFK: case X_MINFK:
+      case X_RSUBFK: case X_RDIVFK: case X_SEL:
+        return 1;
+      case X_LRED: {
+        const uint32_t A = I.opa >> 8;
+        return ((A >> 4) & 7u) ? 0 : 2 * int64_t(((A >> 8) & 3u) + 1) - 1;
+      }
+      default:
+        return 0;
+    }
+  }
 
   void run(size_t a, size_t b, int64_t t0) {
     for (size_t pc = a; pc < b && st == PC_OK;) {
@@ -130,12 +157,14 @@ struct TimeWalk {
           if (o > frontier) frontier = o;
           else if (frontier - o > lookback) lookback = frontier - o;
         }
+        entries += entry_count(I);
         ++pc;
       } else if (op == X_LOOPANY) {
         const int64_t n = I.b;
         const size_t end = I.e;  // pc after LEND
         for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(pc + 1, pc + 2, t0 + k);
         run(pc + 2, end - 1, t0 + n);
+        entries += 1;  // LEND
         pc = end;
       } else if (op == X_LOOP) {
         const int64_t n = I.b;
@@ -144,6 +173,7 @@ struct TimeWalk {
           const size_t end = C[test].e;  // pc after LEND
           for (int64_t k = 0; k <= n && st == PC_OK; ++k) run(cond, test, t0 + k);
           run(test + 1, end - 1, t0 + n);  // else-branch (before LEND)
+          entries += (n + 1) + 1;          // LSTEPK per iteration, LEND
           pc = end;
           continue;
         }
@@ -154,10 +184,12 @@ struct TimeWalk {
           run(test + 1, next - 1, t0 + k);  // then-branch (before LLATCH)
         }
         run(next + 1, end - 1, t0 + n);  // else-branch (before LEND)
+        entries += (n + 1) + 1;          // LLATCH per iteration, LEND
         pc = end;
       } else if (op == X_END) {
         return;
       } else {
+        entries += entry_count(I);
         ++pc;
       }
     }
@@ -177,6 +209,12 @@ struct TimeWalk {
 // callers decide where such a window can live).
 pc_status analyse_program(const Program &p, int32_t t_now, int32_t n_dates, int32_t n_hist,
                           int32_t &win, std::string &err);
+
+// cutPayoff (Sec. 4.1) on bytecode: every payoff(t, p1', p2') becomes
+// if(t < now, 0, payoff(t, p1', p2')); the literal 0.0 is appended to the
+// constants unless present.
+pc_status cut_payoff(const uint32_t *words, size_t n_words, const double *consts, size_t n_consts,
+                     std::vector<uint32_t> &out, std::vector<double> &out_consts, std::string &err);
 
 pc_status assemble_text(const char *text, std::vector<uint32_t> &words,
                         std::vector<double> &consts, std::string &err);

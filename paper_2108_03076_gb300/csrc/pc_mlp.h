@@ -59,7 +59,10 @@ struct TcMaps {
 cudaError_t gemm_tc_init();
 bool gemm_tc_supported(const GemmArgs &g);
 bool make_tc_maps(const GemmArgs &g, TcMaps &m);
-cudaError_t launch_gemm_tc(int epi, const GemmArgs &g, const TcMaps &m, int32_t *status, cudaStream_t s);
+// withhold: failure test (the producer withholds its first copies and the
+// bounded waits expire after about 10 ms)
+cudaError_t launch_gemm_tc(int epi, const GemmArgs &g, const TcMaps &m, int32_t *status, cudaStream_t s,
+                           bool withhold = false);
 
 // x [n, fin] FP32 -> X [rows, ld] BF16, zero beyond n rows / fin columns.
 cudaError_t launch_to_bf16(const float *x, size_t n, int fin, __nv_bfloat16 *X, size_t rows, int ld,

@@ -37,6 +37,7 @@ struct pc_mlp {
   size_t n_flat = 0, n_real = 0;
   size_t max_rows = 0;              // padded rows per call
   uint64_t steps = 0;
+  bool tc_withhold = false;         // failure test of the tensor-core product's bounded waits
   void *mem = nullptr;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16 *pb = nullptr;
@@ -203,7 +204,8 @@ cudaError_t forward(pc_mlp *N, size_t rows, cudaStream_t s) {
       if (it != N->tc_maps.end()) maps = &it->second;
       tc = maps != nullptr;
     }
-    cudaError_t e = tc ? launch_gemm_tc(epi, a, *maps, N->dstatus, s) : launch_gemm(kGemmForward, epi, a, 1, s);
+    cudaError_t e = tc ? launch_gemm_tc(epi, a, *maps, N->dstatus, s, N->tc_withhold)
+                       : launch_gemm(kGemmForward, epi, a, 1, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -521,6 +523,16 @@ pc_status pc_mlp_train(pc_mlp *N, const float *d_x, const float *d_t, size_t n_d
   pc_status st = mlp_status(N);
   if (st != PC_OK) return st;
   N->steps += uint64_t(steps);
+  return PC_OK;
+}
+
+pc_status pc_debug_mlp_withhold_tma(pc_mlp *N, int32_t on) {
+  if (!N) return fail(PC_EINVAL, "null network");
+  wait_stream(N->ctx);
+  mlp_drop_graphs(N);
+  if (N->exec) cudaGraphExecDestroy(N->exec);
+  N->exec = nullptr;
+  N->tc_withhold = on != 0;
   return PC_OK;
 }
 

@@ -43,6 +43,7 @@ namespace {
 constexpr int kTcBM = 128, kTcBK = 64, kStages = 2, kTcThreads = 256;
 constexpr uint32_t kATileBytes = kTcBM * kTcBK * 2;  // 16 KB
 constexpr long long kWaitCycles = 2000000000ll;      // ~1 s at 2 GHz
+constexpr long long kTestWaitCycles = 20000000ll;    // ~10 ms: the failure test's limit
 
 __device__ __forceinline__ uint32_t su32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -64,10 +65,10 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for the phase of `parity` to complete; false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (!mbar_test(bar, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 
@@ -133,6 +134,10 @@ struct TcArgs {
   float *Cf;
   int ldc;
   int32_t *status;
+  // failure test: the producer withholds chunk 0's copies, so the waits on
+  // it expire (after wait_cycles) and the kernel takes its abort path
+  int withhold;
+  long long wait_cycles;
 };
 
 template <int EPI, int BN>
@@ -170,11 +175,12 @@ __global__ void __launch_bounds__(kTcThreads)
     int issued = 0;
     for (int c = 0; c < nk; ++c) {
       const int s = c % kStages;
-      if (c >= kStages && !mbar_wait(empty0 + 8 * s, ((c / kStages) + 1) & 1)) {
+      if (c >= kStages && !mbar_wait(empty0 + 8 * s, ((c / kStages) + 1) & 1, g.wait_cycles)) {
         atomicOr(g.status, 4);
         atomicExch(&abort_flag, 1);
       }
       if (*(volatile int *)&abort_flag) break;
+      if (g.withhold && c == 0) continue;
       const uint32_t sa = base + s * kStageBytes, sb = sa + kATileBytes;
       mbar_expect_tx(full0 + 8 * s, kStageBytes);
       tma_load_2d(sa, &ta, c * kTcBK, m0, full0 + 8 * s);
@@ -183,14 +189,14 @@ __global__ void __launch_bounds__(kTcThreads)
     }
     // copies still in flight finish before the CTA can exit
     for (int c = issued - kStages > 0 ? issued - kStages : 0; c < issued; ++c)
-      if (!mbar_wait(full0 + 8 * (c % kStages), (c / kStages) & 1)) atomicOr(g.status, 4);
+      if (!mbar_wait(full0 + 8 * (c % kStages), (c / kStages) & 1, g.wait_cycles)) atomicOr(g.status, 4);
   } else if (threadIdx.x == 32) {
     // MMA issuer
     constexpr uint32_t idesc = idesc_bf16(kTcBM, BN);
     for (int c = 0; c < nk; ++c) {
       const int s = c % kStages;
       if (*(volatile int *)&abort_flag) break;
-      if (!mbar_wait(full0 + 8 * s, (c / kStages) & 1)) {
+      if (!mbar_wait(full0 + 8 * s, (c / kStages) & 1, g.wait_cycles)) {
         atomicOr(g.status, 4);
         atomicExch(&abort_flag, 1);
         break;
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(kTcThreads)
   }
   __syncwarp();
   // epilogue: all warps wait for the accumulator
-  if (!mbar_wait(done, 0)) atomicOr(g.status, 4);
+  if (!mbar_wait(done, 0, g.wait_cycles)) atomicOr(g.status, 4);
   __syncwarp();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const int quarter = warp & 3, half = warp >> 2;
@@ -329,13 +335,15 @@ bool make_tc_maps(const GemmArgs &g, TcMaps &m) {
          make_map(m.b, g.B, uint64_t(g.N), uint64_t(g.K), uint64_t(g.ldb), uint32_t(bn));
 }
 
-cudaError_t launch_gemm_tc(int epi, const GemmArgs &g, const TcMaps &m, int32_t *status, cudaStream_t s) {
+cudaError_t launch_gemm_tc(int epi, const GemmArgs &g, const TcMaps &m, int32_t *status, cudaStream_t s,
+                           bool withhold) {
   if (!status || !gemm_tc_supported(g) || (epi != kEpiBiasSoftplus && epi != kEpiBias))
     return cudaErrorInvalidValue;
   const cudaError_t r = gemm_tc_init();
   if (r != cudaSuccess) return r;
   const int bn = g.N == 64 ? 64 : 128;
-  TcArgs a{g.M, g.N, g.K, g.bias, g.Cb, g.Cf, g.ldc, status};
+  TcArgs a{g.M, g.N, g.K, g.bias, g.Cb, g.Cf, g.ldc, status, withhold ? 1 : 0,
+           withhold ? kTestWaitCycles : kWaitCycles};
   if (epi == kEpiBiasSoftplus) return bn == 64 ? launch_tc<kEpiBiasSoftplus, 64>(m.a, m.b, a, s)
                                                : launch_tc<kEpiBiasSoftplus, 128>(m.a, m.b, a, s);
   return bn == 64 ? launch_tc<kEpiBias, 64>(m.a, m.b, a, s) : launch_tc<kEpiBias, 128>(m.a, m.b, a, s);

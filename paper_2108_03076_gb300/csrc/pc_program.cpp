@@ -591,6 +591,65 @@ pc_status analyse_program(const Program &p, int32_t t_now, int32_t n_dates, int3
 }
 
 // ---------------------------------------------------------------------------
+// cutPayoff (Sec. 4.1) on the bytecode
+// ---------------------------------------------------------------------------
+// Every payoff(t, p1', p2') becomes if(t < now, 0, payoff(t, p1', p2')): in
+// postfix, TEXPR t  NOW  LT  REAL 0.0  PAYOFF p1' p2' t  IF.  Every other
+// instruction is copied; 0.0 is appended to the literals unless present.
+pc_status cut_payoff(const uint32_t *w, size_t n, const double *consts, size_t n_consts,
+                     std::vector<uint32_t> &out, std::vector<double> &out_consts, std::string &err) {
+  out.clear();
+  out_consts.assign(consts, consts + n_consts);
+  uint32_t zero = uint32_t(n_consts);
+  for (size_t k = 0; k < n_consts; ++k)
+    if (consts[k] == 0.0 && !std::signbit(consts[k])) { zero = uint32_t(k); break; }
+  bool zero_used = false;
+  auto time_len = [&](size_t at, size_t &len) -> bool {
+    if (at >= n) return false;
+    const uint32_t c = w[at];
+    if (c == 0 || c > 16 || at + 1 + c > n) return false;
+    len = 1 + c;
+    return true;
+  };
+  for (size_t i = 0; i < n;) {
+    const uint32_t op = w[i] & 0xffu;
+    size_t len = 1, tl = 0;
+    switch (op) {
+      case PC_OP_REAL: case PC_OP_BOOL: case PC_OP_NAT: case PC_OP_NOW:
+      case PC_OP_NEG: case PC_OP_NOT: case PC_OP_ADD: case PC_OP_SUB: case PC_OP_MULT: case PC_OP_DIV:
+      case PC_OP_LT: case PC_OP_LE: case PC_OP_EQ: case PC_OP_AND: case PC_OP_OR: case PC_OP_MAX:
+      case PC_OP_MIN: case PC_OP_IF:
+        break;
+      case PC_OP_TEXPR: case PC_OP_MODEL: case PC_OP_LOOPIF:
+        if (!time_len(i + 1, tl)) { err = "truncated time expression"; return PC_EBYTECODE; }
+        len = 1 + tl;
+        break;
+      case PC_OP_PAYOFF: {
+        if (!time_len(i + 3, tl)) { err = "truncated payoff"; return PC_EBYTECODE; }
+        const uint32_t *t = w + i + 3;
+        out.push_back(PC_OP_TEXPR);
+        out.insert(out.end(), t, t + tl);
+        out.push_back(PC_OP_NOW);
+        out.push_back(PC_OP_LT);
+        out.push_back(PC_OP_REAL | (zero << 8));
+        zero_used = true;
+        out.insert(out.end(), w + i, w + i + 3 + tl);
+        out.push_back(PC_OP_IF);
+        i += 3 + tl;
+        continue;
+      }
+      default:
+        err = "bad opcode " + std::to_string(op) + " at word " + std::to_string(i);
+        return PC_EBYTECODE;
+    }
+    out.insert(out.end(), w + i, w + i + len);
+    i += len;
+  }
+  if (zero_used && zero == n_consts) out_consts.push_back(0.0);
+  return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Text assembler
 // ---------------------------------------------------------------------------
 namespace {

@@ -213,6 +213,15 @@ struct PriceArgs {
   int32_t greek_label;      // sensitivity kernel: the underlying g of the tangents
 };
 
+// The adjoint sensitivity kernel's tape (pc_adjoint.cuh): one region per
+// resident warp of the launch, entry e of lane l at [e * 32 + l].
+struct TapeArgs {
+  float4 *part;   // [warp][emax][32]: (p1 of both paths, p2 of both paths)
+  float2 *adj;    // [warp][emax][32]: adjoints of both paths
+  int2 *ids;      // [warp][emax]: input entries (in1, in2); a leaf: in1 = -2 - label
+  int32_t emax;   // entries per warp region
+};
+
 // Reduction scratch "control" block (zero between launches; every launch
 // leaves it zero): 64-bit counters at byte 0 (next tile, finished blocks,
 // finished chunks), 32-bit per-chunk tile counters at kChunkCountOff, and

@@ -250,13 +250,24 @@ def basket_call_greeks(n_paths: int = 1 << 20) -> Workload:
                     PATH_SEED_BASE + 4, 1.0)
 
 
+def daily_barrier_greeks(n_paths: int = 1 << 20) -> Workload:
+    """The daily barrier contract on four correlated GBMs (S0 = 1, sigma
+    drawn as above, pairwise corr 0.5, 365 daily dates): delta and vega of
+    four underlyings, the knock-out decisions held fixed."""
+    d = 4
+    mk = MarketSpec([1.0] * d, draw_sigmas(d), const_corr(d, 0.5), 0.03, list(range(1, 366)))
+    return Workload("greeks_daily_barrier_4u_365d", mk, barrier_ladder_text(mk.S0), [365], n_paths,
+                    PATH_SEED_BASE + 5, 1.0)
+
+
 ALL = {
     "european_call_1u_1d": european_call,
     "worst_of_autocall_3u_5d": worst_of_autocall,
     "daily_barrier_3u_365d": daily_barrier,
     "reverse_asian_2u_300d": reverse_asian,
 }
-GREEKS = {"greeks_basket_call_3u_5d": basket_call_greeks}
+GREEKS = {"greeks_basket_call_3u_5d": basket_call_greeks,
+          "greeks_daily_barrier_4u_365d": daily_barrier_greeks}
 
 
 # ---------------------------------------------------------------------------
