@@ -1,10 +1,11 @@
 #!/usr/bin/env python
 """Benchmark of the fused payoff-expression Monte Carlo engine.
 
-One step prices one contract of the selected workload (default: the
-worst-of autocallable note, 3 correlated GBM underlyings, 5 annual dates,
-2^20 paths): Philox normals -> Brownian bridge -> correlated GBM -> payoff
-bytecode -> mean / variance, all in one kernel launch.
+One step prices one contract of the selected workload (default: the daily
+knock-out barrier on the worst-of, 3 correlated GBM underlyings, 365 daily
+dates, 2^22 paths -- the largest single-GPU configuration): Philox normals
+-> Brownian bridge -> correlated GBM -> payoff bytecode -> mean / variance,
+all in one kernel launch.
 
 Prints one JSON line (rank 0):
   value   -- path-date evaluations per second over all ranks, kernel time
@@ -16,7 +17,9 @@ Prints one JSON line (rank 0):
   roofline, cpu_baseline (the FP64 oracle on host cores), clocks, ...
 ``--impl reference`` times the oracle instead (the reference arm).
 Multi-GPU (torchrun): each rank prices its own disjoint path range of the
-same contract (no data-path collective; weak scaling).
+same contract (no data-path collective; weak scaling); after the timed
+region the ranks' (sum, sum of squares, n) are merged in rank order on the
+host (merge.allgather_sums over a gloo group) and the merged price printed.
 """
 from __future__ import annotations
 
@@ -54,6 +57,8 @@ GREEKS_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
 JIT_GREEKS_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
                    for f in ("pc_types.h", "pc_device.cuh", "pc_greeks.cuh", "pc_greeks_state.inc",
                              "pc_greeks_ops.inc")]
+ADJOINT_SRCS = [os.path.join(ROOT, "paper_2108_03076_gb300", "csrc", f)
+                for f in ("pc_adjoint.cu", "pc_adjoint.cuh", "pc_device.cuh", "pc_types.h")]
 PORTFOLIO = "portfolio_1024"
 LEARNED = "learned_cv_worst_of_autocall"
 PORTFOLIO_SEED = 0x5EED0004
@@ -168,6 +173,7 @@ def measured_peaks() -> dict:
 
 PROFILED = {  # kernel kind: (profiles/ file prefix, sources, specialised-kernel kind or None)
     "interpreter": ("price_kernel", KERNEL_SRCS, None),
+    "adjoint": ("adjoint_kernel", ADJOINT_SRCS, None),
     "specialised": ("jit_price_kernel", JIT_SRCS, 0),
     "greeks": ("greeks_kernel", GREEKS_SRCS, None),
     "greeks_specialised": ("jit_greeks_kernel", JIT_GREEKS_SRCS, 32),
@@ -311,12 +317,15 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="worst_of_autocall_3u_5d",
+    ap.add_argument("--workload", default="daily_barrier_3u_365d",
                     choices=sorted(W.ALL) + sorted(W.GREEKS) + [PORTFOLIO, LEARNED])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--interpret", action="store_true",
                     help="time the interpreting kernel instead of the contract's specialised kernel")
+    ap.add_argument("--paths", type=int, default=0,
+                    help="price this many paths instead of the workload's own count (small profiling runs; "
+                         "the line's config records it)")
     args = ap.parse_args()
     if args.workload == PORTFOLIO:
         return run_portfolio(args)
@@ -324,7 +333,7 @@ def main():
         return run_learned(args)
     if args.workload in W.GREEKS:
         return run_greeks(args)
-    w = W.ALL[args.workload]()
+    w = W.ALL[args.workload](args.paths) if args.paths > 0 else W.ALL[args.workload]()
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -401,6 +410,34 @@ def main():
             ims.append(a.elapsed_time(b))
         interp_ms = statistics.median(ims)
         pc.pc_set_jit(ctx, True)
+    # cutPayoff (Sec. 4.1) of the same contract priced at now = 0: every
+    # payoff guarded by if(t < now, 0, .) -- the paper's "-Cut" timings
+    cw, ck = pc.pc_cut_payoff(words, consts)
+    kcut = pc.pc_load_payoff(ctx, cw, ck, w.tparams, 0, 1)
+    if not args.interpret:
+        pc.pc_jit_compile(model, kcut)
+    cut_out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    cms = []
+    for i in range(3 + max(3, min(args.steps, 20))):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pc.pc_price_async(model, kcut, w.n_paths, offset, w.seed, 0, cut_out.data_ptr())
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            cms.append(a.elapsed_time(b))
+    cut_ms = statistics.median(cms)
+    cut_same = bool(np.array_equal(cut_out.cpu().numpy()[:3], sums[:3]))
+    pc.pc_contract_destroy(kcut)
+    merged = None
+    if ws > 1:
+        from paper_2108_03076_gb300 import merge
+        gloo = dist.new_group(backend="gloo")
+        tot = merge.allgather_sums(np.asarray(sums[:3]), group=gloo)[0]
+        mp_, mse = merge.estimate(tot)
+        merged = {"price": mp_, "stderr": mse, "n_paths": int(tot[2]),
+                  "note": "ranks' (sum, sum of squares, n) merged in rank order over gloo"}
     mean = sums[0] / w.n_paths
     var = max(0.0, (sums[1] - w.n_paths * mean * mean) / (w.n_paths - 1))
 
@@ -465,6 +502,11 @@ def main():
                        "hbm_bytes": int(linfo.hbm_window_bytes),
                        "bytes_written_per_path_date": int(linfo.window_bytes_written_per_path_date)},
             "interpreter_ms_per_step": interp_ms, "specialised_compile_s": jit_s,
+            "cut_payoff": {"ms_per_step": cut_ms, "overhead": cut_ms / (1e3 * t_dev / args.steps) - 1.0,
+                           "sums_equal_uncut": cut_same,
+                           "note": "cutPayoff (Sec. 4.1) of the contract, loaded once, priced at now = 0 "
+                                   "(Table 1's -Cut column): median of launches after 3 warm-up"},
+            "merged": merged,
             "contracts_per_sec_at_1e-4_rel_se": contracts_per_s,
             "price": mean, "stderr": math.sqrt(var / w.n_paths),
             "paths_for_1e-4_rel_se": paths_needed,
@@ -768,7 +810,7 @@ def greeks_oracle_rate(w, budget_s: float) -> tuple:
 
 
 def run_greeks(args):
-    w = W.GREEKS[args.workload]()
+    w = W.GREEKS[args.workload](args.paths) if args.paths > 0 else W.GREEKS[args.workload]()
     spec = w.market
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -829,22 +871,46 @@ def run_greeks(args):
             b.record(stream)
             torch.cuda.synchronize()
             ms.append(a.elapsed_time(b))
-    t_step = statistics.median(ms) / 1e3
+    t_tan = statistics.median(ms) / 1e3
     price, delta, vega, se = res
+    # the adjoint: every underlying's delta and vega from one launch
+    v = 1 + 2 * d
+    adj_out = torch.zeros(2 * v + 1, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        pc.pc_greeks_adjoint_async(model, contract, w.n_paths, 0, w.seed, 0, adj_out.data_ptr())
+    torch.cuda.synchronize()
+    ams = []
+    with ClockSampler(local) as clk:
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pc.pc_greeks_adjoint_async(model, contract, w.n_paths, 0, w.seed, 0, adj_out.data_ptr())
+            b.record(stream)
+            torch.cuda.synchronize()
+            ams.append(a.elapsed_time(b))
+    t_step = statistics.median(ams) / 1e3
+    sums = adj_out.cpu().numpy()
+    adj_mean = sums[0:2 * v:2] / w.n_paths
+    adj_se = np.sqrt(np.maximum(0.0, (sums[1:2 * v:2] - w.n_paths * adj_mean ** 2) / (w.n_paths - 1))
+                     / w.n_paths)
+    # the two methods agree within their standard errors (same paths)
+    agree = bool(np.all(np.abs(adj_mean[1:] - np.concatenate([delta, vega]))
+                        <= 1e-3 * np.abs(adj_mean[1:]) + 3e-2 * adj_se[1:] + 1e-9))
     # end to end through the public API: load, sensitivities, drop
     t0 = time.perf_counter()
     for _ in range(5):
         k = pc.pc_load_payoff(ctx, words, consts, w.tparams, 0, 1)
-        pc.pc_greeks(model, k, w.n_paths, w.seed, d)
+        pc.pc_greeks_adjoint(model, k, w.n_paths, w.seed, d)
         pc.pc_contract_destroy(k)
     e2e_step = (time.perf_counter() - t0) / 5
-    path_dates = d * w.n_paths * spec.n          # every underlying's launch re-simulates the paths
+    path_dates = w.n_paths * spec.n
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(local)
     clock_hz = 1e6 * float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = props.multi_processor_count * 128 * clock_hz
     ops = alg_ops_per_path(pc.pc_model_query(model))
-    prof = profile_record(w, "greeks_specialised" if specialised else "greeks")
+    prof = profile_record(w, "adjoint")
     traffic = prof.get("dram_bytes_per_launch")
     if traffic is not None and prof.get("n_paths"):
         traffic = traffic * w.n_paths / prof["n_paths"]
@@ -852,27 +918,31 @@ def run_greeks(args):
         "metric": METRIC, "value": ws * path_dates / t_step, "unit": UNIT, "n_gpus": ws, "steps": steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**greeks_config(w, ws),
-                   "kernel": "specialised to the program (run-time compiled, NVRTC)" if specialised
-                   else "interpreter"},
-        "interpreter_ms_per_step": interp_ms,
-        "value_note": "path-dates per second, each of the d tangent launches (delta and vega of one "
-                      "underlying) counted",
-        "price": price, "delta": list(delta), "vega": list(vega), "stderr": list(se),
-        "gpu_launches": steps * d,
+        "config": {**greeks_config(w, ws), "kernel": "adjoint (interpreter, one launch)"},
+        "value_note": "path-dates per second with the price and every underlying's delta and vega "
+                      "(one adjoint launch per step)",
+        "price": float(adj_mean[0]), "delta": list(adj_mean[1:1 + d]), "vega": list(adj_mean[1 + d:]),
+        "stderr": list(adj_se),
+        "tangent": {"ms_per_step": 1e3 * t_tan, "launches_per_step": d,
+                    "kernel": "specialised to the program (run-time compiled, NVRTC)" if specialised
+                    else "interpreter",
+                    "interpreter_ms_per_step": interp_ms, "value": ws * path_dates / t_tan,
+                    "delta": list(delta), "vega": list(vega), "agrees_with_adjoint": agree},
+        "adjoint_speedup_over_tangent": t_tan / t_step,
+        "gpu_launches": steps,
         "e2e": {"value": ws * path_dates / e2e_step, "unit": UNIT,
                 "h2d_bytes_per_step": int(words.nbytes + consts.nbytes + 4 * len(w.tparams)),
-                "d2h_bytes_per_step": 8 * (2 + 4 * d),
-                "note": "pc_load_payoff + pc_greeks + pc_contract_destroy per step, host wall clock"},
-        "roofline": {"bound": "alu", "achieved": d * ops["ops"] * w.n_paths / t_step / 1e12,
+                "d2h_bytes_per_step": 8 * (2 * v + 1),
+                "note": "pc_load_payoff + pc_greeks_adjoint + pc_contract_destroy per step, host wall clock"},
+        "roofline": {"bound": "alu", "achieved": ops["ops"] * w.n_paths / t_step / 1e12,
                      "peak": peak_ops / 1e12, "unit": "Tops/s",
-                     "frac": d * ops["ops"] * w.n_paths / t_step / peak_ops, "traffic": traffic,
+                     "frac": ops["ops"] * w.n_paths / t_step / peak_ops, "traffic": traffic,
                      "ncu_max_pipe": prof.get("ncu_max_pipe"),
                      "ncu_max_pipe_frac": prof.get("ncu_max_pipe_frac"),
                      "ncu_issue_active": prof.get("ncu_issue_active"),
                      "alg_ops_per_path": ops["ops"],
-                     "note": "path generation of each tangent launch counted (the tangent arithmetic "
-                             "is not: a lower bound)",
+                     "note": "path generation counted once (the adjoint tape and sweep are not: a "
+                             "lower bound)",
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 lanes x "
                                    f"{clock_hz / 1e6:.0f} MHz issue"},
         "clocks": clk.summary(),
@@ -891,7 +961,8 @@ def run_greeks(args):
 
 def greeks_config(w, ws) -> dict:
     return {"workload": w.name, "n_paths": w.n_paths, "n_dates": w.market.n, "underlyings": w.market.d,
-            "sensitivities": "pathwise delta and vega of every underlying (tangent mode, one launch each)",
+            "sensitivities": "pathwise delta and vega of every underlying (adjoint: one launch; "
+                             "tangent mode, one launch per underlying, timed beside it)",
             "seed": w.seed, "parallelism": f"replicas x{ws}",
             "l2": "flushed between steps by a 256 MiB device write"}
 

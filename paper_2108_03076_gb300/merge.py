@@ -36,18 +36,19 @@ def estimate(sums: Sequence[float]) -> Tuple[float, float]:
     return mean, math.sqrt(var / n)
 
 
-def allgather_sums(local: np.ndarray, timeout_s: float = 30.0) -> np.ndarray:
-    """Merge per-rank triples over the default torch.distributed process
-    group: every rank contributes `local` ([k, 3] for k contracts) and gets
-    the fixed-order merge [k, 3].  Before the exchange each rank checks in
-    through the group's store; a rank that has not checked in within
-    `timeout_s` makes every waiting rank raise RuntimeError instead of
-    blocking in the collective."""
+def allgather_sums(local: np.ndarray, timeout_s: float = 30.0, group=None) -> np.ndarray:
+    """Merge per-rank triples over a torch.distributed process group with a
+    CPU backend (the default group, or `group`, e.g. a gloo group beside an
+    NCCL default): every rank contributes `local` ([k, 3] for k contracts)
+    and gets the fixed-order merge [k, 3].  Before the exchange each rank
+    checks in through the default store; a rank that has not checked in
+    within `timeout_s` makes every waiting rank raise RuntimeError instead
+    of blocking in the collective."""
     import torch
     import torch.distributed as dist
 
     local = np.atleast_2d(np.asarray(local, dtype=np.float64))
-    ws, rank = dist.get_world_size(), dist.get_rank()
+    ws, rank = dist.get_world_size(group), dist.get_rank(group)
     store = _store()
     key = f"pc_merge_{_next_round()}"
     store.set(f"{key}/{rank}", "1")
@@ -57,7 +58,7 @@ def allgather_sums(local: np.ndarray, timeout_s: float = 30.0) -> np.ndarray:
         raise RuntimeError(f"merge: a rank did not check in within {timeout_s} s") from e
     t = torch.from_numpy(local.copy())
     parts = [torch.zeros_like(t) for _ in range(ws)]
-    dist.all_gather(parts, t)
+    dist.all_gather(parts, t, group=group)
     return np.stack([merge_sums([p.numpy()[i] for p in parts]) for i in range(local.shape[0])])
 
 
