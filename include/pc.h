@@ -609,6 +609,15 @@ typedef struct pc_cv_desc {
   int32_t use_gamma;         /* 1: include M2 (pc_cv_grid: 0)                */
 } pc_cv_desc;
 
+/* Training labels of the learned control variate from the engine's prices
+ * of sampled states: row c of out (width floats, host) = the price at the
+ * state, then the central-difference hedge ratios on common random numbers
+ * (P(S_i (1 + bump)) - P(S_i (1 - bump))) / (2 bump S_i), i < d, then zeros.
+ * prices: [(2d + 1) x n] doubles, row 0 at the state, rows 1 + 2i and 2 + 2i
+ * with S_i bumped up and down; spots: [n x d].  Errors: PC_EINVAL. */
+pc_status pc_cv_labels(size_t n, int32_t d, const double *prices, const double *spots, double bump,
+                       int32_t width, float *out);
+
 /* Fill d, n, grid, lo and h from the model: axis i at date k is centred on
  * ln S0_i + (r - sigma_i^2 / 2) tau_k with half-width width_sd sigma_i
  * sqrt(tau_k).  The caller sets ref, the levels, coupon (and delta0 when it

@@ -119,6 +119,7 @@ _SIGS = {
     "pc_price_noalloc": [VP, VP, U64, U64, U64, U32, VP],
     "pc_cut_payoff": [PU32, SZ, PD, SZ, PU32, SZ, C.POINTER(SZ), PD, SZ, C.POINTER(SZ)],
     "pc_set_timeout": [VP, DBL],
+    "pc_cv_labels": [SZ, I32, PD, PD, DBL, I32, PF],
     "pc_debug_fail_allocations": [VP, I32],
     "pc_debug_set_status": [VP, I32],
     "pc_debug_mlp_withhold_tma": [VP, I32],
@@ -521,6 +522,17 @@ def pc_cv_grid(model: int, grid: int, width_sd: float, ref=(1.0, 1.0, 1.0), call
         desc.ref[i] = float(ref[i]) if i < len(ref) else 1.0
     desc.call_level, desc.ki_level, desc.coupon = float(call_level), float(ki_level), float(coupon)
     return desc
+
+
+def pc_cv_labels(prices, spots, bump: float, width: int) -> np.ndarray:
+    """Labels [n, width] (float32): price, central-difference hedge ratios, zeros."""
+    p = _arr(prices, np.float64)
+    S = _arr(spots, np.float64)
+    n, d = S.shape
+    out = np.zeros((n, width), np.float32)
+    _check(lib().pc_cv_labels(n, d, _ptr(p, C.c_double), _ptr(S, C.c_double), float(bump), int(width),
+                              _ptr(out, C.c_float)))
+    return out
 
 
 def pc_cv_table_size(desc: CvDesc) -> int:

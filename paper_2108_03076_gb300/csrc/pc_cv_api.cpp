@@ -152,6 +152,23 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
 
 extern "C" {
 
+pc_status pc_cv_labels(size_t n, int32_t d, const double *prices, const double *spots, double bump,
+                       int32_t width, float *out) {
+  if (!prices || !spots || !out) return fail(PC_EINVAL, "null argument");
+  if (d < 1 || d > PC_MAX_UNDERLYINGS || width < 1 + d) return fail(PC_EINVAL, "need 1 <= d <= 4 and width >= 1 + d");
+  if (!(bump > 0.0)) return fail(PC_EINVAL, "bump must be > 0");
+  for (size_t c = 0; c < n; ++c) {
+    float *row = out + c * size_t(width);
+    row[0] = float(prices[c]);
+    for (int i = 0; i < d; ++i) {
+      const double up = prices[(1 + 2 * size_t(i)) * n + c], dn = prices[(2 + 2 * size_t(i)) * n + c];
+      row[1 + i] = float((up - dn) / (2.0 * bump * spots[c * size_t(d) + i]));
+    }
+    for (int j = 1 + d; j < width; ++j) row[j] = 0.f;
+  }
+  return PC_OK;
+}
+
 pc_status pc_cv_grid(const pc_model *m, int32_t grid, float width_sd, pc_cv_desc *c) {
   if (!m || !c) return fail(PC_EINVAL, "null argument");
   if (m->H.d > kCvMaxD || m->H.n > kCvMaxDates) return fail(PC_ELIMIT, "control variate: d <= 3, n <= 32");

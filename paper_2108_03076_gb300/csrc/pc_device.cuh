@@ -418,6 +418,70 @@ __device__ __forceinline__ float2 fused_value(const uint4 &I, int o, const float
   return v;
 }
 
+// The same instruction as a test only (X_LANY, or X_LRED with a compare),
+// as booleans for the lane's two paths: the whole-loop barrier op decides
+// its latches from it without the 0/1 value bits.
+template <int D, bool GW = false>
+__device__ __forceinline__ void fused_test(const uint4 &I, int o, const float *pool, const float2 *R,
+                                           const ModelDev &m, const Layout &lay, bool &t0, bool &t1) {
+  const uint32_t A = I.x >> 8;
+  const int n = int((A >> 8) & 3u) + 1, kind = int((A >> 2) & 3u), code = int((A >> 4) & 7u);
+  const bool any = (I.x & 0xffu) == X_LANY, conj = (A & 1u) != 0;
+  const int rop = int(A & 3u);
+  const float k = __uint_as_float(I.w);
+  const int base = (o & (lay.win - 1)) * D;
+  auto cmp = [&](float v) {
+    return code == 1 ? v < k : code == 2 ? v <= k : code == 3 ? k < v : k <= v;
+  };
+  float2 v = make_float2(0.f, 0.f);
+  bool b0 = false, b1 = false;
+  for (int i = 0; i < n; ++i) {
+    int l = int(A >> (10 + 2 * i)) & 3;
+    l = l < D ? l : 0;
+    float2 s;
+    if (o > 0) {
+      s = win_load<GW>(R, lay, base + l);
+    } else {
+      const float sv = __ldg(m.sval + (o + m.n_hist) * D + l);
+      s = make_float2(sv, sv);
+    }
+    if (kind == 1) {
+      const float c = pool[I.z + i];
+      s = make_float2(__fmul_rn(s.x, c), __fmul_rn(s.y, c));
+    } else if (kind == 2) {
+      const float c = pool[I.z + i];
+      s = make_float2(__fdiv_rn(s.x, c), __fdiv_rn(s.y, c));
+    }
+    if (any) {
+      const bool p0 = cmp(s.x), p1 = cmp(s.y);
+      if (i == 0) {
+        b0 = p0;
+        b1 = p1;
+      } else if (conj) {
+        b0 = b0 && p0;
+        b1 = b1 && p1;
+      } else {
+        b0 = b0 || p0;
+        b1 = b1 || p1;
+      }
+    } else if (i == 0) {
+      v = s;
+    } else if (rop == 0) {
+      v = make_float2(fminf(v.x, s.x), fminf(v.y, s.y));
+    } else if (rop == 1) {
+      v = make_float2(fmaxf(v.x, s.x), fmaxf(v.y, s.y));
+    } else {
+      v = make_float2(__fadd_rn(v.x, s.x), __fadd_rn(v.y, s.y));
+    }
+  }
+  if (!any) {
+    b0 = cmp(v.x);
+    b1 = cmp(v.y);
+  }
+  t0 = b0;
+  t1 = b1;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);

@@ -27,7 +27,7 @@ from typing import List, Sequence, Tuple
 import numpy as np
 
 from . import (pc_assemble, pc_batch_create, pc_batch_destroy, pc_batch_launch, pc_batch_results,
-               pc_contract_destroy, pc_cv_beta, pc_cv_grid, pc_cv_table_size, pc_cv_tables, pc_load_payoff,
+               pc_contract_destroy, pc_cv_beta, pc_cv_grid, pc_cv_labels, pc_cv_table_size, pc_cv_tables, pc_load_payoff,
                pc_mlp_create, pc_mlp_destroy, pc_mlp_forward, pc_mlp_train, pc_model_create,
                pc_model_destroy, pc_price_cv)
 
@@ -168,11 +168,7 @@ def engine_training_set(ctx: int, n_samples: int, paths: int, seed: int, bump: f
                 pc_model_destroy(m)
         for kc in contracts:
             pc_contract_destroy(kc)
-    S = np.exp(st["lnS"])
-    y = np.zeros((n_samples, 5))
-    y[:, 0] = prices[0]
-    for i in range(D):
-        y[:, 1 + i] = (prices[1 + 2 * i] - prices[2 + 2 * i]) / (2.0 * bump * S[:, i])
+    y = pc_cv_labels(np.stack(prices), np.exp(st["lnS"]), bump, 5)
     x = features(st["lnS"], st["ki"], st["k"], N_DATES, st["sig"], st["rho"], st["r"],
                  np.ones(n_samples), st["coupon"], st["call"], st["kil"])
     return TrainingSet(x.astype(np.float32), y.astype(np.float32), paths)
