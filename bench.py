@@ -209,10 +209,16 @@ def profile_record(w, kind: str) -> dict:
 
 
 def profile_traffic(w, kind: str):
-    """DRAM bytes per launch and the paths that launch ran, from the
-    committed ncu summary, if it was taken on the current kernel source."""
+    """DRAM bytes of one launch of the workload, from the committed ncu
+    summary if it was taken on the current kernel source (else None).  A
+    summary taken on fewer paths is scaled by the paths, unless it records
+    that the kernel's traffic does not grow with them ("traffic": "fixed":
+    only the program, model tables and partial sums reach DRAM)."""
     p = profile_record(w, kind)
-    return p.get("dram_bytes_per_launch"), p.get("n_paths")
+    b, n = p.get("dram_bytes_per_launch"), p.get("n_paths")
+    if b is None or not n or p.get("traffic") == "fixed":
+        return b
+    return b * w.n_paths / n
 
 
 def oracle_run(w, n_paths: int, offset: int = 0):
@@ -477,10 +483,8 @@ def main():
     launch_s = t_dev / args.steps
     achieved = ops["ops"] * w.n_paths / launch_s
     kind = "interpreter" if args.interpret or info.n_insn > pc.JIT_MAX_INSNS else "specialised"
-    traffic, traffic_paths = profile_traffic(w, kind)
+    traffic = profile_traffic(w, kind)
     prof = profile_record(w, kind)
-    if traffic is not None and traffic_paths:
-        traffic = traffic * w.n_paths / traffic_paths
 
     if rank == 0:
         line = {
@@ -911,9 +915,7 @@ def run_greeks(args):
     peak_ops = props.multi_processor_count * 128 * clock_hz
     ops = alg_ops_per_path(pc.pc_model_query(model))
     prof = profile_record(w, "adjoint")
-    traffic = prof.get("dram_bytes_per_launch")
-    if traffic is not None and prof.get("n_paths"):
-        traffic = traffic * w.n_paths / prof["n_paths"]
+    traffic = profile_traffic(w, "adjoint")
     line = {
         "metric": METRIC, "value": ws * path_dates / t_step, "unit": UNIT, "n_gpus": ws, "steps": steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",

@@ -529,6 +529,8 @@ def pc_cv_labels(prices, spots, bump: float, width: int) -> np.ndarray:
     p = _arr(prices, np.float64)
     S = _arr(spots, np.float64)
     n, d = S.shape
+    if p.size != (2 * d + 1) * n:
+        raise ValueError(f"prices: need {(2 * d + 1) * n} values ([2d + 1, n]), got {p.size}")
     out = np.zeros((n, width), np.float32)
     _check(lib().pc_cv_labels(n, d, _ptr(p, C.c_double), _ptr(S, C.c_double), float(bump), int(width),
                               _ptr(out, C.c_float)))

@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 
+#include "pc_device.cuh"
 #include "pc_mlp.h"
 
 namespace pc {
@@ -182,34 +183,14 @@ __global__ void to_bf16_kernel(const float *x, size_t n, int fin, __nv_bfloat16 
   }
 }
 
-__device__ __forceinline__ uint32_t mulhilo(uint32_t a, uint32_t b, uint32_t &hi) {
-  hi = __umulhi(a, b);
-  return a * b;
-}
-
-// Philox4x32-10 (Salmon et al., SC'11), first output word only.
-__device__ uint32_t philox_x(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
-  for (int i = 0; i < 10; ++i) {
-    uint32_t h0, h1;
-    const uint32_t l0 = mulhilo(0xD2511F53u, c0, h0), l1 = mulhilo(0xCD9E8D57u, c2, h1);
-    const uint32_t n0 = h1 ^ c1 ^ k0, n2 = h0 ^ c3 ^ k1;
-    c0 = n0;
-    c1 = l1;
-    c2 = n2;
-    c3 = l0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  return c0;
-}
-
 __global__ void gather_kernel(const float *x, const float *t, size_t n_data, int fin, int fout,
                               const uint64_t *step, uint32_t s0, uint32_t s1, size_t batch,
                               __nv_bfloat16 *X, int ldx, float *T) {
   const size_t b = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
   if (b >= batch) return;
   const uint64_t st = *step;
-  const uint32_t u = philox_x(uint32_t(b), uint32_t(b >> 32), uint32_t(st), uint32_t(st >> 32), s0, s1);
+  // the first word of Philox4x32-10 at counter (b, step), key (s0, s1)
+  const uint32_t u = philox(make_uint4(uint32_t(b), uint32_t(b >> 32), uint32_t(st), uint32_t(st >> 32)), s0, s1).x;
   const size_t src = size_t(u) % n_data;
   for (int c = 0; c < ldx; ++c) X[b * ldx + c] = __float2bfloat16_rn(c < fin ? x[src * fin + c] : 0.f);
   for (int c = 0; c < fout; ++c) T[b * fout + c] = t[src * fout + c];
