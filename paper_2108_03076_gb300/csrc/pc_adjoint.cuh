@@ -91,7 +91,7 @@ __device__ float2 eval_adjoint(const uint4 *P, const float *pool, float2 *R, con
   const ModelDev &m = a.m;
   const Layout &lay = a.lay;
   PathState<D> ps;
-  path_state_init<D>(ps);
+  path_state_init<D>(ps, R, lay);
   const int t_now = m.t_now;
   int pc = 0, sp = 0, t0 = 0;
   float2 tos = make_float2(0.f, 0.f);

@@ -328,6 +328,32 @@ pc_status run_greeks(const pc_model *m, const pc_contract *k, uint64_t n_paths, 
   return PC_OK;
 }
 
+// The specialised evaluator keeps its operand stack in registers: drop the
+// stack words from the per-thread shared region of the launch.  Returns the
+// launch's dynamic shared memory.
+size_t jit_layout(const pc_contract *k, Launch &L) {
+  Layout &lay = L.args.lay;
+  const int shift = lay.off_bstack;
+  lay.stack = 0;
+  lay.off_bstack -= shift;
+  lay.off_cache -= shift;
+  lay.off_win -= shift;
+  lay.words -= shift;
+  return price_smem_bytes(k->prog.code.size(), pool_padded(k->prog), lay.words, L.block);
+}
+
+// Resident blocks per SM (of kBlock threads, the block the kernel's bound
+// is written for) the specialised pricing kernel's register bound is set
+// for: the default, or fewer when the launch's shared memory allows no more
+// warps (the kernel may then use the registers those blocks leave).  The
+// kernel's own static shared memory is a few words (kJitStaticSmem bounds it).
+int jit_min_blocks(const pc_ctx *c, size_t smem, int block) {
+  if (c->sm_smem <= 0) return kJitMinBlocks;
+  const size_t per = smem + kJitStaticSmem + size_t(c->smem_reserve);
+  const int warps = int(size_t(c->sm_smem) / per) * (block / 32);
+  return std::max(1, std::min(kJitMinBlocks, warps / (kBlock / 32)));
+}
+
 pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, uint64_t offset,
                     uint64_t seed, uint32_t stream, double *d_out, float *d_payoffs) {
   Launch L;
@@ -346,20 +372,11 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
   if (c->jit && jit_eligible(k)) {
     // the contract's run-time specialised kernel (same arguments and shape)
     cudaKernel_t jk = nullptr;
+    const size_t smem = jit_layout(k, L);
     s = jit_kernel(k, m->H.d, (d_payoffs != nullptr ? kJitPriceWrite : kJitPrice) | (L.hbm_window ? kJitHbm : 0),
-                   L.block, jk);
+                   L.block, jk, jit_min_blocks(c, smem, L.block));
     if (s != PC_OK) return s;
     const void *kern = reinterpret_cast<const void *>(jk);
-    // the specialised evaluator keeps its operand stack in registers: drop
-    // the stack words from the per-thread shared region
-    Layout &lay = L.args.lay;
-    const int shift = lay.off_bstack;
-    lay.stack = 0;
-    lay.off_bstack -= shift;
-    lay.off_cache -= shift;
-    lay.off_win -= shift;
-    lay.words -= shift;
-    const size_t smem = price_smem_bytes(k->prog.code.size(), pool_padded(k->prog), lay.words, L.block);
     int nb = 0;
     CU(jit_occupancy(c, kern, L.block, smem, nb), "jit occupancy");
     if (nb < 1) return fail(PC_ELIMIT, "specialised kernel cannot be resident");
@@ -512,6 +529,8 @@ pc_status pc_create(pc_ctx **out, int device, void *cuda_stream) {
   c->device = device;
   c->sm_count = prop.multiProcessorCount;
   c->max_smem = max_dynamic_smem();
+  CU(cudaDeviceGetAttribute(&c->sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device), "device attribute");
+  CU(cudaDeviceGetAttribute(&c->smem_reserve, cudaDevAttrReservedSharedMemoryPerBlock, device), "device attribute");
   if (const char *t = std::getenv("PC_TIMEOUT_S")) c->timeout_s = std::max(1.0, std::atof(t));
   cudaError_t e = cudaSuccess;
   if (cuda_stream) {
@@ -924,7 +943,9 @@ pc_status pc_jit_compile(const pc_model *m, const pc_contract *k) {
   if (s != PC_OK) return s;
   CU(cudaSetDevice(m->ctx->device), "cudaSetDevice");
   cudaKernel_t jk = nullptr;
-  return jit_kernel(k, m->H.d, kJitPrice | (L.hbm_window ? kJitHbm : 0), L.block, jk);
+  const size_t smem = jit_layout(k, L);
+  return jit_kernel(k, m->H.d, kJitPrice | (L.hbm_window ? kJitHbm : 0), L.block, jk,
+                    jit_min_blocks(m->ctx, smem, L.block));
 }
 
 pc_status pc_price_info(const pc_model *m, const pc_contract *k, uint64_t n_paths, pc_launch_info *info) {

@@ -187,8 +187,12 @@ struct PathState {
   int k;                        // ops run so far (the next op's number), warp-uniform
 };
 
+// A path's state at its start; the bottom slot of the bridge stack is
+// zeroed (the root op reads it with weight 0).
 template <int D>
-__device__ __forceinline__ void path_state_init(PathState<D> &ps) {
+__device__ __forceinline__ void path_state_init(PathState<D> &ps, float2 *R, const Layout &lay) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) SL(lay.off_bstack + i) = make_float2(0.f, 0.f);
 #pragma unroll
   for (int i = 0; i < D; ++i) ps.w[i] = make_float2(0.f, 0.f);
 #pragma unroll
@@ -263,11 +267,10 @@ __device__ __forceinline__ void node_normals(uint32_t k, const Rng2 &g, float2 (
   }
 }
 
-// A bridge op's weights as packed pairs and its flags (two 16-byte loads
-// through the read-only path: the address is the same in every lane).
+// A bridge op's weights as packed pairs (two 16-byte loads through the
+// read-only path: the address is the same in every lane).
 struct OpRegs {
   float2 wl, wr, sd;
-  uint32_t flags;
 };
 __device__ __forceinline__ OpRegs load_op(const BridgeOp *p) {
   const float4 *q = reinterpret_cast<const float4 *>(p);
@@ -276,7 +279,6 @@ __device__ __forceinline__ OpRegs load_op(const BridgeOp *p) {
   o.wl = make_float2(a.x, a.y);
   o.wr = make_float2(a.z, a.w);
   o.sd = make_float2(b.x, b.y);
-  o.flags = __float_as_uint(b.w) & 0xffffu;
   return o;
 }
 
@@ -291,34 +293,26 @@ __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev
                                          const float (&Bm)[D * D], const float (&S0)[D],
                                          const float *Lm = nullptr) {
   const int k1 = __ldg(m.date_ops + t + 1);  // ops of date t: [ps.k, k1)
-  if (ps.k == k1) {
-    --ps.bsp;
+  // Every op pushes its node; the date's own value (the last node, or one
+  // pushed on an earlier date when t has no op) is then popped as the new
+  // frontier value.  The root op has wl = wr = 0 and reads the bottom slot,
+  // zeroed at the path's start, as its right end.  (Branch-free: a push or
+  // keep decision per op, and a root test, cost register moves at the joins.)
+  for (; ps.k < k1; ++ps.k) {
+    const OpRegs op = load_op(m.ops + ps.k);
+    float2 z[D];
+    node_normals<D>(uint32_t(ps.k), g, ps.zc, z);
+    const int top = lay.off_bstack + max(ps.bsp - 1, 0) * D;
+    float2 nw[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) ps.w[i] = SL(lay.off_bstack + ps.bsp * D + i);
-  } else {
-    for (; ps.k < k1; ++ps.k) {
-      const OpRegs op = load_op(m.ops + ps.k);
-      float2 z[D];
-      node_normals<D>(uint32_t(ps.k), g, ps.zc, z);
-      float2 nw[D];
-      if (op.flags & BR_ROOT) {
+    for (int i = 0; i < D; ++i) nw[i] = fma_x2(op.wl, ps.w[i], fma_x2(op.wr, SL(top + i), mul_x2(op.sd, z[i])));
 #pragma unroll
-        for (int i = 0; i < D; ++i) nw[i] = mul_x2(op.sd, z[i]);
-      } else {
-        const int top = lay.off_bstack + (ps.bsp - 1) * D;
-#pragma unroll
-        for (int i = 0; i < D; ++i) nw[i] = fma_x2(op.wl, ps.w[i], fma_x2(op.wr, SL(top + i), mul_x2(op.sd, z[i])));
-      }
-      if (ps.k + 1 < k1) {
-#pragma unroll
-        for (int i = 0; i < D; ++i) SL(lay.off_bstack + ps.bsp * D + i) = nw[i];
-        ++ps.bsp;
-      } else {
-#pragma unroll
-        for (int i = 0; i < D; ++i) ps.w[i] = nw[i];
-      }
-    }
+    for (int i = 0; i < D; ++i) SL(lay.off_bstack + ps.bsp * D + i) = nw[i];
+    ++ps.bsp;
   }
+  --ps.bsp;
+#pragma unroll
+  for (int i = 0; i < D; ++i) ps.w[i] = SL(lay.off_bstack + ps.bsp * D + i);
   const int ws = (t & (lay.win - 1)) * D;
 #pragma unroll
   for (int i = 0; i < D; ++i) {

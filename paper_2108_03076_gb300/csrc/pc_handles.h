@@ -21,12 +21,17 @@
 // per-path payoffs; bit kJitHbm: the window of dates in HBM), and the
 // control-variate kernel (kJitCv + its kCv* mode bits).
 constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitHbm = 2, kJitCv = 16, kJitGreeks = 32;
+// resident blocks per SM the specialised pricing kernel's register bound is
+// set for by default (<= 72 registers at 128 threads: the fastest measured)
+constexpr int kJitMinBlocks = 7;
+constexpr size_t kJitStaticSmem = 256;  // bound on price_tiles' static shared memory
 
 struct JitEntry {
   std::vector<uint32_t> program;
   int d = 0;
   int kind = kJitPrice;
   int block = 0;  // the launch block the kernel is compiled for (its slot stride)
+  int min_blocks = 0;  // its launch bound's resident blocks per SM (0: the kernel's own)
   cudaLibrary_t lib = nullptr;
   cudaKernel_t kernel = nullptr;
 };
@@ -37,6 +42,8 @@ struct pc_ctx {
   bool own_stream = false;
   int sm_count = 0;
   int max_smem = 0;
+  int sm_smem = 0;       // shared memory per SM (bytes)
+  int smem_reserve = 0;  // shared memory the system reserves per resident block (bytes)
   double *d_res = nullptr;       // [8]: sum, sumsq, n, -, status word (int32 at d_res+4)
   double *d_gout = nullptr;      // [PC_MAX_UNDERLYINGS * 8]: sensitivity sums per underlying
   double *d_partials = nullptr;  // tile partials (scratch)
@@ -149,7 +156,9 @@ pc_status ensure_partials(pc_ctx *c, size_t doubles);
 // underlyings, a kernel kind (kJit*) and the launch's block size (the
 // per-thread slot stride, a constant in the compiled code); compiled on
 // first use, cached on the context by program content.
-pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKernel_t &out);
+// min_blocks: for pc_jit_price, the resident blocks per SM its launch bound
+// asks for (0: the default, 7); other kinds fix their own bound.
+pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKernel_t &out, int min_blocks = 0);
 // Programs of at most PC_JIT_MAX_INSNS instructions are specialised; the
 // launches of longer ones interpret them.
 bool jit_eligible(const pc_contract *k);

@@ -275,9 +275,12 @@ std::string generate(const Program &p, int d, int kind) {
       << "}\n";
     return o.str();
   }
-  // at least 7 resident 128-thread blocks (<= 72 registers): the fastest
-  // measured cap (autocall unchanged, daily barrier -7 %, 5 blocks slower)
-  o << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ", 7) pc_jit_price(const __grid_constant__ pc::PriceArgs a) {\n"
+  // resident 128-thread blocks per SM the register bound is set for
+  // (PC_MIN_BLOCKS, passed by the launcher: 7, <= 72 registers, unless the
+  // launch's shared memory already allows fewer, whose bound then leaves the
+  // kernel the registers those blocks can have)
+  o << "#ifndef PC_MIN_BLOCKS\n#define PC_MIN_BLOCKS " << kJitMinBlocks << "\n#endif\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ", PC_MIN_BLOCKS) pc_jit_price(const __grid_constant__ pc::PriceArgs a) {\n"
     << "  pc::price_tiles<pc::D, " << (kind & kJitPriceWrite ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
     << "      float2 *R, const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
     << "      const float (&S0)[pc::D]) { return pc::jit_eval(P, pool, R, a, g, live0, live1, Bm, S0); });\n"
@@ -298,7 +301,7 @@ pc_status nvrtc_fail(nvrtcResult r, nvrtcProgram prog, const char *what) {
 
 // NVRTC: the generated source and the embedded device headers to a cubin
 // for `arch` (e.g. "sm_103a").
-pc_status to_cubin(const Program &p, int d, int kind, int block, const std::string &arch,
+pc_status to_cubin(const Program &p, int d, int kind, int block, int min_blocks, const std::string &arch,
                    std::vector<char> &cubin) {
   const std::string src = generate(p, d, kind);
   nvrtcProgram prog = nullptr;
@@ -307,8 +310,9 @@ pc_status to_cubin(const Program &p, int d, int kind, int block, const std::stri
   if (r != NVRTC_SUCCESS) return nvrtc_fail(r, nullptr, "run-time compiler");
   const std::string a = "-arch=" + arch;
   const std::string stride = "-DPC_SLOT_STRIDE=" + std::to_string(block);
-  const char *opts[] = {a.c_str(), "-std=c++17", "-default-device", "-DPC_JIT", stride.c_str()};
-  r = nvrtcCompileProgram(prog, 5, opts);
+  const std::string bound = "-DPC_MIN_BLOCKS=" + std::to_string(min_blocks > 0 ? min_blocks : kJitMinBlocks);
+  const char *opts[] = {a.c_str(), "-std=c++17", "-default-device", "-DPC_JIT", stride.c_str(), bound.c_str()};
+  r = nvrtcCompileProgram(prog, 6, opts);
   if (r != NVRTC_SUCCESS) {
     pc_status s = nvrtc_fail(r, prog, "run-time compilation");
     nvrtcDestroyProgram(&prog);
@@ -323,13 +327,13 @@ pc_status to_cubin(const Program &p, int d, int kind, int block, const std::stri
   return PC_OK;
 }
 
-pc_status compile(const Program &p, int d, int kind, int block, int device, cudaLibrary_t &lib,
+pc_status compile(const Program &p, int d, int kind, int block, int min_blocks, int device, cudaLibrary_t &lib,
                   cudaKernel_t &kern) {
   cudaDeviceProp prop{};
   CU(cudaGetDeviceProperties(&prop, device), "device properties");
   std::vector<char> cubin;
-  pc_status s = to_cubin(p, d, kind, block, "sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a",
-                         cubin);
+  pc_status s = to_cubin(p, d, kind, block, min_blocks,
+                         "sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a", cubin);
   if (s != PC_OK) return s;
   CU(cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0), "module load");
   cudaError_t e = cudaLibraryGetKernel(&kern, lib, kind >= kJitGreeks ? "pc_jit_greeks"
@@ -349,7 +353,7 @@ namespace pc {
 
 bool jit_eligible(const pc_contract *k) { return k->prog.code.size() <= size_t(PC_JIT_MAX_INSNS); }
 
-pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKernel_t &out) {
+pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKernel_t &out, int min_blocks) {
   // the program's words: code, then pool bits
   std::vector<uint32_t> words;
   words.reserve(k->prog.code.size() * 4 + k->prog.pool.size());
@@ -372,7 +376,7 @@ pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKerne
   auto range = c->jit_cache.equal_range(h);
   for (auto it = range.first; it != range.second; ++it) {
     const JitEntry &E = it->second;
-    if (E.d == d && E.kind == kind && E.block == block && E.program == words) {
+    if (E.d == d && E.kind == kind && E.block == block && E.min_blocks == min_blocks && E.program == words) {
       out = E.kernel;
       return PC_OK;
     }
@@ -382,7 +386,8 @@ pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKerne
   E.d = d;
   E.kind = kind;
   E.block = block;
-  pc_status s = compile(k->prog, d, kind, block, c->device, E.lib, E.kernel);
+  E.min_blocks = min_blocks;
+  pc_status s = compile(k->prog, d, kind, block, min_blocks, c->device, E.lib, E.kernel);
   if (s != PC_OK) return s;
   out = E.kernel;
   c->jit_cache.emplace(h, std::move(E));
@@ -415,7 +420,7 @@ extern "C" pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_wor
   pc_status s = compile_program(bytecode, n_words, consts, n_consts, tparams, n_params, p1, p2, true, p, err);
   if (s != PC_OK) return fail(s, err);
   std::vector<char> cubin;
-  s = to_cubin(p, d, kind, kBlock, "sm_103a", cubin);
+  s = to_cubin(p, d, kind, kBlock, 0, "sm_103a", cubin);
   if (s != PC_OK) return s;
   *cubin_bytes = cubin.size();
   return PC_OK;

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kBlock) debug_paths_kernel(const __grid_consta
 #pragma unroll
   for (int i = 0; i < 20; ++i) g.rk[i] = rk.k[i];
   PathState<D> ps;
-  path_state_init<D>(ps);
+  path_state_init<D>(ps, R, lay);
   const size_t row = size_t(m.n) + 1;
   const bool has1 = i1 < n_paths;
   for (int l = 0; l < D; ++l) {

@@ -146,11 +146,11 @@ pc_status build_model(const pc_model_desc &desc, ModelHost &M, std::string &err)
       js.push_back(it->second);
       stk.push_back(nodes[it->second].m);
     }
+    // the kernel pushes every op's node and then pops the date's value, so
+    // it holds the schedule's stack including the date itself
+    depth_max = std::max(depth_max, int(stk.size()));
     stk.pop_back();
     cur = t;
-    // the kernel keeps the last op's result in registers instead of pushing
-    // it, so the stack it holds is the schedule's stack minus one
-    depth_max = std::max(depth_max, int(stk.size()));
     for (int j : js) {
       BridgeOp op{};
       const Node &nd = nodes[j];

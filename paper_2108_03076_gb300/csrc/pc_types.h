@@ -124,7 +124,7 @@ struct BridgeOp {
 static_assert(sizeof(BridgeOp) == 32, "BridgeOp layout: two 16-byte loads");
 
 enum : uint16_t {
-  BR_ROOT = 1,  // first node (last date): W = sd * z, no endpoint reads
+  BR_ROOT = 1,  // first node (last date): W = sd * z (its wl = wr = 0)
 };
 
 // Device image of a model (one allocation, offsets in bytes).
