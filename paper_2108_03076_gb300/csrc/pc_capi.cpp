@@ -328,9 +328,17 @@ pc_status run_greeks(const pc_model *m, const pc_contract *k, uint64_t n_paths, 
   return PC_OK;
 }
 
-// The specialised evaluator keeps its operand stack in registers: drop the
-// stack words from the per-thread shared region of the launch.  Returns the
-// launch's dynamic shared memory.
+// Kind bits of the launch's specialised pricing kernel beyond the variant:
+// the window of dates in HBM, or a window of one date (a program that reads
+// no date behind the frontier), which the kernel keeps in registers.
+int jit_window_kind(const Launch &L) {
+  if (L.hbm_window) return kJitHbm;
+  return L.args.lay.win == 1 ? kJitWinRegs : 0;
+}
+
+// The specialised evaluator keeps its operand stack in registers, and with
+// kJitWinRegs the window too: drop those words from the per-thread shared
+// region of the launch.  Returns the launch's dynamic shared memory.
 size_t jit_layout(const pc_contract *k, Launch &L) {
   Layout &lay = L.args.lay;
   const int shift = lay.off_bstack;
@@ -339,6 +347,7 @@ size_t jit_layout(const pc_contract *k, Launch &L) {
   lay.off_cache -= shift;
   lay.off_win -= shift;
   lay.words -= shift;
+  if (jit_window_kind(L) == kJitWinRegs) lay.words = lay.off_win;
   return price_smem_bytes(k->prog.code.size(), pool_padded(k->prog), lay.words, L.block);
 }
 
@@ -372,9 +381,10 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
   if (c->jit && jit_eligible(k)) {
     // the contract's run-time specialised kernel (same arguments and shape)
     cudaKernel_t jk = nullptr;
+    const int wk = jit_window_kind(L);
     const size_t smem = jit_layout(k, L);
-    s = jit_kernel(k, m->H.d, (d_payoffs != nullptr ? kJitPriceWrite : kJitPrice) | (L.hbm_window ? kJitHbm : 0),
-                   L.block, jk, jit_min_blocks(c, smem, L.block));
+    s = jit_kernel(k, m->H.d, (d_payoffs != nullptr ? kJitPriceWrite : kJitPrice) | wk, L.block, jk,
+                   jit_min_blocks(c, smem, L.block));
     if (s != PC_OK) return s;
     const void *kern = reinterpret_cast<const void *>(jk);
     int nb = 0;
@@ -943,9 +953,9 @@ pc_status pc_jit_compile(const pc_model *m, const pc_contract *k) {
   if (s != PC_OK) return s;
   CU(cudaSetDevice(m->ctx->device), "cudaSetDevice");
   cudaKernel_t jk = nullptr;
+  const int wk = jit_window_kind(L);
   const size_t smem = jit_layout(k, L);
-  return jit_kernel(k, m->H.d, kJitPrice | (L.hbm_window ? kJitHbm : 0), L.block, jk,
-                    jit_min_blocks(m->ctx, smem, L.block));
+  return jit_kernel(k, m->H.d, kJitPrice | wk, L.block, jk, jit_min_blocks(m->ctx, smem, L.block));
 }
 
 pc_status pc_price_info(const pc_model *m, const pc_contract *k, uint64_t n_paths, pc_launch_info *info) {

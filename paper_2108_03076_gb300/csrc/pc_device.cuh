@@ -185,6 +185,10 @@ struct PathState {
   int f;                        // last produced ordinal (frontier), warp-uniform
   int bsp;                      // bridge stack size, warp-uniform
   int k;                        // ops run so far (the next op's number), warp-uniform
+#ifdef PC_WIN_REGS
+  float2 s[D];                  // S at the frontier date: the whole window of a program
+                                // that reads no date behind the frontier
+#endif
 };
 
 // A path's state at its start; the bottom slot of the bridge stack is
@@ -320,7 +324,12 @@ __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev
 #pragma unroll
     for (int k = 0; k <= i; ++k)
       x = make_float2(fmaf(Bm[i * D + k], ps.w[k].x, x.x), fmaf(Bm[i * D + k], ps.w[k].y, x.y));
+#ifdef PC_WIN_REGS
+    ps.s[i] = make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y));
+    (void)ws;
+#else
     win_store<GW>(R, lay, ws + i, make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y)));
+#endif
   }
   if constexpr (XW) {
     const int xs = lay.off_xwin + (t & (lay.win - 1)) * D;
@@ -365,23 +374,22 @@ __device__ __forceinline__ float cmp_code(int code, float v, float k) {
 
 // Fused multi-asset value (X_LRED) or test (X_LANY) of instruction I at
 // ordinal o for both paths; results of compares are 0/1 int bits.
-template <int D, bool GW = false>
-__device__ __forceinline__ float2 fused_value(const uint4 &I, int o, const float *pool,
-                                              const float2 *R, const ModelDev &m,
-                                              const Layout &lay) {
+// rd(l): S of underlying l at o (o > 0).
+template <int D, typename RD>
+__device__ __forceinline__ float2 fused_value_rd(const uint4 &I, int o, const float *pool, const ModelDev &m,
+                                                 RD rd) {
   const uint32_t A = I.x >> 8;
   const int n = int((A >> 8) & 3u) + 1, kind = int((A >> 2) & 3u), code = int((A >> 4) & 7u);
   const bool any = (I.x & 0xffu) == X_LANY, conj = (A & 1u) != 0;
   const int rop = int(A & 3u);
   const float k = __uint_as_float(I.w);
-  const int base = (o & (lay.win - 1)) * D;
   float2 v = make_float2(0.f, 0.f);
   for (int i = 0; i < n; ++i) {
     int l = int(A >> (10 + 2 * i)) & 3;
     l = l < D ? l : 0;
     float2 s;
     if (o > 0) {
-      s = win_load<GW>(R, lay, base + l);
+      s = rd(l);
     } else {
       const float sv = __ldg(m.sval + (o + m.n_hist) * D + l);
       s = make_float2(sv, sv);
@@ -412,18 +420,30 @@ __device__ __forceinline__ float2 fused_value(const uint4 &I, int o, const float
   return v;
 }
 
+template <int D, bool GW = false>
+__device__ __forceinline__ float2 fused_value(const uint4 &I, int o, const float *pool, const float2 *R,
+                                              const ModelDev &m, const Layout &lay) {
+  const int base = (o & (lay.win - 1)) * D;
+  return fused_value_rd<D>(I, o, pool, m, [&](int l) { return win_load<GW>(R, lay, base + l); });
+}
+// The same with the frontier date's S in registers (cur; a window of one date).
+template <int D>
+__device__ __forceinline__ float2 fused_value_regs(const uint4 &I, int o, const float *pool,
+                                                   const float2 (&cur)[D], const ModelDev &m) {
+  return fused_value_rd<D>(I, o, pool, m, [&](int l) { return cur[l]; });
+}
+
 // The same instruction as a test only (X_LANY, or X_LRED with a compare),
 // as booleans for the lane's two paths: the whole-loop barrier op decides
 // its latches from it without the 0/1 value bits.
-template <int D, bool GW = false>
-__device__ __forceinline__ void fused_test(const uint4 &I, int o, const float *pool, const float2 *R,
-                                           const ModelDev &m, const Layout &lay, bool &t0, bool &t1) {
+template <int D, typename RD>
+__device__ __forceinline__ void fused_test_rd(const uint4 &I, int o, const float *pool, const ModelDev &m,
+                                              RD rd, bool &t0, bool &t1) {
   const uint32_t A = I.x >> 8;
   const int n = int((A >> 8) & 3u) + 1, kind = int((A >> 2) & 3u), code = int((A >> 4) & 7u);
   const bool any = (I.x & 0xffu) == X_LANY, conj = (A & 1u) != 0;
   const int rop = int(A & 3u);
   const float k = __uint_as_float(I.w);
-  const int base = (o & (lay.win - 1)) * D;
   auto cmp = [&](float v) {
     return code == 1 ? v < k : code == 2 ? v <= k : code == 3 ? k < v : k <= v;
   };
@@ -434,7 +454,7 @@ __device__ __forceinline__ void fused_test(const uint4 &I, int o, const float *p
     l = l < D ? l : 0;
     float2 s;
     if (o > 0) {
-      s = win_load<GW>(R, lay, base + l);
+      s = rd(l);
     } else {
       const float sv = __ldg(m.sval + (o + m.n_hist) * D + l);
       s = make_float2(sv, sv);
@@ -474,6 +494,17 @@ __device__ __forceinline__ void fused_test(const uint4 &I, int o, const float *p
   }
   t0 = b0;
   t1 = b1;
+}
+template <int D, bool GW = false>
+__device__ __forceinline__ void fused_test(const uint4 &I, int o, const float *pool, const float2 *R,
+                                           const ModelDev &m, const Layout &lay, bool &t0, bool &t1) {
+  const int base = (o & (lay.win - 1)) * D;
+  fused_test_rd<D>(I, o, pool, m, [&](int l) { return win_load<GW>(R, lay, base + l); }, t0, t1);
+}
+template <int D>
+__device__ __forceinline__ void fused_test_regs(const uint4 &I, int o, const float *pool, const float2 (&cur)[D],
+                                                const ModelDev &m, bool &t0, bool &t1) {
+  fused_test_rd<D>(I, o, pool, m, [&](int l) { return cur[l]; }, t0, t1);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

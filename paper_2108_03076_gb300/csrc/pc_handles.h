@@ -18,9 +18,10 @@
 // A run-time specialised pricing kernel: the program it was compiled from
 // (code and pool words), the underlying count and the per-path variant.
 // Kinds of run-time specialised kernels: pricing (bit kJitPriceWrite: with
-// per-path payoffs; bit kJitHbm: the window of dates in HBM), and the
+// per-path payoffs; bit kJitHbm: the window of dates in HBM; bit
+// kJitWinRegs: a window of one date, kept in registers), and the
 // control-variate kernel (kJitCv + its kCv* mode bits).
-constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitHbm = 2, kJitCv = 16, kJitGreeks = 32;
+constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitHbm = 2, kJitWinRegs = 4, kJitCv = 16, kJitGreeks = 32;
 // resident blocks per SM the specialised pricing kernel's register bound is
 // set for by default (<= 72 registers at 128 threads: the fastest measured)
 constexpr int kJitMinBlocks = 7;

@@ -210,6 +210,9 @@ std::string generate(const Program &p, int d, int kind) {
   // without re-entry points, many reading instructions call one
   // out-of-line copy instead of inlining the generator at each
   if (!shared && date_sites(p) > kInlineDateSites) o << "#define PC_JIT_OUTLINE_DATES 1\n";
+  // a program that reads no date behind the frontier keeps that date's S in
+  // registers instead of a shared-memory window
+  if (kind < kJitCv && (kind & kJitWinRegs)) o << "#define PC_WIN_REGS 1\n";
   o << "#include \"pc_price.cuh\"\n";
   if (kind >= kJitCv) o << "#include \"pc_cv.cuh\"\n";
   o
@@ -412,7 +415,7 @@ extern "C" pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_wor
   const bool cv_kind = kind >= kJitCv && kind < kJitCv + 8 && kind != kJitCv + kCvWrite &&
                        kind != kJitCv + (kCvWrite | kCvPilot) && kind != kJitCv + (kCvWrite | kCvPilot | kCvGamma);
   const bool greeks_kind = kind == kJitGreeks || kind == kJitGreeks + 1;
-  if ((kind < 0 || kind > (kJitPriceWrite | kJitHbm)) && !cv_kind && !greeks_kind)
+  if ((kind < 0 || kind > (kJitPriceWrite | kJitHbm | kJitWinRegs)) && !cv_kind && !greeks_kind)
     return fail(PC_EINVAL, "unknown kernel kind");
   if (cv_kind && d > kCvMaxD) return fail(PC_EINVAL, "control-variate kernels take d <= 3");
   Program p;
@@ -432,7 +435,8 @@ extern "C" pc_status pc_debug_jit_source(const uint32_t *bytecode, size_t n_word
                                          size_t cap, size_t *len) {
   if (!len) return fail(PC_EINVAL, "null output");
   if (d < 1 || d > PC_MAX_UNDERLYINGS) return fail(PC_EINVAL, "d must be 1..4");
-  const bool known = (kind >= 0 && kind <= (kJitPriceWrite | kJitHbm)) || (kind >= kJitCv && kind < kJitCv + 8) ||
+  const bool known = (kind >= 0 && kind <= (kJitPriceWrite | kJitHbm | kJitWinRegs)) ||
+                     (kind >= kJitCv && kind < kJitCv + 8) ||
                      kind == kJitGreeks || kind == kJitGreeks + 1;
   if (!known) return fail(PC_EINVAL, "unknown kernel kind");
   Program p;
