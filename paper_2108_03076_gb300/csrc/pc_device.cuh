@@ -103,34 +103,31 @@ __device__ __forceinline__ float lg2_approx(float x) {
   return y;
 }
 
-// q = -2 ln u for the uniform u = (k + 1/2) 2^-24 of a 24-bit integer k
-// (given as the float kf, exact).  Away from u = 1: -2 ln 2 lg2.approx(u),
-// whose absolute error (about 7e-8 over (0, 1)) is small beside q.  Near 1,
-// where q is tiny and both that error and the rounding of u to a float
-// would dominate, the series 2v + v^2 + (2/3) v^3 of q = -2 ln(1 - v) in
-// v = 1 - u, which is exact in float for u > 1/2 (an odd multiple of 2^-25
-// below 2^-1); for v < 2^-8 the terms left out are below 2^-26 of q.
-__device__ __forceinline__ float neg2log_u24(float kf) {
-  const float u = fmaf(kf, 0x1p-24f, 0x1p-25f);
-  const float v = __fadd_rn(fmaf(kf, -0x1p-24f, 1.0f), -0x1p-25f);
-  const float ql = -1.3862943611198906f * lg2_approx(u);
-  const float qs = v * fmaf(v, fmaf(v, 0.6666666666666666f, 1.0f), 2.0f);
-  return v < 0x1p-8f ? qs : ql;
-}
-
 // Box-Muller on one word pair of each of the lane's two paths: u_a from the
 // even word, u_b from the odd word (path 0 in .x, path 1 in .y); even normal
-// r cos(2 pi u_b), odd normal r sin(2 pi u_b) with r = sqrt(-2 ln u_a).  The
-// angle is reduced to 2 pi u_b - pi in (-pi, pi), where cos and sin change
-// sign.
+// r cos(2 pi u_b), odd normal r sin(2 pi u_b) with r = sqrt(q), q = -2 ln u_a.
+// u = (k + 1/2) 2^-24 for the 24-bit integer k = word >> 8.  Away from u = 1,
+// q = -2 ln 2 lg2.approx(u), whose absolute error (about 7e-8 over (0, 1)) is
+// small beside q.  Near 1, where q is tiny and both that error and the
+// rounding of u to a float would dominate, q is the series 2v + v^2 +
+// (2/3) v^3 of -2 ln(1 - v) in v = 1 - u, which is exact in float for
+// u > 1/2 (an odd multiple of 2^-25 below 2^-1); for v < 2^-8 the terms left
+// out are below 2^-26 of q.  The angle is reduced to 2 pi u_b - pi in
+// (-pi, pi), where cos and sin change sign.  The scalar steps run on packed
+// pairs (each lane of a packed operation rounds as the scalar one).
 __device__ __forceinline__ void box_muller2(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1,
                                             float2 &ze, float2 &zo) {
-  const float2 nr = make_float2(-sqrt_approx(neg2log_u24(__uint2float_rn(a0 >> 8))),
-                                -sqrt_approx(neg2log_u24(__uint2float_rn(a1 >> 8))));
-  const float th0 = fmaf(__uint2float_rn(b0 >> 8), kThetaScale, kThetaOffset);
-  const float th1 = fmaf(__uint2float_rn(b1 >> 8), kThetaScale, kThetaOffset);
-  ze = mul_x2(nr, make_float2(cos_approx(th0), cos_approx(th1)));
-  zo = mul_x2(nr, make_float2(sin_approx(th0), sin_approx(th1)));
+  const float2 ka = make_float2(__uint2float_rn(a0 >> 8), __uint2float_rn(a1 >> 8));
+  const float2 u = fma_x2(ka, dup2(0x1p-24f), dup2(0x1p-25f));
+  const float2 v = fma_x2(fma_x2(ka, dup2(-0x1p-24f), dup2(1.0f)), dup2(1.0f), dup2(-0x1p-25f));
+  const float2 ql = mul_x2(dup2(-1.3862943611198906f), make_float2(lg2_approx(u.x), lg2_approx(u.y)));
+  const float2 qs = mul_x2(v, fma_x2(v, fma_x2(v, dup2(0.6666666666666666f), dup2(1.0f)), dup2(2.0f)));
+  const float2 q = make_float2(v.x < 0x1p-8f ? qs.x : ql.x, v.y < 0x1p-8f ? qs.y : ql.y);
+  const float2 nr = make_float2(-sqrt_approx(q.x), -sqrt_approx(q.y));
+  const float2 kb = make_float2(__uint2float_rn(b0 >> 8), __uint2float_rn(b1 >> 8));
+  const float2 th = fma_x2(kb, dup2(kThetaScale), dup2(kThetaOffset));
+  ze = mul_x2(nr, make_float2(cos_approx(th.x), cos_approx(th.y)));
+  zo = mul_x2(nr, make_float2(sin_approx(th.x), sin_approx(th.y)));
 }
 
 // Two paths per lane: every value of the stack machine is a float2 (.x for
