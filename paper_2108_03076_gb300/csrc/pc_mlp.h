@@ -46,10 +46,14 @@ struct GemmArgs {
 enum GemmKind { kGemmForward, kGemmDataGrad, kGemmWeightGrad };
 cudaError_t launch_gemm(GemmKind kind, int epi, const GemmArgs &g, int splits, cudaStream_t s);
 
-// Forward products on the tcgen05 tensor cores (pc_mlp_tc.cu): both
-// operands K-major, K a multiple of 64, M of 64, N = 64 or a multiple of
-// 128; epilogues kEpiBiasSoftplus and kEpiBias.  *status |= 4 when a
-// bounded wait expires.  gemm_tc_init (once, outside stream capture):
+// The products on the tcgen05 tensor cores (pc_mlp_tc.cu), operands staged
+// by TMA in the 128-byte swizzled layout: kGemmForward (A [M][K] and B [N][K]
+// K-major; epilogues kEpiBiasSoftplus, kEpiBias), kGemmDataGrad (A [M][K]
+// K-major, B = W [K][N] N-major; kEpiDSoftplus), kGemmWeightGrad (A = dZ
+// [K][M] M-major, B = the layer input [K][N] N-major; kEpiPartial, split over
+// K in k_split ranges by blockIdx.z).  K and k_split multiples of 64, M of
+// 64, N = 64 or a multiple of 128.  *status |= 4 when a bounded wait
+// expires.  gemm_tc_init (once, outside stream capture):
 // cudaErrorNotSupported on devices or drivers without them.
 // The TMA descriptors of a product's operands (encoded once per buffer and
 // shape on the host; kernel parameters by value).
@@ -57,12 +61,12 @@ struct TcMaps {
   CUtensorMap a, b;
 };
 cudaError_t gemm_tc_init();
-bool gemm_tc_supported(const GemmArgs &g);
-bool make_tc_maps(const GemmArgs &g, TcMaps &m);
+bool gemm_tc_supported(GemmKind kind, const GemmArgs &g);
+bool make_tc_maps(GemmKind kind, const GemmArgs &g, TcMaps &m);
 // withhold: failure test (the producer withholds its first copies and the
 // bounded waits expire after about 10 ms)
-cudaError_t launch_gemm_tc(int epi, const GemmArgs &g, const TcMaps &m, int32_t *status, cudaStream_t s,
-                           bool withhold = false);
+cudaError_t launch_gemm_tc(GemmKind kind, int epi, const GemmArgs &g, const TcMaps &m, int splits,
+                           int32_t *status, cudaStream_t s, bool withhold = false);
 
 // x [n, fin] FP32 -> X [rows, ld] BF16, zero beyond n rows / fin columns.
 cudaError_t launch_to_bf16(const float *x, size_t n, int fin, __nv_bfloat16 *X, size_t rows, int ld,

@@ -61,7 +61,7 @@ struct pc_mlp {
   int32_t *dstatus = nullptr;       // device status of the tensor-core products
   int32_t gemm = PC_MLP_GEMM_AUTO;  // product kernel choice (pc_mlp_set_gemm)
   bool tc_ok = false;               // tcgen05 products available on this device
-  std::map<uint64_t, TcMaps> tc_maps;  // forward operand descriptors by (layer, rows)
+  std::map<uint64_t, TcMaps> tc_maps;  // operand descriptors by (product kind, layer, rows)
   float *h_pin = nullptr;             // pinned [8]: read-back of captured table builds
   std::vector<std::pair<std::vector<uint8_t>, cudaGraphExec_t>> graphs;  // captured table builds
 };
@@ -119,6 +119,17 @@ int grad_splits(const pc_mlp *N, int M, int Nn, size_t rows, int &k_split) {
   return int((rows + k_split - 1) / k_split);
 }
 
+// The same for the tensor-core weight gradient: 128 x (64 or 128) output
+// tiles, k ranges in whole 64-row chunks.
+int tc_grad_splits(const pc_mlp *N, int M, int Nn, size_t rows, int &k_split) {
+  const int tiles = ((M + 127) / 128) * (Nn == 64 ? 1 : Nn / 128);
+  int want = std::max(1, (2 * N->ctx->sm_count + tiles - 1) / tiles);
+  const int steps64 = int(rows / 64);
+  want = std::max(1, std::min(want, steps64));
+  k_split = ((steps64 + want - 1) / want) * 64;
+  return int((rows + k_split - 1) / k_split);
+}
+
 // Parameter offsets and the device buffers for `rows` padded rows, carved
 // from N->mem; with N->mem null only the size is computed.
 size_t layout(pc_mlp *N, size_t rows) {
@@ -139,6 +150,10 @@ size_t layout(pc_mlp *N, size_t rows) {
     int ks = 0;
     const int sp = grad_splits(N, N->wp[l + 1], N->wp[l], rows, ks);
     part = std::max(part, size_t(sp) * N->wp[l + 1] * N->wp[l]);
+    if (rows % 64 == 0) {
+      const int tsp = tc_grad_splits(N, N->wp[l + 1], N->wp[l], rows, ks);
+      part = std::max(part, size_t(tsp) * N->wp[l + 1] * N->wp[l]);
+    }
   }
   N->part_cap = part;
   const size_t chunks = (rows + 255) / 256;
@@ -171,6 +186,34 @@ GemmArgs gemm0() {
   return a;
 }
 
+// One product: on the tensor cores when they serve this shape (operand
+// descriptors cached by kind, layer and rows), else the warp-level kernel.
+// A weight gradient is split over k differently on each path (splits and
+// a.k_split on the warp-level kernel, tc_splits and tc_k_split on the tensor
+// cores); *used receives the split count of the path taken.
+cudaError_t product(pc_mlp *N, GemmKind kind, int epi, int layer, size_t rows, GemmArgs a, int splits,
+                    int tc_k_split, int tc_splits, cudaStream_t s, int *used = nullptr) {
+  if (used) *used = splits;
+  if (N->tc_ok && N->gemm == PC_MLP_GEMM_AUTO) {
+    GemmArgs t = a;
+    if (kind == kGemmWeightGrad) t.k_split = tc_k_split;
+    if (gemm_tc_supported(kind, t)) {
+      const uint64_t key = (uint64_t(kind) << 56) | (uint64_t(layer) << 40) | uint64_t(rows);
+      auto it = N->tc_maps.find(key);
+      if (it == N->tc_maps.end()) {
+        TcMaps m;
+        if (make_tc_maps(kind, t, m)) it = N->tc_maps.emplace(key, m).first;
+      }
+      if (it != N->tc_maps.end()) {
+        const int sp = kind == kGemmWeightGrad ? tc_splits : 1;
+        if (used) *used = sp;
+        return launch_gemm_tc(kind, epi, t, it->second, sp, N->dstatus, s, N->tc_withhold);
+      }
+    }
+  }
+  return launch_gemm(kind, epi, a, splits, s);
+}
+
 // Forward over `rows` padded rows already in X.
 cudaError_t forward(pc_mlp *N, size_t rows, cudaStream_t s) {
   for (int l = 0; l < N->L; ++l) {
@@ -192,20 +235,7 @@ cudaError_t forward(pc_mlp *N, size_t rows, cudaStream_t s) {
     }
     a.ldc = N->wp[l + 1];
     const int epi = last ? kEpiBias : kEpiBiasSoftplus;
-    bool tc = N->tc_ok && N->gemm == PC_MLP_GEMM_AUTO && gemm_tc_supported(a);
-    const TcMaps *maps = nullptr;
-    if (tc) {
-      const uint64_t key = (uint64_t(l) << 40) | uint64_t(rows);
-      auto it = N->tc_maps.find(key);
-      if (it == N->tc_maps.end()) {
-        TcMaps m;
-        if (make_tc_maps(a, m)) it = N->tc_maps.emplace(key, m).first;
-      }
-      if (it != N->tc_maps.end()) maps = &it->second;
-      tc = maps != nullptr;
-    }
-    cudaError_t e = tc ? launch_gemm_tc(epi, a, *maps, N->dstatus, s, N->tc_withhold)
-                       : launch_gemm(kGemmForward, epi, a, 1, s);
+    cudaError_t e = product(N, kGemmForward, epi, l, rows, a, 1, 0, 1, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -231,10 +261,12 @@ cudaError_t backward(pc_mlp *N, size_t n, size_t rows, cudaStream_t s) {
     a.M = out_w;
     a.N = in_w;
     a.K = int(rows);
-    const int splits = grad_splits(N, out_w, in_w, rows, a.k_split);
+    int splits = grad_splits(N, out_w, in_w, rows, a.k_split);
+    int tc_ks = 0;
+    const int tc_splits = rows % 64 == 0 ? tc_grad_splits(N, out_w, in_w, rows, tc_ks) : 0;
     a.Cf = N->part;
     a.ldc = in_w;
-    e = launch_gemm(kGemmWeightGrad, kEpiPartial, a, splits, s);
+    e = product(N, kGemmWeightGrad, kEpiPartial, l, rows, a, splits, tc_ks, tc_splits, s, &splits);
     if (e != cudaSuccess) return e;
     const size_t cnt = size_t(out_w) * in_w;
     e = launch_split_sum(N->part, splits, cnt, cnt, N->g + N->offW[l], s);
@@ -256,7 +288,7 @@ cudaError_t backward(pc_mlp *N, size_t n, size_t rows, cudaStream_t s) {
       b.ldaux = in_w;
       b.Cb = N->dZ[cur ^ 1];
       b.ldc = in_w;
-      e = launch_gemm(kGemmDataGrad, kEpiDSoftplus, b, 1, s);
+      e = product(N, kGemmDataGrad, kEpiDSoftplus, l, rows, b, 1, 0, 1, s);
       if (e != cudaSuccess) return e;
       cur ^= 1;
     }

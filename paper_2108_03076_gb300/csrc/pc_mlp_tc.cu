@@ -94,8 +94,21 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1),
 // A and B BF16 (7-9 = 1, 10-12 = 1), both K-major (15, 16 = 0), N >> 3 at
 // bits 17-22, M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn = false, bool b_mn = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(a_mn) << 15) | (uint32_t(b_mn) << 16) |
+         (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+// The same descriptor for an MN-major operand in the 128-byte swizzle
+// layout: atoms of 64 M (or N) elements (128 contiguous bytes) by 8 k rows,
+// the k rows of an atom 128 bytes apart and the atom's 8-row groups along k
+// 1024 bytes apart (stride byte offset), consecutive atoms along M (N)
+// kMnAtomBytes apart (leading byte offset: one TMA box of 64 x 64).  A k step
+// of 16 is two 8-row groups: the start advances 2048 bytes.
+constexpr uint32_t kMnAtomBytes = 64 * 64 * 2;
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr) {
+  return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(kMnAtomBytes >> 4) << 16) |
+         (uint64_t(1024 >> 4) << 32) | (uint64_t(1) << 46) | (uint64_t(2) << 61);
 }
 
 __device__ __forceinline__ void mma_bf16_tc(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -129,7 +142,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 struct TcArgs {
   int M, N, K;
+  int k_split;                  // k range per blockIdx.z (a multiple of 64)
   const float *bias;
+  const __nv_bfloat16 *aux;     // stored activations (kEpiDSoftplus)
+  int ldaux;
   __nv_bfloat16 *Cb;
   float *Cf;
   int ldc;
@@ -140,7 +156,9 @@ struct TcArgs {
   long long wait_cycles;
 };
 
-template <int EPI, int BN>
+// AMN / BMN: operand A (B) is M-major (N-major) in memory, loaded as
+// BM / 64 (BN / 64) boxes of 64 x 64 in the MN-major swizzled layout.
+template <int EPI, int BN, bool AMN, bool BMN>
 __global__ void __launch_bounds__(kTcThreads)
     mlp_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcArgs g) {
   constexpr uint32_t kBTileBytes = BN * kTcBK * 2;
@@ -151,7 +169,9 @@ __global__ void __launch_bounds__(kTcThreads)
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
-  const int nk = g.K / kTcBK;
+  // this CTA's k chunks: [c0, c0 + nk)
+  const int c0 = int(blockIdx.z) * (g.k_split / kTcBK);
+  const int nk = min(g.k_split, g.K - int(blockIdx.z) * g.k_split) / kTcBK;
   const uint32_t base = (su32(tc_smem_raw) + 1023u) & ~1023u;
   const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[kStages]), done = su32(&bars[2 * kStages]);
 
@@ -182,9 +202,20 @@ __global__ void __launch_bounds__(kTcThreads)
       if (*(volatile int *)&abort_flag) break;
       if (g.withhold && c == 0) continue;
       const uint32_t sa = base + s * kStageBytes, sb = sa + kATileBytes;
+      const int kc = (c0 + c) * kTcBK;
       mbar_expect_tx(full0 + 8 * s, kStageBytes);
-      tma_load_2d(sa, &ta, c * kTcBK, m0, full0 + 8 * s);
-      tma_load_2d(sb, &tb, c * kTcBK, n0, full0 + 8 * s);
+      if (AMN) {
+#pragma unroll
+        for (int q = 0; q < kTcBM / 64; ++q) tma_load_2d(sa + q * kMnAtomBytes, &ta, m0 + 64 * q, kc, full0 + 8 * s);
+      } else {
+        tma_load_2d(sa, &ta, kc, m0, full0 + 8 * s);
+      }
+      if (BMN) {
+#pragma unroll
+        for (int q = 0; q < BN / 64; ++q) tma_load_2d(sb + q * kMnAtomBytes, &tb, n0 + 64 * q, kc, full0 + 8 * s);
+      } else {
+        tma_load_2d(sb, &tb, kc, n0, full0 + 8 * s);
+      }
       issued = c + 1;
     }
     // copies still in flight finish before the CTA can exit
@@ -192,7 +223,7 @@ __global__ void __launch_bounds__(kTcThreads)
       if (!mbar_wait(full0 + 8 * (c % kStages), (c / kStages) & 1, g.wait_cycles)) atomicOr(g.status, 4);
   } else if (threadIdx.x == 32) {
     // MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(kTcBM, BN);
+    constexpr uint32_t idesc = idesc_bf16(kTcBM, BN, AMN, BMN);
     for (int c = 0; c < nk; ++c) {
       const int s = c % kStages;
       if (*(volatile int *)&abort_flag) break;
@@ -204,8 +235,11 @@ __global__ void __launch_bounds__(kTcThreads)
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t sa = base + s * kStageBytes, sb = sa + kATileBytes;
 #pragma unroll
-      for (int kk = 0; kk < kTcBK / 16; ++kk)
-        mma_bf16_tc(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc, (c | kk) != 0);
+      for (int kk = 0; kk < kTcBK / 16; ++kk) {
+        const uint64_t da = AMN ? sw128_desc_mn(sa + kk * 2048) : sw128_desc(sa + kk * 32);
+        const uint64_t db = BMN ? sw128_desc_mn(sb + kk * 2048) : sw128_desc(sb + kk * 32);
+        mma_bf16_tc(tmem, da, db, idesc, (c | kk) != 0);
+      }
       mma_commit(empty0 + 8 * s);
     }
     mma_commit(done);
@@ -223,7 +257,7 @@ __global__ void __launch_bounds__(kTcThreads)
     float v[32];
     tmem_ld32(trow + j, v);
     if (row < g.M) {
-      const float *bias = g.bias + n0 + j;
+      const float *bias = g.bias + n0 + j;  // bias epilogues only
       if (EPI == kEpiBiasSoftplus) {
         uint32_t pk[16];
 #pragma unroll
@@ -236,12 +270,37 @@ __global__ void __launch_bounds__(kTcThreads)
         uint4 *dst = reinterpret_cast<uint4 *>(g.Cb + size_t(row) * g.ldc + n0 + j);
 #pragma unroll
         for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-      } else {
+      } else if (EPI == kEpiBias) {
         float4 *dst = reinterpret_cast<float4 *>(g.Cf + size_t(row) * g.ldc + n0 + j);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
           dst[q] = make_float4(v[4 * q] + __ldg(bias + 4 * q), v[4 * q + 1] + __ldg(bias + 4 * q + 1),
                                v[4 * q + 2] + __ldg(bias + 4 * q + 2), v[4 * q + 3] + __ldg(bias + 4 * q + 3));
+      } else if (EPI == kEpiDSoftplus) {
+        // the softplus derivative sigma(z) = 1 - exp(-softplus(z)) from the
+        // stored activation (32 BF16 values of this row: four 16-byte loads)
+        const uint4 *hv = reinterpret_cast<const uint4 *>(g.aux + size_t(row) * g.ldaux + n0 + j);
+        uint32_t pk[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 h4 = __ldg(hv + q);
+          const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[e]));
+            const int i = 8 * q + 2 * e;
+            const __nv_bfloat162 o = __floats2bfloat162_rn(v[i] * -expm1f(-hf.x), v[i + 1] * -expm1f(-hf.y));
+            pk[4 * q + e] = *reinterpret_cast<const uint32_t *>(&o);
+          }
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(g.Cb + size_t(row) * g.ldc + n0 + j);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+      } else {  // kEpiPartial: this k split's FP32 partial
+        float4 *dst = reinterpret_cast<float4 *>(g.Cf + size_t(blockIdx.z) * size_t(g.M) * g.ldc +
+                                                 size_t(row) * g.ldc + n0 + j);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
     }
   }
@@ -272,36 +331,40 @@ EncodeTiledFn encode_fn() {
 }
 
 // 2-D BF16 tensor [rows, cols] (cols contiguous, row stride ld elements),
-// box of box_rows x 64 columns, 128-byte swizzle, zero fill out of range.
+// box of box_rows x box_cols, 128-byte swizzle, zero fill out of range.
 bool make_map(CUtensorMap &m, const __nv_bfloat16 *p, uint64_t rows, uint64_t cols, uint64_t ld,
-              uint32_t box_rows) {
+              uint32_t box_rows, uint32_t box_cols = kTcBK) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {cols, rows};
   const cuuint64_t strides[1] = {ld * 2};
-  const cuuint32_t box[2] = {uint32_t(kTcBK), box_rows};
+  const cuuint32_t box[2] = {box_cols, box_rows};
   const cuuint32_t es[2] = {1, 1};
   return fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(p), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int EPI, int BN>
+template <int BN>
 constexpr size_t tc_smem() {
   return size_t(kStages) * (kATileBytes + size_t(BN) * kTcBK * 2) + 1024;
 }
 
-template <int EPI, int BN>
-cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, const TcArgs &a, cudaStream_t s) {
-  const dim3 grid(unsigned(a.N / BN), unsigned((a.M + kTcBM - 1) / kTcBM));
-  mlp_gemm_tc<EPI, BN><<<grid, kTcThreads, tc_smem<EPI, BN>(), s>>>(ta, tb, a);
+template <int EPI, int BN, bool AMN, bool BMN>
+cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, const TcArgs &a, int splits, cudaStream_t s) {
+  const dim3 grid(unsigned(a.N / BN), unsigned((a.M + kTcBM - 1) / kTcBM), unsigned(splits));
+  mlp_gemm_tc<EPI, BN, AMN, BMN><<<grid, kTcThreads, tc_smem<BN>(), s>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
-template <int EPI, int BN>
+template <int EPI, bool AMN, bool BMN>
 cudaError_t tc_attr() {
-  return cudaFuncSetAttribute(mlp_gemm_tc<EPI, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(tc_smem<EPI, BN>()));
+  cudaError_t r = cudaFuncSetAttribute(mlp_gemm_tc<EPI, 64, AMN, BMN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(tc_smem<64>()));
+  if (r == cudaSuccess)
+    r = cudaFuncSetAttribute(mlp_gemm_tc<EPI, 128, AMN, BMN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(tc_smem<128>()));
+  return r;
 }
 
 }  // namespace
@@ -315,38 +378,84 @@ cudaError_t gemm_tc_init() {
     if (r == cudaSuccess) r = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     if (r == cudaSuccess && major < 10) r = cudaErrorNotSupported;
     if (r == cudaSuccess && !encode_fn()) r = cudaErrorNotSupported;
-    if (r == cudaSuccess) r = tc_attr<kEpiBiasSoftplus, 64>();
-    if (r == cudaSuccess) r = tc_attr<kEpiBiasSoftplus, 128>();
-    if (r == cudaSuccess) r = tc_attr<kEpiBias, 64>();
-    if (r == cudaSuccess) r = tc_attr<kEpiBias, 128>();
+    if (r == cudaSuccess) r = tc_attr<kEpiBiasSoftplus, false, false>();
+    if (r == cudaSuccess) r = tc_attr<kEpiBias, false, false>();
+    if (r == cudaSuccess) r = tc_attr<kEpiDSoftplus, false, true>();
+    if (r == cudaSuccess) r = tc_attr<kEpiPartial, true, true>();
   });
   return r;
 }
 
-bool gemm_tc_supported(const GemmArgs &g) {
-  return g.K % kTcBK == 0 && g.K >= kTcBK && g.M % 64 == 0 && g.M > 0 && (g.N == 64 || g.N % 128 == 0) &&
-         g.lda % 8 == 0 && g.ldb % 8 == 0 && g.ldc % 8 == 0;
+bool gemm_tc_supported(GemmKind kind, const GemmArgs &g) {
+  const bool shape = g.K % kTcBK == 0 && g.K >= kTcBK && g.M % 64 == 0 && g.M > 0 &&
+                     (g.N == 64 || g.N % 128 == 0) && g.lda % 8 == 0 && g.ldb % 8 == 0 && g.ldc % 8 == 0;
+  if (!shape) return false;
+  if (kind == kGemmDataGrad) return g.aux != nullptr && g.ldaux % 8 == 0;
+  if (kind == kGemmWeightGrad) return g.k_split % kTcBK == 0 && g.k_split > 0;
+  return true;
 }
 
-bool make_tc_maps(const GemmArgs &g, TcMaps &m) {
-  if (!gemm_tc_supported(g) || gemm_tc_init() != cudaSuccess) return false;
-  const int bn = g.N == 64 ? 64 : 128;
-  return make_map(m.a, g.A, uint64_t(g.M), uint64_t(g.K), uint64_t(g.lda), kTcBM) &&
-         make_map(m.b, g.B, uint64_t(g.N), uint64_t(g.K), uint64_t(g.ldb), uint32_t(bn));
+bool make_tc_maps(GemmKind kind, const GemmArgs &g, TcMaps &m) {
+  if (!gemm_tc_supported(kind, g) || gemm_tc_init() != cudaSuccess) return false;
+  const uint32_t bn = g.N == 64 ? 64 : 128;
+  switch (kind) {
+    case kGemmForward:  // A [M][K], B [N][K]
+      return make_map(m.a, g.A, uint64_t(g.M), uint64_t(g.K), uint64_t(g.lda), kTcBM) &&
+             make_map(m.b, g.B, uint64_t(g.N), uint64_t(g.K), uint64_t(g.ldb), bn);
+    case kGemmDataGrad:  // A [M][K], B [K][N] (N-major: boxes of 64 k rows x 64 columns)
+      return make_map(m.a, g.A, uint64_t(g.M), uint64_t(g.K), uint64_t(g.lda), kTcBM) &&
+             make_map(m.b, g.B, uint64_t(g.K), uint64_t(g.N), uint64_t(g.ldb), kTcBK, 64);
+    case kGemmWeightGrad:  // A [K][M] (M-major), B [K][N] (N-major)
+      return make_map(m.a, g.A, uint64_t(g.K), uint64_t(g.M), uint64_t(g.lda), kTcBK, 64) &&
+             make_map(m.b, g.B, uint64_t(g.K), uint64_t(g.N), uint64_t(g.ldb), kTcBK, 64);
+  }
+  return false;
 }
 
-cudaError_t launch_gemm_tc(int epi, const GemmArgs &g, const TcMaps &m, int32_t *status, cudaStream_t s,
-                           bool withhold) {
-  if (!status || !gemm_tc_supported(g) || (epi != kEpiBiasSoftplus && epi != kEpiBias))
+cudaError_t launch_gemm_tc(GemmKind kind, int epi, const GemmArgs &g, const TcMaps &m, int splits,
+                           int32_t *status, cudaStream_t s, bool withhold) {
+  if (!status || !gemm_tc_supported(kind, g)) return cudaErrorInvalidValue;
+  const bool ok_epi = kind == kGemmForward ? (epi == kEpiBiasSoftplus || epi == kEpiBias)
+                      : kind == kGemmDataGrad ? epi == kEpiDSoftplus
+                                              : epi == kEpiPartial;
+  if (!ok_epi) return cudaErrorInvalidValue;
+  // every split has at least one k chunk
+  const int k_split = kind == kGemmWeightGrad ? g.k_split : g.K;
+  if (splits < 1 || (kind != kGemmWeightGrad && splits != 1) || (splits - 1) * k_split >= g.K ||
+      splits * k_split < g.K)
     return cudaErrorInvalidValue;
   const cudaError_t r = gemm_tc_init();
   if (r != cudaSuccess) return r;
-  const int bn = g.N == 64 ? 64 : 128;
-  TcArgs a{g.M, g.N, g.K, g.bias, g.Cb, g.Cf, g.ldc, status, withhold ? 1 : 0,
-           withhold ? kTestWaitCycles : kWaitCycles};
-  if (epi == kEpiBiasSoftplus) return bn == 64 ? launch_tc<kEpiBiasSoftplus, 64>(m.a, m.b, a, s)
-                                               : launch_tc<kEpiBiasSoftplus, 128>(m.a, m.b, a, s);
-  return bn == 64 ? launch_tc<kEpiBias, 64>(m.a, m.b, a, s) : launch_tc<kEpiBias, 128>(m.a, m.b, a, s);
+  TcArgs a{};
+  a.M = g.M;
+  a.N = g.N;
+  a.K = g.K;
+  a.k_split = k_split;
+  a.bias = g.bias;
+  a.aux = g.aux;
+  a.ldaux = g.ldaux;
+  a.Cb = g.Cb;
+  a.Cf = g.Cf;
+  a.ldc = g.ldc;
+  a.status = status;
+  a.withhold = withhold ? 1 : 0;
+  a.wait_cycles = withhold ? kTestWaitCycles : kWaitCycles;
+  const bool n64 = g.N == 64;
+  switch (kind) {
+    case kGemmForward:
+      if (epi == kEpiBiasSoftplus)
+        return n64 ? launch_tc<kEpiBiasSoftplus, 64, false, false>(m.a, m.b, a, 1, s)
+                   : launch_tc<kEpiBiasSoftplus, 128, false, false>(m.a, m.b, a, 1, s);
+      return n64 ? launch_tc<kEpiBias, 64, false, false>(m.a, m.b, a, 1, s)
+                 : launch_tc<kEpiBias, 128, false, false>(m.a, m.b, a, 1, s);
+    case kGemmDataGrad:
+      return n64 ? launch_tc<kEpiDSoftplus, 64, false, true>(m.a, m.b, a, 1, s)
+                 : launch_tc<kEpiDSoftplus, 128, false, true>(m.a, m.b, a, 1, s);
+    case kGemmWeightGrad:
+      return n64 ? launch_tc<kEpiPartial, 64, true, true>(m.a, m.b, a, splits, s)
+                 : launch_tc<kEpiPartial, 128, true, true>(m.a, m.b, a, splits, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace pc

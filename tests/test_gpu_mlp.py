@@ -194,8 +194,81 @@ def test_tensor_core_forward_matches_oracle_and_warp_kernel(ctx, widths, n):
         pc.pc_mlp_destroy(net)
 
 
+@pytest.mark.parametrize("widths,n", [(WIDTHS, 4099), ([16, 1024, 384, 5], 2000), ([9, 128, 64], 200)])
+def test_tensor_core_gradients_match_oracle_and_warp_kernel(ctx, widths, n):
+    """tcgen05 backward products: the data gradient reads W N-major, the
+    weight gradient reads dZ M-major and the layer input N-major (TMA boxes
+    of 64 x 64 in the MN-major swizzled layout), split over the rows in
+    64-row chunks with a fixed-order sum.  Element by element against the
+    oracle's FP64 backpropagation, and against the warp-level kernel (same
+    BF16 operands, FP32 sums in another order)."""
+    rng = np.random.default_rng(n + 3 * len(widths))
+    params = mlp.init(widths, rng)
+    net = pc.pc_mlp_create(ctx, widths, 4160)
+    try:
+        assert pc.pc_mlp_gemm_info(net), "tcgen05 products not available"
+        pc.pc_mlp_set_params(net, flat(params))
+        x = rng.normal(size=(n, widths[0])).astype(np.float32)
+        t = rng.normal(size=(n, widths[-1])).astype(np.float32)
+        w = np.linspace(0.25, 2.0, widths[-1]).astype(np.float32)
+        dx, dt = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+        outs = []
+        for kind in (pc.MLP_GEMM_AUTO, pc.MLP_GEMM_MMA_SYNC):
+            pc.pc_mlp_set_gemm(net, kind)
+            dg = torch.full((pc.pc_mlp_query(net).n_params,), float("nan"), dtype=torch.float32, device="cuda")
+            pc.pc_mlp_gradients(net, dx.data_ptr(), dt.data_ptr(), w, n, dg.data_ptr())
+            torch.cuda.synchronize()
+            outs.append(unflat(dg.double().cpu().numpy(), widths))
+        _, grads = mlp.backward(rounded(params), bf16(x), t.astype(np.float64), w.astype(np.float64))
+        for l, ((tW, tb), (sW, sb), (rW, rb)) in enumerate(zip(outs[0], outs[1], grads)):
+            assert np.isfinite(tW).all() and np.isfinite(tb).all(), l
+            assert_close_el(tW, rW, 8.0, np.sqrt(np.mean(rW ** 2)), f"tcgen05 dW{l}")
+            assert_close_el(tb, rb, 8.0, np.sqrt(np.mean(rb ** 2)), f"tcgen05 db{l}")
+            assert_close_el(sW, rW, 8.0, np.sqrt(np.mean(rW ** 2)), f"mma.sync dW{l}")
+            assert rel_err(tW, sW) < 1e-2, (l, rel_err(tW, sW))
+    finally:
+        pc.pc_mlp_destroy(net)
+
+
+def test_tensor_core_products_on_a_65536_row_batch(ctx):
+    """A 2^16-row gradient (every product on tcgen05: forward, data and
+    weight gradients) agrees with the warp-level kernel's element by element
+    to FP32 summation order, and the forward outputs too."""
+    rng = np.random.default_rng(65536)
+    n = 1 << 16
+    params = mlp.init(WIDTHS, rng)
+    net = pc.pc_mlp_create(ctx, WIDTHS, n)
+    try:
+        assert pc.pc_mlp_gemm_info(net), "tcgen05 products not available"
+        pc.pc_mlp_set_params(net, flat(params))
+        x = rng.normal(size=(n, 16)).astype(np.float32)
+        t = rng.normal(size=(n, 5)).astype(np.float32)
+        w = np.array([1.0, 0.5, 0.25, 2.0, 1.0], np.float32)
+        dx, dt = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+        grads, ys = [], []
+        for kind in (pc.MLP_GEMM_AUTO, pc.MLP_GEMM_MMA_SYNC):
+            pc.pc_mlp_set_gemm(net, kind)
+            dg = torch.empty(pc.pc_mlp_query(net).n_params, dtype=torch.float32, device="cuda")
+            for _ in range(3):
+                pc.pc_mlp_gradients(net, dx.data_ptr(), dt.data_ptr(), w, n, dg.data_ptr())
+            dy = torch.empty((n, 5), dtype=torch.float32, device="cuda")
+            pc.pc_mlp_forward(net, dx.data_ptr(), n, dy.data_ptr())
+            torch.cuda.synchronize()
+            grads.append(unflat(dg.double().cpu().numpy(), WIDTHS))
+            ys.append(dy.double().cpu().numpy())
+        assert_close_el(ys[0], ys[1], 2.0, float(np.sqrt(np.mean(ys[1] ** 2))), "output")
+        for l, ((tW, tb), (sW, sb)) in enumerate(zip(*grads)):
+            assert np.isfinite(tW).all(), l
+            # both are FP32 sums of the same BF16 products: within the
+            # gradient rule of the oracle comparisons, element by element
+            assert_close_el(tW, sW, 8.0, np.sqrt(np.mean(sW ** 2)), f"dW{l}")
+            assert_close_el(tb, sb, 8.0, np.sqrt(np.mean(sb ** 2)), f"db{l}")
+    finally:
+        pc.pc_mlp_destroy(net)
+
+
 def test_tensor_core_training_matches_warp_kernel(ctx):
-    """The training step with tcgen05 forward products fits like the
+    """The training step with every product on tcgen05 fits like the
     warp-level kernel's and is deterministic."""
     rng = np.random.default_rng(19)
     n = 1 << 13
