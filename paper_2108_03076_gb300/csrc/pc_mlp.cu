@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(128) mlp_gemm(const GemmArgs g) {
         }
         if (EPI == kEpiBiasSoftplus) {
           *reinterpret_cast<__nv_bfloat162 *>(g.Cb + size_t(r) * g.ldc + c) =
-              __floats2bfloat162_rn(softplus_sfu(v0), softplus_sfu(v1));
+              __floats2bfloat162_rn(softplus_fast(v0), softplus_fast(v1));
         } else if (EPI == kEpiBias) {
           *reinterpret_cast<float2 *>(g.Cf + size_t(r) * g.ldc + c) = make_float2(v0, v1);
         } else if (EPI == kEpiDSoftplus) {

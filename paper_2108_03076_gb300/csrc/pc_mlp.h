@@ -11,12 +11,22 @@
 namespace pc {
 
 #ifdef __CUDACC__
-// softplus(z) = max(z, 0) + log(1 + exp(-|z|)) on the SFU (ex2, lg2): the
-// absolute error (about 1e-7) is far inside the BF16 rounding (2^-9
-// relative) of the stored activation, at a fifth of the accurate
-// functions' instructions -- the forward epilogues' main cost.
-__device__ __forceinline__ float softplus_sfu(float z) {
-  return fmaxf(z, 0.f) + __logf(1.f + __expf(-fabsf(z)));
+// softplus(z) = max(z, 0) + log(1 + u), u = exp(-|z|) in (0, 1]: u from the
+// SFU (ex2), log(1 + u) = u p(u) with p a degree-6 polynomial fitted here by
+// least squares to log(1 + u) / u on Chebyshev points of [0, 1] (relative
+// error of u p(u) below 1.5e-6 in FP32): one SFU operation instead of two,
+// far inside the BF16 rounding (2^-9 relative) of the stored activation.
+__device__ __forceinline__ float softplus_fast(float z) {
+  float u;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(u) : "f"(-1.4426950408889634f * fabsf(z)));
+  float p = 0.014202825725078583f;
+  p = fmaf(p, u, -0.06658805161714554f);
+  p = fmaf(p, u, 0.14943458139896393f);
+  p = fmaf(p, u, -0.23514863848686218f);
+  p = fmaf(p, u, 0.3311205208301544f);
+  p = fmaf(p, u, -0.4998719096183777f);
+  p = fmaf(p, u, 0.9999987483024597f);
+  return fmaxf(z, 0.f) + u * p;
 }
 #endif
 

@@ -1,34 +1,44 @@
-// pc_mlp_tc.cu -- the network's forward products on the fifth-generation
-// tensor cores: tcgen05.mma with the accumulator in tensor memory (TMEM),
-// operands staged in shared memory by TMA (cp.async.bulk.tensor) in the
-// 128-byte swizzled K-major layout the MMA reads through its shared-memory
-// descriptors.
+// pc_mlp_tc.cu -- the network's products on the fifth-generation tensor
+// cores: tcgen05.mma with the accumulator in tensor memory (TMEM), operands
+// staged in shared memory by TMA (cp.async.bulk.tensor) in the 128-byte
+// swizzled layouts the MMA reads through its shared-memory descriptors.
 //
-// Z[M, N] = H[M, K] W[N, K]^T + b, H the activations (rows = samples,
-// K contiguous) and W a layer's BF16 weights ([out, in], in contiguous):
-// both operands K-major, FP32 accumulation.  One CTA computes a 128 x BN
-// tile (BN = 64 or 128) over the whole K range:
-//   warp 0, lane 0   TMA producer: 64-deep k chunks into a ring of kStages
-//                    stage buffers (A 16 KB, B BN x 128 B), one "full"
-//                    mbarrier per stage (expect_tx = the chunk's bytes) and
-//                    one "empty" mbarrier the MMA side frees it with;
-//   warp 1, lane 0   MMA issuer: four 128 x BN x 16 tcgen05.mma per chunk
-//                    (the descriptor start advanced by 32 bytes per step of
-//                    16 inside the 128-byte swizzle row), tcgen05.commit to
-//                    the stage's empty barrier, and after the last chunk to
-//                    the "done" barrier;
-//   all eight warps  epilogue: warp w reads TMEM lanes 32(w % 4) .. +31
-//                    (tile rows), columns of half w / 4 of the tile, with
-//                    tcgen05.ld 32 columns at a time, adds the bias, applies
-//                    softplus and stores BF16 (hidden layers) or stores
-//                    FP32 (output layer).
-// Two stages (64 KB at BN = 128) let three CTAs share an SM, so 24 warps
-// hide the epilogue's latency.
-// Warp 0 allocates BN TMEM columns and frees them after the epilogue.
-// Every wait is bounded (about a second of SM clocks): on expiry the kernel
-// sets *status, stops issuing work, still commits so the done barrier
-// completes, waits (bounded) for its copies in flight, frees TMEM and
-// returns; the host reports the status.
+// C[M, N] = A B^T over K with BF16 operands and FP32 accumulation, in three
+// forms (rows = samples, W a layer's weights [out, in]):
+//   forward       Z = H W^T      A = H [M][K], B = W [N][K]: both K-major
+//   data grad     dH = dZ W      A = dZ [M][K] K-major, B = W [K][N] N-major
+//   weight grad   dW = dZ^T H    A = dZ [K][M] M-major, B = H [K][N] N-major,
+//                                split over K (the rows) into FP32 partials
+// A K-major operand tile is one TMA box of 64 k columns by its rows; an
+// MN-major one is BM / 64 (BN / 64) boxes of 64 k rows by 64 columns, the
+// MN-major swizzled layout (descriptors sw128_desc / sw128_desc_mn).
+//
+// The kernel is persistent: one CTA per SM walks the
+// output tiles (128 x BN, BN = 64 or 128; with the k splits as a third tile
+// coordinate):
+//   warp 0, lane 0    TMA producer: 64-deep k chunks into a ring of kStages
+//                     stage buffers across tiles, one "full" mbarrier per
+//                     stage (expect_tx = the chunk's bytes) and one "empty"
+//                     mbarrier the MMA side frees it with;
+//   warp 1, lane 0    MMA issuer: four 128 x BN x 16 tcgen05.mma per chunk
+//                     into TMEM buffer i & 1 of the CTA's i-th tile (two
+//                     buffers of BN columns), tcgen05.commit to the stage's
+//                     empty barrier and, after a tile's last chunk, to the
+//                     buffer's "tfull" barrier;
+//   warps 4..11       epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+//                     (tile rows) of half (w - 4) / 4 of the tile's columns,
+//                     32 columns at a time (tcgen05.ld), applies
+//                     the product's epilogue (bias + softplus -> BF16; bias ->
+//                     FP32; times the softplus derivative from the stored
+//                     activation -> BF16; FP32 split partial) and frees the
+//                     buffer ("tempty", one arrival per warp), so one tile's
+//                     epilogue overlaps the next tile's loads and MMAs.
+// Warp 0 allocates 2 BN TMEM columns and frees them once the "done" barrier
+// (committed after the last MMA) has completed.  Every wait is bounded
+// (about a second of SM clocks) and gives up early once another role has
+// given up: on expiry the kernel sets *status, stops issuing work, waits
+// (bounded) for its copies and MMAs in flight, frees TMEM and returns; the
+// host reports the status.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -40,7 +50,8 @@
 namespace pc {
 namespace {
 
-constexpr int kTcBM = 128, kTcBK = 64, kStages = 2, kTcThreads = 256;
+constexpr int kTcBM = 128, kTcBK = 64, kStages = 6, kTcThreads = 384;
+constexpr int kEpiWarps = 8;  // warps 4..11: two per TMEM lane quarter, each half the columns
 constexpr uint32_t kATileBytes = kTcBM * kTcBK * 2;  // 16 KB
 constexpr long long kWaitCycles = 2000000000ll;      // ~1 s at 2 GHz
 constexpr long long kTestWaitCycles = 20000000ll;    // ~10 ms: the failure test's limit
@@ -64,12 +75,19 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of `parity` to complete; false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+// Bounded wait for the phase of `parity` to complete; false on expiry or
+// when *abort is raised (another role of the CTA gave up).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit,
+                                          const volatile int *abort = nullptr) {
   const long long t0 = clock64();
-  while (!mbar_test(bar, parity))
+  while (!mbar_test(bar, parity)) {
+    if (abort && *abort) return false;
     if (clock64() - t0 > limit) return false;
+  }
   return true;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
@@ -149,6 +167,7 @@ struct TcArgs {
   __nv_bfloat16 *Cb;
   float *Cf;
   int ldc;
+  int splits;                   // k splits (blockIdx-independent: tiles enumerate them)
   int32_t *status;
   // failure test: the producer withholds chunk 0's copies, so the waits on
   // it expire (after wait_cycles) and the kernel takes its abort path
@@ -156,32 +175,116 @@ struct TcArgs {
   long long wait_cycles;
 };
 
+// The softplus derivative sigma(z) = 1 - exp(-h) from h = softplus(z) >= 0:
+// for h >= 2^-5 with the SFU exponential (absolute error about 1e-7, below
+// 4e-6 of the result), below it the series h (1 - h/2 (1 - h/3)) (relative
+// error under h^3 / 24 < 2e-6): both far inside the BF16 rounding of dZ.
+__device__ __forceinline__ float dsoftplus(float h) {
+  return h >= 0.03125f ? 1.f - __expf(-h) : h * fmaf(-0.5f * h, fmaf(-h, 0.3333333333f, 1.f), 1.f);
+}
+
+// The epilogue of 32 accumulator columns of one row: row `row`, columns
+// col .. col + 31 of C (bias epilogues: + bias; k split z for kEpiPartial).
+template <int EPI>
+__device__ __forceinline__ void epilogue32(const TcArgs &g, int row, int col, int z, const float (&v)[32]) {
+  if (EPI == kEpiBiasSoftplus) {
+    const float *bias = g.bias + col;
+    uint32_t pk[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float a0 = softplus_fast(v[2 * i] + __ldg(bias + 2 * i));
+      const float a1 = softplus_fast(v[2 * i + 1] + __ldg(bias + 2 * i + 1));
+      const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+      pk[i] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(g.Cb + size_t(row) * g.ldc + col);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+  } else if (EPI == kEpiBias) {
+    const float *bias = g.bias + col;
+    float4 *dst = reinterpret_cast<float4 *>(g.Cf + size_t(row) * g.ldc + col);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      dst[q] = make_float4(v[4 * q] + __ldg(bias + 4 * q), v[4 * q + 1] + __ldg(bias + 4 * q + 1),
+                           v[4 * q + 2] + __ldg(bias + 4 * q + 2), v[4 * q + 3] + __ldg(bias + 4 * q + 3));
+  } else if (EPI == kEpiDSoftplus) {
+    // the softplus derivative sigma(z) = 1 - exp(-softplus(z)) from the
+    // stored activation (32 BF16 values of this row: four 16-byte loads)
+    const uint4 *hv = reinterpret_cast<const uint4 *>(g.aux + size_t(row) * g.ldaux + col);
+    uint32_t pk[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 h4 = __ldg(hv + q);
+      const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[e]));
+        const int i = 8 * q + 2 * e;
+        const __nv_bfloat162 o = __floats2bfloat162_rn(v[i] * dsoftplus(hf.x), v[i + 1] * dsoftplus(hf.y));
+        pk[4 * q + e] = *reinterpret_cast<const uint32_t *>(&o);
+      }
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(g.Cb + size_t(row) * g.ldc + col);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+  } else {  // kEpiPartial: this k split's FP32 partial
+    float4 *dst = reinterpret_cast<float4 *>(g.Cf + size_t(z) * size_t(g.M) * g.ldc + size_t(row) * g.ldc + col);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  }
+}
+
+// Persistent product: one CTA per SM walks the output tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (tile t: k split t / (tm tn), then row tile,
+// then column tile).  The producer streams 64-deep k chunks through a ring
+// of kStages stages across tiles; the MMA issuer accumulates tile i into TMEM
+// buffer i & 1 (two buffers of BN columns), so the epilogue warps (4..7,
+// warp w reading TMEM lanes 32 (w % 4) ..) drain one buffer while the next
+// tile's MMAs fill the other.  Barriers: full / empty per stage, tfull /
+// tempty per TMEM buffer (tempty: one arrival per epilogue warp), done.
+// Warps 2 and 3 have no role (the epilogue warps must sit at positions
+// 0..3 of their warp quarter to reach their TMEM lanes).
 // AMN / BMN: operand A (B) is M-major (N-major) in memory, loaded as
 // BM / 64 (BN / 64) boxes of 64 x 64 in the MN-major swizzled layout.
 template <int EPI, int BN, bool AMN, bool BMN>
-__global__ void __launch_bounds__(kTcThreads)
+__global__ void __launch_bounds__(kTcThreads, 1)
     mlp_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcArgs g) {
   constexpr uint32_t kBTileBytes = BN * kTcBK * 2;
   constexpr uint32_t kStageBytes = kATileBytes + kBTileBytes;
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];
-  __shared__ __align__(8) uint64_t bars[2 * kStages + 1];
+  __shared__ __align__(8) uint64_t bars[2 * kStages + 5];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+  const volatile int *abort = &abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
-  // this CTA's k chunks: [c0, c0 + nk)
-  const int c0 = int(blockIdx.z) * (g.k_split / kTcBK);
-  const int nk = min(g.k_split, g.K - int(blockIdx.z) * g.k_split) / kTcBK;
+  const int tm = (g.M + kTcBM - 1) / kTcBM, tn = g.N / BN;
+  const int tiles = tm * tn * g.splits;
+  const int split_chunks = g.k_split / kTcBK;
   const uint32_t base = (su32(tc_smem_raw) + 1023u) & ~1023u;
-  const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[kStages]), done = su32(&bars[2 * kStages]);
+  const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[kStages]);
+  const uint32_t tfull0 = su32(&bars[2 * kStages]), tempty0 = su32(&bars[2 * kStages + 2]);
+  const uint32_t done = su32(&bars[2 * kStages + 4]);
+  auto decode = [&](int t, int &z, int &m0, int &n0, int &c0, int &nk) {
+    z = t / (tm * tn);
+    const int r = t - z * tm * tn;
+    m0 = (r / tn) * kTcBM;
+    n0 = (r % tn) * BN;
+    c0 = z * split_chunks;
+    nk = min(g.k_split, g.K - z * g.k_split) / kTcBK;
+  };
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
-                 "r"(BN));
+                 "r"(2 * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (threadIdx.x == 32) {
-    for (int s = 0; s < 2 * kStages + 1; ++s) mbar_init(su32(&bars[s]), 1);
+    for (int s = 0; s < 2 * kStages; ++s) mbar_init(su32(&bars[s]), 1);
+    mbar_init(tfull0, 1);
+    mbar_init(tfull0 + 8, 1);
+    mbar_init(tempty0, kEpiWarps);
+    mbar_init(tempty0 + 8, kEpiWarps);
+    mbar_init(done, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -191,124 +294,118 @@ __global__ void __launch_bounds__(kTcThreads)
   const uint32_t tmem = tmem_slot;
 
   if (threadIdx.x == 0) {
-    // TMA producer
-    int issued = 0;
-    for (int c = 0; c < nk; ++c) {
-      const int s = c % kStages;
-      if (c >= kStages && !mbar_wait(empty0 + 8 * s, ((c / kStages) + 1) & 1, g.wait_cycles)) {
-        atomicOr(g.status, 4);
-        atomicExch(&abort_flag, 1);
-      }
-      if (*(volatile int *)&abort_flag) break;
-      if (g.withhold && c == 0) continue;
-      const uint32_t sa = base + s * kStageBytes, sb = sa + kATileBytes;
-      const int kc = (c0 + c) * kTcBK;
-      mbar_expect_tx(full0 + 8 * s, kStageBytes);
-      if (AMN) {
+    // TMA producer: chunk counter q runs across this CTA's tiles
+    uint32_t q = 0, issued = 0;  // chunks issued: their copies land before exit
+    for (int t = blockIdx.x; t < tiles && !*abort; t += gridDim.x) {
+      int z, m0, n0, c0, nk;
+      decode(t, z, m0, n0, c0, nk);
+      for (int c = 0; c < nk; ++c, ++q) {
+        const uint32_t s = q % kStages, u = q / kStages;
+        if (u >= 1 && !mbar_wait(empty0 + 8 * s, (u - 1) & 1, g.wait_cycles, abort)) {
+          if (!*abort) atomicOr(g.status, 4);
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (g.withhold && q == 0) continue;  // failure test: chunk 0 never arrives
+        const uint32_t sa = base + s * kStageBytes, sb = sa + kATileBytes;
+        const int kc = (c0 + c) * kTcBK;
+        mbar_expect_tx(full0 + 8 * s, kStageBytes);
+        if (AMN) {
 #pragma unroll
-        for (int q = 0; q < kTcBM / 64; ++q) tma_load_2d(sa + q * kMnAtomBytes, &ta, m0 + 64 * q, kc, full0 + 8 * s);
-      } else {
-        tma_load_2d(sa, &ta, kc, m0, full0 + 8 * s);
-      }
-      if (BMN) {
+          for (int b = 0; b < kTcBM / 64; ++b) tma_load_2d(sa + b * kMnAtomBytes, &ta, m0 + 64 * b, kc, full0 + 8 * s);
+        } else {
+          tma_load_2d(sa, &ta, kc, m0, full0 + 8 * s);
+        }
+        if (BMN) {
 #pragma unroll
-        for (int q = 0; q < BN / 64; ++q) tma_load_2d(sb + q * kMnAtomBytes, &tb, n0 + 64 * q, kc, full0 + 8 * s);
-      } else {
-        tma_load_2d(sb, &tb, kc, n0, full0 + 8 * s);
+          for (int b = 0; b < BN / 64; ++b) tma_load_2d(sb + b * kMnAtomBytes, &tb, n0 + 64 * b, kc, full0 + 8 * s);
+        } else {
+          tma_load_2d(sb, &tb, kc, n0, full0 + 8 * s);
+        }
+        issued = q + 1;
       }
-      issued = c + 1;
     }
-    // copies still in flight finish before the CTA can exit
-    for (int c = issued - kStages > 0 ? issued - kStages : 0; c < issued; ++c)
-      if (!mbar_wait(full0 + 8 * (c % kStages), (c / kStages) & 1, g.wait_cycles)) atomicOr(g.status, 4);
+    // the last kStages issued chunks' copies complete before the CTA exits
+    for (uint32_t c = issued > kStages ? issued - kStages : 0; c < issued; ++c)
+      if (!(g.withhold && c == 0) && !mbar_wait(full0 + 8 * (c % kStages), (c / kStages) & 1, g.wait_cycles))
+        atomicOr(g.status, 4);
   } else if (threadIdx.x == 32) {
     // MMA issuer
     constexpr uint32_t idesc = idesc_bf16(kTcBM, BN, AMN, BMN);
-    for (int c = 0; c < nk; ++c) {
-      const int s = c % kStages;
-      if (*(volatile int *)&abort_flag) break;
-      if (!mbar_wait(full0 + 8 * s, (c / kStages) & 1, g.wait_cycles)) {
-        atomicOr(g.status, 4);
+    uint32_t q = 0;
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles && !*abort; t += gridDim.x, ++i) {
+      int z, m0, n0, c0, nk;
+      decode(t, z, m0, n0, c0, nk);
+      const int buf = i & 1, v = i >> 1;
+      if (v >= 1 && !mbar_wait(tempty0 + 8 * buf, (v - 1) & 1, g.wait_cycles, abort)) {
+        if (!*abort) atomicOr(g.status, 4);
         atomicExch(&abort_flag, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t sa = base + s * kStageBytes, sb = sa + kATileBytes;
+      const uint32_t acc = tmem + uint32_t(buf * BN);
+      bool ok = true;
+      for (int c = 0; c < nk; ++c, ++q) {
+        const uint32_t s = q % kStages, u = q / kStages;
+        if (!mbar_wait(full0 + 8 * s, u & 1, g.wait_cycles, abort)) {
+          if (!*abort) atomicOr(g.status, 4);
+          atomicExch(&abort_flag, 1);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t sa = base + s * kStageBytes, sb = sa + kATileBytes;
 #pragma unroll
-      for (int kk = 0; kk < kTcBK / 16; ++kk) {
-        const uint64_t da = AMN ? sw128_desc_mn(sa + kk * 2048) : sw128_desc(sa + kk * 32);
-        const uint64_t db = BMN ? sw128_desc_mn(sb + kk * 2048) : sw128_desc(sb + kk * 32);
-        mma_bf16_tc(tmem, da, db, idesc, (c | kk) != 0);
+        for (int kk = 0; kk < kTcBK / 16; ++kk) {
+          const uint64_t da = AMN ? sw128_desc_mn(sa + kk * 2048) : sw128_desc(sa + kk * 32);
+          const uint64_t db = BMN ? sw128_desc_mn(sb + kk * 2048) : sw128_desc(sb + kk * 32);
+          mma_bf16_tc(acc, da, db, idesc, (c | kk) != 0);
+        }
+        mma_commit(empty0 + 8 * s);
       }
-      mma_commit(empty0 + 8 * s);
+      if (!ok) break;
+      mma_commit(tfull0 + 8 * buf);
     }
+    // every MMA this thread issued completes before `done`
     mma_commit(done);
-  }
-  __syncwarp();
-  // epilogue: all warps wait for the accumulator
-  if (!mbar_wait(done, 0, g.wait_cycles)) atomicOr(g.status, 4);
-  __syncwarp();
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  const int quarter = warp & 3, half = warp >> 2;
-  const int row = m0 + 32 * quarter + lane;
-  const uint32_t trow = tmem + (uint32_t(32 * quarter) << 16);
-#pragma unroll 1
-  for (int j = half * (BN / 2); j < (half + 1) * (BN / 2); j += 32) {
-    float v[32];
-    tmem_ld32(trow + j, v);
-    if (row < g.M) {
-      const float *bias = g.bias + n0 + j;  // bias epilogues only
-      if (EPI == kEpiBiasSoftplus) {
-        uint32_t pk[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float a0 = softplus_sfu(v[2 * i] + __ldg(bias + 2 * i));
-          const float a1 = softplus_sfu(v[2 * i + 1] + __ldg(bias + 2 * i + 1));
-          const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
-          pk[i] = *reinterpret_cast<const uint32_t *>(&h);
-        }
-        uint4 *dst = reinterpret_cast<uint4 *>(g.Cb + size_t(row) * g.ldc + n0 + j);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-      } else if (EPI == kEpiBias) {
-        float4 *dst = reinterpret_cast<float4 *>(g.Cf + size_t(row) * g.ldc + n0 + j);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          dst[q] = make_float4(v[4 * q] + __ldg(bias + 4 * q), v[4 * q + 1] + __ldg(bias + 4 * q + 1),
-                               v[4 * q + 2] + __ldg(bias + 4 * q + 2), v[4 * q + 3] + __ldg(bias + 4 * q + 3));
-      } else if (EPI == kEpiDSoftplus) {
-        // the softplus derivative sigma(z) = 1 - exp(-softplus(z)) from the
-        // stored activation (32 BF16 values of this row: four 16-byte loads)
-        const uint4 *hv = reinterpret_cast<const uint4 *>(g.aux + size_t(row) * g.ldaux + n0 + j);
-        uint32_t pk[16];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint4 h4 = __ldg(hv + q);
-          const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[e]));
-            const int i = 8 * q + 2 * e;
-            const __nv_bfloat162 o = __floats2bfloat162_rn(v[i] * -expm1f(-hf.x), v[i + 1] * -expm1f(-hf.y));
-            pk[4 * q + e] = *reinterpret_cast<const uint32_t *>(&o);
-          }
-        }
-        uint4 *dst = reinterpret_cast<uint4 *>(g.Cb + size_t(row) * g.ldc + n0 + j);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-      } else {  // kEpiPartial: this k split's FP32 partial
-        float4 *dst = reinterpret_cast<float4 *>(g.Cf + size_t(blockIdx.z) * size_t(g.M) * g.ldc +
-                                                 size_t(row) * g.ldc + n0 + j);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else if (warp >= 4) {
+    // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 (rows of the
+    // tile), columns of half (w - 4) / 4 of it
+    const int qw = warp & 3, half = (warp - 4) >> 2;
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles && !*abort; t += gridDim.x, ++i) {
+      int z, m0, n0, c0, nk;
+      decode(t, z, m0, n0, c0, nk);
+      const int buf = i & 1, v = i >> 1;
+      if (!mbar_wait(tfull0 + 8 * buf, v & 1, g.wait_cycles, abort)) {
+        if (!*abort) atomicOr(g.status, 4);
+        atomicExch(&abort_flag, 1);
+        break;
       }
+      __syncwarp();
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int row = m0 + 32 * qw + lane;
+      const uint32_t trow = tmem + (uint32_t(32 * qw) << 16) + uint32_t(buf * BN);
+#pragma unroll 1
+      for (int j = half * (BN / 2); j < (half + 1) * (BN / 2); j += 32) {
+        float r[32];
+        tmem_ld32(trow + j, r);
+        if (row < g.M) epilogue32<EPI>(g, row, n0 + j, z, r);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
     }
   }
+  __syncwarp();
+  // every MMA has completed before TMEM is released
+  if (warp == 0 && !mbar_wait(done, 0, g.wait_cycles)) atomicOr(g.status, 4);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * BN));
   }
 }
 
@@ -350,9 +447,24 @@ constexpr size_t tc_smem() {
   return size_t(kStages) * (kATileBytes + size_t(BN) * kTcBK * 2) + 1024;
 }
 
+int sm_count() {
+  static int n = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 1;
+  });
+  return n;
+}
+
+// Persistent grid: the tiles, at most one CTA per SM.
 template <int EPI, int BN, bool AMN, bool BMN>
-cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, const TcArgs &a, int splits, cudaStream_t s) {
-  const dim3 grid(unsigned(a.N / BN), unsigned((a.M + kTcBM - 1) / kTcBM), unsigned(splits));
+cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, const TcArgs &a, cudaStream_t s) {
+  const long long tiles = (long long)(a.N / BN) * ((a.M + kTcBM - 1) / kTcBM) * a.splits;
+  const long long cap = (long long)sm_count();
+  const unsigned grid = unsigned(tiles < cap ? tiles : cap);
   mlp_gemm_tc<EPI, BN, AMN, BMN><<<grid, kTcThreads, tc_smem<BN>(), s>>>(ta, tb, a);
   return cudaGetLastError();
 }
@@ -431,6 +543,7 @@ cudaError_t launch_gemm_tc(GemmKind kind, int epi, const GemmArgs &g, const TcMa
   a.N = g.N;
   a.K = g.K;
   a.k_split = k_split;
+  a.splits = splits;
   a.bias = g.bias;
   a.aux = g.aux;
   a.ldaux = g.ldaux;
@@ -444,16 +557,16 @@ cudaError_t launch_gemm_tc(GemmKind kind, int epi, const GemmArgs &g, const TcMa
   switch (kind) {
     case kGemmForward:
       if (epi == kEpiBiasSoftplus)
-        return n64 ? launch_tc<kEpiBiasSoftplus, 64, false, false>(m.a, m.b, a, 1, s)
-                   : launch_tc<kEpiBiasSoftplus, 128, false, false>(m.a, m.b, a, 1, s);
-      return n64 ? launch_tc<kEpiBias, 64, false, false>(m.a, m.b, a, 1, s)
-                 : launch_tc<kEpiBias, 128, false, false>(m.a, m.b, a, 1, s);
+        return n64 ? launch_tc<kEpiBiasSoftplus, 64, false, false>(m.a, m.b, a, s)
+                   : launch_tc<kEpiBiasSoftplus, 128, false, false>(m.a, m.b, a, s);
+      return n64 ? launch_tc<kEpiBias, 64, false, false>(m.a, m.b, a, s)
+                 : launch_tc<kEpiBias, 128, false, false>(m.a, m.b, a, s);
     case kGemmDataGrad:
-      return n64 ? launch_tc<kEpiDSoftplus, 64, false, true>(m.a, m.b, a, 1, s)
-                 : launch_tc<kEpiDSoftplus, 128, false, true>(m.a, m.b, a, 1, s);
+      return n64 ? launch_tc<kEpiDSoftplus, 64, false, true>(m.a, m.b, a, s)
+                 : launch_tc<kEpiDSoftplus, 128, false, true>(m.a, m.b, a, s);
     case kGemmWeightGrad:
-      return n64 ? launch_tc<kEpiPartial, 64, true, true>(m.a, m.b, a, splits, s)
-                 : launch_tc<kEpiPartial, 128, true, true>(m.a, m.b, a, splits, s);
+      return n64 ? launch_tc<kEpiPartial, 64, true, true>(m.a, m.b, a, s)
+                 : launch_tc<kEpiPartial, 128, true, true>(m.a, m.b, a, s);
   }
   return cudaErrorInvalidValue;
 }
