@@ -50,7 +50,7 @@
 namespace pc {
 namespace {
 
-constexpr int kTcBM = 128, kTcBK = 64, kStages = 6, kTcThreads = 384;
+constexpr int kTcBM = 128, kTcBK = 64, kStages = 4, kTcThreads = 384;
 constexpr int kEpiWarps = 8;  // warps 4..11: two per TMEM lane quarter, each half the columns
 constexpr uint32_t kATileBytes = kTcBM * kTcBK * 2;  // 16 KB
 constexpr long long kWaitCycles = 2000000000ll;      // ~1 s at 2 GHz
@@ -183,54 +183,75 @@ __device__ __forceinline__ float dsoftplus(float h) {
   return h >= 0.03125f ? 1.f - __expf(-h) : h * fmaf(-0.5f * h, fmaf(-h, 0.3333333333f, 1.f), 1.f);
 }
 
-// The epilogue of 32 accumulator columns of one row: row `row`, columns
-// col .. col + 31 of C (bias epilogues: + bias; k split z for kEpiPartial).
+// Output element size of an epilogue (BF16 activations or gradients, FP32
+// outputs and partials) and the staging area of one epilogue warp: its 32
+// rows by half the tile's columns, at most 32 x 64 FP32 values.
 template <int EPI>
-__device__ __forceinline__ void epilogue32(const TcArgs &g, int row, int col, int z, const float (&v)[32]) {
-  if (EPI == kEpiBiasSoftplus) {
-    const float *bias = g.bias + col;
-    uint32_t pk[16];
+__host__ __device__ constexpr int out_bytes() { return (EPI == kEpiBiasSoftplus || EPI == kEpiDSoftplus) ? 2 : 4; }
+constexpr uint32_t kStageWarpBytes = 32 * 64 * 4;
+
+// The epilogue of 32 accumulator columns of one row (row `row`, columns
+// col .. col + 31 of C; bias epilogues add the bias; kEpiDSoftplus reads the
+// stored activation), written as 16-byte chunks c0 .. of this lane's row in
+// the warp's staging area (rows of rb bytes, chunk c of row r at chunk
+// c ^ (r & m), m = min(rb / 16, 8) - 1: the lanes' rows spread over the
+// banks, for these writes and for the row-wise copy).
+template <int EPI>
+__device__ __forceinline__ void epilogue32(const TcArgs &g, int row, int col, const float (&v)[32], uint32_t st,
+                                           int lane, int rb, int c0) {
+  auto put = [&](int c, uint4 x) {
+    const int m = (rb / 16 < 8 ? rb / 16 : 8) - 1;
+    const uint32_t a = st + uint32_t(lane * rb + ((c ^ (lane & m)) << 4));
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(x.x), "r"(x.y), "r"(x.z), "r"(x.w)
+                 : "memory");
+  };
+  if (EPI == kEpiBiasSoftplus || EPI == kEpiBias) {
+    const float4 *b4 = reinterpret_cast<const float4 *>(g.bias + col);
+    float b[32];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const float a0 = softplus_fast(v[2 * i] + __ldg(bias + 2 * i));
-      const float a1 = softplus_fast(v[2 * i + 1] + __ldg(bias + 2 * i + 1));
-      const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
-      pk[i] = *reinterpret_cast<const uint32_t *>(&h);
+    for (int q = 0; q < 8; ++q) {
+      const float4 t = __ldg(b4 + q);
+      b[4 * q] = t.x; b[4 * q + 1] = t.y; b[4 * q + 2] = t.z; b[4 * q + 3] = t.w;
     }
-    uint4 *dst = reinterpret_cast<uint4 *>(g.Cb + size_t(row) * g.ldc + col);
+    if (EPI == kEpiBiasSoftplus) {
+      uint32_t pk[16];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-  } else if (EPI == kEpiBias) {
-    const float *bias = g.bias + col;
-    float4 *dst = reinterpret_cast<float4 *>(g.Cf + size_t(row) * g.ldc + col);
+      for (int i = 0; i < 16; ++i) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(softplus_fast(v[2 * i] + b[2 * i]),
+                                                       softplus_fast(v[2 * i + 1] + b[2 * i + 1]));
+        pk[i] = *reinterpret_cast<const uint32_t *>(&h);
+      }
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      dst[q] = make_float4(v[4 * q] + __ldg(bias + 4 * q), v[4 * q + 1] + __ldg(bias + 4 * q + 1),
-                           v[4 * q + 2] + __ldg(bias + 4 * q + 2), v[4 * q + 3] + __ldg(bias + 4 * q + 3));
+      for (int q = 0; q < 4; ++q) put(c0 + q, make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]));
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        put(c0 + q, make_uint4(__float_as_uint(v[4 * q] + b[4 * q]), __float_as_uint(v[4 * q + 1] + b[4 * q + 1]),
+                               __float_as_uint(v[4 * q + 2] + b[4 * q + 2]), __float_as_uint(v[4 * q + 3] + b[4 * q + 3])));
+    }
   } else if (EPI == kEpiDSoftplus) {
-    // the softplus derivative sigma(z) = 1 - exp(-softplus(z)) from the
-    // stored activation (32 BF16 values of this row: four 16-byte loads)
+    // the softplus derivative from the stored activation (32 BF16 values of
+    // this row: four 16-byte loads)
     const uint4 *hv = reinterpret_cast<const uint4 *>(g.aux + size_t(row) * g.ldaux + col);
-    uint32_t pk[16];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint4 h4 = __ldg(hv + q);
       const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w};
+      uint32_t pk[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float2 hf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hw[e]));
         const int i = 8 * q + 2 * e;
         const __nv_bfloat162 o = __floats2bfloat162_rn(v[i] * dsoftplus(hf.x), v[i + 1] * dsoftplus(hf.y));
-        pk[4 * q + e] = *reinterpret_cast<const uint32_t *>(&o);
+        pk[e] = *reinterpret_cast<const uint32_t *>(&o);
       }
+      put(c0 + q, make_uint4(pk[0], pk[1], pk[2], pk[3]));
     }
-    uint4 *dst = reinterpret_cast<uint4 *>(g.Cb + size_t(row) * g.ldc + col);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
   } else {  // kEpiPartial: this k split's FP32 partial
-    float4 *dst = reinterpret_cast<float4 *>(g.Cf + size_t(z) * size_t(g.M) * g.ldc + size_t(row) * g.ldc + col);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    for (int q = 0; q < 8; ++q)
+      put(c0 + q, make_uint4(__float_as_uint(v[4 * q]), __float_as_uint(v[4 * q + 1]), __float_as_uint(v[4 * q + 2]),
+                             __float_as_uint(v[4 * q + 3])));
   }
 }
 
@@ -264,6 +285,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[kStages]);
   const uint32_t tfull0 = su32(&bars[2 * kStages]), tempty0 = su32(&bars[2 * kStages + 2]);
   const uint32_t done = su32(&bars[2 * kStages + 4]);
+  const uint32_t stage0 = base + kStages * kStageBytes;  // epilogue staging, kStageWarpBytes per warp
   auto decode = [&](int t, int &z, int &m0, int &n0, int &c0, int &nk) {
     z = t / (tm * tn);
     const int r = t - z * tm * tn;
@@ -387,15 +409,42 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const int row = m0 + 32 * qw + lane;
       const uint32_t trow = tmem + (uint32_t(32 * qw) << 16) + uint32_t(buf * BN);
+      // this warp's 32 rows x BN / 2 columns, staged as rows of rb bytes
+      constexpr int EB = out_bytes<EPI>();
+      constexpr int rb = (BN / 2) * EB;
+      const uint32_t st = stage0 + uint32_t(warp - 4) * kStageWarpBytes;
+      const int col0 = n0 + half * (BN / 2);
 #pragma unroll 1
-      for (int j = half * (BN / 2); j < (half + 1) * (BN / 2); j += 32) {
+      for (int j = 0; j < BN / 2; j += 32) {
         float r[32];
-        tmem_ld32(trow + j, r);
-        if (row < g.M) epilogue32<EPI>(g, row, n0 + j, z, r);
+        tmem_ld32(trow + half * (BN / 2) + j, r);
+        if (row < g.M) epilogue32<EPI>(g, row, col0 + j, r, st, lane, rb, j * EB / 16);
       }
+      // the accumulator buffer is free once read
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+      // row-wise copy to C: CPR lanes per row, each 16 bytes (whole lines)
+      {
+        constexpr int CPR = rb / 16, RPI = 32 / CPR, SW = (CPR < 8 ? CPR : 8) - 1;
+        const int rr = lane / CPR, cc = lane % CPR;
+        char *cbase = EPI == kEpiBiasSoftplus || EPI == kEpiDSoftplus
+                          ? reinterpret_cast<char *>(g.Cb)
+                          : reinterpret_cast<char *>(g.Cf + (EPI == kEpiPartial ? size_t(z) * size_t(g.M) * g.ldc : 0));
+#pragma unroll 4
+        for (int r0 = 0; r0 < 32; r0 += RPI) {
+          const int lr = r0 + rr, grow = m0 + 32 * qw + lr;
+          uint4 x;
+          const uint32_t a = st + uint32_t(lr * rb + ((cc ^ (lr & SW)) << 4));
+          asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];\n"
+                       : "=r"(x.x), "=r"(x.y), "=r"(x.z), "=r"(x.w)
+                       : "r"(a)
+                       : "memory");
+          if (grow < g.M)
+            *reinterpret_cast<uint4 *>(cbase + (size_t(grow) * g.ldc + col0) * EB + size_t(cc) * 16) = x;
+        }
+        __syncwarp();
+      }
     }
   }
   __syncwarp();
@@ -444,7 +493,7 @@ bool make_map(CUtensorMap &m, const __nv_bfloat16 *p, uint64_t rows, uint64_t co
 
 template <int BN>
 constexpr size_t tc_smem() {
-  return size_t(kStages) * (kATileBytes + size_t(BN) * kTcBK * 2) + 1024;
+  return size_t(kStages) * (kATileBytes + size_t(BN) * kTcBK * 2) + size_t(kEpiWarps) * kStageWarpBytes + 1024;
 }
 
 int sm_count() {
