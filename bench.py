@@ -717,6 +717,26 @@ def run_portfolio(args):
     t_dev = sum(a.elapsed_time(b) for a, b in evs) / 1e3
     price, se = pc.pc_batch_results(plan, len(mine))
 
+    # the other arrangement, timed beside it: one launch of the kernel for
+    # every underlying count instead of one launch per group
+    pc.pc_batch_set_single_launch(plan, True)
+    pc.pc_batch_tune(plan, 2)
+    sinfo = pc.pc_batch_query(plan)
+    s_ms = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pc.pc_batch_launch(plan)
+        b.record(stream)
+        torch.cuda.synchronize()
+        s_ms.append(a.elapsed_time(b))
+    s_price, _ = pc.pc_batch_results(plan, len(mine))
+    single = {"ms_per_step": statistics.median(s_ms), "block": sinfo.config.block,
+              "unit_split": sinfo.config.unit_split, "prices_equal_grouped": bool(np.array_equal(s_price, price)),
+              "note": "pc_batch_set_single_launch: one persistent launch for every contract, tuned the same way"}
+    pc.pc_batch_set_single_launch(plan, False)
+
     # end to end through the public API: load every program from host
     # memory, price the portfolio in one call, read the prices back
     n_e2e = max(2, min(args.e2e_steps, 5))
@@ -761,6 +781,7 @@ def run_portfolio(args):
             "batch": {"groups": binfo.n_groups, "units": binfo.n_units, "tiles": binfo.n_tiles,
                       "block": binfo.config.block, "unit_split": binfo.config.unit_split,
                       "paths_per_thread": binfo.paths_per_thread, "tuned_ms": binfo.last_ms},
+            "single_launch": single,
             "e2e": {"value": ws * len(mine) / e2e_step, "unit": "contracts/s",
                     "h2d_bytes_per_step": int(sum(w_.nbytes + k_.nbytes + 4 * len(tp)
                                                   for (w_, k_, tp) in programs)),

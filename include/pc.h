@@ -448,6 +448,19 @@ pc_status pc_batch_results(pc_batch *plan, double *out_price, double *out_stderr
                            double *out_sums);
 
 pc_status pc_batch_query(const pc_batch *plan, pc_batch_info *info);
+
+/* Launch arrangement of a plan's replay.  enabled = 0 (the default): one
+ * persistent launch per (underlying count, power-of-two class of per-path
+ * shared words) group, as parallel branches of the graph, each kernel
+ * specialised to its count and sized for its group's footprint.
+ * enabled = 1: one persistent launch for every contract (one kernel for all
+ * underlying counts, at the register bound of the four-underlying
+ * generator, sized for the largest footprint of all), units ordered
+ * costliest first over the whole portfolio.  Re-instantiates the graph with
+ * the current launch shape (pc_batch_tune may be run again); results are
+ * the same either way.  Errors: PC_EINVAL, PC_ELIMIT (the largest footprint
+ * does not fit one launch; the plan keeps its grouping), PC_ECUDA. */
+pc_status pc_batch_set_single_launch(pc_batch *plan, int32_t enabled);
 pc_status pc_batch_destroy(pc_batch *plan);
 
 /* One-shot portfolio pricing: pc_batch_create with the default shape,

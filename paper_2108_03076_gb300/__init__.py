@@ -139,6 +139,7 @@ _SIGS = {
     "pc_batch_launch": [VP],
     "pc_batch_results": [VP, PD, PD, PD],
     "pc_batch_query": [VP, C.POINTER(BatchInfo)],
+    "pc_batch_set_single_launch": [VP, C.c_int32],
     "pc_batch_destroy": [VP],
     "pc_mlp_create": [VP, C.POINTER(C.c_int32), C.c_int32, U64, U64, C.POINTER(VP)],
     "pc_mlp_destroy": [VP],
@@ -439,6 +440,10 @@ def pc_batch_results(plan: int, n: int, sums: bool = False):
     _check(lib().pc_batch_results(VP(plan), _ptr(price, C.c_double), _ptr(se, C.c_double),
                                   _ptr(out, C.c_double) if sums else None))
     return (price, se, out.reshape(n, 3)) if sums else (price, se)
+
+
+def pc_batch_set_single_launch(plan: int, enabled: bool) -> None:
+    _check(lib().pc_batch_set_single_launch(VP(plan), 1 if enabled else 0))
 
 
 def pc_batch_query(plan: int) -> BatchInfo:

@@ -66,6 +66,7 @@ struct pc_batch {
   uint64_t n_units = 0;
   double paths_per_thread = 0.0;
   bool tuned = false;
+  bool single = false;              // one launch of batch_kernel_any for every contract
   double last_ms = 0.0;
 };
 
@@ -86,17 +87,18 @@ int words_class(int words) {
 
 // Contracts grouped by (underlying count, power-of-two class of per-path
 // shared words): one persistent launch per group, sized for its largest
-// footprint.
+// footprint.  In single-launch mode every contract is in one group (d = 0:
+// batch_kernel_any, sized for the largest footprint of all).
 void build_groups(pc_batch *B) {
   std::map<std::pair<int, int>, uint32_t> index;
   B->groups.clear();
   for (size_t i = 0; i < B->n; ++i) {
-    const auto key = std::make_pair(B->d[i], words_class(B->words[i]));
+    const auto key = B->single ? std::make_pair(0, 0) : std::make_pair(B->d[i], words_class(B->words[i]));
     auto it = index.find(key);
     if (it == index.end()) {
       it = index.emplace(key, uint32_t(B->groups.size())).first;
       Group g;
-      g.d = B->d[i];
+      g.d = B->single ? 0 : B->d[i];
       B->groups.push_back(g);
     }
     Group &g = B->groups[it->second];
@@ -416,6 +418,25 @@ pc_status pc_batch_tune(pc_batch *B, int32_t reps) {
   if (s != PC_OK) return s;
   B->tuned = true;
   B->last_ms = best_ms;
+  return PC_OK;
+}
+
+pc_status pc_batch_set_single_launch(pc_batch *B, int32_t enabled) {
+  if (!B || !B->exec) return fail(PC_EINVAL, "null or unconfigured batch plan");
+  if (enabled != 0 && enabled != 1) return fail(PC_EINVAL, "enabled must be 0 or 1");
+  const bool was = B->single;
+  B->single = enabled != 0;
+  build_groups(B);
+  pc_status s = configure(B, B->cfg);
+  if (s == PC_OK) s = capture(B);
+  if (s != PC_OK) {
+    // back to the previous grouping (its configuration was valid)
+    B->single = was;
+    build_groups(B);
+    if (configure(B, B->cfg) == PC_OK) capture(B);
+    return s;
+  }
+  B->tuned = false;
   return PC_OK;
 }
 

@@ -39,25 +39,62 @@ __global__ void __launch_bounds__(kBlock) price_kernel(const __grid_constant__ P
   });
 }
 
-// Portfolio kernel.  Warps take work units (a contract and a run of its
-// tiles) from the group's counter in the order of the unit array.  When a
+// Portfolio kernels.  Warps take work units (a contract and a run of its
+// tiles) from the launch's counter in the order of the unit array.  When a
 // warp's unit belongs to another contract than its previous one, the warp
 // copies that contract's arguments into its own slot of shared memory; the
 // program and constant pool are read from global memory through L1.  The
-// tiles run as in price_kernel and finish into
-// the contract's own reduction scratch, so each contract's sums are those of
-// a single-contract launch.
-// At least 5 resident 128-thread blocks (<= 102 registers): -4 % per
-// portfolio replay against the uncapped 112 registers, 6 blocks spill.
+// tiles run as in price_kernel and finish into the contract's own reduction
+// scratch, so each contract's sums are those of a single-contract launch.
+// batch_kernel<d> serves the contracts of one underlying count;
+// batch_kernel_any serves every count in one launch (the unit's contract
+// selects the generator), at the register bound the four-underlying
+// generator needs.
+
+// The tiles of unit U of contract a (arguments in the warp's slot).
 template <int D>
-__global__ void __launch_bounds__(kBlock, 5) batch_kernel(const BatchArgs b) {
+__device__ __forceinline__ void batch_unit(const PriceArgs &a, const BatchUnit &U, float2 *R, int lane) {
+  const uint4 *P = reinterpret_cast<const uint4 *>(a.prog);
+  const float *pool = reinterpret_cast<const float *>(P + a.n_insn);
+  float Bm[D * D], S0[D];
+  load_model_regs<D>(a.m, Bm, S0);
+  Rng2 g;
+  g.stream = a.stream;
+#pragma unroll
+  for (int i = 0; i < 20; ++i) g.rk[i] = a.rk[i];
+  for (uint32_t k = 0; k < U.n_tiles; ++k) {
+    const uint64_t tile = U.tile0 + k;
+    const uint64_t i0 = tile * kTilePaths + lane, i1 = i0 + 32;
+    const bool live0 = i0 < a.n_paths, live1 = i1 < a.n_paths;
+    const uint64_t p0 = a.path_offset + i0, p1 = a.path_offset + i1;
+    g.plo[0] = uint32_t(p0);
+    g.phi[0] = uint32_t(p0 >> 32);
+    g.plo[1] = uint32_t(p1);
+    g.phi[1] = uint32_t(p1 >> 32);
+    const float2 x = eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0);
+    Moments<2> mo;
+    if (live0) {
+      mo.add(0, x.x);
+      mo.add_prod(1, x.x, x.x);
+    }
+    if (live1) {
+      mo.add(0, x.y);
+      mo.add_prod(1, x.y, x.y);
+    }
+    double tp[2];
+    mo.warp_total(tp);
+    finish_tile<2>(a, tile, tp, lane);
+  }
+}
+
+// The unit loop; RUN(a, U, R, lane) runs one unit.
+template <typename RUN>
+__device__ __forceinline__ void batch_units(const BatchArgs &b, RUN run) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *slot = smem + (b.slot_bytes / 4) * warp;
   float2 *R = reinterpret_cast<float2 *>(smem + (b.slot_bytes / 4) * (blockDim.x >> 5)) + threadIdx.x;
   const PriceArgs &a = *reinterpret_cast<const PriceArgs *>(slot);
-  float Bm[D * D], S0[D];
-  Rng2 g;
   uint32_t cur = 0xffffffffu;
   for (;;) {
     unsigned long long u = 0;
@@ -72,36 +109,26 @@ __global__ void __launch_bounds__(kBlock, 5) batch_kernel(const BatchArgs b) {
       __syncwarp();
       cur = U.item;
     }
-    const uint4 *P = reinterpret_cast<const uint4 *>(a.prog);
-    const float *pool = reinterpret_cast<const float *>(P + a.n_insn);
-    load_model_regs<D>(a.m, Bm, S0);
-    g.stream = a.stream;
-#pragma unroll
-    for (int i = 0; i < 20; ++i) g.rk[i] = a.rk[i];
-    for (uint32_t k = 0; k < U.n_tiles; ++k) {
-      const uint64_t tile = U.tile0 + k;
-      const uint64_t i0 = tile * kTilePaths + lane, i1 = i0 + 32;
-      const bool live0 = i0 < a.n_paths, live1 = i1 < a.n_paths;
-      const uint64_t p0 = a.path_offset + i0, p1 = a.path_offset + i1;
-      g.plo[0] = uint32_t(p0);
-      g.phi[0] = uint32_t(p0 >> 32);
-      g.plo[1] = uint32_t(p1);
-      g.phi[1] = uint32_t(p1 >> 32);
-      const float2 x = eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0);
-      Moments<2> mo;
-      if (live0) {
-        mo.add(0, x.x);
-        mo.add_prod(1, x.x, x.x);
-      }
-      if (live1) {
-        mo.add(0, x.y);
-        mo.add_prod(1, x.y, x.y);
-      }
-      double tp[2];
-      mo.warp_total(tp);
-      finish_tile<2>(a, tile, tp, lane);
-    }
+    run(a, U, R, lane);
   }
+}
+
+// At least 5 resident 128-thread blocks (<= 102 registers): -4 % per
+// portfolio replay against the uncapped 112 registers, 6 blocks spill.
+template <int D>
+__global__ void __launch_bounds__(kBlock, 5) batch_kernel(const BatchArgs b) {
+  batch_units(b, [](const PriceArgs &a, const BatchUnit &U, float2 *R, int lane) { batch_unit<D>(a, U, R, lane); });
+}
+
+__global__ void __launch_bounds__(kBlock, 5) batch_kernel_any(const BatchArgs b) {
+  batch_units(b, [](const PriceArgs &a, const BatchUnit &U, float2 *R, int lane) {
+    switch (a.m.d) {
+      case 1: batch_unit<1>(a, U, R, lane); break;
+      case 2: batch_unit<2>(a, U, R, lane); break;
+      case 3: batch_unit<3>(a, U, R, lane); break;
+      default: batch_unit<4>(a, U, R, lane); break;
+    }
+  });
 }
 
 __global__ void debug_philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
@@ -202,6 +229,10 @@ int price_occupancy(uint64_t v, int block, size_t smem) {
     }                                                                                                \
   } while (0)
   switch (d) {
+    case 0:
+      e = set_smem(batch_kernel_any, smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_any, block, smem);
+      break;
     case 1: OCC(1); break;
     case 2: OCC(2); break;
     case 3: OCC(3); break;
@@ -248,6 +279,10 @@ int batch_blocks_per_sm(int d, int block, size_t smem) {
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<DD>, block, smem); \
   } while (0)
   switch (d) {
+    case 0:
+      e = set_smem(batch_kernel_any, smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_any, block, smem);
+      break;
     case 1: OCC(1); break;
     case 2: OCC(2); break;
     case 3: OCC(3); break;
@@ -260,6 +295,7 @@ int batch_blocks_per_sm(int d, int block, size_t smem) {
 
 cudaError_t launch_batch(const BatchArgs &b, int d, int grid, int block, size_t smem, cudaStream_t s) {
   switch (d) {
+    case 0: batch_kernel_any<<<grid, block, smem, s>>>(b); break;
     case 1: batch_kernel<1><<<grid, block, smem, s>>>(b); break;
     case 2: batch_kernel<2><<<grid, block, smem, s>>>(b); break;
     case 3: batch_kernel<3><<<grid, block, smem, s>>>(b); break;

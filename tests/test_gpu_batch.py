@@ -111,6 +111,30 @@ def test_autotuner_keeps_results_and_reports_its_choice(eng, mixed):
         pc.pc_batch_destroy(plan)
 
 
+@pytest.mark.parametrize("block,split", [(128, 128), (64, 8)])
+def test_single_launch_gives_the_same_bits(eng, mixed, block, split):
+    """One launch of the kernel for every underlying count (the contracts'
+    generators selected per unit) against single-contract launches, and
+    back to the grouped arrangement."""
+    models, contracts, n_paths = mixed
+    want = single_sums(eng, models, contracts, n_paths, range(len(contracts)))
+    plan = pc.pc_batch_create(models, contracts, n_paths, SEED, block=block, unit_split=split)
+    try:
+        grouped = pc.pc_batch_query(plan).n_groups
+        pc.pc_batch_set_single_launch(plan, True)
+        assert pc.pc_batch_query(plan).n_groups == 1
+        check_identical(eng, plan, models, contracts, n_paths, want)
+        pc.pc_batch_tune(plan, 1)
+        check_identical(eng, plan, models, contracts, n_paths, want)
+        pc.pc_batch_set_single_launch(plan, False)
+        assert pc.pc_batch_query(plan).n_groups == grouped
+        check_identical(eng, plan, models, contracts, n_paths, want)
+        with pytest.raises(pc.PcError):   # only 0 and 1
+            pc._check(pc.lib().pc_batch_set_single_launch(pc.VP(plan), 2))
+    finally:
+        pc.pc_batch_destroy(plan)
+
+
 @pytest.fixture(scope="module")
 def portfolio(eng):
     items = W.portfolio()
