@@ -1086,11 +1086,29 @@ def run_learned(args):
     d1, t1 = net.tables(model, gamma=False)   # same tables, first-order control only
     (_, s_delta), (pp, sp) = pc.pc_price_cv(model, contract, d1, t1.data_ptr(), 1 << 18, VS)
     (_, s_gamma), _ = pc.pc_price_cv(model, contract, desc, tabs.data_ptr(), 1 << 18, VS)
-    if s_gamma >= s_delta:          # keep the first-order control alone
-        desc, tabs = d1, t1
-    scv_b = min(s_gamma, s_delta)
     n_plain = int(math.ceil((sp * math.sqrt(1 << 18) / (TARGET_REL_SE * abs(pp))) ** 2))
-    n_cv = int(math.ceil((scv_b * math.sqrt(1 << 18) / (TARGET_REL_SE * abs(pp))) ** 2))
+    n_for = lambda s_: int(math.ceil((s_ * math.sqrt(1 << 18) / (TARGET_REL_SE * abs(pp))) ** 2))  # noqa: E731
+
+    def cv_ms(dsc, tb, n):
+        for _ in range(2):
+            pc.pc_price_cv(model, contract, dsc, tb.data_ptr(), n, w.seed)
+        ts = []
+        for _ in range(5):
+            a, b = ev(), ev()
+            a.record(stream)
+            pc.pc_price_cv(model, contract, dsc, tb.data_ptr(), n, w.seed)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    # the arm that reaches the target in less GPU time: the second-order
+    # term removes more variance, the first-order kernel is cheaper per path
+    arm_ms = {"first_order": cv_ms(d1, t1, n_for(s_delta)), "second_order": cv_ms(desc, tabs, n_for(s_gamma))}
+    if arm_ms["first_order"] <= arm_ms["second_order"]:
+        desc, tabs = d1, t1
+    scv_b = s_delta if desc is d1 else s_gamma
+    n_cv = n_for(scv_b)
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
@@ -1148,7 +1166,8 @@ def run_learned(args):
                        "price": cv_price, "stderr": cv_se,
                        "second_order_term": bool(desc.use_gamma), "beta": desc.beta, "beta2": desc.beta2,
                        "variance_ratio": (sp / scv_b) ** 2,
-                       "variance_ratio_first_order_only": (sp / s_delta) ** 2},
+                       "variance_ratio_first_order_only": (sp / s_delta) ** 2,
+                       "arm_pricing_ms": arm_ms},
         "gpu_time_ratio_plain_over_cv": t_plain / t_cv,
         "training": {"data_s_wall": t_data, "train_s_gpu": t_train, "samples": len(data.x)},
         "surrogate": {"value": surrogate, "mc_price": plain_price,
