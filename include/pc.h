@@ -690,6 +690,15 @@ pc_status pc_debug_fail_allocations(pc_ctx *ctx, int32_t count);
  * clears it.  Blocks until written. */
 pc_status pc_debug_set_status(pc_ctx *ctx, int32_t value);
 
+/* Paths a lane of the context's specialised pricing kernels for programs
+ * that read no date behind the frontier: pairs = 1 (two paths a lane), 2
+ * (four: the per-op bridge schedule and the per-instruction control serve
+ * twice the paths, with twice the per-thread bridge stack) or 0, the
+ * default (two pairs when the model has at least 64 dates, else one).  The
+ * per-path values and sums are the same either way; the kernels are cached
+ * per choice.  Errors: PC_EINVAL. */
+pc_status pc_debug_set_jit_pairs(pc_ctx *ctx, int32_t pairs);
+
 /* Failure test of the network's tensor-core product: while `on`, its TMA
  * producer withholds the copies of the first k-chunk, so the MMA issuer's
  * and the producer's bounded mbarrier waits expire (after about 10 ms

@@ -129,6 +129,7 @@ _SIGS = {
     "pc_price_batch": [SZ, C.POINTER(VP), C.POINTER(VP), C.POINTER(U64), U64, PD, PD],
     "pc_set_window_mode": [VP, C.c_int32],
     "pc_set_jit": [VP, C.c_int32],
+    "pc_debug_set_jit_pairs": [VP, C.c_int32],
     "pc_jit_compile": [VP, VP],
     "pc_debug_jit_compile": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, I32, I32, C.POINTER(SZ)],
     "pc_debug_jit_source": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, I32, I32, C.c_char_p, SZ, C.POINTER(SZ)],
@@ -356,6 +357,10 @@ def pc_debug_set_status(ctx: int, value: int) -> None:
 
 def pc_debug_mlp_withhold_tma(net: int, on: bool) -> None:
     _check(lib().pc_debug_mlp_withhold_tma(VP(net), int(bool(on))))
+
+
+def pc_debug_set_jit_pairs(ctx: int, pairs: int) -> None:
+    _check(lib().pc_debug_set_jit_pairs(VP(ctx), int(pairs)))
 
 
 def pc_set_jit(ctx: int, enabled: bool) -> None:

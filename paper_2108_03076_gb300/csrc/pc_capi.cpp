@@ -330,16 +330,25 @@ pc_status run_greeks(const pc_model *m, const pc_contract *k, uint64_t n_paths, 
 
 // Kind bits of the launch's specialised pricing kernel beyond the variant:
 // the window of dates in HBM, or a window of one date (a program that reads
-// no date behind the frontier), which the kernel keeps in registers.
-int jit_window_kind(const Launch &L) {
+// no date behind the frontier), which the kernel keeps in registers, then
+// with the context's choice of two path pairs a lane.
+int jit_window_kind(const pc_ctx *c, const Launch &L) {
   if (L.hbm_window) return kJitHbm;
-  return L.args.lay.win == 1 ? kJitWinRegs : 0;
+  if (L.args.lay.win != 1) return 0;
+  // automatic: two pairs where a path walks many dates (the daily barrier's
+  // 365: 6.84 -> 6.49 ms at 2^22 paths); a few dates gain nothing (5 dates:
+  // 0.069 ms either way), the tile loop and the reduction dominate there
+  const bool two = c->jit_pairs == 2 || (c->jit_pairs == 0 && L.args.m.n >= kJitPairsMinDates);
+  return kJitWinRegs | (two ? kJitPairs2 : 0);
 }
 
 // The specialised evaluator keeps its operand stack in registers, and with
 // kJitWinRegs the window too: drop those words from the per-thread shared
 // region of the launch.  Returns the launch's dynamic shared memory.
-size_t jit_layout(const pc_contract *k, Launch &L) {
+// With two path pairs a lane the bridge stack holds both pairs' values per
+// level (twice the words), and the block is re-chosen for the most resident
+// warps that shared memory allows.
+size_t jit_layout(const pc_ctx *c, const pc_contract *k, Launch &L, int bits) {
   Layout &lay = L.args.lay;
   const int shift = lay.off_bstack;
   lay.stack = 0;
@@ -347,7 +356,22 @@ size_t jit_layout(const pc_contract *k, Launch &L) {
   lay.off_cache -= shift;
   lay.off_win -= shift;
   lay.words -= shift;
-  if (jit_window_kind(L) == kJitWinRegs) lay.words = lay.off_win;
+  if (bits & kJitWinRegs) lay.words = lay.off_win;
+  if (bits & kJitPairs2) {
+    lay.words = lay.off_bstack + 2 * (lay.off_cache - lay.off_bstack);
+    int best = 0, best_warps = 0;
+    for (int b = kBlock; b >= 32; b /= 2) {
+      const size_t sm = price_smem_bytes(k->prog.code.size(), pool_padded(k->prog), lay.words, b);
+      if (sm + kStaticSmemReserve > size_t(c->max_smem)) continue;
+      const size_t per = sm + kJitStaticSmem + size_t(c->smem_reserve);
+      const int blocks = c->sm_smem > 0 ? std::min<int>(32, int(size_t(c->sm_smem) / per)) : 1;
+      if (blocks * (b / 32) > best_warps) {
+        best_warps = blocks * (b / 32);
+        best = b;
+      }
+    }
+    if (best) L.block = best;
+  }
   return price_smem_bytes(k->prog.code.size(), pool_padded(k->prog), lay.words, L.block);
 }
 
@@ -381,8 +405,8 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
   if (c->jit && jit_eligible(k)) {
     // the contract's run-time specialised kernel (same arguments and shape)
     cudaKernel_t jk = nullptr;
-    const int wk = jit_window_kind(L);
-    const size_t smem = jit_layout(k, L);
+    const int wk = jit_window_kind(c, L);
+    const size_t smem = jit_layout(c, k, L, wk);
     s = jit_kernel(k, m->H.d, (d_payoffs != nullptr ? kJitPriceWrite : kJitPrice) | wk, L.block, jk,
                    jit_min_blocks(c, smem, L.block));
     if (s != PC_OK) return s;
@@ -391,7 +415,9 @@ pc_status run_price(const pc_model *m, const pc_contract *k, uint64_t n_paths, u
     CU(jit_occupancy(c, kern, L.block, smem, nb), "jit occupancy");
     if (nb < 1) return fail(PC_ELIMIT, "specialised kernel cannot be resident");
     const uint64_t wpb = uint64_t(L.block) / 32;
-    const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * nb, (L.args.n_tiles + wpb - 1) / wpb));
+    // a warp takes a tile, or a pair of tiles with two path pairs a lane
+    const uint64_t units = (wk & kJitPairs2) ? (L.args.n_tiles + 1) / 2 : L.args.n_tiles;
+    const int grid = int(std::min<uint64_t>(uint64_t(c->sm_count) * nb, (units + wpb - 1) / wpb));
     if (L.hbm_window) {
       // the HBM window holds a column per thread of this launch's grid
       L.grid = grid;
@@ -935,6 +961,13 @@ pc_status pc_set_window_mode(pc_ctx *c, int32_t mode) {
   return PC_OK;
 }
 
+pc_status pc_debug_set_jit_pairs(pc_ctx *c, int32_t pairs) {
+  if (!c) return fail(PC_EINVAL, "null context");
+  if (pairs < 0 || pairs > 2) return fail(PC_EINVAL, "pairs must be 0 (automatic), 1 or 2");
+  c->jit_pairs = pairs;
+  return PC_OK;
+}
+
 pc_status pc_set_jit(pc_ctx *c, int32_t enabled) {
   if (!c) return fail(PC_EINVAL, "null context");
   if (enabled != 0 && enabled != 1) return fail(PC_EINVAL, "enabled must be 0 or 1");
@@ -953,8 +986,8 @@ pc_status pc_jit_compile(const pc_model *m, const pc_contract *k) {
   if (s != PC_OK) return s;
   CU(cudaSetDevice(m->ctx->device), "cudaSetDevice");
   cudaKernel_t jk = nullptr;
-  const int wk = jit_window_kind(L);
-  const size_t smem = jit_layout(k, L);
+  const int wk = jit_window_kind(m->ctx, L);
+  const size_t smem = jit_layout(m->ctx, k, L, wk);
   return jit_kernel(k, m->H.d, kJitPrice | wk, L.block, jk, jit_min_blocks(m->ctx, smem, L.block));
 }
 

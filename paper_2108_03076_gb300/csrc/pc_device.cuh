@@ -134,11 +134,15 @@ __device__ __forceinline__ void box_muller2(uint32_t a0, uint32_t b0, uint32_t a
 // the lane's first path, .y for its second), so each fetched and decoded
 // instruction does the work of two paths and the two independent dependency
 // chains (Philox rounds, Box-Muller, bridge) overlap in the pipeline.
-struct Rng2 {
-  uint32_t plo[2], phi[2];
+// A lane with H pairs of paths (H = 2 in a specialised kernel with four
+// paths per lane) keeps the counters of its 2H paths.
+template <int H>
+struct RngH {
+  uint32_t plo[2 * H], phi[2 * H];
   uint32_t stream;
   uint32_t rk[20];  // Philox round keys (PriceArgs::rk), copied: the compiler keeps them uniform
 };
+using Rng2 = RngH<1>;
 
 // The four normals of Philox block b of both paths.
 __device__ __forceinline__ void block_normals2(uint32_t b, const Rng2 &g, float2 (&e)[4]) {
@@ -146,6 +150,18 @@ __device__ __forceinline__ void block_normals2(uint32_t b, const Rng2 &g, float2
   const uint4 x1 = philox_rk(make_uint4(b, g.plo[1], g.phi[1], g.stream), g.rk);
   box_muller2(x0.x, x0.y, x1.x, x1.y, e[0], e[1]);
   box_muller2(x0.z, x0.w, x1.z, x1.w, e[2], e[3]);
+}
+
+// The same for each pair h of a lane's 2H paths.
+template <int H>
+__device__ __forceinline__ void block_normals_h(uint32_t b, const RngH<H> &g, float2 (&e)[H][4]) {
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const uint4 x0 = philox_rk(make_uint4(b, g.plo[2 * h], g.phi[2 * h], g.stream), g.rk);
+    const uint4 x1 = philox_rk(make_uint4(b, g.plo[2 * h + 1], g.phi[2 * h + 1], g.stream), g.rk);
+    box_muller2(x0.x, x0.y, x1.x, x1.y, e[h][0], e[h][1]);
+    box_muller2(x0.z, x0.w, x1.z, x1.w, e[h][2], e[h][3]);
+  }
 }
 
 // Slot s of this thread in the word-interleaved per-thread region (the
@@ -175,95 +191,119 @@ __device__ __forceinline__ void win_store(float2 *R, const Layout &lay, int w, f
     SL(lay.off_win + w) = v;
 }
 
-template <int D>
+// Per-path state of a lane's H pairs of paths; the bridge stack holds, per
+// level, the D values of pair 0, then of pair 1 (D H slots a level).
+template <int D, int H = 1>
 struct PathState {
-  float2 w[D];                  // W at the last produced date
-  float2 zc[3];                 // words 1..3 of the last Philox block (d < 4)
+  float2 w[H][D];               // W at the last produced date
+  float2 zc[H][3];              // words 1..3 of the last Philox block (d < 4)
   int f;                        // last produced ordinal (frontier), warp-uniform
   int bsp;                      // bridge stack size, warp-uniform
   int k;                        // ops run so far (the next op's number), warp-uniform
 #ifdef PC_WIN_REGS
-  float2 s[D];                  // S at the frontier date: the whole window of a program
+  float2 s[H][D];               // S at the frontier date: the whole window of a program
                                 // that reads no date behind the frontier
 #endif
 };
 
-// A path's state at its start; the bottom slot of the bridge stack is
+// A path's state at its start; the bottom level of the bridge stack is
 // zeroed (the root op reads it with weight 0).
-template <int D>
-__device__ __forceinline__ void path_state_init(PathState<D> &ps, float2 *R, const Layout &lay) {
+template <int D, int H>
+__device__ __forceinline__ void path_state_init(PathState<D, H> &ps, float2 *R, const Layout &lay) {
 #pragma unroll
-  for (int i = 0; i < D; ++i) SL(lay.off_bstack + i) = make_float2(0.f, 0.f);
+  for (int i = 0; i < D * H; ++i) SL(lay.off_bstack + i) = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int i = 0; i < D; ++i) ps.w[i] = make_float2(0.f, 0.f);
+  for (int h = 0; h < H; ++h) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) ps.zc[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < D; ++i) ps.w[h][i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ps.zc[h][i] = make_float2(0.f, 0.f);
+  }
   ps.f = 0;
   ps.bsp = 0;
   ps.k = 0;
 }
 
-// The normals of op k for both paths: normals D k .. D k + D - 1 of the
-// path (Philox block m >> 2, word m & 3).  Ops run in order, so the block
-// holding normal D k is either new or the last block computed, whose words
-// 1..3 the state keeps (zc); a new block is computed at most once per op.
-template <int D>
-__device__ __forceinline__ void node_normals(uint32_t k, const Rng2 &g, float2 (&zc)[3],
-                                             float2 (&z)[D]) {
+// The normals of op k for every path of the lane: normals D k .. D k + D - 1
+// of the path (Philox block m >> 2, word m & 3).  Ops run in order, so the
+// block holding normal D k is either new or the last block computed, whose
+// words 1..3 the state keeps (zc); a new block is computed at most once per
+// op.
+template <int D, int H>
+__device__ __forceinline__ void node_normals(uint32_t k, const RngH<H> &g, float2 (&zc)[H][3],
+                                             float2 (&z)[H][D]) {
   if constexpr (D == 4) {
-    float2 e[4];
-    block_normals2(k, g, e);
+    float2 e[H][4];
+    block_normals_h<H>(k, g, e);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) z[i] = e[i];
+    for (int h = 0; h < H; ++h)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) z[h][i] = e[h][i];
   } else if constexpr (D == 2) {
     if (k & 1) {  // words 2, 3 of block k / 2
-      z[0] = zc[1];
-      z[1] = zc[2];
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        z[h][0] = zc[h][1];
+        z[h][1] = zc[h][2];
+      }
     } else {
-      float2 e[4];
-      block_normals2(k >> 1, g, e);
-      z[0] = e[0];
-      z[1] = e[1];
-      zc[1] = e[2];
-      zc[2] = e[3];
+      float2 e[H][4];
+      block_normals_h<H>(k >> 1, g, e);
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        z[h][0] = e[h][0];
+        z[h][1] = e[h][1];
+        zc[h][1] = e[h][2];
+        zc[h][2] = e[h][3];
+      }
     }
   } else if constexpr (D == 1) {
     const uint32_t ph = k & 3;
     if (ph == 0) {
-      float2 e[4];
-      block_normals2(k >> 2, g, e);
-      z[0] = e[0];
-      zc[0] = e[1];
-      zc[1] = e[2];
-      zc[2] = e[3];
+      float2 e[H][4];
+      block_normals_h<H>(k >> 2, g, e);
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        z[h][0] = e[h][0];
+        zc[h][0] = e[h][1];
+        zc[h][1] = e[h][2];
+        zc[h][2] = e[h][3];
+      }
     } else {
-      z[0] = ph == 1 ? zc[0] : ph == 2 ? zc[1] : zc[2];
+#pragma unroll
+      for (int h = 0; h < H; ++h) z[h][0] = ph == 1 ? zc[h][0] : ph == 2 ? zc[h][1] : zc[h][2];
     }
   } else {  // D == 3: the first normal is word ph = 3k & 3 of its block
     const uint32_t ph = (3 * k) & 3;
     if (ph == 1) {  // words 1..3 of the last block
-      z[0] = zc[0];
-      z[1] = zc[1];
-      z[2] = zc[2];
-    } else {
-      float2 e[4];
-      block_normals2((3 * k + 2) >> 2, g, e);
-      if (ph == 0) {
-        z[0] = e[0];
-        z[1] = e[1];
-        z[2] = e[2];
-      } else if (ph == 2) {
-        z[0] = zc[1];
-        z[1] = zc[2];
-        z[2] = e[0];
-      } else {
-        z[0] = zc[2];
-        z[1] = e[0];
-        z[2] = e[1];
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        z[h][0] = zc[h][0];
+        z[h][1] = zc[h][1];
+        z[h][2] = zc[h][2];
       }
-      zc[0] = e[1];
-      zc[1] = e[2];
-      zc[2] = e[3];
+    } else {
+      float2 e[H][4];
+      block_normals_h<H>((3 * k + 2) >> 2, g, e);
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        if (ph == 0) {
+          z[h][0] = e[h][0];
+          z[h][1] = e[h][1];
+          z[h][2] = e[h][2];
+        } else if (ph == 2) {
+          z[h][0] = zc[h][1];
+          z[h][1] = zc[h][2];
+          z[h][2] = e[h][0];
+        } else {
+          z[h][0] = zc[h][2];
+          z[h][1] = e[h][0];
+          z[h][2] = e[h][1];
+        }
+        zc[h][0] = e[h][1];
+        zc[h][1] = e[h][2];
+        zc[h][2] = e[h][3];
+      }
     }
   }
 }
@@ -283,58 +323,70 @@ __device__ __forceinline__ OpRegs load_op(const BridgeOp *p) {
   return o;
 }
 
-// Produce date t (= frontier + 1) for both paths: bridge ops of t, then GBM
-// into the window slot of t.  With XW the correlated Brownian values
-// X = L W of the date are also kept (window at lay.off_xwin), which the
-// pathwise sensitivities need.  The bridge, correlation and GBM products run
-// on packed pairs (the two paths of the lane).
-template <int D, bool XW = false, bool GW = false>
-__device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev &m,
-                                         const Layout &lay, const Rng2 &g, float2 *R,
+// Produce date t (= frontier + 1) for the lane's paths: bridge ops of t,
+// then GBM into the window slot of t.  With XW the correlated Brownian
+// values X = L W of the date are also kept (window at lay.off_xwin), which
+// the pathwise sensitivities need.  The bridge, correlation and GBM products
+// run on packed pairs (two paths of the lane); with H pairs a lane, each op's
+// schedule and control serve all 2H paths.
+template <int D, bool XW = false, bool GW = false, int H = 1>
+__device__ __forceinline__ void gen_date(int t, PathState<D, H> &ps, const ModelDev &m,
+                                         const Layout &lay, const RngH<H> &g, float2 *R,
                                          const float (&Bm)[D * D], const float (&S0)[D],
                                          const float *Lm = nullptr) {
+  static_assert(H == 1 || (!XW && !GW), "several path pairs a lane: no X window, no HBM window");
   const int k1 = __ldg(m.date_ops + t + 1);  // ops of date t: [ps.k, k1)
   // Every op pushes its node; the date's own value (the last node, or one
   // pushed on an earlier date when t has no op) is then popped as the new
-  // frontier value.  The root op has wl = wr = 0 and reads the bottom slot,
+  // frontier value.  The root op has wl = wr = 0 and reads the bottom level,
   // zeroed at the path's start, as its right end.  (Branch-free: a push or
   // keep decision per op, and a root test, cost register moves at the joins.)
   for (; ps.k < k1; ++ps.k) {
     const OpRegs op = load_op(m.ops + ps.k);
-    float2 z[D];
-    node_normals<D>(uint32_t(ps.k), g, ps.zc, z);
-    const int top = lay.off_bstack + max(ps.bsp - 1, 0) * D;
-    float2 nw[D];
+    float2 z[H][D];
+    node_normals<D, H>(uint32_t(ps.k), g, ps.zc, z);
+    const int top = lay.off_bstack + max(ps.bsp - 1, 0) * D * H;
+    const int nxt = lay.off_bstack + ps.bsp * D * H;
 #pragma unroll
-    for (int i = 0; i < D; ++i) nw[i] = fma_x2(op.wl, ps.w[i], fma_x2(op.wr, SL(top + i), mul_x2(op.sd, z[i])));
+    for (int h = 0; h < H; ++h) {
+      float2 nw[D];
 #pragma unroll
-    for (int i = 0; i < D; ++i) SL(lay.off_bstack + ps.bsp * D + i) = nw[i];
+      for (int i = 0; i < D; ++i)
+        nw[i] = fma_x2(op.wl, ps.w[h][i], fma_x2(op.wr, SL(top + h * D + i), mul_x2(op.sd, z[h][i])));
+#pragma unroll
+      for (int i = 0; i < D; ++i) SL(nxt + h * D + i) = nw[i];
+    }
     ++ps.bsp;
   }
   --ps.bsp;
 #pragma unroll
-  for (int i = 0; i < D; ++i) ps.w[i] = SL(lay.off_bstack + ps.bsp * D + i);
+  for (int h = 0; h < H; ++h)
+#pragma unroll
+    for (int i = 0; i < D; ++i) ps.w[h][i] = SL(lay.off_bstack + ps.bsp * D * H + h * D + i);
   const int ws = (t & (lay.win - 1)) * D;
 #pragma unroll
-  for (int i = 0; i < D; ++i) {
-    float2 x = __ldg(m.A + t * D + i);
+  for (int h = 0; h < H; ++h) {
 #pragma unroll
-    for (int k = 0; k <= i; ++k)
-      x = make_float2(fmaf(Bm[i * D + k], ps.w[k].x, x.x), fmaf(Bm[i * D + k], ps.w[k].y, x.y));
+    for (int i = 0; i < D; ++i) {
+      float2 x = __ldg(m.A + t * D + i);
+#pragma unroll
+      for (int k = 0; k <= i; ++k)
+        x = make_float2(fmaf(Bm[i * D + k], ps.w[h][k].x, x.x), fmaf(Bm[i * D + k], ps.w[h][k].y, x.y));
 #ifdef PC_WIN_REGS
-    ps.s[i] = make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y));
-    (void)ws;
+      ps.s[h][i] = make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y));
+      (void)ws;
 #else
-    win_store<GW>(R, lay, ws + i, make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y)));
+      win_store<GW>(R, lay, ws + i, make_float2(S0[i] * ex2_approx(x.x), S0[i] * ex2_approx(x.y)));
 #endif
+    }
   }
   if constexpr (XW) {
     const int xs = lay.off_xwin + (t & (lay.win - 1)) * D;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      float2 x = mul_x2(dup2(Lm[i * D]), ps.w[0]);
+      float2 x = mul_x2(dup2(Lm[i * D]), ps.w[0][0]);
 #pragma unroll
-      for (int k = 1; k <= i; ++k) x = fma_x2(dup2(Lm[i * D + k]), ps.w[k], x);
+      for (int k = 1; k <= i; ++k) x = fma_x2(dup2(Lm[i * D + k]), ps.w[0][k], x);
       SL(xs + i) = x;
     }
   }
@@ -343,9 +395,9 @@ __device__ __forceinline__ void gen_date(int t, PathState<D> &ps, const ModelDev
 
 // Dates ps.f + 1 .. o, out of line (the specialised evaluator calls it from
 // every instruction that reads a date, so it is not inlined there).
-template <int D, bool GW>
-__device__ __noinline__ void advance_dates(int o, PathState<D> &ps, const ModelDev &m, const Layout &lay,
-                                           const Rng2 &g, float2 *R, const float (&Bm)[D * D],
+template <int D, bool GW, int H>
+__device__ __noinline__ void advance_dates(int o, PathState<D, H> &ps, const ModelDev &m, const Layout &lay,
+                                           const RngH<H> &g, float2 *R, const float (&Bm)[D * D],
                                            const float (&S0)[D]) {
   while (ps.f < o) gen_date<D, false, GW>(ps.f + 1, ps, m, lay, g, R, Bm, S0);
 }
@@ -503,6 +555,41 @@ __device__ __forceinline__ void fused_test_regs(const uint4 &I, int o, const flo
                                                 const ModelDev &m, bool &t0, bool &t1) {
   fused_test_rd<D>(I, o, pool, m, [&](int l) { return cur[l]; }, t0, t1);
 }
+
+// Values of the stack machine: one per path of the lane, kPL = 2 PC_PAIRS of
+// them (PC_PAIRS pairs; a specialised kernel with four paths a lane defines
+// PC_PAIRS 2).  pv_get / pv_set take a path index that is a constant once the
+// loops over it are unrolled.
+#ifndef PC_PAIRS
+#define PC_PAIRS 1
+#endif
+constexpr int kPL = 2 * PC_PAIRS;
+#if PC_PAIRS == 2
+struct PV {
+  float2 a, b;
+};
+__device__ __forceinline__ float pv_get(const PV &v, int p) {
+  return p == 0 ? v.a.x : p == 1 ? v.a.y : p == 2 ? v.b.x : v.b.y;
+}
+__device__ __forceinline__ void pv_set(PV &v, int p, float x) {
+  if (p == 0) v.a.x = x;
+  else if (p == 1) v.a.y = x;
+  else if (p == 2) v.b.x = x;
+  else v.b.y = x;
+}
+__device__ __forceinline__ PV pv_splat(float x) { return PV{make_float2(x, x), make_float2(x, x)}; }
+__device__ __forceinline__ PV pv_pairs(float2 p0, float2 p1) { return PV{p0, p1}; }
+#else
+typedef float2 PV;
+__device__ __forceinline__ float pv_get(const PV &v, int p) { return p ? v.y : v.x; }
+__device__ __forceinline__ void pv_set(PV &v, int p, float x) {
+  if (p) v.y = x;
+  else v.x = x;
+}
+__device__ __forceinline__ PV pv_splat(float x) { return make_float2(x, x); }
+__device__ __forceinline__ PV pv_pairs(float2 p0) { return p0; }
+#endif
+#define PV_FOR(p) _Pragma("unroll") for (int p = 0; p < kPL; ++p)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -19,12 +19,16 @@
 // (code and pool words), the underlying count and the per-path variant.
 // Kinds of run-time specialised kernels: pricing (bit kJitPriceWrite: with
 // per-path payoffs; bit kJitHbm: the window of dates in HBM; bit
-// kJitWinRegs: a window of one date, kept in registers), and the
+// kJitWinRegs: a window of one date, kept in registers; bit kJitPairs2 (with
+// kJitWinRegs): four paths a lane), and the
 // control-variate kernel (kJitCv + its kCv* mode bits).
-constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitHbm = 2, kJitWinRegs = 4, kJitCv = 16, kJitGreeks = 32;
+constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitHbm = 2, kJitWinRegs = 4, kJitPairs2 = 8, kJitCv = 16,
+              kJitGreeks = 32;
 // resident blocks per SM the specialised pricing kernel's register bound is
 // set for by default (<= 72 registers at 128 threads: the fastest measured)
 constexpr int kJitMinBlocks = 7;
+// dates of the model from which a one-date-window kernel takes two path pairs a lane
+constexpr int kJitPairsMinDates = 64;
 constexpr size_t kJitStaticSmem = 256;  // bound on price_tiles' static shared memory
 
 struct JitEntry {
@@ -56,6 +60,7 @@ struct pc_ctx {
   size_t gwin_cap = 0;           // float2 slots
   int32_t window_mode = 0;       // PC_WINDOW_AUTO / _SHARED / _HBM
   int32_t jit = 0;               // 1: price with run-time specialised kernels
+  int32_t jit_pairs = 0;         // path pairs a lane of a specialised kernel with a one-date window (0 automatic, 1 or 2)
   std::mutex jit_mu;
   std::multimap<uint64_t, JitEntry> jit_cache;  // program hash -> compiled kernels
   std::map<std::pair<const void *, size_t>, int> jit_occ;  // (kernel, smem) -> resident blocks

@@ -213,6 +213,10 @@ std::string generate(const Program &p, int d, int kind) {
   // a program that reads no date behind the frontier keeps that date's S in
   // registers instead of a shared-memory window
   if (kind < kJitCv && (kind & kJitWinRegs)) o << "#define PC_WIN_REGS 1\n";
+  // four paths a lane: the per-op and per-instruction control serves twice
+  // the paths
+  const bool pairs2 = kind < kJitCv && (kind & kJitPairs2);
+  if (pairs2) o << "#define PC_PAIRS 2\n";
   o << "#include \"pc_price.cuh\"\n";
   if (kind >= kJitCv) o << "#include \"pc_cv.cuh\"\n";
   o
@@ -221,8 +225,9 @@ std::string generate(const Program &p, int d, int kind) {
     << "constexpr int D = " << d << ";\n"
     << "constexpr bool GW = " << (kind < kJitCv && (kind & kJitHbm) ? "true" : "false") << ";\n"
     << "#define PC_JIT_STACK_SLOTS " << std::max(1, int(p.frame_slots)) << "\n"
-    << "__device__ __forceinline__ float2 jit_eval(const uint4 *P, const float *pool, float2 *R,\n"
-    << "    const PriceArgs &a, const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],\n"
+    << "__device__ __forceinline__ PV jit_eval(const uint4 *P, const float *pool, float2 *R,\n"
+    << (pairs2 ? "    const PriceArgs &a, const RngH<2> &g, const bool (&live_)[kPL], const float (&Bm)[D * D],\n"
+               : "    const PriceArgs &a, const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],\n")
     << "    const float (&S0)[D], int *frontier = nullptr) {\n"
     << "#include \"pc_eval_state.inc\"\n"
     << "  (void)pc;\n";
@@ -283,11 +288,16 @@ std::string generate(const Program &p, int d, int kind) {
   // launch's shared memory already allows fewer, whose bound then leaves the
   // kernel the registers those blocks can have)
   o << "#ifndef PC_MIN_BLOCKS\n#define PC_MIN_BLOCKS " << kJitMinBlocks << "\n#endif\n"
-    << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ", PC_MIN_BLOCKS) pc_jit_price(const __grid_constant__ pc::PriceArgs a) {\n"
-    << "  pc::price_tiles<pc::D, " << (kind & kJitPriceWrite ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
-    << "      float2 *R, const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
-    << "      const float (&S0)[pc::D]) { return pc::jit_eval(P, pool, R, a, g, live0, live1, Bm, S0); });\n"
-    << "}\n";
+    << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << ", PC_MIN_BLOCKS) pc_jit_price(const __grid_constant__ pc::PriceArgs a) {\n";
+  if (pairs2)
+    o << "  pc::price_tiles2<pc::D, " << (kind & kJitPriceWrite ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
+      << "      float2 *R, const pc::RngH<2> &g, const bool (&live)[4], const float (&Bm)[pc::D * pc::D],\n"
+      << "      const float (&S0)[pc::D]) { return pc::jit_eval(P, pool, R, a, g, live, Bm, S0); });\n";
+  else
+    o << "  pc::price_tiles<pc::D, " << (kind & kJitPriceWrite ? "true" : "false") << ">(a, [&](const uint4 *P, const float *pool,\n"
+      << "      float2 *R, const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
+      << "      const float (&S0)[pc::D]) { return pc::jit_eval(P, pool, R, a, g, live0, live1, Bm, S0); });\n";
+  o << "}\n";
   return o.str();
 }
 
@@ -415,7 +425,9 @@ extern "C" pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_wor
   const bool cv_kind = kind >= kJitCv && kind < kJitCv + 8 && kind != kJitCv + kCvWrite &&
                        kind != kJitCv + (kCvWrite | kCvPilot) && kind != kJitCv + (kCvWrite | kCvPilot | kCvGamma);
   const bool greeks_kind = kind == kJitGreeks || kind == kJitGreeks + 1;
-  if ((kind < 0 || kind > (kJitPriceWrite | kJitHbm | kJitWinRegs)) && !cv_kind && !greeks_kind)
+  const bool price_kind = kind >= 0 && kind <= (kJitPriceWrite | kJitHbm | kJitWinRegs | kJitPairs2) &&
+                          (!(kind & kJitPairs2) || (kind & (kJitWinRegs | kJitHbm)) == kJitWinRegs);
+  if (!price_kind && !cv_kind && !greeks_kind)
     return fail(PC_EINVAL, "unknown kernel kind");
   if (cv_kind && d > kCvMaxD) return fail(PC_EINVAL, "control-variate kernels take d <= 3");
   Program p;
@@ -435,7 +447,8 @@ extern "C" pc_status pc_debug_jit_source(const uint32_t *bytecode, size_t n_word
                                          size_t cap, size_t *len) {
   if (!len) return fail(PC_EINVAL, "null output");
   if (d < 1 || d > PC_MAX_UNDERLYINGS) return fail(PC_EINVAL, "d must be 1..4");
-  const bool known = (kind >= 0 && kind <= (kJitPriceWrite | kJitHbm | kJitWinRegs)) ||
+  const bool known = (kind >= 0 && kind <= (kJitPriceWrite | kJitHbm | kJitWinRegs | kJitPairs2) &&
+                      (!(kind & kJitPairs2) || (kind & (kJitWinRegs | kJitHbm)) == kJitWinRegs)) ||
                      (kind >= kJitCv && kind < kJitCv + 8) ||
                      kind == kJitGreeks || kind == kJitGreeks + 1;
   if (!known) return fail(PC_EINVAL, "unknown kernel kind");

@@ -46,6 +46,54 @@ def test_specialised_equals_interpreter(eng, name):
     np.testing.assert_array_equal(a1, a0)
 
 
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_four_paths_a_lane_equals_interpreter(eng, name):
+    """Specialised kernels with two path pairs a lane (programs that read no
+    date behind the frontier; the others keep one pair): per-path payoffs
+    and sums bit for bit those of the interpreter, on a ragged path count
+    (the last tile pair half empty)."""
+    text, tp, spec, notional = CASES[name]
+    m, k = eng.model(spec), eng.contract(text, tp)
+    n, seed = 4096 + 64 + 37, 0xABD + len(name)
+    pc.pc_set_jit(eng.ctx, False)
+    x0, s0 = eng.paths(m, k, n, seed)
+    a0 = eng.sums(m, k, (1 << 16) + 64 * 3 + 5, seed)
+    pc.pc_set_jit(eng.ctx, True)
+    try:
+        for pairs in (1, 2):
+            pc.pc_debug_set_jit_pairs(eng.ctx, pairs)
+            x1, s1 = eng.paths(m, k, n, seed)
+            a1 = eng.sums(m, k, (1 << 16) + 64 * 3 + 5, seed)
+            np.testing.assert_array_equal(x1, x0)
+            np.testing.assert_array_equal(s1, s0)
+            np.testing.assert_array_equal(a1, a0)
+    finally:
+        pc.pc_debug_set_jit_pairs(eng.ctx, 0)
+        pc.pc_set_jit(eng.ctx, False)
+
+
+def test_four_paths_a_lane_daily_barrier_full_size(eng):
+    """The daily barrier at 2^22 paths with two path pairs a lane: the same
+    sums as with one pair and as the interpreter."""
+    w = W.daily_barrier()
+    m, k = eng.model(w.market), eng.contract(w.il_text, w.tparams)
+    pc.pc_set_jit(eng.ctx, False)
+    a0 = eng.sums(m, k, w.n_paths, w.seed)
+    pc.pc_set_jit(eng.ctx, True)
+    try:
+        pc.pc_debug_set_jit_pairs(eng.ctx, 1)
+        a1 = eng.sums(m, k, w.n_paths, w.seed)
+        pc.pc_debug_set_jit_pairs(eng.ctx, 2)
+        a2 = eng.sums(m, k, w.n_paths, w.seed)
+    finally:
+        pc.pc_debug_set_jit_pairs(eng.ctx, 0)
+        pc.pc_set_jit(eng.ctx, False)
+    np.testing.assert_array_equal(a1, a0)
+    np.testing.assert_array_equal(a2, a0)
+    with pytest.raises(pc.PcError):
+        pc.pc_debug_set_jit_pairs(eng.ctx, 3)
+
+
 def test_specialised_matches_oracle_and_is_reused(eng):
     w = W.worst_of_autocall()
     m = eng.model(w.market)
