@@ -699,6 +699,13 @@ pc_status pc_debug_set_status(pc_ctx *ctx, int32_t value);
  * per choice.  Errors: PC_EINVAL. */
 pc_status pc_debug_set_jit_pairs(pc_ctx *ctx, int32_t pairs);
 
+/* Resident 128-thread blocks per SM the register bound of the context's
+ * specialised control-variate kernels is set for (1..16), or 0 for the
+ * default (5).  The values
+ * are the same under any bound; the kernels are cached per choice.
+ * Errors: PC_EINVAL. */
+pc_status pc_debug_set_cv_min_blocks(pc_ctx *ctx, int32_t blocks);
+
 /* Failure test of the network's tensor-core product: while `on`, its TMA
  * producer withholds the copies of the first k-chunk, so the MMA issuer's
  * and the producer's bounded mbarrier waits expire (after about 10 ms

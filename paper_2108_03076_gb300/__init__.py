@@ -130,6 +130,7 @@ _SIGS = {
     "pc_set_window_mode": [VP, C.c_int32],
     "pc_set_jit": [VP, C.c_int32],
     "pc_debug_set_jit_pairs": [VP, C.c_int32],
+    "pc_debug_set_cv_min_blocks": [VP, C.c_int32],
     "pc_jit_compile": [VP, VP],
     "pc_debug_jit_compile": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, I32, I32, C.POINTER(SZ)],
     "pc_debug_jit_source": [PU32, SZ, PD, SZ, PI32, SZ, I32, I32, I32, I32, C.c_char_p, SZ, C.POINTER(SZ)],
@@ -361,6 +362,10 @@ def pc_debug_mlp_withhold_tma(net: int, on: bool) -> None:
 
 def pc_debug_set_jit_pairs(ctx: int, pairs: int) -> None:
     _check(lib().pc_debug_set_jit_pairs(VP(ctx), int(pairs)))
+
+
+def pc_debug_set_cv_min_blocks(ctx: int, blocks: int) -> None:
+    _check(lib().pc_debug_set_cv_min_blocks(VP(ctx), int(blocks)))
 
 
 def pc_set_jit(ctx: int, enabled: bool) -> None:

@@ -968,6 +968,13 @@ pc_status pc_debug_set_jit_pairs(pc_ctx *c, int32_t pairs) {
   return PC_OK;
 }
 
+pc_status pc_debug_set_cv_min_blocks(pc_ctx *c, int32_t blocks) {
+  if (!c) return fail(PC_EINVAL, "null context");
+  if (blocks < 0 || blocks > 16) return fail(PC_EINVAL, "blocks must be 0 (the kernel's default) .. 16");
+  c->cv_min_blocks = blocks;
+  return PC_OK;
+}
+
 pc_status pc_set_jit(pc_ctx *c, int32_t enabled) {
   if (!c) return fail(PC_EINVAL, "null context");
   if (enabled != 0 && enabled != 1) return fail(PC_EINVAL, "enabled must be 0 or 1");

@@ -14,10 +14,12 @@ namespace {
 
 
 template <int D, int MODE>
-__global__ void __launch_bounds__(kBlock) cv_kernel(const __grid_constant__ PriceArgs a, const CvArgs c) {
+__global__ void __launch_bounds__(kBlock) cv_kernel(const __grid_constant__ PriceArgs a,
+                                                    const __grid_constant__ CvArgs c) {
+  using Hook = CvOnline<D, (MODE & kCvGamma) != 0>;
   cv_tiles<D, MODE>(a, c, [&](const uint4 *P, const float *pool, float2 *R, const Rng2 &g, bool live0,
-                              bool live1, const float (&Bm)[D * D], const float (&S0)[D], int *frontier) {
-    return eval_path<D>(P, pool, R, a, g, live0, live1, Bm, S0, frontier);
+                              bool live1, const float (&Bm)[D * D], const float (&S0)[D], Hook *hook) {
+    return eval_path<D, false, Hook>(P, pool, R, a, g, live0, live1, Bm, S0, nullptr, hook);
   });
 }
 

@@ -4,8 +4,8 @@
 // hedge gains.  Included by pc_cv.cu and by the run-time compiler.
 //
 // For the worst-of autocallable template each path's payoff X comes from the
-// evaluator exactly as in the pricing kernel; the kernel then walks the dates
-// kept in the window and accumulates the discounted hedge gains
+// evaluator exactly as in the pricing kernel; as the evaluator generates each
+// date, the kernel accumulates the discounted hedge gains
 //   M = sum_{k<n} alive_k sum_i Delta_i(k) (D_{k+1} S_i(t_{k+1}) - D_k S_i(t_k))
 // with Delta from a table over ln S (multilinear interpolation) per date and
 // knock-in state.  Every factor of a term is known at t_k, so E[M] = 0.  An
@@ -93,58 +93,98 @@ __device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, cons
   }
 }
 
-// Hedge gains of the lane's two paths (q = 0, 1): first order M and second
-// order M2.  S of path q at ordinal o is s(q, o, i) (o = 0: spot).  Both
-// paths are worked in step (independent table reads in flight together);
-// a dead path's terms are computed and discarded.
-template <int D, bool GAMMA, typename SFn>
-__device__ void hedge_gain2(const CvArgs &c, const ModelDev &m, int frontier, SFn s, float (&M)[2],
-                            float (&M2)[2]) {
-  bool alive[2] = {true, true};
-  int ki[2] = {0, 0};
+// Hedge gains of the lane's two paths (q = 0, 1), accumulated online: the
+// evaluators call on_date(t, read) after generating date t, and the period
+// k = t - 1 (from t_k to t_{k+1}) is added then, from S at t_k (kept here)
+// and S at t_{k+1} (read from the evaluator).  A period whose end date the
+// warp never generates is never added.  First order M and second order M2;
+// a dead path's terms are computed and discarded, a period in which both
+// are dead is skipped.
+template <int D, bool GAMMA>
+struct CvOnline {
+  static constexpr bool kNone = false;
+  const CvArgs &c;
+  const ModelDev &m;
+  float sk[2][D];  // S at t_k (t_0: the spot)
+  float M[2], M2[2];
+  bool alive[2];
+  int ki[2];
+
+  __device__ __forceinline__ CvOnline(const CvArgs &c_, const ModelDev &m_, const float (&S0)[D])
+      : c(c_), m(m_) {
 #pragma unroll
-  for (int q = 0; q < 2; ++q) M[q] = M2[q] = 0.f;
-  for (int k = 0; k < c.n; ++k) {
-    if (k + 1 > frontier) break;
+    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) sk[q][i] = S0[i];
+      M[q] = M2[q] = 0.f;
+      alive[q] = true;
+      ki[q] = 0;
+    }
+  }
+
+  template <class RD>
+  __device__ __forceinline__ void on_date(int t, RD &read) {
+    const int k = t - 1;
+    if (k >= c.n) return;
+    float sn[2][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float2 v = read(t, i);
+      sn[0][i] = v.x;
+      sn[1][i] = v.y;
+    }
+    period(k, sn);
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int i = 0; i < D; ++i) sk[q][i] = sn[q][i];
+  }
+
+  __device__ __forceinline__ void period(int k, const float (&sn)[2][D]) {
     if (k >= 1) {
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        float worst = s(q, k, 0) * c.inv_ref[0];
+        float worst = sk[q][0] * c.inv_ref[0];
 #pragma unroll
-        for (int i = 1; i < D; ++i) worst = fminf(worst, s(q, k, i) * c.inv_ref[i]);
+        for (int i = 1; i < D; ++i) worst = fminf(worst, sk[q][i] * c.inv_ref[i]);
         ki[q] |= worst <= c.ki_level ? 1 : 0;
         alive[q] = alive[q] && !(worst >= c.call_level);
       }
     }
-    if (!alive[0] && !alive[1]) break;
+    if (!alive[0] && !alive[1]) return;
     const float d0 = __ldg(m.disc + k + m.n_hist), d1 = __ldg(m.disc + k + 1 + m.n_hist);
-    float delta[2][D], sl[2][D][D];
-    if (k == 0) {
+    // one path at a time (a rolled loop over register selects): the
+    // evaluator's state is live around this call, so only one path's corner
+    // values are held at once
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+      float s0[D], s1[D], delta[D], sl[D][D];
 #pragma unroll
-      for (int q = 0; q < 2; ++q)
+      for (int i = 0; i < D; ++i) {
+        s0[i] = q ? sk[1][i] : sk[0][i];
+        s1[i] = q ? sn[1][i] : sn[0][i];
+      }
+      const bool al = q ? alive[1] : alive[0];
+      if (k == 0) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) delta[q][i] = c.delta0[i];
-    } else {
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
+        for (int i = 0; i < D; ++i) delta[i] = c.delta0[i];
+      } else {
         float l2[D];
 #pragma unroll
-        for (int i = 0; i < D; ++i) l2[i] = __log2f(s(q, k, i));
-        table_delta<D, GAMMA>(c, k, ki[q], l2, delta[q], sl[q]);
+        for (int i = 0; i < D; ++i) l2[i] = __log2f(s0[i]);
+        table_delta<D, GAMMA>(c, k, q ? ki[1] : ki[0], l2, delta, sl);
       }
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      float X[D], Sk[D], inv[D];
+      float X[D], inv[D];
       float dm = 0.f;
 #pragma unroll
       for (int i = 0; i < D; ++i) {
-        Sk[i] = s(q, k, i);
-        X[i] = d1 * s(q, k + 1, i) - d0 * Sk[i];
-        dm = fmaf(delta[q][i], X[i], dm);
-        inv[i] = __frcp_rn(Sk[i]);
+        X[i] = d1 * s1[i] - d0 * s0[i];
+        dm = fmaf(delta[i], X[i], dm);
+        inv[i] = __frcp_rn(s0[i]);
       }
-      M[q] += alive[q] ? dm : 0.f;
+      const float dM = al ? dm : 0.f;
+      if (q) M[1] += dM;
+      else M[0] += dM;
       if (GAMMA && k >= 1) {
         // Gamma = sym(t), t_ij = s_ij / (h_j S_j); the quadratic forms of
         // a symmetric weight need only t itself
@@ -154,21 +194,23 @@ __device__ void hedge_gain2(const CvArgs &c, const ModelDev &m, int frontier, SF
           float rq = 0.f, re = 0.f;
 #pragma unroll
           for (int j = 0; j < D; ++j) {
-            const float t = sl[q][i][j] * c.inv_h[k - 1][j] * inv[j];
-            rq = fmaf(t, X[j], rq);
-            re = fmaf(t, Sk[j] * c.cq[k][i * kCvMaxD + j], re);
+            const float tt = sl[i][j] * c.inv_h[k - 1][j] * inv[j];
+            rq = fmaf(tt, X[j], rq);
+            re = fmaf(tt, s0[j] * c.cq[k][i * kCvMaxD + j], re);
           }
           qf = fmaf(X[i], rq, qf);
-          e = fmaf(Sk[i], re, e);
+          e = fmaf(s0[i], re, e);
         }
-        M2[q] += alive[q] ? 0.5f * (qf - d0 * d0 * e) : 0.f;
+        const float dM2 = al ? 0.5f * (qf - d0 * d0 * e) : 0.f;
+        if (q) M2[1] += dM2;
+        else M2[0] += dM2;
       }
     }
   }
-}
+};
 
-// EVAL(P, pool, R, g, live0, live1, Bm, S0, &frontier) -> float2 payoffs
-// of the lane's two paths; frontier receives the last simulated ordinal.
+// EVAL(P, pool, R, g, live0, live1, Bm, S0, &hook) -> float2 payoffs of the
+// lane's two paths; the evaluator calls hook.on_date after each date.
 template <int D, int MODE, typename EVAL>
 __device__ __forceinline__ void cv_tiles(const PriceArgs &a, const CvArgs &c, EVAL eval) {
   constexpr bool WRITE = (MODE & kCvWrite) != 0, GAMMA = (MODE & kCvGamma) != 0,
@@ -186,7 +228,6 @@ __device__ __forceinline__ void cv_tiles(const PriceArgs &a, const CvArgs &c, EV
   const float(&S0)[D] = *reinterpret_cast<const float(*)[D]>(a.m.S0v);
   const int lane = threadIdx.x & 31;
   unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.control);
-  const Layout &lay = a.lay;
   Rng2 g;
   g.stream = a.stream;
 #pragma unroll
@@ -203,15 +244,10 @@ __device__ __forceinline__ void cv_tiles(const PriceArgs &a, const CvArgs &c, EV
     g.phi[0] = uint32_t(p0 >> 32);
     g.plo[1] = uint32_t(p1);
     g.phi[1] = uint32_t(p1 >> 32);
-    int frontier = 0;
-    const float2 x = eval(P, pool, R, g, live0, live1, Bm, S0, &frontier);
-    float Mv[2], M2v[2];
-    auto s = [&](int q, int o, int i) -> float {
-      if (o == 0) return S0[i];
-      const float2 v = SL(lay.off_win + (o & (lay.win - 1)) * D + i);
-      return q ? v.y : v.x;
-    };
-    hedge_gain2<D, GAMMA>(c, a.m, frontier, s, Mv, M2v);
+    CvOnline<D, GAMMA> hg(c, a.m, S0);
+    const float2 x = eval(P, pool, R, g, live0, live1, Bm, S0, &hg);
+    const float(&Mv)[2] = hg.M;
+    const float(&M2v)[2] = hg.M2;
     const float xs[2] = {x.x, x.y};
     const bool live[2] = {live0, live1};
     if (WRITE) {

@@ -77,7 +77,10 @@ CvArgs device_args(const pc_cv_desc *c, const float *tables, const ModelHost &H,
   return a;
 }
 
-// The pricing launch with a window holding every date 1..n.
+// The control-variate pricing launch.  The hedge gains accumulate as the
+// evaluator generates each date, so the launch keeps the program's own
+// window of dates (in registers for a specialised kernel when that window is
+// one date).
 pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c, const float *tables,
                     uint64_t n_paths, uint64_t seed, double *d_out, float *d_xm, bool pilot) {
   pc_status s = check_desc(m, c);
@@ -88,11 +91,7 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
   s = prepare(m, k, n_paths, 0, seed, 0, L);
   if (s != PC_OK) return s;
   pc_ctx *ctx = m->ctx;
-  Layout lay = L.args.lay;
-  int32_t win = lay.win;
-  while (win < c->n + 1) win *= 2;
-  lay.win = win;
-  lay.words = lay.off_win + std::min(win, c->n + 1) * c->d;  // slots 0..n (o & (win - 1) = o)
+  const Layout lay = L.args.lay;
   const size_t pool = (k->prog.pool.size() + 3) & ~size_t(3);
   int block = 0, best = 0;
   size_t smem = 0;
@@ -119,8 +118,13 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
     // the contract's run-time specialised control-variate kernel: the
     // evaluator keeps its operand stack in registers, so the stack words
     // leave the per-thread shared region
+    const bool win_regs = lay.win == 1;
     cudaKernel_t jk = nullptr;
-    s = jit_kernel(k, m->H.d, kJitCv + cv_mode(d_xm != nullptr, ca), kBlock, jk);
+    // register bound: 5 resident blocks by default (measured at 2^22 paths
+    // of the autocall: 3 / 4 / 5 / 6 blocks 0.522 / 0.461 / 0.439 / 0.479 ms
+    // first order, 0.610 / 0.539 / 0.524 / 0.648 ms with the second-order term)
+    s = jit_kernel(k, m->H.d, kJitCv + cv_mode(d_xm != nullptr, ca) + (win_regs ? kCvWinRegs : 0), kBlock, jk,
+                   ctx->cv_min_blocks > 0 ? ctx->cv_min_blocks : kJitCvMinBlocks);
     if (s != PC_OK) return s;
     const void *kern = reinterpret_cast<const void *>(jk);
     Layout &jl = a.lay;
@@ -130,6 +134,7 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
     jl.off_cache -= shift;
     jl.off_win -= shift;
     jl.words -= shift;
+    if (win_regs) jl.words = jl.off_win;  // the frontier's S in registers: no window words
     const size_t jsm = price_smem_bytes(k->prog.code.size(), pool, jl.words, kBlock);
     int nb = 0;
     CU(jit_occupancy(ctx, kern, kBlock, jsm, nb), "jit occupancy");

@@ -31,7 +31,8 @@ struct CvArgs {
 
 // MODE bits of the control-variate kernels: kCvWrite (per-path X, M, M2
 // out), kCvGamma (second-order term), kCvPilot (moment sums for the betas
-// instead of X, X^2, Y, Y^2).
-constexpr int kCvWrite = 1, kCvGamma = 2, kCvPilot = 4;
+// instead of X, X^2, Y, Y^2); and for the run-time specialised kernel
+// kCvWinRegs (a window of one date, the frontier's S in registers).
+constexpr int kCvWrite = 1, kCvGamma = 2, kCvPilot = 4, kCvWinRegs = 8;
 
 }  // namespace pc

@@ -393,6 +393,16 @@ __device__ __forceinline__ void gen_date(int t, PathState<D, H> &ps, const Model
   ps.f = t;
 }
 
+// The evaluators' per-date hook: called after each generated date t with
+// the evaluator's reader (read(t, i): S_i at ordinal t of the lane's paths).
+// NoDateHook (pricing) does nothing; the control-variate kernel's hook
+// accumulates its hedge gains there.
+struct NoDateHook {
+  static constexpr bool kNone = true;
+  template <class RD>
+  __device__ __forceinline__ void on_date(int, RD &) {}
+};
+
 // Dates ps.f + 1 .. o, out of line (the specialised evaluator calls it from
 // every instruction that reads a date, so it is not inlined there).
 template <int D, bool GW, int H>

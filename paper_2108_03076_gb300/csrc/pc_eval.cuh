@@ -13,10 +13,11 @@ namespace {
 // it costs a load per instruction the compiler cannot sink.)  `frontier`
 // (optional) receives the last generated date ordinal: the window holds the
 // simulated dates up to it.
-template <int D, bool GW = false>
+// `hook_` (optional, type PcHook) is called after each generated date.
+template <int D, bool GW = false, class PcHook = NoDateHook>
 __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const PriceArgs &a,
                             const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],
-                            const float (&S0)[D], int *frontier = nullptr) {
+                            const float (&S0)[D], int *frontier = nullptr, PcHook *hook_ = nullptr) {
 #include "pc_eval_state.inc"
 #define NEXT      \
   {               \
@@ -53,6 +54,9 @@ __device__ float2 eval_path(const uint4 *P, const float *pool, float2 *R, const 
 #undef BINF
 #undef BINI
 #undef IMM
+#undef GEN_DATE
+#undef FUSED_VALUE
+#undef FUSED_TEST
 }
 
 }  // namespace

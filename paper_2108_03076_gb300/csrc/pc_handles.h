@@ -27,6 +27,8 @@ constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitHbm = 2, kJitWinRegs = 4, k
 // resident blocks per SM the specialised pricing kernel's register bound is
 // set for by default (<= 72 registers at 128 threads: the fastest measured)
 constexpr int kJitMinBlocks = 7;
+// resident blocks per SM the specialised control-variate kernel's register bound is set for
+constexpr int kJitCvMinBlocks = 5;
 // dates of the model from which a one-date-window kernel takes two path pairs a lane
 constexpr int kJitPairsMinDates = 64;
 constexpr size_t kJitStaticSmem = 256;  // bound on price_tiles' static shared memory
@@ -60,6 +62,7 @@ struct pc_ctx {
   size_t gwin_cap = 0;           // float2 slots
   int32_t window_mode = 0;       // PC_WINDOW_AUTO / _SHARED / _HBM
   int32_t jit = 0;               // 1: price with run-time specialised kernels
+  int32_t cv_min_blocks = 0;     // launch bound of the specialised control-variate kernel (0: its default)
   int32_t jit_pairs = 0;         // path pairs a lane of a specialised kernel with a one-date window (0 automatic, 1 or 2)
   std::mutex jit_mu;
   std::multimap<uint64_t, JitEntry> jit_cache;  // program hash -> compiled kernels

@@ -212,7 +212,8 @@ std::string generate(const Program &p, int d, int kind) {
   if (!shared && date_sites(p) > kInlineDateSites) o << "#define PC_JIT_OUTLINE_DATES 1\n";
   // a program that reads no date behind the frontier keeps that date's S in
   // registers instead of a shared-memory window
-  if (kind < kJitCv && (kind & kJitWinRegs)) o << "#define PC_WIN_REGS 1\n";
+  if ((kind < kJitCv && (kind & kJitWinRegs)) || (kind >= kJitCv && ((kind - kJitCv) & kCvWinRegs)))
+    o << "#define PC_WIN_REGS 1\n";
   // four paths a lane: the per-op and per-instruction control serves twice
   // the paths
   const bool pairs2 = kind < kJitCv && (kind & kJitPairs2);
@@ -225,17 +226,18 @@ std::string generate(const Program &p, int d, int kind) {
     << "constexpr int D = " << d << ";\n"
     << "constexpr bool GW = " << (kind < kJitCv && (kind & kJitHbm) ? "true" : "false") << ";\n"
     << "#define PC_JIT_STACK_SLOTS " << std::max(1, int(p.frame_slots)) << "\n"
+    << "template <class PcHook = NoDateHook>\n"
     << "__device__ __forceinline__ PV jit_eval(const uint4 *P, const float *pool, float2 *R,\n"
     << (pairs2 ? "    const PriceArgs &a, const RngH<2> &g, const bool (&live_)[kPL], const float (&Bm)[D * D],\n"
                : "    const PriceArgs &a, const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],\n")
-    << "    const float (&S0)[D], int *frontier = nullptr) {\n"
+    << "    const float (&S0)[D], int *frontier = nullptr, PcHook *hook_ = nullptr) {\n"
     << "#include \"pc_eval_state.inc\"\n"
     << "  (void)pc;\n";
   if (shared) {
     o << "  int need_ = 0, resume_ = -1;\n"
       << "  goto L0;\n"
       << "PC_GEN:\n"
-      << "  while (ps.f < need_) gen_date<D, false, GW>(ps.f + 1, ps, m, lay, g, R, Bm, S0);\n"
+      << "  while (ps.f < need_) GEN_DATE(ps.f + 1);\n"
       << "  switch (resume_) {\n";
     for (size_t i = 0; i < n; ++i)
       if (reads_dates(p.code[i]) && sp_at[i] >= 0)
@@ -265,21 +267,23 @@ std::string generate(const Program &p, int d, int kind) {
       << "}\n";
   }
   o << "  return tos;\n"
-    << "#undef PUSH\n#undef STK\n#undef BINF\n#undef BINI\n#undef IMM\n"
+    << "#undef PUSH\n#undef STK\n#undef BINF\n#undef BINI\n#undef IMM\n#undef GEN_DATE\n"
     << "}\n"
     << "}  // namespace\n"
     << "}  // namespace pc\n";
   if (kind >= kJitCv) {
-    // the second-order term needs many registers: at least 5 resident
-    // blocks there (-10 %; the first-order kernel is fastest uncapped)
+    // the register bound (PC_MIN_BLOCKS resident blocks) is passed by the
+    // launcher
     const bool gamma = ((kind - kJitCv) & kCvGamma) != 0;
-    o << "extern \"C\" __global__ void __launch_bounds__(" << kBlock << (gamma ? ", 5" : "")
-      << ") pc_jit_cv(const __grid_constant__ pc::PriceArgs a,\n"
-      << "    const pc::CvArgs c) {\n"
-      << "  pc::cv_tiles<pc::D, " << (kind - kJitCv) << ">(a, c, [&](const uint4 *P, const float *pool, float2 *R,\n"
+    o << "#ifndef PC_MIN_BLOCKS\n#define PC_MIN_BLOCKS " << kJitCvMinBlocks << "\n#endif\n"
+      << "extern \"C\" __global__ void __launch_bounds__(" << kBlock
+      << ", PC_MIN_BLOCKS) pc_jit_cv(const __grid_constant__ pc::PriceArgs a,\n"
+      << "    const __grid_constant__ pc::CvArgs c) {\n"
+      << "  using Hook = pc::CvOnline<pc::D, " << (gamma ? "true" : "false") << ">;\n"
+      << "  pc::cv_tiles<pc::D, " << ((kind - kJitCv) & 7) << ">(a, c, [&](const uint4 *P, const float *pool, float2 *R,\n"
       << "      const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
-      << "      const float (&S0)[pc::D], int *frontier) {\n"
-      << "    return pc::jit_eval(P, pool, R, a, g, live0, live1, Bm, S0, frontier); });\n"
+      << "      const float (&S0)[pc::D], Hook *hook) {\n"
+      << "    return pc::jit_eval<Hook>(P, pool, R, a, g, live0, live1, Bm, S0, nullptr, hook); });\n"
       << "}\n";
     return o.str();
   }
@@ -422,8 +426,9 @@ extern "C" pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_wor
                                           size_t *cubin_bytes) {
   if (!cubin_bytes) return fail(PC_EINVAL, "null output");
   if (d < 1 || d > PC_MAX_UNDERLYINGS) return fail(PC_EINVAL, "d must be 1..4");
-  const bool cv_kind = kind >= kJitCv && kind < kJitCv + 8 && kind != kJitCv + kCvWrite &&
-                       kind != kJitCv + (kCvWrite | kCvPilot) && kind != kJitCv + (kCvWrite | kCvPilot | kCvGamma);
+  const int cvm = (kind - kJitCv) & 7;  // mode bits, with or without kCvWinRegs
+  const bool cv_kind = kind >= kJitCv && kind < kJitCv + 16 && cvm != kCvWrite && cvm != (kCvWrite | kCvPilot) &&
+                       cvm != (kCvWrite | kCvPilot | kCvGamma);
   const bool greeks_kind = kind == kJitGreeks || kind == kJitGreeks + 1;
   const bool price_kind = kind >= 0 && kind <= (kJitPriceWrite | kJitHbm | kJitWinRegs | kJitPairs2) &&
                           (!(kind & kJitPairs2) || (kind & (kJitWinRegs | kJitHbm)) == kJitWinRegs);
@@ -449,7 +454,7 @@ extern "C" pc_status pc_debug_jit_source(const uint32_t *bytecode, size_t n_word
   if (d < 1 || d > PC_MAX_UNDERLYINGS) return fail(PC_EINVAL, "d must be 1..4");
   const bool known = (kind >= 0 && kind <= (kJitPriceWrite | kJitHbm | kJitWinRegs | kJitPairs2) &&
                       (!(kind & kJitPairs2) || (kind & (kJitWinRegs | kJitHbm)) == kJitWinRegs)) ||
-                     (kind >= kJitCv && kind < kJitCv + 8) ||
+                     (kind >= kJitCv && kind < kJitCv + 16) ||
                      kind == kJitGreeks || kind == kJitGreeks + 1;
   if (!known) return fail(PC_EINVAL, "unknown kernel kind");
   Program p;

@@ -161,20 +161,24 @@ def test_specialised_control_variate_equals_interpreter(eng, gamma):
     desc.beta, desc.beta2 = 0.9, 0.4
     n, seed = 4096 + 77, 0x5EED0303
     out = {}
-    for jit in (False, True):
-        pc.pc_set_jit(eng.ctx, jit)
+    # interpreted; specialised at the default launch bound and at 6 blocks
+    for key in ((False, 0), (True, 0), (True, 6)):
+        pc.pc_set_jit(eng.ctx, key[0])
+        pc.pc_debug_set_cv_min_blocks(eng.ctx, key[1])
         try:
             xm = torch.empty(3 * n, dtype=torch.float32, device="cuda")
             pc.pc_debug_cv_paths(m, k, desc, tab.data_ptr(), n, seed, xm.data_ptr())
             torch.cuda.synchronize()
             res = pc.pc_price_cv(m, k, desc, tab.data_ptr(), 1 << 16, seed)
             betas = pc.pc_cv_beta(m, k, desc, tab.data_ptr(), 1 << 15, seed + 1)
-            out[jit] = (xm.cpu().numpy(), res, betas)
+            out[key] = (xm.cpu().numpy(), res, betas)
         finally:
             pc.pc_set_jit(eng.ctx, False)
-    np.testing.assert_array_equal(out[True][0].view(np.uint32), out[False][0].view(np.uint32))
-    assert out[True][1] == out[False][1]
-    assert out[True][2] == out[False][2]
+            pc.pc_debug_set_cv_min_blocks(eng.ctx, 0)
+    for key in ((True, 0), (True, 6)):
+        np.testing.assert_array_equal(out[key][0].view(np.uint32), out[(False, 0)][0].view(np.uint32))
+        assert out[key][1] == out[(False, 0)][1]
+        assert out[key][2] == out[(False, 0)][2]
 
 
 @pytest.mark.parametrize("name", ["autocall", "lookback", "double_barrier", "nested_loops", "average_40"])
