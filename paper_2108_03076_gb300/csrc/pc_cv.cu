@@ -23,39 +23,13 @@ __global__ void __launch_bounds__(kBlock) cv_kernel(const __grid_constant__ Pric
   });
 }
 
-// Network inputs of every table node (row ((k-1) * 2 + ki) * G^d + node),
-// then one row for the spot at t_0 (k = 0, no knock-in).
+// Network inputs of every table node (cv_feature_row).
 __global__ void cv_features_kernel(const CvArgs c, CvFeatureArgs fa, float *X, size_t rows) {
   const size_t r = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
   if (r >= rows) return;
-  float y[3] = {0.f, 0.f, 0.f};
-  int k = 0, ki = 0;
-  if (r + 1 < rows) {
-    size_t node = r % size_t(c.nodes);
-    const size_t grp = r / size_t(c.nodes);
-    k = int(grp / 2) + 1;
-    ki = int(grp % 2);
-    for (int ax = c.d - 1; ax >= 0; --ax) {
-      const int a = int(node % size_t(c.grid));
-      node /= size_t(c.grid);
-      y[ax] = c.lo[k - 1][ax] + float(a) * c.h[k - 1][ax];
-    }
-  } else {
-    for (int i = 0; i < c.d; ++i) y[i] = fa.ln_spot[i];
-  }
-  float *f = X + r * kCvFeatures;
-  for (int i = 0; i < 3; ++i) f[i] = i < c.d ? y[i] - logf(c.ref[i]) : 0.f;
-  for (int i = 0; i < 3; ++i) f[3 + i] = i < c.d ? fa.sigma[i] : 0.f;
-  f[6] = fa.rho;
-  f[7] = fa.r;
-  f[8] = fa.tau[k + 1] - fa.tau[k];
-  f[9] = float(c.n - k) / 5.f;
-  f[10] = float(k) / 5.f;
-  f[11] = float(ki);
-  f[12] = c.coupon;
-  f[13] = c.call_level;
-  f[14] = c.ki_level;
-  f[15] = 1.f;
+  float f[kCvFeatures];
+  cv_feature_row(c, fa, r, rows, f);
+  for (int i = 0; i < kCvFeatures; ++i) X[r * kCvFeatures + i] = f[i];
 }
 
 // Table entries from the network outputs (value, then one hedge ratio per

@@ -9,11 +9,15 @@
 
 #include "pc_internal.h"
 #include "pc_cv_types.h"
+#include "pc_mlp.h"
 
 namespace pc {
 
 // Device scratch owned by a network (grow-only, freed with it).
 float *mlp_scratch(struct ::pc_mlp *net, size_t floats);
+// The fused table build's network description (false: build with the
+// layer products).
+bool mlp_cv_tables_tc(struct ::pc_mlp *net, size_t rows, float *tables, float *delta0, CvTablesTc &t);
 // Waits for the context's stream; PC_ETIMEOUT (and the status cleared) if a
 // tensor-core product of the network reported an expired wait.
 pc_status mlp_status(struct ::pc_mlp *net);
@@ -24,13 +28,6 @@ pc_status mlp_forward_on(struct ::pc_mlp *net, const float *d_x, size_t n, float
 cudaGraphExec_t *mlp_graph(struct ::pc_mlp *net, const std::vector<uint8_t> &key);
 float *mlp_pinned(struct ::pc_mlp *net);
 int32_t *mlp_status_word(struct ::pc_mlp *net);
-
-struct CvFeatureArgs {
-  float ln_spot[kCvMaxD];
-  float sigma[kCvMaxD];
-  float rho, r;
-  float tau[kCvMaxDates + 1];     // year fractions of ordinals 0..n
-};
 
 cudaError_t launch_cv(const PriceArgs &a, const CvArgs &c, int grid, int block, size_t smem, cudaStream_t s);
 // The kernel mode (kCv* bits) of a launch: per-path outputs, second-order

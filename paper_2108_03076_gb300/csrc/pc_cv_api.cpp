@@ -261,9 +261,15 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
       cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       pc_status st = PC_OK;
       if (e == cudaSuccess) {
-        e = launch_cv_features(kc, fa, X, rows, cap);
-        if (e == cudaSuccess) st = mlp_forward_on(net, X, rows, Y, cap);
-        if (e == cudaSuccess && st == PC_OK) e = launch_cv_scatter(Y, kCvOutputs, rows, c->d, d_tables, d0, cap);
+        CvTablesTc tt;
+        if (mlp_cv_tables_tc(net, rows, d_tables, d0, tt)) {
+          // one launch: features, every layer on tcgen05, scatter
+          e = launch_cv_tables_tc(tt, kc, fa, cap);
+        } else {
+          e = launch_cv_features(kc, fa, X, rows, cap);
+          if (e == cudaSuccess) st = mlp_forward_on(net, X, rows, Y, cap);
+          if (e == cudaSuccess && st == PC_OK) e = launch_cv_scatter(Y, kCvOutputs, rows, c->d, d_tables, d0, cap);
+        }
         if (e == cudaSuccess && st == PC_OK)
           e = cudaMemcpyAsync(pin, d0, 4 * sizeof(float), cudaMemcpyDeviceToHost, cap);
         if (e == cudaSuccess && st == PC_OK)

@@ -29,6 +29,54 @@ struct CvArgs {
   int32_t pilot;                  // 1: sums of X, M, M2 and their products (8), else X, X^2, Y, Y^2
 };
 
+// Template and model inputs of the network that are the same for every
+// table node.
+struct CvFeatureArgs {
+  float ln_spot[kCvMaxD];
+  float sigma[kCvMaxD];
+  float rho, r;
+  float tau[kCvMaxDates + 1];     // year fractions of ordinals 0..n
+};
+
+#ifdef __CUDACC__
+// The network inputs of table row r of `rows`: node r mod G^d of the grid
+// of date k = (r / G^d) / 2 + 1 and knock-in state (r / G^d) mod 2, the
+// node's ln S per axis; the last row is the spot at t_0 (k = 0, no
+// knock-in).  Inputs: ln S - ln ref, sigmas, rho, r, the period's length,
+// remaining and elapsed dates / 5, knock-in, coupon, call and knock-in
+// levels, 1.
+__device__ __forceinline__ void cv_feature_row(const CvArgs &c, const CvFeatureArgs &fa, size_t r, size_t rows,
+                                               float (&f)[kCvFeatures]) {
+  float y[3] = {0.f, 0.f, 0.f};
+  int k = 0, ki = 0;
+  if (r + 1 < rows) {
+    size_t node = r % size_t(c.nodes);
+    const size_t grp = r / size_t(c.nodes);
+    k = int(grp / 2) + 1;
+    ki = int(grp % 2);
+    for (int ax = c.d - 1; ax >= 0; --ax) {
+      const int a = int(node % size_t(c.grid));
+      node /= size_t(c.grid);
+      y[ax] = c.lo[k - 1][ax] + float(a) * c.h[k - 1][ax];
+    }
+  } else {
+    for (int i = 0; i < c.d; ++i) y[i] = fa.ln_spot[i];
+  }
+  for (int i = 0; i < 3; ++i) f[i] = i < c.d ? y[i] - logf(c.ref[i]) : 0.f;
+  for (int i = 0; i < 3; ++i) f[3 + i] = i < c.d ? fa.sigma[i] : 0.f;
+  f[6] = fa.rho;
+  f[7] = fa.r;
+  f[8] = fa.tau[k + 1] - fa.tau[k];
+  f[9] = float(c.n - k) / 5.f;
+  f[10] = float(k) / 5.f;
+  f[11] = float(ki);
+  f[12] = c.coupon;
+  f[13] = c.call_level;
+  f[14] = c.ki_level;
+  f[15] = 1.f;
+}
+#endif
+
 // MODE bits of the control-variate kernels: kCvWrite (per-path X, M, M2
 // out), kCvGamma (second-order term), kCvPilot (moment sums for the betas
 // instead of X, X^2, Y, Y^2); and for the run-time specialised kernel

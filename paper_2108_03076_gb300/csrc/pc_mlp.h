@@ -78,6 +78,28 @@ bool make_tc_maps(GemmKind kind, const GemmArgs &g, TcMaps &m);
 cudaError_t launch_gemm_tc(GemmKind kind, int epi, const GemmArgs &g, const TcMaps &m, int splits,
                            int32_t *status, cudaStream_t s, bool withhold = false);
 
+// The control variate's hedge tables in one launch (cv_tables_tc): per
+// 128-row tile, the network inputs of the table rows (cv_feature_row) go to
+// shared memory, every layer's product runs on tcgen05 from there (weights
+// streamed by TMA, the accumulator in TMEM), the hidden activations return
+// to shared memory as the next layer's operand, and the last layer's hedge
+// ratios go to the tables (row r < rows - 1: tables[4 r + i]; the last row:
+// delta0).  Networks of up to kCvNetMaxLayers layers, input and output
+// padded to 64, hidden widths multiples of 64 up to 256.
+constexpr int kCvNetMaxLayers = 4;
+struct CvTablesTc {
+  CUtensorMap w[kCvNetMaxLayers];       // layer l's BF16 weights [wp[l+1]][wp[l]], box 64 x wp[l+1]
+  const float *bias[kCvNetMaxLayers];   // [wp[l+1]], zero padded
+  int L;
+  int wp[kCvNetMaxLayers + 1];
+  size_t rows;
+  float *tables, *delta0;
+  int32_t *status;                      // |= 4 when a bounded wait expires
+};
+bool cv_tables_tc_shape(int L, const int *wp);
+bool make_weight_map(CUtensorMap &m, const __nv_bfloat16 *w, int n_out, int n_in);
+cudaError_t launch_cv_tables_tc(const CvTablesTc &t, const struct CvArgs &c, const struct CvFeatureArgs &fa,
+                                cudaStream_t s);
 // x [n, fin] FP32 -> X [rows, ld] BF16, zero beyond n rows / fin columns.
 cudaError_t launch_to_bf16(const float *x, size_t n, int fin, __nv_bfloat16 *X, size_t rows, int ld,
                            cudaStream_t s);

@@ -361,6 +361,34 @@ cudaGraphExec_t *mlp_graph(pc_mlp *N, const std::vector<uint8_t> &key) {
 float *mlp_pinned(pc_mlp *N) { return N->h_pin; }
 int32_t *mlp_status_word(pc_mlp *N) { return N->dstatus; }
 
+// The fused table build's network description (cv_tables_tc): false when
+// the products do not run on tcgen05 or the network's shape is outside the
+// kernel's (then the caller builds the tables with the layer products).
+bool mlp_cv_tables_tc(pc_mlp *N, size_t rows, float *tables, float *delta0, CvTablesTc &t) {
+  if (!N->tc_ok || N->gemm != PC_MLP_GEMM_AUTO || N->tc_withhold || !cv_tables_tc_shape(N->L, N->wp.data()))
+    return false;
+  std::memset(&t, 0, sizeof(t));
+  t.L = N->L;
+  for (int l = 0; l <= N->L; ++l) t.wp[l] = N->wp[l];
+  for (int l = 0; l < N->L; ++l) {
+    // the weight map of layer l, encoded once per network
+    const uint64_t key = (uint64_t(7) << 56) | uint64_t(l);
+    auto it = N->tc_maps.find(key);
+    if (it == N->tc_maps.end()) {
+      TcMaps mm;
+      if (!make_weight_map(mm.b, N->pb + N->offW[l], N->wp[l + 1], N->wp[l])) return false;
+      it = N->tc_maps.emplace(key, mm).first;
+    }
+    t.w[l] = it->second.b;
+    t.bias[l] = N->p + N->offB[l];
+  }
+  t.rows = rows;
+  t.tables = tables;
+  t.delta0 = delta0;
+  t.status = N->dstatus;
+  return true;
+}
+
 pc_status mlp_forward_on(pc_mlp *N, const float *d_x, size_t n, float *d_y, cudaStream_t s) {
   for (size_t b0 = 0; b0 < n; b0 += N->max_rows) {
     const size_t nb = std::min(N->max_rows, n - b0), rows = rows_for(nb);

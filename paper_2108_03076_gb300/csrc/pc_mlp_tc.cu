@@ -46,6 +46,7 @@
 #include <mutex>
 
 #include "pc_mlp.h"
+#include "pc_cv_types.h"
 
 namespace pc {
 namespace {
@@ -458,6 +459,238 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// The hedge tables in one launch (cv_tables_tc): one CTA per 128-row tile
+// (persistent over tiles), the tile's activations resident in shared memory
+// between layers.  Shared memory: A, the current layer's input, 128 rows x
+// up to 256 columns as four K-major 128-byte-swizzled blocks of 64 columns
+// (16 KB each, what the MMA's A descriptor reads); a ring of kStages weight
+// stages of up to 256 rows x 64 k (32 KB, written by TMA).  Roles:
+//   thread 0      TMA producer: every layer's 64-deep weight chunks, in
+//                 order, through the ring (full / empty barriers);
+//   thread 32     MMA issuer: per layer, once its input is in A ("aready",
+//                 one arrival per epilogue warp), wp[l] / 64 chunks of four
+//                 128 x N x 16 tcgen05.mma into TMEM columns 0 .. N - 1, then
+//                 a commit to "afull";
+//   warps 4..11   epilogue: the tile's inputs (features) into A block 0;
+//                 after each hidden layer's "afull", bias + softplus of their
+//                 32 rows x N / 2 columns back into A as BF16 (the next
+//                 layer's input); after the last layer, the hedge ratios to
+//                 the tables.  A and TMEM are single buffers: a layer's MMAs
+//                 start only after the epilogue has read TMEM and written A,
+//                 and the epilogue writes A only after the MMAs reading it
+//                 completed.
+constexpr uint32_t kFzABytes = 4 * kATileBytes;       // 64 KB
+constexpr uint32_t kFzStageBytes = 256 * kTcBK * 2;   // 32 KB
+constexpr size_t kFzSmem = 1024 + size_t(kFzABytes) + size_t(kStages) * kFzStageBytes;
+
+__device__ __forceinline__ void st_shared16(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+// 16-byte chunk ch (of 8) of row r in a K-major 128-byte-swizzled block
+__device__ __forceinline__ uint32_t sw128_chunk(uint32_t block, int r, int ch) {
+  return block + uint32_t(r * 128 + ((ch ^ (r & 7)) << 4));
+}
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+// generic-proxy writes to shared memory visible to the tensor core's reads
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    cv_tables_tc(const __grid_constant__ CvTablesTc t, const __grid_constant__ CvArgs c,
+                 const __grid_constant__ CvFeatureArgs fa) {
+  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2 * kStages + 3];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const volatile int *abort = &abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tiles = int((t.rows + kTcBM - 1) / kTcBM);
+  const uint32_t abuf = (su32(tc_smem_raw) + 1023u) & ~1023u, ring = abuf + kFzABytes;
+  const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[kStages]);
+  const uint32_t aready = su32(&bars[2 * kStages]), afull = aready + 8, done = aready + 16;
+  const long long lim = kWaitCycles;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
+                 "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < 2 * kStages; ++s) mbar_init(su32(&bars[s]), 1);
+    mbar_init(aready, kEpiWarps);
+    mbar_init(afull, 1);
+    mbar_init(done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  if (threadIdx.x == 0) {
+    // TMA producer: chunk counter q runs across layers and tiles
+    uint32_t q = 0, issued = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < tiles && ok && !*abort; tile += gridDim.x) {
+      for (int l = 0; l < t.L && ok; ++l) {
+        const int nk = t.wp[l] / kTcBK;
+        const uint32_t bytes = uint32_t(t.wp[l + 1]) * kTcBK * 2;
+        for (int ch = 0; ch < nk; ++ch, ++q) {
+          const uint32_t s = q % kStages, u = q / kStages;
+          if (u >= 1 && !mbar_wait(empty0 + 8 * s, (u - 1) & 1, lim, abort)) {
+            if (!*abort) atomicOr(t.status, 4);
+            atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full0 + 8 * s, bytes);
+          tma_load_2d(ring + s * kFzStageBytes, &t.w[l], ch * kTcBK, 0, full0 + 8 * s);
+          issued = q + 1;
+        }
+      }
+    }
+    // the last kStages issued chunks' copies complete before the CTA exits
+    for (uint32_t k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
+      if (!mbar_wait(full0 + 8 * (k % kStages), (k / kStages) & 1, lim)) atomicOr(t.status, 4);
+  } else if (threadIdx.x == 32) {
+    // MMA issuer; ph counts the layers issued (the aready / afull phases)
+    uint32_t q = 0, ph = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < tiles && ok && !*abort; tile += gridDim.x) {
+      for (int l = 0; l < t.L && ok; ++l, ++ph) {
+        if (!mbar_wait(aready, ph & 1, lim, abort)) {
+          if (!*abort) atomicOr(t.status, 4);
+          atomicExch(&abort_flag, 1);
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t idesc = idesc_bf16(kTcBM, t.wp[l + 1]);
+        const int nk = t.wp[l] / kTcBK;
+        for (int ch = 0; ch < nk; ++ch, ++q) {
+          const uint32_t s = q % kStages, u = q / kStages;
+          if (!mbar_wait(full0 + 8 * s, u & 1, lim, abort)) {
+            if (!*abort) atomicOr(t.status, 4);
+            atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t sa = abuf + uint32_t(ch) * kATileBytes, sb = ring + s * kFzStageBytes;
+#pragma unroll
+          for (int kk = 0; kk < kTcBK / 16; ++kk)
+            mma_bf16_tc(tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), idesc, (ch | kk) != 0);
+          mma_commit(empty0 + 8 * s);
+        }
+        if (ok) mma_commit(afull);
+      }
+    }
+    // every MMA this thread issued completes before `done`
+    mma_commit(done);
+  } else if (warp >= 4) {
+    // epilogue: warp w owns TMEM lanes (tile rows) 32 (w % 4) .. + 31 and
+    // half (w - 4) / 4 of each layer's columns; ph counts the layers drained
+    const int qw = warp & 3, half = (warp - 4) >> 2, rl = 32 * qw + lane;
+    const uint32_t trow = tmem + (uint32_t(32 * qw) << 16);
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < tiles && ok && !*abort; tile += gridDim.x) {
+      const size_t r = size_t(tile) * kTcBM + size_t(rl);
+      // layer 0's input: the row's 16 features (columns 0..15 of block 0),
+      // zeros up to column 63
+      if (half == 0) {
+        float f[kCvFeatures];
+        if (r < t.rows) {
+          cv_feature_row(c, fa, r, t.rows, f);
+        } else {
+#pragma unroll
+          for (int i = 0; i < kCvFeatures; ++i) f[i] = 0.f;
+        }
+        uint32_t pk[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(f[2 * i], f[2 * i + 1]);
+        st_shared16(sw128_chunk(abuf, rl, 0), pk[0], pk[1], pk[2], pk[3]);
+        st_shared16(sw128_chunk(abuf, rl, 1), pk[4], pk[5], pk[6], pk[7]);
+        st_shared16(sw128_chunk(abuf, rl, 2), 0u, 0u, 0u, 0u);
+        st_shared16(sw128_chunk(abuf, rl, 3), 0u, 0u, 0u, 0u);
+      } else {
+#pragma unroll
+        for (int ch = 4; ch < 8; ++ch) st_shared16(sw128_chunk(abuf, rl, ch), 0u, 0u, 0u, 0u);
+      }
+      fence_async_shared();
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(aready);
+      for (int l = 0; l < t.L; ++l, ++ph) {
+        if (!mbar_wait(afull, ph & 1, lim, abort)) {
+          if (!*abort) atomicOr(t.status, 4);
+          atomicExch(&abort_flag, 1);
+          ok = false;
+          break;
+        }
+        __syncwarp();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (l + 1 < t.L) {
+          // bias + softplus -> BF16 into A, the next layer's input
+          const int cols = t.wp[l + 1] / 2, c0 = half * cols;
+#pragma unroll 1
+          for (int j = 0; j < cols; j += 32) {
+            const int col = c0 + j;
+            float v[32];
+            tmem_ld32(trow + uint32_t(col), v);
+            const float4 *b4 = reinterpret_cast<const float4 *>(t.bias[l] + col);
+            uint32_t pk[16];
+#pragma unroll
+            for (int q4 = 0; q4 < 8; ++q4) {
+              const float4 b = __ldg(b4 + q4);
+              pk[2 * q4] = pack_bf16(softplus_fast(v[4 * q4] + b.x), softplus_fast(v[4 * q4 + 1] + b.y));
+              pk[2 * q4 + 1] = pack_bf16(softplus_fast(v[4 * q4 + 2] + b.z), softplus_fast(v[4 * q4 + 3] + b.w));
+            }
+            const uint32_t blk = abuf + uint32_t(col >> 6) * kATileBytes;
+            const int ch0 = (col & 63) >> 3;
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4)
+              st_shared16(sw128_chunk(blk, rl, ch0 + q4), pk[4 * q4], pk[4 * q4 + 1], pk[4 * q4 + 2], pk[4 * q4 + 3]);
+          }
+          fence_async_shared();
+          asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(aready);
+        } else if (half == 0) {
+          // the last layer: hedge ratios (outputs 1 .. d) + bias
+          float v[32];
+          tmem_ld32(trow, v);
+          asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+          if (r < t.rows) {
+#pragma unroll
+            for (int i = 0; i < kCvMaxD; ++i) {
+              if (i >= c.d) break;
+              const float y = v[1 + i] + __ldg(t.bias[l] + 1 + i);
+              if (r + 1 < t.rows) t.tables[r * 4 + i] = y;
+              else t.delta0[i] = y;
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // every MMA has completed before TMEM is released
+  if (warp == 0 && !mbar_wait(done, 0, lim)) atomicOr(t.status, 4);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256));
+  }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -618,6 +851,38 @@ cudaError_t launch_gemm_tc(GemmKind kind, int epi, const GemmArgs &g, const TcMa
                  : launch_tc<kEpiPartial, 128, true, true>(m.a, m.b, a, s);
   }
   return cudaErrorInvalidValue;
+}
+
+}  // namespace pc
+
+namespace pc {
+
+bool cv_tables_tc_shape(int L, const int *wp) {
+  if (L < 2 || L > kCvNetMaxLayers || wp[0] != kTcBK || wp[L] != kTcBK) return false;
+  for (int l = 1; l < L; ++l)
+    if (wp[l] % kTcBK || wp[l] > 256) return false;
+  return true;
+}
+
+bool make_weight_map(CUtensorMap &m, const __nv_bfloat16 *w, int n_out, int n_in) {
+  if (gemm_tc_init() != cudaSuccess || n_out > 256) return false;
+  return make_map(m, w, uint64_t(n_out), uint64_t(n_in), uint64_t(n_in), uint32_t(n_out));
+}
+
+cudaError_t launch_cv_tables_tc(const CvTablesTc &t, const CvArgs &c, const CvFeatureArgs &fa, cudaStream_t s) {
+  if (!t.status || !t.tables || !t.delta0 || t.rows < 1 || !cv_tables_tc_shape(t.L, t.wp))
+    return cudaErrorInvalidValue;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = gemm_tc_init();
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(cv_tables_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kFzSmem));
+  });
+  if (attr != cudaSuccess) return attr;
+  const long long tiles = (long long)((t.rows + kTcBM - 1) / kTcBM), cap = (long long)sm_count();
+  cv_tables_tc<<<unsigned(tiles < cap ? tiles : cap), kTcThreads, kFzSmem, s>>>(t, c, fa);
+  return cudaGetLastError();
 }
 
 }  // namespace pc

@@ -77,3 +77,33 @@ def test_surrogate_value_at_the_spot(eng, trained):
     k = eng.contract(w.il_text, w.tparams)
     price, _ = pc.pc_price(m, k, 1 << 20, 0x5EED0001)
     assert abs(v - price) < 0.05 * price, (v, price)
+
+
+@pytest.mark.parametrize("grid", [5, 12])
+def test_fused_table_build_matches_layer_products(eng, trained, grid):
+    """The one-launch table build (features, every layer on tcgen05 with the
+    activations in shared memory, scatter) against the build from separate
+    layer products on the warp-level kernel (itself checked against the
+    oracle's backpropagation network): every table entry and delta0 within
+    the BF16 tolerance of the network's outputs, 2 * 2^-8 (|b| + RMS); grid 5
+    makes 1001 rows, a ragged last tile."""
+    w = W.worst_of_autocall()
+    m = eng.model(w.market)
+    desc, fused = trained.tables(m, grid=grid)
+    d_fused = [desc.delta0[i] for i in range(3)]
+    a = fused[:pc.pc_cv_table_size(desc)].cpu().numpy().astype(np.float64)
+    pc.pc_mlp_set_gemm(trained.net, pc.MLP_GEMM_MMA_SYNC)
+    try:
+        desc2, layered = trained.tables(m, grid=grid)
+    finally:
+        pc.pc_mlp_set_gemm(trained.net, pc.MLP_GEMM_AUTO)
+    b = layered[:pc.pc_cv_table_size(desc2)].cpu().numpy().astype(np.float64)
+    d_layered = [desc2.delta0[i] for i in range(3)]
+    assert a.shape == b.shape and np.all(np.isfinite(a))
+    used = np.arange(a.size) % 4 < 3          # 16-byte node groups: 3 ratios + padding
+    s = np.sqrt(np.mean(b[used] ** 2))
+    assert s > 1e-3
+    tol = 2 * 2.0 ** -8 * (np.abs(b[used]) + s)
+    err = np.abs(a[used] - b[used])
+    assert np.all(err <= tol), (err.max(), np.argmax(err - tol))
+    assert np.allclose(d_fused, d_layered, rtol=0, atol=2 * 2.0 ** -8 * (np.abs(d_layered).max() + s))
