@@ -25,9 +25,9 @@
 //                     buffers of BN columns), tcgen05.commit to the stage's
 //                     empty barrier and, after a tile's last chunk, to the
 //                     buffer's "tfull" barrier;
-//   warps 4..11       epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
-//                     (tile rows) of half (w - 4) / 4 of the tile's columns,
-//                     32 columns at a time (tcgen05.ld), applies
+//   warps 4..        epilogue, BN / 8 warps (4 + BN / 8 warps in all): warp
+//                     w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) of
+//                     columns 32 ((w - 4) / 4) .. + 31 (tcgen05.ld), applies
 //                     the product's epilogue (bias + softplus -> BF16; bias ->
 //                     FP32; times the softplus derivative from the stored
 //                     activation -> BF16; FP32 split partial) and frees the
@@ -52,7 +52,13 @@ namespace pc {
 namespace {
 
 constexpr int kTcBM = 128, kTcBK = 64, kStages = 4, kTcThreads = 384;
-constexpr int kEpiWarps = 8;  // warps 4..11: two per TMEM lane quarter, each half the columns
+constexpr int kEpiWarps = 8;  // warps 4..11 of the table build: two per TMEM lane quarter
+// epilogue warps of a product with BN-wide tiles: BN / 32 per TMEM lane
+// quarter, each 32 of the tile's columns (8 for BN = 64, 16 for BN = 128)
+template <int BN>
+__host__ __device__ constexpr int epi_warps() { return BN / 8; }
+template <int BN>
+__host__ __device__ constexpr int tc_threads() { return 128 + 32 * epi_warps<BN>(); }
 constexpr uint32_t kATileBytes = kTcBM * kTcBK * 2;  // 16 KB
 constexpr long long kWaitCycles = 2000000000ll;      // ~1 s at 2 GHz
 constexpr long long kTestWaitCycles = 20000000ll;    // ~10 ms: the failure test's limit
@@ -186,10 +192,10 @@ __device__ __forceinline__ float dsoftplus(float h) {
 
 // Output element size of an epilogue (BF16 activations or gradients, FP32
 // outputs and partials) and the staging area of one epilogue warp: its 32
-// rows by half the tile's columns, at most 32 x 64 FP32 values.
+// rows by its 32 columns, at most 32 x 32 FP32 values.
 template <int EPI>
 __host__ __device__ constexpr int out_bytes() { return (EPI == kEpiBiasSoftplus || EPI == kEpiDSoftplus) ? 2 : 4; }
-constexpr uint32_t kStageWarpBytes = 32 * 64 * 4;
+constexpr uint32_t kStageWarpBytes = 32 * 32 * 4;
 
 // The epilogue of 32 accumulator columns of one row (row `row`, columns
 // col .. col + 31 of C; bias epilogues add the bias; kEpiDSoftplus reads the
@@ -269,7 +275,7 @@ __device__ __forceinline__ void epilogue32(const TcArgs &g, int row, int col, co
 // AMN / BMN: operand A (B) is M-major (N-major) in memory, loaded as
 // BM / 64 (BN / 64) boxes of 64 x 64 in the MN-major swizzled layout.
 template <int EPI, int BN, bool AMN, bool BMN>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(tc_threads<BN>(), 1)
     mlp_gemm_tc(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcArgs g) {
   constexpr uint32_t kBTileBytes = BN * kTcBK * 2;
   constexpr uint32_t kStageBytes = kATileBytes + kBTileBytes;
@@ -305,8 +311,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int s = 0; s < 2 * kStages; ++s) mbar_init(su32(&bars[s]), 1);
     mbar_init(tfull0, 1);
     mbar_init(tfull0 + 8, 1);
-    mbar_init(tempty0, kEpiWarps);
-    mbar_init(tempty0 + 8, kEpiWarps);
+    mbar_init(tempty0, epi_warps<BN>());
+    mbar_init(tempty0 + 8, epi_warps<BN>());
     mbar_init(done, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -394,8 +400,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     mma_commit(done);
   } else if (warp >= 4) {
     // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 (rows of the
-    // tile), columns of half (w - 4) / 4 of it
-    const int qw = warp & 3, half = (warp - 4) >> 2;
+    // tile), columns 32 ((w - 4) / 4) .. + 31 of it
+    const int qw = warp & 3, grp = (warp - 4) >> 2;
     int i = 0;
     for (int t = blockIdx.x; t < tiles && !*abort; t += gridDim.x, ++i) {
       int z, m0, n0, c0, nk;
@@ -410,15 +416,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const int row = m0 + 32 * qw + lane;
       const uint32_t trow = tmem + (uint32_t(32 * qw) << 16) + uint32_t(buf * BN);
-      // this warp's 32 rows x BN / 2 columns, staged as rows of rb bytes
+      // this warp's 32 rows x 32 columns, staged as rows of rb bytes
       constexpr int EB = out_bytes<EPI>();
-      constexpr int rb = (BN / 2) * EB;
+      constexpr int rb = 32 * EB;
       const uint32_t st = stage0 + uint32_t(warp - 4) * kStageWarpBytes;
-      const int col0 = n0 + half * (BN / 2);
+      const int col0 = n0 + grp * 32;
 #pragma unroll 1
-      for (int j = 0; j < BN / 2; j += 32) {
+      for (int j = 0; j < 32; j += 32) {
         float r[32];
-        tmem_ld32(trow + half * (BN / 2) + j, r);
+        tmem_ld32(trow + grp * 32 + j, r);
         if (row < g.M) epilogue32<EPI>(g, row, col0 + j, r, st, lane, rb, j * EB / 16);
       }
       // the accumulator buffer is free once read
@@ -726,7 +732,7 @@ bool make_map(CUtensorMap &m, const __nv_bfloat16 *p, uint64_t rows, uint64_t co
 
 template <int BN>
 constexpr size_t tc_smem() {
-  return size_t(kStages) * (kATileBytes + size_t(BN) * kTcBK * 2) + size_t(kEpiWarps) * kStageWarpBytes + 1024;
+  return size_t(kStages) * (kATileBytes + size_t(BN) * kTcBK * 2) + size_t(epi_warps<BN>()) * kStageWarpBytes + 1024;
 }
 
 int sm_count() {
@@ -747,7 +753,7 @@ cudaError_t launch_tc(const CUtensorMap &ta, const CUtensorMap &tb, const TcArgs
   const long long tiles = (long long)(a.N / BN) * ((a.M + kTcBM - 1) / kTcBM) * a.splits;
   const long long cap = (long long)sm_count();
   const unsigned grid = unsigned(tiles < cap ? tiles : cap);
-  mlp_gemm_tc<EPI, BN, AMN, BMN><<<grid, kTcThreads, tc_smem<BN>(), s>>>(ta, tb, a);
+  mlp_gemm_tc<EPI, BN, AMN, BMN><<<grid, tc_threads<BN>(), tc_smem<BN>(), s>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
