@@ -204,3 +204,95 @@ def table_gammas(S: np.ndarray, ki: np.ndarray, tables: np.ndarray, lo: np.ndarr
             g = sl / (h[k - 1][None, None, :] * S[sel, k, :][:, None, :])
             out[sel, k] = 0.5 * (g + np.swapaxes(g, 1, 2))
     return out
+
+
+# --- nearest-node Taylor tables -------------------------------------------
+# The hedge tables the engine prices with: each node keeps its hedge ratios
+# and their slopes along the grid axes (central differences of the node
+# values, one-sided on the grid's faces), and a point takes the nearest
+# node's ratios plus the first-order step to it, Delta_i(u) = Delta_i(a) +
+# sum_j s_ij(a) (u_j - a_j) with a = floor(u + 1/2), u the grid coordinate
+# (ln S - lo) / h clamped to [0, G - 1].  Its gamma is the node's slopes
+# divided by h_j S_j, symmetrised.  Any such hedge is adapted, so the
+# martingales above keep mean zero.
+
+
+def node_slopes(table: np.ndarray, G: int) -> np.ndarray:
+    """Slopes [G^d, d, d] (s[node, i, j] = d Delta_i / d u_j) of a table
+    [G^d, d] by central differences along each axis, one-sided at the ends."""
+    nodes, d = table.shape
+    T = table.reshape((G,) * d + (d,))
+    out = np.zeros((G,) * d + (d, d))
+    for j in range(d):
+        fwd = np.take(T, np.minimum(np.arange(G) + 1, G - 1), axis=j)
+        bwd = np.take(T, np.maximum(np.arange(G) - 1, 0), axis=j)
+        span = np.where((np.arange(G) == 0) | (np.arange(G) == G - 1), 1.0, 2.0)
+        shape = [1] * d + [1]
+        shape[j] = G
+        out[..., :, j] = (fwd - bwd) / span.reshape(shape)
+    return out.reshape(nodes, d, d)
+
+
+def taylor_lookup(table: np.ndarray, slopes: np.ndarray, lo: np.ndarray, h: np.ndarray, G: int,
+                  y: np.ndarray):
+    """(Delta [N, d], slopes [N, d, d]) at points y [N, d] from the nearest node."""
+    N, d = y.shape
+    u = np.clip((y - lo[None, :]) / h[None, :], 0.0, G - 1.0)
+    a = np.floor(u + 0.5).astype(np.int64)
+    node = np.zeros(N, np.int64)
+    for ax in range(d):
+        node = node * G + a[:, ax]
+    s = slopes[node]
+    return table[node] + np.einsum("pij,pj->pi", s, u - a), s
+
+
+def table_deltas_taylor(S: np.ndarray, ki: np.ndarray, tables: np.ndarray, lo: np.ndarray,
+                        h: np.ndarray, G: int, delta0: Sequence[float]) -> np.ndarray:
+    """``table_deltas`` with nearest-node Taylor tables (node values tables
+    [n-1, 2, G^d, d], slopes by ``node_slopes``)."""
+    N, n1, d = S.shape
+    n = n1 - 1
+    out = np.zeros((N, n, d))
+    out[:, 0, :] = np.asarray(delta0)[None, :]
+    for k in range(1, n):
+        y = np.log(S[:, k, :])
+        for s in (0, 1):
+            sel = ki[:, k] == bool(s)
+            if sel.any():
+                sl = node_slopes(tables[k - 1, s], G)
+                out[sel, k, :] = taylor_lookup(tables[k - 1, s], sl, lo[k - 1], h[k - 1], G, y[sel])[0]
+    return out
+
+
+def table_gammas_taylor(S: np.ndarray, ki: np.ndarray, tables: np.ndarray, lo: np.ndarray,
+                        h: np.ndarray, G: int) -> np.ndarray:
+    """``table_gammas`` with nearest-node Taylor tables: the node's slopes."""
+    N, n1, d = S.shape
+    n = n1 - 1
+    out = np.zeros((N, n, d, d))
+    for k in range(1, n):
+        y = np.log(S[:, k, :])
+        for s in (0, 1):
+            sel = ki[:, k] == bool(s)
+            if not sel.any():
+                continue
+            sl = node_slopes(tables[k - 1, s], G)
+            g = taylor_lookup(tables[k - 1, s], sl, lo[k - 1], h[k - 1], G, y[sel])[1]
+            g = g / (h[k - 1][None, None, :] * S[sel, k, :][:, None, :])
+            out[sel, k] = 0.5 * (g + np.swapaxes(g, 1, 2))
+    return out
+
+
+def node_records(tables: np.ndarray, G: int) -> np.ndarray:
+    """The engine's table layout from node values [n-1, 2, G^d, d]: per node
+    12 floats, Delta_0..2 then s_ij at 3 + 3 i + j (zero beyond d)."""
+    m, two, nodes, d = tables.shape
+    rec = np.zeros((m, two, nodes, 12))
+    for a in range(m):
+        for b in range(two):
+            sl = node_slopes(tables[a, b], G)
+            rec[a, b, :, :d] = tables[a, b]
+            for i in range(d):
+                for j in range(d):
+                    rec[a, b, :, 3 + 3 * i + j] = sl[:, i, j]
+    return rec

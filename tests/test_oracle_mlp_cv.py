@@ -239,3 +239,85 @@ def test_table_slopes_are_the_derivatives_of_the_interpolant():
         ym[:, j] -= eps * h[j]
         fd = (cv.table_lookup(table, lo, h, G, yp) - cv.table_lookup(table, lo, h, G, ym)) / (2 * eps)
         np.testing.assert_allclose(sl[:, :, j], fd, rtol=1e-6, atol=1e-8)
+
+
+def test_taylor_tables_are_exact_on_affine_functions_and_clamp():
+    """Nearest-node Taylor tables: node slopes of an affine table are its
+    coefficients (central and one-sided differences alike), and the lookup
+    reproduces the affine function anywhere in the grid; points outside
+    take the clamped coordinate."""
+    G, d = 6, 3
+    rng = np.random.default_rng(3)
+    A, b = rng.normal(size=(d, d)), rng.normal(size=d)
+    lo, h = np.array([-1.0, -0.5, 0.2]), np.array([0.3, 0.2, 0.25])
+    nodes = np.stack(np.meshgrid(*[np.arange(G)] * d, indexing="ij"), -1).reshape(-1, d)
+    table = nodes @ A.T + b
+    sl = cv.node_slopes(table, G)
+    np.testing.assert_allclose(sl, np.broadcast_to(A, sl.shape), atol=1e-12)
+    y = lo + h * rng.uniform(0.0, G - 1.0, size=(2000, d))
+    delta, s = cv.taylor_lookup(table, sl, lo, h, G, y)
+    np.testing.assert_allclose(delta, ((y - lo) / h) @ A.T + b, atol=1e-12)
+    out = lo + h * np.array([[-2.0, 0.5, G + 3.0]])
+    clamp = lo + h * np.array([[0.0, 0.5, G - 1.0]])
+    np.testing.assert_allclose(cv.taylor_lookup(table, sl, lo, h, G, out)[0],
+                               cv.taylor_lookup(table, sl, lo, h, G, clamp)[0])
+
+
+def test_taylor_node_slopes_and_nearest_node_on_a_quadratic():
+    """On Delta = u^2 along one axis: interior slopes are the exact 2u
+    (central differences), the ends one-sided (1 at node 0, 2G - 3 at the
+    last), and a point takes its nearest node: u = 2.4 -> node 2 (4 + 4 x
+    0.4), u = 2.6 -> node 3 (9 - 6 x 0.4)."""
+    G = 7
+    table = (np.arange(G, dtype=np.float64) ** 2)[:, None]
+    sl = cv.node_slopes(table, G)[:, 0, 0]
+    np.testing.assert_allclose(sl, [1.0] + [2.0 * a for a in range(1, G - 1)] + [2.0 * G - 3.0])
+    lo, h = np.array([0.0]), np.array([1.0])
+    got = cv.taylor_lookup(table, cv.node_slopes(table, G), lo, h, G, np.array([[2.4], [2.6]]))[0][:, 0]
+    np.testing.assert_allclose(got, [4.0 + 4.0 * 0.4, 9.0 - 6.0 * 0.4])
+
+
+def test_taylor_hedges_keep_the_martingales_at_mean_zero():
+    """Hedge ratios and gammas from nearest-node Taylor tables (random node
+    values) keep E[M] = E[M2] = 0 on GBM paths (a few standard errors)."""
+    rng = np.random.default_rng(11)
+    N, n, d, G = 200000, 4, 2, 5
+    sig = np.array([0.25, 0.3])
+    corr = np.array([[1.0, 0.4], [0.4, 1.0]])
+    r = 0.02
+    tau = np.arange(n + 1) * 0.5
+    L = np.linalg.cholesky(corr)
+    S = np.ones((N, n + 1, d))
+    for k in range(n):
+        dt = tau[k + 1] - tau[k]
+        z = rng.standard_normal((N, d)) @ L.T
+        S[:, k + 1] = S[:, k] * np.exp((r - 0.5 * sig ** 2) * dt + sig * np.sqrt(dt) * z)
+    disc = np.exp(-r * tau)
+    alive = np.ones((N, n), bool)
+    ki = np.zeros((N, n + 1), bool)
+    ki[:, 2:] = S[:, 1:2, 0] < 0.9
+    lo = np.tile(np.array([-0.6, -0.6]), (n - 1, 1))
+    h = np.tile(np.array([0.3, 0.3]), (n - 1, 1))
+    tables = rng.normal(0.5, 0.2, size=(n - 1, 2, G ** d, d))
+    delta = cv.table_deltas_taylor(S, ki, tables, lo, h, G, [0.5, 0.4])
+    M = cv.hedge_martingale(S, disc, alive, delta)
+    assert abs(M.mean()) < 4 * M.std() / np.sqrt(N)
+    gam = cv.table_gammas_taylor(S, ki, tables, lo, h, G)
+    M2 = cv.gamma_martingale(S, disc, alive, gam, corr, sig, tau)
+    assert abs(M2.mean()) < 4 * M2.std() / np.sqrt(N)
+    assert M.std() > 0.01 and M2.std() > 1e-4
+
+
+def test_node_records_layout():
+    """The engine's 12-float node records: ratios, then s_ij at 3 + 3 i + j."""
+    G, d = 4, 2
+    rng = np.random.default_rng(5)
+    tables = rng.normal(size=(2, 2, G ** d, d))
+    rec = cv.node_records(tables, G)
+    assert rec.shape == (2, 2, G ** d, 12)
+    np.testing.assert_array_equal(rec[..., :d], tables)
+    sl = cv.node_slopes(tables[1, 0], G)
+    for i in range(d):
+        for j in range(d):
+            np.testing.assert_array_equal(rec[1, 0, :, 3 + 3 * i + j], sl[:, i, j])
+    assert not rec[..., 2].any() and not rec[..., 3 + 3 * 2:].any() and not rec[..., 5].any()
