@@ -637,10 +637,18 @@ pc_status pc_cv_labels(size_t n, int32_t d, const double *prices, const double *
  * fills the tables itself).  Errors: PC_EINVAL, PC_ELIMIT (d > 3 or more
  * than PC_CV_MAX_DATES dates). */
 pc_status pc_cv_grid(const pc_model *model, int32_t grid, float width_sd, pc_cv_desc *desc);
-/* Floats of the tables of desc: (n - 1) * 2 * grid^d * 4. */
+/* Floats of the tables of desc: (n - 1) * 2 * grid^d * 12.  Table (k - 1) * 2
+ * + knock-in holds date k's nodes, node index sum_i a_i grid^(d-1-i), 12
+ * floats each: the hedge ratios Delta_0..2, then their slopes along the grid
+ * axes s_ij = d Delta_i / d u_j at 3 + 3 i + j (zero beyond d).  A path at
+ * grid coordinate u (u_i = (ln S_i - lo_i) / h_i, clamped to [0, grid - 1])
+ * takes the nearest node a = floor(u + 1/2): Delta_i = Delta_i(a) + sum_j
+ * s_ij(a) (u_j - a_j), and gamma_ij = s_ij / (h_j S_j) symmetrised. */
 pc_status pc_cv_table_size(const pc_cv_desc *desc, size_t *floats);
 /* Evaluate the network (16 inputs, outputs value and hedge ratios) at every
- * table node and at the spot and write d_tables (device, cap_floats) and
+ * table node and at the spot and write d_tables (device, cap_floats: the
+ * ratios from the network, the slopes as central differences of the
+ * neighbouring nodes' ratios, one-sided on the grid's faces) and
  * desc->delta0.  Network inputs of a state (date k, y = ln S, knock-in):
  * y_i - ln ref_i (i < 3, 0 beyond d), sigma_i (i < 3), the correlation of
  * underlyings 0 and 1 (0 if d = 1), r, tau_{k+1} - tau_k, (n - k) / 5,

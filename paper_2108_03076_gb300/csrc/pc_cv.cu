@@ -33,17 +33,43 @@ __global__ void cv_features_kernel(const CvArgs c, CvFeatureArgs fa, float *X, s
 }
 
 // Table entries from the network outputs (value, then one hedge ratio per
-// underlying) of the rows above, four floats per node (d used); the last
-// row's ratios are delta0.
+// underlying) of the rows above, the ratios of node r at record r (slots
+// 0 .. d - 1); the last row's ratios are delta0.
 __global__ void cv_scatter_kernel(const float *Y, int out_w, size_t rows, int d, float *tables,
                                   float *delta0) {
   const size_t r = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
   if (r >= rows) return;
   for (int i = 0; i < d; ++i) {
     const float v = Y[r * out_w + 1 + i];
-    if (r + 1 < rows) tables[r * 4 + i] = v;
+    if (r + 1 < rows) tables[r * kCvRecord + i] = v;
     else delta0[i] = v;
   }
+}
+
+// The slopes of every node record from its neighbours' ratios along each
+// grid axis: central differences (Delta(a + e_j) - Delta(a - e_j)) / 2, one-
+// sided (a difference of 1) on the grid's faces; slots beyond d zeroed.
+// Reads slots 0 .. d - 1 and writes the others, in place.
+__global__ void cv_slopes_kernel(float *tables, size_t records, int nodes, int G, int d) {
+  const size_t r = blockIdx.x * size_t(blockDim.x) + threadIdx.x;
+  if (r >= records) return;
+  const size_t base = r - r % size_t(nodes);
+  const int node = int(r % size_t(nodes));
+  float *rec = tables + r * kCvRecord;
+  for (int i = d; i < 3; ++i) rec[i] = 0.f;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      float v = 0.f;
+      if (i < d && j < d) {
+        int stride = 1;
+        for (int ax = d - 1; ax > j; --ax) stride *= G;
+        const int a = (node / stride) % G;
+        const int fwd = a < G - 1 ? node + stride : node, bwd = a > 0 ? node - stride : node;
+        const float df = tables[(base + size_t(fwd)) * kCvRecord + i] - tables[(base + size_t(bwd)) * kCvRecord + i];
+        v = (a == 0 || a == G - 1) ? df : 0.5f * df;
+      }
+      rec[3 + 3 * i + j] = v;
+    }
 }
 
 template <typename K>
@@ -136,6 +162,12 @@ cudaError_t launch_cv_features(const CvArgs &c, const CvFeatureArgs &fa, float *
 cudaError_t launch_cv_scatter(const float *Y, int out_w, size_t rows, int d, float *tables, float *delta0,
                               cudaStream_t s) {
   cv_scatter_kernel<<<unsigned((rows + 127) / 128), 128, 0, s>>>(Y, out_w, rows, d, tables, delta0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cv_slopes(float *tables, size_t records, int nodes, int G, int d, cudaStream_t s) {
+  if (records == 0) return cudaSuccess;
+  cv_slopes_kernel<<<unsigned((records + 127) / 128), 128, 0, s>>>(tables, records, nodes, G, d);
   return cudaGetLastError();
 }
 

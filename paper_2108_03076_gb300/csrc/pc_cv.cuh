@@ -26,70 +26,49 @@
 
 namespace pc {
 
-// Multilinear interpolation of the d hedge ratios at ln S (given as
-// l2 = log2 S: the axis coordinate is u = l2 ln2 / h - lo / h), and with
-// SLOPES the interpolant's derivatives s[i][j] = d Delta_i / d u_j on the
-// cell.  The 2^d corner values are reduced one axis at a time, last axis
-// first: a pair (lo, hi) along the axis becomes lo + f (hi - lo), its
-// difference hi - lo is the slope along that axis there, and slopes along
-// axes already reduced are interpolated like the values.  Same interpolant
-// as the sum over corners of the products of (f or 1 - f), in about a third
-// of the arithmetic.
+// Hedge ratios at ln S (given as l2 = log2 S: the axis coordinate is
+// u = l2 ln2 / h - lo / h, clamped to the grid) from the nearest table node
+// a = floor(u + 1/2): its ratios plus the first-order step along its slopes,
+// Delta_i = Delta_i(a) + sum_j s_ij(a) (u_j - a_j); with SLOPES also the
+// slopes s[i][j] = d Delta_i / d u_j (the node's).  A node is kCvRecord
+// floats (ratios, then s_ij at 3 + 3 i + j): one to three 16-byte loads.
 template <int D, bool SLOPES>
 __device__ __forceinline__ void table_delta(const CvArgs &c, int k, int ki, const float (&l2)[D],
                                             float (&delta)[D], float (&s)[D][D]) {
-  const float4 *tab = reinterpret_cast<const float4 *>(c.tables) + (size_t(k - 1) * 2 + ki) * size_t(c.nodes);
-  constexpr int NC = 1 << D;
-  int a[D];
-  float f[D];
+  const float4 *tab = reinterpret_cast<const float4 *>(c.tables) +
+                      (size_t(k - 1) * 2 + ki) * size_t(c.nodes) * (kCvRecord / 4);
   const int G = c.grid;
+  int node = 0;
+  float f[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     float u = fmaf(l2[i], c.ua[k - 1][i], -c.ub[k - 1][i]);
     u = fminf(fmaxf(u, 0.f), float(G - 1));
-    int ai = int(floorf(u));
-    ai = ai < G - 2 ? ai : G - 2;
-    a[i] = ai;
-    f[i] = u - float(ai);
+    const float a = floorf(u + 0.5f);
+    f[i] = u - a;
+    node = node * G + int(a);
   }
-  int base = 0;
+  constexpr int NV = D == 1 ? 1 : D == 2 ? 2 : 3;  // float4s holding slots 0 .. 3 + 3 (D - 1) + D - 1
+  float r[4 * NV];
+  const float4 *rec = tab + size_t(node) * (kCvRecord / 4);
 #pragma unroll
-  for (int ax = 0; ax < D; ++ax) base = base * G + a[ax];
-  // corner c: bit (D - 1 - ax) selects a[ax] + 1 on axis ax
-  float v[NC][D];
-#pragma unroll
-  for (int cn = 0; cn < NC; ++cn) {
-    int off = 0;
-#pragma unroll
-    for (int ax = 0; ax < D; ++ax) off = off * G + ((cn >> (D - 1 - ax)) & 1);
-    const float4 v4 = __ldg(tab + base + off);  // one 16-byte load per corner
-    const float w3[3] = {v4.x, v4.y, v4.z};
-#pragma unroll
-    for (int i = 0; i < D; ++i) v[cn][i] = w3[i];
-  }
-  float sj[D][NC / 2][D];
-#pragma unroll
-  for (int ax = D - 1; ax >= 0; --ax) {
-#pragma unroll
-    for (int cn = 0; cn < (1 << ax); ++cn) {
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        const float lo = v[2 * cn][i], dd = v[2 * cn + 1][i] - lo;
-        if (SLOPES) {
-#pragma unroll
-          for (int j = ax + 1; j < D; ++j)
-            sj[j][cn][i] = fmaf(f[ax], sj[j][2 * cn + 1][i] - sj[j][2 * cn][i], sj[j][2 * cn][i]);
-          sj[ax][cn][i] = dd;
-        }
-        v[cn][i] = fmaf(f[ax], dd, lo);
-      }
-    }
+  for (int v = 0; v < NV; ++v) {
+    const float4 x = __ldg(rec + v);
+    r[4 * v] = x.x;
+    r[4 * v + 1] = x.y;
+    r[4 * v + 2] = x.z;
+    r[4 * v + 3] = x.w;
   }
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    delta[i] = v[0][i];
+    float di = r[i];
 #pragma unroll
-    for (int j = 0; j < D; ++j) s[i][j] = SLOPES ? sj[j][0][i] : 0.f;
+    for (int jj = 0; jj < D; ++jj) {
+      const float sij = r[3 + 3 * i + jj];
+      di = fmaf(sij, f[jj], di);
+      if (SLOPES) s[i][jj] = sij;
+    }
+    delta[i] = di;
   }
 }
 

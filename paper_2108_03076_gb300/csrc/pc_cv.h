@@ -38,5 +38,8 @@ cudaError_t launch_cv_features(const CvArgs &c, const CvFeatureArgs &fa, float *
                                cudaStream_t s);
 cudaError_t launch_cv_scatter(const float *Y, int out_w, size_t rows, int d, float *tables, float *delta0,
                               cudaStream_t s);
+// The node records' slopes from their ratios (after the scatter or the fused
+// build): records = (n - 1) * 2 * nodes.
+cudaError_t launch_cv_slopes(float *tables, size_t records, int nodes, int G, int d, cudaStream_t s);
 
 }  // namespace pc

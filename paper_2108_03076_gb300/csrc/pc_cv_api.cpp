@@ -121,8 +121,8 @@ pc_status cv_launch(const pc_model *m, const pc_contract *k, const pc_cv_desc *c
     const bool win_regs = lay.win == 1;
     cudaKernel_t jk = nullptr;
     // register bound: 5 resident blocks by default (measured at 2^22 paths
-    // of the autocall: 3 / 4 / 5 / 6 blocks 0.522 / 0.461 / 0.439 / 0.479 ms
-    // first order, 0.610 / 0.539 / 0.524 / 0.648 ms with the second-order term)
+    // of the autocall: 4 / 5 / 6 blocks 0.428 / 0.396 / 0.392 ms first
+    // order, 0.490 / 0.466 / 0.552 ms with the second-order term)
     s = jit_kernel(k, m->H.d, kJitCv + cv_mode(d_xm != nullptr, ca) + (win_regs ? kCvWinRegs : 0), kBlock, jk,
                    ctx->cv_min_blocks > 0 ? ctx->cv_min_blocks : kJitCvMinBlocks);
     if (s != PC_OK) return s;
@@ -205,7 +205,7 @@ pc_status pc_cv_grid(const pc_model *m, int32_t grid, float width_sd, pc_cv_desc
 pc_status pc_cv_table_size(const pc_cv_desc *c, size_t *floats) {
   if (!c || !floats) return fail(PC_EINVAL, "null argument");
   if (c->d < 1 || c->d > 3 || c->n < 1 || c->grid < 2) return fail(PC_EINVAL, "bad description");
-  *floats = size_t(std::max(0, c->n - 1)) * 2 * nodes_of(c) * 4;
+  *floats = size_t(std::max(0, c->n - 1)) * 2 * nodes_of(c) * kCvRecord;
   return PC_OK;
 }
 
@@ -231,7 +231,7 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
   fa.rho = H.d > 1 ? float(H.corr[1]) : 0.f;
   fa.r = float(H.r);
   for (int o = 0; o <= H.n; ++o) fa.tau[o] = H.tau[o];
-  const size_t rows = need / 4 + 1;
+  const size_t rows = need / kCvRecord + 1;
   pc_ctx *ctx = m->ctx;
   CU(cudaSetDevice(ctx->device), "cudaSetDevice");
   float *buf = mlp_scratch(net, rows * (kCvFeatures + kCvOutputs) + 64);
@@ -270,6 +270,7 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
           if (e == cudaSuccess) st = mlp_forward_on(net, X, rows, Y, cap);
           if (e == cudaSuccess && st == PC_OK) e = launch_cv_scatter(Y, kCvOutputs, rows, c->d, d_tables, d0, cap);
         }
+        if (e == cudaSuccess && st == PC_OK) e = launch_cv_slopes(d_tables, rows - 1, kc.nodes, c->grid, c->d, cap);
         if (e == cudaSuccess && st == PC_OK)
           e = cudaMemcpyAsync(pin, d0, 4 * sizeof(float), cudaMemcpyDeviceToHost, cap);
         if (e == cudaSuccess && st == PC_OK)
@@ -301,6 +302,7 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
   if (s == PC_OK) s = pc_mlp_forward(net, X, rows, Y);
   if (s == PC_OK) {
     e = launch_cv_scatter(Y, kCvOutputs, rows, c->d, d_tables, d0, ctx->stream);
+    if (e == cudaSuccess) e = launch_cv_slopes(d_tables, rows - 1, ca.nodes, c->grid, c->d, ctx->stream);
     if (e != cudaSuccess) s = cuda_fail(e, "table scatter");
   }
   float h0[4] = {0, 0, 0, 0};

@@ -10,9 +10,12 @@ constexpr int kCvMaxDates = 32;   // observation dates of the template
 constexpr int kCvMaxD = 3;        // underlyings
 constexpr int kCvFeatures = 16;   // network inputs
 constexpr int kCvOutputs = 5;     // network outputs: value, up to 4 hedge ratios
+// floats of a table node: hedge ratios 0..2, then the slopes d Delta_i / d u_j
+// at 3 + 3 i + j (u: the grid coordinate; zero beyond d)
+constexpr int kCvRecord = 12;
 
 struct CvArgs {
-  const float *tables;            // [(n-1) * 2][nodes][4] (d used), 16-byte aligned
+  const float *tables;            // [(n-1) * 2][nodes][kCvRecord], 16-byte aligned
   int32_t d, n, grid, nodes;      // nodes = grid^d
   float ref[kCvMaxD];
   float call_level, ki_level, coupon;

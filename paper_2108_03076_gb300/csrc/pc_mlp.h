@@ -83,7 +83,7 @@ cudaError_t launch_gemm_tc(GemmKind kind, int epi, const GemmArgs &g, const TcMa
 // shared memory, every layer's product runs on tcgen05 from there (weights
 // streamed by TMA, the accumulator in TMEM), the hidden activations return
 // to shared memory as the next layer's operand, and the last layer's hedge
-// ratios go to the tables (row r < rows - 1: tables[4 r + i]; the last row:
+// ratios go to the tables (row r < rows - 1: tables[12 r + i]; the last row:
 // delta0).  Networks of up to kCvNetMaxLayers layers, input and output
 // padded to 64, hidden widths multiples of 64 up to 256.
 constexpr int kCvNetMaxLayers = 4;

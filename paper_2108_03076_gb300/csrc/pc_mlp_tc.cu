@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (int i = 0; i < kCvMaxD; ++i) {
               if (i >= c.d) break;
               const float y = v[1 + i] + __ldg(t.bias[l] + 1 + i);
-              if (r + 1 < t.rows) t.tables[r * 4 + i] = y;
+              if (r + 1 < t.rows) t.tables[r * kCvRecord + i] = y;
               else t.delta0[i] = y;
             }
           }

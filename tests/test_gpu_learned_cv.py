@@ -16,6 +16,7 @@ from gpu_common import Engine, torch
 import paper_2108_03076_gb300 as pc
 import workloads as W
 from paper_2108_03076_gb300 import learned_cv as L
+from oracle import cv
 
 pytestmark = pytest.mark.gpu
 
@@ -100,10 +101,16 @@ def test_fused_table_build_matches_layer_products(eng, trained, grid):
     b = layered[:pc.pc_cv_table_size(desc2)].cpu().numpy().astype(np.float64)
     d_layered = [desc2.delta0[i] for i in range(3)]
     assert a.shape == b.shape and np.all(np.isfinite(a))
-    used = np.arange(a.size) % 4 < 3          # 16-byte node groups: 3 ratios + padding
+    used = np.arange(a.size) % 12 < 3         # node records: 3 ratios, then the slopes
     s = np.sqrt(np.mean(b[used] ** 2))
     assert s > 1e-3
     tol = 2 * 2.0 ** -8 * (np.abs(b[used]) + s)
     err = np.abs(a[used] - b[used])
     assert np.all(err <= tol), (err.max(), np.argmax(err - tol))
     assert np.allclose(d_fused, d_layered, rtol=0, atol=2 * 2.0 ** -8 * (np.abs(d_layered).max() + s))
+    # every record's slopes are the central differences of its neighbours'
+    # ratios (one-sided on the faces), as the oracle takes them
+    G = desc.grid
+    rec = a.reshape(desc.n - 1, 2, G ** 3, 12)
+    want = cv.node_records(rec[..., :3], G)
+    np.testing.assert_allclose(rec[..., 3:], want[..., 3:], rtol=0, atol=1e-6 * (1.0 + np.abs(rec[..., :3]).max()))
