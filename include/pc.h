@@ -620,6 +620,9 @@ typedef struct pc_cv_desc {
   float beta;                /* Y = X - beta M - beta2 M2 (pc_cv_grid: 1)    */
   float beta2;               /* (pc_cv_grid: 1)                              */
   int32_t use_gamma;         /* 1: include M2 (pc_cv_grid: 0)                */
+  int32_t delta0_on_device;  /* 1: the pricing reads delta0 from the device,
+                                the 4 floats after the tables (set by
+                                pc_cv_tables_async); 0: delta0 above      */
 } pc_cv_desc;
 
 /* Training labels of the learned control variate from the engine's prices
@@ -656,6 +659,15 @@ pc_status pc_cv_table_size(const pc_cv_desc *desc, size_t *floats);
  * Errors: PC_EINVAL (widths other than 16 in / 5 out, cap too small). */
 pc_status pc_cv_tables(pc_mlp *net, const pc_model *model, pc_cv_desc *desc, float *d_tables,
                        size_t cap_floats);
+/* pc_cv_tables without the wait: the build is enqueued on the context's
+ * stream and delta0 is written on the device, to the 4 floats after the
+ * tables (cap_floats >= pc_cv_table_size + 4), where pc_price_cv reads it:
+ * sets desc->delta0_on_device = 1 and zeroes desc->delta0.  A bounded wait
+ * that expires in the build is reported (PC_ETIMEOUT) by the next blocking
+ * call on the network (pc_cv_tables, pc_mlp_forward, pc_mlp_gradients,
+ * pc_mlp_train).  Errors: as pc_cv_tables. */
+pc_status pc_cv_tables_async(pc_mlp *net, const pc_model *model, pc_cv_desc *desc, float *d_tables,
+                             size_t cap_floats);
 /* Price with the control variate: out[0..3] (host) = price and standard
  * error of Y = X - beta M - beta2 M2 (betas from desc), then of X on the
  * same paths (pc_price's estimate with this seed).  d_tables: device

@@ -78,7 +78,7 @@ class CvDesc(C.Structure):
                 ("call_level", C.c_float), ("ki_level", C.c_float), ("coupon", C.c_float),
                 ("lo", (C.c_float * 3) * CV_MAX_DATES), ("h", (C.c_float * 3) * CV_MAX_DATES),
                 ("delta0", C.c_float * 3), ("beta", C.c_float), ("beta2", C.c_float),
-                ("use_gamma", C.c_int32)]
+                ("use_gamma", C.c_int32), ("delta0_on_device", C.c_int32)]
 
 
 class LaunchInfo(C.Structure):
@@ -156,6 +156,7 @@ _SIGS = {
     "pc_cv_grid": [VP, C.c_int32, C.c_float, C.POINTER(CvDesc)],
     "pc_cv_table_size": [C.POINTER(CvDesc), C.POINTER(SZ)],
     "pc_cv_tables": [VP, VP, C.POINTER(CvDesc), VP, SZ],
+    "pc_cv_tables_async": [VP, VP, C.POINTER(CvDesc), VP, SZ],
     "pc_price_cv": [VP, VP, C.POINTER(CvDesc), VP, U64, U64, PD],
     "pc_cv_beta": [VP, VP, C.POINTER(CvDesc), VP, U64, U64, PD],
     "pc_debug_cv_paths": [VP, VP, C.POINTER(CvDesc), VP, U64, U64, VP],
@@ -560,6 +561,12 @@ def pc_cv_table_size(desc: CvDesc) -> int:
 
 def pc_cv_tables(net: int, model: int, desc: CvDesc, d_tables: int, cap_floats: int) -> None:
     _check(lib().pc_cv_tables(VP(net), VP(model), C.byref(desc), VP(d_tables), int(cap_floats)))
+
+
+def pc_cv_tables_async(net: int, model: int, desc: CvDesc, d_tables: int, cap_floats: int) -> None:
+    """pc_cv_tables without the wait: delta0 stays on the device, after the
+    tables (cap_floats >= table size + 4)."""
+    _check(lib().pc_cv_tables_async(VP(net), VP(model), C.byref(desc), VP(d_tables), int(cap_floats)))
 
 
 def pc_price_cv(model: int, contract: int, desc: CvDesc, d_tables: int, n_paths: int, seed: int):

@@ -146,7 +146,7 @@ struct CvOnline {
       const bool al = q ? alive[1] : alive[0];
       if (k == 0) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) delta[i] = c.delta0[i];
+        for (int i = 0; i < D; ++i) delta[i] = c.delta0_dev ? __ldg(c.delta0_dev + i) : c.delta0[i];
       } else {
         float l2[D];
 #pragma unroll

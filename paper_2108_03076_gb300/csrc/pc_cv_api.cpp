@@ -49,6 +49,8 @@ CvArgs device_args(const pc_cv_desc *c, const float *tables, const ModelHost &H,
     a.ref[i] = c->ref[i];
     a.delta0[i] = c->delta0[i];
   }
+  if (c->delta0_on_device && tables)  // after the tables (pc_cv_tables_async)
+    a.delta0_dev = tables + size_t(std::max(0, c->n - 1)) * 2 * nodes_of(c) * kCvRecord;
   a.call_level = c->call_level;
   a.ki_level = c->ki_level;
   a.coupon = c->coupon;
@@ -209,7 +211,11 @@ pc_status pc_cv_table_size(const pc_cv_desc *c, size_t *floats) {
   return PC_OK;
 }
 
-pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_tables, size_t cap) {
+}  // extern "C"
+
+namespace {
+// The table build (pc_cv_tables; with `async`, pc_cv_tables_async).
+pc_status cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_tables, size_t cap, bool async) {
   pc_status s = check_desc(m, c);
   if (s != PC_OK) return s;
   pc_mlp_info info;
@@ -219,7 +225,7 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
     return fail(PC_EINVAL, "network must map 16 inputs to 5 outputs");
   size_t need = 0;
   pc_cv_table_size(c, &need);
-  if (cap < need || (need && !d_tables)) return fail(PC_EINVAL, "table capacity too small");
+  if (cap < need + (async ? 4 : 0) || ((need || async) && !d_tables)) return fail(PC_EINVAL, "table capacity too small");
   if (reinterpret_cast<uintptr_t>(d_tables) & 15u) return fail(PC_EINVAL, "tables must be 16-byte aligned");
   const ModelHost &H = m->H;
   CvFeatureArgs fa;
@@ -236,7 +242,7 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
   CU(cudaSetDevice(ctx->device), "cudaSetDevice");
   float *buf = mlp_scratch(net, rows * (kCvFeatures + kCvOutputs) + 64);
   if (!buf) return fail(PC_ENOMEM, "table scratch");
-  float *X = buf, *Y = buf + rows * kCvFeatures, *d0 = Y + rows * kCvOutputs;
+  float *X = buf, *Y = buf + rows * kCvFeatures, *d0 = async ? d_tables + need : Y + rows * kCvOutputs;
   const CvArgs ca = device_args(c, nullptr, m->H, false);
   float *pin = mlp_pinned(net);
   if (pin) {
@@ -249,8 +255,9 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
     kc.beta = kc.beta2 = 0.f;
     kc.use_gamma = kc.pilot = 0;
     for (float &v : kc.delta0) v = 0.f;
-    std::vector<uint8_t> key(sizeof(kc) + sizeof(fa) + 3 * sizeof(uint64_t));
-    const uint64_t extra[3] = {reinterpret_cast<uint64_t>(d_tables), reinterpret_cast<uint64_t>(buf), rows};
+    std::vector<uint8_t> key(sizeof(kc) + sizeof(fa) + 4 * sizeof(uint64_t));
+    const uint64_t extra[4] = {reinterpret_cast<uint64_t>(d_tables), reinterpret_cast<uint64_t>(buf), rows,
+                               async ? 1u : 0u};
     std::memcpy(key.data(), &kc, sizeof(kc));
     std::memcpy(key.data() + sizeof(ca), &fa, sizeof(fa));
     std::memcpy(key.data() + sizeof(ca) + sizeof(fa), extra, sizeof(extra));
@@ -271,9 +278,9 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
           if (e == cudaSuccess && st == PC_OK) e = launch_cv_scatter(Y, kCvOutputs, rows, c->d, d_tables, d0, cap);
         }
         if (e == cudaSuccess && st == PC_OK) e = launch_cv_slopes(d_tables, rows - 1, kc.nodes, c->grid, c->d, cap);
-        if (e == cudaSuccess && st == PC_OK)
+        if (e == cudaSuccess && st == PC_OK && !async)
           e = cudaMemcpyAsync(pin, d0, 4 * sizeof(float), cudaMemcpyDeviceToHost, cap);
-        if (e == cudaSuccess && st == PC_OK)
+        if (e == cudaSuccess && st == PC_OK && !async)
           e = cudaMemcpyAsync(pin + 4, mlp_status_word(net), sizeof(int32_t), cudaMemcpyDeviceToHost, cap);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
@@ -289,12 +296,18 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
       }
     }
     CU(cudaGraphLaunch(*slot, ctx->stream), "table build");
+    if (async) {
+      c->delta0_on_device = 1;
+      for (float &v : c->delta0) v = 0.f;
+      return PC_OK;
+    }
     s = wait_stream(ctx);
     if (s != PC_OK) return s;
     int32_t status = 0;
     std::memcpy(&status, pin + 4, sizeof(status));
     if (status != 0) return mlp_status(net);  // clears the word, reports PC_ETIMEOUT
     for (int i = 0; i < 3; ++i) c->delta0[i] = i < c->d ? pin[i] : 0.f;
+    c->delta0_on_device = 0;
     return PC_OK;
   }
   cudaError_t e = launch_cv_features(ca, fa, X, rows, ctx->stream);
@@ -306,14 +319,26 @@ pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_t
     if (e != cudaSuccess) s = cuda_fail(e, "table scatter");
   }
   float h0[4] = {0, 0, 0, 0};
-  if (s == PC_OK) {
+  if (s == PC_OK && !async) {
     e = cudaMemcpyAsync(h0, d0, 4 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) s = cuda_fail(e, "delta0 copy");
   }
   if (s == PC_OK) s = mlp_status(net);
   if (s != PC_OK) return s;
   for (int i = 0; i < 3; ++i) c->delta0[i] = i < c->d ? h0[i] : 0.f;
+  c->delta0_on_device = async ? 1 : 0;
   return PC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+pc_status pc_cv_tables(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_tables, size_t cap) {
+  return cv_tables(net, m, c, d_tables, cap, false);
+}
+
+pc_status pc_cv_tables_async(pc_mlp *net, const pc_model *m, pc_cv_desc *c, float *d_tables, size_t cap) {
+  return cv_tables(net, m, c, d_tables, cap, true);
 }
 
 // Sums of the launch (width doubles) to the host, with the status check.

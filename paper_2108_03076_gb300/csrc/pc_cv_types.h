@@ -27,6 +27,7 @@ struct CvArgs {
   float cq[kCvMaxDates][kCvMaxD * kCvMaxD];
   float inv_ref[kCvMaxD];
   float delta0[kCvMaxD];
+  const float *delta0_dev;         // non-null: delta0 read from the device instead
   float beta, beta2;              // Y = X - beta M - beta2 M2
   int32_t use_gamma;              // add the second-order term M2
   int32_t pilot;                  // 1: sums of X, M, M2 and their products (8), else X, X^2, Y, Y^2

@@ -27,8 +27,8 @@ from typing import List, Sequence, Tuple
 import numpy as np
 
 from . import (pc_assemble, pc_batch_create, pc_batch_destroy, pc_batch_launch, pc_batch_results,
-               pc_contract_destroy, pc_cv_beta, pc_cv_grid, pc_cv_labels, pc_cv_table_size, pc_cv_tables, pc_load_payoff,
-               pc_mlp_create, pc_mlp_destroy, pc_mlp_forward, pc_mlp_train, pc_model_create,
+               pc_contract_destroy, pc_cv_beta, pc_cv_grid, pc_cv_labels, pc_cv_table_size, pc_cv_tables,
+               pc_cv_tables_async, pc_load_payoff, pc_mlp_create, pc_mlp_destroy, pc_mlp_forward, pc_mlp_train, pc_model_create,
                pc_model_destroy, pc_price_cv)
 
 WIDTHS = (16, 256, 256, 256, 5)
@@ -214,17 +214,20 @@ class LearnedCV:
         return dy.cpu().numpy()
 
     def tables(self, model: int, grid: int = 12, width_sd: float = 4.5, call_level: float = 1.0,
-               ki_level: float = 0.6, coupon: float = 0.05, gamma: bool = True, out=None):
+               ki_level: float = 0.6, coupon: float = 0.05, gamma: bool = True, out=None,
+               asynchronous: bool = False):
         """(description, device tables) for a model of the template, with the
         calibrated betas (and the second-order term when ``gamma``).  ``out``:
         a float32 CUDA tensor to fill (large enough), else a new one; rebuilding
-        into the same buffer replays the build's captured graph."""
+        into the same buffer replays the build's captured graph.
+        ``asynchronous``: enqueue the build without waiting; delta0 stays on
+        the device after the tables (pc_cv_tables_async)."""
         import torch
         desc = pc_cv_grid(model, grid, width_sd, (1.0, 1.0, 1.0), call_level, ki_level, coupon)
         n = pc_cv_table_size(desc)
-        dt = out if out is not None and out.numel() >= max(n, 1) else torch.empty(max(n, 1), dtype=torch.float32,
-                                                                                 device="cuda")
-        pc_cv_tables(self.net, model, desc, dt.data_ptr(), n)
+        dt = out if out is not None and out.numel() >= n + 4 else torch.empty(n + 4, dtype=torch.float32,
+                                                                             device="cuda")
+        (pc_cv_tables_async if asynchronous else pc_cv_tables)(self.net, model, desc, dt.data_ptr(), n + 4)
         desc.use_gamma = 1 if gamma else 0
         desc.beta, desc.beta2 = self.betas if gamma else (self.betas_first_order, 0.0)
         return desc, dt

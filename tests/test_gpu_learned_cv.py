@@ -114,3 +114,25 @@ def test_fused_table_build_matches_layer_products(eng, trained, grid):
     rec = a.reshape(desc.n - 1, 2, G ** 3, 12)
     want = cv.node_records(rec[..., :3], G)
     np.testing.assert_allclose(rec[..., 3:], want[..., 3:], rtol=0, atol=1e-6 * (1.0 + np.abs(rec[..., :3]).max()))
+
+
+def test_asynchronous_table_build_prices_the_same(eng, trained):
+    """pc_cv_tables_async: the same tables bit for bit, delta0 left on the
+    device after them (desc.delta0_on_device), and the same control-variate
+    price and standard error bit for bit as with the blocking build."""
+    w = W.worst_of_autocall()
+    m = eng.model(w.market)
+    k = eng.contract(w.il_text, w.tparams)
+    d_sync, t_sync = trained.tables(m)
+    d_async, t_async = trained.tables(m, asynchronous=True)
+    assert d_sync.delta0_on_device == 0 and d_async.delta0_on_device == 1
+    assert list(d_async.delta0) == [0.0, 0.0, 0.0]
+    n = pc.pc_cv_table_size(d_sync)
+    a, b = t_sync.cpu().numpy(), t_async.cpu().numpy()
+    np.testing.assert_array_equal(b[:n].view(np.uint32), a[:n].view(np.uint32))
+    np.testing.assert_array_equal(b[n:n + 3], np.array(list(d_sync.delta0), np.float32))
+    r_sync = pc.pc_price_cv(m, k, d_sync, t_sync.data_ptr(), 1 << 18, 0x5EED0404)
+    r_async = pc.pc_price_cv(m, k, d_async, t_async.data_ptr(), 1 << 18, 0x5EED0404)
+    assert r_sync == r_async
+    with pytest.raises(pc.PcError):  # no room for delta0 after the tables
+        pc.pc_cv_tables_async(trained.net, m, d_async, t_async.data_ptr(), n)
