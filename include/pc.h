@@ -212,6 +212,17 @@ pc_status pc_load_payoff(pc_ctx *ctx, const uint32_t *bytecode, size_t n_words,
                          const int32_t *template_params, size_t n_params,
                          int32_t p1, int32_t p2, pc_contract **out);
 pc_status pc_contract_destroy(pc_contract *contract);
+/* Load n programs in one call (a portfolio): program i is words
+ * [word_off[i], word_off[i+1]), real literals [const_off[i], const_off[i+1])
+ * and template parameters [param_off[i], param_off[i+1]) of the
+ * concatenated arrays (offset arrays of n + 1 entries, non-decreasing; a
+ * NULL array with all-zero extents may be passed for consts and params),
+ * each loaded as pc_load_payoff with the view (p1, p2) into out[i].  On an
+ * error no contract is left loaded (out untouched) and the message names
+ * the program.  Errors: as pc_load_payoff. */
+pc_status pc_load_payoffs(pc_ctx *ctx, size_t n, const uint32_t *words, const size_t *word_off,
+                          const double *consts, const size_t *const_off, const int32_t *params,
+                          const size_t *param_off, int32_t p1, int32_t p2, pc_contract **out);
 
 /* Host-only: the checks of pc_load_payoff without a context or device.
  * Fills *info (may be NULL).  Errors as pc_load_payoff. */

@@ -110,6 +110,8 @@ _SIGS = {
     "pc_model_destroy": [VP],
     "pc_model_query": [VP, C.POINTER(ModelInfo)],
     "pc_load_payoff": [VP, PU32, SZ, PD, SZ, PI32, SZ, I32, I32, C.POINTER(VP)],
+    "pc_load_payoffs": [VP, SZ, PU32, C.POINTER(SZ), PD, C.POINTER(SZ), PI32, C.POINTER(SZ), I32, I32,
+                        C.POINTER(VP)],
     "pc_contract_destroy": [VP],
     "pc_verify_payoff": [PU32, SZ, PD, SZ, PI32, SZ, C.POINTER(ProgramInfo)],
     "pc_assemble": [C.c_char_p, PU32, SZ, C.POINTER(SZ), PD, SZ, C.POINTER(SZ), C.c_char_p, SZ],
@@ -300,6 +302,35 @@ def pc_load_payoff(ctx: int, words, consts, tparams=(), p1: int = 0, p2: int = 1
     _check(lib().pc_load_payoff(VP(ctx), _ptr(w, C.c_uint32), w.size, _ptr(k, C.c_double), k.size,
                                 _ptr(t, C.c_int32), t.size, int(p1), int(p2), C.byref(h)))
     return h.value
+
+
+class ProgramSet:
+    """Programs concatenated once for pc_load_payoffs: a list of
+    (words, consts, tparams)."""
+
+    def __init__(self, programs):
+        progs = list(programs)
+        self.n = len(progs)
+        parts = [(_arr(w, np.uint32), _arr(k, np.float64), _arr(t, np.int32)) for w, k, t in progs]
+        off = lambda xs: np.concatenate([[0], np.cumsum([x.size for x in xs])]).astype(np.uintp)  # noqa: E731
+        self.words = np.ascontiguousarray(np.concatenate([p[0] for p in parts]) if parts else np.zeros(0, np.uint32))
+        self.consts = np.ascontiguousarray(np.concatenate([p[1] for p in parts]) if parts else np.zeros(0))
+        self.params = np.ascontiguousarray(np.concatenate([p[2] for p in parts]) if parts else np.zeros(0, np.int32))
+        self.word_off = off([p[0] for p in parts])
+        self.const_off = off([p[1] for p in parts])
+        self.param_off = off([p[2] for p in parts])
+
+
+def pc_load_payoffs(ctx: int, programs, p1: int = 0, p2: int = 1):
+    """Load many programs in one call (a ProgramSet, or a list of
+    (words, consts, tparams)); returns the contract handles."""
+    ps = programs if isinstance(programs, ProgramSet) else ProgramSet(programs)
+    out = (VP * max(ps.n, 1))()
+    szp = lambda a: a.ctypes.data_as(C.POINTER(SZ))  # noqa: E731
+    _check(lib().pc_load_payoffs(VP(ctx), ps.n, _ptr(ps.words, C.c_uint32), szp(ps.word_off),
+                                 _ptr(ps.consts, C.c_double), szp(ps.const_off), _ptr(ps.params, C.c_int32),
+                                 szp(ps.param_off), int(p1), int(p2), out))
+    return [out[i] for i in range(ps.n)]
 
 
 def pc_contract_destroy(contract: int) -> None:

@@ -252,6 +252,40 @@ pc_status launch(pc_batch *B) {
   return PC_OK;
 }
 
+// The plan's work without a graph (one-shot pricing): the same group
+// launches as the captured replay, forked onto the context's cached
+// streams and joined back into its stream.
+pc_status launch_direct(pc_batch *B) {
+  pc_ctx *c = B->ctx;
+  CU(cudaSetDevice(c->device), "cudaSetDevice");
+  if (!c->batch_fork) CU(cudaEventCreateWithFlags(&c->batch_fork, cudaEventDisableTiming), "event");
+  while (c->batch_aux.size() < B->groups.size()) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
+    c->batch_aux.push_back(st);
+    CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    c->batch_join.push_back(ev);
+  }
+  CU(cudaMemsetAsync(B->d_zero, 0, B->zero_bytes, c->stream), "counters");
+  CU(cudaEventRecord(c->batch_fork, c->stream), "fork");
+  for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+    const Group &g = B->groups[gi];
+    if (g.n_units == 0) continue;
+    BatchArgs a;
+    a.items = B->d_items;
+    a.units = B->d_units + g.u0;
+    a.n_units = g.n_units;
+    a.slot_bytes = uint32_t(g.slot);
+    a.counter = reinterpret_cast<unsigned long long *>(B->d_zero) + gi;
+    CU(cudaStreamWaitEvent(c->batch_aux[gi], c->batch_fork, 0), "fork wait");
+    CU(launch_batch(a, g.d, g.grid, g.block, g.smem, c->batch_aux[gi]), "batch kernel");
+    CU(cudaEventRecord(c->batch_join[gi], c->batch_aux[gi]), "join");
+    CU(cudaStreamWaitEvent(c->stream, c->batch_join[gi], 0), "join wait");
+  }
+  return PC_OK;
+}
+
 void release(pc_batch *B) {
   if (!B) return;
   destroy_graph(B);
@@ -265,7 +299,7 @@ void release(pc_batch *B) {
 
 pc_status create(size_t n, const pc_model *const *models, const pc_contract *const *contracts,
                  const uint64_t *n_paths, uint64_t seed, const pc_batch_config *config,
-                 pc_batch *B) {
+                 pc_batch *B, bool graph = true) {
   if (n == 0) return fail(PC_EINVAL, "empty batch");
   if (!models || !contracts || !n_paths) return fail(PC_EINVAL, "null argument");
   if (n > 0xfffffffful) return fail(PC_ELIMIT, "more than 2^32 - 1 contracts");
@@ -326,8 +360,10 @@ pc_status create(size_t n, const pc_model *const *models, const pc_contract *con
   }
   CU(cudaMemcpy(B->d_items, B->items.data(), n * sizeof(PriceArgs), cudaMemcpyHostToDevice), "items");
   CU(cudaMemset(B->d_out, 0, n * 4 * sizeof(double)), "outputs");
-  CU(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking), "capture stream");
-  CU(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming), "event");
+  if (graph) {
+    CU(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking), "capture stream");
+    CU(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming), "event");
+  }
   build_groups(B);
   if (B->groups.size() > size_t(kMaxGroups)) return fail(PC_ELIMIT, "too many batch groups");
   // default: the tuner's pick on the 1024-contract synthetic portfolio
@@ -335,7 +371,7 @@ pc_status create(size_t n, const pc_model *const *models, const pc_contract *con
   if (config) cfg = *config;
   pc_status s = configure(B, cfg);
   if (s != PC_OK) return s;
-  return capture(B);
+  return graph ? capture(B) : PC_OK;
 }
 
 // Device milliseconds of `reps` replays (after one untimed replay).
@@ -500,10 +536,11 @@ pc_status pc_price_batch(size_t n, const pc_model *const *models, const pc_contr
                          double *out_stderr) {
   if (n == 0) return PC_OK;
   if (!out_price || !out_stderr) return fail(PC_EINVAL, "null argument");
-  pc_batch *B = nullptr;
-  pc_status s = pc_batch_create(n, models, contracts, n_paths, seed, nullptr, &B);
-  if (s != PC_OK) return s;
-  s = launch(B);
+  // a plan without a graph: its groups launched once, straight away
+  pc_batch *B = new (std::nothrow) pc_batch;
+  if (!B) return fail(PC_ENOMEM, "batch plan");
+  pc_status s = create(n, models, contracts, n_paths, seed, nullptr, B, false);
+  if (s == PC_OK) s = launch_direct(B);
   if (s == PC_OK) s = pc_batch_results(B, out_price, out_stderr, nullptr);
   pc_batch_destroy(B);
   return s;

@@ -641,6 +641,9 @@ pc_status pc_destroy(pc_ctx *c) {
   if (c->d_res) cudaFree(c->d_res);
   for (cudaEvent_t ev : c->stage_ev)
     if (ev) cudaEventDestroy(ev);
+  for (cudaStream_t st : c->batch_aux) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : c->batch_join) cudaEventDestroy(ev);
+  if (c->batch_fork) cudaEventDestroy(c->batch_fork);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->h_res) cudaFreeHost(c->h_res);
   if (c->pool) cudaMemPoolDestroy(c->pool);
@@ -753,6 +756,34 @@ pc_status pc_verify_payoff(const uint32_t *bytecode, size_t n_words, const doubl
   } catch (...) {
     return fail(PC_EINVAL, "unexpected error in pc_verify_payoff");
   }
+}
+
+pc_status pc_load_payoffs(pc_ctx *c, size_t n, const uint32_t *words, const size_t *word_off,
+                          const double *consts, const size_t *const_off, const int32_t *params,
+                          const size_t *param_off, int32_t p1, int32_t p2, pc_contract **out) {
+  if (!c || !out || !word_off || !const_off || !param_off || (n && !words)) return fail(PC_EINVAL, "null argument");
+  for (size_t i = 0; i < n; ++i)
+    if (word_off[i + 1] < word_off[i] || const_off[i + 1] < const_off[i] || param_off[i + 1] < param_off[i])
+      return fail(PC_EINVAL, "offsets must be non-decreasing");
+  if ((const_off[n] > const_off[0] && !consts) || (param_off[n] > param_off[0] && !params))
+    return fail(PC_EINVAL, "null literals or parameters");
+  std::vector<pc_contract *> done;
+  done.reserve(n);
+  for (size_t i = 0; i < n; ++i) {
+    pc_contract *k = nullptr;
+    const pc_status s = pc_load_payoff(c, words + word_off[i], word_off[i + 1] - word_off[i],
+                                       consts ? consts + const_off[i] : nullptr, const_off[i + 1] - const_off[i],
+                                       params ? params + param_off[i] : nullptr, param_off[i + 1] - param_off[i],
+                                       p1, p2, &k);
+    if (s != PC_OK) {
+      const std::string msg = "program " + std::to_string(i) + ": " + pc_last_error(nullptr);
+      for (pc_contract *d : done) pc_contract_destroy(d);
+      return fail(s, msg);
+    }
+    done.push_back(k);
+  }
+  for (size_t i = 0; i < n; ++i) out[i] = done[i];
+  return PC_OK;
 }
 
 pc_status pc_load_payoff(pc_ctx *c, const uint32_t *bytecode, size_t n_words, const double *consts,

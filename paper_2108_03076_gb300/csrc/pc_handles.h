@@ -62,6 +62,11 @@ struct pc_ctx {
   size_t gwin_cap = 0;           // float2 slots
   int32_t window_mode = 0;       // PC_WINDOW_AUTO / _SHARED / _HBM
   int32_t jit = 0;               // 1: price with run-time specialised kernels
+  // streams and events of one-shot portfolio launches (pc_price_batch),
+  // created once per context
+  std::vector<cudaStream_t> batch_aux;
+  std::vector<cudaEvent_t> batch_join;
+  cudaEvent_t batch_fork = nullptr;
   int32_t cv_min_blocks = 0;     // launch bound of the specialised control-variate kernel (0: its default)
   int32_t jit_pairs = 0;         // path pairs a lane of a specialised kernel with a one-date window (0 automatic, 1 or 2)
   std::mutex jit_mu;

@@ -200,3 +200,34 @@ def test_argument_errors(eng, mixed):
         assert np.all(np.isfinite(p))
     finally:
         pc.pc_batch_destroy(plan)
+
+
+def test_programs_loaded_in_one_call_price_the_same(eng, mixed):
+    """pc_load_payoffs: the test programs and 40 portfolio contracts loaded
+    in one call price bit for bit as the ones loaded one at a time (one-shot
+    pc_price_batch, no graph); a bad program names its index and leaves
+    nothing loaded."""
+    models, contracts, n_paths = mixed
+    progs = []
+    for name in sorted(CASES):
+        text, tp, spec, _ = CASES[name]
+        w, k = pc.pc_assemble(text)
+        progs.append((w, k, tp))
+    for it in W.portfolio()[:40]:
+        w, k = pc.pc_assemble(it.il_text)
+        progs.append((w, k, it.tparams))
+    ks = pc.pc_load_payoffs(eng.ctx, progs)
+    try:
+        assert len(ks) == len(contracts)
+        p1, s1 = pc.pc_price_batch(models, ks, n_paths, SEED)
+        p0, s0 = pc.pc_price_batch(models, contracts, n_paths, SEED)
+        np.testing.assert_array_equal(p1, p0)
+        np.testing.assert_array_equal(s1, s0)
+    finally:
+        for k in ks:
+            pc.pc_contract_destroy(k)
+    bad = list(progs[:5])
+    bad[3] = (np.asarray(bad[3][0], np.uint32)[:-1], bad[3][1], bad[3][2])  # truncated bytecode
+    with pytest.raises(pc.PcError) as e:
+        pc.pc_load_payoffs(eng.ctx, bad)
+    assert "program 3" in str(e.value)
