@@ -75,6 +75,26 @@ def test_per_path_sensitivities_match_oracle(eng, name):
         assert sums[4] == pytest.approx(dv.sum(), rel=1e-9, abs=1e-9)
 
 
+@pytest.mark.parametrize("name", GREEK_CASES)
+def test_per_path_tangents_match_oracle_adjoint(eng, name):
+    """The tangent kernel's per-path delta and vega against the oracle's
+    reverse-mode derivatives (the chain rule, no difference step): the
+    price parity's bar, every path within 5e-5 relative except those whose
+    decisions were within a tie, at most max(2, 1e-4 N) of them."""
+    from test_gpu_adjoint import check_derivative
+    text, tp, spec, notional = CASES[name]
+    n, seed = 2048 + 11, 0x7777 + len(name)
+    m, k = eng.model(spec), eng.contract(text, tp)
+    prog = il_text.parse(text)
+    x, rS, rv = pathwise.adjoint(prog, market(spec), tparam_env(tp), 0, 1, n, seed)
+    _, _, _, marg = pathwise.pathwise(prog, market(spec), tparam_env(tp), 0, 1, n, seed, 0)
+    for label in range(spec.d):
+        v, dS, dv, _ = greek_paths(eng, m, k, n, seed, label)
+        compare(v, x, marg, notional, (name, label, "value"))
+        check_derivative(dS, rS[:, label], marg, (name, label, "delta"))
+        check_derivative(dv, rv[:, label], marg, (name, label, "vega"))
+
+
 def test_full_size_sampled_sensitivities(eng):
     """The sensitivities workload at the benchmark's size and seed: per-path
     (payoff, d/dS0, d/dsigma) of every underlying on three runs of paths

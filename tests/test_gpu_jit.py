@@ -175,6 +175,8 @@ def test_specialised_control_variate_equals_interpreter(eng, gamma):
         finally:
             pc.pc_set_jit(eng.ctx, False)
             pc.pc_debug_set_cv_min_blocks(eng.ctx, 0)
+    with pytest.raises(pc.PcError):
+        pc.pc_debug_set_cv_min_blocks(eng.ctx, 17)
     for key in ((True, 0), (True, 6)):
         np.testing.assert_array_equal(out[key][0].view(np.uint32), out[(False, 0)][0].view(np.uint32))
         assert out[key][1] == out[(False, 0)][1]
