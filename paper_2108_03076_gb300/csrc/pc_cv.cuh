@@ -153,27 +153,31 @@ struct CvOnline {
         for (int i = 0; i < D; ++i) l2[i] = __log2f(s0[i]);
         table_delta<D, GAMMA>(c, k, q ? ki[1] : ki[0], l2, delta, sl);
       }
-      float X[D], inv[D];
+      float X[D];
       float dm = 0.f;
 #pragma unroll
       for (int i = 0; i < D; ++i) {
         X[i] = d1 * s1[i] - d0 * s0[i];
         dm = fmaf(delta[i], X[i], dm);
-        inv[i] = __frcp_rn(s0[i]);
       }
       const float dM = al ? dm : 0.f;
       if (q) M[1] += dM;
       else M[0] += dM;
       if (GAMMA && k >= 1) {
         // Gamma = sym(t), t_ij = s_ij / (h_j S_j); the quadratic forms of
-        // a symmetric weight need only t itself
+        // a symmetric weight need only t itself.  1 / (h_j S_j) with the
+        // approximate reciprocal: any hedge ratio known at t_k keeps the
+        // term's mean zero, so the weights need no exact rounding.
+        float wj[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) wj[j] = __fdividef(c.inv_h[k - 1][j], s0[j]);
         float qf = 0.f, e = 0.f;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
           float rq = 0.f, re = 0.f;
 #pragma unroll
           for (int j = 0; j < D; ++j) {
-            const float tt = sl[i][j] * c.inv_h[k - 1][j] * inv[j];
+            const float tt = sl[i][j] * wj[j];
             rq = fmaf(tt, X[j], rq);
             re = fmaf(tt, s0[j] * c.cq[k][i * kCvMaxD + j], re);
           }
