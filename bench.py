@@ -685,6 +685,8 @@ def run_portfolio(args):
     stream = torch.cuda.Stream(device=local)
     torch.cuda.set_stream(stream)
     ctx = pc.pc_create(local, stream.cuda_stream)
+    # the costliest contracts on their run-time specialised kernels
+    pc.pc_set_jit(ctx, not args.interpret)
     models, contracts, programs = [], [], []
     for it in mine:
         s = it.market
@@ -784,8 +786,9 @@ def run_portfolio(args):
             "path_date_evals_per_sec": ws * sum(it.n_paths * it.market.n for it in mine) / step_s,
             "median_rel_stderr": float(np.nanmedian(rel)),
             "path_dates_per_step": path_dates,
-            "gpu_launches": args.steps * binfo.n_groups,
-            "batch": {"groups": binfo.n_groups, "units": binfo.n_units, "tiles": binfo.n_tiles,
+            "gpu_launches": args.steps * (binfo.n_groups + binfo.n_specialised),
+            "batch": {"groups": binfo.n_groups, "specialised_contracts": binfo.n_specialised,
+                      "units": binfo.n_units, "tiles": binfo.n_tiles,
                       "block": binfo.config.block, "unit_split": binfo.config.unit_split,
                       "paths_per_thread": binfo.paths_per_thread, "tuned_ms": binfo.last_ms},
             "single_launch": single,

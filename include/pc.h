@@ -424,10 +424,17 @@ typedef struct pc_batch_info {
   pc_batch_config config;    /* current launch shape                        */
   double paths_per_thread;   /* mean paths a thread evaluates per unit      */
   double last_ms;            /* device time of the last timed replay (tune) */
+  int32_t n_specialised;     /* contracts on their own run-time specialised
+                                kernel (with pc_set_jit: the costliest)    */
 } pc_batch_info;
 
 /* Build a plan over n contracts: contract i is priced against models[i]
  * with n_paths[i] paths (2 .. 2^40) on Philox stream word i under `seed`.
+ * With the context's pc_set_jit on, the costliest contracts (up to 160, and
+ * until 80 % of the estimated work) are priced by their run-time
+ * specialised kernels, each its own branch of the replay, the rest by the
+ * interpreting group kernels; the results are the same bits either way
+ * (compiling takes a few tens of ms per new program, cached per context).
  * All models and contracts must belong to one context and stay alive until
  * pc_batch_destroy.  config may be NULL (block 128, unit_split 128).
  * Allocates the plan's device memory (per-contract arguments, units,

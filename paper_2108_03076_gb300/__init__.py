@@ -62,7 +62,7 @@ class BatchConfig(C.Structure):
 class BatchInfo(C.Structure):
     _fields_ = [("n_contracts", C.c_uint64), ("n_tiles", C.c_uint64), ("n_units", C.c_uint64),
                 ("n_groups", C.c_int32), ("tuned", C.c_int32), ("config", BatchConfig),
-                ("paths_per_thread", C.c_double), ("last_ms", C.c_double)]
+                ("paths_per_thread", C.c_double), ("last_ms", C.c_double), ("n_specialised", C.c_int32)]
 
 
 class MlpInfo(C.Structure):

@@ -68,6 +68,17 @@ struct pc_batch {
   bool tuned = false;
   bool single = false;              // one launch of batch_kernel_any for every contract
   double last_ms = 0.0;
+  // contracts priced by their run-time specialised kernel, each its own
+  // branch of the graph (the costliest, with the context's pc_set_jit)
+  struct JitItem {
+    uint32_t item = 0;
+    cudaKernel_t kern = nullptr;
+    int grid = 0, block = 0;
+    size_t smem = 0;
+    PriceArgs args{};
+  };
+  std::vector<JitItem> jit;
+  std::vector<char> is_jit;
 };
 
 namespace {
@@ -93,6 +104,7 @@ void build_groups(pc_batch *B) {
   std::map<std::pair<int, int>, uint32_t> index;
   B->groups.clear();
   for (size_t i = 0; i < B->n; ++i) {
+    if (!B->single && !B->is_jit.empty() && B->is_jit[i]) continue;  // its own specialised launch
     const auto key = B->single ? std::make_pair(0, 0) : std::make_pair(B->d[i], words_class(B->words[i]));
     auto it = index.find(key);
     if (it == index.end()) {
@@ -204,11 +216,82 @@ pc_status configure(pc_batch *B, const pc_batch_config &cfg) {
   return PC_OK;
 }
 
+// With the context's pc_set_jit: the costliest contracts (by estimated tile
+// cost x tiles, until kBatchJitShare of the portfolio's cost or kBatchJitMax
+// contracts; at least kBatchJitMinTiles tiles each) priced by their
+// run-time specialised kernel on their own graph branch instead of the
+// interpreting group kernels -- the same per-tile work and reduction, so
+// the same bits.  Their arguments are the plan's, with the specialised
+// kernel's layout.
+constexpr size_t kBatchJitMax = 160;
+constexpr double kBatchJitShare = 0.8;
+constexpr uint64_t kBatchJitMinTiles = 64;
+
+pc_status choose_jit(pc_batch *B, const pc_model *const *models, const pc_contract *const *contracts,
+                     const uint64_t *n_paths, uint64_t seed) {
+  pc_ctx *c = B->ctx;
+  B->jit.clear();
+  B->is_jit.assign(B->n, 0);
+  if (!c->jit) return PC_OK;
+  std::vector<uint32_t> order(B->n);
+  for (size_t i = 0; i < B->n; ++i) order[i] = uint32_t(i);
+  auto cost = [&](uint32_t i) { return double(B->items[i].n_tiles) * B->tile_cost[i]; };
+  std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return cost(x) > cost(y); });
+  double acc = 0.0;
+  for (uint32_t i : order) {
+    if (B->jit.size() >= kBatchJitMax || acc >= kBatchJitShare * B->total_cost) break;
+    if (B->items[i].n_tiles < kBatchJitMinTiles || !jit_eligible(contracts[i])) continue;
+    Launch L;
+    pc_status s = prepare(models[i], contracts[i], n_paths[i], 0, seed, i, L);
+    if (s != PC_OK) return s;
+    const int wk = jit_window_kind(c, L);
+    if (wk & kJitHbm) continue;
+    const size_t smem = jit_layout(c, contracts[i], L, wk);
+    cudaKernel_t jk = nullptr;
+    s = jit_kernel(contracts[i], models[i]->H.d, kJitPrice | wk, L.block, jk, jit_min_blocks(c, smem, L.block));
+    if (s != PC_OK) return s;
+    int nb = 0;
+    CU(jit_occupancy(c, reinterpret_cast<const void *>(jk), L.block, smem, nb), "jit occupancy");
+    if (nb < 1) continue;
+    const uint64_t tiles = B->items[i].n_tiles;
+    const uint64_t units = (wk & kJitPairs2) ? (tiles + 1) / 2 : tiles, wpb = uint64_t(L.block / 32);
+    pc_batch::JitItem J;
+    J.item = i;
+    J.kern = jk;
+    J.block = L.block;
+    J.smem = smem;
+    J.grid = int(std::max<uint64_t>(1, std::min<uint64_t>(uint64_t(c->sm_count) * nb, (units + wpb - 1) / wpb)));
+    J.args = B->items[i];
+    J.args.lay = L.args.lay;
+    B->jit.push_back(J);
+    B->is_jit[i] = 1;
+    acc += cost(i);
+  }
+  // a kernel shared by several contracts takes the largest of their
+  // dynamic shared memory sizes
+  for (const pc_batch::JitItem &J : B->jit) {
+    size_t mx = 0;
+    for (const pc_batch::JitItem &K : B->jit)
+      if (K.kern == J.kern) mx = std::max(mx, K.smem);
+    CU(cudaFuncSetAttribute(reinterpret_cast<const void *>(J.kern), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            int(mx)), "specialised kernel shared memory");
+  }
+  return PC_OK;
+}
+
+// One specialised contract's launch (its PriceArgs by value).
+cudaError_t launch_jit_item(const pc_batch::JitItem &J, cudaStream_t st) {
+  PriceArgs a = J.args;
+  void *args[] = {&a};
+  return cudaLaunchKernel(reinterpret_cast<const void *>(J.kern), dim3(J.grid), dim3(J.block), args, J.smem, st);
+}
+
 // Capture: memset of the counters and control blocks, then every group's
 // launch on its own branch, joined back into the capture stream.
 pc_status capture(pc_batch *B) {
   pc_ctx *c = B->ctx;
-  while (B->aux.size() < B->groups.size()) {
+  const size_t n_jit = B->single ? 0 : B->jit.size();
+  while (B->aux.size() < B->groups.size() + n_jit) {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
@@ -232,6 +315,13 @@ pc_status capture(pc_batch *B) {
     if (e == cudaSuccess) e = launch_batch(a, g.d, g.grid, g.block, g.smem, B->aux[gi]);
     if (e == cudaSuccess) e = cudaEventRecord(B->joins[gi], B->aux[gi]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cap, B->joins[gi], 0);
+  }
+  for (size_t j = 0; j < n_jit && e == cudaSuccess; ++j) {
+    const size_t si = B->groups.size() + j;
+    e = cudaStreamWaitEvent(B->aux[si], B->fork, 0);
+    if (e == cudaSuccess) e = launch_jit_item(B->jit[j], B->aux[si]);
+    if (e == cudaSuccess) e = cudaEventRecord(B->joins[si], B->aux[si]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cap, B->joins[si], 0);
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(B->cap, &graph);
@@ -259,7 +349,8 @@ pc_status launch_direct(pc_batch *B) {
   pc_ctx *c = B->ctx;
   CU(cudaSetDevice(c->device), "cudaSetDevice");
   if (!c->batch_fork) CU(cudaEventCreateWithFlags(&c->batch_fork, cudaEventDisableTiming), "event");
-  while (c->batch_aux.size() < B->groups.size()) {
+  const size_t n_jit = B->single ? 0 : B->jit.size();
+  while (c->batch_aux.size() < B->groups.size() + n_jit) {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
     CU(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
@@ -282,6 +373,13 @@ pc_status launch_direct(pc_batch *B) {
     CU(launch_batch(a, g.d, g.grid, g.block, g.smem, c->batch_aux[gi]), "batch kernel");
     CU(cudaEventRecord(c->batch_join[gi], c->batch_aux[gi]), "join");
     CU(cudaStreamWaitEvent(c->stream, c->batch_join[gi], 0), "join wait");
+  }
+  for (size_t j = 0; j < n_jit; ++j) {
+    const size_t si = B->groups.size() + j;
+    CU(cudaStreamWaitEvent(c->batch_aux[si], c->batch_fork, 0), "fork wait");
+    CU(launch_jit_item(B->jit[j], c->batch_aux[si]), "specialised contract");
+    CU(cudaEventRecord(c->batch_join[si], c->batch_aux[si]), "join");
+    CU(cudaStreamWaitEvent(c->stream, c->batch_join[si], 0), "join wait");
   }
   return PC_OK;
 }
@@ -364,6 +462,8 @@ pc_status create(size_t n, const pc_model *const *models, const pc_contract *con
     CU(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking), "capture stream");
     CU(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming), "event");
   }
+  pc_status sj = choose_jit(B, models, contracts, n_paths, seed);
+  if (sj != PC_OK) return sj;
   build_groups(B);
   if (B->groups.size() > size_t(kMaxGroups)) return fail(PC_ELIMIT, "too many batch groups");
   // default: the tuner's pick on the 1024-contract synthetic portfolio
@@ -518,6 +618,7 @@ pc_status pc_batch_query(const pc_batch *B, pc_batch_info *info) {
   info->config = B->cfg;
   info->paths_per_thread = B->paths_per_thread;
   info->last_ms = B->last_ms;
+  info->n_specialised = B->single ? 0 : int32_t(B->jit.size());
   return PC_OK;
 }
 

@@ -176,6 +176,12 @@ pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKerne
 // Programs of at most PC_JIT_MAX_INSNS instructions are specialised; the
 // launches of longer ones interpret them.
 bool jit_eligible(const pc_contract *k);
+// The specialised pricing kernel's variant for a prepared launch (window in
+// registers, path pairs a lane, HBM window), its layout (the launch's shared
+// memory; may re-choose the block) and the register bound it is compiled for.
+int jit_window_kind(const pc_ctx *c, const Launch &L);
+size_t jit_layout(const pc_ctx *c, const pc_contract *k, Launch &L, int bits);
+int jit_min_blocks(const pc_ctx *c, size_t smem, int block);
 void jit_release(pc_ctx *c);
 
 // Turn a raised device status word into PC_EDEVICE (and clear it).

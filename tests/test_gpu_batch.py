@@ -231,3 +231,41 @@ def test_programs_loaded_in_one_call_price_the_same(eng, mixed):
     with pytest.raises(pc.PcError) as e:
         pc.pc_load_payoffs(eng.ctx, bad)
     assert "program 3" in str(e.value)
+
+
+def test_specialised_contracts_in_the_plan_give_the_same_bits(eng, mixed):
+    """With pc_set_jit the costliest contracts run on their own specialised
+    kernels inside the replay: the same bits as single launches, and on the
+    1024-contract portfolio the same prices as the all-interpreted plan
+    (one-shot pricing too)."""
+    models, contracts, n_paths = mixed
+    pc.pc_set_jit(eng.ctx, True)
+    try:
+        plan = pc.pc_batch_create(models, contracts, n_paths, SEED)
+        try:
+            assert pc.pc_batch_query(plan).n_specialised >= 1
+            check_identical(eng, plan, models, contracts, n_paths)
+        finally:
+            pc.pc_batch_destroy(plan)
+    finally:
+        pc.pc_set_jit(eng.ctx, False)
+    items = W.portfolio()
+    pm = [eng.model(it.market) for it in items]
+    pk = [eng.contract(it.il_text, it.tparams) for it in items]
+    pn = [it.n_paths for it in items]
+    p0, s0 = pc.pc_price_batch(pm, pk, pn, SEED)
+    pc.pc_set_jit(eng.ctx, True)
+    try:
+        plan = pc.pc_batch_create(pm, pk, pn, SEED)
+        try:
+            assert pc.pc_batch_query(plan).n_specialised > 8
+            pc.pc_batch_launch(plan)
+            p1, s1 = pc.pc_batch_results(plan, len(items))
+        finally:
+            pc.pc_batch_destroy(plan)
+        p2, s2 = pc.pc_price_batch(pm, pk, pn, SEED)
+    finally:
+        pc.pc_set_jit(eng.ctx, False)
+    np.testing.assert_array_equal(p1, p0)
+    np.testing.assert_array_equal(s1, s0)
+    np.testing.assert_array_equal(p2, p0)
