@@ -237,18 +237,41 @@ pc_status choose_jit(pc_batch *B, const pc_model *const *models, const pc_contra
   for (size_t i = 0; i < B->n; ++i) order[i] = uint32_t(i);
   auto cost = [&](uint32_t i) { return double(B->items[i].n_tiles) * B->tile_cost[i]; };
   std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) { return cost(x) > cost(y); });
-  double acc = 0.0;
-  for (uint32_t i : order) {
-    if (B->jit.size() >= kBatchJitMax || acc >= kBatchJitShare * B->total_cost) break;
-    if (B->items[i].n_tiles < kBatchJitMinTiles || !jit_eligible(contracts[i])) continue;
+  // the candidates and their kernels' variants, compiled together
+  struct Cand {
+    uint32_t i;
     Launch L;
-    pc_status s = prepare(models[i], contracts[i], n_paths[i], 0, seed, i, L);
+    int wk;
+    size_t smem;
+    int min_blocks;
+  };
+  std::vector<Cand> cand;
+  std::vector<JitRequest> reqs;
+  double est = 0.0;
+  for (uint32_t i : order) {
+    if (cand.size() >= kBatchJitMax || est >= kBatchJitShare * B->total_cost) break;
+    if (B->items[i].n_tiles < kBatchJitMinTiles || !jit_eligible(contracts[i])) continue;
+    Cand cd;
+    cd.i = i;
+    pc_status s = prepare(models[i], contracts[i], n_paths[i], 0, seed, i, cd.L);
     if (s != PC_OK) return s;
-    const int wk = jit_window_kind(c, L);
-    if (wk & kJitHbm) continue;
-    const size_t smem = jit_layout(c, contracts[i], L, wk);
+    cd.wk = jit_window_kind(c, cd.L);
+    if (cd.wk & kJitHbm) continue;
+    cd.smem = jit_layout(c, contracts[i], cd.L, cd.wk);
+    cd.min_blocks = jit_min_blocks(c, cd.smem, cd.L.block);
+    reqs.push_back({contracts[i], models[i]->H.d, kJitPrice | cd.wk, cd.L.block, cd.min_blocks});
+    cand.push_back(cd);
+    est += cost(i);
+  }
+  pc_status sc = jit_compile_many(c, reqs);
+  if (sc != PC_OK) return sc;
+  for (Cand &cd : cand) {
+    const uint32_t i = cd.i;
+    Launch &L = cd.L;
+    const int wk = cd.wk;
+    const size_t smem = cd.smem;
     cudaKernel_t jk = nullptr;
-    s = jit_kernel(contracts[i], models[i]->H.d, kJitPrice | wk, L.block, jk, jit_min_blocks(c, smem, L.block));
+    pc_status s = jit_kernel(contracts[i], models[i]->H.d, kJitPrice | wk, L.block, jk, cd.min_blocks);
     if (s != PC_OK) return s;
     int nb = 0;
     CU(jit_occupancy(c, reinterpret_cast<const void *>(jk), L.block, smem, nb), "jit occupancy");
@@ -265,7 +288,6 @@ pc_status choose_jit(pc_batch *B, const pc_model *const *models, const pc_contra
     J.args.lay = L.args.lay;
     B->jit.push_back(J);
     B->is_jit[i] = 1;
-    acc += cost(i);
   }
   // a kernel shared by several contracts takes the largest of their
   // dynamic shared memory sizes

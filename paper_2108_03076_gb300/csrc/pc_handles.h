@@ -176,6 +176,14 @@ pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKerne
 // Programs of at most PC_JIT_MAX_INSNS instructions are specialised; the
 // launches of longer ones interpret them.
 bool jit_eligible(const pc_contract *k);
+// Compile the specialised kernels of many requests into the context's cache
+// (those not there yet), NVRTC on the host's cores in parallel; jit_kernel
+// then finds them.
+struct JitRequest {
+  const pc_contract *k;
+  int d, kind, block, min_blocks;
+};
+pc_status jit_compile_many(pc_ctx *c, const std::vector<JitRequest> &reqs);
 // The specialised pricing kernel's variant for a prepared launch (window in
 // registers, path pairs a lane, HBM window), its layout (the launch's shared
 // memory; may re-choose the block) and the register bound it is compiled for.

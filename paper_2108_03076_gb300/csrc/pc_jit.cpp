@@ -11,10 +11,12 @@
 // the same order.  NVRTC compiles the module for the device the context
 // runs on; the kernel is price_tiles (pc_price.cuh) with this evaluator.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvrtc.h>
@@ -408,6 +410,97 @@ pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKerne
   if (s != PC_OK) return s;
   out = E.kernel;
   c->jit_cache.emplace(h, std::move(E));
+  return PC_OK;
+}
+
+namespace {
+std::vector<uint32_t> program_words(const Program &p) {
+  std::vector<uint32_t> words;
+  words.reserve(p.code.size() * 4 + p.pool.size());
+  for (const XInsn &I : p.code) {
+    words.push_back(I.opa);
+    words.push_back(I.b);
+    words.push_back(I.c);
+    words.push_back(I.e);
+  }
+  for (float f : p.pool) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    words.push_back(u);
+  }
+  return words;
+}
+}  // namespace
+
+pc_status jit_compile_many(pc_ctx *c, const std::vector<JitRequest> &reqs) {
+  // the requests not yet in the context's cache (each once)
+  struct Miss {
+    const JitRequest *r;
+    std::vector<uint32_t> words;
+    uint64_t h;
+    std::vector<char> cubin;
+    pc_status s = PC_OK;
+  };
+  std::vector<Miss> miss;
+  {
+    std::lock_guard<std::mutex> g(c->jit_mu);
+    for (const JitRequest &r : reqs) {
+      Miss m;
+      m.r = &r;
+      m.words = program_words(r.k->prog);
+      uint64_t h = 1469598103934665603ull;  // FNV-1a, as jit_kernel
+      for (uint32_t w : m.words)
+        for (int b = 0; b < 4; ++b) h = (h ^ ((w >> (8 * b)) & 0xffu)) * 1099511628211ull;
+      m.h = h;
+      bool have = false;
+      auto range = c->jit_cache.equal_range(h);
+      for (auto it = range.first; it != range.second && !have; ++it) {
+        const JitEntry &E = it->second;
+        have = E.d == r.d && E.kind == r.kind && E.block == r.block && E.min_blocks == r.min_blocks &&
+               E.program == m.words;
+      }
+      for (const Miss &o : miss)
+        have = have || (o.h == h && o.r->d == r.d && o.r->kind == r.kind && o.r->block == r.block &&
+                         o.r->min_blocks == r.min_blocks && o.words == m.words);
+      if (!have) miss.push_back(std::move(m));
+    }
+  }
+  if (miss.empty()) return PC_OK;
+  cudaDeviceProp prop{};
+  CU(cudaGetDeviceProperties(&prop, c->device), "device properties");
+  const std::string arch = "sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a";
+  // NVRTC on the host's cores, one program per thread at a time
+  std::atomic<size_t> next{0};
+  auto work = [&]() {
+    for (size_t i = next++; i < miss.size(); i = next++) {
+      const JitRequest &r = *miss[i].r;
+      miss[i].s = to_cubin(r.k->prog, r.d, r.kind, r.block, r.min_blocks, arch, miss[i].cubin);
+    }
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nt = std::min<size_t>(miss.size(), std::min<unsigned>(hw, 32u));
+  std::vector<std::thread> pool;
+  for (size_t t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (std::thread &t : pool) t.join();
+  std::lock_guard<std::mutex> g(c->jit_mu);
+  for (Miss &m : miss) {
+    if (m.s != PC_OK) return m.s;
+    JitEntry E;
+    E.program = m.words;
+    E.d = m.r->d;
+    E.kind = m.r->kind;
+    E.block = m.r->block;
+    E.min_blocks = m.r->min_blocks;
+    CU(cudaLibraryLoadData(&E.lib, m.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0), "module load");
+    cudaError_t e = cudaLibraryGetKernel(&E.kernel, E.lib, E.kind >= kJitGreeks ? "pc_jit_greeks"
+                                                           : E.kind >= kJitCv ? "pc_jit_cv" : "pc_jit_price");
+    if (e != cudaSuccess) {
+      cudaLibraryUnload(E.lib);
+      return cuda_fail(e, "kernel lookup");
+    }
+    c->jit_cache.emplace(m.h, std::move(E));
+  }
   return PC_OK;
 }
 
