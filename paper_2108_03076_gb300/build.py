@@ -53,7 +53,8 @@ def up_to_date() -> bool:
 # Device sources the run-time compiler (NVRTC) needs, embedded in the
 # library as string literals (pc_jit.cpp includes the generated header).
 JIT_HEADERS = ["pc_types.h", "pc_device.cuh", "pc_price.cuh", "pc_eval_state.inc", "pc_ops.inc", "pc_cv_types.h",
-               "pc_cv.cuh", "pc_greeks.cuh", "pc_greeks_state.inc", "pc_greeks_ops.inc"]
+               "pc_cv.cuh", "pc_greeks.cuh", "pc_greeks_state.inc", "pc_greeks_ops.inc", "pc_adjoint.cuh",
+               "pc_adjoint_state.inc", "pc_adjoint_ops.inc"]
 
 
 def _op_cases():

@@ -10,7 +10,11 @@ namespace {
 
 template <int D, bool WRITE>
 __global__ void __launch_bounds__(kBlock) adjoint_kernel(const __grid_constant__ PriceArgs a, const TapeArgs t) {
-  adjoint_tiles<D, WRITE>(a, t);
+  adjoint_tiles<D, WRITE>(a, t, [&](const uint4 *P, const float *pool, float2 *R, const Rng2 &g, bool live0,
+                                   bool live1, const float (&Bm)[D * D], const float (&S0)[D],
+                                   const float (&Lm)[D * D], Tape &T, int &res) {
+    return eval_adjoint<D>(P, pool, R, a, g, live0, live1, Bm, S0, Lm, T, res);
+  });
 }
 
 template <typename K>

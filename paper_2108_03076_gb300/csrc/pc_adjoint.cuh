@@ -88,397 +88,12 @@ template <int D>
 __device__ float2 eval_adjoint(const uint4 *P, const float *pool, float2 *R, const PriceArgs &a,
                                const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],
                                const float (&S0)[D], const float (&Lm)[D * D], Tape &T, int &res) {
-  const ModelDev &m = a.m;
-  const Layout &lay = a.lay;
-  PathState<D> ps;
-  path_state_init<D>(ps, R, lay);
-  const int t_now = m.t_now;
-  int pc = 0, sp = 0, t0 = 0;
-  float2 tos = make_float2(0.f, 0.f);
-  int tid = -1;  // entry of tos
-  // logical slot s: value at physical slot 2s, entry number at 2s + 1
-  auto sv = [&](int s) -> float2 & { return SL(2 * s); };
-  auto sid_get = [&](int s) { return __float_as_int(SL(2 * s + 1).x); };
-  auto sid_set = [&](int s, int e) { SL(2 * s + 1) = make_float2(__int_as_float(e), 0.f); };
-  auto push = [&](float2 v, int e) {
-    sv(sp) = tos;
-    sid_set(sp, tid);
-    ++sp;
-    tos = v;
-    tid = e;
-  };
-  auto pop = [&](int &e) {
-    const float2 v = tos;
-    e = tid;
-    --sp;
-    tos = sv(sp);
-    tid = sid_get(sp);
-    return v;
-  };
-  auto ensure = [&](int &o) {
-    if (o > m.n || o < -m.n_hist) {
-      atomicOr(a.status, 1);
-      o = o > m.n ? m.n : -m.n_hist;
-    }
-    while (ps.f < o) gen_date<D, true>(ps.f + 1, ps, m, lay, g, R, Bm, S0, Lm);
-  };
-  auto read = [&](int o, int l) -> float2 {
-    if (o > 0) return SL(lay.off_win + (o & (lay.win - 1)) * D + l);
-    const float v = __ldg(m.sval + (o + m.n_hist) * D + l);
-    return make_float2(v, v);
-  };
-  const float2 one = make_float2(1.f, 1.f), zero = make_float2(0.f, 0.f);
+#include "pc_adjoint_state.inc"
   for (;;) {
     const uint4 I = P[pc];
     const uint32_t op = I.x & 0xffu;
     const float kk = __uint_as_float(I.y);
-    switch (op) {
-      case X_CONST: push(make_float2(kk, kk), -1); ++pc; break;
-      case X_MODEL:
-      case X_MODEL_MULK:
-      case X_MODEL_DIVK: {
-        int o = int(I.y) + t0 - t_now;
-        ensure(o);
-        int l = int(I.x >> 8) & 3;
-        l = l < D ? l : 0;
-        float2 v = read(o, l);
-        const float k = __uint_as_float(I.z);
-        const float2 s = v;
-        float scale = 1.f;
-        if (op == X_MODEL_MULK) {
-          v = make_float2(__fmul_rn(v.x, k), __fmul_rn(v.y, k));
-          scale = k;
-        } else if (op == X_MODEL_DIVK) {
-          v = make_float2(__fdiv_rn(v.x, k), __fdiv_rn(v.y, k));
-          scale = __frcp_rn(k);
-        }
-        push(v, adj_leaf<D>(T, o, l, s, scale, R, m, lay, S0));
-        ++pc;
-        break;
-      }
-      case X_LRED:
-      case X_LANY: {
-        int o = int(I.y) + t0 - t_now;
-        ensure(o);
-        const uint32_t A = I.x >> 8;
-        const int code = int((A >> 4) & 7u);
-        if (op == X_LANY || code) {  // a test: boolean, no derivative
-          push(fused_value<D>(I, o, pool, R, m, lay), -1);
-          ++pc;
-          break;
-        }
-        const int n = int((A >> 8) & 3u) + 1, kind = int((A >> 2) & 3u), rop = int(A & 3u);
-        float2 v = zero;
-        int e = -1;
-        for (int i = 0; i < n; ++i) {
-          int l = int(A >> (10 + 2 * i)) & 3;
-          l = l < D ? l : 0;
-          const float2 s0 = read(o, l);
-          float2 s = s0;
-          float scale = 1.f;
-          if (kind == 1) {
-            const float c = pool[I.z + i];
-            s = make_float2(__fmul_rn(s.x, c), __fmul_rn(s.y, c));
-            scale = c;
-          } else if (kind == 2) {
-            const float c = pool[I.z + i];
-            s = make_float2(__fdiv_rn(s.x, c), __fdiv_rn(s.y, c));
-            scale = __frcp_rn(c);
-          }
-          const int el = adj_leaf<D>(T, o, l, s0, scale, R, m, lay, S0);
-          if (i == 0) {
-            v = s;
-            e = el;
-          } else if (rop == 2) {
-            v = make_float2(__fadd_rn(v.x, s.x), __fadd_rn(v.y, s.y));
-            e = T.add(e, el, one, one);
-          } else {
-            // the leaf taken when it is strictly beyond the running value
-            const float2 t = fl2(int(rop == 0 ? s.x < v.x : s.x > v.x), int(rop == 0 ? s.y < v.y : s.y > v.y));
-            v = rop == 0 ? make_float2(fminf(v.x, s.x), fminf(v.y, s.y)) : make_float2(fmaxf(v.x, s.x), fmaxf(v.y, s.y));
-            e = T.add(e, el, adsel(t, zero, one), adsel(t, one, zero));
-          }
-        }
-        push(v, e);
-        ++pc;
-        break;
-      }
-      case X_PAYOFF: {
-        int o = int(I.y) + t0 - t_now;
-        if (o > m.n || o < -m.n_hist) {
-          atomicOr(a.status, 1);
-          o = 0;
-        }
-        float v = __fmul_rn(__uint_as_float(I.z), __ldg(m.disc + o + m.n_hist));
-        if (I.x >> 8) v = -v;
-        push(make_float2(v, v), -1);
-        ++pc;
-        break;
-      }
-      case X_TIME: push(fl2(int(I.y) + t0, int(I.y) + t0), -1); ++pc; break;
-      case X_NOW: push(fl2(t_now, t_now), -1); ++pc; break;
-      case X_NEGF:
-        tos = make_float2(-tos.x, -tos.y);
-        tid = T.add(tid, -1, make_float2(-1.f, -1.f), zero);
-        ++pc;
-        break;
-      case X_NOT: tos = fl2(bits(tos.x) ^ 1, bits(tos.y) ^ 1); ++pc; break;
-      case X_ADDF: case X_SUBF: case X_MULF: case X_DIVF: case X_MAXF: case X_MINF: {
-        int ey;
-        const float2 y = pop(ey), x = tos;
-        const int ex = tid;
-        float2 r, p1, p2;
-        if (op == X_ADDF) {
-          r = make_float2(__fadd_rn(x.x, y.x), __fadd_rn(x.y, y.y));
-          p1 = one;
-          p2 = one;
-        } else if (op == X_SUBF) {
-          r = make_float2(__fsub_rn(x.x, y.x), __fsub_rn(x.y, y.y));
-          p1 = one;
-          p2 = make_float2(-1.f, -1.f);
-        } else if (op == X_MULF) {
-          r = make_float2(__fmul_rn(x.x, y.x), __fmul_rn(x.y, y.y));
-          p1 = y;
-          p2 = x;
-        } else if (op == X_DIVF) {
-          r = make_float2(__fdiv_rn(x.x, y.x), __fdiv_rn(x.y, y.y));
-          p1 = make_float2(__frcp_rn(y.x), __frcp_rn(y.y));
-          p2 = make_float2(-__fdiv_rn(r.x, y.x), -__fdiv_rn(r.y, y.y));
-        } else {
-          const bool mx = op == X_MAXF;
-          const float2 t = fl2(int(mx ? y.x > x.x : y.x < x.x), int(mx ? y.y > x.y : y.y < x.y));
-          r = mx ? make_float2(fmaxf(x.x, y.x), fmaxf(x.y, y.y)) : make_float2(fminf(x.x, y.x), fminf(x.y, y.y));
-          p1 = adsel(t, zero, one);
-          p2 = adsel(t, one, zero);
-        }
-        tos = r;
-        tid = T.add(ex, ey, p1, p2);
-        ++pc;
-        break;
-      }
-      case X_LTF: case X_LEF: case X_EQF: {
-        int ey;
-        const float2 y = pop(ey), x = tos;
-        tos = op == X_LTF ? fl2(int(x.x < y.x), int(x.y < y.y))
-              : op == X_LEF ? fl2(int(x.x <= y.x), int(x.y <= y.y))
-                            : fl2(int(x.x == y.x), int(x.y == y.y));
-        tid = -1;
-        ++pc;
-        break;
-      }
-      case X_ADDI: case X_SUBI: case X_MULI: case X_MAXI: case X_MINI: case X_LTI: case X_LEI:
-      case X_EQI: case X_AND: case X_OR: {
-        int ey;
-        const float2 y = pop(ey), x = tos;
-        int r[2];
-        const int xa[2] = {bits(x.x), bits(x.y)}, ya[2] = {bits(y.x), bits(y.y)};
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int a_ = xa[q], b_ = ya[q];
-          r[q] = op == X_ADDI ? a_ + b_ : op == X_SUBI ? (a_ > b_ ? a_ - b_ : 0) : op == X_MULI ? a_ * b_
-               : op == X_MAXI ? (a_ > b_ ? a_ : b_) : op == X_MINI ? (a_ < b_ ? a_ : b_)
-               : op == X_LTI ? int(a_ < b_) : op == X_LEI ? int(a_ <= b_) : op == X_EQI ? int(a_ == b_)
-               : op == X_AND ? (a_ & b_) : (a_ | b_);
-        }
-        tos = fl2(r[0], r[1]);
-        tid = -1;
-        ++pc;
-        break;
-      }
-      case X_ADDFK: case X_SUBFK: case X_MULFK: case X_DIVFK: case X_MAXFK: case X_MINFK:
-      case X_RSUBFK: case X_RDIVFK: {
-        const float2 x = tos;
-        float2 r, p;
-        if (op == X_ADDFK) {
-          r = make_float2(__fadd_rn(x.x, kk), __fadd_rn(x.y, kk));
-          p = one;
-        } else if (op == X_SUBFK) {
-          r = make_float2(__fsub_rn(x.x, kk), __fsub_rn(x.y, kk));
-          p = one;
-        } else if (op == X_MULFK) {
-          r = make_float2(__fmul_rn(x.x, kk), __fmul_rn(x.y, kk));
-          p = make_float2(kk, kk);
-        } else if (op == X_DIVFK) {
-          r = make_float2(__fdiv_rn(x.x, kk), __fdiv_rn(x.y, kk));
-          const float q = __frcp_rn(kk);
-          p = make_float2(q, q);
-        } else if (op == X_RSUBFK) {
-          r = make_float2(__fsub_rn(kk, x.x), __fsub_rn(kk, x.y));
-          p = make_float2(-1.f, -1.f);
-        } else if (op == X_RDIVFK) {
-          r = make_float2(__fdiv_rn(kk, x.x), __fdiv_rn(kk, x.y));
-          p = make_float2(-__fdiv_rn(r.x, x.x), -__fdiv_rn(r.y, x.y));
-        } else {  // the literal taken: no derivative
-          const bool mx = op == X_MAXFK;
-          const float2 t = fl2(int(mx ? kk > x.x : kk < x.x), int(mx ? kk > x.y : kk < x.y));
-          r = mx ? make_float2(fmaxf(x.x, kk), fmaxf(x.y, kk)) : make_float2(fminf(x.x, kk), fminf(x.y, kk));
-          p = adsel(t, zero, one);
-        }
-        tos = r;
-        tid = T.add(tid, -1, p, zero);
-        ++pc;
-        break;
-      }
-      case X_LTFK: case X_LEFK: case X_EQFK: case X_RLTFK: case X_RLEFK: {
-        const float2 x = tos;
-        tos = op == X_LTFK ? fl2(int(x.x < kk), int(x.y < kk))
-              : op == X_LEFK ? fl2(int(x.x <= kk), int(x.y <= kk))
-              : op == X_EQFK ? fl2(int(x.x == kk), int(x.y == kk))
-              : op == X_RLTFK ? fl2(int(kk < x.x), int(kk < x.y))
-                              : fl2(int(kk <= x.x), int(kk <= x.y));
-        tid = -1;
-        ++pc;
-        break;
-      }
-      case X_IF: {
-        const bool c0 = bits(tos.x) != 0, c1 = bits(tos.y) != 0;
-        if (__any_sync(kFull, (live0 && c0) || (live1 && c1))) { ++pc; break; }
-        push(zero, -1);
-        pc = int(I.z);
-        break;
-      }
-      case X_ELSE: {
-        const float2 c = sv(sp - 1);
-        const bool c0 = bits(c.x) != 0, c1 = bits(c.y) != 0;
-        if (__any_sync(kFull, (live0 && !c0) || (live1 && !c1))) { ++pc; break; }
-        push(zero, -1);
-        pc = int(I.z);
-        break;
-      }
-      case X_SEL: {
-        const float2 th = sv(sp - 1), c = sv(sp - 2);
-        const int eth = sid_get(sp - 1);
-        sp -= 2;
-        const float2 ct = fl2(bits(c.x) != 0, bits(c.y) != 0);
-        tid = T.add(eth, tid, adsel(ct, one, zero), adsel(ct, zero, one));
-        tos = adsel(ct, th, tos);
-        ++pc;
-        break;
-      }
-      case X_LOOP: {
-        const int F = int(I.x >> 8);
-        sv(F + LF_K) = fl2(0, 0);
-        sv(F + LF_T0) = fl2(t0, t0);
-        sv(F + LF_DONE) = fl2(live0 ? 0 : 1, live1 ? 0 : 1);
-        sv(F + LF_RES) = zero;
-        sid_set(F + LF_RES, -1);
-        ++pc;
-        break;
-      }
-      case X_LOOPANY: {
-        const int F = int((I.x >> 8) & 0xffu);
-        const float lit = pool[I.x >> 16];
-        const uint4 Dsc = P[pc + 1];
-        bool d0 = !live0, d1 = !live1;
-        float r0 = 0.f, r1 = 0.f;
-        int n = int(I.y);
-        bool all = false;
-        int o0 = int(Dsc.y) + t0 - t_now;
-        if (o0 < -m.n_hist || o0 + n > m.n) {
-          atomicOr(a.status, 1);
-          o0 = o0 < -m.n_hist ? -m.n_hist : o0 > m.n ? m.n : o0;
-          n = o0 + n > m.n ? m.n - o0 : n;
-        }
-        for (int k = 0;; ++k) {
-          const int o = o0 + k;
-          while (ps.f < o) gen_date<D, true>(ps.f + 1, ps, m, lay, g, R, Bm, S0, Lm);
-          const float2 c = fused_value<D>(Dsc, o, pool, R, m, lay);
-          if (bits(c.x) && !d0) { d0 = true; r0 = lit; }
-          if (bits(c.y) && !d1) { d1 = true; r1 = lit; }
-          all = __all_sync(kFull, d0 && d1);
-          if (all || k == n) break;
-        }
-        if (all) {
-          push(make_float2(r0, r1), -1);
-          pc = int(I.w);
-          break;
-        }
-        sv(F + LF_T0) = fl2(t0, t0);
-        sv(F + LF_DONE) = fl2(d0, d1);
-        sv(F + LF_RES) = make_float2(r0, r1);
-        sid_set(F + LF_RES, -1);
-        t0 += n;
-        pc += 2;
-        break;
-      }
-      case X_LTEST: {
-        const int F = int(I.x >> 8);
-        int ec;
-        const float2 c = pop(ec);
-        const float2 d = sv(F + LF_DONE);
-        const int n0 = bits(c.x) != 0 && bits(d.x) == 0, n1 = bits(c.y) != 0 && bits(d.y) == 0;
-        sv(F + LF_NEWLY) = fl2(n0, n1);
-        pc = __any_sync(kFull, n0 | n1) ? pc + 1 : int(I.z);
-        break;
-      }
-      case X_LLATCH: {
-        const int F = int(I.x >> 8);
-        int ev;
-        const float2 v = pop(ev);
-        const float2 nw = sv(F + LF_NEWLY);
-        if (__any_sync(kFull, (bits(nw.x) | bits(nw.y)) != 0)) {  // uniform: an entry for the warp
-          const float2 r = sv(F + LF_RES), d = sv(F + LF_DONE);
-          const float2 nt = fl2(bits(nw.x) != 0, bits(nw.y) != 0);
-          const int er = T.add(ev, sid_get(F + LF_RES), adsel(nt, one, zero), adsel(nt, zero, one));
-          sv(F + LF_RES) = adsel(nt, v, r);
-          sid_set(F + LF_RES, er);
-          sv(F + LF_DONE) = fl2(bits(d.x) | bits(nw.x), bits(d.y) | bits(nw.y));
-        }
-        ++pc;
-        break;
-      }
-      case X_LSTEPK:
-      case X_LNEXT: {
-        const bool step = op == X_LSTEPK;
-        const int F = step ? int((I.x >> 8) & 0xffu) : int(I.x >> 8);
-        float2 d = sv(F + LF_DONE);
-        if (step) {  // latch the literal (no derivative) on newly true lanes
-          int ec;
-          const float2 c = pop(ec);
-          const int n0 = bits(c.x) != 0 && bits(d.x) == 0, n1 = bits(c.y) != 0 && bits(d.y) == 0;
-          if (__any_sync(kFull, (n0 | n1) != 0)) {
-            const float lit = pool[I.x >> 16];
-            const float2 r = sv(F + LF_RES), nt = fl2(n0, n1);
-            const int er = T.add(-1, sid_get(F + LF_RES), zero, adsel(nt, zero, one));
-            sv(F + LF_RES) = adsel(nt, make_float2(lit, lit), r);
-            sid_set(F + LF_RES, er);
-            d = fl2(bits(d.x) | n0, bits(d.y) | n1);
-            sv(F + LF_DONE) = d;
-          }
-        }
-        const int t0e = bits(sv(F + LF_T0).x);
-        if (__all_sync(kFull, (bits(d.x) & bits(d.y)) != 0)) {
-          t0 = t0e;
-          push(sv(F + LF_RES), sid_get(F + LF_RES));
-          pc = int(I.w);
-          break;
-        }
-        int k = bits(sv(F + LF_K).x);
-        if (k == int(I.y)) {
-          t0 = t0e + k;
-          ++pc;
-          break;
-        }
-        ++k;
-        sv(F + LF_K) = fl2(k, k);
-        t0 = t0e + k;
-        pc = int(I.z);
-        break;
-      }
-      case X_LEND: {
-        const int F = int(I.x >> 8);
-        const float2 d = sv(F + LF_DONE), r = sv(F + LF_RES);
-        const float2 dt = fl2(bits(d.x) != 0, bits(d.y) != 0);
-        tid = T.add(sid_get(F + LF_RES), tid, adsel(dt, one, zero), adsel(dt, zero, one));
-        tos = adsel(dt, r, tos);
-        t0 = bits(sv(F + LF_T0).x);
-        ++pc;
-        break;
-      }
-      default:
-        res = tid;
-        return tos;
-    }
+#include "pc_adjoint_ops.inc"
   }
 }
 
@@ -522,8 +137,10 @@ __device__ __forceinline__ void reverse_sweep(Tape &T, int res, float2 (&dS)[D],
 // The sensitivity launch: per path (x, dx/dS0_l, dx/dsigma_l for l < D), per
 // tile the FP64 sums and sums of squares of the 1 + 2D values in the
 // deterministic chunked reduction (width 2 (1 + 2D)).
-template <int D, bool WRITE>
-__device__ __forceinline__ void adjoint_tiles(const PriceArgs &a, const TapeArgs &ta) {
+// EVAL(P, pool, R, g, live0, live1, Bm, S0, Lm, T, res) -> the lane's two
+// payoffs with the tape (eval_adjoint, or a run-time specialised evaluator).
+template <int D, bool WRITE, typename EVAL>
+__device__ __forceinline__ void adjoint_tiles(const PriceArgs &a, const TapeArgs &ta, EVAL eval) {
   constexpr int V = 1 + 2 * D, W = 2 * V;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ int last_block;
@@ -567,7 +184,7 @@ __device__ __forceinline__ void adjoint_tiles(const PriceArgs &a, const TapeArgs
     g.phi[1] = uint32_t(p1 >> 32);
     T.n = 0;
     int res = -1;
-    const float2 x = eval_adjoint<D>(P, pool, R, a, g, live0, live1, Bm, S0, Lm, T, res);
+    const float2 x = eval(P, pool, R, g, live0, live1, Bm, S0, Lm, T, res);
     __syncwarp();  // the ids lane 0 wrote are read by every lane
     float2 dS[D], dv[D];
     reverse_sweep<D>(T, res, dS, dv);

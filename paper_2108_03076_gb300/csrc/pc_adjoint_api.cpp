@@ -106,6 +106,22 @@ pc_status run_adjoint(const pc_model *m, const pc_contract *k, uint64_t n_paths,
   a.out = d_out;
   a.out_paths = d_paths;
   CU(cudaSetDevice(c->device), "cudaSetDevice");
+  if (c->jit && adjoint_jit_eligible(k)) {
+    // the program's run-time specialised adjoint kernel (same arguments,
+    // block and tape regions; at most the interpreter's grid)
+    cudaKernel_t jk = nullptr;
+    s = jit_kernel(k, d, kJitAdjoint + (d_paths ? 1 : 0), block, jk);
+    if (s != PC_OK) return s;
+    const void *kern = reinterpret_cast<const void *>(jk);
+    int nb = 0;
+    CU(jit_occupancy(c, kern, block, smem, nb), "jit occupancy");
+    if (nb >= 1) {
+      const int jgrid = std::min(grid, c->sm_count * nb);
+      void *args[] = {&a, &t};
+      CU(cudaLaunchKernel(kern, dim3(jgrid), dim3(block), args, smem, c->stream), "specialised adjoint kernel");
+      return PC_OK;
+    }
+  }
   CU(launch_adjoint(a, t, grid, block, smem, c->stream), "adjoint kernel");
   return PC_OK;
 }

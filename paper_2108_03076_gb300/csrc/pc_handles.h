@@ -21,9 +21,11 @@
 // per-path payoffs; bit kJitHbm: the window of dates in HBM; bit
 // kJitWinRegs: a window of one date, kept in registers; bit kJitPairs2 (with
 // kJitWinRegs): four paths a lane), and the
-// control-variate kernel (kJitCv + its kCv* mode bits).
+// control-variate kernel (kJitCv + its kCv* mode bits), the tangent kernel
+// (kJitGreeks, + 1: per-path outputs) and the adjoint kernel (kJitAdjoint,
+// + 1: per-path outputs).
 constexpr int kJitPrice = 0, kJitPriceWrite = 1, kJitHbm = 2, kJitWinRegs = 4, kJitPairs2 = 8, kJitCv = 16,
-              kJitGreeks = 32;
+              kJitGreeks = 32, kJitAdjoint = 64;
 // resident blocks per SM the specialised pricing kernel's register bound is
 // set for by default (<= 72 registers at 128 threads: the fastest measured)
 constexpr int kJitMinBlocks = 7;
@@ -176,6 +178,9 @@ pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKerne
 // Programs of at most PC_JIT_MAX_INSNS instructions are specialised; the
 // launches of longer ones interpret them.
 bool jit_eligible(const pc_contract *k);
+// A program the specialised adjoint kernel takes (its date generator is
+// inlined at each reading instruction: a few of them at most).
+bool adjoint_jit_eligible(const pc_contract *k);
 // Compile the specialised kernels of many requests into the context's cache
 // (those not there yet), NVRTC on the host's cores in parallel; jit_kernel
 // then finds them.

@@ -151,6 +151,54 @@ bool stack_depths(const Program &p, std::vector<int> &sp_at) {
 // operand stack of value-with-tangents stays in shared memory, as in the
 // interpreter.  Beyond kInlineTangentDateSites reading instructions they
 // call one out-of-line copy of the date generator.
+// The adjoint evaluator straight-line over the program (each instruction's
+// block includes pc_adjoint_ops.inc with the instruction as a constant),
+// and pc_jit_adjoint: adjoint_tiles around it.  The date generator (with
+// the X window) is inlined at each reading instruction: programs with more
+// than kInlineTangentDateSites of them are not specialised (adjoint_eligible).
+std::string generate_adjoint(const Program &p, int d, bool write) {
+  std::ostringstream o;
+  const size_t n = p.code.size();
+  o << "#include \"pc_adjoint.cuh\"\n"
+    << "namespace pc {\n"
+    << "namespace {\n"
+    << "constexpr int D = " << d << ";\n"
+    << "__device__ __forceinline__ float2 jit_eval_adjoint(const uint4 *P, const float *pool, float2 *R,\n"
+    << "    const PriceArgs &a, const Rng2 &g, bool live0, bool live1, const float (&Bm)[D * D],\n"
+    << "    const float (&S0)[D], const float (&Lm)[D * D], Tape &T, int &res) {\n"
+    << "#include \"pc_adjoint_state.inc\"\n"
+    << "  goto L0;\n";
+  for (size_t i = 0; i < n; ++i) {
+    const XInsn &I = p.code[i];
+    o << "L" << i << ": {\n"
+      << "  pc = " << i << ";\n"
+      << "  const uint4 I = " << insn_literal(I) << ";\n"
+      << "  const uint32_t op = " << hex(I.opa & 0xffu) << ";\n"
+      << "  const float kk = __uint_as_float(" << hex(I.b) << ");\n"
+      << "#include \"pc_adjoint_ops.inc\"\n";
+    std::vector<uint32_t> next = {uint32_t(i + 1), I.c, I.e, uint32_t(i + 2)};
+    for (size_t j = 0; j < next.size(); ++j) {
+      bool seen = false;
+      for (size_t q = 0; q < j; ++q) seen = seen || next[q] == next[j];
+      if (!seen && next[j] < n) o << "  if (pc == " << next[j] << ") goto L" << next[j] << ";\n";
+    }
+    o << "  res = tid;\n"
+      << "  return tos;\n"
+      << "}\n";
+  }
+  o << "}\n"
+    << "}  // namespace\n"
+    << "}  // namespace pc\n"
+    << "extern \"C\" __global__ void __launch_bounds__(" << kBlock
+    << ") pc_jit_adjoint(const __grid_constant__ pc::PriceArgs a, const pc::TapeArgs t) {\n"
+    << "  pc::adjoint_tiles<pc::D, " << (write ? "true" : "false") << ">(a, t, [&](const uint4 *P, const float *pool,\n"
+    << "      float2 *R, const pc::Rng2 &g, bool live0, bool live1, const float (&Bm)[pc::D * pc::D],\n"
+    << "      const float (&S0)[pc::D], const float (&Lm)[pc::D * pc::D], pc::Tape &T, int &res) {\n"
+    << "    return pc::jit_eval_adjoint(P, pool, R, a, g, live0, live1, Bm, S0, Lm, T, res); });\n"
+    << "}\n";
+  return o.str();
+}
+
 std::string generate_greeks(const Program &p, int d, bool write) {
   std::ostringstream o;
   const size_t n = p.code.size();
@@ -204,6 +252,7 @@ std::string generate_greeks(const Program &p, int d, bool write) {
 // Otherwise the generator is inlined at each reading instruction (out of
 // line beyond kInlineDateSites of them).
 std::string generate(const Program &p, int d, int kind) {
+  if (kind >= kJitAdjoint) return generate_adjoint(p, d, (kind & 1) != 0);
   if (kind >= kJitGreeks) return generate_greeks(p, d, (kind & 1) != 0);
   std::ostringstream o;
   const size_t n = p.code.size();
@@ -355,7 +404,8 @@ pc_status compile(const Program &p, int d, int kind, int block, int min_blocks, 
                          "sm_" + std::to_string(prop.major) + std::to_string(prop.minor) + "a", cubin);
   if (s != PC_OK) return s;
   CU(cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0), "module load");
-  cudaError_t e = cudaLibraryGetKernel(&kern, lib, kind >= kJitGreeks ? "pc_jit_greeks"
+  cudaError_t e = cudaLibraryGetKernel(&kern, lib, kind >= kJitAdjoint ? "pc_jit_adjoint"
+                                                    : kind >= kJitGreeks ? "pc_jit_greeks"
                                                     : kind >= kJitCv ? "pc_jit_cv" : "pc_jit_price");
   if (e != cudaSuccess) {
     cudaLibraryUnload(lib);
@@ -371,6 +421,10 @@ pc_status compile(const Program &p, int d, int kind, int block, int min_blocks, 
 namespace pc {
 
 bool jit_eligible(const pc_contract *k) { return k->prog.code.size() <= size_t(PC_JIT_MAX_INSNS); }
+
+bool adjoint_jit_eligible(const pc_contract *k) {
+  return jit_eligible(k) && date_sites(k->prog) <= kInlineTangentDateSites;
+}
 
 pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKernel_t &out, int min_blocks) {
   // the program's words: code, then pool bits
@@ -414,6 +468,11 @@ pc_status jit_kernel(const pc_contract *k, int d, int kind, int block, cudaKerne
 }
 
 namespace {
+const char *jit_entry_name(int kind) {
+  return kind >= kJitAdjoint ? "pc_jit_adjoint" : kind >= kJitGreeks ? "pc_jit_greeks"
+         : kind >= kJitCv ? "pc_jit_cv" : "pc_jit_price";
+}
+
 std::vector<uint32_t> program_words(const Program &p) {
   std::vector<uint32_t> words;
   words.reserve(p.code.size() * 4 + p.pool.size());
@@ -493,8 +552,7 @@ pc_status jit_compile_many(pc_ctx *c, const std::vector<JitRequest> &reqs) {
     E.block = m.r->block;
     E.min_blocks = m.r->min_blocks;
     CU(cudaLibraryLoadData(&E.lib, m.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0), "module load");
-    cudaError_t e = cudaLibraryGetKernel(&E.kernel, E.lib, E.kind >= kJitGreeks ? "pc_jit_greeks"
-                                                           : E.kind >= kJitCv ? "pc_jit_cv" : "pc_jit_price");
+    cudaError_t e = cudaLibraryGetKernel(&E.kernel, E.lib, jit_entry_name(E.kind));
     if (e != cudaSuccess) {
       cudaLibraryUnload(E.lib);
       return cuda_fail(e, "kernel lookup");
@@ -522,7 +580,8 @@ extern "C" pc_status pc_debug_jit_compile(const uint32_t *bytecode, size_t n_wor
   const int cvm = (kind - kJitCv) & 7;  // mode bits, with or without kCvWinRegs
   const bool cv_kind = kind >= kJitCv && kind < kJitCv + 16 && cvm != kCvWrite && cvm != (kCvWrite | kCvPilot) &&
                        cvm != (kCvWrite | kCvPilot | kCvGamma);
-  const bool greeks_kind = kind == kJitGreeks || kind == kJitGreeks + 1;
+  const bool greeks_kind = kind == kJitGreeks || kind == kJitGreeks + 1 || kind == kJitAdjoint ||
+                           kind == kJitAdjoint + 1;
   const bool price_kind = kind >= 0 && kind <= (kJitPriceWrite | kJitHbm | kJitWinRegs | kJitPairs2) &&
                           (!(kind & kJitPairs2) || (kind & (kJitWinRegs | kJitHbm)) == kJitWinRegs);
   if (!price_kind && !cv_kind && !greeks_kind)
@@ -548,7 +607,7 @@ extern "C" pc_status pc_debug_jit_source(const uint32_t *bytecode, size_t n_word
   const bool known = (kind >= 0 && kind <= (kJitPriceWrite | kJitHbm | kJitWinRegs | kJitPairs2) &&
                       (!(kind & kJitPairs2) || (kind & (kJitWinRegs | kJitHbm)) == kJitWinRegs)) ||
                      (kind >= kJitCv && kind < kJitCv + 16) ||
-                     kind == kJitGreeks || kind == kJitGreeks + 1;
+                     kind == kJitGreeks || kind == kJitGreeks + 1 || kind == kJitAdjoint || kind == kJitAdjoint + 1;
   if (!known) return fail(PC_EINVAL, "unknown kernel kind");
   Program p;
   std::string err;

@@ -143,3 +143,44 @@ def test_full_size_sampled_adjoint(eng):
             check_derivative(dS[sl, l], rS[:, l], marg, ("delta", l, off))
             check_derivative(dv[sl, l], rv[:, l], marg, ("vega", l, off))
     assert sums[-1] == n
+
+
+@pytest.mark.parametrize("name", GREEK_CASES)
+def test_specialised_adjoint_equals_interpreter(eng, name):
+    """The adjoint kernel compiled at run time for the program (pc_set_jit):
+    per-path value, deltas and vegas and the launch's sums bit for bit those
+    of the interpreting adjoint kernel (programs with many reading
+    instructions stay interpreted)."""
+    text, tp, spec, _ = CASES[name]
+    n, seed = 4096 + 21, 0x61 + len(name)
+    m, k = eng.model(spec), eng.contract(text, tp)
+    ref = adjoint_paths(m, k, n, seed, spec.d)
+    pc.pc_set_jit(eng.ctx, True)
+    try:
+        got = adjoint_paths(m, k, n, seed, spec.d)
+    finally:
+        pc.pc_set_jit(eng.ctx, False)
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(np.asarray(a), np.asarray(b))
+
+
+def test_specialised_adjoint_full_size():
+    """The sensitivities workload of 4 underlyings and 365 dates at 2^20
+    paths: the specialised adjoint's sums equal the interpreter's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    e = Engine()
+    try:
+        w = W.GREEKS["greeks_daily_barrier_4u_365d"]()
+        m, k = e.model(w.market), e.contract(w.il_text, w.tparams)
+        outs = []
+        for jit in (False, True):
+            pc.pc_set_jit(e.ctx, jit)
+            out = torch.zeros(2 * (1 + 2 * w.market.d) + 1, dtype=torch.float64, device="cuda")
+            pc.pc_greeks_adjoint_async(m, k, w.n_paths, 0, w.seed, 0, out.data_ptr())
+            torch.cuda.synchronize()
+            outs.append(out.cpu().numpy())
+        pc.pc_set_jit(e.ctx, False)
+        np.testing.assert_array_equal(outs[1], outs[0])
+    finally:
+        e.close()

@@ -31,7 +31,7 @@ def test_compile_errors_are_reported():
     assert e.value.name == "PC_EINVAL"
 
 
-@pytest.mark.parametrize("kind", [1, 2, 3, 4, 5, 12, 16, 16 + 2, 16 + 4, 16 + 6, 16 + 3, 24, 24 + 2, 24 + 6, 32, 33])
+@pytest.mark.parametrize("kind", [1, 2, 3, 4, 5, 12, 16, 16 + 2, 16 + 4, 16 + 6, 16 + 3, 24, 24 + 2, 24 + 6, 32, 33, 64, 65])
 def test_specialised_variants_compile(kind):
     """The per-path, HBM-window, register-window and four-paths-a-lane pricing
     variants, the control-variate kernel in each mode (second-order term,
@@ -44,7 +44,7 @@ def test_specialised_variants_compile(kind):
     assert pc.pc_debug_jit_compile(w, k, w_.tparams, 3, kind=kind) > 1000
 
 
-@pytest.mark.parametrize("kind,d", [(8, 1), (16 + 1, 3), (24 + 1, 3), (16, 4), (34, 1), (31, 1), (14, 1)])
+@pytest.mark.parametrize("kind,d", [(8, 1), (16 + 1, 3), (24 + 1, 3), (16, 4), (34, 1), (31, 1), (14, 1), (66, 1)])
 def test_unknown_kinds_are_refused(kind, d):
     w, k = pc.pc_assemble("(model 0 1)")
     with pytest.raises(pc.PcError) as e:
