@@ -95,6 +95,10 @@ struct CvTablesTc {
   size_t rows;
   float *tables, *delta0;
   int32_t *status;                      // |= 4 when a bounded wait expires
+  // failure test: the producer withholds the first weight chunk's copy, so
+  // the waits on it expire (after about 10 ms) and the kernel takes its
+  // abort path
+  int withhold;
 };
 bool cv_tables_tc_shape(int L, const int *wp);
 bool make_weight_map(CUtensorMap &m, const __nv_bfloat16 *w, int n_out, int n_in);

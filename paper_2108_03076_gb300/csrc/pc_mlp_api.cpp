@@ -365,8 +365,7 @@ int32_t *mlp_status_word(pc_mlp *N) { return N->dstatus; }
 // the products do not run on tcgen05 or the network's shape is outside the
 // kernel's (then the caller builds the tables with the layer products).
 bool mlp_cv_tables_tc(pc_mlp *N, size_t rows, float *tables, float *delta0, CvTablesTc &t) {
-  if (!N->tc_ok || N->gemm != PC_MLP_GEMM_AUTO || N->tc_withhold || !cv_tables_tc_shape(N->L, N->wp.data()))
-    return false;
+  if (!N->tc_ok || N->gemm != PC_MLP_GEMM_AUTO || !cv_tables_tc_shape(N->L, N->wp.data())) return false;
   std::memset(&t, 0, sizeof(t));
   t.L = N->L;
   for (int l = 0; l <= N->L; ++l) t.wp[l] = N->wp[l];
@@ -386,6 +385,7 @@ bool mlp_cv_tables_tc(pc_mlp *N, size_t rows, float *tables, float *delta0, CvTa
   t.tables = tables;
   t.delta0 = delta0;
   t.status = N->dstatus;
+  t.withhold = N->tc_withhold ? 1 : 0;
   return true;
 }
 

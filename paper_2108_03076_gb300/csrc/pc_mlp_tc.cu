@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t abuf = (su32(tc_smem_raw) + 1023u) & ~1023u, ring = abuf + kFzABytes;
   const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[kStages]);
   const uint32_t aready = su32(&bars[2 * kStages]), afull = aready + 8, done = aready + 16;
-  const long long lim = kWaitCycles;
+  const long long lim = t.withhold ? kTestWaitCycles : kWaitCycles;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(&tmem_slot)),
@@ -555,15 +555,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             ok = false;
             break;
           }
+          issued = q + 1;
+          if (t.withhold && q == 0) continue;  // failure test: chunk 0 never arrives
           mbar_expect_tx(full0 + 8 * s, bytes);
           tma_load_2d(ring + s * kFzStageBytes, &t.w[l], ch * kTcBK, 0, full0 + 8 * s);
-          issued = q + 1;
         }
       }
     }
     // the last kStages issued chunks' copies complete before the CTA exits
     for (uint32_t k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
-      if (!mbar_wait(full0 + 8 * (k % kStages), (k / kStages) & 1, lim)) atomicOr(t.status, 4);
+      if (!(t.withhold && k == 0) && !mbar_wait(full0 + 8 * (k % kStages), (k / kStages) & 1, lim))
+        atomicOr(t.status, 4);
   } else if (threadIdx.x == 32) {
     // MMA issuer; ph counts the layers issued (the aready / afull phases)
     uint32_t q = 0, ph = 0;

@@ -146,3 +146,31 @@ def test_tensor_core_bounded_wait_expiry(ctx):
         assert torch.equal(g0, g1)
     finally:
         pc.pc_mlp_destroy(net)
+
+
+def test_fused_table_build_bounded_wait_expiry(ctx):
+    """The one-launch hedge-table build (cv_tables_tc) with its producer
+    withholding the first weight chunk: every bounded wait expires (about
+    10 ms), the kernel returns, pc_cv_tables reports PC_ETIMEOUT; afterwards
+    the same build gives the tables it gave before, bit for bit."""
+    from paper_2108_03076_gb300 import learned_cv as L
+    w = W.worst_of_autocall()
+    s = w.market
+    model = pc.pc_model_create(ctx, s.S0, s.sigma, s.corr, s.r, s.days)
+    net = L.LearnedCV(ctx, seed=5)
+    try:
+        if not pc.pc_mlp_gemm_info(net.net):
+            pytest.skip("tcgen05 products not available")
+        _, t0 = net.tables(model)
+        ref = t0.cpu().numpy().copy()
+        pc.pc_debug_mlp_withhold_tma(net.net, True)
+        with pytest.raises(pc.PcError) as ei:
+            net.tables(model, out=t0)
+        assert ei.value.name == "PC_ETIMEOUT"
+        pc.pc_debug_mlp_withhold_tma(net.net, False)
+        _, t1 = net.tables(model, out=t0)
+        n = pc.pc_cv_table_size(pc.pc_cv_grid(model, 12, 4.5))
+        np.testing.assert_array_equal(t1.cpu().numpy()[:n].view(np.uint32), ref[:n].view(np.uint32))
+    finally:
+        net.close()
+        pc.pc_model_destroy(model)
